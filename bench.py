@@ -1,0 +1,344 @@
+#!/usr/bin/env python
+"""Throughput of the driven coronal MHD step on GB300: MHD cell-updates/s per
+RK3 step (cells x steps / time), FP32 path (FP32 state and stencils, FP64
+potential-field FFT and reductions) on the 256^3 bipole workload, with the
+FP64 path measured beside it.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
+
+Under torchrun (N > 1) every rank runs an independent replica of the
+workload (the single-GPU path is not split across GPUs); value = all cells
+updated by all ranks / max-over-ranks time.  --impl reference times the FP64
+CPU oracle (rank 0 only) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MHD cell-updates/s per RK step"
+UNIT = "cell-updates/s"
+WORDS_PER_CELL_STEP = 80  # algorithmic state words moved per cell per RK3 step
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--workload", default="bipoles40_256x256x256")
+    ap.add_argument("--stats-every", type=int, default=10)
+    ap.add_argument("--fp64-steps", type=int, default=3)
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_setup():
+    import torch
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+    elif torch.cuda.is_available():
+        torch.cuda.set_device(local)
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, ws):
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+class ClockSampler:
+    """nvidia-smi samples every 200 ms while the timed region runs."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.idx)], stdout=self.fh,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, mx, reasons = [], [], set()
+        names = ["active", "hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names[1:], parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return None
+
+
+def rk_traffic_bytes():
+    """Per-launch DRAM traffic of the RK kernel from the committed ncu summary,
+    valid only if the kernel source is unchanged since the capture."""
+    path = os.path.join(ROOT, "profiles", "rk_traffic.txt")
+    src = os.path.join(ROOT, "paper_1908_08557_gb300", "csrc", "mhd_rk.cu")
+    try:
+        kv = {}
+        for line in open(path):
+            if line.strip() and not line.startswith("#"):
+                k, v = line.split(None, 1)
+                kv[k] = v.strip()
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        if kv.get("kernel_source_sha") != sha:
+            return None
+        return float(kv["bytes_per_launch_scaled"])
+    except Exception:
+        return None
+
+
+def cpu_oracle_sample(nx=256, ny=256, nz=32, steps=1):
+    """One RK3 step of the FP64 oracle on a 256 x 256 x 32 slab of the same
+    recipe (bipoles, solenoidal driver); returns (cell-updates/s, seconds)."""
+    import inputs
+    import oracle
+    case = inputs.make_box(nx, ny, nz, seed=0, magnetogram="bipoles", n_mag=40, driver="solenoidal")
+    axt, ayt = oracle.a_target(case.params, case.bz)
+    u = oracle.to_padded(case.state)
+    t0 = time.perf_counter()
+    oracle.run(case.params, u, case.lnrho0, axt, ayt, case.v0, case.v1, case.t0, case.t1, 0.0, steps)
+    dt = time.perf_counter() - t0
+    return nx * ny * nz * steps / dt, dt
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    nx, ny, nz = 128, 128, 16
+    for _ in range(args.warmup):
+        cpu_oracle_sample(nx, ny, nz, 1)
+    times = []
+    for _ in range(args.steps):
+        _, dt = cpu_oracle_sample(nx, ny, nz, 1)
+        times.append(dt)
+    tot = sum(times)
+    val = nx * ny * nz * args.steps / tot
+    sample = f"one RK3 step of a {nx}x{ny}x{nz} box of the same recipe per step (FP64 oracle, OpenMP)"
+    line = {"metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": args.workload},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_native(args, ws, rank, local):
+    import numpy as np
+    import torch
+
+    import inputs
+    from paper_1908_08557_gb300 import Simulation
+    from paper_1908_08557_gb300.build import build
+    if rank == 0:
+        build()
+    barrier(ws)
+    build()  # no-op when up to date
+
+    case = inputs.make_case(args.workload)
+    p = case.params
+    cells = p["nx"] * p["ny"] * p["nz"]
+    dev = torch.device("cuda", local)
+
+    def make(precision, stats_every):
+        dt = torch.float32 if precision == 32 else torch.float64
+        sim = Simulation(p, torch.tensor(case.state, dtype=dt, device=dev), case.lnrho0, case.lnT0,
+                         precision=precision, stats_every=stats_every, device=str(dev))
+        sim.set_driver(torch.tensor(case.bz, dtype=dt, device=dev), torch.tensor(case.v0, dtype=dt, device=dev),
+                       torch.tensor(case.v1, dtype=dt, device=dev), case.t0, case.t1)
+        return sim
+
+    sim = make(32, args.stats_every)
+    stream = sim.stream
+    sim.step(args.warmup)
+    torch.cuda.synchronize()
+    barrier(ws)
+    torch.cuda.synchronize()
+    clk = ClockSampler(local)
+    clk.start()
+    n0 = sim.launch_count()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    sim.step(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    launches = sim.launch_count() - n0
+    clocks = clk.stop()
+    barrier(ws)
+    ms_max = max_over_ranks(ms, ws)
+    value = ws * cells * args.steps / (ms_max / 1e3)
+
+    # per-kernel-class timing on the library's stream (separate pass)
+    sim.profile(True)
+    sim.step(args.steps)
+    prof = sim.read_profile()
+    sim.profile(False)
+    rk_ms, rk_n = prof["rk"]
+    esz = 4
+    alg_bytes_per_launch = WORDS_PER_CELL_STEP * cells * esz / 3.0
+    achieved = alg_bytes_per_launch / (rk_ms / rk_n / 1e3) / 1e9
+    peaks = measured_peaks()
+    peak = peaks["hbm_gbs"] if peaks and "hbm_gbs" in peaks else 6800.0
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": rk_traffic_bytes(), "kernel": "rk (fused RHS + RK update)",
+                "peak_source": "measured" if peaks else "fallback",
+                "alg_bytes_per_launch": alg_bytes_per_launch, "avg_launch_ms": rk_ms / rk_n,
+                "class_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()}}
+
+    # end to end through the C ABI with host buffers: each step uploads its
+    # driver snapshot (B_z, v0, v1) from pinned host memory and reads back
+    # the time and time step
+    e2e = None
+    if not args.no_e2e:
+        pin = lambda a: torch.tensor(a, dtype=torch.float32).pin_memory().numpy()
+        hb, hv0, hv1 = pin(case.bz), pin(case.v0), pin(case.v1)
+        for _ in range(2):
+            sim.set_driver(hb, hv0, hv1, case.t0, case.t1)
+            sim.step(1)
+            sim.time()
+        barrier(ws)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            sim.set_driver(hb, hv0, hv1, case.t0, case.t1)
+            sim.step(1)
+            sim.time()
+        el = time.perf_counter() - t0
+        el = max_over_ranks(el, ws)
+        e2e = {"value": ws * cells * args.steps / el, "unit": UNIT,
+               "h2d_bytes_per_step": int(hb.nbytes + hv0.nbytes + hv1.nbytes), "d2h_bytes_per_step": 20}
+    sim.close()
+    del sim
+    torch.cuda.empty_cache()
+
+    fp64 = None
+    if not args.no_fp64:
+        s64 = make(64, args.stats_every)
+        s64.step(1)
+        torch.cuda.synchronize()
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        f0.record(s64.stream)
+        s64.step(args.fp64_steps)
+        f1.record(s64.stream)
+        torch.cuda.synchronize()
+        ms64 = max_over_ranks(f0.elapsed_time(f1), ws)
+        fp64 = {"value": ws * cells * args.fp64_steps / (ms64 / 1e3), "unit": UNIT,
+                "ms_per_step": ms64 / args.fp64_steps, "steps": args.fp64_steps,
+                "dtype": "f64"}
+        s64.close()
+        del s64
+        torch.cuda.empty_cache()
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        v, secs = cpu_oracle_sample()
+        cpu = {"value": v, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"one RK3 step of a 256x256x32 slab of the same recipe ({secs:.1f} s, FP64 oracle, OpenMP)"}
+
+    if rank == 0:
+        state_gb = 3 * 8 * (p["nx"] + 8) * (p["ny"] + 6) * (p["nz"] + 6) * 4 / 1e9
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": args.workload, "nx": p["nx"], "ny": p["ny"], "nz": p["nz"],
+                           "precision": "fp32 state and stencils; fp64 FFT, CFL and diagnostics",
+                           "stats_every": args.stats_every,
+                           "l2": f"working set {state_gb:.2f} GB > 129 MB L2, no flush",
+                           "parallelism": f"replicas x{ws}"},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+                "clocks": clocks, "fp64": fp64}
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    ws, rank, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+    else:
+        run_native(args, ws, rank, local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,211 @@
+/*
+ * mhd.h -- C ABI of the GB300 driven coronal MHD library (libmhd.so).
+ *
+ * One low-storage third-order Runge-Kutta step of compressible resistive MHD
+ * in vector-potential form with state (A, u, ln rho, ln T), sixth-order
+ * centred differences, and the boundary conditions of Bourdin (2019),
+ * "Driving solar coronal MHD simulations on high-performance computers":
+ * photospheric nudging toward a magnetogram and a driver velocity
+ * (Sect. 2.1, 2.3, Eq. 5), inverted potential-field extrapolation below the
+ * photosphere (Sect. 2.4), hydrostatic / symmetric atmospheric ghosts
+ * (Sect. 2.5 Eq. 8, Sect. 4.1 Eqs. 11, 13), regular potential-field
+ * extrapolation above the top (Sect. 4.2, Eqs. 16-17) and the swamp layer
+ * (Sect. 4.3, Eqs. 18-20).
+ *
+ * Conventions shared by every entry point
+ * - Fields, in this order: Ax, Ay, Az, ux, uy, uz, ln rho, ln T (the
+ *   variables the paper's snapshots hold, Sect. 5.3).
+ * - State arrays are interior-only, C order with x fastest:
+ *   [field][z][y][x] = [8][nz][ny][nx]; 2D arrays are [ny][nx]; driver
+ *   velocities are [2][ny][nx] (vx, vy).  z index 0 is the photosphere.
+ * - Element type = the handle's precision (float for 32, double for 64).
+ * - `mem` selects where a caller array lives: MHD_MEM_DEVICE (device pointer,
+ *   copied device-to-device on the handle's stream) or MHD_MEM_HOST (host
+ *   pointer; the call copies and returns when the host buffer may be reused).
+ * - The library never allocates device memory: the caller passes one
+ *   workspace of mhd_workspace_bytes() bytes (256-byte aligned) and owns it;
+ *   mhd_destroy() frees only host-side bookkeeping.
+ * - Every launch goes to the stream given to mhd_create(); calls are
+ *   asynchronous unless stated otherwise.
+ * - Return value: MHD_OK (0) or a negative MHD_ERR_* code; the message is
+ *   available from mhd_last_error().  Argument errors are reported before any
+ *   launch.  A non-finite value met by the time-step reduction sets a device
+ *   flag: from then on every kernel of the handle returns without work, and
+ *   the next synchronising call returns MHD_ERR_NONFINITE.
+ */
+#ifndef MHD_H
+#define MHD_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MHD_OK 0
+#define MHD_ERR_ARG (-1)        /* invalid argument, shape or pointer        */
+#define MHD_ERR_WORKSPACE (-2)  /* workspace missing, misaligned or too small */
+#define MHD_ERR_CUDA (-3)       /* a CUDA runtime call failed                 */
+#define MHD_ERR_NONFINITE (-4)  /* NaN/Inf detected in the state              */
+#define MHD_ERR_UNSUPPORTED (-5)/* valid but not built (e.g. FFT size)        */
+
+#define MHD_MEM_DEVICE 0
+#define MHD_MEM_HOST 1
+
+#define MHD_NFIELD 8
+#define MHD_NGHOST 3
+
+/* Scheme parameters, code units (mu0 = 1, p = rho T).  Geometry: interior
+ * nx x ny x nz cells, periodic in x and y; nx, ny powers of two in [8, 1024]
+ * when bc_z = 0 (the potential-field boundary needs the FFT), any size >= 4
+ * otherwise; nz >= 7. */
+typedef struct mhd_params {
+  int nx, ny, nz;
+  int precision;       /* 32 or 64: state storage and stencil arithmetic */
+  int bc_z;            /* 0: the paper's boundaries; 1: periodic in z (tests) */
+  int stats_every;     /* compute diagnostics every n steps (0: never) */
+  double dx, dy, dz;
+  double gamma;        /* ratio of specific heats */
+  double gz;           /* gravity, signed (< 0 points down) */
+  double nu;           /* kinematic viscosity */
+  double eta;          /* magnetic diffusivity */
+  double kappa0;       /* Spitzer coefficient, kappa = kappa0 T^{5/2} */
+  double diff_rho;     /* mass diffusivity D_rho (Sect. 2.5) */
+  double eta_swamp;    /* swamp magnetic diffusivity eta_s (Eq. 18) */
+  double chi_swamp;    /* swamp heat diffusivity chi_s on ln T (Eq. 19) */
+  double diffrho_swamp;/* swamp mass diffusivity chi_rho on ln rho (Eq. 20) */
+  double z_swamp_start, z_swamp_end; /* cubic weight from 0 to 1 (Sect. 4.3) */
+  double tau_u;        /* velocity nudging rate (Eq. 5) */
+  double tau_A;        /* magnetic nudging rate at the photosphere (Sect. 2.1) */
+  double t_ramp;       /* linear driver switch-on time (Sect. 2.3); <= 0: off */
+  double f_pfe_bottom; /* contrast-growth factor of the inverted extrapolation (0.2) */
+  double c_adv, c_diff;/* CFL coefficients */
+  double dt_fixed;     /* > 0: fixed time step instead of the CFL rule */
+  double bext[3];      /* uniform external field added to curl A */
+} mhd_params;
+
+/* Diagnostics of the ghost-filled state at time t (FP64 sums). */
+typedef struct mhd_stats {
+  double t, dt;        /* time of the state; last time step taken */
+  double e_kin;        /* sum rho u^2 / 2 dV */
+  double e_mag;        /* sum B^2 / 2 dV */
+  double e_th;         /* sum rho T / (gamma - 1) dV */
+  double mass;         /* sum rho dV */
+  double flux_net;     /* sum B_z(z = 0) dx dy (flux balance, Sect. 2.1) */
+  double flux_abs;     /* sum |B_z(z = 0)| dx dy */
+  double divb_max;     /* max |div B| (zero for B = curl A, Eq. 6) */
+  long long step;      /* number of RK steps taken */
+  int nonfinite;       /* nonzero once a NaN/Inf was met */
+  int pad_;
+} mhd_stats;
+
+typedef struct mhd_ctx* mhd_handle;
+
+/* Bytes of device workspace a handle with these parameters needs
+ * (0 if the parameters are invalid). */
+size_t mhd_workspace_bytes(const mhd_params* p);
+
+/* Create a handle.  workspace: caller-owned device memory of at least
+ * mhd_workspace_bytes(p) bytes, 256-byte aligned, kept alive until
+ * mhd_destroy.  init_state: [8][nz][ny][nx] initial state (mem selects host or
+ * device).  lnrho0: host array of nz + 6 doubles, the initial ln rho profile
+ * rho0(z) at z indices -3 .. nz+2; the three values below the photosphere are
+ * the fixed density ghosts (Sect. 2.5, 'fg').  lnT0: host array of nz + 6
+ * doubles, the initial ln T stratification T0(z) (Sect. 3.1), or NULL to use
+ * the layer means of init_state.  ln rho and ln T are stored as perturbations
+ * about these FP64 profiles (the equations are unchanged; FP32 rounding then
+ * scales with the perturbation).  The stateful horizontal-velocity ghost
+ * layers below the photosphere (Eq. 5 acts on j in {0,-1,-2,-3}) start equal
+ * to the photospheric layer.  stream: a cudaStream_t (NULL: the legacy default
+ * stream).  Synchronises the stream before returning. */
+int mhd_create(const mhd_params* p, void* workspace, size_t ws_bytes,
+               const void* init_state, int mem, const double* lnrho0,
+               const double* lnT0, void* stream, mhd_handle* out);
+
+/* Set the photospheric driver (Sect. 2.1, 2.3): the target magnetogram
+ * bz [ny][nx] (flux balanced by the caller) and two velocity snapshots
+ * v0, v1 [2][ny][nx] taken at times t0 < t1, interpolated linearly in time and
+ * multiplied by the switch-on ramp.  The vector potential of bz (Eq. 7, Weyl
+ * gauge, A_z = 0) is computed here with the FP64 FFT.  Must be called before
+ * the first mhd_step. */
+int mhd_set_driver(mhd_handle h, const void* bz, const void* v0,
+                   const void* v1, double t0, double t1, int mem);
+
+/* Advance the state by nsteps full RK3 steps (three substeps each: ghost
+ * fill, potential-field FFT, fused right-hand side + RK update; the time step
+ * from the FP64 CFL reduction at the first substep).  Asynchronous. */
+int mhd_step(mhd_handle h, int nsteps);
+
+/* Copy the interior of one field (0..7) or of all fields (-1) into dst
+ * ([nz][ny][nx] or [8][nz][ny][nx]).  With MHD_MEM_HOST the call
+ * synchronises the stream. */
+int mhd_read(mhd_handle h, int field, void* dst, int mem);
+
+/* Copy the whole state into the handle (same layout as init_state); the
+ * stateful velocity ghosts are reset to the photospheric layer. */
+int mhd_write(mhd_handle h, const void* src, int mem);
+
+/* Synchronise the stream and return the diagnostics of the last step that
+ * computed them (stats_every), plus time, dt and step count. */
+int mhd_read_stats(mhd_handle h, mhd_stats* out);
+
+/* Synchronise and return the current time and the last time step. */
+int mhd_get_time(mhd_handle h, double* t, double* dt);
+
+void mhd_destroy(mhd_handle h);
+
+/* Message of the last error of this handle (or of the last failed
+ * mhd_create when h is NULL).  Never NULL. */
+const char* mhd_last_error(mhd_handle h);
+
+/* ---- diagnostics and kernel-level entry points (used by the tests) ---- */
+
+/* Fill every ghost cell of the current state (rims, bottom/top rules and the
+ * potential-field ghosts), as the first substep does. */
+int mhd_fill_ghosts(mhd_handle h);
+
+/* Copy the padded state (which = 0) or the RK accumulator (which = 1) as
+ * [8][nz+6][ny+6][nx+6] (x fastest, ghosts included) into dst. */
+int mhd_read_padded(mhd_handle h, int which, void* dst, int mem);
+
+/* Evaluate the right-hand side of the current (ghost-filled) state at time t
+ * and copy it as [8][nz+6][ny+6][nx+6] into dst (cells that carry no state
+ * are zero).  Uses the accumulator buffer as scratch. */
+int mhd_eval_rhs(mhd_handle h, double t, void* dst, int mem);
+
+/* CFL time step of the current ghost-filled state (synchronising). */
+int mhd_compute_dt(mhd_handle h, double* dt);
+
+/* Diagnostics of the current ghost-filled state (synchronising). */
+int mhd_compute_stats(mhd_handle h, mhd_stats* out);
+
+/* Copy the vector potential of the driver magnetogram, A_x then A_y, as
+ * [2][ny][nx] into dst. */
+int mhd_read_target(mhd_handle h, void* dst, int mem);
+
+/* ---- instrumentation ---- */
+
+/* Kernel classes timed by the profiler. */
+#define MHD_KC_GHOST 0   /* pointwise ghost rules (and periodic copies)   */
+#define MHD_KC_PFE 1     /* potential-field FFT, three kernels             */
+#define MHD_KC_CFL 2     /* time-step reduction, two kernels               */
+#define MHD_KC_STATS 3   /* diagnostics reduction, two kernels             */
+#define MHD_KC_RK 4      /* fused right-hand side + RK update              */
+#define MHD_NKC 5
+
+/* enable != 0: from now on bracket every kernel class launched by mhd_step
+ * with CUDA events on the handle's stream; enable = 0 stops recording. */
+int mhd_profile(mhd_handle h, int enable);
+
+/* Synchronise, then return per class the summed event time in ms and the
+ * number of kernel launches recorded since profiling was enabled, and reset
+ * the record.  ms and launches point to MHD_NKC entries each. */
+int mhd_read_profile(mhd_handle h, double* ms, long long* launches);
+
+/* Number of kernels this handle has launched since mhd_create. */
+long long mhd_launch_count(mhd_handle h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MHD_H */

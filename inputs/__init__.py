@@ -235,6 +235,7 @@ class Case:
     params: Dict
     state: np.ndarray          # (8, nz, ny, nx) interior, float64
     lnrho0: np.ndarray         # (nz + 6,) k = -3 .. nz+2
+    lnT0: np.ndarray           # (nz + 6,) initial ln T stratification
     bz: np.ndarray             # (ny, nx) photospheric target
     v0: np.ndarray             # (2, ny, nx) driver snapshot at t0
     v1: np.ndarray             # (2, ny, nx) driver snapshot at t1
@@ -264,7 +265,7 @@ def make_box(nx, ny, nz, seed=0, magnetogram="spots", n_mag=4, sigma=3.0,
     st[0], st[1], st[2] = ax, ay, az
     st[6] = lnrho0[NGHOST:NGHOST + nz, None, None]
     st[7] = lnT0[NGHOST:NGHOST + nz, None, None]
-    return Case(name or f"box_{nx}x{ny}x{nz}", p, st, lnrho0, bz, v0, v1, 0.0,
+    return Case(name or f"box_{nx}x{ny}x{nz}", p, st, lnrho0, lnT0, bz, v0, v1, 0.0,
                 float(t1), nsteps)
 
 

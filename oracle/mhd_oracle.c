@@ -128,13 +128,15 @@ static void dft_axis(int n, int count, int stride_elem, int stride_line,
                      double* re, double* im, int sign) {
   double* cr = (double*)malloc(sizeof(double) * n);
   double* ci = (double*)malloc(sizeof(double) * n);
-  double* tr = (double*)malloc(sizeof(double) * n);
-  double* ti = (double*)malloc(sizeof(double) * n);
   for (int r = 0; r < n; ++r) {
     cr[r] = cos(2.0 * M_PI * (double)r / (double)n);
     ci[r] = (double)sign * sin(2.0 * M_PI * (double)r / (double)n);
   }
+  /* lines are independent */
+#pragma omp parallel for schedule(static)
   for (int l = 0; l < count; ++l) {
+    double* tr = (double*)malloc(sizeof(double) * n);
+    double* ti = (double*)malloc(sizeof(double) * n);
     double* xr = re + (size_t)l * stride_line;
     double* xi = im + (size_t)l * stride_line;
     for (int m = 0; m < n; ++m) {
@@ -152,8 +154,10 @@ static void dft_axis(int n, int count, int stride_elem, int stride_line,
       xr[(size_t)m * stride_elem] = tr[m];
       xi[(size_t)m * stride_elem] = ti[m];
     }
+    free(tr);
+    free(ti);
   }
-  free(cr); free(ci); free(tr); free(ti);
+  free(cr); free(ci);
 }
 
 /* forward (sign=-1) or unnormalised inverse (sign=+1) 2D DFT of ny x nx */

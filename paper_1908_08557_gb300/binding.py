@@ -1,0 +1,300 @@
+"""Thin ctypes binding of libmhd (include/mhd.h): argument marshalling only.
+
+Every step of the method runs inside the CUDA library; this module converts
+Python arguments (torch tensors on the GPU, or numpy arrays on the host) into
+the pointers, sizes and flags of the C ABI.  Device memory (the one
+workspace) comes from PyTorch's allocator; the library itself allocates none.
+There is no CPU fallback: if libmhd.so is missing or cannot be loaded, the
+calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Dict, Optional
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libmhd.so")
+
+MHD_OK = 0
+MHD_ERR_ARG = -1
+MHD_ERR_WORKSPACE = -2
+MHD_ERR_CUDA = -3
+MHD_ERR_NONFINITE = -4
+MHD_ERR_UNSUPPORTED = -5
+MHD_MEM_DEVICE = 0
+MHD_MEM_HOST = 1
+NFIELD = 8
+NGHOST = 3
+
+EXPORTED = ("mhd_workspace_bytes", "mhd_create", "mhd_set_driver", "mhd_step",
+            "mhd_read", "mhd_write", "mhd_read_stats", "mhd_get_time",
+            "mhd_destroy", "mhd_last_error", "mhd_fill_ghosts",
+            "mhd_read_padded", "mhd_eval_rhs", "mhd_compute_dt",
+            "mhd_compute_stats", "mhd_read_target", "mhd_profile",
+            "mhd_read_profile", "mhd_launch_count")
+KERNEL_CLASSES = ("ghost", "pfe", "cfl", "stats", "rk")
+
+
+class MHDError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"libmhd error {code}: {msg}")
+        self.code = code
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("precision", ctypes.c_int), ("bc_z", ctypes.c_int),
+                ("stats_every", ctypes.c_int),
+                ("dx", ctypes.c_double), ("dy", ctypes.c_double), ("dz", ctypes.c_double),
+                ("gamma", ctypes.c_double), ("gz", ctypes.c_double),
+                ("nu", ctypes.c_double), ("eta", ctypes.c_double),
+                ("kappa0", ctypes.c_double), ("diff_rho", ctypes.c_double),
+                ("eta_swamp", ctypes.c_double), ("chi_swamp", ctypes.c_double),
+                ("diffrho_swamp", ctypes.c_double),
+                ("z_swamp_start", ctypes.c_double), ("z_swamp_end", ctypes.c_double),
+                ("tau_u", ctypes.c_double), ("tau_A", ctypes.c_double),
+                ("t_ramp", ctypes.c_double), ("f_pfe_bottom", ctypes.c_double),
+                ("c_adv", ctypes.c_double), ("c_diff", ctypes.c_double),
+                ("dt_fixed", ctypes.c_double), ("bext", ctypes.c_double * 3)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("t", ctypes.c_double), ("dt", ctypes.c_double),
+                ("e_kin", ctypes.c_double), ("e_mag", ctypes.c_double),
+                ("e_th", ctypes.c_double), ("mass", ctypes.c_double),
+                ("flux_net", ctypes.c_double), ("flux_abs", ctypes.c_double),
+                ("divb_max", ctypes.c_double), ("step", ctypes.c_longlong),
+                ("nonfinite", ctypes.c_int), ("pad_", ctypes.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad_"}
+
+
+_lib = None
+
+
+def load(path: Optional[str] = None):
+    """Load libmhd.so (build it first with paper_1908_08557_gb300.build)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise RuntimeError(f"libmhd.so not found at {p}: run __graft_entry__.build() "
+                           "(the CUDA library is required; there is no fallback)")
+    lib = ctypes.CDLL(p)
+    vp, i, d, sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_size_t
+    P = ctypes.POINTER(Params)
+    lib.mhd_workspace_bytes.argtypes = [P]
+    lib.mhd_workspace_bytes.restype = sz
+    dpp = ctypes.POINTER(ctypes.c_double)
+    lib.mhd_create.argtypes = [P, vp, sz, vp, i, dpp, dpp, vp, ctypes.POINTER(vp)]
+    lib.mhd_set_driver.argtypes = [vp, vp, vp, vp, d, d, i]
+    lib.mhd_step.argtypes = [vp, i]
+    lib.mhd_read.argtypes = [vp, i, vp, i]
+    lib.mhd_write.argtypes = [vp, vp, i]
+    lib.mhd_read_stats.argtypes = [vp, ctypes.POINTER(Stats)]
+    lib.mhd_get_time.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
+    lib.mhd_destroy.argtypes = [vp]
+    lib.mhd_destroy.restype = None
+    lib.mhd_last_error.argtypes = [vp]
+    lib.mhd_last_error.restype = ctypes.c_char_p
+    lib.mhd_fill_ghosts.argtypes = [vp]
+    lib.mhd_read_padded.argtypes = [vp, i, vp, i]
+    lib.mhd_eval_rhs.argtypes = [vp, d, vp, i]
+    lib.mhd_compute_dt.argtypes = [vp, ctypes.POINTER(ctypes.c_double)]
+    lib.mhd_compute_stats.argtypes = [vp, ctypes.POINTER(Stats)]
+    lib.mhd_read_target.argtypes = [vp, vp, i]
+    lib.mhd_profile.argtypes = [vp, i]
+    lib.mhd_read_profile.argtypes = [vp, ctypes.POINTER(ctypes.c_double),
+                                     ctypes.POINTER(ctypes.c_longlong)]
+    lib.mhd_launch_count.argtypes = [vp]
+    lib.mhd_launch_count.restype = ctypes.c_longlong
+    for name in EXPORTED:
+        if name not in ("mhd_workspace_bytes", "mhd_destroy", "mhd_last_error",
+                        "mhd_launch_count"):
+            getattr(lib, name).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def make_params(p: Dict, precision: int = 32, stats_every: int = 0) -> Params:
+    q = Params()
+    q.nx, q.ny, q.nz = int(p["nx"]), int(p["ny"]), int(p["nz"])
+    q.precision = int(precision)
+    q.bc_z = int(p.get("bc_z", 0))
+    q.stats_every = int(stats_every)
+    for k in ("dx", "dy", "dz", "gamma", "gz", "nu", "eta", "kappa0", "diff_rho",
+              "eta_swamp", "chi_swamp", "diffrho_swamp", "z_swamp_start",
+              "z_swamp_end", "tau_u", "tau_A", "t_ramp", "f_pfe_bottom", "c_adv",
+              "c_diff", "dt_fixed"):
+        setattr(q, k, float(p[k]))
+    q.bext[0], q.bext[1], q.bext[2] = (float(p.get("bext_x", 0.0)),
+                                       float(p.get("bext_y", 0.0)),
+                                       float(p.get("bext_z", 0.0)))
+    return q
+
+
+def workspace_bytes(p: Dict, precision: int = 32) -> int:
+    q = make_params(p, precision)
+    return int(load().mhd_workspace_bytes(ctypes.byref(q)))
+
+
+class Simulation:
+    """One libmhd handle.  Arrays passed in may be torch CUDA tensors
+    (device pointers) or numpy arrays (host pointers); the element type must
+    match the precision (float32 / float64)."""
+
+    def __init__(self, params: Dict, init_state, lnrho0, lnT0=None, precision: int = 32,
+                 stats_every: int = 0, device: str = "cuda:0", stream=None):
+        import torch
+        self.lib = load()
+        self.params = dict(params)
+        self.precision = int(precision)
+        self.np_dtype = np.float32 if precision == 32 else np.float64
+        self.torch_dtype = torch.float32 if precision == 32 else torch.float64
+        self.device = torch.device(device)
+        self._p = make_params(params, precision, stats_every)
+        nbytes = int(self.lib.mhd_workspace_bytes(ctypes.byref(self._p)))
+        if nbytes == 0:
+            raise MHDError(MHD_ERR_ARG, "invalid parameters")
+        self.workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
+        base = self.workspace.data_ptr()
+        self._ws_ptr = (base + 255) // 256 * 256
+        self._ws_bytes = nbytes
+        if stream is None:
+            stream = torch.cuda.current_stream(self.device)
+        self.stream = stream
+        lr = np.ascontiguousarray(lnrho0, dtype=np.float64)
+        if lr.shape != (self._p.nz + 2 * NGHOST,):
+            raise ValueError("lnrho0 must have nz + 6 entries")
+        lt = None
+        if lnT0 is not None:
+            lt = np.ascontiguousarray(lnT0, dtype=np.float64)
+            if lt.shape != (self._p.nz + 2 * NGHOST,):
+                raise ValueError("lnT0 must have nz + 6 entries")
+        ptr, mem, keep = self._in(init_state, (NFIELD, self._p.nz, self._p.ny, self._p.nx))
+        h = ctypes.c_void_p()
+        rc = self.lib.mhd_create(ctypes.byref(self._p), ctypes.c_void_p(self._ws_ptr),
+                                 ctypes.c_size_t(nbytes), ptr, mem,
+                                 lr.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                 None if lt is None else lt.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                 ctypes.c_void_p(stream.cuda_stream), ctypes.byref(h))
+        del keep
+        if rc != MHD_OK:
+            raise MHDError(rc, self.lib.mhd_last_error(None).decode())
+        self.h = h
+
+    # -- marshalling --
+    def _in(self, a, shape):
+        import torch
+        if isinstance(a, torch.Tensor):
+            if not a.is_cuda:
+                a = a.numpy()
+            else:
+                if a.dtype != self.torch_dtype or tuple(a.shape) != tuple(shape) or not a.is_contiguous():
+                    raise ValueError(f"expected contiguous {self.torch_dtype} tensor of shape {shape}")
+                return ctypes.c_void_p(a.data_ptr()), MHD_MEM_DEVICE, a
+        arr = np.ascontiguousarray(a, dtype=self.np_dtype)
+        if arr.shape != tuple(shape):
+            raise ValueError(f"expected shape {shape}, got {arr.shape}")
+        return ctypes.c_void_p(arr.ctypes.data), MHD_MEM_HOST, arr
+
+    def _check(self, rc):
+        if rc != MHD_OK:
+            raise MHDError(rc, self.lib.mhd_last_error(self.h).decode())
+
+    # -- API --
+    def set_driver(self, bz, v0, v1, t0: float, t1: float):
+        n = (self._p.ny, self._p.nx)
+        b, mb, k1 = self._in(bz, n)
+        a0, m0, k2 = self._in(v0, (2,) + n)
+        a1, m1, k3 = self._in(v1, (2,) + n)
+        if not (mb == m0 == m1):
+            raise ValueError("bz, v0, v1 must all be host arrays or all device tensors")
+        self._check(self.lib.mhd_set_driver(self.h, b, a0, a1, float(t0), float(t1), mb))
+
+    def step(self, nsteps: int = 1):
+        self._check(self.lib.mhd_step(self.h, int(nsteps)))
+
+    def read(self, field: int = -1, out=None):
+        import torch
+        shape = ((NFIELD,) if field < 0 else ()) + (self._p.nz, self._p.ny, self._p.nx)
+        if out is None:
+            out = torch.empty(shape, dtype=self.torch_dtype, device=self.device)
+        if isinstance(out, np.ndarray):
+            self._check(self.lib.mhd_read(self.h, int(field), ctypes.c_void_p(out.ctypes.data), MHD_MEM_HOST))
+        else:
+            self._check(self.lib.mhd_read(self.h, int(field), ctypes.c_void_p(out.data_ptr()), MHD_MEM_DEVICE))
+        return out
+
+    def write(self, state):
+        ptr, mem, keep = self._in(state, (NFIELD, self._p.nz, self._p.ny, self._p.nx))
+        self._check(self.lib.mhd_write(self.h, ptr, mem))
+
+    def padded_shape(self):
+        return (NFIELD, self._p.nz + 2 * NGHOST, self._p.ny + 2 * NGHOST, self._p.nx + 2 * NGHOST)
+
+    def read_padded(self, which: int = 0) -> np.ndarray:
+        out = np.empty(self.padded_shape(), dtype=self.np_dtype)
+        self._check(self.lib.mhd_read_padded(self.h, int(which), ctypes.c_void_p(out.ctypes.data), MHD_MEM_HOST))
+        return out
+
+    def fill_ghosts(self):
+        self._check(self.lib.mhd_fill_ghosts(self.h))
+
+    def eval_rhs(self, t: float) -> np.ndarray:
+        out = np.empty(self.padded_shape(), dtype=self.np_dtype)
+        self._check(self.lib.mhd_eval_rhs(self.h, float(t), ctypes.c_void_p(out.ctypes.data), MHD_MEM_HOST))
+        return out
+
+    def compute_dt(self) -> float:
+        dt = ctypes.c_double()
+        self._check(self.lib.mhd_compute_dt(self.h, ctypes.byref(dt)))
+        return dt.value
+
+    def compute_stats(self) -> Dict:
+        s = Stats()
+        self._check(self.lib.mhd_compute_stats(self.h, ctypes.byref(s)))
+        return s.as_dict()
+
+    def read_stats(self) -> Dict:
+        s = Stats()
+        self._check(self.lib.mhd_read_stats(self.h, ctypes.byref(s)))
+        return s.as_dict()
+
+    def time(self):
+        t, dt = ctypes.c_double(), ctypes.c_double()
+        self._check(self.lib.mhd_get_time(self.h, ctypes.byref(t), ctypes.byref(dt)))
+        return t.value, dt.value
+
+    def read_target(self) -> np.ndarray:
+        out = np.empty((2, self._p.ny, self._p.nx), dtype=self.np_dtype)
+        self._check(self.lib.mhd_read_target(self.h, ctypes.c_void_p(out.ctypes.data), MHD_MEM_HOST))
+        return out
+
+    def profile(self, enable: bool = True):
+        self._check(self.lib.mhd_profile(self.h, 1 if enable else 0))
+
+    def read_profile(self) -> Dict:
+        ms = (ctypes.c_double * len(KERNEL_CLASSES))()
+        n = (ctypes.c_longlong * len(KERNEL_CLASSES))()
+        self._check(self.lib.mhd_read_profile(self.h, ms, n))
+        return {c: (ms[q], n[q]) for q, c in enumerate(KERNEL_CLASSES)}
+
+    def launch_count(self) -> int:
+        return int(self.lib.mhd_launch_count(self.h))
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.mhd_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

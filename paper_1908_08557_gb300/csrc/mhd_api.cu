@@ -1,0 +1,797 @@
+// mhd_api.cu -- the C ABI of libmhd (declared in include/mhd.h): handle,
+// workspace carving, host-built FFT tables, and the launch sequence of one RK3
+// step.  All device memory comes from the caller's workspace.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <vector>
+
+#include "../../include/mhd.h"
+#include "mhd_internal.h"
+
+using namespace mhd;
+
+struct mhd_ctx {
+  mhd_params p;
+  Layout L;
+  cudaStream_t st;
+  size_t esz;          // bytes per state element
+  char* ws;
+  size_t ws_bytes;
+  void* f[2];          // two state sets (ping-pong)
+  void* df;            // RK accumulator (also interior pack scratch)
+  int cur;
+  void* lnrho0;        // [3] fixed density ghosts below the photosphere (state precision)
+  void* wtab;          // [nz] swamp weight w(z_k)
+  void* wptab;         // [nz] dw/dz
+  void* bz;            // [ny][nx]
+  void* axt;           // [ny][nx]
+  void* ayt;
+  void* v0;            // [2][ny][nx]
+  void* v1;
+  double* red;         // reduction partials
+  StepState* ss;
+  void* bgtab;         // background tables: lbar, tbar [nz+6]; dl, d2l, dt, d2t [nz]
+  Background<float> bgf;
+  Background<double> bgd;
+  FFTPlan fp;
+  bool have_fft;
+  bool driver_set;
+  double t0, t1;
+  long long host_steps;
+  long long nlaunch;                  // kernels launched since create
+  bool prof;                          // bracket kernel classes with events
+  struct Ev { cudaEvent_t a, b; int cls; int nk; };
+  std::vector<Ev>* evs;
+  char err[512];
+};
+
+// bracket one kernel class launch (nk kernels) with events when profiling
+struct ClassTimer {
+  mhd_ctx* h;
+  mhd_ctx::Ev ev;
+  ClassTimer(mhd_ctx* h_, int cls, int nk) : h(h_) {
+    h->nlaunch += nk;
+    ev.cls = cls;
+    ev.nk = nk;
+    if (h->prof) {
+      cudaEventCreate(&ev.a);
+      cudaEventCreate(&ev.b);
+      cudaEventRecord(ev.a, h->st);
+    }
+  }
+  ~ClassTimer() {
+    if (h->prof) {
+      cudaEventRecord(ev.b, h->st);
+      h->evs->push_back(ev);
+    }
+  }
+};
+
+static char g_err[512] = "no error";
+
+static int fail(mhd_ctx* h, int code, const char* fmt, ...) {
+  char* buf = h ? h->err : g_err;
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, 512, fmt, ap);
+  va_end(ap);
+  return code;
+}
+
+static int cuda_check(mhd_ctx* h, cudaError_t e, const char* what) {
+  if (e == cudaSuccess) e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(h, MHD_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+  return MHD_OK;
+}
+
+static bool is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
+static int ilog2(int n) {
+  int l = 0;
+  while ((1 << l) < n) ++l;
+  return l;
+}
+
+static const char* check_params(const mhd_params* p) {
+  if (!p) return "params is NULL";
+  if (p->precision != 32 && p->precision != 64) return "precision must be 32 or 64";
+  if (p->nx < 4 || p->ny < 4) return "nx, ny must be >= 4";
+  if (p->nz < 7) return "nz must be >= 7";
+  if (p->bc_z != 0 && p->bc_z != 1) return "bc_z must be 0 or 1";
+  if (p->bc_z == 0) {
+    if (!is_pow2(p->nx) || !is_pow2(p->ny) || p->nx < 8 || p->ny < 8 || p->nx > 1024 || p->ny > 1024)
+      return "with bc_z = 0, nx and ny must be powers of two in [8, 1024]";
+  }
+  if (!(p->dx > 0) || !(p->dy > 0) || !(p->dz > 0)) return "grid spacings must be positive";
+  if (!(p->gamma > 1.0)) return "gamma must exceed 1";
+  if (p->stats_every < 0) return "stats_every must be >= 0";
+  if ((long long)p->nx * p->ny * p->nz > (1LL << 34)) return "grid too large";
+  if ((long long)((p->nx + 31) / 32) * ((p->ny + 7) / 8) > RED_BLOCKS_MAX)
+    return "horizontal grid too large for the reduction buffer (nx * ny <= 2^20)";
+  return nullptr;
+}
+
+// ---- workspace carving ------------------------------------------------------
+struct Carve {
+  size_t off = 0;
+  size_t take(size_t bytes) {
+    size_t o = off;
+    off += (bytes + 255) / 256 * 256;
+    return o;
+  }
+};
+
+struct Offsets {
+  size_t f0, f1, df, lnrho0, wtab, wptab, bz, axt, ayt, v0, v1, red, ss, bg;
+  size_t twx, twy, et, eb, ktx, kty, P, Q;
+  size_t total;
+};
+
+static Offsets plan_offsets(const mhd_params* p) {
+  Offsets o;
+  Carve c;
+  Layout L = make_layout(p->nx, p->ny, p->nz);
+  size_t es = p->precision == 64 ? 8 : 4;
+  size_t set = (size_t)NF * L.fs * es;
+  size_t n2 = (size_t)p->nx * p->ny;
+  o.f0 = c.take(set);
+  o.f1 = c.take(set);
+  o.df = c.take(set);
+  o.lnrho0 = c.take(8 * es);
+  o.wtab = c.take((size_t)p->nz * es);
+  o.wptab = c.take((size_t)p->nz * es);
+  o.bz = c.take(n2 * es);
+  o.axt = c.take(n2 * es);
+  o.ayt = c.take(n2 * es);
+  o.v0 = c.take(2 * n2 * es);
+  o.v1 = c.take(2 * n2 * es);
+  o.red = c.take((size_t)RED_BLOCKS_MAX * 8 * sizeof(double));
+  o.ss = c.take(sizeof(StepState));
+  o.bg = c.take((size_t)(6 * p->nz + 12) * es);
+  if (p->bc_z == 0) {
+    o.twx = c.take((size_t)p->nx * 16);
+    o.twy = c.take((size_t)p->ny * 16);
+    o.et = c.take(n2 * 8);
+    o.eb = c.take(n2 * 8);
+    o.ktx = c.take((size_t)p->nx * 8);
+    o.kty = c.take((size_t)p->ny * 8);
+    o.P = c.take(3 * n2 * 16);
+    o.Q = c.take(9 * n2 * 16);
+  } else {
+    o.twx = o.twy = o.et = o.eb = o.ktx = o.kty = o.P = o.Q = 0;
+  }
+  o.total = c.off;
+  return o;
+}
+
+extern "C" size_t mhd_workspace_bytes(const mhd_params* p) {
+  if (check_params(p)) return 0;
+  return plan_offsets(p).total;
+}
+
+// ---- helpers ----------------------------------------------------------------
+template <typename R>
+static Phys<R> make_phys(const mhd_params* p) {
+  Phys<R> ph;
+  ph.idx = (R)(1.0 / p->dx);
+  ph.idy = (R)(1.0 / p->dy);
+  ph.idz = (R)(1.0 / p->dz);
+  ph.idx2 = (R)(1.0 / (p->dx * p->dx));
+  ph.idy2 = (R)(1.0 / (p->dy * p->dy));
+  ph.idz2 = (R)(1.0 / (p->dz * p->dz));
+  ph.gamma = (R)p->gamma;
+  ph.gm1 = (R)(p->gamma - 1.0);
+  ph.gz = (R)p->gz;
+  ph.nu = (R)p->nu;
+  ph.eta = (R)p->eta;
+  ph.kappa0 = (R)p->kappa0;
+  ph.drho = (R)p->diff_rho;
+  ph.eta_s = (R)p->eta_swamp;
+  ph.chi_s = (R)p->chi_swamp;
+  ph.drho_s = (R)p->diffrho_swamp;
+  ph.tau_u = (R)p->tau_u;
+  ph.tau_A = (R)p->tau_A;
+  for (int c = 0; c < 3; ++c) ph.bext[c] = (R)p->bext[c];
+  ph.bcz = p->bc_z;
+  return ph;
+}
+
+// cubic swamp weight (Sect. 4.3): 0 below z_s, 1 above z_t, zero end slopes
+static void swamp_weight(const mhd_params* p, double z, double* w, double* wp) {
+  double zs = p->z_swamp_start, zt = p->z_swamp_end;
+  *w = 0.0;
+  *wp = 0.0;
+  if (!(zt > zs)) return;
+  double s = (z - zs) / (zt - zs);
+  if (s <= 0.0) return;
+  if (s >= 1.0) { *w = 1.0; return; }
+  *w = s * s * (3.0 - 2.0 * s);
+  *wp = 6.0 * s * (1.0 - s) / (zt - zs);
+}
+
+static void driver_weights(const mhd_ctx* h, double t, double* r, double* s) {
+  *r = 1.0;
+  if (h->p.t_ramp > 0.0) *r = fmin(fmax(t / h->p.t_ramp, 0.0), 1.0);
+  double q = h->t1 > h->t0 ? (t - h->t0) / (h->t1 - h->t0) : 0.0;
+  *s = fmin(fmax(q, 0.0), 1.0);
+}
+
+static cudaMemcpyKind kind_in(int mem) { return mem == MHD_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice; }
+static cudaMemcpyKind kind_out(int mem) { return mem == MHD_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice; }
+
+static int sync_status(mhd_ctx* h) {
+  int rc = cuda_check(h, cudaStreamSynchronize(h->st), "stream synchronize");
+  if (rc) return rc;
+  int nf = 0;
+  rc = cuda_check(h, cudaMemcpy(&nf, &h->ss->nonfinite, sizeof(int), cudaMemcpyDeviceToHost), "read status");
+  if (rc) return rc;
+  if (nf) return fail(h, MHD_ERR_NONFINITE, "non-finite value in the state (time stepping halted)");
+  return MHD_OK;
+}
+
+template <typename R> static const Background<R>& bgr(const mhd_ctx* h);
+template <> const Background<float>& bgr<float>(const mhd_ctx* h) { return h->bgf; }
+template <> const Background<double>& bgr<double>(const mhd_ctx* h) { return h->bgd; }
+
+// Background profiles of ln rho and ln T (FP64): the given initial profiles
+// (ln T: horizontal means of the initial state when no profile is given),
+// their sixth-order z derivatives at interior layers, and the constants the
+// ghost rules need in perturbation form.  Zero in the periodic-z geometry.
+template <typename R>
+static int upload_background(mhd_ctx* h, const double* lnrho0, const double* lnT0, const double* tmean) {
+  const mhd_params* p = &h->p;
+  const int nz = p->nz, n6 = nz + 2 * NG, kt = nz - 1;
+  std::vector<double> lb(n6, 0.0), tb(n6, 0.0);
+  if (p->bc_z == 0) {
+    for (int q = 0; q < n6; ++q) lb[q] = lnrho0[q];
+    if (lnT0) {
+      for (int q = 0; q < n6; ++q) tb[q] = lnT0[q];
+    } else {
+      for (int k = 0; k < nz; ++k) tb[k + NG] = tmean[k];
+      for (int m = 1; m <= NG; ++m) {
+        const int b1 = NG - m + 1, b0 = NG - m;
+        tb[b0] = tb[b1] + lb[b1] - lb[b0] - p->dz * p->gz / exp(tb[b1]);
+        tb[NG + kt + m] = tb[NG + kt - m];
+      }
+    }
+  }
+  static const double W1[4] = {0.0, 45.0 / 60.0, -9.0 / 60.0, 1.0 / 60.0};
+  static const double W2[4] = {-490.0 / 180.0, 270.0 / 180.0, -27.0 / 180.0, 2.0 / 180.0};
+  std::vector<R> tab((size_t)6 * nz + 12, R(0));
+  R* t_lb = tab.data();
+  R* t_tb = t_lb + n6;
+  R* t_dl = t_tb + n6;
+  R* t_d2l = t_dl + nz;
+  R* t_dt = t_d2l + nz;
+  R* t_d2t = t_dt + nz;
+  for (int q = 0; q < n6; ++q) { t_lb[q] = (R)lb[q]; t_tb[q] = (R)tb[q]; }
+  for (int k = 0; k < nz; ++k) {
+    const int c = k + NG;
+    double a1 = 0, a2 = W2[0] * lb[c], b1 = 0, b2 = W2[0] * tb[c];
+    for (int m = 1; m <= 3; ++m) {
+      a1 += W1[m] * (lb[c + m] - lb[c - m]);
+      a2 += W2[m] * (lb[c + m] + lb[c - m]);
+      b1 += W1[m] * (tb[c + m] - tb[c - m]);
+      b2 += W2[m] * (tb[c + m] + tb[c - m]);
+    }
+    t_dl[k] = (R)(a1 / p->dz);
+    t_d2l[k] = (R)(a2 / (p->dz * p->dz));
+    t_dt[k] = (R)(b1 / p->dz);
+    t_d2t[k] = (R)(b2 / (p->dz * p->dz));
+  }
+  Background<R> bg;
+  bg.lbar = (const R*)h->bgtab;
+  bg.tbar = bg.lbar + n6;
+  bg.dl = bg.tbar + n6;
+  bg.d2l = bg.dl + nz;
+  bg.dt = bg.d2l + nz;
+  bg.d2t = bg.dt + nz;
+  for (int m = 0; m <= NG; ++m) { bg.cb[m] = R(0); bg.ctT[m] = R(0); bg.ctL[m] = R(0); }
+  for (int m = 1; m <= NG; ++m) {
+    const int b1 = NG - m + 1, b0 = NG - m;
+    bg.cb[m] = (R)(tb[b1] - tb[b0] + lb[b1] - lb[b0]);
+    bg.ctT[m] = (R)(tb[NG + kt - m] - tb[NG + kt + m]);
+    bg.ctL[m] = (R)(lb[NG + kt - m] - lb[NG + kt + m]);
+  }
+  if (sizeof(R) == 8) h->bgd = *(Background<double>*)&bg; else h->bgf = *(Background<float>*)&bg;
+  return cuda_check(h, cudaMemcpy(h->bgtab, tab.data(), tab.size() * sizeof(R), cudaMemcpyHostToDevice),
+                    "upload background");
+}
+
+// ---- launch sequence ----------------------------------------------------------
+template <typename R>
+static void ghost_fill(mhd_ctx* h, R* f) {
+  Phys<R> ph = make_phys<R>(&h->p);
+  {
+    ClassTimer ct(h, MHD_KC_GHOST, 1);
+    launch_bc<R>(h->L, ph, bgr<R>(h), f, (R)h->p.dz, h->ss, h->st);
+  }
+  if (h->p.bc_z == 0) {
+    ClassTimer ct(h, MHD_KC_PFE, 3);
+    launch_pfe<R>(h->fp, h->L, f, h->ss, h->st);
+  }
+}
+
+static double inv2sum(const mhd_params* p) {
+  return 1.0 / (p->dx * p->dx) + 1.0 / (p->dy * p->dy) + 1.0 / (p->dz * p->dz);
+}
+
+template <typename R>
+static void run_stats(mhd_ctx* h, R* f) {
+  Phys<R> ph = make_phys<R>(&h->p);
+  ClassTimer ct(h, MHD_KC_STATS, 2);
+  int nb = launch_stats_partial<R>(h->L, ph, bgr<R>(h), f, h->red, h->ss, h->st);
+  launch_stats_finalize(h->red, nb, h->ss, h->p.dx * h->p.dy * h->p.dz, h->p.dx * h->p.dy, h->st);
+}
+
+template <typename R>
+static void run_step(mhd_ctx* h, bool stats) {
+  Phys<R> ph = make_phys<R>(&h->p);
+  Driver drv{h->axt, h->ayt, h->v0, h->v1};
+  for (int sub = 0; sub < 3; ++sub) {
+    R* fin = (R*)h->f[h->cur];
+    R* fout = (R*)h->f[1 - h->cur];
+    ghost_fill<R>(h, fin);
+    if (sub == 0) {
+      if (stats) run_stats<R>(h, fin);
+      const bool adaptive = !(h->p.dt_fixed > 0.0);
+      ClassTimer ct(h, MHD_KC_CFL, adaptive ? 2 : 1);
+      int nb = 0;
+      if (adaptive) nb = launch_cfl_partial<R>(h->L, ph, bgr<R>(h), fin, (const R*)h->wtab, h->red, h->ss, h->st);
+      launch_cfl_finalize(h->red, nb, h->ss, h->p.c_adv, h->p.c_diff, h->p.dt_fixed, inv2sum(&h->p), h->t0,
+                          h->t1, h->p.t_ramp, 0, h->st);
+    }
+    {
+      ClassTimer ct(h, MHD_KC_RK, 1);
+      launch_rk<R>(h->L, ph, bgr<R>(h), fin, fout, (R*)h->df, (const R*)h->wtab, (const R*)h->wptab, drv, h->ss,
+                   sub, h->st);
+    }
+    h->cur = 1 - h->cur;
+  }
+}
+
+// ---- FFT tables (host, FP64) ----------------------------------------------------
+static int upload_fft_tables(mhd_ctx* h, const Offsets& o) {
+  const mhd_params* p = &h->p;
+  int nx = p->nx, ny = p->ny;
+  std::vector<double> tw((size_t)2 * (nx > ny ? nx : ny));
+  FFTPlan& fp = h->fp;
+  fp.nx = nx;
+  fp.ny = ny;
+  fp.lognx = ilog2(nx);
+  fp.logny = ilog2(ny);
+  fp.twx = (const double2*)(h->ws + o.twx);
+  fp.twy = (const double2*)(h->ws + o.twy);
+  fp.et = (const double*)(h->ws + o.et);
+  fp.eb = (const double*)(h->ws + o.eb);
+  fp.ktx = (const double*)(h->ws + o.ktx);
+  fp.kty = (const double*)(h->ws + o.kty);
+  fp.P = (double2*)(h->ws + o.P);
+  fp.Q = (double2*)(h->ws + o.Q);
+  int rc;
+  for (int axis = 0; axis < 2; ++axis) {
+    int n = axis == 0 ? nx : ny;
+    for (int r = 0; r < n; ++r) {
+      tw[2 * r] = cos(2.0 * M_PI * r / n);
+      tw[2 * r + 1] = -sin(2.0 * M_PI * r / n);
+    }
+    rc = cuda_check(h, cudaMemcpy((void*)(axis == 0 ? fp.twx : fp.twy), tw.data(), (size_t)n * 16,
+                                  cudaMemcpyHostToDevice), "upload twiddles");
+    if (rc) return rc;
+  }
+  // continuous |k| = 2 pi sqrt((m/Lx)^2 + (n/Ly)^2), signed m, n; tables [kx][ky]
+  double lx = nx * p->dx, ly = ny * p->dy;
+  std::vector<double> et((size_t)nx * ny), eb((size_t)nx * ny);
+  for (int a = 0; a < nx; ++a) {
+    int ma = 2 * a > nx ? a - nx : a;
+    double kx = 2.0 * M_PI * ma / lx;
+    for (int b = 0; b < ny; ++b) {
+      int mb = 2 * b > ny ? b - ny : b;
+      double ky = 2.0 * M_PI * mb / ly;
+      double kk = sqrt(kx * kx + ky * ky);
+      et[(size_t)a * ny + b] = exp(-kk * p->dz);
+      eb[(size_t)a * ny + b] = exp(p->f_pfe_bottom * kk * p->dz);
+    }
+  }
+  rc = cuda_check(h, cudaMemcpy((void*)fp.et, et.data(), et.size() * 8, cudaMemcpyHostToDevice), "upload et");
+  if (rc) return rc;
+  rc = cuda_check(h, cudaMemcpy((void*)fp.eb, eb.data(), eb.size() * 8, cudaMemcpyHostToDevice), "upload eb");
+  if (rc) return rc;
+  // modified wavenumber of the sixth-order first derivative; zero at m = 0
+  // and at the Nyquist mode
+  for (int axis = 0; axis < 2; ++axis) {
+    int n = axis == 0 ? nx : ny;
+    double hsp = axis == 0 ? p->dx : p->dy;
+    std::vector<double> kt((size_t)n);
+    for (int m = 0; m < n; ++m) {
+      if (m == 0 || 2 * m == n) { kt[m] = 0.0; continue; }
+      double th = 2.0 * M_PI * (2 * m > n ? m - n : m) / n;
+      kt[m] = (45.0 * sin(th) - 9.0 * sin(2.0 * th) + sin(3.0 * th)) / (30.0 * hsp);
+    }
+    rc = cuda_check(h, cudaMemcpy((void*)(axis == 0 ? fp.ktx : fp.kty), kt.data(), (size_t)n * 8,
+                                  cudaMemcpyHostToDevice), "upload kt");
+    if (rc) return rc;
+  }
+  return MHD_OK;
+}
+
+// ---- entry points --------------------------------------------------------------
+extern "C" int mhd_create(const mhd_params* p, void* workspace, size_t ws_bytes, const void* init_state,
+                          int mem, const double* lnrho0, const double* lnT0, void* stream, mhd_handle* out) {
+  if (!out) return fail(nullptr, MHD_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  const char* bad = check_params(p);
+  if (bad) return fail(nullptr, MHD_ERR_ARG, "%s", bad);
+  if (!init_state || !lnrho0) return fail(nullptr, MHD_ERR_ARG, "init_state and lnrho0 are required");
+  if (mem != MHD_MEM_DEVICE && mem != MHD_MEM_HOST) return fail(nullptr, MHD_ERR_ARG, "bad mem flag");
+  Offsets o = plan_offsets(p);
+  if (!workspace) return fail(nullptr, MHD_ERR_WORKSPACE, "workspace is NULL");
+  if (((uintptr_t)workspace & 255u) != 0) return fail(nullptr, MHD_ERR_WORKSPACE, "workspace not 256-byte aligned");
+  if (ws_bytes < o.total)
+    return fail(nullptr, MHD_ERR_WORKSPACE, "workspace too small: %zu < %zu bytes", ws_bytes, o.total);
+
+  mhd_ctx* h = (mhd_ctx*)calloc(1, sizeof(mhd_ctx));
+  if (!h) return fail(nullptr, MHD_ERR_ARG, "host allocation failed");
+  h->p = *p;
+  h->L = make_layout(p->nx, p->ny, p->nz);
+  h->st = (cudaStream_t)stream;
+  h->esz = p->precision == 64 ? 8 : 4;
+  h->ws = (char*)workspace;
+  h->ws_bytes = ws_bytes;
+  h->f[0] = h->ws + o.f0;
+  h->f[1] = h->ws + o.f1;
+  h->df = h->ws + o.df;
+  h->lnrho0 = h->ws + o.lnrho0;
+  h->wtab = h->ws + o.wtab;
+  h->wptab = h->ws + o.wptab;
+  h->bz = h->ws + o.bz;
+  h->axt = h->ws + o.axt;
+  h->ayt = h->ws + o.ayt;
+  h->v0 = h->ws + o.v0;
+  h->v1 = h->ws + o.v1;
+  h->red = (double*)(h->ws + o.red);
+  h->ss = (StepState*)(h->ws + o.ss);
+  h->bgtab = h->ws + o.bg;
+  h->have_fft = p->bc_z == 0;
+  h->t0 = 0.0;
+  h->t1 = 0.0;
+  snprintf(h->err, sizeof h->err, "no error");
+
+  int rc = MHD_OK;
+  // host tables: density ghosts, swamp weights
+  {
+    size_t es = h->esz;
+    std::vector<char> buf(8 * es + 2 * (size_t)p->nz * es);
+    for (int m = 0; m < NG; ++m) {
+      double v = lnrho0[m];  // z index m - 3
+      if (es == 8) ((double*)buf.data())[m] = v; else ((float*)buf.data())[m] = (float)v;
+    }
+    rc = cuda_check(h, cudaMemcpy(h->lnrho0, buf.data(), 8 * es, cudaMemcpyHostToDevice), "upload lnrho0");
+    std::vector<double> w(p->nz), wp(p->nz);
+    for (int k = 0; k < p->nz; ++k) swamp_weight(p, k * p->dz, &w[k], &wp[k]);
+    char* wb = buf.data() + 8 * es;
+    for (int k = 0; k < p->nz; ++k) {
+      if (es == 8) { ((double*)wb)[k] = w[k]; ((double*)wb)[p->nz + k] = wp[k]; }
+      else { ((float*)wb)[k] = (float)w[k]; ((float*)wb)[p->nz + k] = (float)wp[k]; }
+    }
+    if (!rc) rc = cuda_check(h, cudaMemcpy(h->wtab, wb, (size_t)p->nz * es, cudaMemcpyHostToDevice), "upload w");
+    if (!rc) rc = cuda_check(h, cudaMemcpy(h->wptab, wb + (size_t)p->nz * es, (size_t)p->nz * es,
+                                            cudaMemcpyHostToDevice), "upload wp");
+  }
+  if (!rc && h->have_fft) rc = upload_fft_tables(h, o);
+  if (!rc) {
+    StepState s0;
+    memset(&s0, 0, sizeof s0);
+    rc = cuda_check(h, cudaMemcpy(h->ss, &s0, sizeof s0, cudaMemcpyHostToDevice), "init step state");
+  }
+  if (!rc) {
+    // zero the driver (no nudging target until mhd_set_driver)
+    rc = cuda_check(h, cudaMemsetAsync(h->bz, 0, (size_t)(o.red - o.bz), h->st), "zero driver");
+  }
+  // background profiles: ln T from the given profile or the layer means of
+  // the initial state (staged in the accumulator buffer)
+  if (!rc) {
+    std::vector<double> tmean((size_t)p->nz, 0.0);
+    if (!lnT0 && p->bc_z == 0) {
+      size_t bytes = (size_t)NF * p->nx * p->ny * p->nz * h->esz;
+      rc = cuda_check(h, cudaMemcpyAsync(h->df, init_state, bytes, kind_in(mem), h->st), "stage state");
+      if (!rc) {
+        if (h->esz == 8) launch_layer_mean<double>(h->L, (const double*)h->df, LT, h->red, h->st);
+        else launch_layer_mean<float>(h->L, (const float*)h->df, LT, h->red, h->st);
+        rc = cuda_check(h, cudaMemcpyAsync(tmean.data(), h->red, (size_t)p->nz * 8, cudaMemcpyDeviceToHost, h->st),
+                        "layer means");
+      }
+      if (!rc) rc = cuda_check(h, cudaStreamSynchronize(h->st), "layer means synchronize");
+    }
+    if (!rc) rc = h->esz == 8 ? upload_background<double>(h, lnrho0, lnT0, tmean.data())
+                              : upload_background<float>(h, lnrho0, lnT0, tmean.data());
+  }
+  if (!rc) rc = mhd_write(h, init_state, mem);
+  if (!rc) rc = cuda_check(h, cudaStreamSynchronize(h->st), "create synchronize");
+  if (rc) {
+    snprintf(g_err, sizeof g_err, "%s", h->err);
+    free(h);
+    return rc;
+  }
+  *out = h;
+  return MHD_OK;
+}
+
+extern "C" int mhd_write(mhd_handle h, const void* src, int mem) {
+  if (!h) return fail(nullptr, MHD_ERR_ARG, "NULL handle");
+  if (!src) return fail(h, MHD_ERR_ARG, "src is NULL");
+  if (mem != MHD_MEM_DEVICE && mem != MHD_MEM_HOST) return fail(h, MHD_ERR_ARG, "bad mem flag");
+  const Layout& L = h->L;
+  size_t bytes = (size_t)NF * L.nx * L.ny * L.nz * h->esz;
+  int rc = cuda_check(h, cudaMemcpyAsync(h->df, src, bytes, kind_in(mem), h->st), "copy state in");
+  if (rc) return rc;
+  for (int s = 0; s < 2; ++s) {
+    if (h->esz == 8) {
+      double* f = (double*)h->f[s];
+      cudaMemsetAsync(f, 0, (size_t)NF * L.fs * 8, h->st);
+      launch_unpack<double>(L, h->bgd, (const double*)h->df, f, h->st);
+      launch_rims<double>(L, f, 0, L.nz, h->st);
+      if (h->p.bc_z == 0) launch_init_u_ghosts<double>(L, f, h->st);
+    } else {
+      float* f = (float*)h->f[s];
+      cudaMemsetAsync(f, 0, (size_t)NF * L.fs * 4, h->st);
+      launch_unpack<float>(L, h->bgf, (const float*)h->df, f, h->st);
+      launch_rims<float>(L, f, 0, L.nz, h->st);
+      if (h->p.bc_z == 0) launch_init_u_ghosts<float>(L, f, h->st);
+    }
+  }
+  h->cur = 0;
+  rc = cuda_check(h, cudaSuccess, "state unpack");
+  if (rc) return rc;
+  if (mem == MHD_MEM_HOST) rc = cuda_check(h, cudaStreamSynchronize(h->st), "write synchronize");
+  return rc;
+}
+
+extern "C" int mhd_set_driver(mhd_handle h, const void* bz, const void* v0, const void* v1, double t0,
+                              double t1, int mem) {
+  if (!h) return fail(nullptr, MHD_ERR_ARG, "NULL handle");
+  if (!bz || !v0 || !v1) return fail(h, MHD_ERR_ARG, "bz, v0, v1 are required");
+  if (mem != MHD_MEM_DEVICE && mem != MHD_MEM_HOST) return fail(h, MHD_ERR_ARG, "bad mem flag");
+  if (!(t1 > t0)) return fail(h, MHD_ERR_ARG, "driver times need t1 > t0");
+  size_t n2 = (size_t)h->p.nx * h->p.ny * h->esz;
+  int rc = cuda_check(h, cudaMemcpyAsync(h->bz, bz, n2, kind_in(mem), h->st), "copy bz");
+  if (!rc) rc = cuda_check(h, cudaMemcpyAsync(h->v0, v0, 2 * n2, kind_in(mem), h->st), "copy v0");
+  if (!rc) rc = cuda_check(h, cudaMemcpyAsync(h->v1, v1, 2 * n2, kind_in(mem), h->st), "copy v1");
+  if (rc) return rc;
+  h->t0 = t0;
+  h->t1 = t1;
+  if (h->have_fft) {
+    if (h->esz == 8) launch_atarget<double>(h->fp, (const double*)h->bz, (double*)h->axt, (double*)h->ayt, h->st);
+    else launch_atarget<float>(h->fp, (const float*)h->bz, (float*)h->axt, (float*)h->ayt, h->st);
+    rc = cuda_check(h, cudaSuccess, "magnetogram inversion");
+    if (rc) return rc;
+  }
+  h->driver_set = true;
+  if (mem == MHD_MEM_HOST) rc = cuda_check(h, cudaStreamSynchronize(h->st), "driver synchronize");
+  return rc;
+}
+
+extern "C" int mhd_step(mhd_handle h, int nsteps) {
+  if (!h) return fail(nullptr, MHD_ERR_ARG, "NULL handle");
+  if (nsteps < 0) return fail(h, MHD_ERR_ARG, "nsteps < 0");
+  for (int n = 0; n < nsteps; ++n) {
+    bool stats = h->p.stats_every > 0 && (h->host_steps % h->p.stats_every) == 0;
+    if (h->esz == 8) run_step<double>(h, stats); else run_step<float>(h, stats);
+    h->host_steps++;
+  }
+  return cuda_check(h, cudaSuccess, "step launch");
+}
+
+extern "C" int mhd_read(mhd_handle h, int field, void* dst, int mem) {
+  if (!h) return fail(nullptr, MHD_ERR_ARG, "NULL handle");
+  if (!dst) return fail(h, MHD_ERR_ARG, "dst is NULL");
+  if (field < -1 || field >= NF) return fail(h, MHD_ERR_ARG, "field must be -1..7");
+  if (mem != MHD_MEM_DEVICE && mem != MHD_MEM_HOST) return fail(h, MHD_ERR_ARG, "bad mem flag");
+  const Layout& L = h->L;
+  size_t bytes = (size_t)(field < 0 ? NF : 1) * L.nx * L.ny * L.nz * h->esz;
+  void* tgt = mem == MHD_MEM_HOST ? h->df : dst;
+  if (h->esz == 8) launch_pack<double>(L, h->bgd, (const double*)h->f[h->cur], (double*)tgt, field, h->st);
+  else launch_pack<float>(L, h->bgf, (const float*)h->f[h->cur], (float*)tgt, field, h->st);
+  int rc = cuda_check(h, cudaSuccess, "pack");
+  if (rc) return rc;
+  if (mem == MHD_MEM_HOST) {
+    rc = cuda_check(h, cudaMemcpyAsync(dst, h->df, bytes, cudaMemcpyDeviceToHost, h->st), "copy out");
+    if (!rc) rc = cuda_check(h, cudaStreamSynchronize(h->st), "read synchronize");
+  }
+  return rc;
+}
+
+extern "C" int mhd_read_padded(mhd_handle h, int which, void* dst, int mem) {
+  if (!h) return fail(nullptr, MHD_ERR_ARG, "NULL handle");
+  if (!dst || (which != 0 && which != 1)) return fail(h, MHD_ERR_ARG, "bad dst or which");
+  if (mem != MHD_MEM_DEVICE && mem != MHD_MEM_HOST) return fail(h, MHD_ERR_ARG, "bad mem flag");
+  const Layout& L = h->L;
+  size_t w = (size_t)(L.nx + 2 * NG) * h->esz;
+  size_t rows = (size_t)L.mz * L.my;
+  if (which == 0) {
+    // state: background added, staged in the accumulator buffer
+    if (h->esz == 8) launch_pack_padded<double>(L, h->bgd, (const double*)h->f[h->cur], (double*)h->df, h->st);
+    else launch_pack_padded<float>(L, h->bgf, (const float*)h->f[h->cur], (float*)h->df, h->st);
+    int rc = cuda_check(h, cudaMemcpyAsync(dst, h->df, (size_t)NF * rows * w, kind_out(mem), h->st), "copy padded");
+    if (rc) return rc;
+  } else {
+    const char* src = (const char*)h->df;
+    for (int fl = 0; fl < NF; ++fl) {
+      const char* s = src + ((size_t)fl * L.fs + (XOFF - NG)) * h->esz;
+      char* d = (char*)dst + (size_t)fl * rows * w;
+      int rc = cuda_check(h, cudaMemcpy2DAsync(d, w, s, (size_t)L.mx * h->esz, w, rows, kind_out(mem), h->st),
+                          "copy padded");
+      if (rc) return rc;
+    }
+  }
+  if (mem == MHD_MEM_HOST) return cuda_check(h, cudaStreamSynchronize(h->st), "read synchronize");
+  return MHD_OK;
+}
+
+extern "C" int mhd_fill_ghosts(mhd_handle h) {
+  if (!h) return fail(nullptr, MHD_ERR_ARG, "NULL handle");
+  if (h->esz == 8) ghost_fill<double>(h, (double*)h->f[h->cur]);
+  else ghost_fill<float>(h, (float*)h->f[h->cur]);
+  return cuda_check(h, cudaSuccess, "ghost fill");
+}
+
+extern "C" int mhd_eval_rhs(mhd_handle h, double t, void* dst, int mem) {
+  if (!h) return fail(nullptr, MHD_ERR_ARG, "NULL handle");
+  double r, s;
+  driver_weights(h, t, &r, &s);
+  double rs[2] = {r, s};
+  int rc = cuda_check(h, cudaMemcpyAsync(&h->ss->eval_r, rs, sizeof rs, cudaMemcpyHostToDevice, h->st),
+                      "eval weights");
+  if (rc) return rc;
+  rc = cuda_check(h, cudaMemsetAsync(h->df, 0, (size_t)NF * h->L.fs * h->esz, h->st), "zero df");
+  if (rc) return rc;
+  Driver drv{h->axt, h->ayt, h->v0, h->v1};
+  if (h->esz == 8) {
+    Phys<double> ph = make_phys<double>(&h->p);
+    launch_rk<double>(h->L, ph, h->bgd, (const double*)h->f[h->cur], nullptr, (double*)h->df, (const double*)h->wtab,
+                      (const double*)h->wptab, drv, h->ss, -1, h->st);
+  } else {
+    Phys<float> ph = make_phys<float>(&h->p);
+    launch_rk<float>(h->L, ph, h->bgf, (const float*)h->f[h->cur], nullptr, (float*)h->df, (const float*)h->wtab,
+                     (const float*)h->wptab, drv, h->ss, -1, h->st);
+  }
+  rc = cuda_check(h, cudaSuccess, "rhs");
+  if (rc) return rc;
+  if (mem == MHD_MEM_HOST) {
+    rc = cuda_check(h, cudaStreamSynchronize(h->st), "rhs synchronize");
+    if (rc) return rc;
+  }
+  return mhd_read_padded(h, 1, dst, mem);
+}
+
+extern "C" int mhd_compute_dt(mhd_handle h, double* dt) {
+  if (!h || !dt) return fail(h, MHD_ERR_ARG, "NULL argument");
+  int nb;
+  if (h->esz == 8) {
+    Phys<double> ph = make_phys<double>(&h->p);
+    nb = launch_cfl_partial<double>(h->L, ph, h->bgd, (const double*)h->f[h->cur], (const double*)h->wtab, h->red,
+                                    h->ss, h->st);
+  } else {
+    Phys<float> ph = make_phys<float>(&h->p);
+    nb = launch_cfl_partial<float>(h->L, ph, h->bgf, (const float*)h->f[h->cur], (const float*)h->wtab, h->red,
+                                   h->ss, h->st);
+  }
+  launch_cfl_finalize(h->red, nb, h->ss, h->p.c_adv, h->p.c_diff, 0.0, inv2sum(&h->p), h->t0, h->t1,
+                      h->p.t_ramp, 1, h->st);
+  int rc = sync_status(h);
+  if (rc) return rc;
+  return cuda_check(h, cudaMemcpy(dt, &h->ss->probe_dt, sizeof(double), cudaMemcpyDeviceToHost), "read dt");
+}
+
+static int fetch_stats(mhd_ctx* h, mhd_stats* out) {
+  StepState s;
+  int rc = cuda_check(h, cudaMemcpy(&s, h->ss, sizeof s, cudaMemcpyDeviceToHost), "read stats");
+  if (rc) return rc;
+  memset(out, 0, sizeof *out);
+  out->t = s.t;
+  out->dt = s.dt;
+  out->e_kin = s.stats[0];
+  out->e_mag = s.stats[1];
+  out->e_th = s.stats[2];
+  out->mass = s.stats[3];
+  out->flux_net = s.stats[4];
+  out->flux_abs = s.stats[5];
+  out->divb_max = s.stats[6];
+  out->step = s.step;
+  out->nonfinite = s.nonfinite;
+  return MHD_OK;
+}
+
+extern "C" int mhd_compute_stats(mhd_handle h, mhd_stats* out) {
+  if (!h || !out) return fail(h, MHD_ERR_ARG, "NULL argument");
+  if (h->esz == 8) run_stats<double>(h, (double*)h->f[h->cur]);
+  else run_stats<float>(h, (float*)h->f[h->cur]);
+  int rc = cuda_check(h, cudaStreamSynchronize(h->st), "stats synchronize");
+  if (rc) return rc;
+  rc = fetch_stats(h, out);
+  if (rc) return rc;
+  if (out->nonfinite) return fail(h, MHD_ERR_NONFINITE, "non-finite value in the state");
+  return MHD_OK;
+}
+
+extern "C" int mhd_read_stats(mhd_handle h, mhd_stats* out) {
+  if (!h || !out) return fail(h, MHD_ERR_ARG, "NULL argument");
+  int rc = cuda_check(h, cudaStreamSynchronize(h->st), "stats synchronize");
+  if (rc) return rc;
+  rc = fetch_stats(h, out);
+  if (rc) return rc;
+  if (out->nonfinite) return fail(h, MHD_ERR_NONFINITE, "non-finite value in the state (time stepping halted)");
+  return MHD_OK;
+}
+
+extern "C" int mhd_get_time(mhd_handle h, double* t, double* dt) {
+  if (!h || !t || !dt) return fail(h, MHD_ERR_ARG, "NULL argument");
+  double td[2];
+  int nf = 0;
+  int rc = cuda_check(h, cudaStreamSynchronize(h->st), "time synchronize");
+  if (!rc) rc = cuda_check(h, cudaMemcpy(td, &h->ss->t, sizeof td, cudaMemcpyDeviceToHost), "read time");
+  if (!rc) rc = cuda_check(h, cudaMemcpy(&nf, &h->ss->nonfinite, sizeof nf, cudaMemcpyDeviceToHost), "read status");
+  if (rc) return rc;
+  *t = td[0];
+  *dt = td[1];
+  if (nf) return fail(h, MHD_ERR_NONFINITE, "non-finite value in the state (time stepping halted)");
+  return MHD_OK;
+}
+
+extern "C" int mhd_read_target(mhd_handle h, void* dst, int mem) {
+  if (!h || !dst) return fail(h, MHD_ERR_ARG, "NULL argument");
+  size_t n2 = (size_t)h->p.nx * h->p.ny * h->esz;
+  int rc = cuda_check(h, cudaMemcpyAsync(dst, h->axt, n2, kind_out(mem), h->st), "copy axt");
+  if (!rc) rc = cuda_check(h, cudaMemcpyAsync((char*)dst + n2, h->ayt, n2, kind_out(mem), h->st), "copy ayt");
+  if (!rc && mem == MHD_MEM_HOST) rc = cuda_check(h, cudaStreamSynchronize(h->st), "target synchronize");
+  return rc;
+}
+
+static void drop_events(mhd_ctx* h) {
+  if (!h->evs) return;
+  for (auto& e : *h->evs) {
+    cudaEventDestroy(e.a);
+    cudaEventDestroy(e.b);
+  }
+  h->evs->clear();
+}
+
+extern "C" int mhd_profile(mhd_handle h, int enable) {
+  if (!h) return fail(nullptr, MHD_ERR_ARG, "NULL handle");
+  if (!h->evs) h->evs = new std::vector<mhd_ctx::Ev>();
+  if (enable && !h->prof) drop_events(h);
+  h->prof = enable != 0;
+  return MHD_OK;
+}
+
+extern "C" int mhd_read_profile(mhd_handle h, double* ms, long long* launches) {
+  if (!h || !ms || !launches) return fail(h, MHD_ERR_ARG, "NULL argument");
+  int rc = cuda_check(h, cudaStreamSynchronize(h->st), "profile synchronize");
+  if (rc) return rc;
+  for (int c = 0; c < MHD_NKC; ++c) { ms[c] = 0.0; launches[c] = 0; }
+  if (h->evs) {
+    for (auto& e : *h->evs) {
+      float t = 0.f;
+      cudaEventElapsedTime(&t, e.a, e.b);
+      ms[e.cls] += t;
+      launches[e.cls] += e.nk;
+    }
+    drop_events(h);
+  }
+  return cuda_check(h, cudaSuccess, "profile read");
+}
+
+extern "C" long long mhd_launch_count(mhd_handle h) { return h ? h->nlaunch : 0; }
+
+extern "C" void mhd_destroy(mhd_handle h) {
+  if (!h) return;
+  cudaStreamSynchronize(h->st);
+  drop_events(h);
+  delete h->evs;
+  free(h);
+}
+
+extern "C" const char* mhd_last_error(mhd_handle h) { return h ? h->err : g_err; }

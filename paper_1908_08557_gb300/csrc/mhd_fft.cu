@@ -1,0 +1,273 @@
+// mhd_fft.cu -- FP64 horizontal FFT of the potential-field boundary
+// (Sect. 4.2, Eqs. 16-17; Sect. 2.4 inverted extrapolation) and of the
+// magnetogram inversion (Sect. 2.4, Eq. 7).
+//
+// The six real boundary planes (A_x, A_y, A_z at the top layer and at the
+// photosphere) travel as three complex planes:
+//   P0 = A_x(top) + i A_y(top),  P1 = A_x(bot) + i A_y(bot),
+//   P2 = A_z(top) + i A_z(bot).
+// The extrapolation multiplier M(k) is real and even in k, so applying it to
+// a packed plane extrapolates both real parts at once.  P2 carries two planes
+// with different multipliers M_t, M_b; with F = FFT(P2) the spectrum to invert
+// is a F(k) + b conj(F(-k)), a = (M_t + M_b)/2, b = (M_t - M_b)/2, whose inverse
+// has real part = top ghost and imaginary part = bottom ghost.
+//
+// Kernels (radix-2 Stockham autosort in shared memory, FP64):
+//   1. rows_fwd: pack rows from the state, FFT along x, store transposed
+//   2. cols:     FFT along y, for each ghost layer j = 1..3 form the
+//                extrapolated spectrum (M_t = exp(-|k| j dz),
+//                M_b = exp(+f_b |k| j dz)), inverse FFT along y
+//   3. rows_inv: inverse FFT along x, write real/imaginary parts into the
+//                ghost layers (with their periodic x,y images)
+#include "mhd_internal.h"
+
+namespace mhd {
+
+__device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+// nb lines of n = 2^logn complex points in a (b is scratch of equal size).
+// Stockham radix-2: at stage p (1, 2, ..., n/2) butterfly i in [0, n/2):
+// k = i mod p, u0 = x[i], u1 = x[i + n/2] w^k with w = exp(-+2 pi i / (2p)),
+// y[2i - k] = u0 + u1, y[2i - k + p] = u0 - u1.  Returns the buffer holding
+// the (unnormalised) transform.
+__device__ double2* fft_lines(double2* a, double2* b, int n, int logn, int nb, const double2* __restrict__ tw,
+                              bool inverse) {
+  const int half = n >> 1;
+  const int total = nb * half;
+  for (int p = 1, s = 0; p < n; p <<= 1, ++s) {
+    const int tws = logn - 1 - s;  // twiddle index k * n / (2p) = k << tws
+    for (int q = threadIdx.x; q < total; q += blockDim.x) {
+      const int line = q >> (logn - 1);
+      const int i = q & (half - 1);
+      const int k = i & (p - 1);
+      double2 w = __ldg(tw + (k << tws));
+      if (inverse) w.y = -w.y;
+      const double2 u0 = a[line * n + i];
+      const double2 u1 = cmul(w, a[line * n + i + half]);
+      const int o = (i << 1) - k;
+      b[line * n + o] = cadd(u0, u1);
+      b[line * n + o + p] = csub(u0, u1);
+    }
+    __syncthreads();
+    double2* t = a;
+    a = b;
+    b = t;
+  }
+  return a;
+}
+
+// ---------------------------------------------------------------------------
+// 1. forward rows.  mode 0: three boundary planes of the state; mode 1: one
+// real plane `src2d` ([ny][nx], the magnetogram).
+template <typename R>
+__global__ void __launch_bounds__(256) rows_fwd_kernel(FFTPlan fp, Layout L, const R* __restrict__ f,
+                                                       const R* __restrict__ src2d, int mode,
+                                                       const StepState* ss) {
+  extern __shared__ double2 sm[];
+  if (ss && halted(ss)) return;
+  const int nx = fp.nx, ny = fp.ny;
+  const int nb = min(FFT_PTS / nx, ny);
+  const int y0 = blockIdx.x * nb;
+  const int p = blockIdx.y;
+  double2* a = sm;
+  double2* b = sm + FFT_PTS;
+  const int kt = L.nz - 1;
+  for (int q = threadIdx.x; q < nb * nx; q += blockDim.x) {
+    const int line = q / nx, x = q - line * nx, y = y0 + line;
+    double re, im;
+    if (mode == 1) {
+      re = (double)src2d[(long long)y * nx + x];
+      im = 0.0;
+    } else if (p == 0) {
+      re = (double)f[L.at(AX, kt, y, x)];
+      im = (double)f[L.at(AY, kt, y, x)];
+    } else if (p == 1) {
+      re = (double)f[L.at(AX, 0, y, x)];
+      im = (double)f[L.at(AY, 0, y, x)];
+    } else {
+      re = (double)f[L.at(AZ, kt, y, x)];
+      im = (double)f[L.at(AZ, 0, y, x)];
+    }
+    a[line * nx + x] = make_double2(re, im);
+  }
+  __syncthreads();
+  double2* r = fft_lines(a, b, nx, fp.lognx, nb, fp.twx, false);
+  // transposed store: P[p][x][y], consecutive threads walk y
+  for (int q = threadIdx.x; q < nb * nx; q += blockDim.x) {
+    const int x = q / nb, line = q - x * nb;
+    fp.P[((long long)p * nx + x) * ny + y0 + line] = r[line * nx + x];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// 2. columns.  A block owns column pairs (kx, nx - kx); both columns of a pair
+// are needed to split the packed plane P2 (F(-k) lives in the mirror column).
+// mode 0: potential-field extrapolation, 3 layers; mode 1: magnetogram
+// inversion (Eq. 7): A^_x + i A^_y = (kt_x + i kt_y) B^_z / kt^2.
+__global__ void __launch_bounds__(256) cols_kernel(FFTPlan fp, int mode, const StepState* ss) {
+  extern __shared__ double2 sm[];
+  if (ss && halted(ss)) return;
+  const int nx = fp.nx, ny = fp.ny;
+  const int npairs = nx / 2 + 1;
+  const int ppb = max(1, FFT_PTS / (2 * ny));  // pairs per block
+  const int pair0 = blockIdx.x * ppb;
+  const int np = min(ppb, npairs - pair0);
+  const int nl = 2 * np;
+  const int p = blockIdx.y;
+  double2* S = sm;
+  double2* Wa = sm + FFT_PTS;
+  double2* Wb = sm + 2 * FFT_PTS;
+  // columns of line l: pair (l >> 1), mirror if odd
+  for (int q = threadIdx.x; q < nl * ny; q += blockDim.x) {
+    const int line = q / ny, y = q - line * ny;
+    const int kx = pair0 + (line >> 1);
+    const int col = (line & 1) ? ((nx - kx) & (nx - 1)) : kx;
+    Wa[line * ny + y] = fp.P[((long long)p * nx + col) * ny + y];
+  }
+  __syncthreads();
+  double2* spec = fft_lines(Wa, S, ny, fp.logny, nl, fp.twy, false);
+  double2* work0 = (spec == Wa) ? S : Wa;
+  const int nout = mode == 0 ? 3 : 1;
+  for (int o = 0; o < nout; ++o) {
+    for (int q = threadIdx.x; q < nl * ny; q += blockDim.x) {
+      const int line = q / ny, ky = q - line * ny;
+      const int kx = pair0 + (line >> 1);
+      const int col = (line & 1) ? ((nx - kx) & (nx - 1)) : kx;
+      const double2 F = spec[line * ny + ky];
+      double2 G;
+      if (mode == 1) {
+        const double kxm = fp.ktx[col], kym = fp.kty[ky];
+        const double k2 = kxm * kxm + kym * kym;
+        if (k2 > 0.0) {
+          const double2 m = make_double2(kxm / k2, kym / k2);
+          G = cmul(m, F);
+        } else {
+          G = make_double2(0.0, 0.0);
+        }
+      } else {
+        const double e_t = fp.et[(long long)col * ny + ky], e_b = fp.eb[(long long)col * ny + ky];
+        double mt = e_t, mb = e_b;
+        for (int jj = 0; jj < o; ++jj) { mt *= e_t; mb *= e_b; }
+        if (p == 0) {
+          G = make_double2(mt * F.x, mt * F.y);
+        } else if (p == 1) {
+          G = make_double2(mb * F.x, mb * F.y);
+        } else {
+          const double2 Fm = spec[(line ^ 1) * ny + ((ny - ky) & (ny - 1))];
+          const double ca = 0.5 * (mt + mb), cb = 0.5 * (mt - mb);
+          G = make_double2(ca * F.x + cb * Fm.x, ca * F.y - cb * Fm.y);
+        }
+      }
+      work0[line * ny + ky] = G;
+    }
+    __syncthreads();
+    double2* r = fft_lines(work0, Wb, ny, fp.logny, nl, fp.twy, true);
+    const int nplanes = mode == 0 ? 3 : 1;
+    for (int q = threadIdx.x; q < nl * ny; q += blockDim.x) {
+      const int line = q / ny, y = q - line * ny;
+      const int kx = pair0 + (line >> 1);
+      const bool self = (kx == 0 || 2 * kx == nx);
+      if ((line & 1) && self) continue;  // the mirror of a self-paired column
+      const int col = (line & 1) ? ((nx - kx) & (nx - 1)) : kx;
+      fp.Q[(((long long)o * nplanes + p) * nx + col) * ny + y] = r[line * ny + y];
+    }
+    __syncthreads();
+    if (r == Wb) { double2* t = Wb; Wb = work0; work0 = t; }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// 3. inverse rows: normalise by 1/(nx ny); mode 0 writes ghost layers of the
+// state, mode 1 the compact planes out_re, out_im ([ny][nx]).
+template <typename R>
+__global__ void __launch_bounds__(256) rows_inv_kernel(FFTPlan fp, Layout L, R* __restrict__ f, R* out_re,
+                                                       R* out_im, int mode, const StepState* ss) {
+  extern __shared__ double2 sm[];
+  if (ss && halted(ss)) return;
+  const int nx = fp.nx, ny = fp.ny;
+  const int nb = min(FFT_PTS / nx, ny);
+  const int y0 = blockIdx.x * nb;
+  const int p = blockIdx.y, o = blockIdx.z;
+  const int nplanes = mode == 0 ? 3 : 1;
+  double2* a = sm;
+  double2* b = sm + FFT_PTS;
+  for (int q = threadIdx.x; q < nb * nx; q += blockDim.x) {
+    const int x = q / nb, line = q - x * nb;
+    a[line * nx + x] = fp.Q[(((long long)o * nplanes + p) * nx + x) * ny + y0 + line];
+  }
+  __syncthreads();
+  double2* r = fft_lines(a, b, nx, fp.lognx, nb, fp.twx, true);
+  const double sc = 1.0 / ((double)nx * (double)ny);
+  const int m = o + 1;
+  const int ktop = L.nz - 1 + m, kbot = -m;
+  for (int q = threadIdx.x; q < nb * nx; q += blockDim.x) {
+    const int line = q / nx, x = q - line * nx, y = y0 + line;
+    const double2 v = r[line * nx + x];
+    const R re = (R)(v.x * sc), im = (R)(v.y * sc);
+    if (mode == 1) {
+      out_re[(long long)y * nx + x] = re;
+      out_im[(long long)y * nx + x] = im;
+      continue;
+    }
+    int f1, k1, f2, k2;
+    if (p == 0) { f1 = AX; k1 = ktop; f2 = AY; k2 = ktop; }
+    else if (p == 1) { f1 = AX; k1 = kbot; f2 = AY; k2 = kbot; }
+    else { f1 = AZ; k1 = ktop; f2 = AZ; k2 = kbot; }
+    int xs[3], ys[3], nxs = 1, nys = 1;
+    xs[0] = x; ys[0] = y;
+    if (x < NG) xs[nxs++] = x + nx;
+    if (x >= nx - NG) xs[nxs++] = x - nx;
+    if (y < NG) ys[nys++] = y + ny;
+    if (y >= ny - NG) ys[nys++] = y - ny;
+    for (int bb = 0; bb < nys; ++bb)
+      for (int aa = 0; aa < nxs; ++aa) {
+        f[L.at(f1, k1, ys[bb], xs[aa])] = re;
+        f[L.at(f2, k2, ys[bb], xs[aa])] = im;
+      }
+  }
+}
+
+static void set_smem_once() {
+  static bool done = false;
+  if (done) return;
+  done = true;
+  cudaFuncSetAttribute(rows_fwd_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * FFT_PTS * 16);
+  cudaFuncSetAttribute(rows_fwd_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * FFT_PTS * 16);
+  cudaFuncSetAttribute(rows_inv_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * FFT_PTS * 16);
+  cudaFuncSetAttribute(rows_inv_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * FFT_PTS * 16);
+  cudaFuncSetAttribute(cols_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 3 * FFT_PTS * 16);
+}
+
+template <typename R>
+void launch_pfe(const FFTPlan& fp, const Layout& L, R* f, const StepState* ss, cudaStream_t st) {
+  set_smem_once();
+  const int nb = FFT_PTS / fp.nx < fp.ny ? FFT_PTS / fp.nx : fp.ny;
+  const int ppb = FFT_PTS / (2 * fp.ny) > 1 ? FFT_PTS / (2 * fp.ny) : 1;
+  const int npairs = fp.nx / 2 + 1;
+  rows_fwd_kernel<R><<<dim3(fp.ny / nb, 3), 256, 2 * FFT_PTS * 16, st>>>(fp, L, f, nullptr, 0, ss);
+  cols_kernel<<<dim3((npairs + ppb - 1) / ppb, 3), 256, 3 * FFT_PTS * 16, st>>>(fp, 0, ss);
+  rows_inv_kernel<R><<<dim3(fp.ny / nb, 3, 3), 256, 2 * FFT_PTS * 16, st>>>(fp, L, f, nullptr, nullptr, 0, ss);
+}
+
+template <typename R>
+void launch_atarget(const FFTPlan& fp, const R* bz, R* axt, R* ayt, cudaStream_t st) {
+  set_smem_once();
+  Layout L{};
+  const int nb = FFT_PTS / fp.nx < fp.ny ? FFT_PTS / fp.nx : fp.ny;
+  const int ppb = FFT_PTS / (2 * fp.ny) > 1 ? FFT_PTS / (2 * fp.ny) : 1;
+  const int npairs = fp.nx / 2 + 1;
+  rows_fwd_kernel<R><<<dim3(fp.ny / nb, 1), 256, 2 * FFT_PTS * 16, st>>>(fp, L, nullptr, bz, 1, nullptr);
+  cols_kernel<<<dim3((npairs + ppb - 1) / ppb, 1), 256, 3 * FFT_PTS * 16, st>>>(fp, 1, nullptr);
+  rows_inv_kernel<R><<<dim3(fp.ny / nb, 1, 1), 256, 2 * FFT_PTS * 16, st>>>(fp, L, nullptr, axt, ayt, 1, nullptr);
+}
+
+template void launch_pfe<float>(const FFTPlan&, const Layout&, float*, const StepState*, cudaStream_t);
+template void launch_pfe<double>(const FFTPlan&, const Layout&, double*, const StepState*, cudaStream_t);
+template void launch_atarget<float>(const FFTPlan&, const float*, float*, float*, cudaStream_t);
+template void launch_atarget<double>(const FFTPlan&, const double*, double*, double*, cudaStream_t);
+
+}  // namespace mhd

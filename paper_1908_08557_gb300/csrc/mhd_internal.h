@@ -1,0 +1,71 @@
+// mhd_internal.h -- launchers shared between the translation units of libmhd.
+#pragma once
+#include <cuda_runtime.h>
+#include "mhd_common.cuh"
+
+namespace mhd {
+
+// Potential-field FFT plan: all arrays live in the caller's workspace.
+struct FFTPlan {
+  int nx, ny, lognx, logny;
+  const double2* twx;  // exp(-2 pi i r / nx), r < nx
+  const double2* twy;  // exp(-2 pi i r / ny), r < ny
+  const double* et;    // [kx][ky] exp(-|k| dz)           (Eq. 17, upward)
+  const double* eb;    // [kx][ky] exp(+f_b |k| dz)       (Sect. 2.4, downward)
+  const double* ktx;   // modified first-derivative wavenumbers, [nx]
+  const double* kty;   // [ny]
+  double2* P;          // [3][nx][ny] row spectra, transposed
+  double2* Q;          // [3][3][nx][ny] extrapolated spectra, transposed
+};
+
+struct Driver {
+  const void* axt;  // [ny][nx] A_x of the target magnetogram
+  const void* ayt;
+  const void* v0;   // [2][ny][nx]
+  const void* v1;
+};
+
+constexpr int FFT_PTS = 2048;          // complex points per shared buffer
+constexpr int RED_BLOCKS_MAX = 4096;   // partial-reduction slots
+
+// ghost fill
+template <typename R> void launch_rims(const Layout& L, R* f, int k0, int k1, cudaStream_t st);
+template <typename R> void launch_init_u_ghosts(const Layout& L, R* f, cudaStream_t st);
+template <typename R> void launch_bc(const Layout& L, const Phys<R>& ph, const Background<R>& bg, R* f,
+                                     R dz, const StepState* ss, cudaStream_t st);
+// potential-field ghosts of A (three FFT kernels)
+template <typename R> void launch_pfe(const FFTPlan& fp, const Layout& L, R* f, const StepState* ss,
+                                      cudaStream_t st);
+// vector potential of the target magnetogram into axt, ayt
+template <typename R> void launch_atarget(const FFTPlan& fp, const R* bz, R* axt, R* ayt, cudaStream_t st);
+// fused right-hand side + RK update; sub = 0,1,2, or -1 to write the raw RHS into df
+template <typename R> void launch_rk(const Layout& L, const Phys<R>& ph, const Background<R>& bg,
+                                     const R* fin, R* fout, R* df,
+                                     const R* wtab, const R* wptab, const Driver& drv, const StepState* ss,
+                                     int sub, cudaStream_t st);
+// reductions
+template <typename R> int launch_cfl_partial(const Layout& L, const Phys<R>& ph, const Background<R>& bg,
+                                             const R* f, const R* wtab,
+                                             double* partial, StepState* ss, cudaStream_t st);
+void launch_cfl_finalize(const double* partial, int nblk, StepState* ss, double c_adv, double c_diff,
+                         double dt_fixed, double inv2sum, double t0, double t1, double t_ramp, int probe,
+                         cudaStream_t st);
+template <typename R> int launch_stats_partial(const Layout& L, const Phys<R>& ph, const Background<R>& bg,
+                                               const R* f,
+                                               double* partial, StepState* ss, cudaStream_t st);
+void launch_stats_finalize(const double* partial, int nblk, StepState* ss, double dv, double da,
+                           cudaStream_t st);
+// pack / unpack interior <-> padded
+// (the background is added on the way out and removed on the way in)
+template <typename R> void launch_pack(const Layout& L, const Background<R>& bg, const R* f, R* out, int field,
+                                       cudaStream_t st);
+template <typename R> void launch_unpack(const Layout& L, const Background<R>& bg, const R* in, R* f,
+                                         cudaStream_t st);
+// padded copy with the background added (diagnostics)
+template <typename R> void launch_pack_padded(const Layout& L, const Background<R>& bg, const R* f, R* out,
+                                              cudaStream_t st);
+// per-layer FP64 mean of field `field` of an interior-packed state
+template <typename R> void launch_layer_mean(const Layout& L, const R* in, int field, double* out,
+                                             cudaStream_t st);
+
+}  // namespace mhd

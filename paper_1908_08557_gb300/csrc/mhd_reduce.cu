@@ -1,0 +1,280 @@
+// mhd_reduce.cu -- FP64 reductions: the CFL time step and the global
+// diagnostics.  Per-cell values are formed in the state precision; block
+// partials and the grid-wide result are FP64.  Maxima are order independent;
+// sums are taken in a fixed order (per thread, warp tree, block, then one
+// block over the partials) so repeated runs give identical bits.
+#include <float.h>
+#include "mhd_internal.h"
+
+namespace mhd {
+
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// grid over (x tiles, y tiles, z chunks); each thread walks its z chunk
+static inline dim3 red_grid(const Layout& L, int* kchunk) {
+  int tx = (L.nx + 31) / 32, ty = (L.ny + 7) / 8;
+  int zc = 1216 / (tx * ty);
+  if (zc < 1) zc = 1;
+  if (zc > L.nz) zc = L.nz;
+  if (tx * ty * zc > RED_BLOCKS_MAX) zc = RED_BLOCKS_MAX / (tx * ty) > 0 ? RED_BLOCKS_MAX / (tx * ty) : 1;
+  *kchunk = (L.nz + zc - 1) / zc;
+  zc = (L.nz + *kchunk - 1) / *kchunk;
+  return dim3(tx, ty, zc);
+}
+
+// B = curl A + B_ext at a cell from sixth-order first derivatives (Eq. 6)
+template <typename R>
+__device__ __forceinline__ void bfield(const Layout& L, const Phys<R>& ph, const R* f, int k, int j, int i,
+                                       R* B) {
+  const long long sy = L.sy(), sz = L.sz();
+  const R* ax = f + L.at(AX, k, j, i);
+  const R* ay = f + L.at(AY, k, j, i);
+  const R* az = f + L.at(AZ, k, j, i);
+  B[0] = d1(az, sy, ph.idy) - d1(ay, sz, ph.idz) + ph.bext[0];
+  B[1] = d1(ax, sz, ph.idz) - d1(az, (long long)1, ph.idx) + ph.bext[1];
+  B[2] = d1(ay, (long long)1, ph.idx) - d1(ax, sy, ph.idy) + ph.bext[2];
+}
+
+// CFL: per cell the advective rate sum|u_i|/dx_i + sqrt(gamma T + B^2/rho)
+// sqrt(sum 1/dx_i^2) and the diffusive rate D_max sum 1/dx_i^2, D_max the
+// largest of nu, eta + eta_s w, D_rho + chi_rho w, chi_s w + (gamma-1)
+// kappa0 T^{5/2}/rho.  Block maxima to partial[2 b], partial[2 b + 1].
+template <typename R>
+__global__ void __launch_bounds__(256) cfl_partial_kernel(Layout L, Phys<R> ph, Background<R> bg,
+                                                          const R* __restrict__ f,
+                                                          const R* __restrict__ wtab, double* partial,
+                                                          StepState* ss, int kchunk, R sqinv2) {
+  __shared__ double sa[8], sd[8];
+  const int i = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y * 8 + threadIdx.y;
+  const int tid = threadIdx.y * 32 + threadIdx.x;
+  double ma = 0.0, md = 0.0;
+  bool bad = false;
+  if (i < L.nx && j < L.ny && !halted(ss)) {
+    const int k0 = blockIdx.z * kchunk, k1 = min(L.nz, k0 + kchunk);
+    for (int k = k0; k < k1; ++k) {
+      R B[3];
+      bfield<R>(L, ph, f, k, j, i, B);
+      const R ux = f[L.at(UX, k, j, i)], uy = f[L.at(UY, k, j, i)], uz = f[L.at(UZ, k, j, i)];
+      const R lr = bg.lbar[k + NG] + f[L.at(LR, k, j, i)], lt = bg.tbar[k + NG] + f[L.at(LT, k, j, i)];
+      const R T = rexp<R>(lt), rho1 = rexp<R>(-lr);
+      const R B2 = B[0] * B[0] + B[1] * B[1] + B[2] * B[2];
+      const R adv = fabs(ux) * ph.idx + fabs(uy) * ph.idy + fabs(uz) * ph.idz +
+                    rsqrt_<R>(ph.gamma * T + B2 * rho1) * sqinv2;
+      const R w = wtab[k];
+      R dm = ph.nu;
+      dm = fmax(dm, ph.eta + ph.eta_s * w);
+      dm = fmax(dm, ph.drho + ph.drho_s * w);
+      dm = fmax(dm, ph.chi_s * w + ph.gm1 * ph.kappa0 * rexp<R>(R(2.5) * lt - lr));
+      const double a = (double)adv, d = (double)dm;
+      if (!isfinite(a) || !isfinite(d)) bad = true;
+      ma = fmax(ma, a);
+      md = fmax(md, d);
+    }
+  }
+  if (bad) atomicOr(&ss->nonfinite, 1);
+  ma = warp_max(ma);
+  md = warp_max(md);
+  if ((tid & 31) == 0) { sa[tid >> 5] = ma; sd[tid >> 5] = md; }
+  __syncthreads();
+  if (tid == 0) {
+    for (int w = 1; w < 8; ++w) { ma = fmax(ma, sa[w]); md = fmax(md, sd[w]); }
+    const int b = (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+    partial[2 * b] = ma;
+    partial[2 * b + 1] = md;
+  }
+}
+
+template <typename R>
+int launch_cfl_partial(const Layout& L, const Phys<R>& ph, const Background<R>& bg, const R* f, const R* wtab,
+                       double* partial, StepState* ss, cudaStream_t st) {
+  int kchunk;
+  dim3 g = red_grid(L, &kchunk);
+  R s2 = (R)sqrt((double)ph.idx2 + (double)ph.idy2 + (double)ph.idz2);
+  cfl_partial_kernel<R><<<g, dim3(32, 8), 0, st>>>(L, ph, bg, f, wtab, partial, ss, kchunk, s2);
+  return (int)(g.x * g.y * g.z);
+}
+
+// dt = min(C_adv / max adv, C_diff / max(D_max) / sum 1/dx_i^2) (or dt_fixed);
+// then the substep times t + c_s dt with their ramp r and driver weight s
+// (Sect. 2.3: linear switch-on, linear interpolation between snapshots).
+__global__ void cfl_finalize_kernel(const double* partial, int nblk, StepState* ss, double c_adv,
+                                    double c_diff, double dt_fixed, double inv2sum, double t0, double t1,
+                                    double t_ramp, int probe) {
+  __shared__ double sa[32], sd[32];
+  double ma = 0.0, md = 0.0;
+  for (int b = threadIdx.x; b < nblk; b += blockDim.x) {
+    ma = fmax(ma, partial[2 * b]);
+    md = fmax(md, partial[2 * b + 1]);
+  }
+  ma = warp_max(ma);
+  md = warp_max(md);
+  if ((threadIdx.x & 31) == 0) { sa[threadIdx.x >> 5] = ma; sd[threadIdx.x >> 5] = md; }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  for (int w = 1; w < (int)(blockDim.x >> 5); ++w) { ma = fmax(ma, sa[w]); md = fmax(md, sd[w]); }
+  double dt;
+  if (dt_fixed > 0.0) {
+    dt = dt_fixed;
+  } else {
+    const double d1 = ma > 0.0 ? c_adv / ma : INFINITY;
+    const double d2 = md > 0.0 ? c_diff / (md * inv2sum) : INFINITY;
+    dt = d1 < d2 ? d1 : d2;
+  }
+  if (!(dt > 0.0) || !isfinite(dt)) ss->nonfinite = 1;
+  if (probe) { ss->probe_dt = dt; return; }
+  if (ss->nonfinite) return;
+  const double t = ss->t;
+  ss->dt = dt;
+  for (int s = 0; s < 3; ++s) {
+    const double ts = t + rk_c(s) * dt;
+    ss->tsub[s] = ts;
+    double r = 1.0;
+    if (t_ramp > 0.0) r = fmin(fmax(ts / t_ramp, 0.0), 1.0);
+    double q = t1 > t0 ? (ts - t0) / (t1 - t0) : 0.0;
+    ss->r[s] = r;
+    ss->s[s] = fmin(fmax(q, 0.0), 1.0);
+  }
+  ss->t = t + dt;
+  ss->step += 1;
+}
+
+void launch_cfl_finalize(const double* partial, int nblk, StepState* ss, double c_adv, double c_diff,
+                         double dt_fixed, double inv2sum, double t0, double t1, double t_ramp, int probe,
+                         cudaStream_t st) {
+  cfl_finalize_kernel<<<1, 256, 0, st>>>(partial, nblk, ss, c_adv, c_diff, dt_fixed, inv2sum, t0, t1,
+                                         t_ramp, probe);
+}
+
+// Diagnostics: per block 7 values (sums of rho u^2/2, B^2/2, rho T/(gamma-1),
+// rho, B_z(k=0), |B_z(k=0)|, and max |div B|) to partial[8 b + q].
+template <typename R>
+__global__ void __launch_bounds__(256) stats_partial_kernel(Layout L, Phys<R> ph, Background<R> bg,
+                                                            const R* __restrict__ f,
+                                                            double* partial, StepState* ss, int kchunk) {
+  __shared__ double sm[8][8];
+  const int i = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y * 8 + threadIdx.y;
+  const int tid = threadIdx.y * 32 + threadIdx.x;
+  double acc[7] = {0, 0, 0, 0, 0, 0, 0};
+  if (i < L.nx && j < L.ny) {
+    const long long sy = L.sy(), sz = L.sz();
+    const int k0 = blockIdx.z * kchunk, k1 = min(L.nz, k0 + kchunk);
+    for (int k = k0; k < k1; ++k) {
+      R B[3];
+      bfield<R>(L, ph, f, k, j, i, B);
+      const R ux = f[L.at(UX, k, j, i)], uy = f[L.at(UY, k, j, i)], uz = f[L.at(UZ, k, j, i)];
+      const R rho = rexp<R>(bg.lbar[k + NG] + f[L.at(LR, k, j, i)]);
+      const R T = rexp<R>(bg.tbar[k + NG] + f[L.at(LT, k, j, i)]);
+      acc[0] += (double)(R(0.5) * rho * (ux * ux + uy * uy + uz * uz));
+      acc[1] += (double)(R(0.5) * (B[0] * B[0] + B[1] * B[1] + B[2] * B[2]));
+      acc[2] += (double)(rho * T) / (double)ph.gm1;
+      acc[3] += (double)rho;
+      if (k == 0) {
+        acc[4] += (double)B[2];
+        acc[5] += fabs((double)B[2]);
+      }
+      // div B with the same stencils: B_x has no x derivative, B_y no y and
+      // B_z no z derivative, so all values used lie inside the ghost zone
+      R dv = R(0);
+      const R cw[4] = {R(0), W<R>::c1, W<R>::c2, W<R>::c3};
+      for (int m = 1; m <= 3; ++m) {
+        const R* azp = f + L.at(AZ, k, j, i + m);
+        const R* azm = f + L.at(AZ, k, j, i - m);
+        const R* ayp = f + L.at(AY, k, j, i + m);
+        const R* aym = f + L.at(AY, k, j, i - m);
+        const R bxp = d1(azp, sy, ph.idy) - d1(ayp, sz, ph.idz);
+        const R bxm = d1(azm, sy, ph.idy) - d1(aym, sz, ph.idz);
+        const R* axq = f + L.at(AX, k, j + m, i);
+        const R* axr = f + L.at(AX, k, j - m, i);
+        const R* azq = f + L.at(AZ, k, j + m, i);
+        const R* azr = f + L.at(AZ, k, j - m, i);
+        const R byp = d1(axq, sz, ph.idz) - d1(azq, (long long)1, ph.idx);
+        const R bym = d1(axr, sz, ph.idz) - d1(azr, (long long)1, ph.idx);
+        const R* ays = f + L.at(AY, k + m, j, i);
+        const R* ayt = f + L.at(AY, k - m, j, i);
+        const R* axs = f + L.at(AX, k + m, j, i);
+        const R* axt = f + L.at(AX, k - m, j, i);
+        const R bzp = d1(ays, (long long)1, ph.idx) - d1(axs, sy, ph.idy);
+        const R bzm = d1(ayt, (long long)1, ph.idx) - d1(axt, sy, ph.idy);
+        dv += cw[m] * ((bxp - bxm) * ph.idx + (byp - bym) * ph.idy + (bzp - bzm) * ph.idz);
+      }
+      acc[6] = fmax(acc[6], fabs((double)dv));
+    }
+  }
+  for (int q = 0; q < 6; ++q) acc[q] = warp_sum(acc[q]);
+  acc[6] = warp_max(acc[6]);
+  if ((tid & 31) == 0)
+    for (int q = 0; q < 7; ++q) sm[tid >> 5][q] = acc[q];
+  __syncthreads();
+  if (tid == 0) {
+    for (int w = 1; w < 8; ++w) {
+      for (int q = 0; q < 6; ++q) acc[q] += sm[w][q];
+      acc[6] = fmax(acc[6], sm[w][6]);
+    }
+    const int b = (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+    for (int q = 0; q < 7; ++q) partial[8 * b + q] = acc[q];
+  }
+}
+
+template <typename R>
+int launch_stats_partial(const Layout& L, const Phys<R>& ph, const Background<R>& bg, const R* f,
+                         double* partial, StepState* ss, cudaStream_t st) {
+  int kchunk;
+  dim3 g = red_grid(L, &kchunk);
+  stats_partial_kernel<R><<<g, dim3(32, 8), 0, st>>>(L, ph, bg, f, partial, ss, kchunk);
+  return (int)(g.x * g.y * g.z);
+}
+
+// fixed-order sums over the block partials; volume sums scaled by dV, the
+// photospheric flux sums by dA
+__global__ void stats_finalize_kernel(const double* partial, int nblk, StepState* ss, double dv, double da) {
+  __shared__ double sm[256][7];
+  double acc[7] = {0, 0, 0, 0, 0, 0, 0};
+  for (int b = threadIdx.x; b < nblk; b += blockDim.x) {
+    for (int q = 0; q < 6; ++q) acc[q] += partial[8 * b + q];
+    acc[6] = fmax(acc[6], partial[8 * b + 6]);
+  }
+  for (int q = 0; q < 7; ++q) sm[threadIdx.x][q] = acc[q];
+  __syncthreads();
+  for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+    if ((int)threadIdx.x < h) {
+      for (int q = 0; q < 6; ++q) sm[threadIdx.x][q] += sm[threadIdx.x + h][q];
+      sm[threadIdx.x][6] = fmax(sm[threadIdx.x][6], sm[threadIdx.x + h][6]);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const double sc[7] = {dv, dv, dv, dv, da, da, 1.0};
+    bool bad = false;
+    for (int q = 0; q < 7; ++q) {
+      ss->stats[q] = sm[0][q] * sc[q];
+      if (!isfinite(ss->stats[q])) bad = true;
+    }
+    ss->stats_t = ss->t;
+    if (bad) ss->nonfinite = 1;
+  }
+}
+
+void launch_stats_finalize(const double* partial, int nblk, StepState* ss, double dv, double da,
+                           cudaStream_t st) {
+  stats_finalize_kernel<<<1, 256, 0, st>>>(partial, nblk, ss, dv, da);
+}
+
+#define INST(R)                                                                                        \
+  template int launch_cfl_partial<R>(const Layout&, const Phys<R>&, const Background<R>&, const R*,      \
+                                     const R*, double*, StepState*, cudaStream_t);                     \
+  template int launch_stats_partial<R>(const Layout&, const Phys<R>&, const Background<R>&, const R*,    \
+                                       double*, StepState*, cudaStream_t);
+INST(float)
+INST(double)
+#undef INST
+
+}  // namespace mhd

@@ -1,0 +1,204 @@
+"""GPU parity: every kernel of libmhd, called through the C ABI, against the
+FP64 CPU oracle on the same seeded inputs.
+
+Tolerances: the FP64 path agrees with the oracle to rounding (1e-11 relative
+L2 per field after 50 steps); the FP32 path to 1e-4 per field after 50 steps
+(FP32 state and stencils, FP64 FFT and reductions).
+"""
+import numpy as np
+import pytest
+
+import inputs
+import oracle
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+NG = oracle.NG
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_1908_08557_gb300.build import build
+    build()
+    oracle.build()
+
+
+def _sim(case, precision, stats_every=0, driver=True, params=None, lnT0=True):
+    from paper_1908_08557_gb300 import Simulation
+    p = params or case.params
+    dt = torch.float64 if precision == 64 else torch.float32
+    sim = Simulation(p, torch.tensor(case.state, dtype=dt, device="cuda"), case.lnrho0,
+                     case.lnT0 if lnT0 else None, precision=precision, stats_every=stats_every)
+    if driver:
+        sim.set_driver(torch.tensor(case.bz, dtype=dt, device="cuda"),
+                       torch.tensor(case.v0, dtype=dt, device="cuda"),
+                       torch.tensor(case.v1, dtype=dt, device="cuda"), case.t0, case.t1)
+    return sim
+
+
+def _perturbed(nx, ny, nz, seed, **kw):
+    case = inputs.make_box(nx, ny, nz, seed=seed, **kw)
+    rng = np.random.default_rng(seed + 100)
+    st = case.state.copy()
+    st[3:6] += 0.05 * rng.standard_normal(st[3:6].shape)
+    st[7] += 0.02 * rng.standard_normal(st[7].shape)
+    st[0:3] += 0.01 * rng.standard_normal(st[0:3].shape)
+    case.state = st
+    return case
+
+
+def _rel_l2(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+@pytest.mark.parametrize("shape", [(16, 16, 12), (32, 8, 9), (8, 64, 7)])
+def test_ghost_fill_fp64(shape):
+    nx, ny, nz = shape
+    case = _perturbed(nx, ny, nz, seed=1)
+    sim = _sim(case, 64)
+    sim.fill_ghosts()
+    got = sim.read_padded(0)
+    u = oracle.to_padded(case.state)
+    oracle.fill_ghosts(case.params, u, case.lnrho0)
+    scale = np.abs(u).max(axis=(1, 2, 3))
+    err = np.abs(got - u).max(axis=(1, 2, 3))
+    assert np.all(err <= 1e-13 * scale), err / scale
+
+
+def test_ghost_fill_periodic_z_ragged():
+    case = _perturbed(40, 24, 20, seed=2)
+    p = dict(case.params, bc_z=1)
+    sim = _sim(case, 64, driver=False, params=p)
+    sim.fill_ghosts()
+    got = sim.read_padded(0)
+    u = oracle.to_padded(case.state)
+    oracle.fill_ghosts(p, u, case.lnrho0)
+    assert np.array_equal(got[:, :, :, :], u)
+
+
+def test_magnetogram_inversion_fp64():
+    case = inputs.make_box(32, 16, 8, seed=4, dy=1.5)
+    sim = _sim(case, 64)
+    ax, ay = oracle.a_target(case.params, case.bz)
+    got = sim.read_target()
+    s = np.abs(np.stack([ax, ay])).max()
+    assert np.abs(got[0] - ax).max() < 1e-13 * s
+    assert np.abs(got[1] - ay).max() < 1e-13 * s
+
+
+@pytest.mark.parametrize("shape,bcz", [((16, 16, 12), 0), ((32, 16, 10), 0), ((40, 24, 20), 1)])
+def test_rhs_fp64(shape, bcz):
+    nx, ny, nz = shape
+    case = _perturbed(nx, ny, nz, seed=3)
+    p = dict(case.params, bc_z=bcz)
+    sim = _sim(case, 64, params=p, driver=(bcz == 0))
+    sim.fill_ghosts()
+    t = 0.37
+    got = sim.eval_rhs(t)
+    u = sim.read_padded(0).astype(np.float64)
+    if bcz == 0:
+        axt, ayt = oracle.a_target(p, case.bz)
+        v0, v1 = case.v0, case.v1
+    else:
+        axt = ayt = np.zeros((ny, nx))
+        v0 = v1 = np.zeros((2, ny, nx))
+    ref = oracle.rhs(p, u, axt, ayt, v0, v1, case.t0, case.t1, t)
+    for f in range(8):
+        s = np.abs(ref[f]).max()
+        e = np.abs(got[f] - ref[f]).max()
+        assert e <= 1e-11 * max(s, 1e-30), (f, e, s)
+
+
+def test_rhs_fp32():
+    case = _perturbed(16, 16, 12, seed=5)
+    sim = _sim(case, 32)
+    sim.fill_ghosts()
+    got = sim.eval_rhs(0.2).astype(np.float64)
+    u = sim.read_padded(0).astype(np.float64)
+    axt, ayt = (a.astype(np.float32).astype(np.float64) for a in oracle.a_target(case.params, case.bz))
+    ref = oracle.rhs(case.params, u, axt, ayt, case.v0.astype(np.float32).astype(np.float64),
+                     case.v1.astype(np.float32).astype(np.float64), case.t0, case.t1, 0.2)
+    for f in range(8):
+        s = np.abs(ref[f]).max()
+        e = np.abs(got[f] - ref[f]).max()
+        assert e <= 2e-4 * max(s, 1e-30), (f, e, s)
+
+
+def test_cfl_and_stats_fp64():
+    case = _perturbed(32, 32, 16, seed=6)
+    sim = _sim(case, 64)
+    sim.fill_ghosts()
+    u = sim.read_padded(0)
+    dt = sim.compute_dt()
+    assert abs(dt - oracle.cfl(case.params, u)) <= 1e-13 * dt
+    st = sim.compute_stats()
+    ref = oracle.stats(case.params, u)
+    keys = ["e_kin", "e_mag", "e_th", "mass", "flux_net", "flux_abs", "divb_max"]
+    for q, k in enumerate(keys[:4] + keys[5:6]):
+        r = ref[keys.index(k)]
+        assert abs(st[k] - r) <= 1e-12 * abs(r), (k, st[k], r)
+    assert abs(st["flux_net"] - ref[4]) <= 1e-12 * ref[5]
+    assert st["divb_max"] < 1e-10 and ref[6] < 1e-10
+
+
+def test_full_run_fp64_spots4_32():
+    """Workload spots4_32x32x32 (4 spots, 50 RK3 steps): FP64 GPU vs oracle,
+    relative L2 <= 1e-11 per field, same time."""
+    case = inputs.make_case("spots4_32x32x32")
+    sim = _sim(case, 64)
+    sim.step(case.nsteps)
+    got = sim.read().cpu().numpy()
+    u, t, dts = oracle.run_case(case)
+    ref = oracle.interior(u)
+    errs = [_rel_l2(got[f], ref[f]) for f in range(8)]
+    assert max(errs) <= 1e-11, errs
+    tg, dtg = sim.time()
+    assert abs(tg - t) <= 1e-12 * t
+    # stateful horizontal-velocity ghosts below the photosphere
+    gp = sim.read_padded(0)
+    for c in (3, 4):
+        a = gp[c, :NG, NG:-NG, NG:-NG]
+        b = u[c, :NG, NG:-NG, NG:-NG]
+        assert _rel_l2(a, b) <= 1e-11
+
+
+def test_full_run_fp32_spots4_32():
+    """Same workload on the FP32 path: relative L2 <= 1e-4 per field."""
+    case = inputs.make_case("spots4_32x32x32")
+    sim = _sim(case, 32)
+    sim.step(case.nsteps)
+    got = sim.read().cpu().numpy().astype(np.float64)
+    u, t, dts = oracle.run_case(case)
+    ref = oracle.interior(u)
+    errs = [_rel_l2(got[f], ref[f]) for f in range(8)]
+    print("fp32 rel L2 per field:", ["%.2e" % e for e in errs])
+    assert max(errs) <= 1e-4, errs
+
+
+def test_periodic_ragged_run_fp64():
+    case = _perturbed(40, 24, 20, seed=7)
+    p = dict(case.params, bc_z=1, eta_swamp=0.0, chi_swamp=0.0, diffrho_swamp=0.0, gz=0.0)
+    sim = _sim(case, 64, params=p, driver=False)
+    sim.step(5)
+    got = sim.read().cpu().numpy()
+    z2 = np.zeros((24, 40)); v2 = np.zeros((2, 24, 40))
+    u = oracle.to_padded(case.state)
+    oracle.run(p, u, case.lnrho0, z2, z2, v2, v2, 0.0, 1.0, 0.0, 5)
+    ref = oracle.interior(u)
+    errs = [_rel_l2(got[f], ref[f]) for f in range(8)]
+    assert max(errs) <= 1e-12, errs
+
+
+def test_nonfinite_detected():
+    from paper_1908_08557_gb300 import MHDError
+    from paper_1908_08557_gb300.binding import MHD_ERR_NONFINITE
+    case = inputs.make_box(16, 16, 10, seed=8)
+    st = case.state.copy()
+    st[7, 4, 5, 6] = np.nan
+    case.state = st
+    sim = _sim(case, 32)
+    sim.step(2)
+    with pytest.raises(MHDError) as e:
+        sim.time()
+    assert e.value.code == MHD_ERR_NONFINITE
