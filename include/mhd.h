@@ -183,6 +183,32 @@ int mhd_compute_stats(mhd_handle h, mhd_stats* out);
  * [2][ny][nx] into dst. */
 int mhd_read_target(mhd_handle h, void* dst, int mem);
 
+/* ---- allocation-free variant ---- */
+
+/* Vector potential A_x, A_y (Weyl gauge, A_z = 0) of the magnetogram bz, the
+ * same result mhd_set_driver stores for its nudging target, for callers that
+ * cannot allocate device memory and have no workspace to give: a host
+ * application that reserves the whole GPU up front, a plugin inside a process
+ * whose caching allocator already holds nearly all of HBM, or code that must
+ * not pay for an allocation.  There is no counterpart in the paper; it is a
+ * library convenience.
+ *   nx, ny: powers of two in [8, 512]; larger sizes return MHD_ERR_ARG with a
+ *     message (the scratch is a fixed 8 MiB + 24 KiB __device__ array that
+ *     every GPU loading the library keeps until the process exits).
+ *   dx, dy: grid spacings; precision: 32 or 64 (element type of bz, ax, ay).
+ *   bz [ny][nx] input, ax, ay [ny][nx] outputs: device pointers owned by the
+ *     caller.  stream: cudaStream_t (NULL: legacy default stream).
+ * Allocates nothing: no cudaMalloc, cudaFree or allocating library call.  The
+ * first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  All calls on a device share the one scratch
+ * array: calls that overlap on the GPU (different streams, or different host
+ * threads) race and give wrong results.  Asynchronous; errors are reported
+ * through mhd_last_error(NULL). */
+int mhd_invert_magnetogram_static(int nx, int ny, double dx, double dy,
+                                  int precision, const void* bz, void* ax,
+                                  void* ay, void* stream);
+
 /* ---- instrumentation ---- */
 
 /* Kernel classes timed by the profiler. */

@@ -34,7 +34,7 @@ EXPORTED = ("mhd_workspace_bytes", "mhd_create", "mhd_set_driver", "mhd_step",
             "mhd_destroy", "mhd_last_error", "mhd_fill_ghosts",
             "mhd_read_padded", "mhd_eval_rhs", "mhd_compute_dt",
             "mhd_compute_stats", "mhd_read_target", "mhd_profile",
-            "mhd_read_profile", "mhd_launch_count")
+            "mhd_read_profile", "mhd_launch_count", "mhd_invert_magnetogram_static")
 KERNEL_CLASSES = ("ghost", "pfe", "cfl", "stats", "rk")
 
 
@@ -111,6 +111,7 @@ def load(path: Optional[str] = None):
     lib.mhd_profile.argtypes = [vp, i]
     lib.mhd_read_profile.argtypes = [vp, ctypes.POINTER(ctypes.c_double),
                                      ctypes.POINTER(ctypes.c_longlong)]
+    lib.mhd_invert_magnetogram_static.argtypes = [i, i, d, d, i, vp, vp, vp, vp]
     lib.mhd_launch_count.argtypes = [vp]
     lib.mhd_launch_count.restype = ctypes.c_longlong
     for name in EXPORTED:

@@ -82,6 +82,14 @@ static int fail(mhd_ctx* h, int code, const char* fmt, ...) {
   return code;
 }
 
+// message for mhd_last_error(NULL), used by entry points without a handle
+void mhd::set_global_error(const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof g_err, fmt, ap);
+  va_end(ap);
+}
+
 static int cuda_check(mhd_ctx* h, cudaError_t e, const char* what) {
   if (e == cudaSuccess) e = cudaGetLastError();
   if (e != cudaSuccess) return fail(h, MHD_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));

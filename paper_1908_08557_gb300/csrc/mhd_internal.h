@@ -25,6 +25,9 @@ struct Driver {
   const void* v1;
 };
 
+// set the message returned by mhd_last_error(NULL)
+void set_global_error(const char* fmt, ...);
+
 constexpr int FFT_PTS = 2048;          // complex points per shared buffer
 constexpr int RED_BLOCKS_MAX = 4096;   // partial-reduction slots
 
