@@ -29,9 +29,10 @@
  *   asynchronous unless stated otherwise.
  * - Return value: MHD_OK (0) or a negative MHD_ERR_* code; the message is
  *   available from mhd_last_error().  Argument errors are reported before any
- *   launch.  A non-finite value met by the time-step reduction sets a device
- *   flag: from then on every kernel of the handle returns without work, and
- *   the next synchronising call returns MHD_ERR_NONFINITE.
+ *   launch.  A non-finite value met by the time-step reduction (or a device
+ *   wait that exceeded its bound) sets a device flag: from then on every
+ *   kernel of the handle returns without work, and the next synchronising
+ *   call returns MHD_ERR_NONFINITE (or MHD_ERR_TIMEOUT).
  */
 #ifndef MHD_H
 #define MHD_H
@@ -48,6 +49,7 @@ extern "C" {
 #define MHD_ERR_CUDA (-3)       /* a CUDA runtime call failed                 */
 #define MHD_ERR_NONFINITE (-4)  /* NaN/Inf detected in the state              */
 #define MHD_ERR_UNSUPPORTED (-5)/* valid but not built (e.g. FFT size)        */
+#define MHD_ERR_TIMEOUT (-6)    /* a bounded device wait gave up              */
 
 #define MHD_MEM_DEVICE 0
 #define MHD_MEM_HOST 1

@@ -69,6 +69,8 @@ def lib():
         _lib.or_deriv.argtypes = [ip, dp, dp, ctypes.c_int, ctypes.c_int,
                                   ctypes.c_int, ctypes.c_int, dp]
         _lib.or_swamp_weight.argtypes = [dp, ctypes.c_double, dp, dp]
+        _lib.or_rhs_cells.argtypes = [ip, dp, dp, dp, dp, dp, dp, ctypes.c_double,
+                                      ctypes.c_double, ctypes.c_double, ctypes.c_int, ip, dp]
     return _lib
 
 
@@ -128,6 +130,17 @@ def rhs(p: Dict, u: np.ndarray, axt, ayt, v0, v1, t0, t1, t) -> np.ndarray:
     c = lambda a: np.ascontiguousarray(a, dtype=np.float64)
     lib().or_rhs(_i(_dims(p)), _d(_pvec(p)), _d(u), _d(c(axt)), _d(c(ayt)),
                  _d(c(v0)), _d(c(v1)), t0, t1, t, _d(out))
+    return out
+
+
+def rhs_cells(p: Dict, u: np.ndarray, axt, ayt, v0, v1, t0, t1, t, cells) -> np.ndarray:
+    """Right-hand side at the listed interior cells (rows of (k, j, i));
+    returns (ncell, 8).  `u` must be ghost-filled."""
+    c = lambda a: np.ascontiguousarray(a, dtype=np.float64)
+    cl = np.ascontiguousarray(cells, dtype=np.int32).reshape(-1, 3)
+    out = np.zeros((len(cl), 8))
+    lib().or_rhs_cells(_i(_dims(p)), _d(_pvec(p)), _d(u), _d(c(axt)), _d(c(ayt)), _d(c(v0)),
+                       _d(c(v1)), t0, t1, t, len(cl), _i(cl), _d(out))
     return out
 
 

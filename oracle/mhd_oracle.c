@@ -384,134 +384,140 @@ static void driver_weights(const double* p, double t0, double t1, double t,
  *          + chi_s w lap ln T                                       (Eq. 19)
  *  photosphere: dlnrho/dt = 0 (density held at its initial profile,
  *  Sect. 2.5), du_z/dt = 0 (closed); top layer: du_z/dt = 0 (Sect. 4). */
+/* Right-hand side at one interior cell (k, j, i); out[8] in field order.
+ * r, s: ramp and driver interpolation weight at the evaluation time. */
+static void rhs_cell(const grid_t* g, const double* u, const double* axt, const double* ayt,
+                     const double* v0, const double* v1, double r, double s, int k, int j, int i,
+                     double* out) {
+  const double* p = g->p;
+  int nx = g->nx, ny = g->ny, nz = g->nz;
+  double gam = p[P_GAMMA], gz = p[P_GZ], nu = p[P_NU], eta = p[P_ETA];
+  double kap = p[P_KAPPA0], drho = p[P_DIFFRHO];
+  double eta_s = p[P_ETA_S], chi_s = p[P_CHI_S], drho_s = p[P_DIFFRHO_S];
+  double w = 0.0, wp = 0.0;
+  or_swamp_weight(p, (double)k * p[P_DZ], &w, &wp);
+  double A[3], U[3], D1A[3][3], D1U[3][3], lapA[3], lapU[3];
+  double gdA[3], gdU[3], gL[3], gT[3];
+  for (int c = 0; c < 3; ++c) {
+    A[c] = u[ix(g, F_AX + c, k, j, i)];
+    U[c] = u[ix(g, F_UX + c, k, j, i)];
+    lapA[c] = lapU[c] = 0.0;
+    for (int a = 0; a < 3; ++a) {
+      D1A[c][a] = d1(g, u, F_AX + c, k, j, i, a); /* d_a A_c */
+      D1U[c][a] = d1(g, u, F_UX + c, k, j, i, a); /* d_a u_c */
+      lapA[c] += d2(g, u, F_AX + c, k, j, i, a);
+      lapU[c] += d2(g, u, F_UX + c, k, j, i, a);
+    }
+  }
+  /* grad(div A)_a = sum_c d_a d_c A_c, with d_a d_a the second
+   * derivative and d_a d_c (a != c) the mixed one */
+  for (int a = 0; a < 3; ++a) {
+    gdA[a] = gdU[a] = 0.0;
+    for (int c = 0; c < 3; ++c) {
+      if (c == a) {
+        gdA[a] += d2(g, u, F_AX + c, k, j, i, a);
+        gdU[a] += d2(g, u, F_UX + c, k, j, i, a);
+      } else {
+        gdA[a] += d11(g, u, F_AX + c, k, j, i, a, c);
+        gdU[a] += d11(g, u, F_UX + c, k, j, i, a, c);
+      }
+    }
+  }
+  double lapL = 0.0, lapT = 0.0;
+  for (int a = 0; a < 3; ++a) {
+    gL[a] = d1(g, u, F_LNRHO, k, j, i, a);
+    gT[a] = d1(g, u, F_LNTT, k, j, i, a);
+    lapL += d2(g, u, F_LNRHO, k, j, i, a);
+    lapT += d2(g, u, F_LNTT, k, j, i, a);
+  }
+  double lnrho = u[ix(g, F_LNRHO, k, j, i)], lnT = u[ix(g, F_LNTT, k, j, i)];
+  double rho = exp(lnrho), T = exp(lnT);
+
+  double B[3] = {D1A[2][1] - D1A[1][2] + p[P_BEXT_X],
+                 D1A[0][2] - D1A[2][0] + p[P_BEXT_Y],
+                 D1A[1][0] - D1A[0][1] + p[P_BEXT_Z]};
+  double J[3];
+  for (int a = 0; a < 3; ++a) J[a] = gdA[a] - lapA[a];
+  double divA = D1A[0][0] + D1A[1][1] + D1A[2][2];
+  double divU = D1U[0][0] + D1U[1][1] + D1U[2][2];
+
+  /* induction */
+  double uxB[3] = {U[1] * B[2] - U[2] * B[1], U[2] * B[0] - U[0] * B[2],
+                   U[0] * B[1] - U[1] * B[0]};
+  double dA[3];
+  for (int a = 0; a < 3; ++a) dA[a] = uxB[a] - eta * J[a] + eta_s * w * lapA[a];
+  dA[2] += eta_s * wp * divA;
+
+  /* momentum */
+  double JxB[3] = {J[1] * B[2] - J[2] * B[1], J[2] * B[0] - J[0] * B[2],
+                   J[0] * B[1] - J[1] * B[0]};
+  double S[3][3], S2 = 0.0;
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) {
+      S[a][b] = 0.5 * (D1U[a][b] + D1U[b][a]) - (a == b ? divU / 3.0 : 0.0);
+      S2 += S[a][b] * S[a][b];
+    }
+  double dU[3];
+  for (int a = 0; a < 3; ++a) {
+    double adv = 0.0, SgL = 0.0;
+    for (int b = 0; b < 3; ++b) {
+      adv += U[b] * D1U[a][b];
+      SgL += S[a][b] * gL[b];
+    }
+    dU[a] = -adv - T * (gL[a] + gT[a]) + JxB[a] / rho +
+            nu * (lapU[a] + gdU[a] / 3.0 + 2.0 * SgL);
+  }
+  dU[2] += gz;
+
+  /* continuity */
+  double ugL = U[0] * gL[0] + U[1] * gL[1] + U[2] * gL[2];
+  double gL2 = gL[0] * gL[0] + gL[1] * gL[1] + gL[2] * gL[2];
+  double dL = -ugL - divU + drho * (lapL + gL2) + drho_s * w * lapL;
+
+  /* energy (ln T) */
+  double ugT = U[0] * gT[0] + U[1] * gT[1] + U[2] * gT[2];
+  double gT2 = gT[0] * gT[0] + gT[1] * gT[1] + gT[2] * gT[2];
+  double J2 = J[0] * J[0] + J[1] * J[1] + J[2] * J[2];
+  double heat = (gam - 1.0) * (eta * J2 + 2.0 * rho * nu * S2) / (rho * T);
+  double cond = (gam - 1.0) * kap * pow(T, 2.5) / rho * (lapT + 3.5 * gT2);
+  double dTh = -ugT - (gam - 1.0) * divU + heat + cond + chi_s * w * lapT;
+
+  if (g->bcz == 0) {
+    if (k == 0) {
+      double vx = v0[(size_t)j * nx + i] + s * (v1[(size_t)j * nx + i] - v0[(size_t)j * nx + i]);
+      double vy = v0[(size_t)nx * ny + (size_t)j * nx + i] +
+                  s * (v1[(size_t)nx * ny + (size_t)j * nx + i] - v0[(size_t)nx * ny + (size_t)j * nx + i]);
+      dA[0] -= p[P_TAU_A] * (A[0] - axt[(size_t)j * nx + i]);
+      dA[1] -= p[P_TAU_A] * (A[1] - ayt[(size_t)j * nx + i]);
+      dU[0] -= p[P_TAU_U] * (U[0] - r * vx);
+      dU[1] -= p[P_TAU_U] * (U[1] - r * vy);
+      dU[2] = 0.0;
+      dL = 0.0;
+    }
+    if (k == nz - 1) dU[2] = 0.0;
+  }
+  out[0] = dA[0]; out[1] = dA[1]; out[2] = dA[2];
+  out[3] = dU[0]; out[4] = dU[1]; out[5] = dU[2];
+  out[6] = dL; out[7] = dTh;
+}
+
 void or_rhs(const int* dims, const double* p, const double* u,
             const double* axt, const double* ayt, const double* v0,
             const double* v1, double t0, double t1, double t, double* rhs) {
   grid_t G = {dims[0], dims[1], dims[2], dims[3], p};
   const grid_t* g = &G;
   int nx = g->nx, ny = g->ny, nz = g->nz;
-  double gam = p[P_GAMMA], gz = p[P_GZ], nu = p[P_NU], eta = p[P_ETA];
-  double kap = p[P_KAPPA0], drho = p[P_DIFFRHO];
-  double eta_s = p[P_ETA_S], chi_s = p[P_CHI_S], drho_s = p[P_DIFFRHO_S];
   double r, s;
   driver_weights(p, t0, t1, t, &r, &s);
 
 #pragma omp parallel for schedule(static)
-  for (int k = 0; k < nz; ++k) {
-    double w = 0.0, wp = 0.0;
-    or_swamp_weight(p, (double)k * p[P_DZ], &w, &wp);
+  for (int k = 0; k < nz; ++k)
     for (int j = 0; j < ny; ++j)
       for (int i = 0; i < nx; ++i) {
-        double A[3], U[3], D1A[3][3], D1U[3][3], lapA[3], lapU[3];
-        double gdA[3], gdU[3], gL[3], gT[3];
-        for (int c = 0; c < 3; ++c) {
-          A[c] = u[ix(g, F_AX + c, k, j, i)];
-          U[c] = u[ix(g, F_UX + c, k, j, i)];
-          lapA[c] = lapU[c] = 0.0;
-          for (int a = 0; a < 3; ++a) {
-            D1A[c][a] = d1(g, u, F_AX + c, k, j, i, a); /* d_a A_c */
-            D1U[c][a] = d1(g, u, F_UX + c, k, j, i, a); /* d_a u_c */
-            lapA[c] += d2(g, u, F_AX + c, k, j, i, a);
-            lapU[c] += d2(g, u, F_UX + c, k, j, i, a);
-          }
-        }
-        /* grad(div A)_a = sum_c d_a d_c A_c, with d_a d_a the second
-         * derivative and d_a d_c (a != c) the mixed one */
-        for (int a = 0; a < 3; ++a) {
-          gdA[a] = gdU[a] = 0.0;
-          for (int c = 0; c < 3; ++c) {
-            if (c == a) {
-              gdA[a] += d2(g, u, F_AX + c, k, j, i, a);
-              gdU[a] += d2(g, u, F_UX + c, k, j, i, a);
-            } else {
-              gdA[a] += d11(g, u, F_AX + c, k, j, i, a, c);
-              gdU[a] += d11(g, u, F_UX + c, k, j, i, a, c);
-            }
-          }
-        }
-        double lapL = 0.0, lapT = 0.0;
-        for (int a = 0; a < 3; ++a) {
-          gL[a] = d1(g, u, F_LNRHO, k, j, i, a);
-          gT[a] = d1(g, u, F_LNTT, k, j, i, a);
-          lapL += d2(g, u, F_LNRHO, k, j, i, a);
-          lapT += d2(g, u, F_LNTT, k, j, i, a);
-        }
-        double lnrho = u[ix(g, F_LNRHO, k, j, i)], lnT = u[ix(g, F_LNTT, k, j, i)];
-        double rho = exp(lnrho), T = exp(lnT);
-
-        double B[3] = {D1A[2][1] - D1A[1][2] + p[P_BEXT_X],
-                       D1A[0][2] - D1A[2][0] + p[P_BEXT_Y],
-                       D1A[1][0] - D1A[0][1] + p[P_BEXT_Z]};
-        double J[3];
-        for (int a = 0; a < 3; ++a) J[a] = gdA[a] - lapA[a];
-        double divA = D1A[0][0] + D1A[1][1] + D1A[2][2];
-        double divU = D1U[0][0] + D1U[1][1] + D1U[2][2];
-
-        /* induction */
-        double uxB[3] = {U[1] * B[2] - U[2] * B[1], U[2] * B[0] - U[0] * B[2],
-                         U[0] * B[1] - U[1] * B[0]};
-        double dA[3];
-        for (int a = 0; a < 3; ++a) dA[a] = uxB[a] - eta * J[a] + eta_s * w * lapA[a];
-        dA[2] += eta_s * wp * divA;
-
-        /* momentum */
-        double JxB[3] = {J[1] * B[2] - J[2] * B[1], J[2] * B[0] - J[0] * B[2],
-                         J[0] * B[1] - J[1] * B[0]};
-        double S[3][3], S2 = 0.0;
-        for (int a = 0; a < 3; ++a)
-          for (int b = 0; b < 3; ++b) {
-            S[a][b] = 0.5 * (D1U[a][b] + D1U[b][a]) - (a == b ? divU / 3.0 : 0.0);
-            S2 += S[a][b] * S[a][b];
-          }
-        double dU[3];
-        for (int a = 0; a < 3; ++a) {
-          double adv = 0.0, SgL = 0.0;
-          for (int b = 0; b < 3; ++b) {
-            adv += U[b] * D1U[a][b];
-            SgL += S[a][b] * gL[b];
-          }
-          dU[a] = -adv - T * (gL[a] + gT[a]) + JxB[a] / rho +
-                  nu * (lapU[a] + gdU[a] / 3.0 + 2.0 * SgL);
-        }
-        dU[2] += gz;
-
-        /* continuity */
-        double ugL = U[0] * gL[0] + U[1] * gL[1] + U[2] * gL[2];
-        double gL2 = gL[0] * gL[0] + gL[1] * gL[1] + gL[2] * gL[2];
-        double dL = -ugL - divU + drho * (lapL + gL2) + drho_s * w * lapL;
-
-        /* energy (ln T) */
-        double ugT = U[0] * gT[0] + U[1] * gT[1] + U[2] * gT[2];
-        double gT2 = gT[0] * gT[0] + gT[1] * gT[1] + gT[2] * gT[2];
-        double J2 = J[0] * J[0] + J[1] * J[1] + J[2] * J[2];
-        double heat = (gam - 1.0) * (eta * J2 + 2.0 * rho * nu * S2) / (rho * T);
-        double cond = (gam - 1.0) * kap * pow(T, 2.5) / rho * (lapT + 3.5 * gT2);
-        double dTh = -ugT - (gam - 1.0) * divU + heat + cond + chi_s * w * lapT;
-
-        if (g->bcz == 0) {
-          if (k == 0) {
-            double vx = v0[(size_t)j * nx + i] + s * (v1[(size_t)j * nx + i] - v0[(size_t)j * nx + i]);
-            double vy = v0[(size_t)nx * ny + (size_t)j * nx + i] +
-                        s * (v1[(size_t)nx * ny + (size_t)j * nx + i] - v0[(size_t)nx * ny + (size_t)j * nx + i]);
-            dA[0] -= p[P_TAU_A] * (A[0] - axt[(size_t)j * nx + i]);
-            dA[1] -= p[P_TAU_A] * (A[1] - ayt[(size_t)j * nx + i]);
-            dU[0] -= p[P_TAU_U] * (U[0] - r * vx);
-            dU[1] -= p[P_TAU_U] * (U[1] - r * vy);
-            dU[2] = 0.0;
-            dL = 0.0;
-          }
-          if (k == nz - 1) dU[2] = 0.0;
-        }
-        rhs[ix(g, F_AX, k, j, i)] = dA[0];
-        rhs[ix(g, F_AY, k, j, i)] = dA[1];
-        rhs[ix(g, F_AZ, k, j, i)] = dA[2];
-        rhs[ix(g, F_UX, k, j, i)] = dU[0];
-        rhs[ix(g, F_UY, k, j, i)] = dU[1];
-        rhs[ix(g, F_UZ, k, j, i)] = dU[2];
-        rhs[ix(g, F_LNRHO, k, j, i)] = dL;
-        rhs[ix(g, F_LNTT, k, j, i)] = dTh;
+        double o8[8];
+        rhs_cell(g, u, axt, ayt, v0, v1, r, s, k, j, i, o8);
+        for (int f = 0; f < NFIELD; ++f) rhs[ix(g, f, k, j, i)] = o8[f];
       }
-  }
 
   if (g->bcz == 0) {
     /* ghost layers of u_hor below the photosphere: nudging only (Eq. 5) */
@@ -525,6 +531,20 @@ void or_rhs(const int* dims, const double* p, const double* u,
           rhs[ix(g, F_UY, -m, j, i)] = -p[P_TAU_U] * (u[ix(g, F_UY, -m, j, i)] - r * vy);
         }
   }
+}
+
+/* Right-hand side at a list of cells: cells[3 c + 0..2] = (k, j, i);
+ * out[8 c + f].  Same arithmetic as or_rhs, for sampled checks of large
+ * grids. */
+void or_rhs_cells(const int* dims, const double* p, const double* u, const double* axt,
+                  const double* ayt, const double* v0, const double* v1, double t0, double t1,
+                  double t, int ncell, const int* cells, double* out) {
+  grid_t G = {dims[0], dims[1], dims[2], dims[3], p};
+  double r, s;
+  driver_weights(p, t0, t1, t, &r, &s);
+#pragma omp parallel for schedule(static)
+  for (int c = 0; c < ncell; ++c)
+    rhs_cell(&G, u, axt, ayt, v0, v1, r, s, cells[3 * c], cells[3 * c + 1], cells[3 * c + 2], out + 8 * c);
 }
 
 /* Magnetic field B = curl A + B_ext at an interior cell (Eq. 6). */

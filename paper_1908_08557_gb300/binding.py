@@ -24,6 +24,7 @@ MHD_ERR_WORKSPACE = -2
 MHD_ERR_CUDA = -3
 MHD_ERR_NONFINITE = -4
 MHD_ERR_UNSUPPORTED = -5
+MHD_ERR_TIMEOUT = -6
 MHD_MEM_DEVICE = 0
 MHD_MEM_HOST = 1
 NFIELD = 8

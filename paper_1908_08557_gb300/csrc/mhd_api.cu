@@ -15,6 +15,8 @@
 using namespace mhd;
 
 struct mhd_ctx {
+  CUtensorMap tm[2];   // TMA descriptors of the two FP32 state sets (64-byte aligned)
+  bool tiled;          // FP32: TMA-fed z-march kernel; otherwise the simple kernel
   mhd_params p;
   Layout L;
   cudaStream_t st;
@@ -335,6 +337,23 @@ static void run_stats(mhd_ctx* h, R* f) {
   launch_stats_finalize(h->red, nb, h->ss, h->p.dx * h->p.dy * h->p.dz, h->p.dx * h->p.dy, h->st);
 }
 
+// fused RHS + RK launch: TMA-fed z-march for FP32 (unless disabled), the
+// simple one-thread-per-cell kernel otherwise
+template <typename R>
+static void launch_rk_any(mhd_ctx* h, const R* fin, R* fout, int sub) {
+  Phys<R> ph = make_phys<R>(&h->p);
+  Driver drv{h->axt, h->ayt, h->v0, h->v1};
+  if (sizeof(R) == 4 && h->tiled) {
+    const int which = (const void*)fin == h->f[0] ? 0 : 1;
+    launch_rk_tiled(&h->tm[which], h->L, *(const Phys<float>*)&ph, h->bgf, (float*)fout, (float*)h->df,
+                    (const float*)h->wtab, (const float*)h->wptab, drv, h->ss, sub, h->p.dx, h->p.dy, h->p.dz,
+                    h->st);
+    return;
+  }
+  launch_rk<R>(h->L, ph, bgr<R>(h), fin, fout, (R*)h->df, (const R*)h->wtab, (const R*)h->wptab, drv, h->ss, sub,
+               h->st);
+}
+
 template <typename R>
 static void run_step(mhd_ctx* h, bool stats) {
   Phys<R> ph = make_phys<R>(&h->p);
@@ -354,8 +373,7 @@ static void run_step(mhd_ctx* h, bool stats) {
     }
     {
       ClassTimer ct(h, MHD_KC_RK, 1);
-      launch_rk<R>(h->L, ph, bgr<R>(h), fin, fout, (R*)h->df, (const R*)h->wtab, (const R*)h->wptab, drv, h->ss,
-                   sub, h->st);
+      launch_rk_any<R>(h, fin, fout, sub);
     }
     h->cur = 1 - h->cur;
   }
@@ -441,8 +459,11 @@ extern "C" int mhd_create(const mhd_params* p, void* workspace, size_t ws_bytes,
   if (ws_bytes < o.total)
     return fail(nullptr, MHD_ERR_WORKSPACE, "workspace too small: %zu < %zu bytes", ws_bytes, o.total);
 
-  mhd_ctx* h = (mhd_ctx*)calloc(1, sizeof(mhd_ctx));
-  if (!h) return fail(nullptr, MHD_ERR_ARG, "host allocation failed");
+  void* mem_ctx = nullptr;
+  if (posix_memalign(&mem_ctx, 64, sizeof(mhd_ctx)) != 0 || !mem_ctx)
+    return fail(nullptr, MHD_ERR_ARG, "host allocation failed");
+  memset(mem_ctx, 0, sizeof(mhd_ctx));
+  mhd_ctx* h = (mhd_ctx*)mem_ctx;
   h->p = *p;
   h->L = make_layout(p->nx, p->ny, p->nz);
   h->st = (cudaStream_t)stream;
@@ -464,6 +485,10 @@ extern "C" int mhd_create(const mhd_params* p, void* workspace, size_t ws_bytes,
   h->ss = (StepState*)(h->ws + o.ss);
   h->bgtab = h->ws + o.bg;
   h->have_fft = p->bc_z == 0;
+  {
+    const char* v = getenv("MHD_RK_VARIANT");
+    h->tiled = p->precision == 32 && !(v && strcmp(v, "simple") == 0);
+  }
   h->t0 = 0.0;
   h->t1 = 0.0;
   snprintf(h->err, sizeof h->err, "no error");
@@ -490,6 +515,11 @@ extern "C" int mhd_create(const mhd_params* p, void* workspace, size_t ws_bytes,
                                             cudaMemcpyHostToDevice), "upload wp");
   }
   if (!rc && h->have_fft) rc = upload_fft_tables(h, o);
+  if (!rc && h->tiled) {
+    for (int s = 0; s < 2 && !rc; ++s)
+      if (make_state_tensor_map(&h->tm[s], h->L, h->f[s]) != 0)
+        rc = fail(h, MHD_ERR_CUDA, "cuTensorMapEncodeTiled failed for state set %d", s);
+  }
   if (!rc) {
     StepState s0;
     memset(&s0, 0, sizeof s0);
@@ -656,16 +686,8 @@ extern "C" int mhd_eval_rhs(mhd_handle h, double t, void* dst, int mem) {
   if (rc) return rc;
   rc = cuda_check(h, cudaMemsetAsync(h->df, 0, (size_t)NF * h->L.fs * h->esz, h->st), "zero df");
   if (rc) return rc;
-  Driver drv{h->axt, h->ayt, h->v0, h->v1};
-  if (h->esz == 8) {
-    Phys<double> ph = make_phys<double>(&h->p);
-    launch_rk<double>(h->L, ph, h->bgd, (const double*)h->f[h->cur], nullptr, (double*)h->df, (const double*)h->wtab,
-                      (const double*)h->wptab, drv, h->ss, -1, h->st);
-  } else {
-    Phys<float> ph = make_phys<float>(&h->p);
-    launch_rk<float>(h->L, ph, h->bgf, (const float*)h->f[h->cur], nullptr, (float*)h->df, (const float*)h->wtab,
-                     (const float*)h->wptab, drv, h->ss, -1, h->st);
-  }
+  if (h->esz == 8) launch_rk_any<double>(h, (const double*)h->f[h->cur], nullptr, -1);
+  else launch_rk_any<float>(h, (const float*)h->f[h->cur], nullptr, -1);
   rc = cuda_check(h, cudaSuccess, "rhs");
   if (rc) return rc;
   if (mem == MHD_MEM_HOST) {
@@ -721,6 +743,7 @@ extern "C" int mhd_compute_stats(mhd_handle h, mhd_stats* out) {
   if (rc) return rc;
   rc = fetch_stats(h, out);
   if (rc) return rc;
+  if (out->nonfinite & 2) return fail(h, MHD_ERR_TIMEOUT, "a device wait exceeded its bound");
   if (out->nonfinite) return fail(h, MHD_ERR_NONFINITE, "non-finite value in the state");
   return MHD_OK;
 }
@@ -731,6 +754,7 @@ extern "C" int mhd_read_stats(mhd_handle h, mhd_stats* out) {
   if (rc) return rc;
   rc = fetch_stats(h, out);
   if (rc) return rc;
+  if (out->nonfinite & 2) return fail(h, MHD_ERR_TIMEOUT, "a device wait exceeded its bound (time stepping halted)");
   if (out->nonfinite) return fail(h, MHD_ERR_NONFINITE, "non-finite value in the state (time stepping halted)");
   return MHD_OK;
 }
@@ -745,6 +769,7 @@ extern "C" int mhd_get_time(mhd_handle h, double* t, double* dt) {
   if (rc) return rc;
   *t = td[0];
   *dt = td[1];
+  if (nf & 2) return fail(h, MHD_ERR_TIMEOUT, "a device wait exceeded its bound (time stepping halted)");
   if (nf) return fail(h, MHD_ERR_NONFINITE, "non-finite value in the state (time stepping halted)");
   return MHD_OK;
 }

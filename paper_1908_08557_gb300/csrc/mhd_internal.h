@@ -1,5 +1,6 @@
 // mhd_internal.h -- launchers shared between the translation units of libmhd.
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include "mhd_common.cuh"
 
@@ -46,6 +47,11 @@ template <typename R> void launch_rk(const Layout& L, const Phys<R>& ph, const B
                                      const R* fin, R* fout, R* df,
                                      const R* wtab, const R* wptab, const Driver& drv, const StepState* ss,
                                      int sub, cudaStream_t st);
+// FP32 TMA-fed variant of launch_rk (tensor map of the input state set)
+void launch_rk_tiled(const CUtensorMap* tm, const Layout& L, const Phys<float>& ph, const Background<float>& bg,
+                     float* fout, float* df, const float* wtab, const float* wptab, const Driver& drv,
+                     StepState* ss, int sub, double dx, double dy, double dz, cudaStream_t st);
+int make_state_tensor_map(CUtensorMap* tm, const Layout& L, void* base);
 // reductions
 template <typename R> int launch_cfl_partial(const Layout& L, const Phys<R>& ph, const Background<R>& bg,
                                              const R* f, const R* wtab,

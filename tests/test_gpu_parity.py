@@ -202,3 +202,76 @@ def test_nonfinite_detected():
     with pytest.raises(MHDError) as e:
         sim.time()
     assert e.value.code == MHD_ERR_NONFINITE
+
+
+def _eval_with_variant(case, variant, t=0.29, params=None, driver=True):
+    import os
+    old = os.environ.get("MHD_RK_VARIANT")
+    os.environ["MHD_RK_VARIANT"] = variant
+    try:
+        sim = _sim(case, 32, params=params, driver=driver)
+    finally:
+        if old is None:
+            del os.environ["MHD_RK_VARIANT"]
+        else:
+            os.environ["MHD_RK_VARIANT"] = old
+    sim.fill_ghosts()
+    out = sim.eval_rhs(t).astype(np.float64)
+    u = sim.read_padded(0).astype(np.float64)
+    sim.close()
+    return out, u
+
+
+@pytest.mark.parametrize("shape,bcz", [((16, 16, 12), 0), ((64, 32, 41), 0), ((40, 24, 20), 1)])
+def test_tiled_kernel_matches_simple_fp32(shape, bcz):
+    """The TMA-fed z-march kernel against the one-thread-per-cell kernel:
+    same FP32 discretisation, different summation order; tiles ragged in x
+    (16 < 32) and chunks ragged in z (41 layers)."""
+    nx, ny, nz = shape
+    case = _perturbed(nx, ny, nz, seed=11)
+    p = dict(case.params, bc_z=bcz)
+    a, ua = _eval_with_variant(case, "tiled", params=p, driver=(bcz == 0))
+    b, ub = _eval_with_variant(case, "simple", params=p, driver=(bcz == 0))
+    assert np.array_equal(ua, ub)
+    for f in range(8):
+        s = np.abs(b[f]).max()
+        assert np.abs(a[f] - b[f]).max() <= 2e-5 * max(s, 1e-30), f
+
+
+def test_tiled_full_size_sampled_bipoles40_256():
+    """Bench workload bipoles40_256x256x256 in the bench configuration (FP32,
+    tiled kernel): ghost fill + RHS at 3000 sampled cells -- random, plus the
+    photosphere, the top layer, the swamp and the x,y edges -- against the
+    FP64 oracle, which fills its own ghosts (plain DFT) and evaluates the
+    sampled cells one by one.  Both sides start from the same values: A and u
+    rounded to FP32, ln rho and ln T the exact FP64 profiles (the GPU stores
+    them as zero perturbations about those profiles)."""
+    case = inputs.make_case("bipoles40_256x256x256")
+    rng = np.random.default_rng(0)
+    st = case.state.copy()
+    st[3:6] += 0.01 * rng.standard_normal(st[3:6].shape)
+    st[0:6] = st[0:6].astype(np.float32).astype(np.float64)
+    case.state = st
+    sim = _sim(case, 32)
+    sim.fill_ghosts()
+    t = 0.21
+    got = sim.eval_rhs(t)
+    sim.close()
+    p = case.params
+    nx, ny, nz = p["nx"], p["ny"], p["nz"]
+    u = oracle.to_padded(st)
+    oracle.fill_ghosts(p, u, case.lnrho0)
+    ks = np.concatenate([rng.integers(0, nz, 2000), np.zeros(300, int), np.full(300, nz - 1),
+                         rng.integers(nz - 5, nz, 200), rng.integers(0, nz, 200)])
+    js = rng.integers(0, ny, len(ks))
+    iss = rng.integers(0, nx, len(ks))
+    iss[-200:] = rng.choice([0, 1, 2, nx - 3, nx - 2, nx - 1], 200)
+    js[-100:] = rng.choice([0, 1, 2, ny - 3, ny - 2, ny - 1], 100)
+    cells = np.stack([ks, js, iss], axis=1)
+    f32 = lambda a: a.astype(np.float32).astype(np.float64)
+    axt, ayt = (f32(x) for x in oracle.a_target(p, case.bz))
+    ref = oracle.rhs_cells(p, u, axt, ayt, f32(case.v0), f32(case.v1), case.t0, case.t1, t, cells)
+    g = got[:, ks + NG, js + NG, iss + NG].T.astype(np.float64)
+    for f in range(8):
+        s = np.abs(ref[:, f]).max()
+        assert np.abs(g[:, f] - ref[:, f]).max() <= 2e-4 * max(s, 1e-30), (f, np.abs(g[:, f] - ref[:, f]).max(), s)
