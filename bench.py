@@ -142,14 +142,16 @@ def rk_traffic_bytes():
     """Per-launch DRAM traffic of the RK kernel from the committed ncu summary,
     valid only if the kernel source is unchanged since the capture."""
     path = os.path.join(ROOT, "profiles", "rk_traffic.txt")
-    src = os.path.join(ROOT, "paper_1908_08557_gb300", "csrc", "mhd_rk.cu")
+    csrc = os.path.join(ROOT, "paper_1908_08557_gb300", "csrc")
     try:
         kv = {}
         for line in open(path):
             if line.strip() and not line.startswith("#"):
                 k, v = line.split(None, 1)
                 kv[k] = v.strip()
-        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        blob = open(os.path.join(csrc, "mhd_rk_tiled.cu"), "rb").read() + \
+            open(os.path.join(csrc, "mhd_common.cuh"), "rb").read()
+        sha = hashlib.sha256(blob).hexdigest()[:16]
         if kv.get("kernel_source_sha") != sha:
             return None
         return float(kv["bytes_per_launch_scaled"])
@@ -257,7 +259,7 @@ def run_native(args, ws, rank, local):
     peaks = measured_peaks()
     peak = peaks["hbm_gbs"] if peaks and "hbm_gbs" in peaks else 6800.0
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": rk_traffic_bytes(), "kernel": "rk (fused RHS + RK update)",
+                "traffic": rk_traffic_bytes(), "kernel": "rk_tiled_kernel (fused RHS + RK update, TMA z-march)",
                 "peak_source": "measured" if peaks else "fallback",
                 "alg_bytes_per_launch": alg_bytes_per_launch, "avg_launch_ms": rk_ms / rk_n,
                 "class_ms_per_step": {k: v[0] / nprof for k, v in prof.items()}}
