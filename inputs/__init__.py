@@ -111,10 +111,13 @@ def magnetogram_spots(nx, ny, n_spots, sigma, seed):
     return flux_balance(bz)
 
 
+BIPOLE_PEAK = 0.3
+
+
 def magnetogram_bipoles(nx, ny, n_bipoles, seed, sigma=3.0, sep=(4.0, 16.0),
                         ar_pair: Optional[Tuple[float, float, float]] = None):
     """Bipoles with log-normal fluxes (mu 0, sigma 1; the flux unit is that of
-    a pole with peak |B_z| = 1), separations uniform in
+    a pole with peak |B_z| = BIPOLE_PEAK), separations uniform in
     `sep` cells, uniform orientation and centre; optional active-region pair
     (amplitude, sigma, separation in cells) at the centre of the box."""
     rng = np.random.default_rng(seed)
@@ -124,10 +127,11 @@ def magnetogram_bipoles(nx, ny, n_bipoles, seed, sigma=3.0, sep=(4.0, 16.0),
         d = rng.uniform(*sep)
         th = rng.uniform(0.0, 2.0 * math.pi)
         xc, yc = rng.uniform(0, nx), rng.uniform(0, ny)
-        # flux in units of 2 pi sigma^2: the median pole peaks at |B_z| = 1,
-        # plasma beta ~ 2 at the photosphere where p = 1 (Sect. 2.1: beta is
-        # near or above unity there)
-        amp = flux
+        # the median pole peaks at |B_z| = 0.3: with p = 1 at the photosphere
+        # even the strongest of 40 log-normal poles keeps plasma beta >~ 1
+        # (Sect. 2.1: beta is near or above unity in the photosphere); a
+        # 4x stronger unit drove grid-scale growth at the strongest pole
+        amp = BIPOLE_PEAK * flux
         dx, dy = 0.5 * d * math.cos(th), 0.5 * d * math.sin(th)
         bz += amp * _periodic_gauss(nx, ny, (xc + dx) % nx, (yc + dy) % ny, sigma)
         bz -= amp * _periodic_gauss(nx, ny, (xc - dx) % nx, (yc - dy) % ny, sigma)

@@ -66,15 +66,14 @@ __device__ double2* fft_lines(double2* a, double2* b, int n, int logn, int nb, c
 template <typename R>
 __global__ void __launch_bounds__(256) rows_fwd_kernel(FFTPlan fp, Layout L, const R* __restrict__ f,
                                                        const R* __restrict__ src2d, int mode,
-                                                       const StepState* ss) {
+                                                       const StepState* ss, int nb) {
   extern __shared__ double2 sm[];
   if (ss && halted(ss)) return;
   const int nx = fp.nx, ny = fp.ny;
-  const int nb = min(FFT_PTS / nx, ny);
   const int y0 = blockIdx.x * nb;
   const int p = blockIdx.y;
   double2* a = sm;
-  double2* b = sm + FFT_PTS;
+  double2* b = sm + nb * nx;
   const int kt = L.nz - 1;
   for (int q = threadIdx.x; q < nb * nx; q += blockDim.x) {
     const int line = q / nx, x = q - line * nx, y = y0 + line;
@@ -108,19 +107,19 @@ __global__ void __launch_bounds__(256) rows_fwd_kernel(FFTPlan fp, Layout L, con
 // are needed to split the packed plane P2 (F(-k) lives in the mirror column).
 // mode 0: potential-field extrapolation, 3 layers; mode 1: magnetogram
 // inversion (Eq. 7): A^_x + i A^_y = (kt_x + i kt_y) B^_z / kt^2.
-__global__ void __launch_bounds__(256) cols_kernel(FFTPlan fp, int mode, const StepState* ss) {
+__global__ void __launch_bounds__(256) cols_kernel(FFTPlan fp, int mode, const StepState* ss, int ppb) {
   extern __shared__ double2 sm[];
   if (ss && halted(ss)) return;
   const int nx = fp.nx, ny = fp.ny;
   const int npairs = nx / 2 + 1;
-  const int ppb = max(1, FFT_PTS / (2 * ny));  // pairs per block
-  const int pair0 = blockIdx.x * ppb;
+  const int pair0 = blockIdx.x * ppb;  // ppb column pairs per block
   const int np = min(ppb, npairs - pair0);
   const int nl = 2 * np;
   const int p = blockIdx.y;
+  const int buf = 2 * ppb * ny;
   double2* S = sm;
-  double2* Wa = sm + FFT_PTS;
-  double2* Wb = sm + 2 * FFT_PTS;
+  double2* Wa = sm + buf;
+  double2* Wb = sm + 2 * buf;
   // columns of line l: pair (l >> 1), mirror if odd
   for (int q = threadIdx.x; q < nl * ny; q += blockDim.x) {
     const int line = q / ny, y = q - line * ny;
@@ -185,16 +184,15 @@ __global__ void __launch_bounds__(256) cols_kernel(FFTPlan fp, int mode, const S
 // state, mode 1 the compact planes out_re, out_im ([ny][nx]).
 template <typename R>
 __global__ void __launch_bounds__(256) rows_inv_kernel(FFTPlan fp, Layout L, R* __restrict__ f, R* out_re,
-                                                       R* out_im, int mode, const StepState* ss) {
+                                                       R* out_im, int mode, const StepState* ss, int nb) {
   extern __shared__ double2 sm[];
   if (ss && halted(ss)) return;
   const int nx = fp.nx, ny = fp.ny;
-  const int nb = min(FFT_PTS / nx, ny);
   const int y0 = blockIdx.x * nb;
   const int p = blockIdx.y, o = blockIdx.z;
   const int nplanes = mode == 0 ? 3 : 1;
   double2* a = sm;
-  double2* b = sm + FFT_PTS;
+  double2* b = sm + nb * nx;
   for (int q = threadIdx.x; q < nb * nx; q += blockDim.x) {
     const int x = q / nb, line = q - x * nb;
     a[line * nx + x] = fp.Q[(((long long)o * nplanes + p) * nx + x) * ny + y0 + line];
@@ -242,27 +240,46 @@ static void set_smem_once() {
   cudaFuncSetAttribute(cols_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 3 * FFT_PTS * 16);
 }
 
+// batch sizes: rows per block (nb) so a block holds ~1024 points, column
+// pairs per block (ppb) so there are enough blocks for every SM; shared
+// memory sized to the batch
+struct FFTLaunch {
+  int nb, ppb;
+  size_t smem_rows, smem_cols;
+};
+
+static FFTLaunch fft_launch(const FFTPlan& fp) {
+  FFTLaunch l;
+  l.nb = 1024 / fp.nx;
+  if (l.nb < 1) l.nb = 1;
+  if (l.nb > fp.ny) l.nb = fp.ny;
+  l.ppb = 256 / fp.ny;
+  if (l.ppb < 1) l.ppb = 1;
+  l.smem_rows = (size_t)2 * l.nb * fp.nx * sizeof(double2);
+  l.smem_cols = (size_t)3 * 2 * l.ppb * fp.ny * sizeof(double2);
+  return l;
+}
+
 template <typename R>
 void launch_pfe(const FFTPlan& fp, const Layout& L, R* f, const StepState* ss, cudaStream_t st) {
   set_smem_once();
-  const int nb = FFT_PTS / fp.nx < fp.ny ? FFT_PTS / fp.nx : fp.ny;
-  const int ppb = FFT_PTS / (2 * fp.ny) > 1 ? FFT_PTS / (2 * fp.ny) : 1;
+  const FFTLaunch l = fft_launch(fp);
   const int npairs = fp.nx / 2 + 1;
-  rows_fwd_kernel<R><<<dim3(fp.ny / nb, 3), 256, 2 * FFT_PTS * 16, st>>>(fp, L, f, nullptr, 0, ss);
-  cols_kernel<<<dim3((npairs + ppb - 1) / ppb, 3), 256, 3 * FFT_PTS * 16, st>>>(fp, 0, ss);
-  rows_inv_kernel<R><<<dim3(fp.ny / nb, 3, 3), 256, 2 * FFT_PTS * 16, st>>>(fp, L, f, nullptr, nullptr, 0, ss);
+  rows_fwd_kernel<R><<<dim3(fp.ny / l.nb, 3), 256, l.smem_rows, st>>>(fp, L, f, nullptr, 0, ss, l.nb);
+  cols_kernel<<<dim3((npairs + l.ppb - 1) / l.ppb, 3), 256, l.smem_cols, st>>>(fp, 0, ss, l.ppb);
+  rows_inv_kernel<R><<<dim3(fp.ny / l.nb, 3, 3), 256, l.smem_rows, st>>>(fp, L, f, nullptr, nullptr, 0, ss, l.nb);
 }
 
 template <typename R>
 void launch_atarget(const FFTPlan& fp, const R* bz, R* axt, R* ayt, cudaStream_t st) {
   set_smem_once();
   Layout L{};
-  const int nb = FFT_PTS / fp.nx < fp.ny ? FFT_PTS / fp.nx : fp.ny;
-  const int ppb = FFT_PTS / (2 * fp.ny) > 1 ? FFT_PTS / (2 * fp.ny) : 1;
+  const FFTLaunch l = fft_launch(fp);
   const int npairs = fp.nx / 2 + 1;
-  rows_fwd_kernel<R><<<dim3(fp.ny / nb, 1), 256, 2 * FFT_PTS * 16, st>>>(fp, L, nullptr, bz, 1, nullptr);
-  cols_kernel<<<dim3((npairs + ppb - 1) / ppb, 1), 256, 3 * FFT_PTS * 16, st>>>(fp, 1, nullptr);
-  rows_inv_kernel<R><<<dim3(fp.ny / nb, 1, 1), 256, 2 * FFT_PTS * 16, st>>>(fp, L, nullptr, axt, ayt, 1, nullptr);
+  rows_fwd_kernel<R><<<dim3(fp.ny / l.nb, 1), 256, l.smem_rows, st>>>(fp, L, nullptr, bz, 1, nullptr, l.nb);
+  cols_kernel<<<dim3((npairs + l.ppb - 1) / l.ppb, 1), 256, l.smem_cols, st>>>(fp, 1, nullptr, l.ppb);
+  rows_inv_kernel<R><<<dim3(fp.ny / l.nb, 1, 1), 256, l.smem_rows, st>>>(fp, L, nullptr, axt, ayt, 1, nullptr,
+                                                                          l.nb);
 }
 
 template void launch_pfe<float>(const FFTPlan&, const Layout&, float*, const StepState*, cudaStream_t);

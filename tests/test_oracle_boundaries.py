@@ -232,3 +232,5 @@ def test_generated_magnetograms_are_flux_balanced():
         c = inputs.make_case(name)
         assert abs(c.bz.sum()) < 1e-12 * np.abs(c.bz).sum()
         assert np.abs(c.bz).max() > 0.1
+        # photospheric plasma beta 2 p / B^2 (p = 1) near or above unity
+        assert 2.0 / np.abs(c.bz).max() ** 2 > 0.8
