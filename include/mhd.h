@@ -66,6 +66,7 @@ typedef struct mhd_params {
   int precision;       /* 32 or 64: state storage and stencil arithmetic */
   int bc_z;            /* 0: the paper's boundaries; 1: periodic in z (tests) */
   int stats_every;     /* compute diagnostics every n steps (0: never) */
+  int adjoint;         /* 1: also reserve the buffers of mhd_adjoint_step */
   double dx, dy, dz;
   double gamma;        /* ratio of specific heats */
   double gz;           /* gravity, signed (< 0 points down) */
@@ -151,6 +152,9 @@ int mhd_write(mhd_handle h, const void* src, int mem);
  * computed them (stats_every), plus time, dt and step count. */
 int mhd_read_stats(mhd_handle h, mhd_stats* out);
 
+/* Set the time of the current state (e.g. to restart a run at t = 0). */
+int mhd_set_time(mhd_handle h, double t);
+
 /* Synchronise and return the current time and the last time step. */
 int mhd_get_time(mhd_handle h, double* t, double* dt);
 
@@ -184,6 +188,56 @@ int mhd_compute_stats(mhd_handle h, mhd_stats* out);
 /* Copy the vector potential of the driver magnetogram, A_x then A_y, as
  * [2][ny][nx] into dst. */
 int mhd_read_target(mhd_handle h, void* dst, int mem);
+
+/* ---- adjoint (gradients of a loss on the final state) ----
+ *
+ * The transposed linearisation of mhd_step with a frozen time step
+ * (dt_fixed > 0; the CFL rule is not differentiable), for handles created
+ * with params.adjoint = 1 and bc_z = 0.  Parameters: the driver magnetogram
+ * B_z (through the inversion of Eq. 7 and the magnetic nudging of Sect. 2.1)
+ * and the two driver velocity snapshots v0, v1 (through the velocity nudging
+ * of Eq. 5 at the photosphere and in its three ghost layers).  Usage: save
+ * checkpoints while stepping forward; seed the adjoint with dL/d(final
+ * state); for each step in reverse order restore the state at its start and
+ * call mhd_adjoint_step; read the gradients.  Reverse accumulation over many
+ * steps with few checkpoints (binomial checkpointing) is scheduled by the
+ * caller. */
+
+/* Bytes of one checkpoint (the padded state, including the stateful
+ * velocity ghosts). */
+size_t mhd_checkpoint_bytes(mhd_handle h);
+
+/* Copy the current state into dst (device memory of mhd_checkpoint_bytes)
+ * and return its time in *t (synchronising). */
+int mhd_save(mhd_handle h, void* dst, double* t);
+
+/* Make a saved state (device memory) the current state at time t. */
+int mhd_restore(mhd_handle h, const void* src, double t);
+
+/* Start a reverse sweep: the state adjoint is set to lam ([8][nz][ny][nx],
+ * dL/d(final state); zero in the ghost layers), the RK accumulator adjoint
+ * and the parameter gradients to zero. */
+int mhd_adjoint_init(mhd_handle h, const void* lam, int mem);
+
+/* One reverse step: the current state (restored) is the state f_n at the
+ * start of a step; the forward substeps are recomputed from it, then the
+ * state adjoint is taken from step n+1 back to step n and the parameter
+ * gradients are accumulated.  The forward state after the call is that of
+ * f_n again (time undefined until the next mhd_restore). */
+int mhd_adjoint_step(mhd_handle h);
+
+/* Read the results of a reverse sweep: lam ([8][nz][ny][nx]) the adjoint of
+ * the state at the sweep's current step (the velocity ghost adjoints folded
+ * onto the photospheric layer, matching how mhd_create initialises them),
+ * grad_bz ([ny][nx]), grad_v0, grad_v1 ([2][ny][nx]); any may be NULL. */
+int mhd_adjoint_read(mhd_handle h, void* lam, void* grad_bz, void* grad_v0, void* grad_v1, int mem);
+
+/* Loss helper: B_z = D1x A_y - D1y A_x on layer k of a state
+ * ([8][nz][ny][nx], device) into out ([ny][nx], device), and the transpose:
+ * given bbar ([ny][nx], device) write lam ([8][nz][ny][nx], device): zero
+ * except A_x and A_y on layer k. */
+int mhd_bz_plane(mhd_handle h, const void* state, int k, void* out);
+int mhd_bz_plane_adjoint(mhd_handle h, const void* bbar, int k, void* lam);
 
 /* ---- allocation-free variant ---- */
 

@@ -1,0 +1,147 @@
+"""Gradients of a loss on the final state of an N-step driven run with
+respect to the driver magnetogram B_z and the driver velocity snapshots
+v0, v1, through the library's hand-written adjoint step.
+
+* `binomial_split`, `Revolver`: binomial checkpointing (the treeverse
+  recursion of Griewank 1992, "Achieving logarithmic growth of temporal and
+  spatial complexity in reverse automatic differentiation"): with s free
+  checkpoint slots an interval of l steps is split so that the right part
+  can be reversed with s - 1 slots and the left part with s slots.  The
+  checkpoints along the rightmost chain of splits are taken during the
+  forward sweep; the reverse sweep recomputes the rest.
+* `DrivenRun`: a torch.autograd.Function (B_z, v0, v1) -> final state.
+* `BzPlane`: B_z on one layer of a state, with its transpose, for misfit
+  losses (the adjoint workload's loss is the L2 misfit of B_z at one height).
+
+All arithmetic runs in libmhd; this module schedules calls and holds the
+checkpoint buffers (torch device memory).
+"""
+from __future__ import annotations
+
+from math import comb
+from typing import Dict, List, Optional
+
+import torch
+
+
+def binomial_split(l: int, s: int) -> int:
+    """Length of the left part when reversing l > 1 steps with s >= 1 slots:
+    with t the smallest repetition number for which C(s + t, s) >= l, the
+    right part gets at most C(s - 1 + t, s - 1) steps (reversed with s - 1
+    slots), the left part the rest (at least 1, at most l - 1)."""
+    t = 0
+    while comb(s + t, s) < l:
+        t += 1
+    right = comb(s - 1 + t, s - 1)
+    left = max(1, l - right)
+    return min(left, l - 1)
+
+
+class Revolver:
+    """Forward sweep with checkpoints and the reverse sweep over them."""
+
+    def __init__(self, sim, slots: int):
+        if slots < 0:
+            raise ValueError("slots >= 0")
+        self.sim = sim
+        self.slots = slots
+        self.pool: List[torch.Tensor] = [sim.new_checkpoint() for _ in range(slots + 1)]
+        self.free = list(range(1, slots + 1))
+        self.forward_steps = 0      # steps taken in the forward sweep
+        self.recomputed_steps = 0   # steps recomputed during the reverse sweep
+        self.adjoint_steps = 0
+
+    def _chain(self, n: int) -> List[int]:
+        out, i0, s = [], 0, self.slots
+        while n - i0 > 1 and s > 0:
+            m = i0 + binomial_split(n - i0, s)
+            out.append(m)
+            i0, s = m, s - 1
+        return out
+
+    def forward(self, nsteps: int):
+        """From the current state (time t0), take nsteps, saving the
+        checkpoints the reverse sweep starts from."""
+        sim = self.sim
+        self.n = nsteps
+        self.t_start = sim.save(self.pool[0])
+        self.saved: Dict[int, tuple] = {}
+        pos = 0
+        for m in self._chain(nsteps):
+            sim.step(m - pos)
+            slot = self.free.pop()
+            self.saved[m] = (slot, sim.save(self.pool[slot]))
+            pos = m
+        sim.step(nsteps - pos)
+        self.forward_steps += nsteps
+
+    def reverse(self):
+        """Reverse sweep over the forward run; the adjoint must have been
+        seeded with mhd_adjoint_init."""
+        self._rev(0, self.n, (0, self.t_start), self.slots)
+
+    def _rev(self, i0: int, i1: int, ck, s: int):
+        sim = self.sim
+        slot0, t0 = ck
+        if i1 - i0 == 1:
+            sim.restore(self.pool[slot0], t0)
+            sim.adjoint_step()
+            self.adjoint_steps += 1
+            return
+        if s == 0:
+            for j in range(i1 - 1, i0 - 1, -1):
+                sim.restore(self.pool[slot0], t0)
+                if j > i0:
+                    sim.step(j - i0)
+                    self.recomputed_steps += j - i0
+                sim.adjoint_step()
+                self.adjoint_steps += 1
+            return
+        m = i0 + binomial_split(i1 - i0, s)
+        if m in self.saved:
+            ckm = self.saved.pop(m)
+        else:
+            sim.restore(self.pool[slot0], t0)
+            sim.step(m - i0)
+            self.recomputed_steps += m - i0
+            slot = self.free.pop()
+            ckm = (slot, sim.save(self.pool[slot]))
+        self._rev(m, i1, ckm, s - 1)
+        self.free.append(ckm[0])
+        self._rev(i0, m, ck, s)
+
+
+class DrivenRun(torch.autograd.Function):
+    """(bz, v0, v1) -> state after `nsteps` steps from `state0` at t = 0.
+    The handle must have been created with adjoint=True and dt_fixed > 0."""
+
+    @staticmethod
+    def forward(ctx, bz, v0, v1, sim, state0, nsteps: int, slots: int, t0: float = 0.0, t1: float = 1.0):
+        sim.set_driver(bz.detach().contiguous(), v0.detach().contiguous(), v1.detach().contiguous(), t0, t1)
+        sim.write(state0.detach().contiguous())
+        sim.set_time(0.0)
+        rv = Revolver(sim, slots)
+        rv.forward(nsteps)
+        ctx.sim, ctx.rv = sim, rv
+        return sim.read()
+
+    @staticmethod
+    def backward(ctx, gstate):
+        sim, rv = ctx.sim, ctx.rv
+        sim.adjoint_init(gstate.contiguous())
+        rv.reverse()
+        g = sim.adjoint_read()
+        return g["bz"], g["v0"], g["v1"], None, None, None, None, None, None
+
+
+class BzPlane(torch.autograd.Function):
+    """state [8, nz, ny, nx] -> B_z = D1x A_y - D1y A_x on layer k."""
+
+    @staticmethod
+    def forward(ctx, state, sim, k: int):
+        ctx.sim, ctx.k = sim, k
+        return sim.bz_plane(state.detach(), k)
+
+    @staticmethod
+    def backward(ctx, gbz):
+        return ctx.sim.bz_plane_adjoint(gbz, ctx.k), None, None

@@ -35,7 +35,10 @@ EXPORTED = ("mhd_workspace_bytes", "mhd_create", "mhd_set_driver", "mhd_step",
             "mhd_destroy", "mhd_last_error", "mhd_fill_ghosts",
             "mhd_read_padded", "mhd_eval_rhs", "mhd_compute_dt",
             "mhd_compute_stats", "mhd_read_target", "mhd_profile",
-            "mhd_read_profile", "mhd_launch_count", "mhd_invert_magnetogram_static")
+            "mhd_read_profile", "mhd_launch_count", "mhd_invert_magnetogram_static",
+            "mhd_set_time", "mhd_checkpoint_bytes", "mhd_save", "mhd_restore",
+            "mhd_adjoint_init", "mhd_adjoint_step", "mhd_adjoint_read", "mhd_bz_plane",
+            "mhd_bz_plane_adjoint")
 KERNEL_CLASSES = ("ghost", "pfe", "cfl", "stats", "rk")
 
 
@@ -48,7 +51,7 @@ class MHDError(RuntimeError):
 class Params(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
                 ("precision", ctypes.c_int), ("bc_z", ctypes.c_int),
-                ("stats_every", ctypes.c_int),
+                ("stats_every", ctypes.c_int), ("adjoint", ctypes.c_int),
                 ("dx", ctypes.c_double), ("dy", ctypes.c_double), ("dz", ctypes.c_double),
                 ("gamma", ctypes.c_double), ("gz", ctypes.c_double),
                 ("nu", ctypes.c_double), ("eta", ctypes.c_double),
@@ -113,22 +116,33 @@ def load(path: Optional[str] = None):
     lib.mhd_read_profile.argtypes = [vp, ctypes.POINTER(ctypes.c_double),
                                      ctypes.POINTER(ctypes.c_longlong)]
     lib.mhd_invert_magnetogram_static.argtypes = [i, i, d, d, i, vp, vp, vp, vp]
+    lib.mhd_set_time.argtypes = [vp, d]
+    lib.mhd_checkpoint_bytes.argtypes = [vp]
+    lib.mhd_checkpoint_bytes.restype = sz
+    lib.mhd_save.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_double)]
+    lib.mhd_restore.argtypes = [vp, vp, d]
+    lib.mhd_adjoint_init.argtypes = [vp, vp, i]
+    lib.mhd_adjoint_step.argtypes = [vp]
+    lib.mhd_adjoint_read.argtypes = [vp, vp, vp, vp, vp, i]
+    lib.mhd_bz_plane.argtypes = [vp, vp, i, vp]
+    lib.mhd_bz_plane_adjoint.argtypes = [vp, vp, i, vp]
     lib.mhd_launch_count.argtypes = [vp]
     lib.mhd_launch_count.restype = ctypes.c_longlong
     for name in EXPORTED:
         if name not in ("mhd_workspace_bytes", "mhd_destroy", "mhd_last_error",
-                        "mhd_launch_count"):
+                        "mhd_launch_count", "mhd_checkpoint_bytes"):
             getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
 
 
-def make_params(p: Dict, precision: int = 32, stats_every: int = 0) -> Params:
+def make_params(p: Dict, precision: int = 32, stats_every: int = 0, adjoint: bool = False) -> Params:
     q = Params()
     q.nx, q.ny, q.nz = int(p["nx"]), int(p["ny"]), int(p["nz"])
     q.precision = int(precision)
     q.bc_z = int(p.get("bc_z", 0))
     q.stats_every = int(stats_every)
+    q.adjoint = 1 if adjoint else 0
     for k in ("dx", "dy", "dz", "gamma", "gz", "nu", "eta", "kappa0", "diff_rho",
               "eta_swamp", "chi_swamp", "diffrho_swamp", "z_swamp_start",
               "z_swamp_end", "tau_u", "tau_A", "t_ramp", "f_pfe_bottom", "c_adv",
@@ -151,7 +165,7 @@ class Simulation:
     match the precision (float32 / float64)."""
 
     def __init__(self, params: Dict, init_state, lnrho0, lnT0=None, precision: int = 32,
-                 stats_every: int = 0, device: str = "cuda:0", stream=None):
+                 stats_every: int = 0, device: str = "cuda:0", stream=None, adjoint: bool = False):
         import torch
         self.lib = load()
         self.params = dict(params)
@@ -159,7 +173,7 @@ class Simulation:
         self.np_dtype = np.float32 if precision == 32 else np.float64
         self.torch_dtype = torch.float32 if precision == 32 else torch.float64
         self.device = torch.device(device)
-        self._p = make_params(params, precision, stats_every)
+        self._p = make_params(params, precision, stats_every, adjoint)
         nbytes = int(self.lib.mhd_workspace_bytes(ctypes.byref(self._p)))
         if nbytes == 0:
             raise MHDError(MHD_ERR_ARG, "invalid parameters")
@@ -277,6 +291,59 @@ class Simulation:
         out = np.empty((2, self._p.ny, self._p.nx), dtype=self.np_dtype)
         self._check(self.lib.mhd_read_target(self.h, ctypes.c_void_p(out.ctypes.data), MHD_MEM_HOST))
         return out
+
+    # -- adjoint --
+    def set_time(self, t: float):
+        self._check(self.lib.mhd_set_time(self.h, float(t)))
+
+    def checkpoint_bytes(self) -> int:
+        return int(self.lib.mhd_checkpoint_bytes(self.h))
+
+    def new_checkpoint(self):
+        import torch
+        return torch.empty(self.checkpoint_bytes(), dtype=torch.uint8, device=self.device)
+
+    def save(self, buf) -> float:
+        t = ctypes.c_double()
+        self._check(self.lib.mhd_save(self.h, ctypes.c_void_p(buf.data_ptr()), ctypes.byref(t)))
+        return t.value
+
+    def restore(self, buf, t: float):
+        self._check(self.lib.mhd_restore(self.h, ctypes.c_void_p(buf.data_ptr()), float(t)))
+
+    def adjoint_init(self, lam):
+        ptr, mem, keep = self._in(lam, (NFIELD, self._p.nz, self._p.ny, self._p.nx))
+        self._check(self.lib.mhd_adjoint_init(self.h, ptr, mem))
+
+    def adjoint_step(self):
+        self._check(self.lib.mhd_adjoint_step(self.h))
+
+    def adjoint_read(self) -> Dict:
+        import torch
+        n = (self._p.ny, self._p.nx)
+        out = {"lam": torch.empty((NFIELD, self._p.nz) + n, dtype=self.torch_dtype, device=self.device),
+               "bz": torch.empty(n, dtype=self.torch_dtype, device=self.device),
+               "v0": torch.empty((2,) + n, dtype=self.torch_dtype, device=self.device),
+               "v1": torch.empty((2,) + n, dtype=self.torch_dtype, device=self.device)}
+        self._check(self.lib.mhd_adjoint_read(self.h, *(ctypes.c_void_p(out[k].data_ptr()) for k in
+                                                        ("lam", "bz", "v0", "v1")), MHD_MEM_DEVICE))
+        return out
+
+    def bz_plane(self, state, k: int):
+        import torch
+        st = state.contiguous()
+        out = torch.empty((self._p.ny, self._p.nx), dtype=self.torch_dtype, device=self.device)
+        self._check(self.lib.mhd_bz_plane(self.h, ctypes.c_void_p(st.data_ptr()), int(k),
+                                          ctypes.c_void_p(out.data_ptr())))
+        return out
+
+    def bz_plane_adjoint(self, bbar, k: int):
+        import torch
+        bb = bbar.contiguous()
+        lam = torch.empty((NFIELD, self._p.nz, self._p.ny, self._p.nx), dtype=self.torch_dtype, device=self.device)
+        self._check(self.lib.mhd_bz_plane_adjoint(self.h, ctypes.c_void_p(bb.data_ptr()), int(k),
+                                                  ctypes.c_void_p(lam.data_ptr())))
+        return lam
 
     def profile(self, enable: bool = True):
         self._check(self.lib.mhd_profile(self.h, 1 if enable else 0))

@@ -1,0 +1,629 @@
+// mhd_adjoint.cu -- hand-written adjoint (transposed linearisation) of one
+// low-storage RK3 step with a frozen time step.
+//
+// Forward substep s:  r_s = R(f_s) = RHS(ghost_fill(f_s)),
+//                     df_{s+1} = alpha_s df_s + dt r_s,  f_{s+1} = f_s + beta_s df_{s+1}.
+// Reverse, s = 2, 1, 0 (F = adjoint of the state, D = adjoint of df):
+//                     D += beta_s F;  W = dt D;  F += (dR/df)^T W;  D = alpha_s D,
+// with the driver adjoints accumulated from W at the photosphere.
+// (dR/df)^T W is assembled from
+//  1. adj_point_kernel: per interior cell, the transpose of the pointwise
+//     physics (rhs_point) and of the boundary rows / nudging terms, giving
+//     46 coefficients: adjoints of the cell values and of every derivative
+//     the right-hand side used (first, second, mixed);
+//  2. adj_gather_kernel: the transposed stencils (D1^T = -D1, D2^T = D2,
+//     (D1_a D1_b)^T = D1_a D1_b, periodic in x and y) applied to the
+//     coefficient fields, at interior points and z ghost layers;
+//  3. adj_bc_kernel: the transpose of the pointwise ghost rules (Eqs. 8, 11,
+//     13, closed u_z, symmetric u_hor), routing ghost adjoints into the
+//     interior; the potential-field ghosts are transposed by the FFT kernels
+//     (the Eq. 17 multiplier is real and even, so it is its own transpose).
+#include "mhd_internal.h"
+
+namespace mhd {
+
+// coefficient indices
+enum {
+  CV = 0,        // 8 value adjoints (field order)
+  CDA = 8,       // dA[c][a] at CDA + 3c + a
+  CDU = 17,      // dU[c][a]
+  CLA = 26,      // lapA[c]
+  CLU = 29,      // lapU[c]
+  CGA = 32,      // gdA[a]
+  CGU = 35,      // gdU[a]
+  CGL = 38,      // gL[a]
+  CGT = 41,      // gT[a]
+  CLL = 44,      // lapL
+  CLT = 45,      // lapT
+  NCOEF = 46
+};
+
+template <typename R>
+struct AdjPointArgs {
+  Layout L;
+  Phys<R> ph;
+  Background<R> bg;
+  const R* g;        // ghost-filled forward state of the substep (perturbation storage)
+  const R* dbar;     // adjoint of df (padded layout)
+  R* coef;           // [NCOEF][nz][ny][nx]
+  double* thbar;     // [6][ny][nx]: A_target x, y; v0 x, y; v1 x, y
+  const R* wtab;
+  const R* wptab;
+  const StepState* ss;
+  int sub;
+};
+
+// Transpose of rhs_point (see mhd_common.cuh) at one cell: given the output
+// adjoint w[8], accumulate the adjoints of every input of the cell record.
+// Forward intermediates are recomputed in the same order.
+template <typename R>
+__device__ __forceinline__ void rhs_point_adjoint(const Cell<R>& c, const Phys<R>& ph, R w_, R wp, const R wo[8],
+                                                  R cf[NCOEF]) {
+  for (int q = 0; q < NCOEF; ++q) cf[q] = R(0);
+  // forward
+  const R B0 = c.dA[2][1] - c.dA[1][2] + ph.bext[0];
+  const R B1 = c.dA[0][2] - c.dA[2][0] + ph.bext[1];
+  const R B2 = c.dA[1][0] - c.dA[0][1] + ph.bext[2];
+  const R J0 = c.gdA[0] - c.lapA[0], J1 = c.gdA[1] - c.lapA[1], J2 = c.gdA[2] - c.lapA[2];
+  const R divU = c.dU[0][0] + c.dU[1][1] + c.dU[2][2];
+  const R T = rexp<R>(c.Th);
+  const R rho1 = rexp<R>(-c.L);
+  const R u0 = c.U[0], u1 = c.U[1], u2 = c.U[2];
+  const R third = R(1.0 / 3.0);
+  const R s00 = c.dU[0][0] - third * divU, s11 = c.dU[1][1] - third * divU, s22 = c.dU[2][2] - third * divU;
+  const R s01 = R(0.5) * (c.dU[0][1] + c.dU[1][0]);
+  const R s02 = R(0.5) * (c.dU[0][2] + c.dU[2][0]);
+  const R s12 = R(0.5) * (c.dU[1][2] + c.dU[2][1]);
+  const R S2 = s00 * s00 + s11 * s11 + s22 * s22 + R(2) * (s01 * s01 + s02 * s02 + s12 * s12);
+  const R gL0 = c.gL[0], gL1 = c.gL[1], gL2 = c.gL[2];
+  const R F0 = J1 * B2 - J2 * B1, F1 = J2 * B0 - J0 * B2, F2 = J0 * B1 - J1 * B0;
+  const R JJ = J0 * J0 + J1 * J1 + J2 * J2;
+  const R T1 = R(1) / T;
+  const R Q = ph.eta * JJ * rho1 + R(2) * ph.nu * S2;
+  const R kt = ph.gm1 * ph.kappa0 * rexp<R>(R(2.5) * c.Th - c.L);
+  const R gT2 = c.gT[0] * c.gT[0] + c.gT[1] * c.gT[1] + c.gT[2] * c.gT[2];
+
+  R bB0 = 0, bB1 = 0, bB2 = 0, bJ0 = 0, bJ1 = 0, bJ2 = 0, bu0 = 0, bu1 = 0, bu2 = 0;
+  R bdivA = 0, bdivU = 0, bT = 0, brho1 = 0, bTh = 0, bL = 0;
+  R bs00 = 0, bs11 = 0, bs22 = 0, bs01 = 0, bs02 = 0, bs12 = 0;
+  R bF0 = 0, bF1 = 0, bF2 = 0, bS2 = 0;
+  R bgL0 = 0, bgL1 = 0, bgL2 = 0;
+
+  // induction
+  {
+    const R a0 = wo[0], a1 = wo[1], a2 = wo[2];
+    const R ews = ph.eta_s * w_;
+    bu1 += a0 * B2; bB2 += a0 * u1; bu2 -= a0 * B1; bB1 -= a0 * u2; bJ0 -= ph.eta * a0; cf[CLA + 0] += ews * a0;
+    bu2 += a1 * B0; bB0 += a1 * u2; bu0 -= a1 * B2; bB2 -= a1 * u0; bJ1 -= ph.eta * a1; cf[CLA + 1] += ews * a1;
+    bu0 += a2 * B1; bB1 += a2 * u0; bu1 -= a2 * B0; bB0 -= a2 * u1; bJ2 -= ph.eta * a2; cf[CLA + 2] += ews * a2;
+    bdivA += ph.eta_s * wp * a2;
+  }
+  // momentum
+  const R Fc[3] = {F0, F1, F2};
+  R bFc[3] = {0, 0, 0};
+  R bSgL[3] = {0, 0, 0};
+  for (int cc = 0; cc < 3; ++cc) {
+    const R a = wo[3 + cc];
+    // -(u.grad) u_c
+    bu0 -= a * c.dU[cc][0];
+    bu1 -= a * c.dU[cc][1];
+    bu2 -= a * c.dU[cc][2];
+    cf[CDU + 3 * cc + 0] -= a * u0;
+    cf[CDU + 3 * cc + 1] -= a * u1;
+    cf[CDU + 3 * cc + 2] -= a * u2;
+    // -T (gL + gT)
+    bT -= a * (c.gL[cc] + c.gT[cc]);
+    if (cc == 0) bgL0 -= a * T;
+    if (cc == 1) bgL1 -= a * T;
+    if (cc == 2) bgL2 -= a * T;
+    cf[CGT + cc] -= a * T;
+    // F / rho
+    bFc[cc] += a * rho1;
+    brho1 += a * Fc[cc];
+    // viscous force
+    cf[CLU + cc] += ph.nu * a;
+    cf[CGU + cc] += ph.nu * third * a;
+    bSgL[cc] += R(2) * ph.nu * a;
+  }
+  bF0 = bFc[0]; bF1 = bFc[1]; bF2 = bFc[2];
+  // Lorentz force
+  bJ1 += bF0 * B2; bB2 += bF0 * J1; bJ2 -= bF0 * B1; bB1 -= bF0 * J2;
+  bJ2 += bF1 * B0; bB0 += bF1 * J2; bJ0 -= bF1 * B2; bB2 -= bF1 * J0;
+  bJ0 += bF2 * B1; bB1 += bF2 * J0; bJ1 -= bF2 * B0; bB0 -= bF2 * J1;
+  // S . grad ln rho
+  bs00 += bSgL[0] * gL0; bs01 += bSgL[0] * gL1; bs02 += bSgL[0] * gL2;
+  bgL0 += bSgL[0] * s00; bgL1 += bSgL[0] * s01; bgL2 += bSgL[0] * s02;
+  bs01 += bSgL[1] * gL0; bs11 += bSgL[1] * gL1; bs12 += bSgL[1] * gL2;
+  bgL0 += bSgL[1] * s01; bgL1 += bSgL[1] * s11; bgL2 += bSgL[1] * s12;
+  bs02 += bSgL[2] * gL0; bs12 += bSgL[2] * gL1; bs22 += bSgL[2] * gL2;
+  bgL0 += bSgL[2] * s02; bgL1 += bSgL[2] * s12; bgL2 += bSgL[2] * s22;
+  // continuity
+  {
+    const R a = wo[6];
+    bu0 -= a * gL0; bu1 -= a * gL1; bu2 -= a * gL2;
+    bgL0 -= a * u0; bgL1 -= a * u1; bgL2 -= a * u2;
+    bdivU -= a;
+    cf[CLL] += a * (ph.drho + ph.drho_s * w_);
+    bgL0 += a * ph.drho * R(2) * gL0;
+    bgL1 += a * ph.drho * R(2) * gL1;
+    bgL2 += a * ph.drho * R(2) * gL2;
+  }
+  // energy
+  {
+    const R a = wo[7];
+    bu0 -= a * c.gT[0]; bu1 -= a * c.gT[1]; bu2 -= a * c.gT[2];
+    cf[CGT + 0] -= a * u0; cf[CGT + 1] -= a * u1; cf[CGT + 2] -= a * u2;
+    bdivU -= a * ph.gm1;
+    // heat = gm1 Q T1
+    const R bQ = a * ph.gm1 * T1;
+    const R bT1 = a * ph.gm1 * Q;
+    const R bJJ = bQ * ph.eta * rho1;
+    brho1 += bQ * ph.eta * JJ;
+    bS2 += bQ * R(2) * ph.nu;
+    bJ0 += R(2) * J0 * bJJ; bJ1 += R(2) * J1 * bJJ; bJ2 += R(2) * J2 * bJJ;
+    bT -= bT1 * T1 * T1;
+    // conduction kt (lapT + 3.5 gT2) and swamp
+    const R bkt = a * (c.lapT + R(3.5) * gT2);
+    cf[CLT] += a * kt + a * ph.chi_s * w_;
+    cf[CGT + 0] += a * kt * R(7) * c.gT[0];
+    cf[CGT + 1] += a * kt * R(7) * c.gT[1];
+    cf[CGT + 2] += a * kt * R(7) * c.gT[2];
+    bTh += bkt * kt * R(2.5);
+    bL -= bkt * kt;
+  }
+  // S2
+  bs00 += R(2) * s00 * bS2; bs11 += R(2) * s11 * bS2; bs22 += R(2) * s22 * bS2;
+  bs01 += R(4) * s01 * bS2; bs02 += R(4) * s02 * bS2; bs12 += R(4) * s12 * bS2;
+  // strain components
+  cf[CDU + 0] += bs00; cf[CDU + 4] += bs11; cf[CDU + 8] += bs22;
+  bdivU -= third * (bs00 + bs11 + bs22);
+  cf[CDU + 1] += R(0.5) * bs01; cf[CDU + 3] += R(0.5) * bs01;
+  cf[CDU + 2] += R(0.5) * bs02; cf[CDU + 6] += R(0.5) * bs02;
+  cf[CDU + 5] += R(0.5) * bs12; cf[CDU + 7] += R(0.5) * bs12;
+  // exponentials
+  bTh += bT * T;
+  bL -= brho1 * rho1;
+  // divergences
+  cf[CDU + 0] += bdivU; cf[CDU + 4] += bdivU; cf[CDU + 8] += bdivU;
+  cf[CDA + 0] += bdivA; cf[CDA + 4] += bdivA; cf[CDA + 8] += bdivA;
+  // J = gdA - lapA
+  cf[CGA + 0] += bJ0; cf[CGA + 1] += bJ1; cf[CGA + 2] += bJ2;
+  cf[CLA + 0] -= bJ0; cf[CLA + 1] -= bJ1; cf[CLA + 2] -= bJ2;
+  // B = curl A
+  cf[CDA + 3 * 2 + 1] += bB0; cf[CDA + 3 * 1 + 2] -= bB0;
+  cf[CDA + 3 * 0 + 2] += bB1; cf[CDA + 3 * 2 + 0] -= bB1;
+  cf[CDA + 3 * 1 + 0] += bB2; cf[CDA + 3 * 0 + 1] -= bB2;
+  // values and first derivatives of ln rho
+  cf[CV + UX] += bu0; cf[CV + UY] += bu1; cf[CV + UZ] += bu2;
+  cf[CV + LR] += bL; cf[CV + LT] += bTh;
+  cf[CGL + 0] += bgL0; cf[CGL + 1] += bgL1; cf[CGL + 2] += bgL2;
+}
+
+template <typename R>
+__global__ void __launch_bounds__(128) adj_point_kernel(AdjPointArgs<R> a) {
+  const Layout& L = a.L;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int k = blockIdx.z;
+  if (i >= L.nx || j >= L.ny) return;
+  if (halted(a.ss)) return;
+  const Phys<R>& ph = a.ph;
+  const long long st[3] = {1, L.sy(), L.sz()};
+  const R inv[3] = {ph.idx, ph.idy, ph.idz};
+  const R inv2[3] = {ph.idx2, ph.idy2, ph.idz2};
+  const R* base[NF];
+  for (int fl = 0; fl < NF; ++fl) base[fl] = a.g + L.at(fl, k, j, i);
+  // the cell record, exactly as the forward kernels build it
+  Cell<R> c;
+  for (int cc = 0; cc < 3; ++cc) {
+    const R* pa = base[AX + cc];
+    const R* pu = base[UX + cc];
+    c.A[cc] = *pa;
+    c.U[cc] = *pu;
+    c.lapA[cc] = R(0);
+    c.lapU[cc] = R(0);
+    for (int ax = 0; ax < 3; ++ax) {
+      c.dA[cc][ax] = d1(pa, st[ax], inv[ax]);
+      c.dU[cc][ax] = d1(pu, st[ax], inv[ax]);
+      c.lapA[cc] += d2(pa, st[ax], inv2[ax]);
+      c.lapU[cc] += d2(pu, st[ax], inv2[ax]);
+    }
+  }
+  for (int ax = 0; ax < 3; ++ax) {
+    R sa = R(0), su = R(0);
+    for (int cc = 0; cc < 3; ++cc) {
+      if (cc == ax) {
+        sa += d2(base[AX + cc], st[ax], inv2[ax]);
+        su += d2(base[UX + cc], st[ax], inv2[ax]);
+      } else {
+        sa += d11(base[AX + cc], st[ax], st[cc], inv[ax], inv[cc]);
+        su += d11(base[UX + cc], st[ax], st[cc], inv[ax], inv[cc]);
+      }
+    }
+    c.gdA[ax] = sa;
+    c.gdU[ax] = su;
+  }
+  c.L = a.bg.lbar[k + NG] + *base[LR];
+  c.Th = a.bg.tbar[k + NG] + *base[LT];
+  c.lapL = R(0);
+  c.lapT = R(0);
+  for (int ax = 0; ax < 3; ++ax) {
+    c.gL[ax] = d1(base[LR], st[ax], inv[ax]);
+    c.gT[ax] = d1(base[LT], st[ax], inv[ax]);
+    c.lapL += d2(base[LR], st[ax], inv2[ax]);
+    c.lapT += d2(base[LT], st[ax], inv2[ax]);
+  }
+  c.gL[2] += a.bg.dl[k];
+  c.lapL += a.bg.d2l[k];
+  c.gT[2] += a.bg.dt[k];
+  c.lapT += a.bg.d2t[k];
+
+  const R dt = R(a.ss->dt);
+  R wo[NF];
+  for (int fl = 0; fl < NF; ++fl) wo[fl] = dt * a.dbar[L.at(fl, k, j, i)];
+  const long long q2 = (long long)j * L.nx + i, n2 = (long long)L.nx * L.ny;
+  R vA0 = R(0), vA1 = R(0), vU0 = R(0), vU1 = R(0);
+  if (ph.bcz == 0 && k == 0) {
+    // overwritten rows carry no dependence
+    wo[UZ] = R(0);
+    wo[LR] = R(0);
+    // nudging: -tau_A (A_hor - A_target), -tau_u (u_hor - r v*)
+    vA0 = -ph.tau_A * wo[AX];
+    vA1 = -ph.tau_A * wo[AY];
+    vU0 = -ph.tau_u * wo[UX];
+    vU1 = -ph.tau_u * wo[UY];
+    const double r = a.ss->r[a.sub], s = a.ss->s[a.sub];
+    double tgx = (double)(ph.tau_u * wo[UX]), tgy = (double)(ph.tau_u * wo[UY]);
+    // stateful ghost rows below the photosphere: nudging only
+    for (int m = 1; m <= NG; ++m) {
+      tgx += (double)(ph.tau_u * dt * a.dbar[L.at(UX, -m, j, i)]);
+      tgy += (double)(ph.tau_u * dt * a.dbar[L.at(UY, -m, j, i)]);
+    }
+    a.thbar[0 * n2 + q2] += (double)(ph.tau_A * wo[AX]);
+    a.thbar[1 * n2 + q2] += (double)(ph.tau_A * wo[AY]);
+    a.thbar[2 * n2 + q2] += r * (1.0 - s) * tgx;
+    a.thbar[3 * n2 + q2] += r * (1.0 - s) * tgy;
+    a.thbar[4 * n2 + q2] += r * s * tgx;
+    a.thbar[5 * n2 + q2] += r * s * tgy;
+  }
+  if (ph.bcz == 0 && k == L.nz - 1) wo[UZ] = R(0);
+  R cf[NCOEF];
+  rhs_point_adjoint<R>(c, ph, a.wtab[k], a.wptab[k], wo, cf);
+  cf[CV + AX] += vA0;
+  cf[CV + AY] += vA1;
+  cf[CV + UX] += vU0;
+  cf[CV + UY] += vU1;
+  const long long n3 = n2 * L.nz, cq = (long long)k * n2 + q2;
+  for (int q = 0; q < NCOEF; ++q) a.coef[q * n3 + cq] = cf[q];
+}
+
+// ---------------------------------------------------------------------------
+template <typename R>
+struct AdjGatherArgs {
+  Layout L;
+  Phys<R> ph;
+  const R* coef;
+  const R* dbar;
+  R* gbar;           // output: adjoint of the ghost-filled input (padded layout)
+  const StepState* ss;
+};
+
+template <typename R>
+__device__ __forceinline__ R cget(const R* __restrict__ coef, int q, int k, int j, int i, int nx, int ny, int nz) {
+  if (k < 0 || k >= nz) return R(0);
+  i = i < 0 ? i + nx : (i >= nx ? i - nx : i);
+  j = j < 0 ? j + ny : (j >= ny ? j - ny : j);
+  return __ldg(coef + (((long long)q * nz + k) * ny + j) * nx + i);
+}
+
+// transposed first derivative along axis ax of coefficient q at (k, j, i)
+template <typename R>
+__device__ __forceinline__ R t_d1(const R* coef, int q, int k, int j, int i, int ax, int nx, int ny, int nz, R inv) {
+  R s = R(0);
+  const R cw[4] = {R(0), W<R>::c1, W<R>::c2, W<R>::c3};
+  for (int m = 1; m <= 3; ++m) {
+    const int di = ax == 0 ? m : 0, dj = ax == 1 ? m : 0, dk = ax == 2 ? m : 0;
+    s += cw[m] * (cget(coef, q, k - dk, j - dj, i - di, nx, ny, nz) - cget(coef, q, k + dk, j + dj, i + di, nx, ny, nz));
+  }
+  return s * inv;
+}
+template <typename R>
+__device__ __forceinline__ R t_d2(const R* coef, int q, int k, int j, int i, int ax, int nx, int ny, int nz, R inv2) {
+  const R ew[4] = {W<R>::e0, W<R>::e1, W<R>::e2, W<R>::e3};
+  R s = ew[0] * cget(coef, q, k, j, i, nx, ny, nz);
+  for (int m = 1; m <= 3; ++m) {
+    const int di = ax == 0 ? m : 0, dj = ax == 1 ? m : 0, dk = ax == 2 ? m : 0;
+    s += ew[m] * (cget(coef, q, k - dk, j - dj, i - di, nx, ny, nz) + cget(coef, q, k + dk, j + dj, i + di, nx, ny, nz));
+  }
+  return s * inv2;
+}
+// transposed mixed derivative D1_a D1_b (its own transpose)
+template <typename R>
+__device__ __forceinline__ R t_d11(const R* coef, int q, int k, int j, int i, int a, int b, int nx, int ny, int nz,
+                                   R ia, R ib) {
+  const R cw[4] = {R(0), W<R>::c1, W<R>::c2, W<R>::c3};
+  R s = R(0);
+  for (int m = 1; m <= 3; ++m)
+    for (int n = 1; n <= 3; ++n) {
+      int d[2][3] = {{0, 0, 0}, {0, 0, 0}};
+      d[0][a] = m;
+      d[1][b] = n;
+      const int pi = d[0][0] + d[1][0], pj = d[0][1] + d[1][1], pk = d[0][2] + d[1][2];
+      const int qi = d[0][0] - d[1][0], qj = d[0][1] - d[1][1], qk = d[0][2] - d[1][2];
+      const R v = cget(coef, q, k + pk, j + pj, i + pi, nx, ny, nz) - cget(coef, q, k + qk, j + qj, i + qi, nx, ny, nz) -
+                  cget(coef, q, k - qk, j - qj, i - qi, nx, ny, nz) + cget(coef, q, k - pk, j - pj, i - pi, nx, ny, nz);
+      s += cw[m] * cw[n] * v;
+    }
+  return s * ia * ib;
+}
+
+template <typename R>
+__global__ void __launch_bounds__(128) adj_gather_kernel(AdjGatherArgs<R> a) {
+  const Layout& L = a.L;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int k = (int)blockIdx.z - NG;
+  if (i >= L.nx || j >= L.ny) return;
+  if (halted(a.ss)) return;
+  const int nx = L.nx, ny = L.ny, nz = L.nz;
+  const Phys<R>& ph = a.ph;
+  const R inv[3] = {ph.idx, ph.idy, ph.idz};
+  const R inv2[3] = {ph.idx2, ph.idy2, ph.idz2};
+  const bool inside = k >= 0 && k < nz;
+  for (int cc = 0; cc < 3; ++cc) {
+    for (int grp = 0; grp < 2; ++grp) {  // grp 0: A_c, grp 1: u_c
+      const int qd = grp == 0 ? CDA : CDU, ql = grp == 0 ? CLA : CLU, qg = grp == 0 ? CGA : CGU;
+      R s = inside ? cget(a.coef, CV + (grp == 0 ? AX : UX) + cc, k, j, i, nx, ny, nz) : R(0);
+      for (int ax = 0; ax < 3; ++ax) {
+        s += t_d1(a.coef, qd + 3 * cc + ax, k, j, i, ax, nx, ny, nz, inv[ax]);
+        s += t_d2(a.coef, ql + cc, k, j, i, ax, nx, ny, nz, inv2[ax]);
+      }
+      s += t_d2(a.coef, qg + cc, k, j, i, cc, nx, ny, nz, inv2[cc]);
+      for (int ax = 0; ax < 3; ++ax)
+        if (ax != cc) s += t_d11(a.coef, qg + ax, k, j, i, ax, cc, nx, ny, nz, inv[ax], inv[cc]);
+      a.gbar[L.at((grp == 0 ? AX : UX) + cc, k, j, i)] = s;
+    }
+  }
+  for (int grp = 0; grp < 2; ++grp) {  // ln rho, ln T
+    const int qg = grp == 0 ? CGL : CGT, ql = grp == 0 ? CLL : CLT, fl = grp == 0 ? LR : LT;
+    R s = inside ? cget(a.coef, CV + fl, k, j, i, nx, ny, nz) : R(0);
+    for (int ax = 0; ax < 3; ++ax) {
+      s += t_d1(a.coef, qg + ax, k, j, i, ax, nx, ny, nz, inv[ax]);
+      s += t_d2(a.coef, ql, k, j, i, ax, nx, ny, nz, inv2[ax]);
+    }
+    a.gbar[L.at(fl, k, j, i)] = s;
+  }
+  // stateful horizontal-velocity ghost rows: their own nudging term
+  if (ph.bcz == 0 && k < 0) {
+    const R dt = R(a.ss->dt);
+    for (int cc = 0; cc < 2; ++cc) {
+      const long long q = L.at(UX + cc, k, j, i);
+      a.gbar[q] -= ph.tau_u * dt * a.dbar[q];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Transpose of the pointwise ghost rules (per column, interior x,y): ghost
+// adjoints are routed into the layers they were computed from.
+template <typename R>
+__global__ void adj_bc_kernel(Layout L, Phys<R> ph, Background<R> bg, const R* __restrict__ g, R* __restrict__ gbar,
+                              R dz, const StepState* ss) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= L.nx * L.ny) return;
+  if (halted(ss)) return;
+  const int i = q % L.nx, j = q / L.nx;
+  const int kt = L.nz - 1;
+  const R dzg = dz * ph.gz;
+  // bottom: ln T recursion (ln rho ghosts are constants)
+  {
+    const R th0 = bg.tbar[NG] + g[L.at(LT, 0, j, i)];
+    const R thm1 = bg.tbar[NG - 1] + g[L.at(LT, -1, j, i)];
+    const R thm2 = bg.tbar[NG - 2] + g[L.at(LT, -2, j, i)];
+    const R a3 = gbar[L.at(LT, -3, j, i)];
+    const R a2 = gbar[L.at(LT, -2, j, i)] + a3 * (R(1) + dzg * rexp<R>(-thm2));
+    const R a1 = gbar[L.at(LT, -1, j, i)] + a2 * (R(1) + dzg * rexp<R>(-thm1));
+    gbar[L.at(LT, 0, j, i)] += a1 * (R(1) + dzg * rexp<R>(-th0));
+    gbar[L.at(LR, 0, j, i)] += a1;
+    for (int m = 1; m <= NG; ++m) gbar[L.at(UZ, m, j, i)] -= gbar[L.at(UZ, -m, j, i)];
+  }
+  // top
+  {
+    const R Ttop = rexp<R>(bg.tbar[NG + kt] + g[L.at(LT, kt, j, i)]);
+    R bth = R(0);
+    for (int m = 1; m <= NG; ++m) {
+      gbar[L.at(LT, kt - m, j, i)] += gbar[L.at(LT, kt + m, j, i)];
+      const R bl = gbar[L.at(LR, kt + m, j, i)];
+      gbar[L.at(LR, kt - m, j, i)] += bl;
+      bth -= bl * (R(2 * m) * dz) * ph.gz / Ttop;
+      gbar[L.at(UZ, kt - m, j, i)] -= gbar[L.at(UZ, kt + m, j, i)];
+      gbar[L.at(UX, kt - m, j, i)] += gbar[L.at(UX, kt + m, j, i)];
+      gbar[L.at(UY, kt - m, j, i)] += gbar[L.at(UY, kt + m, j, i)];
+    }
+    gbar[L.at(LT, kt, j, i)] += bth;
+  }
+}
+
+// elementwise updates over the cells that carry state (interior, and the
+// u_x, u_y ghost layers below the photosphere)
+template <typename R>
+__global__ void adj_axpy_kernel(Layout L, int bcz, R* __restrict__ fbar, R* __restrict__ dbar,
+                                const R* __restrict__ gbar, R beta, R alpha, int phase, const StepState* ss) {
+  const long long n2 = (long long)L.nx * L.ny;
+  const long long ncell = (long long)NF * L.nz * n2 + (bcz == 0 ? 2LL * NG * n2 : 0);
+  if (halted(ss)) return;
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < ncell;
+       q += (long long)gridDim.x * blockDim.x) {
+    int fl, k;
+    long long r;
+    if (q < (long long)NF * L.nz * n2) {
+      fl = (int)(q / (L.nz * n2));
+      r = q - (long long)fl * L.nz * n2;
+      k = (int)(r / n2);
+    } else {
+      const long long q3 = q - (long long)NF * L.nz * n2;
+      fl = UX + (int)(q3 / (NG * n2));
+      r = q3 - (long long)(fl - UX) * NG * n2;
+      k = -1 - (int)(r / n2);
+    }
+    const long long rem = r % n2;
+    const int j = (int)(rem / L.nx), i = (int)(rem - (long long)j * L.nx);
+    const long long p = L.at(fl, k, j, i);
+    if (phase == 0) {
+      dbar[p] += beta * fbar[p];
+    } else {
+      fbar[p] += gbar[p];
+      dbar[p] *= alpha;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// B_z = D1x A_y - D1y A_x on layer k of an interior-packed state (periodic),
+// and its transpose: lam_Ay = -D1x(bbar), lam_Ax = +D1y(bbar).
+template <typename R>
+__global__ void bz_plane_kernel(int nx, int ny, int nz, int k, R idx, R idy, const R* __restrict__ st,
+                                R* __restrict__ out, int adjoint, const R* __restrict__ bbar, R* __restrict__ lam) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= nx * ny) return;
+  const int i = q % nx, j = q / nx;
+  const long long n2 = (long long)nx * ny, n3 = n2 * nz;
+  const R cw[4] = {R(0), W<R>::c1, W<R>::c2, W<R>::c3};
+  auto at = [&](const R* p, int jj, int ii) -> R {
+    ii = (ii % nx + nx) % nx;
+    jj = (jj % ny + ny) % ny;
+    return p[(long long)jj * nx + ii];
+  };
+  if (!adjoint) {
+    const R* ax = st + 0 * n3 + (long long)k * n2;
+    const R* ay = st + 1 * n3 + (long long)k * n2;
+    R dx = R(0), dy = R(0);
+    for (int m = 1; m <= 3; ++m) {
+      dx += cw[m] * (at(ay, j, i + m) - at(ay, j, i - m));
+      dy += cw[m] * (at(ax, j + m, i) - at(ax, j - m, i));
+    }
+    out[q] = dx * idx - dy * idy;
+  } else {
+    R gx = R(0), gy = R(0);
+    for (int m = 1; m <= 3; ++m) {
+      gx += cw[m] * (at(bbar, j, i - m) - at(bbar, j, i + m));  // D1x^T
+      gy += cw[m] * (at(bbar, j - m, i) - at(bbar, j + m, i));  // D1y^T
+    }
+    lam[1 * n3 + (long long)k * n2 + q] = gx * idx;
+    lam[0 * n3 + (long long)k * n2 + q] = -gy * idy;
+  }
+}
+
+// adjoint state <-> interior layout (no background: these are adjoints);
+// on the way out the stateful u_x, u_y ghost adjoints are folded onto the
+// photospheric layer (the ghosts are initialised from it)
+template <typename R>
+__global__ void adj_pack_kernel(Layout L, int bcz, const R* __restrict__ fbar, R* __restrict__ out) {
+  const long long n2 = (long long)L.nx * L.ny, n3 = n2 * L.nz;
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n3 * NF;
+       q += (long long)gridDim.x * blockDim.x) {
+    const int fl = (int)(q / n3);
+    const long long r = q - (long long)fl * n3;
+    const int k = (int)(r / n2);
+    const long long rem = r - (long long)k * n2;
+    const int j = (int)(rem / L.nx), i = (int)(rem - (long long)j * L.nx);
+    R v = fbar[L.at(fl, k, j, i)];
+    if (bcz == 0 && k == 0 && (fl == UX || fl == UY))
+      for (int m = 1; m <= NG; ++m) v += fbar[L.at(fl, -m, j, i)];
+    out[q] = v;
+  }
+}
+
+template <typename R>
+__global__ void adj_unpack_kernel(Layout L, const R* __restrict__ in, R* __restrict__ fbar) {
+  const long long n2 = (long long)L.nx * L.ny, n3 = n2 * L.nz;
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n3 * NF;
+       q += (long long)gridDim.x * blockDim.x) {
+    const int fl = (int)(q / n3);
+    const long long r = q - (long long)fl * n3;
+    const int k = (int)(r / n2);
+    const long long rem = r - (long long)k * n2;
+    const int j = (int)(rem / L.nx), i = (int)(rem - (long long)j * L.nx);
+    fbar[L.at(fl, k, j, i)] = in[q];
+  }
+}
+
+template <typename R>
+__global__ void d2r_kernel(const double* __restrict__ in, R* __restrict__ out, long long n) {
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x)
+    out[q] = (R)in[q];
+}
+
+template <typename R>
+void launch_adj_pack(const Layout& L, int bcz, const R* fbar, R* out, cudaStream_t st) {
+  adj_pack_kernel<R><<<1216, 256, 0, st>>>(L, bcz, fbar, out);
+}
+template <typename R>
+void launch_adj_unpack(const Layout& L, const R* in, R* fbar, cudaStream_t st) {
+  adj_unpack_kernel<R><<<1216, 256, 0, st>>>(L, in, fbar);
+}
+template <typename R>
+void launch_d2r(const double* in, R* out, long long n, cudaStream_t st) {
+  d2r_kernel<R><<<304, 256, 0, st>>>(in, out, n);
+}
+
+// ---------------------------------------------------------------------------
+template <typename R>
+void launch_adj_point(const Layout& L, const Phys<R>& ph, const Background<R>& bg, const R* g, const R* dbar, R* coef,
+                      double* thbar, const R* wtab, const R* wptab, const StepState* ss, int sub, cudaStream_t st) {
+  AdjPointArgs<R> a;
+  a.L = L; a.ph = ph; a.bg = bg; a.g = g; a.dbar = dbar; a.coef = coef; a.thbar = thbar;
+  a.wtab = wtab; a.wptab = wptab; a.ss = ss; a.sub = sub;
+  dim3 blk(32, 4, 1), grd((L.nx + 31) / 32, (L.ny + 3) / 4, L.nz);
+  adj_point_kernel<R><<<grd, blk, 0, st>>>(a);
+}
+
+template <typename R>
+void launch_adj_gather(const Layout& L, const Phys<R>& ph, const R* coef, const R* dbar, R* gbar, const StepState* ss,
+                       cudaStream_t st) {
+  AdjGatherArgs<R> a;
+  a.L = L; a.ph = ph; a.coef = coef; a.dbar = dbar; a.gbar = gbar; a.ss = ss;
+  dim3 blk(32, 4, 1), grd((L.nx + 31) / 32, (L.ny + 3) / 4, L.nz + 2 * NG);
+  adj_gather_kernel<R><<<grd, blk, 0, st>>>(a);
+}
+
+template <typename R>
+void launch_adj_bc(const Layout& L, const Phys<R>& ph, const Background<R>& bg, const R* g, R* gbar, R dz,
+                   const StepState* ss, cudaStream_t st) {
+  const int n = L.nx * L.ny;
+  adj_bc_kernel<R><<<(n + 127) / 128, 128, 0, st>>>(L, ph, bg, g, gbar, dz, ss);
+}
+
+template <typename R>
+void launch_adj_axpy(const Layout& L, int bcz, R* fbar, R* dbar, const R* gbar, double beta, double alpha, int phase,
+                     const StepState* ss, cudaStream_t st) {
+  adj_axpy_kernel<R><<<1216, 256, 0, st>>>(L, bcz, fbar, dbar, gbar, (R)beta, (R)alpha, phase, ss);
+}
+
+template <typename R>
+void launch_bz_plane(int nx, int ny, int nz, int k, double dx, double dy, const R* st_in, R* out, int adjoint,
+                     const R* bbar, R* lam, cudaStream_t st) {
+  const int n = nx * ny;
+  bz_plane_kernel<R><<<(n + 255) / 256, 256, 0, st>>>(nx, ny, nz, k, (R)(1.0 / dx), (R)(1.0 / dy), st_in, out, adjoint,
+                                                      bbar, lam);
+}
+
+#define INST(R)                                                                                                    \
+  template void launch_adj_point<R>(const Layout&, const Phys<R>&, const Background<R>&, const R*, const R*, R*,     \
+                                    double*, const R*, const R*, const StepState*, int, cudaStream_t);             \
+  template void launch_adj_gather<R>(const Layout&, const Phys<R>&, const R*, const R*, R*, const StepState*,       \
+                                     cudaStream_t);                                                               \
+  template void launch_adj_bc<R>(const Layout&, const Phys<R>&, const Background<R>&, const R*, R*, R,             \
+                                 const StepState*, cudaStream_t);                                                 \
+  template void launch_adj_axpy<R>(const Layout&, int, R*, R*, const R*, double, double, int, const StepState*,     \
+                                   cudaStream_t);                                                                 \
+  template void launch_bz_plane<R>(int, int, int, int, double, double, const R*, R*, int, const R*, R*,             \
+                                   cudaStream_t);                                                                 \
+  template void launch_adj_pack<R>(const Layout&, int, const R*, R*, cudaStream_t);                                \
+  template void launch_adj_unpack<R>(const Layout&, const R*, R*, cudaStream_t);                                   \
+  template void launch_d2r<R>(const double*, R*, long long, cudaStream_t);
+INST(float)
+INST(double)
+#undef INST
+
+}  // namespace mhd

@@ -37,6 +37,13 @@ struct mhd_ctx {
   double* red;         // reduction partials
   StepState* ss;
   void* bgtab;         // background tables: lbar, tbar [nz+6]; dl, d2l, dt, d2t [nz]
+  // adjoint buffers (params.adjoint)
+  void* s2;            // third forward substep state
+  void* fbar;          // state adjoint (padded)
+  void* dbar;          // RK accumulator adjoint (padded)
+  void* gbar;          // adjoint of the ghost-filled input of one RHS (padded)
+  void* coef;          // [46][nz][ny][nx] transposed-stencil coefficients
+  double* thbar;       // [6][ny][nx] parameter adjoints (FP64)
   Background<float> bgf;
   Background<double> bgd;
   FFTPlan fp;
@@ -118,6 +125,7 @@ static const char* check_params(const mhd_params* p) {
   if (!(p->dx > 0) || !(p->dy > 0) || !(p->dz > 0)) return "grid spacings must be positive";
   if (!(p->gamma > 1.0)) return "gamma must exceed 1";
   if (p->stats_every < 0) return "stats_every must be >= 0";
+  if (p->adjoint != 0 && p->adjoint != 1) return "adjoint must be 0 or 1";
   if ((long long)p->nx * p->ny * p->nz > (1LL << 34)) return "grid too large";
   if ((long long)((p->nx + 31) / 32) * ((p->ny + 7) / 8) > RED_BLOCKS_MAX)
     return "horizontal grid too large for the reduction buffer (nx * ny <= 2^20)";
@@ -136,6 +144,7 @@ struct Carve {
 
 struct Offsets {
   size_t f0, f1, df, lnrho0, wtab, wptab, bz, axt, ayt, v0, v1, red, ss, bg;
+  size_t s2, fbar, dbar, gbar, coef, thbar;
   size_t twx, twy, et, eb, ktx, kty, P, Q;
   size_t total;
 };
@@ -161,6 +170,16 @@ static Offsets plan_offsets(const mhd_params* p) {
   o.red = c.take((size_t)RED_BLOCKS_MAX * 8 * sizeof(double));
   o.ss = c.take(sizeof(StepState));
   o.bg = c.take((size_t)(6 * p->nz + 12) * es);
+  if (p->adjoint) {
+    o.s2 = c.take(set);
+    o.fbar = c.take(set);
+    o.dbar = c.take(set);
+    o.gbar = c.take(set);
+    o.coef = c.take((size_t)NCOEF_ADJ * p->nx * p->ny * p->nz * es);
+    o.thbar = c.take(6 * n2 * sizeof(double));
+  } else {
+    o.s2 = o.fbar = o.dbar = o.gbar = o.coef = o.thbar = 0;
+  }
   if (p->bc_z == 0) {
     o.twx = c.take((size_t)p->nx * 16);
     o.twy = c.take((size_t)p->ny * 16);
@@ -484,6 +503,14 @@ extern "C" int mhd_create(const mhd_params* p, void* workspace, size_t ws_bytes,
   h->red = (double*)(h->ws + o.red);
   h->ss = (StepState*)(h->ws + o.ss);
   h->bgtab = h->ws + o.bg;
+  if (p->adjoint) {
+    h->s2 = h->ws + o.s2;
+    h->fbar = h->ws + o.fbar;
+    h->dbar = h->ws + o.dbar;
+    h->gbar = h->ws + o.gbar;
+    h->coef = h->ws + o.coef;
+    h->thbar = (double*)(h->ws + o.thbar);
+  }
   h->have_fft = p->bc_z == 0;
   {
     const char* v = getenv("MHD_RK_VARIANT");
@@ -759,6 +786,14 @@ extern "C" int mhd_read_stats(mhd_handle h, mhd_stats* out) {
   return MHD_OK;
 }
 
+extern "C" int mhd_set_time(mhd_handle h, double t) {
+  if (!h) return fail(nullptr, MHD_ERR_ARG, "NULL handle");
+  double tt = t;
+  int rc = cuda_check(h, cudaMemcpyAsync(&h->ss->t, &tt, sizeof(double), cudaMemcpyHostToDevice, h->st), "set time");
+  if (!rc) rc = cuda_check(h, cudaStreamSynchronize(h->st), "set time synchronize");
+  return rc;
+}
+
 extern "C" int mhd_get_time(mhd_handle h, double* t, double* dt) {
   if (!h || !t || !dt) return fail(h, MHD_ERR_ARG, "NULL argument");
   double td[2];
@@ -781,6 +816,159 @@ extern "C" int mhd_read_target(mhd_handle h, void* dst, int mem) {
   if (!rc) rc = cuda_check(h, cudaMemcpyAsync((char*)dst + n2, h->ayt, n2, kind_out(mem), h->st), "copy ayt");
   if (!rc && mem == MHD_MEM_HOST) rc = cuda_check(h, cudaStreamSynchronize(h->st), "target synchronize");
   return rc;
+}
+
+// ---- adjoint -----------------------------------------------------------------
+extern "C" size_t mhd_checkpoint_bytes(mhd_handle h) {
+  return h ? (size_t)NF * h->L.fs * h->esz : 0;
+}
+
+extern "C" int mhd_save(mhd_handle h, void* dst, double* t) {
+  if (!h || !dst || !t) return fail(h, MHD_ERR_ARG, "NULL argument");
+  int rc = cuda_check(h, cudaMemcpyAsync(dst, h->f[h->cur], mhd_checkpoint_bytes(h), cudaMemcpyDeviceToDevice, h->st),
+                      "save");
+  if (!rc) rc = cuda_check(h, cudaMemcpyAsync(t, &h->ss->t, sizeof(double), cudaMemcpyDeviceToHost, h->st), "save t");
+  if (!rc) rc = cuda_check(h, cudaStreamSynchronize(h->st), "save synchronize");
+  return rc;
+}
+
+extern "C" int mhd_restore(mhd_handle h, const void* src, double t) {
+  if (!h || !src) return fail(h, MHD_ERR_ARG, "NULL argument");
+  int rc = cuda_check(h, cudaMemcpyAsync(h->f[h->cur], src, mhd_checkpoint_bytes(h), cudaMemcpyDeviceToDevice, h->st),
+                      "restore");
+  double tt = t;
+  if (!rc) rc = cuda_check(h, cudaMemcpyAsync(&h->ss->t, &tt, sizeof(double), cudaMemcpyHostToDevice, h->st),
+                           "restore t");
+  if (!rc) rc = cuda_check(h, cudaStreamSynchronize(h->st), "restore synchronize");
+  return rc;
+}
+
+static int adjoint_ready(mhd_ctx* h) {
+  if (!h->p.adjoint) return fail(h, MHD_ERR_ARG, "handle created without params.adjoint");
+  if (h->p.bc_z != 0) return fail(h, MHD_ERR_UNSUPPORTED, "the adjoint is built for bc_z = 0");
+  if (!(h->p.dt_fixed > 0.0)) return fail(h, MHD_ERR_ARG, "the adjoint needs a frozen time step (dt_fixed > 0)");
+  return MHD_OK;
+}
+
+extern "C" int mhd_adjoint_init(mhd_handle h, const void* lam, int mem) {
+  if (!h || !lam) return fail(h, MHD_ERR_ARG, "NULL argument");
+  int rc = adjoint_ready(h);
+  if (rc) return rc;
+  const size_t set = (size_t)NF * h->L.fs * h->esz;
+  const size_t n2 = (size_t)h->p.nx * h->p.ny;
+  rc = cuda_check(h, cudaMemsetAsync(h->fbar, 0, set, h->st), "zero fbar");
+  if (!rc) rc = cuda_check(h, cudaMemsetAsync(h->dbar, 0, set, h->st), "zero dbar");
+  if (!rc) rc = cuda_check(h, cudaMemsetAsync(h->thbar, 0, 6 * n2 * sizeof(double), h->st), "zero thbar");
+  if (!rc) rc = cuda_check(h, cudaMemcpyAsync(h->gbar, lam, (size_t)NF * h->p.nx * h->p.ny * h->p.nz * h->esz,
+                                              kind_in(mem), h->st), "copy lam");
+  if (rc) return rc;
+  if (h->esz == 8) launch_adj_unpack<double>(h->L, (const double*)h->gbar, (double*)h->fbar, h->st);
+  else launch_adj_unpack<float>(h->L, (const float*)h->gbar, (float*)h->fbar, h->st);
+  rc = cuda_check(h, cudaSuccess, "adjoint init");
+  if (!rc && mem == MHD_MEM_HOST) rc = cuda_check(h, cudaStreamSynchronize(h->st), "init synchronize");
+  return rc;
+}
+
+template <typename R>
+static void adjoint_step_impl(mhd_ctx* h) {
+  Phys<R> ph = make_phys<R>(&h->p);
+  const Background<R>& bg = bgr<R>(h);
+  R* S[3] = {(R*)h->f[h->cur], (R*)h->f[1 - h->cur], (R*)h->s2};
+  // forward recompute of the substep states (ghost-filled)
+  ghost_fill<R>(h, S[0]);
+  launch_cfl_finalize(h->red, 0, h->ss, h->p.c_adv, h->p.c_diff, h->p.dt_fixed, inv2sum(&h->p), h->t0, h->t1,
+                      h->p.t_ramp, 0, h->st);
+  launch_rk_any<R>(h, S[0], S[1], 0);
+  ghost_fill<R>(h, S[1]);
+  launch_rk_any<R>(h, S[1], S[2], 1);
+  ghost_fill<R>(h, S[2]);
+  h->nlaunch += 14;
+  // reverse substeps
+  FFTPlan fpa = h->fp;
+  fpa.P = h->fp.Q;   // 9 packed ghost-adjoint planes
+  fpa.Q = h->fp.P;   // 3 summed planes
+  for (int s = 2; s >= 0; --s) {
+    launch_adj_axpy<R>(h->L, h->p.bc_z, (R*)h->fbar, (R*)h->dbar, (const R*)h->gbar, rk_beta(s), 0.0, 0, h->ss,
+                       h->st);
+    launch_adj_point<R>(h->L, ph, bg, S[s], (const R*)h->dbar, (R*)h->coef, h->thbar, (const R*)h->wtab,
+                        (const R*)h->wptab, h->ss, s, h->st);
+    launch_adj_gather<R>(h->L, ph, (const R*)h->coef, (const R*)h->dbar, (R*)h->gbar, h->ss, h->st);
+    launch_adj_bc<R>(h->L, ph, bg, S[s], (R*)h->gbar, (R)h->p.dz, h->ss, h->st);
+    launch_pfe_adjoint<R>(fpa, h->L, (R*)h->gbar, h->ss, h->st);
+    launch_adj_axpy<R>(h->L, h->p.bc_z, (R*)h->fbar, (R*)h->dbar, (const R*)h->gbar, 0.0, rk_alpha(s), 1, h->ss,
+                       h->st);
+    h->nlaunch += 9;
+  }
+}
+
+extern "C" int mhd_adjoint_step(mhd_handle h) {
+  if (!h) return fail(nullptr, MHD_ERR_ARG, "NULL handle");
+  int rc = adjoint_ready(h);
+  if (rc) return rc;
+  if (h->esz == 8) adjoint_step_impl<double>(h); else adjoint_step_impl<float>(h);
+  return cuda_check(h, cudaSuccess, "adjoint step");
+}
+
+extern "C" int mhd_adjoint_read(mhd_handle h, void* lam, void* grad_bz, void* grad_v0, void* grad_v1, int mem) {
+  if (!h) return fail(nullptr, MHD_ERR_ARG, "NULL handle");
+  int rc = adjoint_ready(h);
+  if (rc) return rc;
+  const size_t n2 = (size_t)h->p.nx * h->p.ny;
+  const size_t n3b = (size_t)NF * n2 * h->p.nz * h->esz;
+  // results are staged in the coefficient buffer, then copied out
+  char* stage = (char*)h->coef;
+  if (lam) {
+    if (h->esz == 8) launch_adj_pack<double>(h->L, h->p.bc_z, (const double*)h->fbar, (double*)stage, h->st);
+    else launch_adj_pack<float>(h->L, h->p.bc_z, (const float*)h->fbar, (float*)stage, h->st);
+    rc = cuda_check(h, cudaMemcpyAsync(lam, stage, n3b, kind_out(mem), h->st), "copy lam");
+    if (rc) return rc;
+  }
+  char* stage2 = stage + (n3b + 255) / 256 * 256;
+  if (grad_v0 || grad_v1) {
+    if (h->esz == 8) launch_d2r<double>(h->thbar + 2 * n2, (double*)stage2, 4 * n2, h->st);
+    else launch_d2r<float>(h->thbar + 2 * n2, (float*)stage2, 4 * n2, h->st);
+    if (grad_v0) rc = cuda_check(h, cudaMemcpyAsync(grad_v0, stage2, 2 * n2 * h->esz, kind_out(mem), h->st), "v0");
+    if (!rc && grad_v1)
+      rc = cuda_check(h, cudaMemcpyAsync(grad_v1, stage2 + 2 * n2 * h->esz, 2 * n2 * h->esz, kind_out(mem), h->st),
+                      "v1");
+    if (rc) return rc;
+  }
+  if (grad_bz) {
+    char* stage3 = stage2 + (4 * n2 * h->esz + 255) / 256 * 256;
+    if (h->esz == 8) launch_atarget_adjoint<double>(h->fp, h->thbar, h->thbar + n2, (double*)stage3, h->st);
+    else launch_atarget_adjoint<float>(h->fp, h->thbar, h->thbar + n2, (float*)stage3, h->st);
+    rc = cuda_check(h, cudaMemcpyAsync(grad_bz, stage3, n2 * h->esz, kind_out(mem), h->st), "bz");
+    if (rc) return rc;
+  }
+  rc = cuda_check(h, cudaSuccess, "adjoint read");
+  if (!rc && mem == MHD_MEM_HOST) rc = cuda_check(h, cudaStreamSynchronize(h->st), "read synchronize");
+  return rc;
+}
+
+extern "C" int mhd_bz_plane(mhd_handle h, const void* state, int k, void* out) {
+  if (!h || !state || !out) return fail(h, MHD_ERR_ARG, "NULL argument");
+  if (k < 0 || k >= h->p.nz) return fail(h, MHD_ERR_ARG, "layer out of range");
+  if (h->esz == 8)
+    launch_bz_plane<double>(h->p.nx, h->p.ny, h->p.nz, k, h->p.dx, h->p.dy, (const double*)state, (double*)out, 0,
+                            nullptr, nullptr, h->st);
+  else
+    launch_bz_plane<float>(h->p.nx, h->p.ny, h->p.nz, k, h->p.dx, h->p.dy, (const float*)state, (float*)out, 0,
+                           nullptr, nullptr, h->st);
+  return cuda_check(h, cudaSuccess, "bz plane");
+}
+
+extern "C" int mhd_bz_plane_adjoint(mhd_handle h, const void* bbar, int k, void* lam) {
+  if (!h || !bbar || !lam) return fail(h, MHD_ERR_ARG, "NULL argument");
+  if (k < 0 || k >= h->p.nz) return fail(h, MHD_ERR_ARG, "layer out of range");
+  int rc = cuda_check(h, cudaMemsetAsync(lam, 0, (size_t)NF * h->p.nx * h->p.ny * h->p.nz * h->esz, h->st), "zero lam");
+  if (rc) return rc;
+  if (h->esz == 8)
+    launch_bz_plane<double>(h->p.nx, h->p.ny, h->p.nz, k, h->p.dx, h->p.dy, nullptr, nullptr, 1,
+                            (const double*)bbar, (double*)lam, h->st);
+  else
+    launch_bz_plane<float>(h->p.nx, h->p.ny, h->p.nz, k, h->p.dx, h->p.dy, nullptr, nullptr, 1, (const float*)bbar,
+                           (float*)lam, h->st);
+  return cuda_check(h, cudaSuccess, "bz plane adjoint");
 }
 
 static void drop_events(mhd_ctx* h) {

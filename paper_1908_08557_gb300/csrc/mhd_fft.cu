@@ -63,10 +63,14 @@ __device__ double2* fft_lines(double2* a, double2* b, int n, int logn, int nb, c
 // ---------------------------------------------------------------------------
 // 1. forward rows.  mode 0: three boundary planes of the state; mode 1: one
 // real plane `src2d` ([ny][nx], the magnetogram).
+// mode 2 (adjoint of the potential-field ghosts): plane p = 3c + m - 1 packs
+// the ghost adjoints of A_c at the top layer nz-1+m (real) and at -m
+// (imaginary); mode 3: the complex plane dre + i dim (FP64 inputs).
 template <typename R>
 __global__ void __launch_bounds__(256) rows_fwd_kernel(FFTPlan fp, Layout L, const R* __restrict__ f,
                                                        const R* __restrict__ src2d, int mode,
-                                                       const StepState* ss, int nb) {
+                                                       const StepState* ss, int nb, const double* __restrict__ dre,
+                                                       const double* __restrict__ dim) {
   extern __shared__ double2 sm[];
   if (ss && halted(ss)) return;
   const int nx = fp.nx, ny = fp.ny;
@@ -81,6 +85,13 @@ __global__ void __launch_bounds__(256) rows_fwd_kernel(FFTPlan fp, Layout L, con
     if (mode == 1) {
       re = (double)src2d[(long long)y * nx + x];
       im = 0.0;
+    } else if (mode == 2) {
+      const int cc = p / 3, m = p - 3 * cc + 1;
+      re = (double)f[L.at(AX + cc, kt + m, y, x)];
+      im = (double)f[L.at(AX + cc, -m, y, x)];
+    } else if (mode == 3) {
+      re = dre[(long long)y * nx + x];
+      im = dim[(long long)y * nx + x];
     } else if (p == 0) {
       re = (double)f[L.at(AX, kt, y, x)];
       im = (double)f[L.at(AY, kt, y, x)];
@@ -147,6 +158,21 @@ __global__ void __launch_bounds__(256) cols_kernel(FFTPlan fp, int mode, const S
         } else {
           G = make_double2(0.0, 0.0);
         }
+      } else if (mode == 2) {
+        // transpose of Eq. 7's inversion: with F = FFT(X + i Y) for real X,
+        // Y (the adjoints of A_x, A_y), the spectrum of the B_z adjoint is
+        // conj(m_x) X + conj(m_y) Y = [(kt_x - i kt_y) F - (kt_x + i kt_y) conj F(-k)] / (2 kt^2)
+        const double kxm = fp.ktx[col], kym = fp.kty[ky];
+        const double k2 = kxm * kxm + kym * kym;
+        if (k2 > 0.0) {
+          const double2 Fm = spec[(line ^ 1) * ny + ((ny - ky) & (ny - 1))];
+          const double2 Fc = make_double2(Fm.x, -Fm.y);
+          const double2 t1 = cmul(make_double2(kxm, -kym), F);
+          const double2 t2 = cmul(make_double2(kxm, kym), Fc);
+          G = make_double2((t1.x - t2.x) / (2.0 * k2), (t1.y - t2.y) / (2.0 * k2));
+        } else {
+          G = make_double2(0.0, 0.0);
+        }
       } else {
         const double e_t = fp.et[(long long)col * ny + ky], e_b = fp.eb[(long long)col * ny + ky];
         double mt = e_t, mb = e_b;
@@ -182,6 +208,9 @@ __global__ void __launch_bounds__(256) cols_kernel(FFTPlan fp, int mode, const S
 // ---------------------------------------------------------------------------
 // 3. inverse rows: normalise by 1/(nx ny); mode 0 writes ghost layers of the
 // state, mode 1 the compact planes out_re, out_im ([ny][nx]).
+// mode 2 (adjoint): plane c adds its real part into A_c at the top layer and
+// its imaginary part into A_c at the photosphere (interior x, y only);
+// mode 3: real part into out_re.
 template <typename R>
 __global__ void __launch_bounds__(256) rows_inv_kernel(FFTPlan fp, Layout L, R* __restrict__ f, R* out_re,
                                                        R* out_im, int mode, const StepState* ss, int nb) {
@@ -190,7 +219,7 @@ __global__ void __launch_bounds__(256) rows_inv_kernel(FFTPlan fp, Layout L, R* 
   const int nx = fp.nx, ny = fp.ny;
   const int y0 = blockIdx.x * nb;
   const int p = blockIdx.y, o = blockIdx.z;
-  const int nplanes = mode == 0 ? 3 : 1;
+  const int nplanes = mode == 0 ? 3 : (mode == 2 ? 3 : 1);
   double2* a = sm;
   double2* b = sm + nb * nx;
   for (int q = threadIdx.x; q < nb * nx; q += blockDim.x) {
@@ -211,6 +240,15 @@ __global__ void __launch_bounds__(256) rows_inv_kernel(FFTPlan fp, Layout L, R* 
       out_im[(long long)y * nx + x] = im;
       continue;
     }
+    if (mode == 3) {
+      out_re[(long long)y * nx + x] = re;
+      continue;
+    }
+    if (mode == 2) {
+      f[L.at(AX + p, L.nz - 1, y, x)] += re;
+      f[L.at(AX + p, 0, y, x)] += im;
+      continue;
+    }
     int f1, k1, f2, k2;
     if (p == 0) { f1 = AX; k1 = ktop; f2 = AY; k2 = ktop; }
     else if (p == 1) { f1 = AX; k1 = kbot; f2 = AY; k2 = kbot; }
@@ -229,6 +267,61 @@ __global__ void __launch_bounds__(256) rows_inv_kernel(FFTPlan fp, Layout L, R* 
   }
 }
 
+// Adjoint columns: for component c, sum over the three ghost layers m of the
+// extrapolated spectra of the packed ghost adjoints (top real, bottom
+// imaginary), then one inverse FFT along y.  Input planes 3c + m - 1 in
+// fp.P, output plane c in fp.Q.
+__global__ void __launch_bounds__(256) cols_adj_kernel(FFTPlan fp, const StepState* ss, int ppb) {
+  extern __shared__ double2 sm[];
+  if (ss && halted(ss)) return;
+  const int nx = fp.nx, ny = fp.ny;
+  const int npairs = nx / 2 + 1;
+  const int pair0 = blockIdx.x * ppb;
+  const int np = min(ppb, npairs - pair0);
+  const int nl = 2 * np;
+  const int c = blockIdx.y;
+  const int buf = 2 * ppb * ny;
+  double2* X = sm;
+  double2* Y = sm + buf;
+  double2* acc = sm + 2 * buf;
+  for (int q = threadIdx.x; q < nl * ny; q += blockDim.x) acc[q] = make_double2(0.0, 0.0);
+  for (int m = 1; m <= 3; ++m) {
+    const int p = 3 * c + m - 1;
+    __syncthreads();
+    for (int q = threadIdx.x; q < nl * ny; q += blockDim.x) {
+      const int line = q / ny, y = q - line * ny;
+      const int kx = pair0 + (line >> 1);
+      const int col = (line & 1) ? ((nx - kx) & (nx - 1)) : kx;
+      X[line * ny + y] = fp.P[((long long)p * nx + col) * ny + y];
+    }
+    __syncthreads();
+    double2* spec = fft_lines(X, Y, ny, fp.logny, nl, fp.twy, false);
+    for (int q = threadIdx.x; q < nl * ny; q += blockDim.x) {
+      const int line = q / ny, ky = q - line * ny;
+      const int kx = pair0 + (line >> 1);
+      const int col = (line & 1) ? ((nx - kx) & (nx - 1)) : kx;
+      const double e_t = fp.et[(long long)col * ny + ky], e_b = fp.eb[(long long)col * ny + ky];
+      double mt = e_t, mb = e_b;
+      for (int jj = 1; jj < m; ++jj) { mt *= e_t; mb *= e_b; }
+      const double2 F = spec[line * ny + ky];
+      const double2 Fm = spec[(line ^ 1) * ny + ((ny - ky) & (ny - 1))];
+      const double ca = 0.5 * (mt + mb), cb = 0.5 * (mt - mb);
+      acc[q].x += ca * F.x + cb * Fm.x;
+      acc[q].y += ca * F.y - cb * Fm.y;
+    }
+  }
+  __syncthreads();
+  double2* r = fft_lines(acc, X, ny, fp.logny, nl, fp.twy, true);
+  for (int q = threadIdx.x; q < nl * ny; q += blockDim.x) {
+    const int line = q / ny, y = q - line * ny;
+    const int kx = pair0 + (line >> 1);
+    const bool self = (kx == 0 || 2 * kx == nx);
+    if ((line & 1) && self) continue;
+    const int col = (line & 1) ? ((nx - kx) & (nx - 1)) : kx;
+    fp.Q[((long long)c * nx + col) * ny + y] = r[line * ny + y];
+  }
+}
+
 static void set_smem_once() {
   static bool done = false;
   if (done) return;
@@ -238,6 +331,7 @@ static void set_smem_once() {
   cudaFuncSetAttribute(rows_inv_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * FFT_PTS * 16);
   cudaFuncSetAttribute(rows_inv_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * FFT_PTS * 16);
   cudaFuncSetAttribute(cols_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 3 * FFT_PTS * 16);
+  cudaFuncSetAttribute(cols_adj_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 3 * FFT_PTS * 16);
 }
 
 // batch sizes: rows per block (nb) so a block holds ~1024 points, column
@@ -265,7 +359,8 @@ void launch_pfe(const FFTPlan& fp, const Layout& L, R* f, const StepState* ss, c
   set_smem_once();
   const FFTLaunch l = fft_launch(fp);
   const int npairs = fp.nx / 2 + 1;
-  rows_fwd_kernel<R><<<dim3(fp.ny / l.nb, 3), 256, l.smem_rows, st>>>(fp, L, f, nullptr, 0, ss, l.nb);
+  rows_fwd_kernel<R><<<dim3(fp.ny / l.nb, 3), 256, l.smem_rows, st>>>(fp, L, f, nullptr, 0, ss, l.nb, nullptr,
+                                                                       nullptr);
   cols_kernel<<<dim3((npairs + l.ppb - 1) / l.ppb, 3), 256, l.smem_cols, st>>>(fp, 0, ss, l.ppb);
   rows_inv_kernel<R><<<dim3(fp.ny / l.nb, 3, 3), 256, l.smem_rows, st>>>(fp, L, f, nullptr, nullptr, 0, ss, l.nb);
 }
@@ -276,12 +371,48 @@ void launch_atarget(const FFTPlan& fp, const R* bz, R* axt, R* ayt, cudaStream_t
   Layout L{};
   const FFTLaunch l = fft_launch(fp);
   const int npairs = fp.nx / 2 + 1;
-  rows_fwd_kernel<R><<<dim3(fp.ny / l.nb, 1), 256, l.smem_rows, st>>>(fp, L, nullptr, bz, 1, nullptr, l.nb);
+  rows_fwd_kernel<R><<<dim3(fp.ny / l.nb, 1), 256, l.smem_rows, st>>>(fp, L, nullptr, bz, 1, nullptr, l.nb, nullptr,
+                                                                       nullptr);
   cols_kernel<<<dim3((npairs + l.ppb - 1) / l.ppb, 1), 256, l.smem_cols, st>>>(fp, 1, nullptr, l.ppb);
   rows_inv_kernel<R><<<dim3(fp.ny / l.nb, 1, 1), 256, l.smem_rows, st>>>(fp, L, nullptr, axt, ayt, 1, nullptr,
                                                                           l.nb);
 }
 
+// Adjoint of the potential-field ghosts: gbar (adjoint of the ghost-filled
+// state) has its A ghost-layer entries mapped back onto the top layer and
+// the photosphere.  `fp_adj` is the plan with the 9-plane buffer as P and the
+// 3-plane buffer as Q.
+template <typename R>
+void launch_pfe_adjoint(const FFTPlan& fp_adj, const Layout& L, R* gbar, const StepState* ss, cudaStream_t st) {
+  set_smem_once();
+  const FFTLaunch l = fft_launch(fp_adj);
+  const int npairs = fp_adj.nx / 2 + 1;
+  rows_fwd_kernel<R><<<dim3(fp_adj.ny / l.nb, 9), 256, l.smem_rows, st>>>(fp_adj, L, gbar, nullptr, 2, ss, l.nb,
+                                                                           nullptr, nullptr);
+  cols_adj_kernel<<<dim3((npairs + l.ppb - 1) / l.ppb, 3), 256, l.smem_cols, st>>>(fp_adj, ss, l.ppb);
+  rows_inv_kernel<R><<<dim3(fp_adj.ny / l.nb, 3, 1), 256, l.smem_rows, st>>>(fp_adj, L, gbar, nullptr, nullptr, 2, ss,
+                                                                             l.nb);
+}
+
+// Transpose of the magnetogram inversion: B_z adjoint (out, [ny][nx]) from
+// the FP64 adjoints of A_x, A_y (abx, aby).
+template <typename R>
+void launch_atarget_adjoint(const FFTPlan& fp, const double* abx, const double* aby, R* out, cudaStream_t st) {
+  set_smem_once();
+  Layout L{};
+  const FFTLaunch l = fft_launch(fp);
+  const int npairs = fp.nx / 2 + 1;
+  rows_fwd_kernel<R><<<dim3(fp.ny / l.nb, 1), 256, l.smem_rows, st>>>(fp, L, nullptr, nullptr, 3, nullptr, l.nb, abx,
+                                                                       aby);
+  cols_kernel<<<dim3((npairs + l.ppb - 1) / l.ppb, 1), 256, l.smem_cols, st>>>(fp, 2, nullptr, l.ppb);
+  rows_inv_kernel<R><<<dim3(fp.ny / l.nb, 1, 1), 256, l.smem_rows, st>>>(fp, L, nullptr, out, nullptr, 3, nullptr,
+                                                                          l.nb);
+}
+
+template void launch_pfe_adjoint<float>(const FFTPlan&, const Layout&, float*, const StepState*, cudaStream_t);
+template void launch_pfe_adjoint<double>(const FFTPlan&, const Layout&, double*, const StepState*, cudaStream_t);
+template void launch_atarget_adjoint<float>(const FFTPlan&, const double*, const double*, float*, cudaStream_t);
+template void launch_atarget_adjoint<double>(const FFTPlan&, const double*, const double*, double*, cudaStream_t);
 template void launch_pfe<float>(const FFTPlan&, const Layout&, float*, const StepState*, cudaStream_t);
 template void launch_pfe<double>(const FFTPlan&, const Layout&, double*, const StepState*, cudaStream_t);
 template void launch_atarget<float>(const FFTPlan&, const float*, float*, float*, cudaStream_t);

@@ -52,6 +52,26 @@ void launch_rk_tiled(const CUtensorMap* tm, const Layout& L, const Phys<float>& 
                      float* fout, float* df, const float* wtab, const float* wptab, const Driver& drv,
                      StepState* ss, int sub, double dx, double dy, double dz, cudaStream_t st);
 int make_state_tensor_map(CUtensorMap* tm, const Layout& L, void* base);
+// adjoint (transposed linearisation of one substep)
+constexpr int NCOEF_ADJ = 46;
+template <typename R> void launch_adj_point(const Layout& L, const Phys<R>& ph, const Background<R>& bg, const R* g,
+                                            const R* dbar, R* coef, double* thbar, const R* wtab, const R* wptab,
+                                            const StepState* ss, int sub, cudaStream_t st);
+template <typename R> void launch_adj_gather(const Layout& L, const Phys<R>& ph, const R* coef, const R* dbar,
+                                             R* gbar, const StepState* ss, cudaStream_t st);
+template <typename R> void launch_adj_bc(const Layout& L, const Phys<R>& ph, const Background<R>& bg, const R* g,
+                                         R* gbar, R dz, const StepState* ss, cudaStream_t st);
+template <typename R> void launch_adj_axpy(const Layout& L, int bcz, R* fbar, R* dbar, const R* gbar, double beta,
+                                           double alpha, int phase, const StepState* ss, cudaStream_t st);
+template <typename R> void launch_bz_plane(int nx, int ny, int nz, int k, double dx, double dy, const R* st_in,
+                                           R* out, int adjoint, const R* bbar, R* lam, cudaStream_t st);
+template <typename R> void launch_adj_pack(const Layout& L, int bcz, const R* fbar, R* out, cudaStream_t st);
+template <typename R> void launch_adj_unpack(const Layout& L, const R* in, R* fbar, cudaStream_t st);
+template <typename R> void launch_d2r(const double* in, R* out, long long n, cudaStream_t st);
+template <typename R> void launch_pfe_adjoint(const FFTPlan& fp_adj, const Layout& L, R* gbar, const StepState* ss,
+                                              cudaStream_t st);
+template <typename R> void launch_atarget_adjoint(const FFTPlan& fp, const double* abx, const double* aby, R* out,
+                                                  cudaStream_t st);
 // reductions
 template <typename R> int launch_cfl_partial(const Layout& L, const Phys<R>& ph, const Background<R>& bg,
                                              const R* f, const R* wtab,

@@ -1,0 +1,186 @@
+"""Adjoint of the RK step (frozen dt) through the C ABI: dot-product test
+against central differences of the forward step, finite-difference checks of
+a misfit loss through the torch.autograd.Function, bitwise independence from
+the checkpoint budget, and the brute-force oracle gradient (central
+differences of the FP64 oracle over every parameter) on an 8^3 box."""
+import numpy as np
+import pytest
+
+import inputs
+import oracle
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+NG = oracle.NG
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_1908_08557_gb300.build import build
+    build()
+    oracle.build()
+
+
+def _case(nx, ny, nz, seed, dt=0.01, **kw):
+    c = inputs.make_box(nx, ny, nz, seed=seed, magnetogram="bipoles", n_mag=6, **kw)
+    c.params = dict(c.params, dt_fixed=dt)
+    rng = np.random.default_rng(seed + 7)
+    st = c.state.copy()
+    st[3:6] += 0.02 * rng.standard_normal(st[3:6].shape)
+    st[0:3] += 0.01 * rng.standard_normal(st[0:3].shape)
+    st[7] += 0.01 * rng.standard_normal(st[7].shape)
+    c.state = st
+    return c
+
+
+def _sim(case, prec):
+    from paper_1908_08557_gb300 import Simulation
+    return Simulation(case.params, case.state.astype(np.float64 if prec == 64 else np.float32), case.lnrho0,
+                      case.lnT0, precision=prec, adjoint=True)
+
+
+def _T(a, prec):
+    return torch.tensor(np.ascontiguousarray(a), dtype=torch.float64 if prec == 64 else torch.float32, device="cuda")
+
+
+def test_one_step_dot_product_fp64():
+    """<lam, (F(x + e v) - F(x - e v)) / 2e> = <J^T lam, v> for directions in
+    the state and in every parameter (B_z, v0, v1)."""
+    case = _case(16, 16, 12, seed=1)
+    sim = _sim(case, 64)
+    rng = np.random.default_rng(3)
+    nz, ny, nx = 12, 16, 16
+    lam = rng.standard_normal((8, nz, ny, nx))
+    dx = rng.standard_normal((8, nz, ny, nx)) * 0.01
+    dbz = rng.standard_normal((ny, nx)) * 0.05
+    dv0 = rng.standard_normal((2, ny, nx)) * 0.01
+    dv1 = rng.standard_normal((2, ny, nx)) * 0.01
+    t_start = 0.3  # inside the switch-on ramp and between the driver snapshots
+
+    def F(state, bz, v0, v1):
+        sim.set_driver(_T(bz, 64), _T(v0, 64), _T(v1, 64), case.t0, case.t1)
+        sim.write(_T(state, 64))
+        sim.set_time(t_start)
+        sim.step(1)
+        return sim.read().cpu().numpy()
+
+    eps = 1e-5
+    jv = (F(case.state + eps * dx, case.bz + eps * dbz, case.v0 + eps * dv0, case.v1 + eps * dv1) -
+          F(case.state - eps * dx, case.bz - eps * dbz, case.v0 - eps * dv0, case.v1 - eps * dv1)) / (2 * eps)
+    lhs = float(np.sum(lam * jv))
+    sim.set_driver(_T(case.bz, 64), _T(case.v0, 64), _T(case.v1, 64), case.t0, case.t1)
+    sim.write(_T(case.state, 64))
+    sim.set_time(t_start)
+    ck = sim.new_checkpoint()
+    t = sim.save(ck)
+    sim.adjoint_init(_T(lam, 64))
+    sim.restore(ck, t)
+    sim.adjoint_step()
+    g = sim.adjoint_read()
+    rhs = float(np.sum(g["lam"].cpu().numpy() * dx) + np.sum(g["bz"].cpu().numpy() * dbz) +
+                np.sum(g["v0"].cpu().numpy() * dv0) + np.sum(g["v1"].cpu().numpy() * dv1))
+    assert abs(lhs - rhs) <= 1e-7 * abs(lhs), (lhs, rhs)
+    # each parameter block separately
+    for name, d in (("bz", dbz), ("v0", dv0), ("v1", dv1)):
+        args = [case.state, case.bz, case.v0, case.v1]
+        idx = {"bz": 1, "v0": 2, "v1": 3}[name]
+        ap = list(args); am = list(args)
+        ap[idx] = args[idx] + eps * d
+        am[idx] = args[idx] - eps * d
+        l1 = float(np.sum(lam * (F(*ap) - F(*am)) / (2 * eps)))
+        r1 = float(np.sum(g[name].cpu().numpy() * d))
+        assert abs(l1 - r1) <= 1e-6 * max(abs(l1), 1e-12), (name, l1, r1)
+
+
+def _loss_and_grads(case, prec, nsteps, k, target, slots):
+    from paper_1908_08557_gb300.adjoint import BzPlane, DrivenRun
+    sim = _sim(case, prec)
+    bz = _T(case.bz, prec).requires_grad_(True)
+    v0 = _T(case.v0, prec).requires_grad_(True)
+    v1 = _T(case.v1, prec).requires_grad_(True)
+    st = DrivenRun.apply(bz, v0, v1, sim, _T(case.state, prec), nsteps, slots, case.t0, case.t1)
+    b = BzPlane.apply(st, sim, k)
+    loss = 0.5 * ((b - _T(target, prec)) ** 2).sum()
+    loss.backward()
+    out = (float(loss), bz.grad.double().cpu().numpy(), v0.grad.double().cpu().numpy(), v1.grad.double().cpu().numpy())
+    sim.close()
+    return out
+
+
+def _loss_only(case, prec, nsteps, k, target, bz, v0, v1):
+    sim = _sim(case, prec)
+    sim.set_driver(_T(bz, prec), _T(v0, prec), _T(v1, prec), case.t0, case.t1)
+    sim.set_time(0.0)
+    sim.step(nsteps)
+    b = sim.bz_plane(sim.read(), k).double().cpu().numpy()
+    sim.close()
+    return 0.5 * float(((b - target) ** 2).sum())
+
+
+@pytest.mark.parametrize("prec,tol,eps,k", [(64, 1e-6, 1e-4, 1), (32, 1e-3, 2e-2, 0)])
+def test_misfit_gradient_finite_differences(prec, tol, eps, k):
+    """B_z misfit on a layer near the photosphere (where the parameters act
+    within a few steps) after 8 steps: the gradient from the adjoint
+    (DrivenRun + BzPlane autograd functions) against central differences
+    along random directions in (B_z, v0, v1)."""
+    case = _case(32, 32, 24, seed=4, dt=0.02)
+    target = inputs.magnetogram_bipoles(32, 32, 6, seed=99) * 0.5
+    nsteps = 8
+    loss, gbz, gv0, gv1 = _loss_and_grads(case, prec, nsteps, k, target, slots=2)
+    rng = np.random.default_rng(5)
+    for _ in range(3):
+        d = [rng.standard_normal(case.bz.shape), rng.standard_normal(case.v0.shape) * 0.1,
+             rng.standard_normal(case.v1.shape) * 0.1]
+        lp = _loss_only(case, prec, nsteps, k, target, case.bz + eps * d[0], case.v0 + eps * d[1], case.v1 + eps * d[2])
+        lm = _loss_only(case, prec, nsteps, k, target, case.bz - eps * d[0], case.v0 - eps * d[1], case.v1 - eps * d[2])
+        fd = (lp - lm) / (2 * eps)
+        ad = float(np.sum(gbz * d[0]) + np.sum(gv0 * d[1]) + np.sum(gv1 * d[2]))
+        assert abs(ad) > 1e-6
+        assert abs(fd - ad) <= tol * abs(ad), (fd, ad)
+
+
+def test_checkpoint_budget_does_not_change_the_gradient():
+    """Binomial checkpointing recomputes the same forward states: gradients
+    with 1 slot and with one slot per step are bitwise identical."""
+    case = _case(16, 16, 12, seed=6)
+    target = np.zeros((16, 16))
+    a = _loss_and_grads(case, 64, 9, 6, target, slots=1)
+    b = _loss_and_grads(case, 64, 9, 6, target, slots=9)
+    assert a[0] == b[0]
+    for x, y in zip(a[1:], b[1:]):
+        assert np.array_equal(x, y)
+
+
+def test_bruteforce_oracle_gradient_8cube():
+    """Every component of the gradient of the B_z misfit on the photosphere
+    (8^3 box, 3 steps) against central differences of the FP64 CPU oracle."""
+    case = _case(8, 8, 8, seed=8, dt=0.02)
+    p = case.params
+    k, nsteps = 0, 3
+    target = np.sin(np.arange(64).reshape(8, 8) * 0.3) * 0.1
+    loss, gbz, gv0, gv1 = _loss_and_grads(case, 64, nsteps, k, target, slots=3)
+
+    def oracle_loss(bz, v0, v1):
+        axt, ayt = oracle.a_target(p, bz)
+        u = oracle.to_padded(case.state)
+        oracle.run(p, u, case.lnrho0, axt, ayt, v0, v1, case.t0, case.t1, 0.0, nsteps)
+        oracle.fill_ghosts(p, u, case.lnrho0)
+        b = oracle.deriv(p, u, 1, 0, 0)[k] - oracle.deriv(p, u, 0, 0, 1)[k]
+        return 0.5 * float(((b - target) ** 2).sum())
+
+    assert abs(oracle_loss(case.bz, case.v0, case.v1) - loss) <= 1e-10 * loss
+    eps = 1e-5
+    scale = max(np.abs(gbz).max(), np.abs(gv0).max(), np.abs(gv1).max())
+    assert scale > 1e-4
+    for name, g in (("bz", gbz), ("v0", gv0), ("v1", gv1)):
+        base = {"bz": case.bz, "v0": case.v0, "v1": case.v1}
+        fd = np.zeros_like(g)
+        for idx in np.ndindex(g.shape):
+            args_p = {kk: vv.copy() for kk, vv in base.items()}
+            args_m = {kk: vv.copy() for kk, vv in base.items()}
+            args_p[name][idx] += eps
+            args_m[name][idx] -= eps
+            fd[idx] = (oracle_loss(args_p["bz"], args_p["v0"], args_p["v1"]) -
+                       oracle_loss(args_m["bz"], args_m["v0"], args_m["v1"])) / (2 * eps)
+        assert np.abs(fd - g).max() <= 1e-6 * scale, (name, np.abs(fd - g).max(), scale)
