@@ -43,6 +43,8 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--no-production", action="store_true")
     return ap.parse_args()
 
 
@@ -171,6 +173,105 @@ def cpu_oracle_sample(nx=256, ny=256, nz=32, steps=1):
     oracle.run(case.params, u, case.lnrho0, axt, ayt, case.v0, case.v1, case.t0, case.t1, 0.0, steps)
     dt = time.perf_counter() - t0
     return nx * ny * nz * steps / dt, dt
+
+
+def _cuda_ms(stream, fn):
+    import torch
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1)
+
+
+def adjoint_ratios(case, dev, ws):
+    import torch
+
+    import inputs
+    from paper_1908_08557_gb300 import Simulation
+    from paper_1908_08557_gb300.adjoint import Revolver
+    out = {}
+    # per step at the bench size, frozen dt = 0.017 (about the CFL step)
+    p = dict(case.params, dt_fixed=0.017)
+    sim = Simulation(p, torch.tensor(case.state, dtype=torch.float32, device=dev), case.lnrho0, case.lnT0,
+                     precision=32, adjoint=True, device=str(dev))
+    sim.set_driver(torch.tensor(case.bz, dtype=torch.float32, device=dev),
+                   torch.tensor(case.v0, dtype=torch.float32, device=dev),
+                   torch.tensor(case.v1, dtype=torch.float32, device=dev), case.t0, case.t1)
+    sim.step(2)
+    ck = sim.new_checkpoint()
+    t = sim.save(ck)
+    fwd = _cuda_ms(sim.stream, lambda: sim.step(3)) / 3
+    sim.adjoint_init(torch.zeros((8, p["nz"], p["ny"], p["nx"]), dtype=torch.float32, device=dev))
+
+    def rev():
+        for _ in range(3):
+            sim.restore(ck, t)
+            sim.adjoint_step()
+    adj = _cuda_ms(sim.stream, rev) / 3
+    out["bench_workload"] = {"forward_ms_per_step": fwd, "adjoint_ms_per_step": adj, "ratio": adj / fwd}
+    sim.close()
+    del sim, ck
+    torch.cuda.empty_cache()
+    # full checkpointed sweep of the gradient workload
+    c4 = inputs.make_case("bipoles8_64x64x64")
+    p4 = dict(c4.params, dt_fixed=0.017)
+    sim = Simulation(p4, torch.tensor(c4.state, dtype=torch.float32, device=dev), c4.lnrho0, c4.lnT0, precision=32,
+                     adjoint=True, device=str(dev))
+    sim.set_driver(torch.tensor(c4.bz, dtype=torch.float32, device=dev),
+                   torch.tensor(c4.v0, dtype=torch.float32, device=dev),
+                   torch.tensor(c4.v1, dtype=torch.float32, device=dev), c4.t0, c4.t1)
+    n, slots = c4.nsteps, 10
+    sim.set_time(0.0)
+    ck0 = sim.new_checkpoint()
+    t0 = sim.save(ck0)
+    fwd = _cuda_ms(sim.stream, lambda: sim.step(n))
+    sim.restore(ck0, t0)
+    rv = Revolver(sim, slots)
+    fwd_ck = _cuda_ms(sim.stream, lambda: rv.forward(n))
+    sim.adjoint_init(torch.zeros((8, p4["nz"], p4["ny"], p4["nx"]), dtype=torch.float32, device=dev))
+    rev_ms = _cuda_ms(sim.stream, rv.reverse)
+    out["bipoles8_64x64x64"] = {"steps": n, "slots": slots, "forward_ms": fwd, "forward_with_checkpoints_ms": fwd_ck,
+                                 "reverse_ms": rev_ms, "ratio": rev_ms / fwd,
+                                 "recompute_fraction": rv.recomputed_steps / n}
+    sim.close()
+    del sim
+    torch.cuda.empty_cache()
+    return out
+
+
+def production_line(dev, ws):
+    import numpy as np
+    import torch
+
+    import inputs
+    from paper_1908_08557_gb300 import Simulation
+    c = inputs.make_case("ar_1024x1024x256", dtype=np.float32)
+    p = c.params
+    sim = Simulation(p, c.state, c.lnrho0, c.lnT0, precision=32, stats_every=10, device=str(dev))
+    del c.state
+    sim.set_driver(torch.tensor(c.bz, dtype=torch.float32, device=dev),
+                   torch.tensor(c.v0, dtype=torch.float32, device=dev),
+                   torch.tensor(c.v1, dtype=torch.float32, device=dev), c.t0, c.t1)
+    sim.step(3)
+    torch.cuda.synchronize()
+    k = 10
+    ms = _cuda_ms(sim.stream, lambda: sim.step(k))
+    ms = max_over_ranks(ms, ws)
+    cells = p["nx"] * p["ny"] * p["nz"]
+    sim.profile(True)
+    sim.step(3)
+    prof = sim.read_profile()
+    sim.profile(False)
+    sim.close()
+    del sim
+    torch.cuda.empty_cache()
+    rk_ms, rk_n = prof["rk"]
+    achieved = WORDS_PER_CELL_STEP * cells * 4 / 3.0 / (rk_ms / rk_n / 1e3) / 1e9
+    return {"value": ws * cells * k / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / k, "steps": k,
+            "rk_achieved_gbs": achieved, "class_ms_per_step": {kk: v[0] / 3 for kk, v in prof.items()}}
 
 
 def run_reference(args, ws, rank):
@@ -309,6 +410,19 @@ def run_native(args, ws, rank, local):
         del s64
         torch.cuda.empty_cache()
 
+    # adjoint / forward time: one adjoint step (recompute of its substeps
+    # included) against one forward step, at the bench size; and a full
+    # checkpointed sweep of the gradient workload bipoles8_64x64x64
+    # (100 steps, 10 slots) against its forward run
+    adj = None
+    if not args.no_adjoint:
+        adj = adjoint_ratios(case, dev, ws)
+
+    # production size 1024 x 1024 x 256 (FP32, horizontal spacing 4x vertical)
+    prod = None
+    if not args.no_production:
+        prod = production_line(dev, ws)
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         import oracle
@@ -328,7 +442,7 @@ def run_native(args, ws, rank, local):
                            "l2": f"working set {state_gb:.2f} GB > 129 MB L2, no flush",
                            "parallelism": f"replicas x{ws}"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-                "clocks": clocks, "fp64": fp64}
+                "clocks": clocks, "fp64": fp64, "adjoint": adj, "production_1024x1024x256": prod}
         print(json.dumps(line), flush=True)
 
 

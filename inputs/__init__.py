@@ -73,14 +73,23 @@ def scheme_params(nx: int, ny: int, nz: int, dx: float = 1.0, dy: float = 1.0,
 # magnetograms
 
 def _periodic_gauss(nx, ny, x0, y0, sigma):
-    """Gaussian of width sigma (cells) summed over the nearest periodic images."""
-    x = np.arange(nx)[None, :]
-    y = np.arange(ny)[:, None]
+    """Gaussian of width sigma (cells) summed over the nearest periodic images
+    (evaluated within 8 sigma of the centre; beyond that it is below 1e-13)."""
     g = np.zeros((ny, nx))
-    for sx in (-1, 0, 1):
-        for sy in (-1, 0, 1):
-            r2 = (x - x0 - sx * nx) ** 2 + (y - y0 - sy * ny) ** 2
-            g += np.exp(-r2 / (2.0 * sigma * sigma))
+    w = int(np.ceil(8.0 * sigma))
+    if 2 * w + 1 >= min(nx, ny):
+        x = np.arange(nx)[None, :]
+        y = np.arange(ny)[:, None]
+        for sx in (-1, 0, 1):
+            for sy in (-1, 0, 1):
+                r2 = (x - x0 - sx * nx) ** 2 + (y - y0 - sy * ny) ** 2
+                g += np.exp(-r2 / (2.0 * sigma * sigma))
+        return g
+    ic, jc = int(np.floor(x0)), int(np.floor(y0))
+    xi = np.arange(ic - w, ic + w + 1)
+    yj = np.arange(jc - w, jc + w + 1)
+    vals = np.exp(-((yj[:, None] - y0) ** 2 + (xi[None, :] - x0) ** 2) / (2.0 * sigma * sigma))
+    np.add.at(g, (yj[:, None] % ny, xi[None, :] % nx), vals)
     return g
 
 
@@ -206,16 +215,16 @@ def initial_atmosphere(nz, dz, gz, t_bottom=1.0, t_top=100.0, zc_cells=12.0,
     return np.log(T), lnp - np.log(T)
 
 
-def initial_potential_field(bz, nz, dx, dy, dz):
+def initial_potential_field(bz, nz, dx, dy, dz, dtype=np.float64):
     """Potential field whose vertical component at z = 0 is bz, as a vector
     potential in the Weyl gauge with A_z = 0, using exact spectral wavenumbers:
     A^(k, z) = (i k_y, -i k_x, 0) B^_z(k) / |k|^2 exp(-|k| z) for k = 0..nz-1.
     (Initial-condition preparation; not the library's own inversion.)"""
     ny, nx = bz.shape
-    kx = 2 * np.pi * np.fft.fftfreq(nx, d=dx)[None, :]
+    kx = 2 * np.pi * np.fft.rfftfreq(nx, d=dx)[None, :]
     ky = 2 * np.pi * np.fft.fftfreq(ny, d=dy)[:, None]
     kk = np.sqrt(kx ** 2 + ky ** 2)
-    bh = np.fft.fft2(bz)
+    bh = np.fft.rfft2(bz)
     bh[0, 0] = 0.0
     if nx % 2 == 0:
         bh[:, nx // 2] = 0.0
@@ -224,13 +233,13 @@ def initial_potential_field(bz, nz, dx, dy, dz):
     with np.errstate(divide="ignore", invalid="ignore"):
         axh = np.where(kk > 0, 1j * ky * bh / kk ** 2, 0.0)
         ayh = np.where(kk > 0, -1j * kx * bh / kk ** 2, 0.0)
-    ax = np.empty((nz, ny, nx))
-    ay = np.empty((nz, ny, nx))
+    ax = np.empty((nz, ny, nx), dtype=dtype)
+    ay = np.empty((nz, ny, nx), dtype=dtype)
     for k in range(nz):
         dec = np.exp(-kk * k * dz)
-        ax[k] = np.real(np.fft.ifft2(axh * dec))
-        ay[k] = np.real(np.fft.ifft2(ayh * dec))
-    return ax, ay, np.zeros((nz, ny, nx))
+        ax[k] = np.fft.irfft2(axh * dec, s=(ny, nx))
+        ay[k] = np.fft.irfft2(ayh * dec, s=(ny, nx))
+    return ax, ay, np.zeros((nz, ny, nx), dtype=dtype)
 
 
 @dataclasses.dataclass
@@ -250,7 +259,7 @@ class Case:
 
 def make_box(nx, ny, nz, seed=0, magnetogram="spots", n_mag=4, sigma=3.0,
              driver="noise", driver_rms=0.01, dx=1.0, dy=1.0, dz=1.0,
-             nsteps=50, name=None, ar_pair=None, t1=1.0, **over) -> Case:
+             nsteps=50, name=None, ar_pair=None, t1=1.0, dtype=np.float64, **over) -> Case:
     p = scheme_params(nx, ny, nz, dx, dy, dz, **over)
     if magnetogram == "spots":
         bz = magnetogram_spots(nx, ny, n_mag, sigma, seed)
@@ -264,8 +273,8 @@ def make_box(nx, ny, nz, seed=0, magnetogram="spots", n_mag=4, sigma=3.0,
         v0 = driver_solenoidal(nx, ny, km, driver_rms, seed)
         v1 = driver_solenoidal(nx, ny, km, driver_rms, seed + 1)
     lnT0, lnrho0 = initial_atmosphere(nz, dz, p["gz"])
-    ax, ay, az = initial_potential_field(bz, nz, dx, dy, dz)
-    st = np.zeros((NFIELD, nz, ny, nx))
+    ax, ay, az = initial_potential_field(bz, nz, dx, dy, dz, dtype)
+    st = np.zeros((NFIELD, nz, ny, nx), dtype=dtype)
     st[0], st[1], st[2] = ax, ay, az
     st[6] = lnrho0[NGHOST:NGHOST + nz, None, None]
     st[7] = lnT0[NGHOST:NGHOST + nz, None, None]
@@ -289,9 +298,11 @@ WORKLOADS = {
 }
 
 
-def make_case(name: str, seed: int = 0) -> Case:
+def make_case(name: str, seed: int = 0, dtype=np.float64) -> Case:
+    """A named workload; dtype sets the precision of the initial state array
+    (the profiles, magnetogram and drivers stay float64)."""
     kw = dict(WORKLOADS[name])
-    return make_box(seed=seed, name=name, **kw)
+    return make_box(seed=seed, name=name, dtype=dtype, **kw)
 
 
 def padded_shape(nx, ny, nz):

@@ -54,6 +54,7 @@ def lib():
         dp = ctypes.POINTER(ctypes.c_double)
         ip = ctypes.POINTER(ctypes.c_int)
         _lib.or_fill_ghosts.argtypes = [ip, dp, dp, dp]
+        _lib.or_fill_ghosts_nopfe.argtypes = [ip, dp, dp, dp]
         _lib.or_rhs.argtypes = [ip, dp, dp, dp, dp, dp, dp, ctypes.c_double,
                                 ctypes.c_double, ctypes.c_double, dp]
         _lib.or_cfl.argtypes = [ip, dp, dp]
@@ -106,10 +107,25 @@ def interior(u: np.ndarray) -> np.ndarray:
     return u[:, NG:-NG, NG:-NG, NG:-NG].copy()
 
 
-def fill_ghosts(p: Dict, u: np.ndarray, lnrho0: np.ndarray) -> np.ndarray:
-    """Fill every ghost cell of the padded state in place (and return it)."""
+def fill_ghosts(p: Dict, u: np.ndarray, lnrho0: np.ndarray, pfe: str = "dft") -> np.ndarray:
+    """Fill every ghost cell of the padded state in place (and return it).
+    pfe="dft": the potential-field ghosts by the plain DFT (in C);
+    pfe="fft": by numpy's FFT (pfe_plane_fft), for large planes."""
     lnrho0 = np.ascontiguousarray(lnrho0, dtype=np.float64)
-    lib().or_fill_ghosts(_i(_dims(p)), _d(_pvec(p)), _d(u), _d(lnrho0))
+    if pfe == "dft" or int(p.get("bc_z", 0)) == 1:
+        lib().or_fill_ghosts(_i(_dims(p)), _d(_pvec(p)), _d(u), _d(lnrho0))
+        return u
+    lib().or_fill_ghosts_nopfe(_i(_dims(p)), _d(_pvec(p)), _d(u), _d(lnrho0))
+    nx, ny, nz = p["nx"], p["ny"], p["nz"]
+    lx, ly, dz = nx * p["dx"], ny * p["dy"], p["dz"]
+    kt = NG + nz - 1
+    for c in range(3):
+        top = pfe_plane_fft(lx, ly, u[c, kt, NG:-NG, NG:-NG], [-m * dz for m in (1, 2, 3)])
+        bot = pfe_plane_fft(lx, ly, u[c, NG, NG:-NG, NG:-NG],
+                            [p["f_pfe_bottom"] * m * dz for m in (1, 2, 3)])
+        for m in (1, 2, 3):
+            u[c, kt + m] = np.pad(top[m - 1], NG, mode="wrap")
+            u[c, NG - m] = np.pad(bot[m - 1], NG, mode="wrap")
     return u
 
 
@@ -120,6 +136,28 @@ def a_target(p: Dict, bz: np.ndarray):
     ax = np.zeros((ny, nx))
     ay = np.zeros((ny, nx))
     lib().or_a_target(nx, ny, p["dx"], p["dy"], _d(bz), _d(ax), _d(ay))
+    return ax, ay
+
+
+def a_target_fft(p: Dict, bz: np.ndarray):
+    """Same inversion as `a_target` with numpy's FFT as the transform step,
+    for planes too large for the plain DFT (pinned against `a_target`)."""
+    ny, nx = bz.shape
+
+    def kmod(n, h):
+        m = np.arange(n)
+        th = 2 * np.pi * np.where(2 * m > n, m - n, m) / n
+        k = (45 * np.sin(th) - 9 * np.sin(2 * th) + np.sin(3 * th)) / (30 * h)
+        k[(m == 0) | (2 * m == n)] = 0.0
+        return k
+
+    kx = kmod(nx, p["dx"])[None, :]
+    ky = kmod(ny, p["dy"])[:, None]
+    k2 = kx ** 2 + ky ** 2
+    bh = np.fft.fft2(bz)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        ax = np.real(np.fft.ifft2(np.where(k2 > 0, 1j * ky * bh / k2, 0)))
+        ay = np.real(np.fft.ifft2(np.where(k2 > 0, -1j * kx * bh / k2, 0)))
     return ax, ay
 
 

@@ -263,7 +263,19 @@ static void fill_rims(const grid_t* g, double* u, int f, int k) {
     }
 }
 
+static void fill_ghosts_impl(const int* dims, const double* p, double* u, const double* lnrho0, int do_pfe);
+
 void or_fill_ghosts(const int* dims, const double* p, double* u, const double* lnrho0) {
+  fill_ghosts_impl(dims, p, u, lnrho0, 1);
+}
+
+/* Every ghost rule except the potential-field extrapolation of A (for
+ * planes too large for the plain DFT; the caller supplies those ghosts). */
+void or_fill_ghosts_nopfe(const int* dims, const double* p, double* u, const double* lnrho0) {
+  fill_ghosts_impl(dims, p, u, lnrho0, 0);
+}
+
+static void fill_ghosts_impl(const int* dims, const double* p, double* u, const double* lnrho0, int do_pfe) {
   grid_t G = {dims[0], dims[1], dims[2], dims[3], p};
   const grid_t* g = &G;
   int nx = g->nx, ny = g->ny, nz = g->nz;
@@ -326,6 +338,7 @@ void or_fill_ghosts(const int* dims, const double* p, double* u, const double* l
   /* (3) potential-field ghosts of all three components of A: regular
    * extrapolation upward (Eq. 17, Delta''z = m dz), inverted extrapolation
    * downward with the contrast growth reduced by f_b (Sect. 2.4). */
+  if (!do_pfe) return;
   size_t n = (size_t)nx * ny;
   double* plane = (double*)malloc(sizeof(double) * n);
   double* gh = (double*)malloc(sizeof(double) * n * NG);

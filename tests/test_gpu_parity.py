@@ -275,3 +275,50 @@ def test_tiled_full_size_sampled_bipoles40_256():
     for f in range(8):
         s = np.abs(ref[:, f]).max()
         assert np.abs(g[:, f] - ref[:, f]).max() <= 2e-4 * max(s, 1e-30), (f, np.abs(g[:, f] - ref[:, f]).max(), s)
+
+
+@pytest.mark.parametrize("prec", [64, 32])
+def test_production_geometry_1024_sampled(prec):
+    """Production geometry: 1024 x 1024 horizontal points, horizontal spacing
+    4x vertical (workload ar_1024x1024x256 recipe on 8 layers): the full
+    ghost fill (1024^2 FFT planes; FP64) and the RHS at 3000 sampled cells
+    against the oracle (potential-field ghosts by numpy's FFT)."""
+    case = inputs.make_box(1024, 1024, 8, seed=3, dx=4.0, dy=4.0, magnetogram="bipoles", n_mag=400,
+                           driver="solenoidal", ar_pair=(5.0, 40.0, 200.0))
+    rng = np.random.default_rng(1)
+    st = case.state.copy()
+    st[3:6] += 0.01 * rng.standard_normal(st[3:6].shape)
+    if prec == 32:
+        st[0:6] = st[0:6].astype(np.float32).astype(np.float64)
+    case.state = st
+    sim = _sim(case, prec)
+    sim.fill_ghosts()
+    p = case.params
+    u = oracle.to_padded(st)
+    oracle.fill_ghosts(p, u, case.lnrho0, pfe="fft")
+    if prec == 64:
+        got = sim.read_padded(0)
+        for f in range(8):
+            scale = np.abs(u[f]).max()
+            assert np.abs(got[f] - u[f]).max() <= 1e-12 * scale, f
+        del got
+    t = 0.4
+    rhs = sim.eval_rhs(t)
+    sim.close()
+    nx, ny, nz = 1024, 1024, 8
+    ks = rng.integers(0, nz, 3000)
+    js = rng.integers(0, ny, 3000)
+    iss = rng.integers(0, nx, 3000)
+    cells = np.stack([ks, js, iss], axis=1)
+    cast = (lambda a: a.astype(np.float32).astype(np.float64)) if prec == 32 else (lambda a: a)
+    axt, ayt = oracle.a_target_fft(p, case.bz)
+    ref = oracle.rhs_cells(p, u, cast(axt), cast(ayt), cast(case.v0), cast(case.v1), case.t0, case.t1, t, cells)
+    g = rhs[:, ks + NG, js + NG, iss + NG].T.astype(np.float64)
+    # FP32 bound from the arithmetic: |A| reaches ~100 here (flux of the
+    # sigma = 40-cell pair over dx = 4); FP32 second differences of A carry
+    # ~6e-8 * 100 * sum|w2| (~6) / dz^2 = 4e-5 absolute, entering dA/dt with
+    # eta_s w <= 0.5 in the swamp: ~2e-5 against an RHS scale of ~0.1.
+    tol = 1e-10 if prec == 64 else 1e-3
+    for f in range(8):
+        s = np.abs(ref[:, f]).max()
+        assert np.abs(g[:, f] - ref[:, f]).max() <= tol * max(s, 1e-30), (f, np.abs(g[:, f] - ref[:, f]).max(), s)

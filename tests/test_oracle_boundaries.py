@@ -126,6 +126,17 @@ def test_pfe_single_mode(mx, my):
             assert np.allclose(bot, (2 - c) * mode * np.exp(0.2 * kk * m * dz), rtol=0, atol=1e-12)
 
 
+def test_ghost_fill_fft_variant_matches_plain_dft():
+    """The numpy-FFT ghost fill used for large planes equals the plain-DFT
+    one (every ghost cell, all fields)."""
+    case = inputs.make_box(16, 32, 10, seed=12, dx=2.0, dy=0.5)
+    a = oracle.to_padded(case.state)
+    b = a.copy()
+    oracle.fill_ghosts(case.params, a, case.lnrho0, pfe="dft")
+    oracle.fill_ghosts(case.params, b, case.lnrho0, pfe="fft")
+    assert np.allclose(a, b, rtol=0, atol=1e-12)
+
+
 def test_pfe_plain_dft_matches_numpy_fft():
     rng = np.random.default_rng(0)
     nx, ny = 16, 32
@@ -163,6 +174,15 @@ def test_a_target_reproduces_band_limited_bz():
         h[b, a] = 0.0
     band = np.real(np.fft.ifft2(h))
     assert np.allclose(curl, band, rtol=0, atol=1e-12)
+
+
+def test_a_target_fft_variant_matches_plain_dft():
+    nx, ny = 32, 16
+    p = _params(nx, ny, 4, dx=1.0, dy=1.5)
+    bz = np.random.default_rng(8).standard_normal((ny, nx))
+    a = oracle.a_target(p, bz)
+    b = oracle.a_target_fft(p, bz)
+    assert np.allclose(a[0], b[0], rtol=0, atol=1e-13) and np.allclose(a[1], b[1], rtol=0, atol=1e-13)
 
 
 def test_swamp_weight():
