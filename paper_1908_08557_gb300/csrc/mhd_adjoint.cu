@@ -627,3 +627,333 @@ INST(double)
 #undef INST
 
 }  // namespace mhd
+
+namespace mhd {
+
+// ===========================================================================
+// Tiled gather: a block owns 32 x 8 columns and 8 consecutive z points of
+// the output (z in [-3, nz+3)); it walks the 46 coefficient fields, staging
+// each on the block's points plus a 3-cell halo in shared memory (periodic in
+// x and y, zero outside the interior layers), and accumulates the transposed
+// stencils into 8 targets x 8 z points held in registers.  z stencils reuse a
+// 14-value column per thread.
+namespace gtile {
+
+constexpr int TX = 32, TY = 8, TZ = 8;
+constexpr int SX = TX + 6, SY = TY + 6, SZ = TZ + 6;
+constexpr int TILE = SX * SY * SZ;
+
+template <typename R>
+struct Acc {
+  R v[8][TZ];
+};
+
+template <typename R>
+struct GArgs {
+  Layout L;
+  Phys<R> ph;
+  const R* coef;
+  const R* dbar;
+  R* gbar;
+  const StepState* ss;
+  int ntx, nty, ntz;
+};
+
+// asynchronous 4- or 8-byte copy global -> shared; src_bytes = 0 zero-fills
+__device__ __forceinline__ void cp_async_elem(void* dst, const void* src, int bytes, int src_bytes) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  if (bytes == 4)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(src), "r"(src_bytes) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(src), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// Stage coefficient field `base` (one [nz][ny][nx] field) for the block:
+// warp w copies tile rows w, w + 8, ...; rowoff[r] is the offset of tile row
+// r in the field (-1 outside the interior layers: zero fill); ix0, ix1 are
+// the thread's two wrapped x indices (lane and lane + 32).
+template <typename R>
+__device__ __forceinline__ void stage_async(R* __restrict__ s, const R* __restrict__ base, const int* rowoff, int ix0,
+                                            int ix1) {
+  const int lane = threadIdx.x;
+  for (int r = threadIdx.y; r < SY * SZ; r += TY) {
+    const int ro = rowoff[r];
+    const R* src = base + (ro < 0 ? 0 : ro);
+    const int nb = ro < 0 ? 0 : (int)sizeof(R);
+    cp_async_elem(s + r * SX + lane, src + ix0, (int)sizeof(R), nb);
+    if (lane < SX - 32) cp_async_elem(s + r * SX + lane + 32, src + ix1, (int)sizeof(R), nb);
+  }
+}
+
+// index of staged point (x offset dx, y offset dy, z point zz + dz) of the
+// thread's column; the thread's own point sits at (tx + 3, ty + 3, zz + 3)
+__device__ __forceinline__ int sidx(int tx, int ty, int zz, int dx, int dy, int dz) {
+  return ((zz + 3 + dz) * SY + (ty + 3 + dy)) * SX + (tx + 3 + dx);
+}
+
+// D1^T along x or y (AX = 0 / 1) into acc[zz]
+template <typename R, int AXIS>
+__device__ __forceinline__ void t_d1_xy(const R* s, R (&acc)[TZ], int tx, int ty, R inv) {
+#pragma unroll
+  for (int zz = 0; zz < TZ; ++zz) {
+    R v = R(0);
+#pragma unroll
+    for (int m = 1; m <= 3; ++m) {
+      const R cm = m == 1 ? W<R>::c1 : (m == 2 ? W<R>::c2 : W<R>::c3);
+      const int dx = AXIS == 0 ? m : 0, dy = AXIS == 1 ? m : 0;
+      v += cm * (s[sidx(tx, ty, zz, -dx, -dy, 0)] - s[sidx(tx, ty, zz, dx, dy, 0)]);
+    }
+    acc[zz] += v * inv;
+  }
+}
+template <typename R, int AXIS>
+__device__ __forceinline__ void t_d2_xy(const R* s, R (&acc)[TZ], int tx, int ty, R inv2) {
+#pragma unroll
+  for (int zz = 0; zz < TZ; ++zz) {
+    R v = W<R>::e0 * s[sidx(tx, ty, zz, 0, 0, 0)];
+#pragma unroll
+    for (int m = 1; m <= 3; ++m) {
+      const R em = m == 1 ? W<R>::e1 : (m == 2 ? W<R>::e2 : W<R>::e3);
+      const int dx = AXIS == 0 ? m : 0, dy = AXIS == 1 ? m : 0;
+      v += em * (s[sidx(tx, ty, zz, -dx, -dy, 0)] + s[sidx(tx, ty, zz, dx, dy, 0)]);
+    }
+    acc[zz] += v * inv2;
+  }
+}
+// z stencils from a column col[0..13] (z points -3 .. TZ+2)
+template <typename R>
+__device__ __forceinline__ void t_d1_z(const R (&col)[SZ], R (&acc)[TZ], R inv) {
+#pragma unroll
+  for (int zz = 0; zz < TZ; ++zz) {
+    const R v = W<R>::c1 * (col[zz + 2] - col[zz + 4]) + W<R>::c2 * (col[zz + 1] - col[zz + 5]) +
+                W<R>::c3 * (col[zz] - col[zz + 6]);
+    acc[zz] += v * inv;
+  }
+}
+template <typename R>
+__device__ __forceinline__ void t_d2_z(const R (&col)[SZ], R (&acc)[TZ], R inv2) {
+#pragma unroll
+  for (int zz = 0; zz < TZ; ++zz) {
+    const R v = W<R>::e0 * col[zz + 3] + W<R>::e1 * (col[zz + 2] + col[zz + 4]) +
+                W<R>::e2 * (col[zz + 1] + col[zz + 5]) + W<R>::e3 * (col[zz] + col[zz + 6]);
+    acc[zz] += v * inv2;
+  }
+}
+template <typename R>
+__device__ __forceinline__ void load_col(const R* s, R (&col)[SZ], int tx, int ty, int dx, int dy) {
+#pragma unroll
+  for (int z = 0; z < SZ; ++z) col[z] = s[(z * SY + ty + 3 + dy) * SX + tx + 3 + dx];
+}
+// mixed (x, y): D1x D1y applied to the staged field
+template <typename R>
+__device__ __forceinline__ void t_mix_xy(const R* s, R (&acc)[TZ], int tx, int ty, R ia, R ib) {
+#pragma unroll
+  for (int zz = 0; zz < TZ; ++zz) {
+    R v = R(0);
+#pragma unroll
+    for (int m = 1; m <= 3; ++m) {
+      const R cm = m == 1 ? W<R>::c1 : (m == 2 ? W<R>::c2 : W<R>::c3);
+      R w = R(0);
+#pragma unroll
+      for (int n = 1; n <= 3; ++n) {
+        const R cn = n == 1 ? W<R>::c1 : (n == 2 ? W<R>::c2 : W<R>::c3);
+        w += cn * (s[sidx(tx, ty, zz, m, n, 0)] - s[sidx(tx, ty, zz, m, -n, 0)] - s[sidx(tx, ty, zz, -m, n, 0)] +
+                   s[sidx(tx, ty, zz, -m, -n, 0)]);
+      }
+      v += cm * w;
+    }
+    acc[zz] += v * ia * ib;
+  }
+}
+// mixed (h, z), h = x or y: for each h offset a column, then D1z
+template <typename R, int AXIS>
+__device__ __forceinline__ void t_mix_hz(const R* s, R (&acc)[TZ], int tx, int ty, R ih, R iz) {
+  R tmp[TZ];
+#pragma unroll
+  for (int zz = 0; zz < TZ; ++zz) tmp[zz] = R(0);
+#pragma unroll
+  for (int m = 1; m <= 3; ++m) {
+    const R cm = m == 1 ? W<R>::c1 : (m == 2 ? W<R>::c2 : W<R>::c3);
+    R cp[SZ], cmn[SZ];
+    load_col(s, cp, tx, ty, AXIS == 0 ? m : 0, AXIS == 1 ? m : 0);
+    load_col(s, cmn, tx, ty, AXIS == 0 ? -m : 0, AXIS == 1 ? -m : 0);
+#pragma unroll
+    for (int z = 0; z < SZ; ++z) cp[z] = cm * (cp[z] - cmn[z]);
+    // the mixed stencil is its own transpose: D1h D1z
+#pragma unroll
+    for (int zz = 0; zz < TZ; ++zz)
+      tmp[zz] += W<R>::c1 * (cp[zz + 4] - cp[zz + 2]) + W<R>::c2 * (cp[zz + 5] - cp[zz + 1]) +
+                 W<R>::c3 * (cp[zz + 6] - cp[zz]);
+  }
+#pragma unroll
+  for (int zz = 0; zz < TZ; ++zz) acc[zz] += tmp[zz] * ih * iz;
+}
+
+template <typename R>
+__device__ __forceinline__ void t_value(const R* s, R (&acc)[TZ], int tx, int ty) {
+#pragma unroll
+  for (int zz = 0; zz < TZ; ++zz) acc[zz] += s[sidx(tx, ty, zz, 0, 0, 0)];
+}
+
+// order in which the kernel consumes the coefficient fields
+__constant__ int kOrder[46] = {
+    0, 8, 9, 10, 26, 1, 11, 12, 13, 27, 2, 14, 15, 16, 28, 32, 33, 34,      // A
+    3, 17, 18, 19, 29, 4, 20, 21, 22, 30, 5, 23, 24, 25, 31, 35, 36, 37,    // u
+    6, 38, 39, 40, 44, 7, 41, 42, 43, 45};                                  // ln rho, ln T
+
+template <typename R>
+constexpr size_t smem_bytes() {
+  return 2 * TILE * sizeof(R) + SY * SZ * sizeof(int);
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1) gather_tiled_kernel(GArgs<R> a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  R* sbuf0 = reinterpret_cast<R*>(smem_raw);
+  R* sbuf1 = sbuf0 + TILE;
+  int* rowoff = reinterpret_cast<int*>(sbuf1 + TILE);
+  const Layout& L = a.L;
+  if (halted(a.ss)) return;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int bz = blockIdx.x % a.ntz, bxy = blockIdx.x / a.ntz;
+  const int x0 = (bxy % a.ntx) * TX, y0 = (bxy / a.ntx) * TY, z0 = bz * TZ - NG;
+  const int nx = L.nx, ny = L.ny, nz = L.nz;
+  const long long n3 = (long long)nx * ny * nz;
+  for (int r = ty * TX + tx; r < SY * SZ; r += TX * TY) {
+    const int yy = r % SY, zz = r / SY;
+    const int j = ((y0 - 3 + yy) % ny + ny) % ny, k = z0 - 3 + zz;
+    rowoff[r] = (k >= 0 && k < nz) ? (k * ny + j) * nx : -1;
+  }
+  const int ix0 = ((x0 - 3 + tx) % nx + nx) % nx;
+  const int ix1 = ((x0 - 3 + tx + 32) % nx + nx) % nx;
+  __syncthreads();
+  stage_async<R>(sbuf0, a.coef + (long long)kOrder[0] * n3, rowoff, ix0, ix1);
+  cp_async_commit();
+  int nstep = 0;
+  const Phys<R>& ph = a.ph;
+  const R ix = ph.idx, iy = ph.idy, iz = ph.idz, ix2 = ph.idx2, iy2 = ph.idy2, iz2 = ph.idz2;
+  R acc[NF][TZ];
+#pragma unroll
+  for (int f = 0; f < NF; ++f)
+#pragma unroll
+    for (int zz = 0; zz < TZ; ++zz) acc[f][zz] = R(0);
+  R col[SZ];
+
+  // GSTAGE: wait for the staged field, make it visible, prefetch the next
+  // one into the other buffer (free: every thread has finished with it)
+  const R* s = sbuf0;
+#define GSTAGE(q)                                                                      \
+  cp_async_wait_all();                                                                 \
+  __syncthreads();                                                                     \
+  s = (nstep & 1) ? sbuf1 : sbuf0;                                                     \
+  if (nstep + 1 < 46) {                                                                \
+    stage_async<R>((nstep & 1) ? sbuf0 : sbuf1, a.coef + (long long)kOrder[nstep + 1] * n3, rowoff, ix0, ix1); \
+    cp_async_commit();                                                                 \
+  }                                                                                    \
+  ++nstep;
+
+  // vector fields: A (CV + 0..2, CDA, CLA, CGA) and u (CV + 3..5, CDU, CLU, CGU)
+#pragma unroll
+  for (int grp = 0; grp < 2; ++grp) {
+    const int f0 = grp == 0 ? AX : UX;
+    const int qd = grp == 0 ? CDA : CDU, ql = grp == 0 ? CLA : CLU, qg = grp == 0 ? CGA : CGU;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      GSTAGE(CV + f0 + c);
+      t_value<R>(s, acc[f0 + c], tx, ty);
+      GSTAGE(qd + 3 * c + 0);
+      t_d1_xy<R, 0>(s, acc[f0 + c], tx, ty, ix);
+      GSTAGE(qd + 3 * c + 1);
+      t_d1_xy<R, 1>(s, acc[f0 + c], tx, ty, iy);
+      GSTAGE(qd + 3 * c + 2);
+      load_col(s, col, tx, ty, 0, 0);
+      t_d1_z<R>(col, acc[f0 + c], iz);
+      GSTAGE(ql + c);
+      t_d2_xy<R, 0>(s, acc[f0 + c], tx, ty, ix2);
+      t_d2_xy<R, 1>(s, acc[f0 + c], tx, ty, iy2);
+      load_col(s, col, tx, ty, 0, 0);
+      t_d2_z<R>(col, acc[f0 + c], iz2);
+    }
+    // gd coefficients: D2 along their own axis for component a, mixed for
+    // the two other components
+    GSTAGE(qg + 0);
+    t_d2_xy<R, 0>(s, acc[f0 + 0], tx, ty, ix2);
+    t_mix_xy<R>(s, acc[f0 + 1], tx, ty, ix, iy);
+    t_mix_hz<R, 0>(s, acc[f0 + 2], tx, ty, ix, iz);
+    GSTAGE(qg + 1);
+    t_d2_xy<R, 1>(s, acc[f0 + 1], tx, ty, iy2);
+    t_mix_xy<R>(s, acc[f0 + 0], tx, ty, ix, iy);
+    t_mix_hz<R, 1>(s, acc[f0 + 2], tx, ty, iy, iz);
+    GSTAGE(qg + 2);
+    load_col(s, col, tx, ty, 0, 0);
+    t_d2_z<R>(col, acc[f0 + 2], iz2);
+    t_mix_hz<R, 0>(s, acc[f0 + 0], tx, ty, ix, iz);
+    t_mix_hz<R, 1>(s, acc[f0 + 1], tx, ty, iy, iz);
+  }
+  // scalars: ln rho (CV + 6, CGL, CLL), ln T (CV + 7, CGT, CLT)
+#pragma unroll
+  for (int grp = 0; grp < 2; ++grp) {
+    const int f = grp == 0 ? LR : LT;
+    const int qg = grp == 0 ? CGL : CGT, ql = grp == 0 ? CLL : CLT;
+    GSTAGE(CV + f);
+    t_value<R>(s, acc[f], tx, ty);
+    GSTAGE(qg + 0);
+    t_d1_xy<R, 0>(s, acc[f], tx, ty, ix);
+    GSTAGE(qg + 1);
+    t_d1_xy<R, 1>(s, acc[f], tx, ty, iy);
+    GSTAGE(qg + 2);
+    load_col(s, col, tx, ty, 0, 0);
+    t_d1_z<R>(col, acc[f], iz);
+    GSTAGE(ql);
+    t_d2_xy<R, 0>(s, acc[f], tx, ty, ix2);
+    t_d2_xy<R, 1>(s, acc[f], tx, ty, iy2);
+    load_col(s, col, tx, ty, 0, 0);
+    t_d2_z<R>(col, acc[f], iz2);
+  }
+#undef GSTAGE
+
+  const int i = x0 + tx, j = y0 + ty;
+  if (i >= nx || j >= ny) return;
+  const R dt = R(a.ss->dt);
+#pragma unroll
+  for (int zz = 0; zz < TZ; ++zz) {
+    const int k = z0 + zz;
+    if (k >= nz + NG) break;
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+      const long long q = L.at(f, k, j, i);
+      R v = acc[f][zz];
+      if (ph.bcz == 0 && k < 0 && (f == UX || f == UY)) v -= ph.tau_u * dt * a.dbar[q];
+      a.gbar[q] = v;
+    }
+  }
+}
+
+}  // namespace gtile
+
+template <typename R>
+void launch_adj_gather_tiled(const Layout& L, const Phys<R>& ph, const R* coef, const R* dbar, R* gbar,
+                             const StepState* ss, cudaStream_t st) {
+  if ((long long)L.nx * L.ny * L.nz >= (1LL << 31)) {  // row offsets are 32-bit
+    launch_adj_gather<R>(L, ph, coef, dbar, gbar, ss, st);
+    return;
+  }
+  gtile::GArgs<R> a;
+  a.L = L; a.ph = ph; a.coef = coef; a.dbar = dbar; a.gbar = gbar; a.ss = ss;
+  a.ntx = (L.nx + gtile::TX - 1) / gtile::TX;
+  a.nty = (L.ny + gtile::TY - 1) / gtile::TY;
+  a.ntz = (L.nz + 2 * NG + gtile::TZ - 1) / gtile::TZ;
+  const int nblk = a.ntx * a.nty * a.ntz;
+  const size_t smem = gtile::smem_bytes<R>();
+  cudaFuncSetAttribute(gtile::gather_tiled_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  gtile::gather_tiled_kernel<R><<<nblk, dim3(gtile::TX, gtile::TY), smem, st>>>(a);
+}
+
+template void launch_adj_gather_tiled<float>(const Layout&, const Phys<float>&, const float*, const float*, float*,
+                                             const StepState*, cudaStream_t);
+template void launch_adj_gather_tiled<double>(const Layout&, const Phys<double>&, const double*, const double*,
+                                              double*, const StepState*, cudaStream_t);
+
+}  // namespace mhd

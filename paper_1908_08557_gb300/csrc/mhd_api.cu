@@ -17,6 +17,7 @@ using namespace mhd;
 struct mhd_ctx {
   CUtensorMap tm[2];   // TMA descriptors of the two FP32 state sets (64-byte aligned)
   bool tiled;          // FP32: TMA-fed z-march kernel; otherwise the simple kernel
+  bool adj_tiled;  // tiled transposed-stencil gather (else one thread per point)
   mhd_params p;
   Layout L;
   cudaStream_t st;
@@ -515,6 +516,8 @@ extern "C" int mhd_create(const mhd_params* p, void* workspace, size_t ws_bytes,
   {
     const char* v = getenv("MHD_RK_VARIANT");
     h->tiled = p->precision == 32 && !(v && strcmp(v, "simple") == 0);
+    const char* va = getenv("MHD_ADJ_VARIANT");
+    h->adj_tiled = !(va && strcmp(va, "simple") == 0);
   }
   h->t0 = 0.0;
   h->t1 = 0.0;
@@ -892,7 +895,10 @@ static void adjoint_step_impl(mhd_ctx* h) {
                        h->st);
     launch_adj_point<R>(h->L, ph, bg, S[s], (const R*)h->dbar, (R*)h->coef, h->thbar, (const R*)h->wtab,
                         (const R*)h->wptab, h->ss, s, h->st);
-    launch_adj_gather<R>(h->L, ph, (const R*)h->coef, (const R*)h->dbar, (R*)h->gbar, h->ss, h->st);
+    if (h->adj_tiled)
+      launch_adj_gather_tiled<R>(h->L, ph, (const R*)h->coef, (const R*)h->dbar, (R*)h->gbar, h->ss, h->st);
+    else
+      launch_adj_gather<R>(h->L, ph, (const R*)h->coef, (const R*)h->dbar, (R*)h->gbar, h->ss, h->st);
     launch_adj_bc<R>(h->L, ph, bg, S[s], (R*)h->gbar, (R)h->p.dz, h->ss, h->st);
     launch_pfe_adjoint<R>(fpa, h->L, (R*)h->gbar, h->ss, h->st);
     launch_adj_axpy<R>(h->L, h->p.bc_z, (R*)h->fbar, (R*)h->dbar, (const R*)h->gbar, 0.0, rk_alpha(s), 1, h->ss,

@@ -59,6 +59,8 @@ template <typename R> void launch_adj_point(const Layout& L, const Phys<R>& ph, 
                                             const StepState* ss, int sub, cudaStream_t st);
 template <typename R> void launch_adj_gather(const Layout& L, const Phys<R>& ph, const R* coef, const R* dbar,
                                              R* gbar, const StepState* ss, cudaStream_t st);
+template <typename R> void launch_adj_gather_tiled(const Layout& L, const Phys<R>& ph, const R* coef,
+                                                   const R* dbar, R* gbar, const StepState* ss, cudaStream_t st);
 template <typename R> void launch_adj_bc(const Layout& L, const Phys<R>& ph, const Background<R>& bg, const R* g,
                                          R* gbar, R dz, const StepState* ss, cudaStream_t st);
 template <typename R> void launch_adj_axpy(const Layout& L, int bcz, R* fbar, R* dbar, const R* gbar, double beta,

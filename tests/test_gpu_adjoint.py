@@ -184,3 +184,43 @@ def test_bruteforce_oracle_gradient_8cube():
             fd[idx] = (oracle_loss(args_p["bz"], args_p["v0"], args_p["v1"]) -
                        oracle_loss(args_m["bz"], args_m["v0"], args_m["v1"])) / (2 * eps)
         assert np.abs(fd - g).max() <= 1e-6 * scale, (name, np.abs(fd - g).max(), scale)
+
+
+def _adjoint_with_variant(case, prec, variant, lam):
+    import os
+    old = os.environ.get("MHD_ADJ_VARIANT")
+    os.environ["MHD_ADJ_VARIANT"] = variant
+    try:
+        sim = _sim(case, prec)
+    finally:
+        if old is None:
+            del os.environ["MHD_ADJ_VARIANT"]
+        else:
+            os.environ["MHD_ADJ_VARIANT"] = old
+    sim.set_driver(_T(case.bz, prec), _T(case.v0, prec), _T(case.v1, prec), case.t0, case.t1)
+    sim.set_time(0.3)
+    ck = sim.new_checkpoint()
+    t = sim.save(ck)
+    sim.adjoint_init(_T(lam, prec))
+    sim.restore(ck, t)
+    sim.adjoint_step()
+    g = sim.adjoint_read()
+    out = {k: v.double().cpu().numpy() for k, v in g.items()}
+    sim.close()
+    return out
+
+
+@pytest.mark.parametrize("shape,prec", [((16, 8, 13), 64), ((64, 32, 21), 64), ((64, 32, 21), 32)])
+def test_tiled_gather_matches_simple(shape, prec):
+    """The shared-memory tiled transposed-stencil gather against the one
+    thread per point gather: tiles ragged in x (16 < 32) and z (13 + 6 and
+    21 + 6 output layers are not multiples of 8), several tiles in x and y."""
+    nx, ny, nz = shape
+    case = _case(nx, ny, nz, seed=12)
+    lam = np.random.default_rng(13).standard_normal((8, nz, ny, nx))
+    a = _adjoint_with_variant(case, prec, "tiled", lam)
+    b = _adjoint_with_variant(case, prec, "simple", lam)
+    tol = 1e-12 if prec == 64 else 1e-5
+    for name in ("lam", "bz", "v0", "v1"):
+        s = np.abs(b[name]).max()
+        assert np.abs(a[name] - b[name]).max() <= tol * max(s, 1e-30), name
