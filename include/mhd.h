@@ -66,7 +66,8 @@ typedef struct mhd_params {
   int precision;       /* 32 or 64: state storage and stencil arithmetic */
   int bc_z;            /* 0: the paper's boundaries; 1: periodic in z (tests) */
   int stats_every;     /* compute diagnostics every n steps (0: never) */
-  int adjoint;         /* 1: also reserve the buffers of mhd_adjoint_step */
+  int adjoint;         /* 1: also reserve the buffers of mhd_adjoint_step (needs
+                          8 (nz + 6) ny nx / 4 < 2^31) */
   double dx, dy, dz;
   double gamma;        /* ratio of specific heats */
   double gz;           /* gravity, signed (< 0 points down) */

@@ -444,37 +444,71 @@ __global__ void adj_bc_kernel(Layout L, Phys<R> ph, Background<R> bg, const R* _
   }
 }
 
-// elementwise updates over the cells that carry state (interior, and the
-// u_x, u_y ghost layers below the photosphere)
+// Elementwise adjoint updates over the cells that carry state (interior, and
+// the u_x, u_y ghost layers below the photosphere), 16 bytes per thread and
+// row-contiguous (nx is a multiple of 4):
+//   mode 0, start of a step:  D = beta F   (D is zero between steps: alpha_0 = 0)
+//   mode 1, end of substep s: F += G;  D = alpha_s D + beta_{s-1} F  (beta = 0 for s = 0)
 template <typename R>
-__global__ void adj_axpy_kernel(Layout L, int bcz, R* __restrict__ fbar, R* __restrict__ dbar,
-                                const R* __restrict__ gbar, R beta, R alpha, int phase, const StepState* ss) {
-  const long long n2 = (long long)L.nx * L.ny;
-  const long long ncell = (long long)NF * L.nz * n2 + (bcz == 0 ? 2LL * NG * n2 : 0);
+struct Vec16;
+template <>
+struct Vec16<float> {
+  using T = float4;
+  static constexpr int N = 4;
+};
+template <>
+struct Vec16<double> {
+  using T = double2;
+  static constexpr int N = 2;
+};
+template <typename V, typename R>
+__device__ __forceinline__ R& vat(V& v, int e) {
+  return reinterpret_cast<R*>(&v)[e];
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256) adj_update_kernel(Layout L, R* __restrict__ fbar, R* __restrict__ dbar,
+                                                         const R* __restrict__ gbar, R alpha, R beta, int mode,
+                                                         const StepState* ss) {
+  using V = typename Vec16<R>::T;
+  constexpr int E = Vec16<R>::N;
   if (halted(ss)) return;
-  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < ncell;
-       q += (long long)gridDim.x * blockDim.x) {
-    int fl, k;
-    long long r;
-    if (q < (long long)NF * L.nz * n2) {
-      fl = (int)(q / (L.nz * n2));
-      r = q - (long long)fl * L.nz * n2;
-      k = (int)(r / n2);
+  const unsigned ny = L.ny, vpr = L.nx / E, nyz = (unsigned)L.nz * ny, ngy = NG * ny;
+  const unsigned nrow_int = NF * nyz;
+  const unsigned nvec = (nrow_int + 2 * ngy) * vpr;
+  for (unsigned q = blockIdx.x * blockDim.x + threadIdx.x; q < nvec; q += gridDim.x * blockDim.x) {
+    const unsigned row = q / vpr, v = q - row * vpr;
+    int f, k, j;
+    if (row < nrow_int) {
+      f = row / nyz;
+      const unsigned r = row - f * nyz;
+      k = r / ny;
+      j = r - k * ny;
     } else {
-      const long long q3 = q - (long long)NF * L.nz * n2;
-      fl = UX + (int)(q3 / (NG * n2));
-      r = q3 - (long long)(fl - UX) * NG * n2;
-      k = -1 - (int)(r / n2);
+      unsigned r = row - nrow_int;
+      const unsigned g = r / ngy;
+      f = UX + (int)g;
+      r -= g * ngy;
+      k = -1 - (int)(r / ny);
+      j = r % ny;
     }
-    const long long rem = r % n2;
-    const int j = (int)(rem / L.nx), i = (int)(rem - (long long)j * L.nx);
-    const long long p = L.at(fl, k, j, i);
-    if (phase == 0) {
-      dbar[p] += beta * fbar[p];
+    const long long p = L.at(f, k, j, (int)(v * E));
+    V fv = *reinterpret_cast<const V*>(fbar + p);
+    V dv;
+    if (mode == 0) {
+#pragma unroll
+      for (int e = 0; e < E; ++e) vat<V, R>(dv, e) = beta * vat<V, R>(fv, e);
     } else {
-      fbar[p] += gbar[p];
-      dbar[p] *= alpha;
+      const V gv = *reinterpret_cast<const V*>(gbar + p);
+      dv = *reinterpret_cast<const V*>(dbar + p);
+#pragma unroll
+      for (int e = 0; e < E; ++e) {
+        vat<V, R>(fv, e) += vat<V, R>(const_cast<V&>(gv), e);
+        vat<V, R>(dv, e) = alpha * vat<V, R>(dv, e) + beta * vat<V, R>(fv, e);
+      }
+      *reinterpret_cast<V*>(fbar + p) = fv;
     }
+    *reinterpret_cast<V*>(dbar + p) = dv;
   }
 }
 
@@ -595,9 +629,9 @@ void launch_adj_bc(const Layout& L, const Phys<R>& ph, const Background<R>& bg, 
 }
 
 template <typename R>
-void launch_adj_axpy(const Layout& L, int bcz, R* fbar, R* dbar, const R* gbar, double beta, double alpha, int phase,
-                     const StepState* ss, cudaStream_t st) {
-  adj_axpy_kernel<R><<<1216, 256, 0, st>>>(L, bcz, fbar, dbar, gbar, (R)beta, (R)alpha, phase, ss);
+void launch_adj_update(const Layout& L, R* fbar, R* dbar, const R* gbar, double alpha, double beta, int mode,
+                       const StepState* ss, cudaStream_t st) {
+  adj_update_kernel<R><<<152 * 8, 256, 0, st>>>(L, fbar, dbar, gbar, (R)alpha, (R)beta, mode, ss);
 }
 
 template <typename R>
@@ -615,8 +649,8 @@ void launch_bz_plane(int nx, int ny, int nz, int k, double dx, double dy, const 
                                      cudaStream_t);                                                               \
   template void launch_adj_bc<R>(const Layout&, const Phys<R>&, const Background<R>&, const R*, R*, R,             \
                                  const StepState*, cudaStream_t);                                                 \
-  template void launch_adj_axpy<R>(const Layout&, int, R*, R*, const R*, double, double, int, const StepState*,     \
-                                   cudaStream_t);                                                                 \
+  template void launch_adj_update<R>(const Layout&, R*, R*, const R*, double, double, int, const StepState*,        \
+                                     cudaStream_t);                                                               \
   template void launch_bz_plane<R>(int, int, int, int, double, double, const R*, R*, int, const R*, R*,             \
                                    cudaStream_t);                                                                 \
   template void launch_adj_pack<R>(const Layout&, int, const R*, R*, cudaStream_t);                                \
@@ -640,13 +674,13 @@ namespace mhd {
 namespace gtile {
 
 constexpr int TX = 32, TY = 8, TZ = 8;
-constexpr int SX = TX + 6, SY = TY + 6, SZ = TZ + 6;
+// tile rows start 4 columns left of the block (16-byte aligned chunks);
+// the block's own columns sit at XO .. XO + 31
+constexpr int XO = 4;
+constexpr int SX = TX + 8, SY = TY + 6, SZ = TZ + 6;
 constexpr int TILE = SX * SY * SZ;
-
-template <typename R>
-struct Acc {
-  R v[8][TZ];
-};
+constexpr int NBUF = 3;  // staged fields in flight: current + two prefetched
+constexpr int NSTAGE = NCOEF;
 
 template <typename R>
 struct GArgs {
@@ -659,43 +693,64 @@ struct GArgs {
   int ntx, nty, ntz;
 };
 
-// asynchronous 4- or 8-byte copy global -> shared; src_bytes = 0 zero-fills
-__device__ __forceinline__ void cp_async_elem(void* dst, const void* src, int bytes, int src_bytes) {
+// asynchronous 16-byte copy global -> shared; src_bytes = 0 zero-fills
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, int src_bytes) {
   const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-  if (bytes == 4)
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(src), "r"(src_bytes) : "memory");
-  else
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(src), "r"(src_bytes) : "memory");
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src), "r"(src_bytes) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
-// Stage coefficient field `base` (one [nz][ny][nx] field) for the block:
-// warp w copies tile rows w, w + 8, ...; rowoff[r] is the offset of tile row
-// r in the field (-1 outside the interior layers: zero fill); ix0, ix1 are
-// the thread's two wrapped x indices (lane and lane + 32).
+// 16-byte chunks per tile: chunk c covers tile elements c*EPC .. c*EPC+EPC-1
 template <typename R>
-__device__ __forceinline__ void stage_async(R* __restrict__ s, const R* __restrict__ base, const int* rowoff, int ix0,
-                                            int ix1) {
-  const int lane = threadIdx.x;
-  for (int r = threadIdx.y; r < SY * SZ; r += TY) {
-    const int ro = rowoff[r];
-    const R* src = base + (ro < 0 ? 0 : ro);
-    const int nb = ro < 0 ? 0 : (int)sizeof(R);
-    cp_async_elem(s + r * SX + lane, src + ix0, (int)sizeof(R), nb);
-    if (lane < SX - 32) cp_async_elem(s + r * SX + lane + 32, src + ix1, (int)sizeof(R), nb);
+__host__ __device__ constexpr int n_chunks() { return TILE * (int)sizeof(R) / 16; }
+
+template <typename R>
+__host__ __device__ constexpr size_t smem_bytes() {
+  return NBUF * TILE * sizeof(R) + n_chunks<R>() * sizeof(int);
+}
+
+// Stage one coefficient field (base: its [nz][ny][nx] array) into s; chunk
+// c comes from base + choff[c] (-1: outside the interior layers, zero fill).
+template <typename R>
+__device__ __forceinline__ void stage_async(R* __restrict__ s, const R* __restrict__ base, const int* choff) {
+  constexpr int EPC = 16 / (int)sizeof(R);
+  for (int c = threadIdx.y * TX + threadIdx.x; c < n_chunks<R>(); c += TX * TY) {
+    const int o = choff[c];
+    cp_async16(s + c * EPC, base + (o < 0 ? 0 : o), o < 0 ? 0 : 16);
   }
 }
 
+// Stage kinds: what the transposed operator of a coefficient field is, and
+// which adjoint field(s) it feeds.  Gradient-of-divergence coefficients
+// (gd_a = sum_c D1_a D1_c X_c, D1_a D1_a -> D2_a) feed all three components
+// of their vector field.
+enum { K_VAL = 0, K_D1X, K_D1Y, K_D1Z, K_LAP, K_GDX, K_GDY, K_GDZ };
+#define GS(q, kind, f) ((q) | ((kind) << 8) | ((f) << 12))
+__constant__ int kStage[NSTAGE] = {
+    GS(CV + AX, K_VAL, AX), GS(CDA + 0, K_D1X, AX), GS(CDA + 1, K_D1Y, AX), GS(CDA + 2, K_D1Z, AX), GS(CLA + 0, K_LAP, AX),
+    GS(CV + AY, K_VAL, AY), GS(CDA + 3, K_D1X, AY), GS(CDA + 4, K_D1Y, AY), GS(CDA + 5, K_D1Z, AY), GS(CLA + 1, K_LAP, AY),
+    GS(CV + AZ, K_VAL, AZ), GS(CDA + 6, K_D1X, AZ), GS(CDA + 7, K_D1Y, AZ), GS(CDA + 8, K_D1Z, AZ), GS(CLA + 2, K_LAP, AZ),
+    GS(CGA + 0, K_GDX, AX), GS(CGA + 1, K_GDY, AX), GS(CGA + 2, K_GDZ, AX),
+    GS(CV + UX, K_VAL, UX), GS(CDU + 0, K_D1X, UX), GS(CDU + 1, K_D1Y, UX), GS(CDU + 2, K_D1Z, UX), GS(CLU + 0, K_LAP, UX),
+    GS(CV + UY, K_VAL, UY), GS(CDU + 3, K_D1X, UY), GS(CDU + 4, K_D1Y, UY), GS(CDU + 5, K_D1Z, UY), GS(CLU + 1, K_LAP, UY),
+    GS(CV + UZ, K_VAL, UZ), GS(CDU + 6, K_D1X, UZ), GS(CDU + 7, K_D1Y, UZ), GS(CDU + 8, K_D1Z, UZ), GS(CLU + 2, K_LAP, UZ),
+    GS(CGU + 0, K_GDX, UX), GS(CGU + 1, K_GDY, UX), GS(CGU + 2, K_GDZ, UX),
+    GS(CV + LR, K_VAL, LR), GS(CGL + 0, K_D1X, LR), GS(CGL + 1, K_D1Y, LR), GS(CGL + 2, K_D1Z, LR), GS(CLL, K_LAP, LR),
+    GS(CV + LT, K_VAL, LT), GS(CGT + 0, K_D1X, LT), GS(CGT + 1, K_D1Y, LT), GS(CGT + 2, K_D1Z, LT), GS(CLT, K_LAP, LT)};
+#undef GS
+
 // index of staged point (x offset dx, y offset dy, z point zz + dz) of the
-// thread's column; the thread's own point sits at (tx + 3, ty + 3, zz + 3)
+// thread's column
 __device__ __forceinline__ int sidx(int tx, int ty, int zz, int dx, int dy, int dz) {
-  return ((zz + 3 + dz) * SY + (ty + 3 + dy)) * SX + (tx + 3 + dx);
+  return ((zz + 3 + dz) * SY + (ty + 3 + dy)) * SX + (tx + XO + dx);
 }
 
-// D1^T along x or y (AX = 0 / 1) into acc[zz]
+// Transposed 1D stencils along x or y (AXIS 0 / 1) at the TZ points of the
+// thread's column: D1^T = -D1, D2^T = D2
 template <typename R, int AXIS>
-__device__ __forceinline__ void t_d1_xy(const R* s, R (&acc)[TZ], int tx, int ty, R inv) {
+__device__ __forceinline__ void t_d1_xy(const R* s, R (&r)[TZ], int tx, int ty, R inv) {
 #pragma unroll
   for (int zz = 0; zz < TZ; ++zz) {
     R v = R(0);
@@ -705,11 +760,11 @@ __device__ __forceinline__ void t_d1_xy(const R* s, R (&acc)[TZ], int tx, int ty
       const int dx = AXIS == 0 ? m : 0, dy = AXIS == 1 ? m : 0;
       v += cm * (s[sidx(tx, ty, zz, -dx, -dy, 0)] - s[sidx(tx, ty, zz, dx, dy, 0)]);
     }
-    acc[zz] += v * inv;
+    r[zz] += v * inv;
   }
 }
 template <typename R, int AXIS>
-__device__ __forceinline__ void t_d2_xy(const R* s, R (&acc)[TZ], int tx, int ty, R inv2) {
+__device__ __forceinline__ void t_d2_xy(const R* s, R (&r)[TZ], int tx, int ty, R inv2) {
 #pragma unroll
   for (int zz = 0; zz < TZ; ++zz) {
     R v = W<R>::e0 * s[sidx(tx, ty, zz, 0, 0, 0)];
@@ -719,36 +774,32 @@ __device__ __forceinline__ void t_d2_xy(const R* s, R (&acc)[TZ], int tx, int ty
       const int dx = AXIS == 0 ? m : 0, dy = AXIS == 1 ? m : 0;
       v += em * (s[sidx(tx, ty, zz, -dx, -dy, 0)] + s[sidx(tx, ty, zz, dx, dy, 0)]);
     }
-    acc[zz] += v * inv2;
+    r[zz] += v * inv2;
   }
 }
-// z stencils from a column col[0..13] (z points -3 .. TZ+2)
-template <typename R>
-__device__ __forceinline__ void t_d1_z(const R (&col)[SZ], R (&acc)[TZ], R inv) {
-#pragma unroll
-  for (int zz = 0; zz < TZ; ++zz) {
-    const R v = W<R>::c1 * (col[zz + 2] - col[zz + 4]) + W<R>::c2 * (col[zz + 1] - col[zz + 5]) +
-                W<R>::c3 * (col[zz] - col[zz + 6]);
-    acc[zz] += v * inv;
-  }
-}
-template <typename R>
-__device__ __forceinline__ void t_d2_z(const R (&col)[SZ], R (&acc)[TZ], R inv2) {
-#pragma unroll
-  for (int zz = 0; zz < TZ; ++zz) {
-    const R v = W<R>::e0 * col[zz + 3] + W<R>::e1 * (col[zz + 2] + col[zz + 4]) +
-                W<R>::e2 * (col[zz + 1] + col[zz + 5]) + W<R>::e3 * (col[zz] + col[zz + 6]);
-    acc[zz] += v * inv2;
-  }
-}
+// the thread's column (z points -3 .. TZ+2) at x, y offsets dx, dy
 template <typename R>
 __device__ __forceinline__ void load_col(const R* s, R (&col)[SZ], int tx, int ty, int dx, int dy) {
 #pragma unroll
-  for (int z = 0; z < SZ; ++z) col[z] = s[(z * SY + ty + 3 + dy) * SX + tx + 3 + dx];
+  for (int z = 0; z < SZ; ++z) col[z] = s[(z * SY + ty + 3 + dy) * SX + tx + XO + dx];
 }
-// mixed (x, y): D1x D1y applied to the staged field
 template <typename R>
-__device__ __forceinline__ void t_mix_xy(const R* s, R (&acc)[TZ], int tx, int ty, R ia, R ib) {
+__device__ __forceinline__ void t_d1_z(const R (&col)[SZ], R (&r)[TZ], R inv) {
+#pragma unroll
+  for (int zz = 0; zz < TZ; ++zz)
+    r[zz] += inv * (W<R>::c1 * (col[zz + 2] - col[zz + 4]) + W<R>::c2 * (col[zz + 1] - col[zz + 5]) +
+                    W<R>::c3 * (col[zz] - col[zz + 6]));
+}
+template <typename R>
+__device__ __forceinline__ void t_d2_z(const R (&col)[SZ], R (&r)[TZ], R inv2) {
+#pragma unroll
+  for (int zz = 0; zz < TZ; ++zz)
+    r[zz] += inv2 * (W<R>::e0 * col[zz + 3] + W<R>::e1 * (col[zz + 2] + col[zz + 4]) +
+                     W<R>::e2 * (col[zz + 1] + col[zz + 5]) + W<R>::e3 * (col[zz] + col[zz + 6]));
+}
+// mixed D1x D1y (its own transpose)
+template <typename R>
+__device__ __forceinline__ void t_mix_xy(const R* s, R (&r)[TZ], int tx, int ty, R iab) {
 #pragma unroll
   for (int zz = 0; zz < TZ; ++zz) {
     R v = R(0);
@@ -764,56 +815,48 @@ __device__ __forceinline__ void t_mix_xy(const R* s, R (&acc)[TZ], int tx, int t
       }
       v += cm * w;
     }
-    acc[zz] += v * ia * ib;
+    r[zz] += v * iab;
   }
 }
-// mixed (h, z), h = x or y: for each h offset a column, then D1z
+// mixed D1h D1z, h = x or y: D1h of the staged columns, then D1z
 template <typename R, int AXIS>
-__device__ __forceinline__ void t_mix_hz(const R* s, R (&acc)[TZ], int tx, int ty, R ih, R iz) {
-  R tmp[TZ];
+__device__ __forceinline__ void t_mix_hz(const R* s, R (&r)[TZ], int tx, int ty, R ihz) {
+  R h[SZ];
 #pragma unroll
-  for (int zz = 0; zz < TZ; ++zz) tmp[zz] = R(0);
+  for (int z = 0; z < SZ; ++z) h[z] = R(0);
 #pragma unroll
   for (int m = 1; m <= 3; ++m) {
     const R cm = m == 1 ? W<R>::c1 : (m == 2 ? W<R>::c2 : W<R>::c3);
-    R cp[SZ], cmn[SZ];
-    load_col(s, cp, tx, ty, AXIS == 0 ? m : 0, AXIS == 1 ? m : 0);
-    load_col(s, cmn, tx, ty, AXIS == 0 ? -m : 0, AXIS == 1 ? -m : 0);
+    const int dx = AXIS == 0 ? m : 0, dy = AXIS == 1 ? m : 0;
 #pragma unroll
-    for (int z = 0; z < SZ; ++z) cp[z] = cm * (cp[z] - cmn[z]);
-    // the mixed stencil is its own transpose: D1h D1z
-#pragma unroll
-    for (int zz = 0; zz < TZ; ++zz)
-      tmp[zz] += W<R>::c1 * (cp[zz + 4] - cp[zz + 2]) + W<R>::c2 * (cp[zz + 5] - cp[zz + 1]) +
-                 W<R>::c3 * (cp[zz + 6] - cp[zz]);
+    for (int z = 0; z < SZ; ++z)
+      h[z] += cm * (s[(z * SY + ty + 3 + dy) * SX + tx + XO + dx] - s[(z * SY + ty + 3 - dy) * SX + tx + XO - dx]);
   }
 #pragma unroll
-  for (int zz = 0; zz < TZ; ++zz) acc[zz] += tmp[zz] * ih * iz;
+  for (int zz = 0; zz < TZ; ++zz)
+    r[zz] += ihz * (W<R>::c1 * (h[zz + 4] - h[zz + 2]) + W<R>::c2 * (h[zz + 5] - h[zz + 1]) +
+                    W<R>::c3 * (h[zz + 6] - h[zz]));
 }
 
+// acc[f] += r with a runtime field index (each case indexes registers)
 template <typename R>
-__device__ __forceinline__ void t_value(const R* s, R (&acc)[TZ], int tx, int ty) {
-#pragma unroll
-  for (int zz = 0; zz < TZ; ++zz) acc[zz] += s[sidx(tx, ty, zz, 0, 0, 0)];
-}
-
-// order in which the kernel consumes the coefficient fields
-__constant__ int kOrder[46] = {
-    0, 8, 9, 10, 26, 1, 11, 12, 13, 27, 2, 14, 15, 16, 28, 32, 33, 34,      // A
-    3, 17, 18, 19, 29, 4, 20, 21, 22, 30, 5, 23, 24, 25, 31, 35, 36, 37,    // u
-    6, 38, 39, 40, 44, 7, 41, 42, 43, 45};                                  // ln rho, ln T
-
-template <typename R>
-constexpr size_t smem_bytes() {
-  return 2 * TILE * sizeof(R) + SY * SZ * sizeof(int);
+__device__ __forceinline__ void add_to(R (&acc)[NF][TZ], int f, const R (&r)[TZ]) {
+  switch (f) {
+#define ADDF(F)                                            \
+  case F:                                                  \
+    _Pragma("unroll") for (int zz = 0; zz < TZ; ++zz) acc[F][zz] += r[zz]; \
+    break;
+    ADDF(0) ADDF(1) ADDF(2) ADDF(3) ADDF(4) ADDF(5) ADDF(6) ADDF(7)
+#undef ADDF
+    default: break;
+  }
 }
 
 template <typename R>
 __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1) gather_tiled_kernel(GArgs<R> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  R* sbuf0 = reinterpret_cast<R*>(smem_raw);
-  R* sbuf1 = sbuf0 + TILE;
-  int* rowoff = reinterpret_cast<int*>(sbuf1 + TILE);
+  R* sb = reinterpret_cast<R*>(smem_raw);
+  int* choff = reinterpret_cast<int*>(sb + NBUF * TILE);
   const Layout& L = a.L;
   if (halted(a.ss)) return;
   const int tx = threadIdx.x, ty = threadIdx.y;
@@ -821,98 +864,105 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1) gather_tiled_kern
   const int x0 = (bxy % a.ntx) * TX, y0 = (bxy / a.ntx) * TY, z0 = bz * TZ - NG;
   const int nx = L.nx, ny = L.ny, nz = L.nz;
   const long long n3 = (long long)nx * ny * nz;
-  for (int r = ty * TX + tx; r < SY * SZ; r += TX * TY) {
-    const int yy = r % SY, zz = r / SY;
-    const int j = ((y0 - 3 + yy) % ny + ny) % ny, k = z0 - 3 + zz;
-    rowoff[r] = (k >= 0 && k < nz) ? (k * ny + j) * nx : -1;
+  {
+    constexpr int EPC = 16 / (int)sizeof(R), CH = SX / EPC;
+    for (int c = ty * TX + tx; c < n_chunks<R>(); c += TX * TY) {
+      const int r = c / CH, ch = c - r * CH;
+      const int yy = r % SY, zz = r / SY;
+      const int j = ((y0 - 3 + yy) % ny + ny) % ny, k = z0 - 3 + zz;
+      const int i = ((x0 - XO + ch * EPC) % nx + nx) % nx;
+      choff[c] = (k >= 0 && k < nz) ? (k * ny + j) * nx + i : -1;
+    }
   }
-  const int ix0 = ((x0 - 3 + tx) % nx + nx) % nx;
-  const int ix1 = ((x0 - 3 + tx + 32) % nx + nx) % nx;
   __syncthreads();
-  stage_async<R>(sbuf0, a.coef + (long long)kOrder[0] * n3, rowoff, ix0, ix1);
+  stage_async<R>(sb, a.coef + (long long)(kStage[0] & 255) * n3, choff);
   cp_async_commit();
-  int nstep = 0;
+  stage_async<R>(sb + TILE, a.coef + (long long)(kStage[1] & 255) * n3, choff);
+  cp_async_commit();
   const Phys<R>& ph = a.ph;
-  const R ix = ph.idx, iy = ph.idy, iz = ph.idz, ix2 = ph.idx2, iy2 = ph.idy2, iz2 = ph.idz2;
   R acc[NF][TZ];
 #pragma unroll
   for (int f = 0; f < NF; ++f)
 #pragma unroll
     for (int zz = 0; zz < TZ; ++zz) acc[f][zz] = R(0);
-  R col[SZ];
 
-  // GSTAGE: wait for the staged field, make it visible, prefetch the next
-  // one into the other buffer (free: every thread has finished with it)
-  const R* s = sbuf0;
-#define GSTAGE(q)                                                                      \
-  cp_async_wait_all();                                                                 \
-  __syncthreads();                                                                     \
-  s = (nstep & 1) ? sbuf1 : sbuf0;                                                     \
-  if (nstep + 1 < 46) {                                                                \
-    stage_async<R>((nstep & 1) ? sbuf0 : sbuf1, a.coef + (long long)kOrder[nstep + 1] * n3, rowoff, ix0, ix1); \
-    cp_async_commit();                                                                 \
-  }                                                                                    \
-  ++nstep;
-
-  // vector fields: A (CV + 0..2, CDA, CLA, CGA) and u (CV + 3..5, CDU, CLU, CGU)
-#pragma unroll
-  for (int grp = 0; grp < 2; ++grp) {
-    const int f0 = grp == 0 ? AX : UX;
-    const int qd = grp == 0 ? CDA : CDU, ql = grp == 0 ? CLA : CLU, qg = grp == 0 ? CGA : CGU;
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      GSTAGE(CV + f0 + c);
-      t_value<R>(s, acc[f0 + c], tx, ty);
-      GSTAGE(qd + 3 * c + 0);
-      t_d1_xy<R, 0>(s, acc[f0 + c], tx, ty, ix);
-      GSTAGE(qd + 3 * c + 1);
-      t_d1_xy<R, 1>(s, acc[f0 + c], tx, ty, iy);
-      GSTAGE(qd + 3 * c + 2);
-      load_col(s, col, tx, ty, 0, 0);
-      t_d1_z<R>(col, acc[f0 + c], iz);
-      GSTAGE(ql + c);
-      t_d2_xy<R, 0>(s, acc[f0 + c], tx, ty, ix2);
-      t_d2_xy<R, 1>(s, acc[f0 + c], tx, ty, iy2);
-      load_col(s, col, tx, ty, 0, 0);
-      t_d2_z<R>(col, acc[f0 + c], iz2);
+#pragma unroll 1
+  for (int st = 0; st < NSTAGE; ++st) {
+    // wait for this stage's field (the one prefetched after it may still be
+    // in flight), make it visible, then prefetch two stages ahead into the
+    // buffer every thread finished with in the previous stage
+    if (st + 1 < NSTAGE) cp_async_wait<1>(); else cp_async_wait<0>();
+    __syncthreads();
+    const R* s = sb + (st % NBUF) * TILE;
+    if (st + 2 < NSTAGE) {
+      stage_async<R>(sb + ((st + 2) % NBUF) * TILE, a.coef + (long long)(kStage[st + 2] & 255) * n3, choff);
+      cp_async_commit();
     }
-    // gd coefficients: D2 along their own axis for component a, mixed for
-    // the two other components
-    GSTAGE(qg + 0);
-    t_d2_xy<R, 0>(s, acc[f0 + 0], tx, ty, ix2);
-    t_mix_xy<R>(s, acc[f0 + 1], tx, ty, ix, iy);
-    t_mix_hz<R, 0>(s, acc[f0 + 2], tx, ty, ix, iz);
-    GSTAGE(qg + 1);
-    t_d2_xy<R, 1>(s, acc[f0 + 1], tx, ty, iy2);
-    t_mix_xy<R>(s, acc[f0 + 0], tx, ty, ix, iy);
-    t_mix_hz<R, 1>(s, acc[f0 + 2], tx, ty, iy, iz);
-    GSTAGE(qg + 2);
-    load_col(s, col, tx, ty, 0, 0);
-    t_d2_z<R>(col, acc[f0 + 2], iz2);
-    t_mix_hz<R, 0>(s, acc[f0 + 0], tx, ty, ix, iz);
-    t_mix_hz<R, 1>(s, acc[f0 + 1], tx, ty, iy, iz);
-  }
-  // scalars: ln rho (CV + 6, CGL, CLL), ln T (CV + 7, CGT, CLT)
+    const int code = kStage[st];
+    const int kind = (code >> 8) & 15, f = code >> 12;
+    R r0[TZ];
 #pragma unroll
-  for (int grp = 0; grp < 2; ++grp) {
-    const int f = grp == 0 ? LR : LT;
-    const int qg = grp == 0 ? CGL : CGT, ql = grp == 0 ? CLL : CLT;
-    GSTAGE(CV + f);
-    t_value<R>(s, acc[f], tx, ty);
-    GSTAGE(qg + 0);
-    t_d1_xy<R, 0>(s, acc[f], tx, ty, ix);
-    GSTAGE(qg + 1);
-    t_d1_xy<R, 1>(s, acc[f], tx, ty, iy);
-    GSTAGE(qg + 2);
-    load_col(s, col, tx, ty, 0, 0);
-    t_d1_z<R>(col, acc[f], iz);
-    GSTAGE(ql);
-    t_d2_xy<R, 0>(s, acc[f], tx, ty, ix2);
-    t_d2_xy<R, 1>(s, acc[f], tx, ty, iy2);
-    load_col(s, col, tx, ty, 0, 0);
-    t_d2_z<R>(col, acc[f], iz2);
+    for (int zz = 0; zz < TZ; ++zz) r0[zz] = R(0);
+    if (kind == K_VAL) {
+#pragma unroll
+      for (int zz = 0; zz < TZ; ++zz) r0[zz] = s[sidx(tx, ty, zz, 0, 0, 0)];
+      add_to(acc, f, r0);
+    } else if (kind == K_D1X) {
+      t_d1_xy<R, 0>(s, r0, tx, ty, ph.idx);
+      add_to(acc, f, r0);
+    } else if (kind == K_D1Y) {
+      t_d1_xy<R, 1>(s, r0, tx, ty, ph.idy);
+      add_to(acc, f, r0);
+    } else if (kind == K_D1Z) {
+      R col[SZ];
+      load_col(s, col, tx, ty, 0, 0);
+      t_d1_z<R>(col, r0, ph.idz);
+      add_to(acc, f, r0);
+    } else if (kind == K_LAP) {
+      t_d2_xy<R, 0>(s, r0, tx, ty, ph.idx2);
+      t_d2_xy<R, 1>(s, r0, tx, ty, ph.idy2);
+      R col[SZ];
+      load_col(s, col, tx, ty, 0, 0);
+      t_d2_z<R>(col, r0, ph.idz2);
+      add_to(acc, f, r0);
+    } else if (kind == K_GDX) {
+      // gd_x: D2x for component x, D1x D1y for y, D1x D1z for z
+      t_d2_xy<R, 0>(s, r0, tx, ty, ph.idx2);
+      add_to(acc, f, r0);
+#pragma unroll
+      for (int zz = 0; zz < TZ; ++zz) r0[zz] = R(0);
+      t_mix_xy<R>(s, r0, tx, ty, ph.idx * ph.idy);
+      add_to(acc, f + 1, r0);
+#pragma unroll
+      for (int zz = 0; zz < TZ; ++zz) r0[zz] = R(0);
+      t_mix_hz<R, 0>(s, r0, tx, ty, ph.idx * ph.idz);
+      add_to(acc, f + 2, r0);
+    } else if (kind == K_GDY) {
+      t_d2_xy<R, 1>(s, r0, tx, ty, ph.idy2);
+      add_to(acc, f + 1, r0);
+#pragma unroll
+      for (int zz = 0; zz < TZ; ++zz) r0[zz] = R(0);
+      t_mix_xy<R>(s, r0, tx, ty, ph.idx * ph.idy);
+      add_to(acc, f, r0);
+#pragma unroll
+      for (int zz = 0; zz < TZ; ++zz) r0[zz] = R(0);
+      t_mix_hz<R, 1>(s, r0, tx, ty, ph.idy * ph.idz);
+      add_to(acc, f + 2, r0);
+    } else {  // K_GDZ
+      R col[SZ];
+      load_col(s, col, tx, ty, 0, 0);
+      t_d2_z<R>(col, r0, ph.idz2);
+      add_to(acc, f + 2, r0);
+#pragma unroll
+      for (int zz = 0; zz < TZ; ++zz) r0[zz] = R(0);
+      t_mix_hz<R, 0>(s, r0, tx, ty, ph.idx * ph.idz);
+      add_to(acc, f, r0);
+#pragma unroll
+      for (int zz = 0; zz < TZ; ++zz) r0[zz] = R(0);
+      t_mix_hz<R, 1>(s, r0, tx, ty, ph.idy * ph.idz);
+      add_to(acc, f + 1, r0);
+    }
   }
-#undef GSTAGE
 
   const int i = x0 + tx, j = y0 + ty;
   if (i >= nx || j >= ny) return;
@@ -936,7 +986,8 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1) gather_tiled_kern
 template <typename R>
 void launch_adj_gather_tiled(const Layout& L, const Phys<R>& ph, const R* coef, const R* dbar, R* gbar,
                              const StepState* ss, cudaStream_t st) {
-  if ((long long)L.nx * L.ny * L.nz >= (1LL << 31)) {  // row offsets are 32-bit
+  // chunk offsets are 32-bit; rows must split into 16-byte chunks
+  if ((long long)L.nx * L.ny * L.nz >= (1LL << 31) || L.nx % 4 != 0) {
     launch_adj_gather<R>(L, ph, coef, dbar, gbar, ss, st);
     return;
   }

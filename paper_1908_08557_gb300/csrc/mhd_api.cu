@@ -128,6 +128,8 @@ static const char* check_params(const mhd_params* p) {
   if (p->stats_every < 0) return "stats_every must be >= 0";
   if (p->adjoint != 0 && p->adjoint != 1) return "adjoint must be 0 or 1";
   if ((long long)p->nx * p->ny * p->nz > (1LL << 34)) return "grid too large";
+  if (p->adjoint && (long long)NF * (p->nz + 2 * NG) * p->ny * (p->nx / 4) >= (1LL << 31))
+    return "grid too large for the adjoint (8 (nz + 6) ny nx / 4 must stay below 2^31)";
   if ((long long)((p->nx + 31) / 32) * ((p->ny + 7) / 8) > RED_BLOCKS_MAX)
     return "horizontal grid too large for the reduction buffer (nx * ny <= 2^20)";
   return nullptr;
@@ -890,9 +892,9 @@ static void adjoint_step_impl(mhd_ctx* h) {
   FFTPlan fpa = h->fp;
   fpa.P = h->fp.Q;   // 9 packed ghost-adjoint planes
   fpa.Q = h->fp.P;   // 3 summed planes
+  launch_adj_update<R>(h->L, (R*)h->fbar, (R*)h->dbar, (const R*)h->gbar, 0.0, rk_beta(2), 0, h->ss, h->st);
+  h->nlaunch += 1;
   for (int s = 2; s >= 0; --s) {
-    launch_adj_axpy<R>(h->L, h->p.bc_z, (R*)h->fbar, (R*)h->dbar, (const R*)h->gbar, rk_beta(s), 0.0, 0, h->ss,
-                       h->st);
     launch_adj_point<R>(h->L, ph, bg, S[s], (const R*)h->dbar, (R*)h->coef, h->thbar, (const R*)h->wtab,
                         (const R*)h->wptab, h->ss, s, h->st);
     if (h->adj_tiled)
@@ -901,9 +903,9 @@ static void adjoint_step_impl(mhd_ctx* h) {
       launch_adj_gather<R>(h->L, ph, (const R*)h->coef, (const R*)h->dbar, (R*)h->gbar, h->ss, h->st);
     launch_adj_bc<R>(h->L, ph, bg, S[s], (R*)h->gbar, (R)h->p.dz, h->ss, h->st);
     launch_pfe_adjoint<R>(fpa, h->L, (R*)h->gbar, h->ss, h->st);
-    launch_adj_axpy<R>(h->L, h->p.bc_z, (R*)h->fbar, (R*)h->dbar, (const R*)h->gbar, 0.0, rk_alpha(s), 1, h->ss,
-                       h->st);
-    h->nlaunch += 9;
+    launch_adj_update<R>(h->L, (R*)h->fbar, (R*)h->dbar, (const R*)h->gbar, rk_alpha(s), s > 0 ? rk_beta(s - 1) : 0.0,
+                         1, h->ss, h->st);
+    h->nlaunch += 8;
   }
 }
 

@@ -63,8 +63,10 @@ template <typename R> void launch_adj_gather_tiled(const Layout& L, const Phys<R
                                                    const R* dbar, R* gbar, const StepState* ss, cudaStream_t st);
 template <typename R> void launch_adj_bc(const Layout& L, const Phys<R>& ph, const Background<R>& bg, const R* g,
                                          R* gbar, R dz, const StepState* ss, cudaStream_t st);
-template <typename R> void launch_adj_axpy(const Layout& L, int bcz, R* fbar, R* dbar, const R* gbar, double beta,
-                                           double alpha, int phase, const StepState* ss, cudaStream_t st);
+// adjoint elementwise updates (mode 0: D = beta F; mode 1: F += G, D = alpha D + beta F);
+// nx must be a multiple of 4 and NF * (nz + 6) * ny * nx / 4 < 2^31
+template <typename R> void launch_adj_update(const Layout& L, R* fbar, R* dbar, const R* gbar, double alpha,
+                                             double beta, int mode, const StepState* ss, cudaStream_t st);
 template <typename R> void launch_bz_plane(int nx, int ny, int nz, int k, double dx, double dy, const R* st_in,
                                            R* out, int adjoint, const R* bbar, R* lam, cudaStream_t st);
 template <typename R> void launch_adj_pack(const Layout& L, int bcz, const R* fbar, R* out, cudaStream_t st);
