@@ -15,9 +15,10 @@
 using namespace mhd;
 
 struct mhd_ctx {
-  CUtensorMap tm[2];   // TMA descriptors of the two FP32 state sets (64-byte aligned)
+  CUtensorMap tm[3];   // TMA descriptors of the two FP32 state sets and of the adjoint's
+                       // third substep state (64-byte aligned)
   bool tiled;          // FP32: TMA-fed z-march kernel; otherwise the simple kernel
-  bool adj_tiled;  // tiled transposed-stencil gather (else one thread per point)
+  bool adj_tiled;      // adjoint: tiled gather and (FP32) z-march point kernel, else one thread per point
   mhd_params p;
   Layout L;
   cudaStream_t st;
@@ -551,6 +552,8 @@ extern "C" int mhd_create(const mhd_params* p, void* workspace, size_t ws_bytes,
     for (int s = 0; s < 2 && !rc; ++s)
       if (make_state_tensor_map(&h->tm[s], h->L, h->f[s]) != 0)
         rc = fail(h, MHD_ERR_CUDA, "cuTensorMapEncodeTiled failed for state set %d", s);
+    if (!rc && p->adjoint && make_state_tensor_map(&h->tm[2], h->L, h->s2) != 0)
+      rc = fail(h, MHD_ERR_CUDA, "cuTensorMapEncodeTiled failed for the adjoint substep state");
   }
   if (!rc) {
     StepState s0;
@@ -894,9 +897,15 @@ static void adjoint_step_impl(mhd_ctx* h) {
   fpa.Q = h->fp.P;   // 3 summed planes
   launch_adj_update<R>(h->L, (R*)h->fbar, (R*)h->dbar, (const R*)h->gbar, 0.0, rk_beta(2), 0, h->ss, h->st);
   h->nlaunch += 1;
+  const int tmi[3] = {h->cur, 1 - h->cur, 2};
   for (int s = 2; s >= 0; --s) {
-    launch_adj_point<R>(h->L, ph, bg, S[s], (const R*)h->dbar, (R*)h->coef, h->thbar, (const R*)h->wtab,
-                        (const R*)h->wptab, h->ss, s, h->st);
+    if (sizeof(R) == 4 && h->tiled && h->adj_tiled)
+      launch_adj_point_tiled(&h->tm[tmi[s]], h->L, *(const Phys<float>*)&ph, h->bgf, (const float*)h->dbar,
+                             (float*)h->coef, h->thbar, (const float*)h->wtab, (const float*)h->wptab, h->ss, s,
+                             h->p.dx, h->p.dy, h->p.dz, h->st);
+    else
+      launch_adj_point<R>(h->L, ph, bg, S[s], (const R*)h->dbar, (R*)h->coef, h->thbar, (const R*)h->wtab,
+                          (const R*)h->wptab, h->ss, s, h->st);
     if (h->adj_tiled)
       launch_adj_gather_tiled<R>(h->L, ph, (const R*)h->coef, (const R*)h->dbar, (R*)h->gbar, h->ss, h->st);
     else

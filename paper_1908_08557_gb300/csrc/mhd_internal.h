@@ -51,6 +51,12 @@ template <typename R> void launch_rk(const Layout& L, const Phys<R>& ph, const B
 void launch_rk_tiled(const CUtensorMap* tm, const Layout& L, const Phys<float>& ph, const Background<float>& bg,
                      float* fout, float* df, const float* wtab, const float* wptab, const Driver& drv,
                      StepState* ss, int sub, double dx, double dy, double dz, cudaStream_t st);
+// FP32 pointwise adjoint of substep `sub` on the TMA-fed z-march (tm maps the
+// ghost-filled substep state): 46 coefficient fields and the driver adjoints
+void launch_adj_point_tiled(const CUtensorMap* tm, const Layout& L, const Phys<float>& ph,
+                            const Background<float>& bg, const float* dbar, float* coef, double* thbar,
+                            const float* wtab, const float* wptab, StepState* ss, int sub, double dx, double dy,
+                            double dz, cudaStream_t st);
 int make_state_tensor_map(CUtensorMap* tm, const Layout& L, void* base);
 // adjoint (transposed linearisation of one substep)
 constexpr int NCOEF_ADJ = 46;

@@ -18,6 +18,7 @@
 // handle's error word, drains its outstanding copies (bounded) and returns.
 #include <cuda.h>
 
+#include "mhd_adjoint_point.cuh"
 #include "mhd_internal.h"
 
 namespace mhd {
@@ -56,6 +57,11 @@ struct Args {
   StepState* ss;
   int sub;
   int ntx, nty, nch, kchunk;
+  // adjoint mode: D (adjoint of the RK accumulator, padded layout) in, the
+  // 46 coefficient fields ([46][nz][ny][nx]) and the driver adjoints out
+  const float* dbar;
+  float* coef;
+  double* thbar;
   float c1x, c2x, c3x, c1y, c2y, c3y, c1z, c2z, c3z;   // D1 weights / spacing
   float e0x, e1x, e2x, e3x, e0y, e1y, e2y, e3y, e0z, e1z, e2z, e3z;  // D2 weights / spacing^2
 };
@@ -186,6 +192,11 @@ __device__ __forceinline__ void front_plane(const Args& a, const FItems& it, con
   __syncthreads();
 }
 
+// ADJ = false: right-hand side + RK update of substep `sub` (sub < 0: store
+// the right-hand side only).  ADJ = true: the pointwise adjoint of substep
+// `sub` (the input is the ghost-filled substep state): per interior cell the
+// 46 coefficients of the transposed right-hand side, nothing else stored.
+template <bool ADJ>
 __global__ void __launch_bounds__(TILE, 1) rk_tiled_kernel(const __grid_constant__ CUtensorMap tm, const Args a) {
   extern __shared__ __align__(128) float smem[];
   float* raw = smem;
@@ -206,7 +217,7 @@ __global__ void __launch_bounds__(TILE, 1) rk_tiled_kernel(const __grid_constant
   __syncthreads();
 
   const int sub = a.sub;
-  const bool eval = sub < 0;
+  const bool eval = !ADJ && sub < 0;
   const float dt = eval ? 1.f : (float)a.ss->dt;
   const float alpha = eval ? 0.f : (float)rk_alpha(sub);
   const float beta = eval ? 0.f : (float)rk_beta(sub);
@@ -258,11 +269,12 @@ __global__ void __launch_bounds__(TILE, 1) rk_tiled_kernel(const __grid_constant
       const bool live = i < L.nx && j < L.ny;
       // RK accumulator of the centre cell, fetched early so its latency hides
       // behind the front processing
+      // (adjoint mode: D of the centre cell)
       float dfo[NF];
       {
-        const float* dq = a.df + (live ? L.at(0, k, j, i) : 0);
+        const float* dq = (ADJ ? a.dbar : a.df) + (live ? L.at(0, k, j, i) : 0);
 #pragma unroll
-        for (int f = 0; f < NF; ++f) dfo[f] = (live && sub > 0) ? __ldg(dq + (long long)f * L.fs) : 0.f;
+        for (int f = 0; f < NF; ++f) dfo[f] = (live && (ADJ || sub > 0)) ? __ldg(dq + (long long)f * L.fs) : 0.f;
       }
       FRONT(k + NG);
       if (bad) break;
@@ -338,60 +350,75 @@ __global__ void __launch_bounds__(TILE, 1) rk_tiled_kernel(const __grid_constant
         c.gT[2] = dz_[LT] + a.bg.dt[k];
         c.lapL = xx_[LR] + yy_[LR] + zz_[LR] + a.bg.d2l[k];
         c.lapT = xx_[LT] + yy_[LT] + zz_[LT] + a.bg.d2t[k];
-        float out[NF];
-        rhs_point<float>(c, a.ph, a.wtab[k], a.wptab[k], out);
-
-        float tgx = 0.f, tgy = 0.f;
-        const Phys<float>& ph = a.ph;
-        if (ph.bcz == 0 && k == 0) {
-          const long long q2 = (long long)j * L.nx + i, n2 = (long long)L.nx * L.ny;
-          const float vx = a.v0[q2] + ss_ * (a.v1[q2] - a.v0[q2]);
-          const float vy = a.v0[n2 + q2] + ss_ * (a.v1[n2 + q2] - a.v0[n2 + q2]);
-          tgx = rr * vx;
-          tgy = rr * vy;
-          out[AX] -= ph.tau_A * (c.A[0] - a.axt[q2]);
-          out[AY] -= ph.tau_A * (c.A[1] - a.ayt[q2]);
-          out[UX] -= ph.tau_u * (c.U[0] - tgx);
-          out[UY] -= ph.tau_u * (c.U[1] - tgy);
-          out[UZ] = 0.f;
-          out[LR] = 0.f;
-        }
-        if (ph.bcz == 0 && k == L.nz - 1) out[UZ] = 0.f;
-        {
-          // periodic images of the cell: offsets computed once for all fields
-          const long long cq = L.at(0, k, j, i);
-          const int ox = i < NG ? L.nx : (i >= L.nx - NG ? -L.nx : 0);
-          const long long oy = j < NG ? (long long)L.ny * L.mx : (j >= L.ny - NG ? -(long long)L.ny * L.mx : 0);
-          const bool small = L.nx < 2 * NG || L.ny < 2 * NG;
+        if constexpr (ADJ) {
+          float wo[NF];
 #pragma unroll
-          for (int f = 0; f < NF; ++f) {
-            const long long q = cq + (long long)f * L.fs;
-            const float dfn = alpha * dfo[f] + dt * out[f];
-            if (sub < 2) a.df[q] = dfn;
-            if (!eval) {
-              const float vn = v_[f] + beta * dfn;
-              if (small) {
-                store_img(L, a.fout, f, k, j, i, vn);
-              } else {
-                float* o = a.fout + q;
-                o[0] = vn;
-                if (ox) o[ox] = vn;
-                if (oy) o[oy] = vn;
-                if (ox && oy) o[ox + oy] = vn;
+          for (int f = 0; f < NF; ++f) wo[f] = dt * dfo[f];
+          const long long q2 = (long long)j * L.nx + i, n2 = (long long)L.nx * L.ny;
+          float cf[NCOEF];
+          const long long cu = L.at(UX, 0, j, i);
+          adjoint_cell<float>(c, a.ph, a.wtab[k], a.wptab[k], wo, dt, k, L.nz, a.dbar + cu, a.dbar + cu + L.fs,
+                              L.sz(), a.thbar, q2, n2, a.ss, sub, cf);
+          float* co = a.coef + (long long)k * n2 + q2;
+          const long long n3 = n2 * L.nz;
+#pragma unroll
+          for (int q = 0; q < NCOEF; ++q) co[q * n3] = cf[q];
+        } else {
+          float out[NF];
+          rhs_point<float>(c, a.ph, a.wtab[k], a.wptab[k], out);
+
+          float tgx = 0.f, tgy = 0.f;
+          const Phys<float>& ph = a.ph;
+          if (ph.bcz == 0 && k == 0) {
+            const long long q2 = (long long)j * L.nx + i, n2 = (long long)L.nx * L.ny;
+            const float vx = a.v0[q2] + ss_ * (a.v1[q2] - a.v0[q2]);
+            const float vy = a.v0[n2 + q2] + ss_ * (a.v1[n2 + q2] - a.v0[n2 + q2]);
+            tgx = rr * vx;
+            tgy = rr * vy;
+            out[AX] -= ph.tau_A * (c.A[0] - a.axt[q2]);
+            out[AY] -= ph.tau_A * (c.A[1] - a.ayt[q2]);
+            out[UX] -= ph.tau_u * (c.U[0] - tgx);
+            out[UY] -= ph.tau_u * (c.U[1] - tgy);
+            out[UZ] = 0.f;
+            out[LR] = 0.f;
+          }
+          if (ph.bcz == 0 && k == L.nz - 1) out[UZ] = 0.f;
+          {
+            // periodic images of the cell: offsets computed once for all fields
+            const long long cq = L.at(0, k, j, i);
+            const int ox = i < NG ? L.nx : (i >= L.nx - NG ? -L.nx : 0);
+            const long long oy = j < NG ? (long long)L.ny * L.mx : (j >= L.ny - NG ? -(long long)L.ny * L.mx : 0);
+            const bool small = L.nx < 2 * NG || L.ny < 2 * NG;
+  #pragma unroll
+            for (int f = 0; f < NF; ++f) {
+              const long long q = cq + (long long)f * L.fs;
+              const float dfn = alpha * dfo[f] + dt * out[f];
+              if (sub < 2) a.df[q] = dfn;
+              if (!eval) {
+                const float vn = v_[f] + beta * dfn;
+                if (small) {
+                  store_img(L, a.fout, f, k, j, i, vn);
+                } else {
+                  float* o = a.fout + q;
+                  o[0] = vn;
+                  if (ox) o[ox] = vn;
+                  if (oy) o[oy] = vn;
+                  if (ox && oy) o[ox + oy] = vn;
+                }
               }
             }
           }
-        }
-        if (ph.bcz == 0 && k == 0) {
-          for (int m = 1; m <= NG; ++m) {
-#pragma unroll
-            for (int cc = 0; cc < 2; ++cc) {
-              const long long q = L.at(UX + cc, -m, j, i);
-              const float u = (m == 1 ? Pz2 : (m == 2 ? Pz1 : Pz0))[(UX + cc) * BY * BX];
-              const float rh = -ph.tau_u * (u - (cc == 0 ? tgx : tgy));
-              const float dfn = (sub > 0 ? alpha * a.df[q] : 0.f) + dt * rh;
-              if (sub < 2) a.df[q] = dfn;
-              if (!eval) store_img(L, a.fout, UX + cc, -m, j, i, u + beta * dfn);
+          if (ph.bcz == 0 && k == 0) {
+            for (int m = 1; m <= NG; ++m) {
+  #pragma unroll
+              for (int cc = 0; cc < 2; ++cc) {
+                const long long q = L.at(UX + cc, -m, j, i);
+                const float u = (m == 1 ? Pz2 : (m == 2 ? Pz1 : Pz0))[(UX + cc) * BY * BX];
+                const float rh = -ph.tau_u * (u - (cc == 0 ? tgx : tgy));
+                const float dfn = (sub > 0 ? alpha * a.df[q] : 0.f) + dt * rh;
+                if (sub < 2) a.df[q] = dfn;
+                if (!eval) store_img(L, a.fout, UX + cc, -m, j, i, u + beta * dfn);
+              }
             }
           }
         }
@@ -427,30 +454,25 @@ bool rk_tiled_supported() { return true; }
 
 size_t rk_tiled_smem() { return tiled::SMEM_BYTES; }
 
-void launch_rk_tiled(const CUtensorMap* tm, const Layout& L, const Phys<float>& ph, const Background<float>& bg,
-                     float* fout, float* df, const float* wtab, const float* wptab, const Driver& drv,
-                     StepState* ss, int sub, double dx, double dy, double dz, cudaStream_t st) {
+static Args tiled_args(const Layout& L, const Phys<float>& ph, const Background<float>& bg, const float* wtab,
+                       const float* wptab, StepState* ss, int sub, double dx, double dy, double dz) {
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(tiled::rk_tiled_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(tiled::rk_tiled_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)tiled::SMEM_BYTES);
+    cudaFuncSetAttribute(tiled::rk_tiled_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)tiled::SMEM_BYTES);
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev);
     attr = true;
   }
-  Args a;
+  Args a{};
   a.L = L;
   a.ph = ph;
   a.bg = bg;
-  a.fout = fout;
-  a.df = df;
   a.wtab = wtab;
   a.wptab = wptab;
-  a.axt = (const float*)drv.axt;
-  a.ayt = (const float*)drv.ayt;
-  a.v0 = (const float*)drv.v0;
-  a.v1 = (const float*)drv.v1;
   a.ss = ss;
   a.sub = sub;
   a.ntx = (L.nx + tiled::TX - 1) / tiled::TX;
@@ -482,9 +504,36 @@ void launch_rk_tiled(const CUtensorMap* tm, const Layout& L, const Phys<float>& 
   a.e2y = (float)(W2[2] / (dy * dy)); a.e3y = (float)(W2[3] / (dy * dy));
   a.e0z = (float)(W2[0] / (dz * dz)); a.e1z = (float)(W2[1] / (dz * dz));
   a.e2z = (float)(W2[2] / (dz * dz)); a.e3z = (float)(W2[3] / (dz * dz));
-  const int nitems = tiles * a.nch;
-  const int grid = nitems < g_sms ? nitems : g_sms;
-  tiled::rk_tiled_kernel<<<grid, dim3(tiled::TX, tiled::TY), tiled::SMEM_BYTES, st>>>(*tm, a);
+  return a;
+}
+
+static int tiled_grid(const Args& a) {
+  const int nitems = a.ntx * a.nty * a.nch;
+  return nitems < g_sms ? nitems : g_sms;
+}
+
+void launch_rk_tiled(const CUtensorMap* tm, const Layout& L, const Phys<float>& ph, const Background<float>& bg,
+                     float* fout, float* df, const float* wtab, const float* wptab, const Driver& drv,
+                     StepState* ss, int sub, double dx, double dy, double dz, cudaStream_t st) {
+  Args a = tiled_args(L, ph, bg, wtab, wptab, ss, sub, dx, dy, dz);
+  a.fout = fout;
+  a.df = df;
+  a.axt = (const float*)drv.axt;
+  a.ayt = (const float*)drv.ayt;
+  a.v0 = (const float*)drv.v0;
+  a.v1 = (const float*)drv.v1;
+  tiled::rk_tiled_kernel<false><<<tiled_grid(a), dim3(tiled::TX, tiled::TY), tiled::SMEM_BYTES, st>>>(*tm, a);
+}
+
+void launch_adj_point_tiled(const CUtensorMap* tm, const Layout& L, const Phys<float>& ph,
+                            const Background<float>& bg, const float* dbar, float* coef, double* thbar,
+                            const float* wtab, const float* wptab, StepState* ss, int sub, double dx, double dy,
+                            double dz, cudaStream_t st) {
+  Args a = tiled_args(L, ph, bg, wtab, wptab, ss, sub, dx, dy, dz);
+  a.dbar = dbar;
+  a.coef = coef;
+  a.thbar = thbar;
+  tiled::rk_tiled_kernel<true><<<tiled_grid(a), dim3(tiled::TX, tiled::TY), tiled::SMEM_BYTES, st>>>(*tm, a);
 }
 
 // Tensor map of one padded FP32 state set: dims (mx, my, mz, 8 fields),
