@@ -9,11 +9,13 @@
 // (dR/df)^T W is assembled from
 //  1. adj_point_kernel: per interior cell, the transpose of the pointwise
 //     physics (rhs_point) and of the boundary rows / nudging terms, giving
-//     46 coefficients: adjoints of the cell values and of every derivative
+//     40 coefficients: adjoints of the cell values and of every derivative
 //     the right-hand side used (first, second, mixed);
-//  2. adj_gather_kernel: the transposed stencils (D1^T = -D1, D2^T = D2,
+//  2. the gather (adj_gather_kernel, or gd_fold_kernel + the tiled
+//     gather_tiled_kernel): the transposed stencils (D1^T = -D1, D2^T = D2,
 //     (D1_a D1_b)^T = D1_a D1_b, periodic in x and y) applied to the
-//     coefficient fields, at interior points and z ghost layers;
+//     coefficient fields, at interior points and z ghost layers, plus the
+//     nudging value adjoints of A and of the u ghost rows;
 //  3. adj_bc_kernel: the transpose of the pointwise ghost rules (Eqs. 8, 11,
 //     13, closed u_z, symmetric u_hor), routing ghost adjoints into the
 //     interior; the potential-field ghosts are transposed by the FFT kernels
@@ -181,18 +183,24 @@ __global__ void __launch_bounds__(128) adj_gather_kernel(AdjGatherArgs<R> a) {
   const R inv[3] = {ph.idx, ph.idy, ph.idz};
   const R inv2[3] = {ph.idx2, ph.idy2, ph.idz2};
   const bool inside = k >= 0 && k < nz;
+  const R dt = R(a.ss->dt);
   for (int cc = 0; cc < 3; ++cc) {
     for (int grp = 0; grp < 2; ++grp) {  // grp 0: A_c, grp 1: u_c
-      const int qd = grp == 0 ? CDA : CDU, ql = grp == 0 ? CLA : CLU, qg = grp == 0 ? CGA : CGU;
-      R s = inside ? cget(a.coef, CV + (grp == 0 ? AX : UX) + cc, k, j, i, nx, ny, nz) : R(0);
+      // gd(u) coefficients are the lap(u) ones divided by 3
+      const int qd = grp == 0 ? CDA : CDU, ql = grp == 0 ? CLA : CLU, qg = grp == 0 ? CGA : CLU;
+      const R gs = grp == 0 ? R(1) : R(1.0 / 3.0);
+      const int fl = (grp == 0 ? AX : UX) + cc;
+      R s = (inside && grp == 1) ? cget(a.coef, CV + fl, k, j, i, nx, ny, nz) : R(0);
       for (int ax = 0; ax < 3; ++ax) {
         s += t_d1(a.coef, qd + 3 * cc + ax, k, j, i, ax, nx, ny, nz, inv[ax]);
         s += t_d2(a.coef, ql + cc, k, j, i, ax, nx, ny, nz, inv2[ax]);
       }
-      s += t_d2(a.coef, qg + cc, k, j, i, cc, nx, ny, nz, inv2[cc]);
+      s += gs * t_d2(a.coef, qg + cc, k, j, i, cc, nx, ny, nz, inv2[cc]);
       for (int ax = 0; ax < 3; ++ax)
-        if (ax != cc) s += t_d11(a.coef, qg + ax, k, j, i, ax, cc, nx, ny, nz, inv[ax], inv[cc]);
-      a.gbar[L.at((grp == 0 ? AX : UX) + cc, k, j, i)] = s;
+        if (ax != cc) s += gs * t_d11(a.coef, qg + ax, k, j, i, ax, cc, nx, ny, nz, inv[ax], inv[cc]);
+      // photospheric nudging of A_x, A_y (Eq. 4): value adjoint -tau_A dt D
+      if (ph.bcz == 0 && k == 0 && grp == 0 && cc < 2) s -= ph.tau_A * dt * a.dbar[L.at(fl, k, j, i)];
+      a.gbar[L.at(fl, k, j, i)] = s;
     }
   }
   for (int grp = 0; grp < 2; ++grp) {  // ln rho, ln T
@@ -206,7 +214,6 @@ __global__ void __launch_bounds__(128) adj_gather_kernel(AdjGatherArgs<R> a) {
   }
   // stateful horizontal-velocity ghost rows: their own nudging term
   if (ph.bcz == 0 && k < 0) {
-    const R dt = R(a.ss->dt);
     for (int cc = 0; cc < 2; ++cc) {
       const long long q = L.at(UX + cc, k, j, i);
       a.gbar[q] -= ph.tau_u * dt * a.dbar[q];
@@ -477,11 +484,55 @@ namespace mhd {
 
 // ===========================================================================
 // Tiled gather: a block owns 32 x 8 columns and 8 consecutive z points of
-// the output (z in [-3, nz+3)); it walks the 46 coefficient fields, staging
-// each on the block's points plus a 3-cell halo in shared memory (periodic in
-// x and y, zero outside the interior layers), and accumulates the transposed
-// stencils into 8 targets x 8 z points held in registers.  z stencils reuse a
-// 14-value column per thread.
+// the output (z in [-3, nz+3)) for one group of adjoint fields ({A, ln rho}
+// or {u, ln T}); it walks that group's 20 coefficient fields, staging each
+// on the block's points plus a 3-cell halo in shared memory (periodic in x
+// and y, zero outside the interior layers), and accumulates the transposed
+// stencils into 4 targets x 8 z points held in registers.  z stencils reuse
+// a 14-value column per thread.  Before it, gd_fold_kernel moves the
+// in-plane mixed derivatives into first-derivative coefficients.
+// In-plane part of the gradient-of-divergence transpose, folded into the
+// first-derivative coefficients before the tiled gather: the mixed term
+// (D1_a D1_c)^T G_a = D1_c^T (D1_a^T G_a) for a in {x, y}, so T_a = D1_a^T G_a
+// is added to the coefficient of D1_c of component c (c != a).  T_a vanishes
+// outside the interior layers (an in-plane stencil of a field that does), so
+// nothing is lost at the z ghost layers; the z-direction mixed terms stay in
+// the gather.
+template <typename R>
+__global__ void __launch_bounds__(256) gd_fold_kernel(int nx, int ny, int nz, R* __restrict__ coef, R idx, R idy,
+                                                      const StepState* ss) {
+  if (halted(ss)) return;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int k = blockIdx.z;
+  if (i >= nx || j >= ny) return;
+  const long long n2 = (long long)nx * ny, n3 = n2 * nz;
+  const long long row = (long long)k * n2 + (long long)j * nx;
+  const R cw[4] = {R(0), W<R>::c1, W<R>::c2, W<R>::c3};
+#pragma unroll
+  for (int grp = 0; grp < 2; ++grp) {
+    // gd(u) coefficients are the lap(u) ones divided by 3
+    const int qg = grp == 0 ? CGA : CLU, qd = grp == 0 ? CDA : CDU;
+    const R gs = grp == 0 ? R(1) : R(1.0 / 3.0);
+    const R* gx = coef + (long long)(qg + 0) * n3 + row;
+    const R* gy = coef + (long long)(qg + 1) * n3 + (long long)k * n2 + i;
+    R tx = R(0), ty = R(0);
+#pragma unroll
+    for (int m = 1; m <= 3; ++m) {
+      const int im = i - m < 0 ? i - m + nx : i - m, ip = i + m >= nx ? i + m - nx : i + m;
+      const int jm = j - m < 0 ? j - m + ny : j - m, jp = j + m >= ny ? j + m - ny : j + m;
+      tx += cw[m] * (__ldg(gx + im) - __ldg(gx + ip));
+      ty += cw[m] * (__ldg(gy + (long long)jm * nx) - __ldg(gy + (long long)jp * nx));
+    }
+    tx *= gs * idx;
+    ty *= gs * idy;
+    const long long c = row + i;
+    coef[(long long)(qd + 3 * 0 + 0) * n3 + c] += ty;       // D1x of component x <- T_y
+    coef[(long long)(qd + 3 * 1 + 1) * n3 + c] += tx;       // D1y of component y <- T_x
+    coef[(long long)(qd + 3 * 2 + 2) * n3 + c] += tx + ty;  // D1z of component z <- T_x + T_y
+  }
+}
+
 namespace gtile {
 
 constexpr int TX = 32, TY = 8, TZ = 8;
@@ -490,8 +541,6 @@ constexpr int TX = 32, TY = 8, TZ = 8;
 constexpr int XO = 4;
 constexpr int SX = TX + 8, SY = TY + 6, SZ = TZ + 6;
 constexpr int TILE = SX * SY * SZ;
-constexpr int NBUF = 3;  // staged fields in flight: current + two prefetched
-constexpr int NSTAGE = NCOEF;
 
 template <typename R>
 struct GArgs {
@@ -518,8 +567,8 @@ template <typename R>
 __host__ __device__ constexpr int n_chunks() { return TILE * (int)sizeof(R) / 16; }
 
 template <typename R>
-__host__ __device__ constexpr size_t smem_bytes() {
-  return NBUF * TILE * sizeof(R) + n_chunks<R>() * sizeof(int);
+__host__ __device__ constexpr size_t smem_bytes(int nbuf) {
+  return nbuf * TILE * sizeof(R) + n_chunks<R>() * sizeof(int);
 }
 
 // Stage one coefficient field (base: its [nz][ny][nx] array) into s; chunk
@@ -534,22 +583,38 @@ __device__ __forceinline__ void stage_async(R* __restrict__ s, const R* __restri
 }
 
 // Stage kinds: what the transposed operator of a coefficient field is, and
-// which adjoint field(s) it feeds.  Gradient-of-divergence coefficients
-// (gd_a = sum_c D1_a D1_c X_c, D1_a D1_a -> D2_a) feed all three components
-// of their vector field.
-enum { K_VAL = 0, K_D1X, K_D1Y, K_D1Z, K_LAP, K_GDX, K_GDY, K_GDZ };
-#define GS(q, kind, f) ((q) | ((kind) << 8) | ((f) << 12))
-__constant__ int kStage[NSTAGE] = {
-    GS(CV + AX, K_VAL, AX), GS(CDA + 0, K_D1X, AX), GS(CDA + 1, K_D1Y, AX), GS(CDA + 2, K_D1Z, AX), GS(CLA + 0, K_LAP, AX),
-    GS(CV + AY, K_VAL, AY), GS(CDA + 3, K_D1X, AY), GS(CDA + 4, K_D1Y, AY), GS(CDA + 5, K_D1Z, AY), GS(CLA + 1, K_LAP, AY),
-    GS(CV + AZ, K_VAL, AZ), GS(CDA + 6, K_D1X, AZ), GS(CDA + 7, K_D1Y, AZ), GS(CDA + 8, K_D1Z, AZ), GS(CLA + 2, K_LAP, AZ),
-    GS(CGA + 0, K_GDX, AX), GS(CGA + 1, K_GDY, AX), GS(CGA + 2, K_GDZ, AX),
-    GS(CV + UX, K_VAL, UX), GS(CDU + 0, K_D1X, UX), GS(CDU + 1, K_D1Y, UX), GS(CDU + 2, K_D1Z, UX), GS(CLU + 0, K_LAP, UX),
-    GS(CV + UY, K_VAL, UY), GS(CDU + 3, K_D1X, UY), GS(CDU + 4, K_D1Y, UY), GS(CDU + 5, K_D1Z, UY), GS(CLU + 1, K_LAP, UY),
-    GS(CV + UZ, K_VAL, UZ), GS(CDU + 6, K_D1X, UZ), GS(CDU + 7, K_D1Y, UZ), GS(CDU + 8, K_D1Z, UZ), GS(CLU + 2, K_LAP, UZ),
-    GS(CGU + 0, K_GDX, UX), GS(CGU + 1, K_GDY, UX), GS(CGU + 2, K_GDZ, UX),
-    GS(CV + LR, K_VAL, LR), GS(CGL + 0, K_D1X, LR), GS(CGL + 1, K_D1Y, LR), GS(CGL + 2, K_D1Z, LR), GS(CLL, K_LAP, LR),
-    GS(CV + LT, K_VAL, LT), GS(CGT + 0, K_D1X, LT), GS(CGT + 1, K_D1Y, LT), GS(CGT + 2, K_D1Z, LT), GS(CLT, K_LAP, LT)};
+// which adjoint field(s) of the block's group it feeds (target t: 0..2
+// vector components, 3 the scalar).
+//   K_LAP: D2x + D2y + D2z, one axis optionally weighted 4/3 (w: 0 none,
+//          1 x, 2 y, 3 z);
+//   K_LZ:  D2z, or the weighted Laplacian when w != 0, into component t + 2,
+//          and the xz, yz mixed terms (scaled by 1/3 when g is set) into
+//          components t and t + 1.
+// Gradient-of-divergence terms (gd_a = sum_c D1_a D1_c X_c, D1_a D1_a ->
+// D2_a): their in-plane mixed parts are folded into the D1 coefficients
+// beforehand (gd_fold_kernel), so gd_x and gd_y take D2 along their own axis
+// only (K_D2X, K_D2Y) and gd_z feeds all three components (K_LZ).  For u the
+// gd coefficient is the lap(u) coefficient / 3: one staged field serves both,
+// with the own-axis D2 weighted 1 + 1/3.
+enum { K_VAL = 0, K_D1X, K_D1Y, K_D1Z, K_LAP, K_D2X, K_D2Y, K_LZ };
+#define GS(q, kind, t, w, g) ((q) | ((kind) << 8) | ((t) << 12) | ((w) << 16) | ((g) << 18))
+// group 0: A and ln rho; group 1: u and ln T
+constexpr int NSTAGE_HALF = 20;
+__constant__ int kStageHalf[2][NSTAGE_HALF] = {
+    {GS(CDA + 0, K_D1X, 0, 0, 0), GS(CDA + 1, K_D1Y, 0, 0, 0), GS(CDA + 2, K_D1Z, 0, 0, 0), GS(CLA + 0, K_LAP, 0, 0, 0),
+     GS(CDA + 3, K_D1X, 1, 0, 0), GS(CDA + 4, K_D1Y, 1, 0, 0), GS(CDA + 5, K_D1Z, 1, 0, 0), GS(CLA + 1, K_LAP, 1, 0, 0),
+     GS(CDA + 6, K_D1X, 2, 0, 0), GS(CDA + 7, K_D1Y, 2, 0, 0), GS(CDA + 8, K_D1Z, 2, 0, 0), GS(CLA + 2, K_LAP, 2, 0, 0),
+     GS(CGA + 0, K_D2X, 0, 0, 0), GS(CGA + 1, K_D2Y, 1, 0, 0), GS(CGA + 2, K_LZ, 0, 0, 0),
+     GS(CV + LR, K_VAL, 3, 0, 0), GS(CGL + 0, K_D1X, 3, 0, 0), GS(CGL + 1, K_D1Y, 3, 0, 0), GS(CGL + 2, K_D1Z, 3, 0, 0),
+     GS(CLL, K_LAP, 3, 0, 0)},
+    {GS(CV + UX, K_VAL, 0, 0, 0), GS(CDU + 0, K_D1X, 0, 0, 0), GS(CDU + 1, K_D1Y, 0, 0, 0), GS(CDU + 2, K_D1Z, 0, 0, 0),
+     GS(CLU + 0, K_LAP, 0, 1, 0),
+     GS(CV + UY, K_VAL, 1, 0, 0), GS(CDU + 3, K_D1X, 1, 0, 0), GS(CDU + 4, K_D1Y, 1, 0, 0), GS(CDU + 5, K_D1Z, 1, 0, 0),
+     GS(CLU + 1, K_LAP, 1, 2, 0),
+     GS(CV + UZ, K_VAL, 2, 0, 0), GS(CDU + 6, K_D1X, 2, 0, 0), GS(CDU + 7, K_D1Y, 2, 0, 0), GS(CDU + 8, K_D1Z, 2, 0, 0),
+     GS(CLU + 2, K_LZ, 0, 3, 1),
+     GS(CV + LT, K_VAL, 3, 0, 0), GS(CGT + 0, K_D1X, 3, 0, 0), GS(CGT + 1, K_D1Y, 3, 0, 0), GS(CGT + 2, K_D1Z, 3, 0, 0),
+     GS(CLT, K_LAP, 3, 0, 0)}};
 #undef GS
 
 // index of staged point (x offset dx, y offset dy, z point zz + dz) of the
@@ -608,27 +673,6 @@ __device__ __forceinline__ void t_d2_z(const R (&col)[SZ], R (&r)[TZ], R inv2) {
     r[zz] += inv2 * (W<R>::e0 * col[zz + 3] + W<R>::e1 * (col[zz + 2] + col[zz + 4]) +
                      W<R>::e2 * (col[zz + 1] + col[zz + 5]) + W<R>::e3 * (col[zz] + col[zz + 6]));
 }
-// mixed D1x D1y (its own transpose)
-template <typename R>
-__device__ __forceinline__ void t_mix_xy(const R* s, R (&r)[TZ], int tx, int ty, R iab) {
-#pragma unroll
-  for (int zz = 0; zz < TZ; ++zz) {
-    R v = R(0);
-#pragma unroll
-    for (int m = 1; m <= 3; ++m) {
-      const R cm = m == 1 ? W<R>::c1 : (m == 2 ? W<R>::c2 : W<R>::c3);
-      R w = R(0);
-#pragma unroll
-      for (int n = 1; n <= 3; ++n) {
-        const R cn = n == 1 ? W<R>::c1 : (n == 2 ? W<R>::c2 : W<R>::c3);
-        w += cn * (s[sidx(tx, ty, zz, m, n, 0)] - s[sidx(tx, ty, zz, m, -n, 0)] - s[sidx(tx, ty, zz, -m, n, 0)] +
-                   s[sidx(tx, ty, zz, -m, -n, 0)]);
-      }
-      v += cm * w;
-    }
-    r[zz] += v * iab;
-  }
-}
 // mixed D1h D1z, h = x or y: D1h of the staged columns, then D1z
 template <typename R, int AXIS>
 __device__ __forceinline__ void t_mix_hz(const R* s, R (&r)[TZ], int tx, int ty, R ihz) {
@@ -650,12 +694,14 @@ __device__ __forceinline__ void t_mix_hz(const R* s, R (&r)[TZ], int tx, int ty,
 }
 
 // acc[f] += r with a runtime field index (each case indexes registers)
-template <typename R>
-__device__ __forceinline__ void add_to(R (&acc)[NF][TZ], int f, const R (&r)[TZ]) {
+template <typename R, int NO>
+__device__ __forceinline__ void add_to(R (&acc)[NO][TZ], int f, const R (&r)[TZ]) {
   switch (f) {
-#define ADDF(F)                                            \
-  case F:                                                  \
-    _Pragma("unroll") for (int zz = 0; zz < TZ; ++zz) acc[F][zz] += r[zz]; \
+#define ADDF(F)                                                                  \
+  case F:                                                                        \
+    if (F < NO) {                                                                \
+      _Pragma("unroll") for (int zz = 0; zz < TZ; ++zz) acc[F < NO ? F : 0][zz] += r[zz]; \
+    }                                                                            \
     break;
     ADDF(0) ADDF(1) ADDF(2) ADDF(3) ADDF(4) ADDF(5) ADDF(6) ADDF(7)
 #undef ADDF
@@ -663,15 +709,22 @@ __device__ __forceinline__ void add_to(R (&acc)[NF][TZ], int f, const R (&r)[TZ]
   }
 }
 
-template <typename R>
-__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1) gather_tiled_kernel(GArgs<R> a) {
+// Each block owns one output group (blockIdx.x & 1: {A, ln rho} or {u, ln T})
+// of a tile; NB staging buffers give a prefetch distance of NB - 1 stages.
+template <typename R, int NB, int MINB>
+__global__ void __launch_bounds__(256, MINB) gather_tiled_kernel(GArgs<R> a) {
+  constexpr int NO = 4;  // output fields per block
   extern __shared__ __align__(16) unsigned char smem_raw[];
   R* sb = reinterpret_cast<R*>(smem_raw);
-  int* choff = reinterpret_cast<int*>(sb + NBUF * TILE);
+  int* choff = reinterpret_cast<int*>(sb + NB * TILE);
   const Layout& L = a.L;
   if (halted(a.ss)) return;
   const int tx = threadIdx.x, ty = threadIdx.y;
-  const int bz = blockIdx.x % a.ntz, bxy = blockIdx.x / a.ntz;
+  const int grp = (int)(blockIdx.x & 1);
+  const int blk = (int)(blockIdx.x >> 1);
+  const int* stab = kStageHalf[grp];
+  constexpr int NST = NSTAGE_HALF;
+  const int bz = blk % a.ntz, bxy = blk / a.ntz;
   const int x0 = (bxy % a.ntx) * TX, y0 = (bxy / a.ntx) * TY, z0 = bz * TZ - NG;
   const int nx = L.nx, ny = L.ny, nz = L.nz;
   const long long n3 = (long long)nx * ny * nz;
@@ -686,31 +739,32 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1) gather_tiled_kern
     }
   }
   __syncthreads();
-  stage_async<R>(sb, a.coef + (long long)(kStage[0] & 255) * n3, choff);
-  cp_async_commit();
-  stage_async<R>(sb + TILE, a.coef + (long long)(kStage[1] & 255) * n3, choff);
-  cp_async_commit();
-  const Phys<R>& ph = a.ph;
-  R acc[NF][TZ];
 #pragma unroll
-  for (int f = 0; f < NF; ++f)
+  for (int b = 0; b < NB - 1; ++b) {
+    stage_async<R>(sb + b * TILE, a.coef + (long long)(stab[b] & 255) * n3, choff);
+    cp_async_commit();
+  }
+  const Phys<R>& ph = a.ph;
+  R acc[NO][TZ];
+#pragma unroll
+  for (int f = 0; f < NO; ++f)
 #pragma unroll
     for (int zz = 0; zz < TZ; ++zz) acc[f][zz] = R(0);
 
 #pragma unroll 1
-  for (int st = 0; st < NSTAGE; ++st) {
-    // wait for this stage's field (the one prefetched after it may still be
-    // in flight), make it visible, then prefetch two stages ahead into the
-    // buffer every thread finished with in the previous stage
-    if (st + 1 < NSTAGE) cp_async_wait<1>(); else cp_async_wait<0>();
+  for (int st = 0; st < NST; ++st) {
+    // wait for this stage's field (with NB = 3 the one prefetched after it
+    // may still be in flight), make it visible, then prefetch NB - 1 stages
+    // ahead into the buffer every thread finished with in the previous stage
+    if (NB == 3 && st + 1 < NST) cp_async_wait<1>(); else cp_async_wait<0>();
     __syncthreads();
-    const R* s = sb + (st % NBUF) * TILE;
-    if (st + 2 < NSTAGE) {
-      stage_async<R>(sb + ((st + 2) % NBUF) * TILE, a.coef + (long long)(kStage[st + 2] & 255) * n3, choff);
+    const R* s = sb + (st % NB) * TILE;
+    if (st + NB - 1 < NST) {
+      stage_async<R>(sb + ((st + NB - 1) % NB) * TILE, a.coef + (long long)(stab[st + NB - 1] & 255) * n3, choff);
       cp_async_commit();
     }
-    const int code = kStage[st];
-    const int kind = (code >> 8) & 15, f = code >> 12;
+    const int code = stab[st];
+    const int kind = (code >> 8) & 15, f = (code >> 12) & 15, w = (code >> 16) & 3;
     R r0[TZ];
 #pragma unroll
     for (int zz = 0; zz < TZ; ++zz) r0[zz] = R(0);
@@ -729,49 +783,37 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1) gather_tiled_kern
       load_col(s, col, tx, ty, 0, 0);
       t_d1_z<R>(col, r0, ph.idz);
       add_to(acc, f, r0);
-    } else if (kind == K_LAP) {
-      t_d2_xy<R, 0>(s, r0, tx, ty, ph.idx2);
-      t_d2_xy<R, 1>(s, r0, tx, ty, ph.idy2);
-      R col[SZ];
-      load_col(s, col, tx, ty, 0, 0);
-      t_d2_z<R>(col, r0, ph.idz2);
-      add_to(acc, f, r0);
-    } else if (kind == K_GDX) {
-      // gd_x: D2x for component x, D1x D1y for y, D1x D1z for z
+    } else if (kind == K_D2X) {
       t_d2_xy<R, 0>(s, r0, tx, ty, ph.idx2);
       add_to(acc, f, r0);
-#pragma unroll
-      for (int zz = 0; zz < TZ; ++zz) r0[zz] = R(0);
-      t_mix_xy<R>(s, r0, tx, ty, ph.idx * ph.idy);
-      add_to(acc, f + 1, r0);
-#pragma unroll
-      for (int zz = 0; zz < TZ; ++zz) r0[zz] = R(0);
-      t_mix_hz<R, 0>(s, r0, tx, ty, ph.idx * ph.idz);
-      add_to(acc, f + 2, r0);
-    } else if (kind == K_GDY) {
+    } else if (kind == K_D2Y) {
       t_d2_xy<R, 1>(s, r0, tx, ty, ph.idy2);
-      add_to(acc, f + 1, r0);
-#pragma unroll
-      for (int zz = 0; zz < TZ; ++zz) r0[zz] = R(0);
-      t_mix_xy<R>(s, r0, tx, ty, ph.idx * ph.idy);
       add_to(acc, f, r0);
+    } else {
+      // K_LAP, K_LZ: weighted Laplacian (or D2z alone for gd_z of A)
+      const int tgt = kind == K_LAP ? f : f + 2;
+      const R four3 = R(4.0 / 3.0);
+      if (kind == K_LAP || w != 0) {
+        t_d2_xy<R, 0>(s, r0, tx, ty, (w == 1 ? four3 : R(1)) * ph.idx2);
+        t_d2_xy<R, 1>(s, r0, tx, ty, (w == 2 ? four3 : R(1)) * ph.idy2);
+      }
+      {
+        R col[SZ];
+        load_col(s, col, tx, ty, 0, 0);
+        t_d2_z<R>(col, r0, (w == 3 ? four3 : R(1)) * ph.idz2);
+      }
+      add_to(acc, tgt, r0);
+      if (kind == K_LZ) {
+        const R g = (code >> 18) & 1 ? R(1.0 / 3.0) : R(1);
 #pragma unroll
-      for (int zz = 0; zz < TZ; ++zz) r0[zz] = R(0);
-      t_mix_hz<R, 1>(s, r0, tx, ty, ph.idy * ph.idz);
-      add_to(acc, f + 2, r0);
-    } else {  // K_GDZ
-      R col[SZ];
-      load_col(s, col, tx, ty, 0, 0);
-      t_d2_z<R>(col, r0, ph.idz2);
-      add_to(acc, f + 2, r0);
+        for (int zz = 0; zz < TZ; ++zz) r0[zz] = R(0);
+        t_mix_hz<R, 0>(s, r0, tx, ty, g * ph.idx * ph.idz);
+        add_to(acc, f, r0);
 #pragma unroll
-      for (int zz = 0; zz < TZ; ++zz) r0[zz] = R(0);
-      t_mix_hz<R, 0>(s, r0, tx, ty, ph.idx * ph.idz);
-      add_to(acc, f, r0);
-#pragma unroll
-      for (int zz = 0; zz < TZ; ++zz) r0[zz] = R(0);
-      t_mix_hz<R, 1>(s, r0, tx, ty, ph.idy * ph.idz);
-      add_to(acc, f + 1, r0);
+        for (int zz = 0; zz < TZ; ++zz) r0[zz] = R(0);
+        t_mix_hz<R, 1>(s, r0, tx, ty, g * ph.idy * ph.idz);
+        add_to(acc, f + 1, r0);
+      }
     }
   }
 
@@ -783,10 +825,14 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1) gather_tiled_kern
     const int k = z0 + zz;
     if (k >= nz + NG) break;
 #pragma unroll
-    for (int f = 0; f < NF; ++f) {
+    for (int l = 0; l < NO; ++l) {
+      const int f = grp == 0 ? (l < 3 ? AX + l : LR) : (l < 3 ? UX + l : LT);
       const long long q = L.at(f, k, j, i);
-      R v = acc[f][zz];
-      if (ph.bcz == 0 && k < 0 && (f == UX || f == UY)) v -= ph.tau_u * dt * a.dbar[q];
+      R v = acc[l][zz];
+      // nudging value adjoints (Eqs. 4, 5): A_x, A_y at the photosphere and
+      // the stateful u_x, u_y ghost rows below it
+      if (ph.bcz == 0 && ((k == 0 && (f == AX || f == AY)) || (k < 0 && (f == UX || f == UY))))
+        v -= (f == AX || f == AY ? ph.tau_A : ph.tau_u) * dt * a.dbar[q];
       a.gbar[q] = v;
     }
   }
@@ -795,27 +841,32 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1) gather_tiled_kern
 }  // namespace gtile
 
 template <typename R>
-void launch_adj_gather_tiled(const Layout& L, const Phys<R>& ph, const R* coef, const R* dbar, R* gbar,
+void launch_adj_gather_tiled(const Layout& L, const Phys<R>& ph, R* coef, const R* dbar, R* gbar,
                              const StepState* ss, cudaStream_t st) {
   // chunk offsets are 32-bit; rows must split into 16-byte chunks
   if ((long long)L.nx * L.ny * L.nz >= (1LL << 31) || L.nx % 4 != 0) {
     launch_adj_gather<R>(L, ph, coef, dbar, gbar, ss, st);
     return;
   }
+  gd_fold_kernel<R><<<dim3((L.nx + 31) / 32, (L.ny + 7) / 8, L.nz), dim3(32, 8), 0, st>>>(
+      L.nx, L.ny, L.nz, coef, ph.idx, ph.idy, ss);
   gtile::GArgs<R> a;
   a.L = L; a.ph = ph; a.coef = coef; a.dbar = dbar; a.gbar = gbar; a.ss = ss;
   a.ntx = (L.nx + gtile::TX - 1) / gtile::TX;
   a.nty = (L.ny + gtile::TY - 1) / gtile::TY;
   a.ntz = (L.nz + 2 * NG + gtile::TZ - 1) / gtile::TZ;
   const int nblk = a.ntx * a.nty * a.ntz;
-  const size_t smem = gtile::smem_bytes<R>();
-  cudaFuncSetAttribute(gtile::gather_tiled_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  gtile::gather_tiled_kernel<R><<<nblk, dim3(gtile::TX, gtile::TY), smem, st>>>(a);
+  const dim3 blk(gtile::TX, gtile::TY);
+  constexpr int NB = 2;
+  const size_t smem = gtile::smem_bytes<R>(NB);
+  auto k = gtile::gather_tiled_kernel<R, NB, sizeof(R) == 4 ? 3 : 1>;
+  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k<<<2 * nblk, blk, smem, st>>>(a);
 }
 
-template void launch_adj_gather_tiled<float>(const Layout&, const Phys<float>&, const float*, const float*, float*,
+template void launch_adj_gather_tiled<float>(const Layout&, const Phys<float>&, float*, const float*, float*,
                                              const StepState*, cudaStream_t);
-template void launch_adj_gather_tiled<double>(const Layout&, const Phys<double>&, const double*, const double*,
+template void launch_adj_gather_tiled<double>(const Layout&, const Phys<double>&, double*, const double*,
                                               double*, const StepState*, cudaStream_t);
 
 }  // namespace mhd

@@ -7,20 +7,24 @@
 
 namespace mhd {
 
-// coefficient indices
+// Coefficient indices: the adjoints of the cell-record entries the
+// right-hand side reads.  Two entries need no field of their own:
+//  - the values of A enter only through the photospheric nudging (Eq. 4),
+//    whose adjoint the gather applies from D directly;
+//  - gd(u) enters only through the viscous force nu (lap u + gd(u) / 3), so
+//    its adjoint is the lap(u) coefficient divided by 3.
 enum {
-  CV = 0,        // 8 value adjoints (field order)
-  CDA = 8,       // dA[c][a] at CDA + 3c + a
-  CDU = 17,      // dU[c][a]
-  CLA = 26,      // lapA[c]
-  CLU = 29,      // lapU[c]
-  CGA = 32,      // gdA[a]
-  CGU = 35,      // gdU[a]
-  CGL = 38,      // gL[a]
-  CGT = 41,      // gT[a]
-  CLL = 44,      // lapL
-  CLT = 45,      // lapT
-  NCOEF = 46
+  CV = -UX,      // value adjoints of u_x, u_y, u_z, ln rho, ln T at CV + field
+  CDA = 5,       // dA[c][a] at CDA + 3c + a
+  CDU = 14,      // dU[c][a]
+  CLA = 23,      // lapA[c]
+  CLU = 26,      // lapU[c] (3 gdU[c] is the same number)
+  CGA = 29,      // gdA[a]
+  CGL = 32,      // gL[a]
+  CGT = 35,      // gT[a]
+  CLL = 38,      // lapL
+  CLT = 39,      // lapT
+  NCOEF = 40
 };
 
 // Transpose of rhs_point (see mhd_common.cuh) at one cell: given the output
@@ -91,8 +95,7 @@ __device__ __forceinline__ void rhs_point_adjoint(const Cell<R>& c, const Phys<R
     bFc[cc] += a * rho1;
     brho1 += a * Fc[cc];
     // viscous force
-    cf[CLU + cc] += ph.nu * a;
-    cf[CGU + cc] += ph.nu * third * a;
+    cf[CLU + cc] += ph.nu * a;  // and nu / 3 for gd(u)_c: implied (see the enum)
     bSgL[cc] += R(2) * ph.nu * a;
   }
   bF0 = bFc[0]; bF1 = bFc[1]; bF2 = bFc[2];
@@ -176,19 +179,18 @@ __device__ __forceinline__ void rhs_point_adjoint(const Cell<R>& c, const Phys<R
 // driver adjoints accumulated into thbar ([6][ny][nx]: A target x, y; v0
 // x, y; v1 x, y).  dux, duy point at D of u_x, u_y at (k = 0, j, i) and sz
 // is the z stride: the stateful ghost rows below sit at -m sz.  cf receives
-// the 46 coefficients.
+// the NCOEF coefficients; the value adjoint of A_x, A_y from the nudging,
+// -tau_A dt D, is left to the gather.
 template <typename R>
 __device__ __forceinline__ void adjoint_cell(const Cell<R>& c, const Phys<R>& ph, R w_, R wp, R (&wo)[NF], R dt,
                                              int k, int nz, const R* dux, const R* duy, long long sz,
                                              double* thbar, long long q2, long long n2, const StepState* ss, int sub,
                                              R (&cf)[NCOEF]) {
-  R vA0 = R(0), vA1 = R(0), vU0 = R(0), vU1 = R(0);
+  R vU0 = R(0), vU1 = R(0);
   if (ph.bcz == 0 && k == 0) {
     wo[UZ] = R(0);
     wo[LR] = R(0);
     // nudging: -tau_A (A_hor - A_target), -tau_u (u_hor - r v*)
-    vA0 = -ph.tau_A * wo[AX];
-    vA1 = -ph.tau_A * wo[AY];
     vU0 = -ph.tau_u * wo[UX];
     vU1 = -ph.tau_u * wo[UY];
     const double r = ss->r[sub], s = ss->s[sub];
@@ -207,8 +209,6 @@ __device__ __forceinline__ void adjoint_cell(const Cell<R>& c, const Phys<R>& ph
   }
   if (ph.bcz == 0 && k == nz - 1) wo[UZ] = R(0);
   rhs_point_adjoint<R>(c, ph, w_, wp, wo, cf);
-  cf[CV + AX] += vA0;
-  cf[CV + AY] += vA1;
   cf[CV + UX] += vU0;
   cf[CV + UY] += vU1;
 }

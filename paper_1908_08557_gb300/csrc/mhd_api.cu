@@ -44,7 +44,7 @@ struct mhd_ctx {
   void* fbar;          // state adjoint (padded)
   void* dbar;          // RK accumulator adjoint (padded)
   void* gbar;          // adjoint of the ghost-filled input of one RHS (padded)
-  void* coef;          // [46][nz][ny][nx] transposed-stencil coefficients
+  void* coef;          // [NCOEF_ADJ][nz][ny][nx] transposed-stencil coefficients
   double* thbar;       // [6][ny][nx] parameter adjoints (FP64)
   Background<float> bgf;
   Background<double> bgd;
@@ -890,7 +890,7 @@ static void adjoint_step_impl(mhd_ctx* h) {
   ghost_fill<R>(h, S[1]);
   launch_rk_any<R>(h, S[1], S[2], 1);
   ghost_fill<R>(h, S[2]);
-  h->nlaunch += 14;
+  h->nlaunch += 3;  // cfl finalize and the two RK substeps (ghost_fill counts its own)
   // reverse substeps
   FFTPlan fpa = h->fp;
   fpa.P = h->fp.Q;   // 9 packed ghost-adjoint planes
@@ -907,14 +907,14 @@ static void adjoint_step_impl(mhd_ctx* h) {
       launch_adj_point<R>(h->L, ph, bg, S[s], (const R*)h->dbar, (R*)h->coef, h->thbar, (const R*)h->wtab,
                           (const R*)h->wptab, h->ss, s, h->st);
     if (h->adj_tiled)
-      launch_adj_gather_tiled<R>(h->L, ph, (const R*)h->coef, (const R*)h->dbar, (R*)h->gbar, h->ss, h->st);
+      launch_adj_gather_tiled<R>(h->L, ph, (R*)h->coef, (const R*)h->dbar, (R*)h->gbar, h->ss, h->st);
     else
       launch_adj_gather<R>(h->L, ph, (const R*)h->coef, (const R*)h->dbar, (R*)h->gbar, h->ss, h->st);
     launch_adj_bc<R>(h->L, ph, bg, S[s], (R*)h->gbar, (R)h->p.dz, h->ss, h->st);
     launch_pfe_adjoint<R>(fpa, h->L, (R*)h->gbar, h->ss, h->st);
     launch_adj_update<R>(h->L, (R*)h->fbar, (R*)h->dbar, (const R*)h->gbar, rk_alpha(s), s > 0 ? rk_beta(s - 1) : 0.0,
                          1, h->ss, h->st);
-    h->nlaunch += 8;
+    h->nlaunch += h->adj_tiled ? 8 : 7;  // point, [fold], gather, bc, 3 FFT, update
   }
 }
 

@@ -59,13 +59,14 @@ void launch_adj_point_tiled(const CUtensorMap* tm, const Layout& L, const Phys<f
                             double dz, cudaStream_t st);
 int make_state_tensor_map(CUtensorMap* tm, const Layout& L, void* base);
 // adjoint (transposed linearisation of one substep)
-constexpr int NCOEF_ADJ = 46;
+constexpr int NCOEF_ADJ = 40;
 template <typename R> void launch_adj_point(const Layout& L, const Phys<R>& ph, const Background<R>& bg, const R* g,
                                             const R* dbar, R* coef, double* thbar, const R* wtab, const R* wptab,
                                             const StepState* ss, int sub, cudaStream_t st);
 template <typename R> void launch_adj_gather(const Layout& L, const Phys<R>& ph, const R* coef, const R* dbar,
                                              R* gbar, const StepState* ss, cudaStream_t st);
-template <typename R> void launch_adj_gather_tiled(const Layout& L, const Phys<R>& ph, const R* coef,
+// tiled gather; folds the in-plane grad-div terms into the coefficients first (coef is modified)
+template <typename R> void launch_adj_gather_tiled(const Layout& L, const Phys<R>& ph, R* coef,
                                                    const R* dbar, R* gbar, const StepState* ss, cudaStream_t st);
 template <typename R> void launch_adj_bc(const Layout& L, const Phys<R>& ph, const Background<R>& bg, const R* g,
                                          R* gbar, R dz, const StepState* ss, cudaStream_t st);

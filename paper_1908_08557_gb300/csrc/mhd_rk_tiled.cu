@@ -58,7 +58,7 @@ struct Args {
   int sub;
   int ntx, nty, nch, kchunk;
   // adjoint mode: D (adjoint of the RK accumulator, padded layout) in, the
-  // 46 coefficient fields ([46][nz][ny][nx]) and the driver adjoints out
+  // NCOEF coefficient fields ([NCOEF][nz][ny][nx]) and the driver adjoints out
   const float* dbar;
   float* coef;
   double* thbar;
@@ -195,7 +195,7 @@ __device__ __forceinline__ void front_plane(const Args& a, const FItems& it, con
 // ADJ = false: right-hand side + RK update of substep `sub` (sub < 0: store
 // the right-hand side only).  ADJ = true: the pointwise adjoint of substep
 // `sub` (the input is the ghost-filled substep state): per interior cell the
-// 46 coefficients of the transposed right-hand side, nothing else stored.
+// NCOEF coefficients of the transposed right-hand side, nothing else stored.
 template <bool ADJ>
 __global__ void __launch_bounds__(TILE, 1) rk_tiled_kernel(const __grid_constant__ CUtensorMap tm, const Args a) {
   extern __shared__ __align__(128) float smem[];
