@@ -265,8 +265,10 @@ __global__ void adj_bc_kernel(Layout L, Phys<R> ph, Background<R> bg, const R* _
 // Elementwise adjoint updates over the cells that carry state (interior, and
 // the u_x, u_y ghost layers below the photosphere), 16 bytes per thread and
 // row-contiguous (nx is a multiple of 4):
-//   mode 0, start of a step:  D = beta F   (D is zero between steps: alpha_0 = 0)
-//   mode 1, end of substep s: F += G;  D = alpha_s D + beta_{s-1} F  (beta = 0 for s = 0)
+//   mode 0, start of a sweep: D = beta_2 F
+//   mode 1, end of substep s: F += G;  D = alpha_s D + beta F, with beta = beta_{s-1},
+//           and for s = 0 (alpha_0 = 0) beta = beta_2: the next step's first update
+// Interior layers klo <= k < khi are skipped (the tiled gather updates them).
 template <typename R>
 struct Vec16;
 template <>
@@ -287,11 +289,11 @@ __device__ __forceinline__ R& vat(V& v, int e) {
 template <typename R>
 __global__ void __launch_bounds__(256) adj_update_kernel(Layout L, R* __restrict__ fbar, R* __restrict__ dbar,
                                                          const R* __restrict__ gbar, R alpha, R beta, int mode,
-                                                         const StepState* ss) {
+                                                         int klo, int khi, const StepState* ss) {
   using V = typename Vec16<R>::T;
   constexpr int E = Vec16<R>::N;
   if (halted(ss)) return;
-  const unsigned ny = L.ny, vpr = L.nx / E, nyz = (unsigned)L.nz * ny, ngy = NG * ny;
+  const unsigned ny = L.ny, vpr = L.nx / E, nyz = (unsigned)(L.nz - (khi - klo)) * ny, ngy = NG * ny;
   const unsigned nrow_int = NF * nyz;
   const unsigned nvec = (nrow_int + 2 * ngy) * vpr;
   for (unsigned q = blockIdx.x * blockDim.x + threadIdx.x; q < nvec; q += gridDim.x * blockDim.x) {
@@ -302,6 +304,7 @@ __global__ void __launch_bounds__(256) adj_update_kernel(Layout L, R* __restrict
       const unsigned r = row - f * nyz;
       k = r / ny;
       j = r - k * ny;
+      if (k >= klo) k += khi - klo;
     } else {
       unsigned r = row - nrow_int;
       const unsigned g = r / ngy;
@@ -448,8 +451,8 @@ void launch_adj_bc(const Layout& L, const Phys<R>& ph, const Background<R>& bg, 
 
 template <typename R>
 void launch_adj_update(const Layout& L, R* fbar, R* dbar, const R* gbar, double alpha, double beta, int mode,
-                       const StepState* ss, cudaStream_t st) {
-  adj_update_kernel<R><<<152 * 8, 256, 0, st>>>(L, fbar, dbar, gbar, (R)alpha, (R)beta, mode, ss);
+                       int klo, int khi, const StepState* ss, cudaStream_t st) {
+  adj_update_kernel<R><<<152 * 8, 256, 0, st>>>(L, fbar, dbar, gbar, (R)alpha, (R)beta, mode, klo, khi, ss);
 }
 
 template <typename R>
@@ -467,8 +470,8 @@ void launch_bz_plane(int nx, int ny, int nz, int k, double dx, double dy, const 
                                      cudaStream_t);                                                               \
   template void launch_adj_bc<R>(const Layout&, const Phys<R>&, const Background<R>&, const R*, R*, R,             \
                                  const StepState*, cudaStream_t);                                                 \
-  template void launch_adj_update<R>(const Layout&, R*, R*, const R*, double, double, int, const StepState*,        \
-                                     cudaStream_t);                                                               \
+  template void launch_adj_update<R>(const Layout&, R*, R*, const R*, double, double, int, int, int,              \
+                                     const StepState*, cudaStream_t);                                             \
   template void launch_bz_plane<R>(int, int, int, int, double, double, const R*, R*, int, const R*, R*,             \
                                    cudaStream_t);                                                                 \
   template void launch_adj_pack<R>(const Layout&, int, const R*, R*, cudaStream_t);                                \
@@ -501,11 +504,15 @@ namespace mhd {
 template <typename R>
 __global__ void __launch_bounds__(256) gd_fold_kernel(int nx, int ny, int nz, R* __restrict__ coef, R idx, R idy,
                                                       const StepState* ss) {
+  // each thread: E consecutive x points (one 16-byte vector; nx % 4 == 0)
+  using V = typename Vec16<R>::T;
+  constexpr int E = Vec16<R>::N;
+  constexpr int NV = (E + 8) / E;  // vectors covering x = i0 - 4 .. i0 + E + 3
   if (halted(ss)) return;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i0 = (blockIdx.x * blockDim.x + threadIdx.x) * E;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
   const int k = blockIdx.z;
-  if (i >= nx || j >= ny) return;
+  if (i0 >= nx || j >= ny) return;
   const long long n2 = (long long)nx * ny, n3 = n2 * nz;
   const long long row = (long long)k * n2 + (long long)j * nx;
   const R cw[4] = {R(0), W<R>::c1, W<R>::c2, W<R>::c3};
@@ -514,22 +521,51 @@ __global__ void __launch_bounds__(256) gd_fold_kernel(int nx, int ny, int nz, R*
     // gd(u) coefficients are the lap(u) ones divided by 3
     const int qg = grp == 0 ? CGA : CLU, qd = grp == 0 ? CDA : CDU;
     const R gs = grp == 0 ? R(1) : R(1.0 / 3.0);
-    const R* gx = coef + (long long)(qg + 0) * n3 + row;
-    const R* gy = coef + (long long)(qg + 1) * n3 + (long long)k * n2 + i;
-    R tx = R(0), ty = R(0);
+    // T_x = D1x^T gd_x at the thread's points; xs[m + 4] = gd_x at i0 + m
+    const R* gx = coef + (long long)qg * n3 + row;
+    R xs[NV * E];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      int i = i0 - 4 + v * E;
+      i = i < 0 ? i + nx : (i >= nx ? i - nx : i);
+      V w = __ldg(reinterpret_cast<const V*>(gx + i));
+#pragma unroll
+      for (int e = 0; e < E; ++e) xs[v * E + e] = vat<V, R>(w, e);
+    }
+    R tx[E], ty[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      R t = R(0);
+#pragma unroll
+      for (int m = 1; m <= 3; ++m) t += cw[m] * (xs[4 + e - m] - xs[4 + e + m]);
+      tx[e] = gs * idx * t;
+      ty[e] = R(0);
+    }
+    // T_y = D1y^T gd_y: rows j -+ m at the same x
+    const R* gy = coef + (long long)(qg + 1) * n3 + (long long)k * n2 + i0;
 #pragma unroll
     for (int m = 1; m <= 3; ++m) {
-      const int im = i - m < 0 ? i - m + nx : i - m, ip = i + m >= nx ? i + m - nx : i + m;
       const int jm = j - m < 0 ? j - m + ny : j - m, jp = j + m >= ny ? j + m - ny : j + m;
-      tx += cw[m] * (__ldg(gx + im) - __ldg(gx + ip));
-      ty += cw[m] * (__ldg(gy + (long long)jm * nx) - __ldg(gy + (long long)jp * nx));
+      V vm = __ldg(reinterpret_cast<const V*>(gy + (long long)jm * nx));
+      V vp = __ldg(reinterpret_cast<const V*>(gy + (long long)jp * nx));
+#pragma unroll
+      for (int e = 0; e < E; ++e) ty[e] += cw[m] * (vat<V, R>(vm, e) - vat<V, R>(vp, e));
     }
-    tx *= gs * idx;
-    ty *= gs * idy;
-    const long long c = row + i;
-    coef[(long long)(qd + 3 * 0 + 0) * n3 + c] += ty;       // D1x of component x <- T_y
-    coef[(long long)(qd + 3 * 1 + 1) * n3 + c] += tx;       // D1y of component y <- T_x
-    coef[(long long)(qd + 3 * 2 + 2) * n3 + c] += tx + ty;  // D1z of component z <- T_x + T_y
+    // D1x of component x <- T_y; D1y of component y <- T_x; D1z of component z <- T_x + T_y
+    V* cxx = reinterpret_cast<V*>(coef + (long long)(qd + 0) * n3 + row + i0);
+    V* cyy = reinterpret_cast<V*>(coef + (long long)(qd + 4) * n3 + row + i0);
+    V* czz = reinterpret_cast<V*>(coef + (long long)(qd + 8) * n3 + row + i0);
+    V vx = *cxx, vy = *cyy, vz = *czz;
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const R yy = gs * idy * ty[e];
+      vat<V, R>(vx, e) += yy;
+      vat<V, R>(vy, e) += tx[e];
+      vat<V, R>(vz, e) += tx[e] + yy;
+    }
+    *cxx = vx;
+    *cyy = vy;
+    *czz = vz;
   }
 }
 
@@ -547,8 +583,11 @@ struct GArgs {
   Layout L;
   Phys<R> ph;
   const R* coef;
-  const R* dbar;
+  R* dbar;
   R* gbar;
+  R* fbar;
+  R alpha, beta;     // the substep's update, applied here on layers klo <= k < khi
+  int klo, khi;
   const StepState* ss;
   int ntx, nty, ntz;
 };
@@ -709,6 +748,62 @@ __device__ __forceinline__ void add_to(R (&acc)[NO][TZ], int f, const R (&r)[TZ]
   }
 }
 
+// Output of one thread's column: on layers klo <= k < khi the substep's
+// update F += G, D = alpha D + beta F (loads of a pair of z points issued
+// before their stores: fb, db, gb do not alias); elsewhere G (with the
+// nudging value adjoints, Eqs. 4 and 5: A_x, A_y at the photosphere and the
+// stateful u_x, u_y ghost rows below it) into gbar.
+template <typename R, int NO>
+__device__ __forceinline__ void epilogue_rows(const Layout& L, const Phys<R>& ph, R* __restrict__ fb,
+                                              R* __restrict__ db, R* __restrict__ gb, R alpha, R beta, R dt,
+                                              int klo, int khi, const R (&acc)[NO][TZ], int grp, int z0, int j,
+                                              int i) {
+#pragma unroll
+  for (int z2 = 0; z2 < TZ; z2 += 2) {
+    R fo[2][NO], dd[2][NO];
+    long long qq[2][NO];
+    bool fz[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int k = z0 + z2 + h;
+      fz[h] = k >= klo && k < khi;
+#pragma unroll
+      for (int l = 0; l < NO; ++l) {
+        const int f = grp == 0 ? (l < 3 ? AX + l : LR) : (l < 3 ? UX + l : LT);
+        qq[h][l] = L.at(f, k, j, i);
+        fo[h][l] = fz[h] ? fb[qq[h][l]] : R(0);
+        dd[h][l] = (fz[h] || (ph.bcz == 0 && k <= 0)) ? db[qq[h][l]] : R(0);
+      }
+    }
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int k = z0 + z2 + h;
+      if (k >= L.nz + NG) break;
+#pragma unroll
+      for (int l = 0; l < NO; ++l) {
+        const int f = grp == 0 ? (l < 3 ? AX + l : LR) : (l < 3 ? UX + l : LT);
+        const R v = acc[l][z2 + h];
+        if (fz[h]) {
+          const R fv = fo[h][l] + v;
+          fb[qq[h][l]] = fv;
+          db[qq[h][l]] = alpha * dd[h][l] + beta * fv;
+        } else {
+          R g = v;
+          if (ph.bcz == 0 && ((k == 0 && (f == AX || f == AY)) || (k < 0 && (f == UX || f == UY))))
+            g -= (f == AX || f == AY ? ph.tau_A : ph.tau_u) * dt * dd[h][l];
+          gb[qq[h][l]] = g;
+        }
+      }
+    }
+  }
+}
+
+template <typename R, int NO>
+__device__ __forceinline__ void epilogue(const GArgs<R>& a, const R (&acc)[NO][TZ], int grp, int z0, int j, int i) {
+  epilogue_rows<R, NO>(a.L, a.ph, a.fbar, a.dbar, a.gbar, a.alpha, a.beta, R(a.ss->dt), a.klo, a.khi, acc, grp, z0,
+                       j, i);
+}
+
 // Each block owns one output group (blockIdx.x & 1: {A, ln rho} or {u, ln T})
 // of a tile; NB staging buffers give a prefetch distance of NB - 1 stages.
 template <typename R, int NB, int MINB>
@@ -819,39 +914,27 @@ __global__ void __launch_bounds__(256, MINB) gather_tiled_kernel(GArgs<R> a) {
 
   const int i = x0 + tx, j = y0 + ty;
   if (i >= nx || j >= ny) return;
-  const R dt = R(a.ss->dt);
-#pragma unroll
-  for (int zz = 0; zz < TZ; ++zz) {
-    const int k = z0 + zz;
-    if (k >= nz + NG) break;
-#pragma unroll
-    for (int l = 0; l < NO; ++l) {
-      const int f = grp == 0 ? (l < 3 ? AX + l : LR) : (l < 3 ? UX + l : LT);
-      const long long q = L.at(f, k, j, i);
-      R v = acc[l][zz];
-      // nudging value adjoints (Eqs. 4, 5): A_x, A_y at the photosphere and
-      // the stateful u_x, u_y ghost rows below it
-      if (ph.bcz == 0 && ((k == 0 && (f == AX || f == AY)) || (k < 0 && (f == UX || f == UY))))
-        v -= (f == AX || f == AY ? ph.tau_A : ph.tau_u) * dt * a.dbar[q];
-      a.gbar[q] = v;
-    }
-  }
+  epilogue<R, NO>(a, acc, grp, z0, j, i);
 }
 
 }  // namespace gtile
 
+// chunk offsets are 32-bit; rows must split into 16-byte chunks
+bool adj_gather_tiled_ok(const Layout& L) { return (long long)L.nx * L.ny * L.nz < (1LL << 31) && L.nx % 4 == 0; }
+
 template <typename R>
-void launch_adj_gather_tiled(const Layout& L, const Phys<R>& ph, R* coef, const R* dbar, R* gbar,
-                             const StepState* ss, cudaStream_t st) {
-  // chunk offsets are 32-bit; rows must split into 16-byte chunks
-  if ((long long)L.nx * L.ny * L.nz >= (1LL << 31) || L.nx % 4 != 0) {
-    launch_adj_gather<R>(L, ph, coef, dbar, gbar, ss, st);
-    return;
+void launch_adj_gather_tiled(const Layout& L, const Phys<R>& ph, R* coef, R* dbar, R* gbar, R* fbar, double alpha,
+                             double beta, int klo, int khi, const StepState* ss, cudaStream_t st) {
+  {
+    constexpr int E = Vec16<R>::N;
+    const int tpx = L.nx / E;                       // threads per row
+    const int bx = tpx < 64 ? tpx : 64, by = 256 / bx;
+    gd_fold_kernel<R><<<dim3((tpx + bx - 1) / bx, (L.ny + by - 1) / by, L.nz), dim3(bx, by), 0, st>>>(
+        L.nx, L.ny, L.nz, coef, ph.idx, ph.idy, ss);
   }
-  gd_fold_kernel<R><<<dim3((L.nx + 31) / 32, (L.ny + 7) / 8, L.nz), dim3(32, 8), 0, st>>>(
-      L.nx, L.ny, L.nz, coef, ph.idx, ph.idy, ss);
   gtile::GArgs<R> a;
   a.L = L; a.ph = ph; a.coef = coef; a.dbar = dbar; a.gbar = gbar; a.ss = ss;
+  a.fbar = fbar; a.alpha = (R)alpha; a.beta = (R)beta; a.klo = klo; a.khi = khi;
   a.ntx = (L.nx + gtile::TX - 1) / gtile::TX;
   a.nty = (L.ny + gtile::TY - 1) / gtile::TY;
   a.ntz = (L.nz + 2 * NG + gtile::TZ - 1) / gtile::TZ;
@@ -864,9 +947,9 @@ void launch_adj_gather_tiled(const Layout& L, const Phys<R>& ph, R* coef, const 
   k<<<2 * nblk, blk, smem, st>>>(a);
 }
 
-template void launch_adj_gather_tiled<float>(const Layout&, const Phys<float>&, float*, const float*, float*,
-                                             const StepState*, cudaStream_t);
-template void launch_adj_gather_tiled<double>(const Layout&, const Phys<double>&, double*, const double*,
-                                              double*, const StepState*, cudaStream_t);
+template void launch_adj_gather_tiled<float>(const Layout&, const Phys<float>&, float*, float*, float*, float*,
+                                             double, double, int, int, const StepState*, cudaStream_t);
+template void launch_adj_gather_tiled<double>(const Layout&, const Phys<double>&, double*, double*, double*,
+                                              double*, double, double, int, int, const StepState*, cudaStream_t);
 
 }  // namespace mhd

@@ -870,8 +870,16 @@ extern "C" int mhd_adjoint_init(mhd_handle h, const void* lam, int mem) {
   if (!rc) rc = cuda_check(h, cudaMemcpyAsync(h->gbar, lam, (size_t)NF * h->p.nx * h->p.ny * h->p.nz * h->esz,
                                               kind_in(mem), h->st), "copy lam");
   if (rc) return rc;
-  if (h->esz == 8) launch_adj_unpack<double>(h->L, (const double*)h->gbar, (double*)h->fbar, h->st);
-  else launch_adj_unpack<float>(h->L, (const float*)h->gbar, (float*)h->fbar, h->st);
+  if (h->esz == 8) {
+    launch_adj_unpack<double>(h->L, (const double*)h->gbar, (double*)h->fbar, h->st);
+    launch_adj_update<double>(h->L, (double*)h->fbar, (double*)h->dbar, nullptr, 0.0, rk_beta(2), 0, 0, 0, h->ss,
+                              h->st);
+  } else {
+    launch_adj_unpack<float>(h->L, (const float*)h->gbar, (float*)h->fbar, h->st);
+    launch_adj_update<float>(h->L, (float*)h->fbar, (float*)h->dbar, nullptr, 0.0, rk_beta(2), 0, 0, 0, h->ss,
+                             h->st);
+  }
+  h->nlaunch += 2;
   rc = cuda_check(h, cudaSuccess, "adjoint init");
   if (!rc && mem == MHD_MEM_HOST) rc = cuda_check(h, cudaStreamSynchronize(h->st), "init synchronize");
   return rc;
@@ -895,10 +903,21 @@ static void adjoint_step_impl(mhd_ctx* h) {
   FFTPlan fpa = h->fp;
   fpa.P = h->fp.Q;   // 9 packed ghost-adjoint planes
   fpa.Q = h->fp.P;   // 3 summed planes
-  launch_adj_update<R>(h->L, (R*)h->fbar, (R*)h->dbar, (const R*)h->gbar, 0.0, rk_beta(2), 0, h->ss, h->st);
-  h->nlaunch += 1;
+  // tiled gather: it applies the update itself on the layers no ghost rule
+  // feeds back into (the ghost-rule transposes touch k < 4 and k >= nz - 4)
+  const bool tg = h->adj_tiled && adj_gather_tiled_ok(h->L);
+  int klo = 0, khi = 0;
+  if (tg && h->p.nz - NG - 1 > NG + 1) {
+    klo = NG + 1;
+    khi = h->p.nz - NG - 1;
+  }
+  // Between reverse steps D already holds beta_2 F, the first update of the
+  // next step: alpha_0 = 0 makes the accumulator's own adjoint vanish at a
+  // step boundary, so the last substep leaves D = beta_2 F (and
+  // mhd_adjoint_init starts from D = beta_2 lam).
   const int tmi[3] = {h->cur, 1 - h->cur, 2};
   for (int s = 2; s >= 0; --s) {
+    const double alpha = rk_alpha(s), beta = rk_beta(s > 0 ? s - 1 : 2);
     if (sizeof(R) == 4 && h->tiled && h->adj_tiled)
       launch_adj_point_tiled(&h->tm[tmi[s]], h->L, *(const Phys<float>*)&ph, h->bgf, (const float*)h->dbar,
                              (float*)h->coef, h->thbar, (const float*)h->wtab, (const float*)h->wptab, h->ss, s,
@@ -906,15 +925,15 @@ static void adjoint_step_impl(mhd_ctx* h) {
     else
       launch_adj_point<R>(h->L, ph, bg, S[s], (const R*)h->dbar, (R*)h->coef, h->thbar, (const R*)h->wtab,
                           (const R*)h->wptab, h->ss, s, h->st);
-    if (h->adj_tiled)
-      launch_adj_gather_tiled<R>(h->L, ph, (R*)h->coef, (const R*)h->dbar, (R*)h->gbar, h->ss, h->st);
+    if (tg)
+      launch_adj_gather_tiled<R>(h->L, ph, (R*)h->coef, (R*)h->dbar, (R*)h->gbar, (R*)h->fbar, alpha, beta, klo, khi,
+                                 h->ss, h->st);
     else
       launch_adj_gather<R>(h->L, ph, (const R*)h->coef, (const R*)h->dbar, (R*)h->gbar, h->ss, h->st);
     launch_adj_bc<R>(h->L, ph, bg, S[s], (R*)h->gbar, (R)h->p.dz, h->ss, h->st);
     launch_pfe_adjoint<R>(fpa, h->L, (R*)h->gbar, h->ss, h->st);
-    launch_adj_update<R>(h->L, (R*)h->fbar, (R*)h->dbar, (const R*)h->gbar, rk_alpha(s), s > 0 ? rk_beta(s - 1) : 0.0,
-                         1, h->ss, h->st);
-    h->nlaunch += h->adj_tiled ? 8 : 7;  // point, [fold], gather, bc, 3 FFT, update
+    launch_adj_update<R>(h->L, (R*)h->fbar, (R*)h->dbar, (const R*)h->gbar, alpha, beta, 1, klo, khi, h->ss, h->st);
+    h->nlaunch += tg ? 8 : 7;  // point, [fold], gather, bc, 3 FFT, update
   }
 }
 

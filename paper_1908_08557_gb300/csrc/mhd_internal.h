@@ -65,15 +65,21 @@ template <typename R> void launch_adj_point(const Layout& L, const Phys<R>& ph, 
                                             const StepState* ss, int sub, cudaStream_t st);
 template <typename R> void launch_adj_gather(const Layout& L, const Phys<R>& ph, const R* coef, const R* dbar,
                                              R* gbar, const StepState* ss, cudaStream_t st);
-// tiled gather; folds the in-plane grad-div terms into the coefficients first (coef is modified)
-template <typename R> void launch_adj_gather_tiled(const Layout& L, const Phys<R>& ph, R* coef,
-                                                   const R* dbar, R* gbar, const StepState* ss, cudaStream_t st);
+// tiled gather (needs adj_gather_tiled_ok): folds the in-plane grad-div terms into the
+// coefficients first (coef is modified); on layers klo <= k < khi it also applies the
+// substep's update F += G, D = alpha D + beta F, elsewhere it stores G in gbar
+bool adj_gather_tiled_ok(const Layout& L);
+template <typename R> void launch_adj_gather_tiled(const Layout& L, const Phys<R>& ph, R* coef, R* dbar, R* gbar,
+                                                   R* fbar, double alpha, double beta, int klo, int khi,
+                                                   const StepState* ss, cudaStream_t st);
 template <typename R> void launch_adj_bc(const Layout& L, const Phys<R>& ph, const Background<R>& bg, const R* g,
                                          R* gbar, R dz, const StepState* ss, cudaStream_t st);
-// adjoint elementwise updates (mode 0: D = beta F; mode 1: F += G, D = alpha D + beta F);
-// nx must be a multiple of 4 and NF * (nz + 6) * ny * nx / 4 < 2^31
+// adjoint elementwise updates (mode 0: D = beta F; mode 1: F += G, D = alpha D + beta F),
+// skipping interior layers klo <= k < khi; nx must be a multiple of 4 and
+// NF * (nz + 6) * ny * nx / 4 < 2^31
 template <typename R> void launch_adj_update(const Layout& L, R* fbar, R* dbar, const R* gbar, double alpha,
-                                             double beta, int mode, const StepState* ss, cudaStream_t st);
+                                             double beta, int mode, int klo, int khi, const StepState* ss,
+                                             cudaStream_t st);
 template <typename R> void launch_bz_plane(int nx, int ny, int nz, int k, double dx, double dy, const R* st_in,
                                            R* out, int adjoint, const R* bbar, R* lam, cudaStream_t st);
 template <typename R> void launch_adj_pack(const Layout& L, int bcz, const R* fbar, R* out, cudaStream_t st);
