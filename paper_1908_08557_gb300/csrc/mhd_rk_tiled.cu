@@ -157,6 +157,8 @@ __device__ __forceinline__ FItems make_items(int tid) {
 }
 
 // front processing of one plane: the z-mixed sources and the xy-mixed terms
+// (WU = false: A only -- the adjoint reads no second derivative of u)
+template <bool WU>
 __device__ __forceinline__ void front_plane(const Args& a, const FItems& it, const float* __restrict__ P,
                                             float* __restrict__ D, float* __restrict__ M, float* __restrict__ wy,
                                             float* __restrict__ wx, int cen, int tx, int ty) {
@@ -167,17 +169,19 @@ __device__ __forceinline__ void front_plane(const Args& a, const FItems& it, con
     if (t < it.n) {
       if (it.isy[t]) {
         wy[it.dst[t]] = D1(P + AY * BY * BX + it.src[t], BX, a.c1y, a.c2y, a.c3y);
-        wy[TY * WYW + it.dst[t]] = D1(P + UY * BY * BX + it.src[t], BX, a.c1y, a.c2y, a.c3y);
+        if (WU) wy[TY * WYW + it.dst[t]] = D1(P + UY * BY * BX + it.src[t], BX, a.c1y, a.c2y, a.c3y);
       } else {
         wx[it.dst[t]] = D1(P + AX * BY * BX + it.src[t], 1, a.c1x, a.c2x, a.c3x);
-        wx[WXH * TX + it.dst[t]] = D1(P + UX * BY * BX + it.src[t], 1, a.c1x, a.c2x, a.c3x);
+        if (WU) wx[WXH * TX + it.dst[t]] = D1(P + UX * BY * BX + it.src[t], 1, a.c1x, a.c2x, a.c3x);
       }
     }
   }
   D[0 * TILE] = D1(P + AZ * BY * BX + cen, 1, a.c1x, a.c2x, a.c3x);
   D[1 * TILE] = D1(P + AZ * BY * BX + cen, BX, a.c1y, a.c2y, a.c3y);
-  D[3 * TILE] = D1(P + UZ * BY * BX + cen, 1, a.c1x, a.c2x, a.c3x);
-  D[4 * TILE] = D1(P + UZ * BY * BX + cen, BX, a.c1y, a.c2y, a.c3y);
+  if (WU) {
+    D[3 * TILE] = D1(P + UZ * BY * BX + cen, 1, a.c1x, a.c2x, a.c3x);
+    D[4 * TILE] = D1(P + UZ * BY * BX + cen, BX, a.c1y, a.c2y, a.c3y);
+  }
   __syncthreads();
   // F2: D1x(D1y A_y), D1y(D1x A_x), D1x(D1y u_y), D1y(D1x u_x);
   // D1x A_x + D1y A_y and D1x u_x + D1y u_y
@@ -185,10 +189,12 @@ __device__ __forceinline__ void front_plane(const Args& a, const FItems& it, con
   const float* wxc = wx + (ty + 3) * TX + tx;
   M[0 * TILE] = D1(wyc, 1, a.c1x, a.c2x, a.c3x);
   M[1 * TILE] = D1(wxc, TX, a.c1y, a.c2y, a.c3y);
-  M[2 * TILE] = D1(wyc + TY * WYW, 1, a.c1x, a.c2x, a.c3x);
-  M[3 * TILE] = D1(wxc + WXH * TX, TX, a.c1y, a.c2y, a.c3y);
   D[2 * TILE] = wxc[0] + wyc[0];
-  D[5 * TILE] = wxc[WXH * TX] + wyc[TY * WYW];
+  if (WU) {
+    M[2 * TILE] = D1(wyc + TY * WYW, 1, a.c1x, a.c2x, a.c3x);
+    M[3 * TILE] = D1(wxc + WXH * TX, TX, a.c1y, a.c2y, a.c3y);
+    D[5 * TILE] = wxc[WXH * TX] + wyc[TY * WYW];
+  }
   __syncthreads();
 }
 
@@ -257,7 +263,7 @@ __global__ void __launch_bounds__(TILE, 1) rk_tiled_kernel(const __grid_constant
     if (!bad) {                                                                                     \
       phase ^= 1u << s__;                                                                           \
       pending &= ~(1u << s__);                                                                      \
-      front_plane(a, items, raw + s__ * PLANE, dring + ((p__ - pbase) % NDR) * NDZ * TILE + tid,     \
+      front_plane<!ADJ>(a, items, raw + s__ * PLANE, dring + ((p__ - pbase) % NDR) * NDZ * TILE + tid, \
                   mring + ((p__ - pbase) & (NMR - 1)) * NMX * TILE + tid, wy, wx, cenoff, tx, ty);  \
     }                                                                                               \
   }
@@ -304,7 +310,7 @@ __global__ void __launch_bounds__(TILE, 1) rk_tiled_kernel(const __grid_constant
                    a.e3z * (Pz6[o] + Pz0[o]);
         }
         // D1z of the z-mixed sources
-        float mz[NDZ];
+        float mz[NDZ] = {};
         {
           // ring slots of planes k-3 .. k+3 (kr - 3 >= 0 here)
           const float* const Dm3 = dring + ((kr - 3) % NDR) * NDZ * TILE + tid;
@@ -314,7 +320,7 @@ __global__ void __launch_bounds__(TILE, 1) rk_tiled_kernel(const __grid_constant
           const float* const Dp2 = dring + ((kr + 2) % NDR) * NDZ * TILE + tid;
           const float* const Dp3 = dring + ((kr + 3) % NDR) * NDZ * TILE + tid;
 #pragma unroll
-          for (int q = 0; q < NDZ; ++q) {
+          for (int q = 0; q < (ADJ ? 3 : NDZ); ++q) {
             const int o = q * TILE;
             mz[q] = a.c1z * (Dp1[o] - Dm1[o]) + a.c2z * (Dp2[o] - Dm2[o]) + a.c3z * (Dp3[o] - Dm3[o]);
           }
@@ -337,9 +343,15 @@ __global__ void __launch_bounds__(TILE, 1) rk_tiled_kernel(const __grid_constant
         c.gdA[0] = xx_[AX] + Mk[0 * TILE] + mz[0];
         c.gdA[1] = Mk[1 * TILE] + yy_[AY] + mz[1];
         c.gdA[2] = mz[2] + zz_[AZ];
-        c.gdU[0] = xx_[UX] + Mk[2 * TILE] + mz[3];
-        c.gdU[1] = Mk[3 * TILE] + yy_[UY] + mz[4];
-        c.gdU[2] = mz[5] + zz_[UZ];
+        if (ADJ) {
+          // the adjoint reads no second derivative of u (its coefficients are
+          // nu times the output adjoint); the front skipped them
+          c.gdU[0] = c.gdU[1] = c.gdU[2] = 0.f;
+        } else {
+          c.gdU[0] = xx_[UX] + Mk[2 * TILE] + mz[3];
+          c.gdU[1] = Mk[3 * TILE] + yy_[UY] + mz[4];
+          c.gdU[2] = mz[5] + zz_[UZ];
+        }
         c.L = a.bg.lbar[k + NG] + v_[LR];
         c.Th = a.bg.tbar[k + NG] + v_[LT];
         c.gL[0] = dx_[LR];
