@@ -314,11 +314,18 @@ def test_production_geometry_1024_sampled(prec):
     axt, ayt = oracle.a_target_fft(p, case.bz)
     ref = oracle.rhs_cells(p, u, cast(axt), cast(ayt), cast(case.v0), cast(case.v1), case.t0, case.t1, t, cells)
     g = rhs[:, ks + NG, js + NG, iss + NG].T.astype(np.float64)
-    # FP32 bound from the arithmetic: |A| reaches ~100 here (flux of the
-    # sigma = 40-cell pair over dx = 4); FP32 second differences of A carry
-    # ~6e-8 * 100 * sum|w2| (~6) / dz^2 = 4e-5 absolute, entering dA/dt with
-    # eta_s w <= 0.5 in the swamp: ~2e-5 against an RHS scale of ~0.1.
+    # FP32 bound from the arithmetic: |A| reaches several hundred here (the
+    # sigma = 40-cell pair's flux over dx = 4); an FP32 second difference of
+    # A in z carries up to u * max|A| * sum|w2| / dz^2 (u = 2^-24, sum|w2| =
+    # 6.04) of rounding, which enters dA/dt through eta J and the swamp term
+    # eta_s w lap A (w <= 1): that bound, with a factor 3, is the absolute
+    # tolerance of the A rows; the other rows take 1e-3 of their scale.
+    amax = np.abs(st[0:3]).max()
+    a_abs = 3.0 * 2.0 ** -24 * amax * 6.04 / p["dz"] ** 2 * (p["eta"] + p["eta_swamp"])
     tol = 1e-10 if prec == 64 else 1e-3
     for f in range(8):
         s = np.abs(ref[:, f]).max()
-        assert np.abs(g[:, f] - ref[:, f]).max() <= tol * max(s, 1e-30), (f, np.abs(g[:, f] - ref[:, f]).max(), s)
+        bound = tol * max(s, 1e-30)
+        if prec == 32 and f < 3:
+            bound = max(bound, a_abs)
+        assert np.abs(g[:, f] - ref[:, f]).max() <= bound, (f, np.abs(g[:, f] - ref[:, f]).max(), s, bound)
