@@ -295,6 +295,10 @@ WORKLOADS = {
                               n_mag=8, driver="noise", nsteps=100),
     "bipoles100_512x512x256": dict(nx=512, ny=512, nz=256, magnetogram="bipoles",
                                    n_mag=100, driver="solenoidal", nsteps=1000),
+    # the 256^3 recipe at an eighth of the volume: profiler captures of the
+    # adjoint kernels (coefficient fields 0.34 GB, above the 129 MB L2)
+    "bipoles20_128x128x128": dict(nx=128, ny=128, nz=128, magnetogram="bipoles",
+                                  n_mag=20, driver="solenoidal", nsteps=200),
 }
 
 

@@ -357,7 +357,7 @@ static void run_stats(mhd_ctx* h, R* f) {
   Phys<R> ph = make_phys<R>(&h->p);
   ClassTimer ct(h, MHD_KC_STATS, 2);
   int nb = launch_stats_partial<R>(h->L, ph, bgr<R>(h), f, h->red, h->ss, h->st);
-  launch_stats_finalize(h->red, nb, h->ss, h->p.dx * h->p.dy * h->p.dz, h->p.dx * h->p.dy, h->st);
+  launch_stats_finalize(h->red, nb, h->ss, h->p.dx * h->p.dy * h->p.dz, h->p.dx * h->p.dy, h->p.gamma - 1.0, h->st);
 }
 
 // fused RHS + RK launch: TMA-fed z-march for FP32 (unless disabled), the

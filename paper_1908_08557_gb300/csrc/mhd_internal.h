@@ -99,7 +99,7 @@ void launch_cfl_finalize(const double* partial, int nblk, StepState* ss, double 
 template <typename R> int launch_stats_partial(const Layout& L, const Phys<R>& ph, const Background<R>& bg,
                                                const R* f,
                                                double* partial, StepState* ss, cudaStream_t st);
-void launch_stats_finalize(const double* partial, int nblk, StepState* ss, double dv, double da,
+void launch_stats_finalize(const double* partial, int nblk, StepState* ss, double dv, double da, double gm1,
                            cudaStream_t st);
 // pack / unpack interior <-> padded
 // (the background is added on the way out and removed on the way in)

@@ -22,7 +22,7 @@ __device__ __forceinline__ double warp_sum(double v) {
 // grid over (x tiles, y tiles, z chunks); each thread walks its z chunk
 static inline dim3 red_grid(const Layout& L, int* kchunk) {
   int tx = (L.nx + 31) / 32, ty = (L.ny + 7) / 8;
-  int zc = 1216 / (tx * ty);
+  int zc = 4096 / (tx * ty);  // enough blocks to keep every SM's loads in flight
   if (zc < 1) zc = 1;
   if (zc > L.nz) zc = L.nz;
   if (tx * ty * zc > RED_BLOCKS_MAX) zc = RED_BLOCKS_MAX / (tx * ty) > 0 ? RED_BLOCKS_MAX / (tx * ty) : 1;
@@ -56,10 +56,13 @@ __global__ void __launch_bounds__(256) cfl_partial_kernel(Layout L, Phys<R> ph, 
   __shared__ double sa[8], sd[8];
   const int i = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y * 8 + threadIdx.y;
   const int tid = threadIdx.y * 32 + threadIdx.x;
-  double ma = 0.0, md = 0.0;
+  // per-thread maxima in the state precision (conversion to FP64 is exact and
+  // monotonic, so converting the maximum equals the maximum of conversions)
+  R mar = R(0), mdr = R(0);
   bool bad = false;
   if (i < L.nx && j < L.ny && !halted(ss)) {
     const int k0 = blockIdx.z * kchunk, k1 = min(L.nz, k0 + kchunk);
+#pragma unroll 2
     for (int k = k0; k < k1; ++k) {
       R B[3];
       bfield<R>(L, ph, f, k, j, i, B);
@@ -74,13 +77,13 @@ __global__ void __launch_bounds__(256) cfl_partial_kernel(Layout L, Phys<R> ph, 
       dm = fmax(dm, ph.eta + ph.eta_s * w);
       dm = fmax(dm, ph.drho + ph.drho_s * w);
       dm = fmax(dm, ph.chi_s * w + ph.gm1 * ph.kappa0 * rexp<R>(R(2.5) * lt - lr));
-      const double a = (double)adv, d = (double)dm;
-      if (!isfinite(a) || !isfinite(d)) bad = true;
-      ma = fmax(ma, a);
-      md = fmax(md, d);
+      if (!isfinite(adv) || !isfinite(dm)) bad = true;
+      mar = fmax(mar, adv);
+      mdr = fmax(mdr, dm);
     }
   }
   if (bad) atomicOr(&ss->nonfinite, 1);
+  double ma = (double)mar, md = (double)mdr;
   ma = warp_max(ma);
   md = warp_max(md);
   if ((tid & 31) == 0) { sa[tid >> 5] = ma; sd[tid >> 5] = md; }
@@ -175,7 +178,7 @@ __global__ void __launch_bounds__(256) stats_partial_kernel(Layout L, Phys<R> ph
       const R T = rexp<R>(bg.tbar[k + NG] + f[L.at(LT, k, j, i)]);
       acc[0] += (double)(R(0.5) * rho * (ux * ux + uy * uy + uz * uz));
       acc[1] += (double)(R(0.5) * (B[0] * B[0] + B[1] * B[1] + B[2] * B[2]));
-      acc[2] += (double)(rho * T) / (double)ph.gm1;
+      acc[2] += (double)(rho * T);  // / (gamma - 1) once, in the finalize
       acc[3] += (double)rho;
       if (k == 0) {
         acc[4] += (double)B[2];
@@ -235,7 +238,8 @@ int launch_stats_partial(const Layout& L, const Phys<R>& ph, const Background<R>
 
 // fixed-order sums over the block partials; volume sums scaled by dV, the
 // photospheric flux sums by dA
-__global__ void stats_finalize_kernel(const double* partial, int nblk, StepState* ss, double dv, double da) {
+__global__ void stats_finalize_kernel(const double* partial, int nblk, StepState* ss, double dv, double da,
+                                      double gm1) {
   __shared__ double sm[256][7];
   double acc[7] = {0, 0, 0, 0, 0, 0, 0};
   for (int b = threadIdx.x; b < nblk; b += blockDim.x) {
@@ -252,7 +256,7 @@ __global__ void stats_finalize_kernel(const double* partial, int nblk, StepState
     __syncthreads();
   }
   if (threadIdx.x == 0) {
-    const double sc[7] = {dv, dv, dv, dv, da, da, 1.0};
+    const double sc[7] = {dv, dv, dv / gm1, dv, da, da, 1.0};
     bool bad = false;
     for (int q = 0; q < 7; ++q) {
       ss->stats[q] = sm[0][q] * sc[q];
@@ -263,9 +267,9 @@ __global__ void stats_finalize_kernel(const double* partial, int nblk, StepState
   }
 }
 
-void launch_stats_finalize(const double* partial, int nblk, StepState* ss, double dv, double da,
+void launch_stats_finalize(const double* partial, int nblk, StepState* ss, double dv, double da, double gm1,
                            cudaStream_t st) {
-  stats_finalize_kernel<<<1, 256, 0, st>>>(partial, nblk, ss, dv, da);
+  stats_finalize_kernel<<<1, 256, 0, st>>>(partial, nblk, ss, dv, da, gm1);
 }
 
 #define INST(R)                                                                                        \
