@@ -29,6 +29,8 @@ sys.path.insert(0, ROOT)
 METRIC = "MHD cell-updates/s per RK step"
 UNIT = "cell-updates/s"
 WORDS_PER_CELL_STEP = 80  # algorithmic state words moved per cell per RK3 step
+RK_KERNEL = ("pass_a_kernel + pass_r_kernel (split TMA z-march: B, J and swamp terms from A; "
+             "physics, nudging and RK update), per substep")
 
 
 def parse():
@@ -151,8 +153,7 @@ def rk_traffic_bytes():
             if line.strip() and not line.startswith("#"):
                 k, v = line.split(None, 1)
                 kv[k] = v.strip()
-        blob = open(os.path.join(csrc, "mhd_rk_tiled.cu"), "rb").read() + \
-            open(os.path.join(csrc, "mhd_common.cuh"), "rb").read()
+        blob = b"".join(open(os.path.join(csrc, f), "rb").read() for f in kv["sources"].split())
         sha = hashlib.sha256(blob).hexdigest()[:16]
         if kv.get("kernel_source_sha") != sha:
             return None
@@ -365,7 +366,7 @@ def run_native(args, ws, rank, local):
     peaks = measured_peaks()
     peak = peaks["hbm_gbs"] if peaks and "hbm_gbs" in peaks else 6800.0
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": rk_traffic_bytes(), "kernel": "rk_tiled_kernel (fused RHS + RK update, TMA z-march)",
+                "traffic": rk_traffic_bytes(), "kernel": RK_KERNEL,
                 "peak_source": "measured" if peaks else "fallback",
                 "alg_bytes_per_launch": alg_bytes_per_launch, "avg_launch_ms": rk_ms / rk_n,
                 "class_ms_per_step": {k: v[0] / nprof for k, v in prof.items()}}

@@ -17,7 +17,13 @@ using namespace mhd;
 struct mhd_ctx {
   CUtensorMap tm[3];   // TMA descriptors of the two FP32 state sets and of the adjoint's
                        // third substep state (64-byte aligned)
-  bool tiled;          // FP32: TMA-fed z-march kernel; otherwise the simple kernel
+  CUtensorMap tma[2];  // the two state sets, boxes of A only (split pass A)
+  CUtensorMap tmr[2];  // the two state sets, boxes of u, ln rho, ln T (split pass R)
+  bool tiled;          // FP32: TMA-fed z-march kernels; otherwise the simple kernel
+  bool split;          // FP32 forward: split passes (else the fused z-march kernel)
+  void* bj;            // split: [6][nz][ny][nx] B, J of the current substep
+  void* sw;            // split: [3][nz - ksw][ny][nx] swamp terms
+  int ksw;             // first layer with a nonzero swamp weight or slope (nz if none)
   bool adj_tiled;      // adjoint: tiled gather and (FP32) z-march point kernel, else one thread per point
   mhd_params p;
   Layout L;
@@ -147,11 +153,23 @@ struct Carve {
 };
 
 struct Offsets {
-  size_t f0, f1, df, lnrho0, wtab, wptab, bz, axt, ayt, v0, v1, red, ss, bg;
+  size_t f0, f1, df, lnrho0, wtab, wptab, bz, axt, ayt, v0, v1, red, ss, bg, bj, sw;
   size_t s2, fbar, dbar, gbar, coef, thbar;
   size_t twx, twy, et, eb, ktx, kty, P, Q;
   size_t total;
 };
+
+static void swamp_weight(const mhd_params* p, double z, double* w, double* wp);
+
+// first layer whose swamp weight or slope is nonzero (nz if none)
+static int swamp_first_layer(const mhd_params* p) {
+  for (int k = 0; k < p->nz; ++k) {
+    double w, wp;
+    swamp_weight(p, k * p->dz, &w, &wp);
+    if (w != 0.0 || wp != 0.0) return k;
+  }
+  return p->nz;
+}
 
 static Offsets plan_offsets(const mhd_params* p) {
   Offsets o;
@@ -174,6 +192,12 @@ static Offsets plan_offsets(const mhd_params* p) {
   o.red = c.take((size_t)RED_BLOCKS_MAX * 8 * sizeof(double));
   o.ss = c.take(sizeof(StepState));
   o.bg = c.take((size_t)(6 * p->nz + 12) * es);
+  if (p->precision == 32) {
+    o.bj = c.take((size_t)6 * n2 * p->nz * 4);
+    o.sw = c.take((size_t)3 * n2 * (p->nz - swamp_first_layer(p)) * 4);
+  } else {
+    o.bj = o.sw = 0;
+  }
   if (p->adjoint) {
     o.s2 = c.take(set);
     o.fbar = c.take(set);
@@ -366,6 +390,13 @@ template <typename R>
 static void launch_rk_any(mhd_ctx* h, const R* fin, R* fout, int sub) {
   Phys<R> ph = make_phys<R>(&h->p);
   Driver drv{h->axt, h->ayt, h->v0, h->v1};
+  if (sizeof(R) == 4 && h->split) {
+    const int which = (const void*)fin == h->f[0] ? 0 : 1;
+    launch_rk_split(&h->tma[which], &h->tmr[which], h->L, *(const Phys<float>*)&ph, h->bgf, (const float*)fin,
+                    (float*)fout, (float*)h->df, (float*)h->bj, (float*)h->sw, h->ksw, (const float*)h->wtab,
+                    (const float*)h->wptab, drv, h->ss, sub, h->p.dx, h->p.dy, h->p.dz, h->st);
+    return;
+  }
   if (sizeof(R) == 4 && h->tiled) {
     const int which = (const void*)fin == h->f[0] ? 0 : 1;
     launch_rk_tiled(&h->tm[which], h->L, *(const Phys<float>*)&ph, h->bgf, (float*)fout, (float*)h->df,
@@ -507,6 +538,9 @@ extern "C" int mhd_create(const mhd_params* p, void* workspace, size_t ws_bytes,
   h->red = (double*)(h->ws + o.red);
   h->ss = (StepState*)(h->ws + o.ss);
   h->bgtab = h->ws + o.bg;
+  h->bj = h->ws + o.bj;
+  h->sw = h->ws + o.sw;
+  h->ksw = swamp_first_layer(p);
   if (p->adjoint) {
     h->s2 = h->ws + o.s2;
     h->fbar = h->ws + o.fbar;
@@ -519,6 +553,7 @@ extern "C" int mhd_create(const mhd_params* p, void* workspace, size_t ws_bytes,
   {
     const char* v = getenv("MHD_RK_VARIANT");
     h->tiled = p->precision == 32 && !(v && strcmp(v, "simple") == 0);
+    h->split = h->tiled && !(v && strcmp(v, "fused") == 0);
     const char* va = getenv("MHD_ADJ_VARIANT");
     h->adj_tiled = !(va && strcmp(va, "simple") == 0);
   }
@@ -554,6 +589,10 @@ extern "C" int mhd_create(const mhd_params* p, void* workspace, size_t ws_bytes,
         rc = fail(h, MHD_ERR_CUDA, "cuTensorMapEncodeTiled failed for state set %d", s);
     if (!rc && p->adjoint && make_state_tensor_map(&h->tm[2], h->L, h->s2) != 0)
       rc = fail(h, MHD_ERR_CUDA, "cuTensorMapEncodeTiled failed for the adjoint substep state");
+    for (int s = 0; s < 2 && !rc; ++s)
+      if (make_state_tensor_map(&h->tma[s], h->L, h->f[s], 3) != 0 ||
+          make_state_tensor_map(&h->tmr[s], h->L, h->f[s], 5) != 0)
+        rc = fail(h, MHD_ERR_CUDA, "cuTensorMapEncodeTiled failed for the split boxes of state set %d", s);
   }
   if (!rc) {
     StepState s0;

@@ -154,23 +154,25 @@ struct Cell {
 // B = curl A + B_ext (Eq. 6), J = grad div A - lap A.  The swamp diffusivity
 // is left out of the Ohmic heating (Sect. 4.3.1).  Boundary rows and nudging
 // are applied by the caller.
+//
+// rhs_point_bj takes A's contribution as three vectors -- B = curl A + B_ext,
+// J = grad div A - lap A and the swamp part of the induction equation
+// sw = eta_s w lap A + eta_s w' div A z^ -- so that a pass that sees only A
+// (split right-hand side) can form them; rhs_point forms them from the cell.
 template <typename R>
-__device__ __forceinline__ void rhs_point(const Cell<R>& c, const Phys<R>& ph, R w, R wp, R out[8]) {
-  const R B0 = c.dA[2][1] - c.dA[1][2] + ph.bext[0];
-  const R B1 = c.dA[0][2] - c.dA[2][0] + ph.bext[1];
-  const R B2 = c.dA[1][0] - c.dA[0][1] + ph.bext[2];
-  const R J0 = c.gdA[0] - c.lapA[0], J1 = c.gdA[1] - c.lapA[1], J2 = c.gdA[2] - c.lapA[2];
-  const R divA = c.dA[0][0] + c.dA[1][1] + c.dA[2][2];
+__device__ __forceinline__ void rhs_point_bj(const Cell<R>& c, const Phys<R>& ph, R w, const R B[3], const R J[3],
+                                             const R sw[3], R out[8]) {
+  const R B0 = B[0], B1 = B[1], B2 = B[2];
+  const R J0 = J[0], J1 = J[1], J2 = J[2];
   const R divU = c.dU[0][0] + c.dU[1][1] + c.dU[2][2];
   const R T = rexp<R>(c.Th);
   const R rho1 = rexp<R>(-c.L);
   const R u0 = c.U[0], u1 = c.U[1], u2 = c.U[2];
-  const R ews = ph.eta_s * w;
 
   // induction
-  out[0] = u1 * B2 - u2 * B1 - ph.eta * J0 + ews * c.lapA[0];
-  out[1] = u2 * B0 - u0 * B2 - ph.eta * J1 + ews * c.lapA[1];
-  out[2] = u0 * B1 - u1 * B0 - ph.eta * J2 + ews * c.lapA[2] + ph.eta_s * wp * divA;
+  out[0] = u1 * B2 - u2 * B1 - ph.eta * J0 + sw[0];
+  out[1] = u2 * B0 - u0 * B2 - ph.eta * J1 + sw[1];
+  out[2] = u0 * B1 - u1 * B0 - ph.eta * J2 + sw[2];
 
   // traceless rate of strain S_ab = (d_a u_b + d_b u_a)/2 - delta_ab div u / 3
   const R third = R(1.0 / 3.0);
@@ -207,6 +209,29 @@ __device__ __forceinline__ void rhs_point(const Cell<R>& c, const Phys<R>& ph, R
   const R heat = ph.gm1 * (ph.eta * JJ * rho1 + R(2) * ph.nu * S2) * T1;
   const R kt = ph.gm1 * ph.kappa0 * rexp<R>(R(2.5) * c.Th - c.L);
   out[7] = -ugT - ph.gm1 * divU + heat + kt * (c.lapT + R(3.5) * gT2) + ph.chi_s * w * c.lapT;
+}
+
+// B, J and the swamp terms of the induction equation from A's derivatives
+template <typename R>
+__device__ __forceinline__ void a_terms(const Cell<R>& c, const Phys<R>& ph, R w, R wp, R B[3], R J[3], R sw[3]) {
+  B[0] = c.dA[2][1] - c.dA[1][2] + ph.bext[0];
+  B[1] = c.dA[0][2] - c.dA[2][0] + ph.bext[1];
+  B[2] = c.dA[1][0] - c.dA[0][1] + ph.bext[2];
+  J[0] = c.gdA[0] - c.lapA[0];
+  J[1] = c.gdA[1] - c.lapA[1];
+  J[2] = c.gdA[2] - c.lapA[2];
+  const R ews = ph.eta_s * w;
+  const R divA = c.dA[0][0] + c.dA[1][1] + c.dA[2][2];
+  sw[0] = ews * c.lapA[0];
+  sw[1] = ews * c.lapA[1];
+  sw[2] = ews * c.lapA[2] + ph.eta_s * wp * divA;
+}
+
+template <typename R>
+__device__ __forceinline__ void rhs_point(const Cell<R>& c, const Phys<R>& ph, R w, R wp, R out[8]) {
+  R B[3], J[3], sw[3];
+  a_terms<R>(c, ph, w, wp, B, J, sw);
+  rhs_point_bj<R>(c, ph, w, B, J, sw, out);
 }
 
 // Error flag checked by every kernel (set by the reductions on NaN/Inf).

@@ -57,7 +57,16 @@ void launch_adj_point_tiled(const CUtensorMap* tm, const Layout& L, const Phys<f
                             const Background<float>& bg, const float* dbar, float* coef, double* thbar,
                             const float* wtab, const float* wptab, StepState* ss, int sub, double dx, double dy,
                             double dz, cudaStream_t st);
-int make_state_tensor_map(CUtensorMap* tm, const Layout& L, void* base);
+// tensor map of one padded FP32 state set (dims mx, my, mz, 8 fields) whose box is
+// one plane with its halo (40 x 14 x 1) of box_fields consecutive fields
+int make_state_tensor_map(CUtensorMap* tm, const Layout& L, void* base, int box_fields = NF);
+// FP32 right-hand side + RK update as two z-march passes (A -> B, J, swamp terms;
+// then u, ln rho, ln T with the physics and the update); tm_a, tm_r map the input
+// state with 3-field (A) and 5-field (u_x .. ln T) boxes
+void launch_rk_split(const CUtensorMap* tm_a, const CUtensorMap* tm_r, const Layout& L, const Phys<float>& ph,
+                     const Background<float>& bg, const float* fin, float* fout, float* df, float* bj, float* sw,
+                     int ksw, const float* wtab, const float* wptab, const Driver& drv, StepState* ss, int sub,
+                     double dx, double dy, double dz, cudaStream_t st);
 // adjoint (transposed linearisation of one substep)
 constexpr int NCOEF_ADJ = 40;
 template <typename R> void launch_adj_point(const Layout& L, const Phys<R>& ph, const Background<R>& bg, const R* g,

@@ -22,7 +22,7 @@ __device__ __forceinline__ double warp_sum(double v) {
 // grid over (x tiles, y tiles, z chunks); each thread walks its z chunk
 static inline dim3 red_grid(const Layout& L, int* kchunk) {
   int tx = (L.nx + 31) / 32, ty = (L.ny + 7) / 8;
-  int zc = 4096 / (tx * ty);  // enough blocks to keep every SM's loads in flight
+  int zc = 2432 / (tx * ty);  // about 16 blocks per SM
   if (zc < 1) zc = 1;
   if (zc > L.nz) zc = L.nz;
   if (tx * ty * zc > RED_BLOCKS_MAX) zc = RED_BLOCKS_MAX / (tx * ty) > 0 ? RED_BLOCKS_MAX / (tx * ty) : 1;
@@ -49,11 +49,17 @@ __device__ __forceinline__ void bfield(const Layout& L, const Phys<R>& ph, const
 // largest of nu, eta + eta_s w, D_rho + chi_rho w, chi_s w + (gamma-1)
 // kappa0 T^{5/2}/rho.  Block maxima to partial[2 b], partial[2 b + 1].
 template <typename R>
+__device__ __forceinline__ R d1s(const R* __restrict__ p, int s, R inv) {
+  return (W<R>::c1 * (__ldg(p + s) - __ldg(p - s)) + W<R>::c2 * (__ldg(p + 2 * s) - __ldg(p - 2 * s)) +
+          W<R>::c3 * (__ldg(p + 3 * s) - __ldg(p - 3 * s))) * inv;
+}
+
+template <typename R>
 __global__ void __launch_bounds__(256) cfl_partial_kernel(Layout L, Phys<R> ph, Background<R> bg,
                                                           const R* __restrict__ f,
                                                           const R* __restrict__ wtab, double* partial,
                                                           StepState* ss, int kchunk, R sqinv2) {
-  __shared__ double sa[8], sd[8];
+  __shared__ R sa[8], sd[8];
   const int i = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y * 8 + threadIdx.y;
   const int tid = threadIdx.y * 32 + threadIdx.x;
   // per-thread maxima in the state precision (conversion to FP64 is exact and
@@ -62,16 +68,41 @@ __global__ void __launch_bounds__(256) cfl_partial_kernel(Layout L, Phys<R> ph, 
   bool bad = false;
   if (i < L.nx && j < L.ny && !halted(ss)) {
     const int k0 = blockIdx.z * kchunk, k1 = min(L.nz, k0 + kchunk);
-#pragma unroll 2
+    const int sy = L.mx;
+    const long long sz = L.sz();
+    // column pointers at (k0, j, i); the z derivatives of A_x, A_y come from
+    // a register window over k - 3 .. k + 3
+    const R* pax = f + L.at(AX, k0, j, i);
+    const R* pay = f + L.at(AY, k0, j, i);
+    const R* paz = f + L.at(AZ, k0, j, i);
+    const R* pux = f + L.at(UX, k0, j, i);
+    const R* puy = f + L.at(UY, k0, j, i);
+    const R* puz = f + L.at(UZ, k0, j, i);
+    const R* plr = f + L.at(LR, k0, j, i);
+    const R* plt = f + L.at(LT, k0, j, i);
+    R wx[7], wy[7];
+#pragma unroll
+    for (int m = 0; m < 6; ++m) {
+      wx[m + 1] = __ldg(pax + (m - 3) * sz);
+      wy[m + 1] = __ldg(pay + (m - 3) * sz);
+    }
     for (int k = k0; k < k1; ++k) {
-      R B[3];
-      bfield<R>(L, ph, f, k, j, i, B);
-      const R ux = f[L.at(UX, k, j, i)], uy = f[L.at(UY, k, j, i)], uz = f[L.at(UZ, k, j, i)];
-      const R lr = bg.lbar[k + NG] + f[L.at(LR, k, j, i)], lt = bg.tbar[k + NG] + f[L.at(LT, k, j, i)];
+#pragma unroll
+      for (int m = 0; m < 6; ++m) { wx[m] = wx[m + 1]; wy[m] = wy[m + 1]; }
+      wx[6] = __ldg(pax + 3 * sz);
+      wy[6] = __ldg(pay + 3 * sz);
+      const R dzax = (W<R>::c1 * (wx[4] - wx[2]) + W<R>::c2 * (wx[5] - wx[1]) + W<R>::c3 * (wx[6] - wx[0])) * ph.idz;
+      const R dzay = (W<R>::c1 * (wy[4] - wy[2]) + W<R>::c2 * (wy[5] - wy[1]) + W<R>::c3 * (wy[6] - wy[0])) * ph.idz;
+      // B = curl A + B_ext (Eq. 6)
+      const R B0 = d1s(paz, sy, ph.idy) - dzay + ph.bext[0];
+      const R B1 = dzax - d1s(paz, 1, ph.idx) + ph.bext[1];
+      const R B2 = d1s(pay, 1, ph.idx) - d1s(pax, sy, ph.idy) + ph.bext[2];
+      const R ux = __ldg(pux), uy = __ldg(puy), uz = __ldg(puz);
+      const R lr = bg.lbar[k + NG] + __ldg(plr), lt = bg.tbar[k + NG] + __ldg(plt);
       const R T = rexp<R>(lt), rho1 = rexp<R>(-lr);
-      const R B2 = B[0] * B[0] + B[1] * B[1] + B[2] * B[2];
+      const R B2s = B0 * B0 + B1 * B1 + B2 * B2;
       const R adv = fabs(ux) * ph.idx + fabs(uy) * ph.idy + fabs(uz) * ph.idz +
-                    rsqrt_<R>(ph.gamma * T + B2 * rho1) * sqinv2;
+                    rsqrt_<R>(ph.gamma * T + B2s * rho1) * sqinv2;
       const R w = wtab[k];
       R dm = ph.nu;
       dm = fmax(dm, ph.eta + ph.eta_s * w);
@@ -80,19 +111,23 @@ __global__ void __launch_bounds__(256) cfl_partial_kernel(Layout L, Phys<R> ph, 
       if (!isfinite(adv) || !isfinite(dm)) bad = true;
       mar = fmax(mar, adv);
       mdr = fmax(mdr, dm);
+      pax += sz; pay += sz; paz += sz; pux += sz; puy += sz; puz += sz; plr += sz; plt += sz;
     }
   }
   if (bad) atomicOr(&ss->nonfinite, 1);
-  double ma = (double)mar, md = (double)mdr;
-  ma = warp_max(ma);
-  md = warp_max(md);
-  if ((tid & 31) == 0) { sa[tid >> 5] = ma; sd[tid >> 5] = md; }
+  // block maxima in the state precision too (exact); FP64 from here on
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    mar = fmax(mar, __shfl_xor_sync(0xffffffffu, mar, o));
+    mdr = fmax(mdr, __shfl_xor_sync(0xffffffffu, mdr, o));
+  }
+  if ((tid & 31) == 0) { sa[tid >> 5] = mar; sd[tid >> 5] = mdr; }
   __syncthreads();
   if (tid == 0) {
-    for (int w = 1; w < 8; ++w) { ma = fmax(ma, sa[w]); md = fmax(md, sd[w]); }
+    for (int w = 1; w < 8; ++w) { mar = fmax(mar, sa[w]); mdr = fmax(mdr, sd[w]); }
     const int b = (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
-    partial[2 * b] = ma;
-    partial[2 * b + 1] = md;
+    partial[2 * b] = (double)mar;
+    partial[2 * b + 1] = (double)mdr;
   }
 }
 
@@ -167,6 +202,16 @@ __global__ void __launch_bounds__(256) stats_partial_kernel(Layout L, Phys<R> ph
   const int i = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y * 8 + threadIdx.y;
   const int tid = threadIdx.y * 32 + threadIdx.x;
   double acc[7] = {0, 0, 0, 0, 0, 0, 0};
+  // a thread's own chunk is summed in the state precision with Neumaier
+  // compensation (sum + correction carried separately), then taken to FP64:
+  // FP64 arithmetic is ~60x slower than FP32 here
+  R ps[6] = {R(0), R(0), R(0), R(0), R(0), R(0)}, pc[6] = {R(0), R(0), R(0), R(0), R(0), R(0)};
+  auto nadd = [&](int q, R x) {
+    const R t = ps[q] + x;
+    pc[q] += fabs(ps[q]) >= fabs(x) ? (ps[q] - t) + x : (x - t) + ps[q];
+    ps[q] = t;
+  };
+  R dmax = R(0);
   if (i < L.nx && j < L.ny) {
     const long long sy = L.sy(), sz = L.sz();
     const int k0 = blockIdx.z * kchunk, k1 = min(L.nz, k0 + kchunk);
@@ -176,13 +221,13 @@ __global__ void __launch_bounds__(256) stats_partial_kernel(Layout L, Phys<R> ph
       const R ux = f[L.at(UX, k, j, i)], uy = f[L.at(UY, k, j, i)], uz = f[L.at(UZ, k, j, i)];
       const R rho = rexp<R>(bg.lbar[k + NG] + f[L.at(LR, k, j, i)]);
       const R T = rexp<R>(bg.tbar[k + NG] + f[L.at(LT, k, j, i)]);
-      acc[0] += (double)(R(0.5) * rho * (ux * ux + uy * uy + uz * uz));
-      acc[1] += (double)(R(0.5) * (B[0] * B[0] + B[1] * B[1] + B[2] * B[2]));
-      acc[2] += (double)(rho * T);  // / (gamma - 1) once, in the finalize
-      acc[3] += (double)rho;
+      nadd(0, R(0.5) * rho * (ux * ux + uy * uy + uz * uz));
+      nadd(1, R(0.5) * (B[0] * B[0] + B[1] * B[1] + B[2] * B[2]));
+      nadd(2, rho * T);  // / (gamma - 1) once, in the finalize
+      nadd(3, rho);
       if (k == 0) {
-        acc[4] += (double)B[2];
-        acc[5] += fabs((double)B[2]);
+        nadd(4, B[2]);
+        nadd(5, fabs(B[2]));
       }
       // div B with the same stencils: B_x has no x derivative, B_y no y and
       // B_z no z derivative, so all values used lie inside the ghost zone
@@ -209,9 +254,11 @@ __global__ void __launch_bounds__(256) stats_partial_kernel(Layout L, Phys<R> ph
         const R bzm = d1(ayt, (long long)1, ph.idx) - d1(axt, sy, ph.idy);
         dv += cw[m] * ((bxp - bxm) * ph.idx + (byp - bym) * ph.idy + (bzp - bzm) * ph.idz);
       }
-      acc[6] = fmax(acc[6], fabs((double)dv));
+      dmax = fmax(dmax, fabs(dv));
     }
   }
+  for (int q = 0; q < 6; ++q) acc[q] = (double)ps[q] + (double)pc[q];
+  acc[6] = (double)dmax;
   for (int q = 0; q < 6; ++q) acc[q] = warp_sum(acc[q]);
   acc[6] = warp_max(acc[6]);
   if ((tid & 31) == 0)

@@ -20,27 +20,35 @@
 
 #include "mhd_adjoint_point.cuh"
 #include "mhd_internal.h"
+#include "mhd_zmarch.cuh"
 
 namespace mhd {
 namespace tiled {
 
-constexpr int TX = 32, TY = 8;
-constexpr int BX = TX + 8;                   // box x: x0 - 4 .. x0 + TX + 3
-constexpr int BY = TY + 6;                   // box y: y0 - 3 .. y0 + TY + 2
+using zm::TX;
+using zm::TY;
+using zm::BX;
+using zm::BY;
+using zm::WYW;
+using zm::WXH;
+using zm::TILE;
+using zm::FItems;
+using zm::make_items;
+using zm::mbar_init;
+using zm::mbar_wait;
+using zm::D1;
+using zm::D2;
+using zm::store_img;
 constexpr int PLANE = NF * BY * BX;          // floats per raw plane
 constexpr int NRAW = 8;                      // raw ring: planes k-3 .. k+4
 constexpr int NDZ = 6;                       // z-mixed sources per plane
 constexpr int NDR = 7;                       // their ring: planes k-3 .. k+3
 constexpr int NMX = 4;                       // xy-mixed terms per plane
 constexpr int NMR = 4;                       // their ring: planes k .. k+3
-constexpr int WYW = TX + 6;                  // D1y scratch, x halo
-constexpr int WXH = TY + 6;                  // D1x scratch, y halo
-constexpr int TILE = TX * TY;
 constexpr unsigned PLANE_BYTES = PLANE * 4;
 constexpr size_t SMEM_FLOATS = (size_t)NRAW * PLANE + NDR * NDZ * TILE + NMR * NMX * TILE + 2 * TY * WYW +
                                2 * WXH * TX;
 constexpr size_t SMEM_BYTES = SMEM_FLOATS * 4 + NRAW * 8;
-constexpr int WAIT_LIMIT = 1 << 22;
 
 struct Args {
   Layout L;
@@ -66,94 +74,8 @@ struct Args {
   float e0x, e1x, e2x, e3x, e0y, e1y, e2y, e3y, e0z, e1z, e2z, e3z;  // D2 weights / spacing^2
 };
 
-__device__ __forceinline__ uint32_t sa(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(uint64_t* b) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(sa(b)), "r"(1) : "memory");
-}
-
 __device__ __forceinline__ void tma_plane(const CUtensorMap* tm, float* dst, uint64_t* bar, int x, int y, int z) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(sa(bar)), "r"(PLANE_BYTES) : "memory");
-  asm volatile(
-      "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
-      "[%6];" ::"r"(sa(dst)),
-      "l"((uint64_t)tm), "r"(x), "r"(y), "r"(z), "r"(0), "r"(sa(bar))
-      : "memory");
-}
-
-// bounded wait for the given phase parity; false on time-out
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-  for (int it = 0; it < WAIT_LIMIT; ++it) {
-    uint32_t ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
-        : "=r"(ok)
-        : "r"(sa(bar)), "r"(parity)
-        : "memory");
-    if (ok) return true;
-  }
-  return false;
-}
-
-__device__ __forceinline__ float D1(const float* p, int s, float c1, float c2, float c3) {
-  return c1 * (p[s] - p[-s]) + c2 * (p[2 * s] - p[-2 * s]) + c3 * (p[3 * s] - p[-3 * s]);
-}
-__device__ __forceinline__ float D2(const float* p, int s, float e0, float e1, float e2, float e3) {
-  return e0 * p[0] + e1 * (p[s] + p[-s]) + e2 * (p[2 * s] + p[-2 * s]) + e3 * (p[3 * s] + p[-3 * s]);
-}
-
-// store v at (k, j, i) and at its periodic x,y images inside the padded
-// plane (no local arrays: at most one image per direction for n >= 6, two
-// for the smallest grids)
-__device__ __forceinline__ void store_img(const Layout& L, float* __restrict__ f, int fl, int k, int j, int i,
-                                          float v) {
-  const long long base = L.at(fl, k, 0, 0);
-  const int mx = L.mx;
-  const int xa = i < NG ? i + L.nx : -100, xb = i >= L.nx - NG ? i - L.nx : -100;
-  const int ya = j < NG ? j + L.ny : -100, yb = j >= L.ny - NG ? j - L.ny : -100;
-  auto put = [&](int jj, int ii) { f[base + (long long)jj * mx + ii] = v; };
-  put(j, i);
-  if (xa != -100) put(j, xa);
-  if (xb != -100) put(j, xb);
-  if (ya != -100) {
-    put(ya, i);
-    if (xa != -100) put(ya, xa);
-    if (xb != -100) put(ya, xb);
-  }
-  if (yb != -100) {
-    put(yb, i);
-    if (xa != -100) put(yb, xa);
-    if (xb != -100) put(yb, xb);
-  }
-}
-
-// F1 work items of a thread (at most 3): source offset inside a field's box
-// plane, destination inside wy/wx, and whether it is a D1y (wy) item
-struct FItems {
-  int n;
-  int src[3], dst[3];
-  bool isy[3];
-};
-
-__device__ __forceinline__ FItems make_items(int tid) {
-  FItems it;
-  it.n = 0;
-  for (int q = tid; q < TY * WYW + WXH * TX; q += TILE) {
-    if (q < TY * WYW) {
-      const int r = q / WYW, cx = q - r * WYW;
-      it.src[it.n] = (r + 3) * BX + cx + 1;
-      it.dst[it.n] = r * WYW + cx;
-      it.isy[it.n] = true;
-    } else {
-      const int q2 = q - TY * WYW;
-      const int r = q2 / TX, cx = q2 - r * TX;
-      it.src[it.n] = r * BX + cx + 4;
-      it.dst[it.n] = r * TX + cx;
-      it.isy[it.n] = false;
-    }
-    ++it.n;
-  }
-  return it;
+  zm::tma_plane(tm, dst, bar, PLANE_BYTES, x, y, z, 0);
 }
 
 // front processing of one plane: the z-mixed sources and the xy-mixed terms
@@ -490,20 +412,7 @@ static Args tiled_args(const Layout& L, const Phys<float>& ph, const Background<
   a.ntx = (L.nx + tiled::TX - 1) / tiled::TX;
   a.nty = (L.ny + tiled::TY - 1) / tiled::TY;
   const int tiles = a.ntx * a.nty;
-  // z chunks: balance whole waves of the persistent grid against the six
-  // extra planes each chunk loads before its first centre plane
-  int best = 1;
-  double best_eff = 0.0;
-  const int maxch = L.nz / 16 > 1 ? L.nz / 16 : 1;
-  for (int nch = 1; nch <= maxch; ++nch) {
-    const int kc = (L.nz + nch - 1) / nch;
-    const int nc = (L.nz + kc - 1) / kc;
-    const long long items = (long long)tiles * nc;
-    const long long waves = (items + g_sms - 1) / g_sms;
-    const double eff = (double)items / (double)(waves * g_sms) * (double)kc / (double)(kc + 6);
-    if (eff > best_eff + 1e-9) { best_eff = eff; best = nch; }
-  }
-  a.kchunk = (L.nz + best - 1) / best;
+  a.kchunk = zm::zchunk(L.nz, tiles, g_sms);
   a.nch = (L.nz + a.kchunk - 1) / a.kchunk;
   const double W1[4] = {0.0, 45.0 / 60.0, -9.0 / 60.0, 1.0 / 60.0};
   const double W2[4] = {-490.0 / 180.0, 270.0 / 180.0, -27.0 / 180.0, 2.0 / 180.0};
@@ -549,8 +458,9 @@ void launch_adj_point_tiled(const CUtensorMap* tm, const Layout& L, const Phys<f
 }
 
 // Tensor map of one padded FP32 state set: dims (mx, my, mz, 8 fields),
-// box (40, 14, 1, 8) = one plane of every field with its halo.
-int make_state_tensor_map(CUtensorMap* tm, const Layout& L, void* base) {
+// box (40, 14, 1, box_fields) = one plane of box_fields consecutive fields
+// with its halo.
+int make_state_tensor_map(CUtensorMap* tm, const Layout& L, void* base, int box_fields) {
   typedef CUresult (*EncodeFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
                                CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
@@ -566,7 +476,7 @@ int make_state_tensor_map(CUtensorMap* tm, const Layout& L, void* base) {
   }
   cuuint64_t dims[4] = {(cuuint64_t)L.mx, (cuuint64_t)L.my, (cuuint64_t)L.mz, (cuuint64_t)NF};
   cuuint64_t strides[3] = {(cuuint64_t)L.mx * 4, (cuuint64_t)L.my * L.mx * 4, (cuuint64_t)L.fs * 4};
-  cuuint32_t box[4] = {(cuuint32_t)tiled::BX, (cuuint32_t)tiled::BY, 1, (cuuint32_t)NF};
+  cuuint32_t box[4] = {(cuuint32_t)tiled::BX, (cuuint32_t)tiled::BY, 1, (cuuint32_t)box_fields};
   cuuint32_t es[4] = {1, 1, 1, 1};
   CUresult r = enc(tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, base, dims, strides, box, es,
                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
