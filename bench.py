@@ -29,8 +29,8 @@ sys.path.insert(0, ROOT)
 METRIC = "MHD cell-updates/s per RK step"
 UNIT = "cell-updates/s"
 WORDS_PER_CELL_STEP = 80  # algorithmic state words moved per cell per RK3 step
-RK_KERNEL = ("pass_a_kernel + pass_r_kernel (split TMA z-march: B, J and swamp terms from A; "
-             "physics, nudging and RK update), per substep")
+RK_KERNEL = ("rk_pair_kernel (fused RHS + RK update, TMA z-march, two cells per thread in f32x2, "
+             "z histories in TMEM)")
 
 
 def parse():

@@ -21,6 +21,7 @@ struct mhd_ctx {
   CUtensorMap tmr[2];  // the two state sets, boxes of u, ln rho, ln T (split pass R)
   bool tiled;          // FP32: TMA-fed z-march kernels; otherwise the simple kernel
   bool split;          // FP32 forward: split passes (else the fused z-march kernel)
+  bool pair;           // FP32 forward: one-pass f32x2 kernel with TMEM z histories
   void* bj;            // split: [6][nz][ny][nx] B, J of the current substep
   void* sw;            // split: [3][nz - ksw][ny][nx] swamp terms
   int ksw;             // first layer with a nonzero swamp weight or slope (nz if none)
@@ -390,6 +391,12 @@ template <typename R>
 static void launch_rk_any(mhd_ctx* h, const R* fin, R* fout, int sub) {
   Phys<R> ph = make_phys<R>(&h->p);
   Driver drv{h->axt, h->ayt, h->v0, h->v1};
+  if (sizeof(R) == 4 && h->pair) {
+    const int which = (const void*)fin == h->f[0] ? 0 : 1;
+    launch_rk_pair(&h->tm[which], h->L, *(const Phys<float>*)&ph, h->bgf, (float*)fout, (float*)h->df,
+                   (const float*)h->wtab, (const float*)h->wptab, drv, h->ss, sub, h->p.dx, h->p.dy, h->p.dz, h->st);
+    return;
+  }
   if (sizeof(R) == 4 && h->split) {
     const int which = (const void*)fin == h->f[0] ? 0 : 1;
     launch_rk_split(&h->tma[which], &h->tmr[which], h->L, *(const Phys<float>*)&ph, h->bgf, (const float*)fin,
@@ -554,6 +561,8 @@ extern "C" int mhd_create(const mhd_params* p, void* workspace, size_t ws_bytes,
     const char* v = getenv("MHD_RK_VARIANT");
     h->tiled = p->precision == 32 && !(v && strcmp(v, "simple") == 0);
     h->split = h->tiled && !(v && strcmp(v, "fused") == 0);
+    h->pair = h->split && !(v && (strcmp(v, "tiled") == 0 || strcmp(v, "split") == 0)) &&
+              rk_pair_supported(h->L);
     const char* va = getenv("MHD_ADJ_VARIANT");
     h->adj_tiled = !(va && strcmp(va, "simple") == 0);
   }

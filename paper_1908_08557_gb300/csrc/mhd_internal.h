@@ -67,6 +67,13 @@ void launch_rk_split(const CUtensorMap* tm_a, const CUtensorMap* tm_r, const Lay
                      const Background<float>& bg, const float* fin, float* fout, float* df, float* bj, float* sw,
                      int ksw, const float* wtab, const float* wptab, const Driver& drv, StepState* ss, int sub,
                      double dx, double dy, double dz, cudaStream_t st);
+// FP32 right-hand side + RK update in one z-march pass, two x-adjacent cells
+// per thread (f32x2), z histories in TMEM; tm maps the input state with
+// 8-field boxes.  Requires nx even, nx >= 8, ny >= 6.
+bool rk_pair_supported(const Layout& L);
+void launch_rk_pair(const CUtensorMap* tm, const Layout& L, const Phys<float>& ph, const Background<float>& bg,
+                    float* fout, float* df, const float* wtab, const float* wptab, const Driver& drv, StepState* ss,
+                    int sub, double dx, double dy, double dz, cudaStream_t st);
 // adjoint (transposed linearisation of one substep)
 constexpr int NCOEF_ADJ = 40;
 template <typename R> void launch_adj_point(const Layout& L, const Phys<R>& ph, const Background<R>& bg, const R* g,

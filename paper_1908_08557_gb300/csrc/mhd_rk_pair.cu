@@ -1,0 +1,550 @@
+// mhd_rk_pair.cu -- FP32 right-hand side + RK3 update in one TMA-fed z-march
+// pass, two x-adjacent cells per thread in packed f32x2 arithmetic, with the z
+// histories of every thread's cells kept in tensor memory (TMEM).
+//
+// A CTA (128 threads) owns a 32 x 8 tile and marches in z over a chunk of
+// layers; thread (tx, ty) owns cells (x0 + 2tx, x0 + 2tx + 1, y0 + ty).
+// Plane p of all 8 fields, with its 3-cell halo, arrives in shared memory
+// through one 4D cp.async.bulk.tensor load into a 5-slot ring (planes k .. k+3
+// in use at centre k, k+4 in flight), guarded by mbarriers with bounded waits.
+//
+//  front (plane k + 3): each thread copies its two cells of the 8 fields into
+//    TMEM (ring of 8 planes) and forms the sources of the xz / yz mixed
+//    derivatives -- D1x X_z, D1y X_z, D1x X_x + D1y X_y for X = A, u -- also
+//    into a TMEM ring of 8 planes;
+//  centre (plane k): D1z and D2z of the fields and D1z of the mixed sources
+//    from TMEM (tcgen05.ld), x and y derivatives from the shared ring, the xy
+//    mixed derivatives D1x(D1y X_y), D1x(D1y X_x) through a small shared
+//    scratch with an x halo (the tensor-product operator D1x D1y equals
+//    D1y D1x), the pointwise physics, nudging and boundary rows, the
+//    low-storage RK update and the stores (with periodic images).
+//
+// TMEM: each CTA allocates 256 columns; thread t owns lane t.  Columns
+// [0, 128): values, 16 per plane slot (field f, cell c at 2f + c); columns
+// [128, 256): mixed sources, 16 per plane slot (source q, cell c at 2q + c).
+// The shared ring (> 76 KB per CTA) admits at most two CTAs per SM, so the
+// two allocations never exceed the SM's 512 columns and tcgen05.alloc never
+// waits.  Every exit path deallocates.
+#include <cuda.h>
+
+#include "mhd_internal.h"
+#include "mhd_zmarch.cuh"
+
+namespace mhd {
+namespace pair {
+
+constexpr int TX = zm::TX, TY = zm::TY;  // 32 x 8 cells
+constexpr int BX = zm::BX, BY = zm::BY;  // 40 x 14 box
+constexpr int NT = TX / 2 * TY;          // 128 threads
+constexpr int NR = 5;                    // shared ring slots
+constexpr int FP = BY * BX;              // floats per field plane of a box
+constexpr int PLANE = NF * FP;           // floats per ring slot (17920 B)
+constexpr int NSC = 4;                   // scratch fields: D1y A_y, D1y A_x, D1y u_y, D1y u_x
+constexpr int SCF = TY * BX;             // floats per scratch field
+constexpr size_t SMEM_BYTES = (size_t)NR * PLANE * 4 + (size_t)NSC * SCF * 4 + NR * 8 + 16;
+static_assert(SMEM_BYTES > 233472 / 3, "ring must keep TMEM users at <= 2 CTAs per SM");
+constexpr int TMEM_COLS = 256;
+constexpr int VCOL = 0, SCOL = 128;      // value / source rings in TMEM
+
+typedef float2 f2;
+__device__ __forceinline__ f2 F2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ f2 add(f2 a, f2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ f2 mul(f2 a, f2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) { return __ffma2_rn(a, b, c); }
+// a - b, one rounding
+__device__ __forceinline__ f2 dif(f2 a, f2 b) { return __ffma2_rn(b, F2(-1.f), a); }
+__device__ __forceinline__ f2 ld2(const float* p) { return *reinterpret_cast<const f2*>(p); }
+
+struct Coef {
+  f2 c1, c2, c3;        // D1 weights / spacing
+  f2 e0, e1, e2, e3;    // D2 weights / spacing^2
+};
+
+struct Args {
+  Layout L;
+  Phys<float> ph;
+  Background<float> bg;
+  float* fout;
+  float* df;
+  const float* wtab;
+  const float* wptab;
+  const float* axt;
+  const float* ayt;
+  const float* v0;
+  const float* v1;
+  StepState* ss;
+  int sub;
+  int ntx, nty, nch, kchunk;
+  Coef cx, cy, cz;
+};
+
+// ---- TMEM access (32x32b shape: each thread its own lane) -----------------
+#define TM_R16(a)                                                                                          \
+  "=r"(a[0]), "=r"(a[1]), "=r"(a[2]), "=r"(a[3]), "=r"(a[4]), "=r"(a[5]), "=r"(a[6]), "=r"(a[7]), "=r"(a[8]), \
+      "=r"(a[9]), "=r"(a[10]), "=r"(a[11]), "=r"(a[12]), "=r"(a[13]), "=r"(a[14]), "=r"(a[15])
+#define TM_W16(a)                                                                                              \
+  "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(a[4]), "r"(a[5]), "r"(a[6]), "r"(a[7]), "r"(a[8]), "r"(a[9]), \
+      "r"(a[10]), "r"(a[11]), "r"(a[12]), "r"(a[13]), "r"(a[14]), "r"(a[15])
+
+struct V16 {
+  uint32_t r[16];
+  __device__ __forceinline__ f2 get(int q) const { return make_float2(__uint_as_float(r[2 * q]), __uint_as_float(r[2 * q + 1])); }
+  __device__ __forceinline__ void set(int q, f2 v) {
+    r[2 * q] = __float_as_uint(v.x);
+    r[2 * q + 1] = __float_as_uint(v.y);
+  }
+};
+__device__ __forceinline__ void tm_ld(uint32_t t, V16& v) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : TM_R16(v.r)
+      : "r"(t));
+}
+__device__ __forceinline__ void tm_st(uint32_t t, const V16& v) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(t),
+      TM_W16(v.r)
+      : "memory");
+}
+__device__ __forceinline__ void tm_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+__device__ __forceinline__ void tm_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
+// ---- stencils on a box row / column at an even x position -----------------
+// first and second x derivatives of the cell pair at p (p even, p - 4 .. p + 5 in the row)
+__device__ __forceinline__ void dx_pair(const float* p, const Coef& c, f2& d1, f2* d2) {
+  const f2 m4 = ld2(p - 4), m2 = ld2(p - 2), z0 = ld2(p), p2 = ld2(p + 2), p4 = ld2(p + 4);
+  const f2 om3 = make_float2(m4.y, m2.x), om1 = make_float2(m2.y, z0.x);
+  const f2 op1 = make_float2(z0.y, p2.x), op3 = make_float2(p2.y, p4.x);
+  d1 = fma2(c.c1, dif(op1, om1), fma2(c.c2, dif(p2, m2), mul(c.c3, dif(op3, om3))));
+  if (d2) *d2 = fma2(c.e0, z0, fma2(c.e1, add(op1, om1), fma2(c.e2, add(p2, m2), mul(c.e3, add(op3, om3)))));
+}
+// first and second derivatives along a stride s (in floats) of the pair at p
+__device__ __forceinline__ void ds_pair(const float* p, int s, const Coef& c, f2& d1, f2* d2) {
+  const f2 z0 = ld2(p), a1 = ld2(p + s), b1 = ld2(p - s), a2 = ld2(p + 2 * s), b2 = ld2(p - 2 * s),
+           a3 = ld2(p + 3 * s), b3 = ld2(p - 3 * s);
+  d1 = fma2(c.c1, dif(a1, b1), fma2(c.c2, dif(a2, b2), mul(c.c3, dif(a3, b3))));
+  if (d2) *d2 = fma2(c.e0, z0, fma2(c.e1, add(a1, b1), fma2(c.e2, add(a2, b2), mul(c.e3, add(a3, b3)))));
+}
+
+// ---- the kernel -------------------------------------------------------------
+__global__ void __launch_bounds__(NT, 2) rk_pair_kernel(const __grid_constant__ CUtensorMap tm, const Args a) {
+  extern __shared__ __align__(128) float smem[];
+  float* raw = smem;
+  float* scr = raw + NR * PLANE;
+  uint64_t* mbar = (uint64_t*)(scr + NSC * SCF);
+  uint32_t* tslot = (uint32_t*)(mbar + NR);
+
+  const Layout& L = a.L;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4, warp = tid >> 5;
+  if (halted(a.ss)) return;
+  if (tid == 0) {
+    for (int s = 0; s < NR; ++s) zm::mbar_init(&mbar[s]);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(zm::sa(tslot)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tbase = *tslot;
+  const uint32_t tlane = tbase + ((uint32_t)(32 * warp) << 16);
+
+  const int sub = a.sub;
+  const bool eval = sub < 0;
+  const float dt = eval ? 1.f : (float)a.ss->dt;
+  const float alpha = eval ? 0.f : (float)rk_alpha(sub);
+  const float beta = eval ? 0.f : (float)rk_beta(sub);
+  float rr = 0.f, ss_ = 0.f;
+  if (a.ph.bcz == 0) {
+    rr = (float)(eval ? a.ss->eval_r : a.ss->r[sub]);
+    ss_ = (float)(eval ? a.ss->eval_s : a.ss->s[sub]);
+  }
+  const int e = 2 * tx + 4;                 // box x of the thread's first cell
+  const int cen = (ty + 3) * BX + e;        // box offset of the pair
+  // halo item of the xy-mixed scratch: field hq = warp, row hr, box x hx
+  const int hq = warp, hr = (tid & 31) >> 2, hx = ((tid & 3) < 2) ? 2 * (tid & 3) : 32 + 2 * (tid & 3);
+  const int hfield = hq == 0 ? AY : (hq == 1 ? AX : (hq == 2 ? UY : UX));
+  uint32_t phase = 0, pending = 0;
+  const int nitems = a.ntx * a.nty * a.nch;
+  const long long n2 = (long long)L.nx * L.ny;
+  bool bad = false;
+
+  auto load = [&](int p, int pbase, int x0, int y0) {
+    const int s = (p - pbase) % NR;
+    zm::tma_plane(&tm, raw + s * PLANE, &mbar[s], PLANE * 4, x0, y0, p + NG, 0);
+    pending |= 1u << s;
+  };
+  // collective bounded wait for plane p; false on time-out (uniform)
+  auto wait = [&](int p, int pbase) -> bool {
+    const int s = (p - pbase) % NR;
+    const bool to = !zm::mbar_wait(&mbar[s], (phase >> s) & 1u);
+    if (__syncthreads_or(to)) return false;
+    phase ^= 1u << s;
+    pending &= ~(1u << s);
+    return true;
+  };
+  // front of plane p: values and mixed sources of the pair into TMEM
+  auto front = [&](int p, int pbase) {
+    const float* P = raw + ((p - pbase) % NR) * PLANE + cen;
+    V16 v, s;
+#pragma unroll
+    for (int f = 0; f < NF; ++f) v.set(f, ld2(P + f * FP));
+#pragma unroll
+    for (int g = 0; g < 2; ++g) {
+      const int X = g == 0 ? AX : UX;
+      f2 zx, zy, xx, yy;
+      dx_pair(P + (X + 2) * FP, a.cx, zx, nullptr);
+      ds_pair(P + (X + 2) * FP, BX, a.cy, zy, nullptr);
+      dx_pair(P + X * FP, a.cx, xx, nullptr);
+      ds_pair(P + (X + 1) * FP, BX, a.cy, yy, nullptr);
+      s.set(3 * g + 0, zx);
+      s.set(3 * g + 1, zy);
+      s.set(3 * g + 2, add(xx, yy));
+    }
+    s.set(6, F2(0.f));
+    s.set(7, F2(0.f));
+    tm_st(tlane + VCOL + (uint32_t)(p & 7) * 16, v);
+    tm_st(tlane + SCOL + (uint32_t)(p & 7) * 16, s);
+  };
+
+  for (int item = blockIdx.x; item < nitems && !bad; item += gridDim.x) {
+    const int ch = item % a.nch, tile = item / a.nch;
+    const int x0 = (tile % a.ntx) * TX, y0 = (tile / a.ntx) * TY;
+    const int k0 = ch * a.kchunk, k1 = min(L.nz, k0 + a.kchunk);
+    const int pbase = k0 - NG, plast = k1 + NG - 1;
+    if (tid == 0)
+      for (int p = pbase; p <= min(pbase + NR - 1, plast); ++p) load(p, pbase, x0, y0);
+    // prologue: planes k0-3 .. k0+2; the three below k0 are released at once
+    for (int p = pbase; p < k0 + NG && !bad; ++p) {
+      bad = !wait(p, pbase);
+      if (bad) break;
+      // every thread is past the front of p - 1; below k0 that was its last use
+      if (p > pbase && p - 1 < k0 && tid == 0 && p - 1 + NR <= plast) load(p - 1 + NR, pbase, x0, y0);
+      front(p, pbase);
+    }
+    for (int k = k0; k < k1 && !bad; ++k) {
+      const int i = x0 + 2 * tx, j = y0 + ty;
+      const bool live = i < L.nx && j < L.ny;
+      const long long cq = live ? L.at(0, k, j, i) : 0;
+      // RK accumulator of the pair, fetched before the waits
+      f2 dfo[NF];
+#pragma unroll
+      for (int f = 0; f < NF; ++f) dfo[f] = (live && sub > 0) ? __ldg(reinterpret_cast<const f2*>(a.df + cq + (long long)f * L.fs)) : F2(0.f);
+      bad = !wait(k + NG, pbase);
+      if (bad) break;
+      // every thread is past centre k - 1: plane k - 1's slot takes k + 4
+      if (k > k0 && tid == 0 && k - 1 + NR <= plast) load(k - 1 + NR, pbase, x0, y0);
+      front(k + NG, pbase);
+      tm_wait_st();
+
+      const float* Pk = raw + ((k - pbase) % NR) * PLANE + cen;
+      // ---- z derivatives from the TMEM rings --------------------------------
+      f2 vz[NF], d1z[NF], d2z[NF], mz[6];
+#pragma unroll
+      for (int f = 0; f < NF; ++f) {
+        vz[f] = ld2(Pk + f * FP);
+        d1z[f] = F2(0.f);
+        d2z[f] = mul(a.cz.e0, vz[f]);
+      }
+#pragma unroll
+      for (int q = 0; q < 6; ++q) mz[q] = F2(0.f);
+#pragma unroll
+      for (int m = 3; m >= 1; --m) {
+        const f2 cm = m == 1 ? a.cz.c1 : (m == 2 ? a.cz.c2 : a.cz.c3);
+        const f2 em = m == 1 ? a.cz.e1 : (m == 2 ? a.cz.e2 : a.cz.e3);
+        V16 vp, vm, sp, sm;
+        tm_ld(tlane + VCOL + (uint32_t)((k + m) & 7) * 16, vp);
+        tm_ld(tlane + VCOL + (uint32_t)((k - m) & 7) * 16, vm);
+        tm_ld(tlane + SCOL + (uint32_t)((k + m) & 7) * 16, sp);
+        tm_ld(tlane + SCOL + (uint32_t)((k - m) & 7) * 16, sm);
+        tm_wait_ld();
+#pragma unroll
+        for (int f = 0; f < NF; ++f) {
+          d1z[f] = fma2(cm, dif(vp.get(f), vm.get(f)), d1z[f]);
+          d2z[f] = fma2(em, add(vp.get(f), vm.get(f)), d2z[f]);
+        }
+#pragma unroll
+        for (int q = 0; q < 6; ++q) mz[q] = fma2(cm, dif(sp.get(q), sm.get(q)), mz[q]);
+      }
+
+      // ---- x, y derivatives from the shared ring ----------------------------
+      const bool swamp = a.wtab[k] != 0.f || a.wptab[k] != 0.f;
+      f2 dxv[NF], dyv[NF], xxv[NF], yyv[NF];
+#pragma unroll
+      for (int f = 0; f < NF; ++f) {
+        const bool needx2 = !(f == AX) || swamp;  // D2x A_x cancels in J
+        const bool needy2 = !(f == AY) || swamp;  // D2y A_y cancels in J
+        dx_pair(Pk + f * FP, a.cx, dxv[f], needx2 ? &xxv[f] : nullptr);
+        ds_pair(Pk + f * FP, BX, a.cy, dyv[f], needy2 ? &yyv[f] : nullptr);
+        if (!needx2) xxv[f] = F2(0.f);
+        if (!needy2) yyv[f] = F2(0.f);
+      }
+      // xy-mixed: D1y of A_y, A_x, u_y, u_x on the tile plus x halo
+      {
+        float* sc = scr + ty * BX + e;
+        *reinterpret_cast<f2*>(sc + 0 * SCF) = dyv[AY];
+        *reinterpret_cast<f2*>(sc + 1 * SCF) = dyv[AX];
+        *reinterpret_cast<f2*>(sc + 2 * SCF) = dyv[UY];
+        *reinterpret_cast<f2*>(sc + 3 * SCF) = dyv[UX];
+        f2 h;
+        ds_pair(raw + ((k - pbase) % NR) * PLANE + hfield * FP + (hr + 3) * BX + hx, BX, a.cy, h, nullptr);
+        *reinterpret_cast<f2*>(scr + hq * SCF + hr * BX + hx) = h;
+      }
+      __syncthreads();
+      f2 mxy[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) dx_pair(scr + q * SCF + ty * BX + e, a.cx, mxy[q], nullptr);
+
+      // stateful u_x, u_y ghost rows below the photosphere (k = 0): their
+      // values are the TMEM copies of planes -1 .. -3 (loaded warp-wide)
+      f2 gux[NG], guy[NG];
+      if (a.ph.bcz == 0 && k == 0) {
+#pragma unroll
+        for (int m = 1; m <= NG; ++m) {
+          uint32_t g[4];
+          asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+                       : "=r"(g[0]), "=r"(g[1]), "=r"(g[2]), "=r"(g[3])
+                       : "r"(tlane + VCOL + (uint32_t)((k - m) & 7) * 16 + 2 * UX));
+          tm_wait_ld();
+          gux[m - 1] = make_float2(__uint_as_float(g[0]), __uint_as_float(g[1]));
+          guy[m - 1] = make_float2(__uint_as_float(g[2]), __uint_as_float(g[3]));
+        }
+      }
+      if (live) {
+        // ---- pointwise physics of the pair ----------------------------------
+        const Phys<float>& ph = a.ph;
+        const f2 w = F2(a.wtab[k]), wp = F2(a.wptab[k]);
+        const f2 A0 = vz[AX], A1 = vz[AY], A2 = vz[AZ];
+        const f2 u0 = vz[UX], u1 = vz[UY], u2 = vz[UZ];
+        // B = curl A + B_ext, J = grad div A - lap A (own-axis D2 cancelled
+        // outside the swamp), swamp terms of the induction equation
+        const f2 B0 = add(dif(dyv[AZ], d1z[AY]), F2(ph.bext[0]));
+        const f2 B1 = add(dif(d1z[AX], dxv[AZ]), F2(ph.bext[1]));
+        const f2 B2 = add(dif(dxv[AY], dyv[AX]), F2(ph.bext[2]));
+        f2 J0, J1, J2, sw0 = F2(0.f), sw1 = F2(0.f), sw2 = F2(0.f);
+        if (!swamp) {
+          J0 = dif(dif(add(mxy[0], mz[0]), yyv[AX]), d2z[AX]);
+          J1 = dif(dif(add(mxy[1], mz[1]), xxv[AY]), d2z[AY]);
+          J2 = dif(dif(mz[2], xxv[AZ]), yyv[AZ]);
+        } else {
+          const f2 lap0 = add(add(xxv[AX], yyv[AX]), d2z[AX]);
+          const f2 lap1 = add(add(xxv[AY], yyv[AY]), d2z[AY]);
+          const f2 lap2 = add(add(xxv[AZ], yyv[AZ]), d2z[AZ]);
+          J0 = dif(add(add(xxv[AX], mxy[0]), mz[0]), lap0);
+          J1 = dif(add(add(mxy[1], yyv[AY]), mz[1]), lap1);
+          J2 = dif(add(mz[2], d2z[AZ]), lap2);
+          const f2 ews = mul(F2(ph.eta_s), w);
+          const f2 divA = add(add(dxv[AX], dyv[AY]), d1z[AZ]);
+          sw0 = mul(ews, lap0);
+          sw1 = mul(ews, lap1);
+          sw2 = fma2(mul(F2(ph.eta_s), wp), divA, mul(ews, lap2));
+        }
+        // dU[c][a] = d_a u_c
+        const f2 U00 = dxv[UX], U01 = dyv[UX], U02 = d1z[UX];
+        const f2 U10 = dxv[UY], U11 = dyv[UY], U12 = d1z[UY];
+        const f2 U20 = dxv[UZ], U21 = dyv[UZ], U22 = d1z[UZ];
+        const f2 lapU0 = add(add(xxv[UX], yyv[UX]), d2z[UX]);
+        const f2 lapU1 = add(add(xxv[UY], yyv[UY]), d2z[UY]);
+        const f2 lapU2 = add(add(xxv[UZ], yyv[UZ]), d2z[UZ]);
+        const f2 gdU0 = add(add(xxv[UX], mxy[2]), mz[3]);
+        const f2 gdU1 = add(add(mxy[3], yyv[UY]), mz[4]);
+        const f2 gdU2 = add(mz[5], d2z[UZ]);
+        const f2 Lr = add(F2(a.bg.lbar[k + NG]), vz[LR]);
+        const f2 Th = add(F2(a.bg.tbar[k + NG]), vz[LT]);
+        const f2 gL0 = dxv[LR], gL1 = dyv[LR], gL2 = add(d1z[LR], F2(a.bg.dl[k]));
+        const f2 gT0 = dxv[LT], gT1 = dyv[LT], gT2 = add(d1z[LT], F2(a.bg.dt[k]));
+        const f2 lapL = add(add(add(xxv[LR], yyv[LR]), d2z[LR]), F2(a.bg.d2l[k]));
+        const f2 lapT = add(add(add(xxv[LT], yyv[LT]), d2z[LT]), F2(a.bg.d2t[k]));
+
+        const f2 divU = add(add(U00, U11), U22);
+        const f2 T = make_float2(expf(Th.x), expf(Th.y));
+        const f2 rho1 = make_float2(expf(-Lr.x), expf(-Lr.y));
+        const f2 eta = F2(ph.eta), nu = F2(ph.nu), gm1 = F2(ph.gm1);
+        f2 out[NF];
+        // induction
+        out[AX] = add(dif(dif(mul(u1, B2), mul(u2, B1)), mul(eta, J0)), sw0);
+        out[AY] = add(dif(dif(mul(u2, B0), mul(u0, B2)), mul(eta, J1)), sw1);
+        out[AZ] = add(dif(dif(mul(u0, B1), mul(u1, B0)), mul(eta, J2)), sw2);
+        // traceless rate of strain
+        const f2 third = F2(1.f / 3.f), half = F2(0.5f), two = F2(2.f);
+        const f2 s00 = dif(U00, mul(third, divU)), s11 = dif(U11, mul(third, divU)), s22 = dif(U22, mul(third, divU));
+        const f2 s01 = mul(half, add(U01, U10));
+        const f2 s02 = mul(half, add(U02, U20));
+        const f2 s12 = mul(half, add(U12, U21));
+        const f2 S2 = fma2(two, fma2(s01, s01, fma2(s02, s02, mul(s12, s12))),
+                           fma2(s00, s00, fma2(s11, s11, mul(s22, s22))));
+        const f2 SgL0 = fma2(s00, gL0, fma2(s01, gL1, mul(s02, gL2)));
+        const f2 SgL1 = fma2(s01, gL0, fma2(s11, gL1, mul(s12, gL2)));
+        const f2 SgL2 = fma2(s02, gL0, fma2(s12, gL1, mul(s22, gL2)));
+        // Lorentz force
+        const f2 F0 = dif(mul(J1, B2), mul(J2, B1));
+        const f2 F1 = dif(mul(J2, B0), mul(J0, B2));
+        const f2 Fz = dif(mul(J0, B1), mul(J1, B0));
+        const f2 adv0 = fma2(u0, U00, fma2(u1, U01, mul(u2, U02)));
+        const f2 adv1 = fma2(u0, U10, fma2(u1, U11, mul(u2, U12)));
+        const f2 adv2 = fma2(u0, U20, fma2(u1, U21, mul(u2, U22)));
+        out[UX] = add(dif(mul(F0, rho1), add(adv0, mul(T, add(gL0, gT0)))),
+                      mul(nu, fma2(two, SgL0, fma2(third, gdU0, lapU0))));
+        out[UY] = add(dif(mul(F1, rho1), add(adv1, mul(T, add(gL1, gT1)))),
+                      mul(nu, fma2(two, SgL1, fma2(third, gdU1, lapU1))));
+        out[UZ] = add(add(dif(mul(Fz, rho1), add(adv2, mul(T, add(gL2, gT2)))),
+                          mul(nu, fma2(two, SgL2, fma2(third, gdU2, lapU2)))),
+                      F2(ph.gz));
+        // continuity
+        const f2 ugL = fma2(u0, gL0, fma2(u1, gL1, mul(u2, gL2)));
+        const f2 gLs = fma2(gL0, gL0, fma2(gL1, gL1, mul(gL2, gL2)));
+        out[LR] = add(dif(mul(F2(ph.drho), add(lapL, gLs)), add(ugL, divU)), mul(mul(F2(ph.drho_s), w), lapL));
+        // energy (ln T)
+        const f2 ugT = fma2(u0, gT0, fma2(u1, gT1, mul(u2, gT2)));
+        const f2 gTs = fma2(gT0, gT0, fma2(gT1, gT1, mul(gT2, gT2)));
+        const f2 JJ = fma2(J0, J0, fma2(J1, J1, mul(J2, J2)));
+        const f2 T1 = make_float2(1.f / T.x, 1.f / T.y);
+        const f2 heat = mul(mul(gm1, fma2(mul(eta, JJ), rho1, mul(two, mul(nu, S2)))), T1);
+        const f2 ka = dif(mul(F2(2.5f), Th), Lr);
+        const f2 kt = mul(F2(ph.gm1 * ph.kappa0), make_float2(expf(ka.x), expf(ka.y)));
+        out[LT] = add(add(dif(heat, fma2(gm1, divU, ugT)), mul(kt, fma2(F2(3.5f), gTs, lapT))),
+                      mul(mul(F2(ph.chi_s), w), lapT));
+
+        // ---- nudging and boundary rows -----------------------------------------
+        f2 tgx = F2(0.f), tgy = F2(0.f);
+        if (ph.bcz == 0 && k == 0) {
+          const long long q2 = (long long)j * L.nx + i;
+          const f2 v0x = ld2(a.v0 + q2), v1x = ld2(a.v1 + q2);
+          const f2 v0y = ld2(a.v0 + n2 + q2), v1y = ld2(a.v1 + n2 + q2);
+          tgx = mul(F2(rr), fma2(F2(ss_), dif(v1x, v0x), v0x));
+          tgy = mul(F2(rr), fma2(F2(ss_), dif(v1y, v0y), v0y));
+          out[AX] = dif(out[AX], mul(F2(ph.tau_A), dif(A0, ld2(a.axt + q2))));
+          out[AY] = dif(out[AY], mul(F2(ph.tau_A), dif(A1, ld2(a.ayt + q2))));
+          out[UX] = dif(out[UX], mul(F2(ph.tau_u), dif(u0, tgx)));
+          out[UY] = dif(out[UY], mul(F2(ph.tau_u), dif(u1, tgy)));
+          out[UZ] = F2(0.f);
+          out[LR] = F2(0.f);
+        }
+        if (ph.bcz == 0 && k == L.nz - 1) out[UZ] = F2(0.f);
+
+        // ---- RK update and stores (pairs; periodic images) ---------------------
+        // x images: pairs (0,1), (2,3) -> +nx; (nx-4, nx-3), (nx-2, nx-1) -> -nx
+        // (the extra cell of each image pair lands in row padding)
+        const int ox = i < NG ? L.nx : (i + 1 >= L.nx - NG ? -L.nx : 0);
+        const long long oy = j < NG ? (long long)L.ny * L.mx : (j >= L.ny - NG ? -(long long)L.ny * L.mx : 0);
+        const f2 vv[NF] = {A0, A1, A2, u0, u1, u2, vz[LR], vz[LT]};
+#pragma unroll
+        for (int f = 0; f < NF; ++f) {
+          const long long q = cq + (long long)f * L.fs;
+          const f2 dfn = fma2(F2(alpha), dfo[f], mul(F2(dt), out[f]));
+          if (sub < 2) *reinterpret_cast<f2*>(a.df + q) = dfn;
+          if (!eval) {
+            const f2 vn = fma2(F2(beta), dfn, vv[f]);
+            f2* o = reinterpret_cast<f2*>(a.fout + q);
+            o[0] = vn;
+            if (ox) *reinterpret_cast<f2*>(a.fout + q + ox) = vn;
+            if (oy) *reinterpret_cast<f2*>(a.fout + q + oy) = vn;
+            if (ox && oy) *reinterpret_cast<f2*>(a.fout + q + ox + oy) = vn;
+          }
+        }
+        if (ph.bcz == 0 && k == 0) {
+          // stateful u_x, u_y ghost rows below the photosphere: nudging only;
+          // their values are the TMEM copies of planes -1 .. -3
+#pragma unroll
+          for (int m = 1; m <= NG; ++m) {
+#pragma unroll
+            for (int cc = 0; cc < 2; ++cc) {
+              const long long q = L.at(UX + cc, -m, j, i);
+              const f2 u = cc == 0 ? gux[m - 1] : guy[m - 1];
+              const f2 rh = mul(F2(-ph.tau_u), dif(u, cc == 0 ? tgx : tgy));
+              const f2 dfn = fma2(F2(alpha), sub > 0 ? ld2(a.df + q) : F2(0.f), mul(F2(dt), rh));
+              if (sub < 2) *reinterpret_cast<f2*>(a.df + q) = dfn;
+              if (!eval) {
+                const f2 vn = fma2(F2(beta), dfn, u);
+                *reinterpret_cast<f2*>(a.fout + q) = vn;
+                if (ox) *reinterpret_cast<f2*>(a.fout + q + ox) = vn;
+                if (oy) *reinterpret_cast<f2*>(a.fout + q + oy) = vn;
+                if (ox && oy) *reinterpret_cast<f2*>(a.fout + q + ox + oy) = vn;
+              }
+            }
+          }
+        }
+      }
+    }
+    if (!bad) {
+      // all threads are past the last centre: the next item may refill any slot
+      __syncthreads();
+    }
+  }
+  if (bad && tid == 0) {
+    // a ring wait timed out: record it and drain the copies in flight (bounded)
+    atomicOr(&a.ss->nonfinite, 2);
+    for (int s = 0; s < NR; ++s)
+      if (pending & (1u << s)) zm::mbar_wait(&mbar[s], (phase >> s) & 1u);
+  }
+  tm_wait_st();
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(TMEM_COLS) : "memory");
+}
+
+}  // namespace pair
+
+static int g_pair_ctas = 0;
+
+bool rk_pair_supported(const Layout& L) { return L.nx % 2 == 0 && L.nx >= 8 && L.ny >= 6; }
+
+void launch_rk_pair(const CUtensorMap* tm, const Layout& L, const Phys<float>& ph, const Background<float>& bg,
+                    float* fout, float* df, const float* wtab, const float* wptab, const Driver& drv, StepState* ss,
+                    int sub, double dx, double dy, double dz, cudaStream_t st) {
+  if (!g_pair_ctas) {
+    cudaFuncSetAttribute(pair::rk_pair_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pair::SMEM_BYTES);
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    // two CTAs per SM: the shared ring admits no third (and TMEM holds two)
+    g_pair_ctas = 2 * sms;
+  }
+  pair::Args a{};
+  a.L = L;
+  a.ph = ph;
+  a.bg = bg;
+  a.fout = fout;
+  a.df = df;
+  a.wtab = wtab;
+  a.wptab = wptab;
+  a.axt = (const float*)drv.axt;
+  a.ayt = (const float*)drv.ayt;
+  a.v0 = (const float*)drv.v0;
+  a.v1 = (const float*)drv.v1;
+  a.ss = ss;
+  a.sub = sub;
+  a.ntx = (L.nx + pair::TX - 1) / pair::TX;
+  a.nty = (L.ny + pair::TY - 1) / pair::TY;
+  const double W1[4] = {0.0, 45.0 / 60.0, -9.0 / 60.0, 1.0 / 60.0};
+  const double W2[4] = {-490.0 / 180.0, 270.0 / 180.0, -27.0 / 180.0, 2.0 / 180.0};
+  auto coef = [&](double h) {
+    pair::Coef c;
+    c.c1 = make_float2((float)(W1[1] / h), (float)(W1[1] / h));
+    c.c2 = make_float2((float)(W1[2] / h), (float)(W1[2] / h));
+    c.c3 = make_float2((float)(W1[3] / h), (float)(W1[3] / h));
+    c.e0 = make_float2((float)(W2[0] / (h * h)), (float)(W2[0] / (h * h)));
+    c.e1 = make_float2((float)(W2[1] / (h * h)), (float)(W2[1] / (h * h)));
+    c.e2 = make_float2((float)(W2[2] / (h * h)), (float)(W2[2] / (h * h)));
+    c.e3 = make_float2((float)(W2[3] / (h * h)), (float)(W2[3] / (h * h)));
+    return c;
+  };
+  a.cx = coef(dx);
+  a.cy = coef(dy);
+  a.cz = coef(dz);
+  const int tiles = a.ntx * a.nty;
+  a.kchunk = zm::zchunk(L.nz, tiles, g_pair_ctas);
+  a.nch = (L.nz + a.kchunk - 1) / a.kchunk;
+  const int nitems = tiles * a.nch;
+  const int grid = nitems < g_pair_ctas ? nitems : g_pair_ctas;
+  pair::rk_pair_kernel<<<grid, pair::NT, pair::SMEM_BYTES, st>>>(*tm, a);
+}
+
+}  // namespace mhd

@@ -222,13 +222,15 @@ def _eval_with_variant(case, variant, t=0.29, params=None, driver=True):
     return out, u
 
 
-@pytest.mark.parametrize("variant", ["tiled", "fused"])
+@pytest.mark.parametrize("variant", ["pair", "tiled", "fused"])
 @pytest.mark.parametrize("shape,bcz", [((16, 16, 12), 0), ((64, 32, 41), 0), ((40, 24, 20), 1)])
 def test_tiled_kernel_matches_simple_fp32(shape, bcz, variant):
-    """The TMA-fed z-march kernels (default: the split A / rest passes;
-    "fused": one pass over all 8 fields) against the one-thread-per-cell
-    kernel: same FP32 discretisation, different summation order; tiles
-    ragged in x (16 < 32) and chunks ragged in z (41 layers)."""
+    """The TMA-fed z-march kernels (default "pair": one pass, two cells per
+    thread in f32x2, z histories in TMEM; "tiled": the split A / rest
+    passes; "fused": one pass over all 8 fields, one cell per thread)
+    against the one-thread-per-cell kernel: same FP32 discretisation,
+    different summation order; tiles ragged in x (16 < 32) and chunks
+    ragged in z (41 layers)."""
     nx, ny, nz = shape
     case = _perturbed(nx, ny, nz, seed=11)
     p = dict(case.params, bc_z=bcz)
