@@ -19,6 +19,7 @@ struct mhd_ctx {
                        // third substep state (64-byte aligned)
   CUtensorMap tma[2];  // the two state sets, boxes of A only (split pass A)
   CUtensorMap tmr[2];  // the two state sets, boxes of u, ln rho, ln T (split pass R)
+  CUtensorMap tmdf;    // the RK accumulator, 32 x 8 tiles of the 8 fields (pair kernel)
   bool tiled;          // FP32: TMA-fed z-march kernels; otherwise the simple kernel
   bool split;          // FP32 forward: split passes (else the fused z-march kernel)
   bool pair;           // FP32 forward: one-pass f32x2 kernel with TMEM z histories
@@ -393,7 +394,7 @@ static void launch_rk_any(mhd_ctx* h, const R* fin, R* fout, int sub) {
   Driver drv{h->axt, h->ayt, h->v0, h->v1};
   if (sizeof(R) == 4 && h->pair) {
     const int which = (const void*)fin == h->f[0] ? 0 : 1;
-    launch_rk_pair(&h->tm[which], h->L, *(const Phys<float>*)&ph, h->bgf, (float*)fout, (float*)h->df,
+    launch_rk_pair(&h->tm[which], &h->tmdf, h->L, *(const Phys<float>*)&ph, h->bgf, (float*)fout, (float*)h->df,
                    (const float*)h->wtab, (const float*)h->wptab, drv, h->ss, sub, h->p.dx, h->p.dy, h->p.dz, h->st);
     return;
   }
@@ -602,6 +603,8 @@ extern "C" int mhd_create(const mhd_params* p, void* workspace, size_t ws_bytes,
       if (make_state_tensor_map(&h->tma[s], h->L, h->f[s], 3) != 0 ||
           make_state_tensor_map(&h->tmr[s], h->L, h->f[s], 5) != 0)
         rc = fail(h, MHD_ERR_CUDA, "cuTensorMapEncodeTiled failed for the split boxes of state set %d", s);
+    if (!rc && make_state_tensor_map(&h->tmdf, h->L, h->df, NF, 32, 8) != 0)
+      rc = fail(h, MHD_ERR_CUDA, "cuTensorMapEncodeTiled failed for the RK accumulator");
   }
   if (!rc) {
     StepState s0;

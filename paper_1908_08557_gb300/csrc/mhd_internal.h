@@ -58,8 +58,10 @@ void launch_adj_point_tiled(const CUtensorMap* tm, const Layout& L, const Phys<f
                             const float* wtab, const float* wptab, StepState* ss, int sub, double dx, double dy,
                             double dz, cudaStream_t st);
 // tensor map of one padded FP32 state set (dims mx, my, mz, 8 fields) whose box is
-// one plane with its halo (40 x 14 x 1) of box_fields consecutive fields
-int make_state_tensor_map(CUtensorMap* tm, const Layout& L, void* base, int box_fields = NF);
+// one plane (box_x x box_y x 1; default a 32 x 8 tile with its halo, 40 x 14)
+// of box_fields consecutive fields
+int make_state_tensor_map(CUtensorMap* tm, const Layout& L, void* base, int box_fields = NF, int box_x = 40,
+                          int box_y = 14);
 // FP32 right-hand side + RK update as two z-march passes (A -> B, J, swamp terms;
 // then u, ln rho, ln T with the physics and the update); tm_a, tm_r map the input
 // state with 3-field (A) and 5-field (u_x .. ln T) boxes
@@ -69,9 +71,10 @@ void launch_rk_split(const CUtensorMap* tm_a, const CUtensorMap* tm_r, const Lay
                      double dx, double dy, double dz, cudaStream_t st);
 // FP32 right-hand side + RK update in one z-march pass, two x-adjacent cells
 // per thread (f32x2), z histories in TMEM; tm maps the input state with
-// 8-field boxes.  Requires nx even, nx >= 8, ny >= 6.
+// 8-field halo boxes, tmd the RK accumulator with 8-field 32 x 8 tiles.
+// Requires nx even, nx >= 8, ny >= 6.
 bool rk_pair_supported(const Layout& L);
-void launch_rk_pair(const CUtensorMap* tm, const Layout& L, const Phys<float>& ph, const Background<float>& bg,
+void launch_rk_pair(const CUtensorMap* tm, const CUtensorMap* tmd, const Layout& L, const Phys<float>& ph, const Background<float>& bg,
                     float* fout, float* df, const float* wtab, const float* wptab, const Driver& drv, StepState* ss,
                     int sub, double dx, double dy, double dz, cudaStream_t st);
 // adjoint (transposed linearisation of one substep)

@@ -41,7 +41,8 @@ constexpr int FP = BY * BX;              // floats per field plane of a box
 constexpr int PLANE = NF * FP;           // floats per ring slot (17920 B)
 constexpr int NSC = 4;                   // scratch fields: D1y A_y, D1y A_x, D1y u_y, D1y u_x
 constexpr int SCF = TY * BX;             // floats per scratch field
-constexpr size_t SMEM_BYTES = (size_t)NR * PLANE * 4 + (size_t)NSC * SCF * 4 + NR * 8 + 16;
+constexpr int DFT = NF * TY * TX;        // floats per RK-accumulator tile (8 KB)
+constexpr size_t SMEM_BYTES = (size_t)NR * PLANE * 4 + (size_t)NSC * SCF * 4 + (size_t)2 * DFT * 4 + (NR + 2) * 8 + 16;
 static_assert(SMEM_BYTES > 233472 / 3, "ring must keep TMEM users at <= 2 CTAs per SM");
 constexpr int TMEM_COLS = 256;
 constexpr int VCOL = 0, SCOL = 128;      // value / source rings in TMEM
@@ -127,18 +128,23 @@ __device__ __forceinline__ void ds_pair(const float* p, int s, const Coef& c, f2
 }
 
 // ---- the kernel -------------------------------------------------------------
-__global__ void __launch_bounds__(NT, 2) rk_pair_kernel(const __grid_constant__ CUtensorMap tm, const Args a) {
+__global__ void __launch_bounds__(NT, 2) rk_pair_kernel(const __grid_constant__ CUtensorMap tm,
+                                                        const __grid_constant__ CUtensorMap tmd, const Args a) {
   extern __shared__ __align__(128) float smem[];
   float* raw = smem;
   float* scr = raw + NR * PLANE;
-  uint64_t* mbar = (uint64_t*)(scr + NSC * SCF);
-  uint32_t* tslot = (uint32_t*)(mbar + NR);
+  float* dfs = scr + NSC * SCF;           // RK accumulator tiles of centres k (double buffer)
+  uint64_t* mbar = (uint64_t*)(dfs + 2 * DFT);
+  uint64_t* mbd = mbar + NR;
+  uint32_t* tslot = (uint32_t*)(mbd + 2);
 
   const Layout& L = a.L;
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4, warp = tid >> 5;
   if (halted(a.ss)) return;
   if (tid == 0) {
     for (int s = 0; s < NR; ++s) zm::mbar_init(&mbar[s]);
+    zm::mbar_init(&mbd[0]);
+    zm::mbar_init(&mbd[1]);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
@@ -169,11 +175,18 @@ __global__ void __launch_bounds__(NT, 2) rk_pair_kernel(const __grid_constant__ 
   // halo item of the xy-mixed scratch: field hq = warp, row hr, box x hx
   const int hq = warp, hr = (tid & 31) >> 2, hx = ((tid & 3) < 2) ? 2 * (tid & 3) : 32 + 2 * (tid & 3);
   const int hfield = hq == 0 ? AY : (hq == 1 ? AX : (hq == 2 ? UY : UX));
-  uint32_t phase = 0, pending = 0;
+  uint32_t phase = 0, pending = 0;        // shared ring: parities, copies in flight (thread 0)
+  uint32_t dphase = 0, dpending = 0;      // accumulator tiles: the same
   const int nitems = a.ntx * a.nty * a.nch;
   const long long n2 = (long long)L.nx * L.ny;
   bool bad = false;
 
+  // RK accumulator tile of centre k (sub > 0) into buffer (k - k0) & 1
+  auto load_df = [&](int k, int k0, int x0, int y0) {
+    const int s = (k - k0) & 1;
+    zm::tma_plane(&tmd, dfs + s * DFT, &mbd[s], DFT * 4, x0 + XOFF, y0 + NG, k + NG, 0);
+    dpending |= 1u << s;
+  };
   auto load = [&](int p, int pbase, int x0, int y0) {
     const int s = (p - pbase) % NR;
     zm::tma_plane(&tm, raw + s * PLANE, &mbar[s], PLANE * 4, x0, y0, p + NG, 0);
@@ -217,8 +230,10 @@ __global__ void __launch_bounds__(NT, 2) rk_pair_kernel(const __grid_constant__ 
     const int x0 = (tile % a.ntx) * TX, y0 = (tile / a.ntx) * TY;
     const int k0 = ch * a.kchunk, k1 = min(L.nz, k0 + a.kchunk);
     const int pbase = k0 - NG, plast = k1 + NG - 1;
-    if (tid == 0)
+    if (tid == 0) {
       for (int p = pbase; p <= min(pbase + NR - 1, plast); ++p) load(p, pbase, x0, y0);
+      if (sub > 0) load_df(k0, k0, x0, y0);
+    }
     // prologue: planes k0-3 .. k0+2; the three below k0 are released at once
     for (int p = pbase; p < k0 + NG && !bad; ++p) {
       bad = !wait(p, pbase);
@@ -231,14 +246,18 @@ __global__ void __launch_bounds__(NT, 2) rk_pair_kernel(const __grid_constant__ 
       const int i = x0 + 2 * tx, j = y0 + ty;
       const bool live = i < L.nx && j < L.ny;
       const long long cq = live ? L.at(0, k, j, i) : 0;
-      // RK accumulator of the pair, fetched before the waits
-      f2 dfo[NF];
-#pragma unroll
-      for (int f = 0; f < NF; ++f) dfo[f] = (live && sub > 0) ? __ldg(reinterpret_cast<const f2*>(a.df + cq + (long long)f * L.fs)) : F2(0.f);
+      // per-layer tables, fetched before the waits
+      const float wk = a.wtab[k], wpk = a.wptab[k];
+      const float lbk = a.bg.lbar[k + NG], tbk = a.bg.tbar[k + NG];
+      const float dlk = a.bg.dl[k], dtk = a.bg.dt[k], d2lk = a.bg.d2l[k], d2tk = a.bg.d2t[k];
       bad = !wait(k + NG, pbase);
       if (bad) break;
-      // every thread is past centre k - 1: plane k - 1's slot takes k + 4
-      if (k > k0 && tid == 0 && k - 1 + NR <= plast) load(k - 1 + NR, pbase, x0, y0);
+      if (tid == 0) {
+        // every thread is past centre k - 1: plane k - 1's slot takes k + 4,
+        // and its accumulator buffer the tile of centre k + 1
+        if (k > k0 && k - 1 + NR <= plast) load(k - 1 + NR, pbase, x0, y0);
+        if (sub > 0 && k + 1 < k1) load_df(k + 1, k0, x0, y0);
+      }
       front(k + NG, pbase);
       tm_wait_st();
 
@@ -272,34 +291,6 @@ __global__ void __launch_bounds__(NT, 2) rk_pair_kernel(const __grid_constant__ 
         for (int q = 0; q < 6; ++q) mz[q] = fma2(cm, dif(sp.get(q), sm.get(q)), mz[q]);
       }
 
-      // ---- x, y derivatives from the shared ring ----------------------------
-      const bool swamp = a.wtab[k] != 0.f || a.wptab[k] != 0.f;
-      f2 dxv[NF], dyv[NF], xxv[NF], yyv[NF];
-#pragma unroll
-      for (int f = 0; f < NF; ++f) {
-        const bool needx2 = !(f == AX) || swamp;  // D2x A_x cancels in J
-        const bool needy2 = !(f == AY) || swamp;  // D2y A_y cancels in J
-        dx_pair(Pk + f * FP, a.cx, dxv[f], needx2 ? &xxv[f] : nullptr);
-        ds_pair(Pk + f * FP, BX, a.cy, dyv[f], needy2 ? &yyv[f] : nullptr);
-        if (!needx2) xxv[f] = F2(0.f);
-        if (!needy2) yyv[f] = F2(0.f);
-      }
-      // xy-mixed: D1y of A_y, A_x, u_y, u_x on the tile plus x halo
-      {
-        float* sc = scr + ty * BX + e;
-        *reinterpret_cast<f2*>(sc + 0 * SCF) = dyv[AY];
-        *reinterpret_cast<f2*>(sc + 1 * SCF) = dyv[AX];
-        *reinterpret_cast<f2*>(sc + 2 * SCF) = dyv[UY];
-        *reinterpret_cast<f2*>(sc + 3 * SCF) = dyv[UX];
-        f2 h;
-        ds_pair(raw + ((k - pbase) % NR) * PLANE + hfield * FP + (hr + 3) * BX + hx, BX, a.cy, h, nullptr);
-        *reinterpret_cast<f2*>(scr + hq * SCF + hr * BX + hx) = h;
-      }
-      __syncthreads();
-      f2 mxy[4];
-#pragma unroll
-      for (int q = 0; q < 4; ++q) dx_pair(scr + q * SCF + ty * BX + e, a.cx, mxy[q], nullptr);
-
       // stateful u_x, u_y ghost rows below the photosphere (k = 0): their
       // values are the TMEM copies of planes -1 .. -3 (loaded warp-wide)
       f2 gux[NG], guy[NG];
@@ -315,51 +306,122 @@ __global__ void __launch_bounds__(NT, 2) rk_pair_kernel(const __grid_constant__ 
           guy[m - 1] = make_float2(__uint_as_float(g[2]), __uint_as_float(g[3]));
         }
       }
-      if (live) {
-        // ---- pointwise physics of the pair ----------------------------------
-        const Phys<float>& ph = a.ph;
-        const f2 w = F2(a.wtab[k]), wp = F2(a.wptab[k]);
-        const f2 A0 = vz[AX], A1 = vz[AY], A2 = vz[AZ];
-        const f2 u0 = vz[UX], u1 = vz[UY], u2 = vz[UZ];
-        // B = curl A + B_ext, J = grad div A - lap A (own-axis D2 cancelled
-        // outside the swamp), swamp terms of the induction equation
-        const f2 B0 = add(dif(dyv[AZ], d1z[AY]), F2(ph.bext[0]));
-        const f2 B1 = add(dif(d1z[AX], dxv[AZ]), F2(ph.bext[1]));
-        const f2 B2 = add(dif(dxv[AY], dyv[AX]), F2(ph.bext[2]));
-        f2 J0, J1, J2, sw0 = F2(0.f), sw1 = F2(0.f), sw2 = F2(0.f);
+
+      // ---- x, y derivatives from the shared ring, folded as they come -------
+      // (the own-axis second derivatives D2x A_x, D2y A_y cancel in J outside
+      // the swamp layers)
+      const bool swamp = wk != 0.f || wpk != 0.f;
+      // y derivatives of A_y, A_x, u_y, u_x: also the sources of the xy-mixed
+      // terms D1x(D1y .), through the scratch with an x halo
+      f2 dyAy, dyAx, yyAx, dyUy, yyUy, dyUx, yyUx, yyAy = F2(0.f);
+      if (swamp)
+        ds_pair(Pk + AY * FP, BX, a.cy, dyAy, &yyAy);
+      else
+        ds_pair(Pk + AY * FP, BX, a.cy, dyAy, nullptr);
+      ds_pair(Pk + AX * FP, BX, a.cy, dyAx, &yyAx);
+      ds_pair(Pk + UY * FP, BX, a.cy, dyUy, &yyUy);
+      ds_pair(Pk + UX * FP, BX, a.cy, dyUx, &yyUx);
+      {
+        float* sc = scr + ty * BX + e;
+        *reinterpret_cast<f2*>(sc + 0 * SCF) = dyAy;
+        *reinterpret_cast<f2*>(sc + 1 * SCF) = dyAx;
+        *reinterpret_cast<f2*>(sc + 2 * SCF) = dyUy;
+        *reinterpret_cast<f2*>(sc + 3 * SCF) = dyUx;
+        f2 h;
+        ds_pair(raw + ((k - pbase) % NR) * PLANE + hfield * FP + (hr + 3) * BX + hx, BX, a.cy, h, nullptr);
+        *reinterpret_cast<f2*>(scr + hq * SCF + hr * BX + hx) = h;
+      }
+      __syncthreads();
+      f2 mxy[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) dx_pair(scr + q * SCF + ty * BX + e, a.cx, mxy[q], nullptr);
+
+      const Phys<float>& ph = a.ph;
+      const f2 w = F2(wk), wp = F2(wpk);
+      // A: B = curl A + B_ext, J = grad div A - lap A, swamp terms of the
+      // induction equation
+      f2 B0, B1, B2, J0, J1, J2, sw0 = F2(0.f), sw1 = F2(0.f), sw2 = F2(0.f);
+      {
+        f2 dxAy, xxAy, dxAz, xxAz, dyAz, yyAz;
+        dx_pair(Pk + AY * FP, a.cx, dxAy, &xxAy);
+        dx_pair(Pk + AZ * FP, a.cx, dxAz, &xxAz);
+        ds_pair(Pk + AZ * FP, BX, a.cy, dyAz, &yyAz);
+        B0 = add(dif(dyAz, d1z[AY]), F2(ph.bext[0]));
+        B1 = add(dif(d1z[AX], dxAz), F2(ph.bext[1]));
+        B2 = add(dif(dxAy, dyAx), F2(ph.bext[2]));
         if (!swamp) {
-          J0 = dif(dif(add(mxy[0], mz[0]), yyv[AX]), d2z[AX]);
-          J1 = dif(dif(add(mxy[1], mz[1]), xxv[AY]), d2z[AY]);
-          J2 = dif(dif(mz[2], xxv[AZ]), yyv[AZ]);
+          J0 = dif(dif(add(mxy[0], mz[0]), yyAx), d2z[AX]);
+          J1 = dif(dif(add(mxy[1], mz[1]), xxAy), d2z[AY]);
+          J2 = dif(dif(mz[2], xxAz), yyAz);
         } else {
-          const f2 lap0 = add(add(xxv[AX], yyv[AX]), d2z[AX]);
-          const f2 lap1 = add(add(xxv[AY], yyv[AY]), d2z[AY]);
-          const f2 lap2 = add(add(xxv[AZ], yyv[AZ]), d2z[AZ]);
-          J0 = dif(add(add(xxv[AX], mxy[0]), mz[0]), lap0);
-          J1 = dif(add(add(mxy[1], yyv[AY]), mz[1]), lap1);
+          f2 dxAx, xxAx;
+          dx_pair(Pk + AX * FP, a.cx, dxAx, &xxAx);
+          const f2 lap0 = add(add(xxAx, yyAx), d2z[AX]);
+          const f2 lap1 = add(add(xxAy, yyAy), d2z[AY]);
+          const f2 lap2 = add(add(xxAz, yyAz), d2z[AZ]);
+          J0 = dif(add(add(xxAx, mxy[0]), mz[0]), lap0);
+          J1 = dif(add(add(mxy[1], yyAy), mz[1]), lap1);
           J2 = dif(add(mz[2], d2z[AZ]), lap2);
           const f2 ews = mul(F2(ph.eta_s), w);
-          const f2 divA = add(add(dxv[AX], dyv[AY]), d1z[AZ]);
+          const f2 divA = add(add(dxAx, dyAy), d1z[AZ]);
           sw0 = mul(ews, lap0);
           sw1 = mul(ews, lap1);
           sw2 = fma2(mul(F2(ph.eta_s), wp), divA, mul(ews, lap2));
         }
-        // dU[c][a] = d_a u_c
-        const f2 U00 = dxv[UX], U01 = dyv[UX], U02 = d1z[UX];
-        const f2 U10 = dxv[UY], U11 = dyv[UY], U12 = d1z[UY];
-        const f2 U20 = dxv[UZ], U21 = dyv[UZ], U22 = d1z[UZ];
-        const f2 lapU0 = add(add(xxv[UX], yyv[UX]), d2z[UX]);
-        const f2 lapU1 = add(add(xxv[UY], yyv[UY]), d2z[UY]);
-        const f2 lapU2 = add(add(xxv[UZ], yyv[UZ]), d2z[UZ]);
-        const f2 gdU0 = add(add(xxv[UX], mxy[2]), mz[3]);
-        const f2 gdU1 = add(add(mxy[3], yyv[UY]), mz[4]);
-        const f2 gdU2 = add(mz[5], d2z[UZ]);
-        const f2 Lr = add(F2(a.bg.lbar[k + NG]), vz[LR]);
-        const f2 Th = add(F2(a.bg.tbar[k + NG]), vz[LT]);
-        const f2 gL0 = dxv[LR], gL1 = dyv[LR], gL2 = add(d1z[LR], F2(a.bg.dl[k]));
-        const f2 gT0 = dxv[LT], gT1 = dyv[LT], gT2 = add(d1z[LT], F2(a.bg.dt[k]));
-        const f2 lapL = add(add(add(xxv[LR], yyv[LR]), d2z[LR]), F2(a.bg.d2l[k]));
-        const f2 lapT = add(add(add(xxv[LT], yyv[LT]), d2z[LT]), F2(a.bg.d2t[k]));
+      }
+      // u: dU[c][a] = d_a u_c, lap u, grad div u
+      f2 U00, U10, U20, U21, lapU0, lapU1, lapU2, gdU0, gdU1, gdU2;
+      {
+        f2 xxUx, xxUy, xxUz, yyUz;
+        dx_pair(Pk + UX * FP, a.cx, U00, &xxUx);
+        dx_pair(Pk + UY * FP, a.cx, U10, &xxUy);
+        dx_pair(Pk + UZ * FP, a.cx, U20, &xxUz);
+        ds_pair(Pk + UZ * FP, BX, a.cy, U21, &yyUz);
+        lapU0 = add(add(xxUx, yyUx), d2z[UX]);
+        lapU1 = add(add(xxUy, yyUy), d2z[UY]);
+        lapU2 = add(add(xxUz, yyUz), d2z[UZ]);
+        gdU0 = add(add(xxUx, mxy[2]), mz[3]);
+        gdU1 = add(add(mxy[3], yyUy), mz[4]);
+        gdU2 = add(mz[5], d2z[UZ]);
+      }
+      const f2 U01 = dyUx, U02 = d1z[UX];
+      const f2 U11 = dyUy, U12 = d1z[UY];
+      const f2 U22 = d1z[UZ];
+      // ln rho, ln T (perturbations about the background profiles)
+      f2 gL0, gL1, lapL, gT0, gT1, lapT;
+      {
+        f2 xx, yy;
+        dx_pair(Pk + LR * FP, a.cx, gL0, &xx);
+        ds_pair(Pk + LR * FP, BX, a.cy, gL1, &yy);
+        lapL = add(add(add(xx, yy), d2z[LR]), F2(d2lk));
+        dx_pair(Pk + LT * FP, a.cx, gT0, &xx);
+        ds_pair(Pk + LT * FP, BX, a.cy, gT1, &yy);
+        lapT = add(add(add(xx, yy), d2z[LT]), F2(d2tk));
+      }
+      const f2 gL2 = add(d1z[LR], F2(dlk));
+      const f2 gT2 = add(d1z[LT], F2(dtk));
+      // RK accumulator of the pair (bounded wait; a time-out is recorded and
+      // the step continues, so the CTA stays convergent)
+      f2 dfo[NF];
+      if (sub > 0) {
+        const int sl = (k - k0) & 1;
+        if (!zm::mbar_wait(&mbd[sl], (dphase >> sl) & 1u)) atomicOr(&a.ss->nonfinite, 2);
+        dphase ^= 1u << sl;
+        if (tid == 0) dpending &= ~(1u << sl);
+        const float* dq = dfs + sl * DFT + ty * TX + 2 * tx;
+#pragma unroll
+        for (int f = 0; f < NF; ++f) dfo[f] = ld2(dq + f * TY * TX);
+      } else {
+#pragma unroll
+        for (int f = 0; f < NF; ++f) dfo[f] = F2(0.f);
+      }
+
+      if (live) {
+        // ---- pointwise physics of the pair ----------------------------------
+        const f2 A0 = vz[AX], A1 = vz[AY], A2 = vz[AZ];
+        const f2 u0 = vz[UX], u1 = vz[UY], u2 = vz[UZ];
+        const f2 Lr = add(F2(lbk), vz[LR]);
+        const f2 Th = add(F2(tbk), vz[LT]);
 
         const f2 divU = add(add(U00, U11), U22);
         const f2 T = make_float2(expf(Th.x), expf(Th.y));
@@ -481,6 +543,8 @@ __global__ void __launch_bounds__(NT, 2) rk_pair_kernel(const __grid_constant__ 
     atomicOr(&a.ss->nonfinite, 2);
     for (int s = 0; s < NR; ++s)
       if (pending & (1u << s)) zm::mbar_wait(&mbar[s], (phase >> s) & 1u);
+    for (int s = 0; s < 2; ++s)
+      if (dpending & (1u << s)) zm::mbar_wait(&mbd[s], (dphase >> s) & 1u);
   }
   tm_wait_st();
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -496,7 +560,7 @@ static int g_pair_ctas = 0;
 
 bool rk_pair_supported(const Layout& L) { return L.nx % 2 == 0 && L.nx >= 8 && L.ny >= 6; }
 
-void launch_rk_pair(const CUtensorMap* tm, const Layout& L, const Phys<float>& ph, const Background<float>& bg,
+void launch_rk_pair(const CUtensorMap* tm, const CUtensorMap* tmd, const Layout& L, const Phys<float>& ph, const Background<float>& bg,
                     float* fout, float* df, const float* wtab, const float* wptab, const Driver& drv, StepState* ss,
                     int sub, double dx, double dy, double dz, cudaStream_t st) {
   if (!g_pair_ctas) {
@@ -544,7 +608,7 @@ void launch_rk_pair(const CUtensorMap* tm, const Layout& L, const Phys<float>& p
   a.nch = (L.nz + a.kchunk - 1) / a.kchunk;
   const int nitems = tiles * a.nch;
   const int grid = nitems < g_pair_ctas ? nitems : g_pair_ctas;
-  pair::rk_pair_kernel<<<grid, pair::NT, pair::SMEM_BYTES, st>>>(*tm, a);
+  pair::rk_pair_kernel<<<grid, pair::NT, pair::SMEM_BYTES, st>>>(*tm, *tmd, a);
 }
 
 }  // namespace mhd

@@ -458,9 +458,9 @@ void launch_adj_point_tiled(const CUtensorMap* tm, const Layout& L, const Phys<f
 }
 
 // Tensor map of one padded FP32 state set: dims (mx, my, mz, 8 fields),
-// box (40, 14, 1, box_fields) = one plane of box_fields consecutive fields
-// with its halo.
-int make_state_tensor_map(CUtensorMap* tm, const Layout& L, void* base, int box_fields) {
+// box (box_x, box_y, 1, box_fields) = one plane of box_fields consecutive
+// fields (default 40 x 14: a 32 x 8 tile with its halo).
+int make_state_tensor_map(CUtensorMap* tm, const Layout& L, void* base, int box_fields, int box_x, int box_y) {
   typedef CUresult (*EncodeFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
                                CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
@@ -476,7 +476,7 @@ int make_state_tensor_map(CUtensorMap* tm, const Layout& L, void* base, int box_
   }
   cuuint64_t dims[4] = {(cuuint64_t)L.mx, (cuuint64_t)L.my, (cuuint64_t)L.mz, (cuuint64_t)NF};
   cuuint64_t strides[3] = {(cuuint64_t)L.mx * 4, (cuuint64_t)L.my * L.mx * 4, (cuuint64_t)L.fs * 4};
-  cuuint32_t box[4] = {(cuuint32_t)tiled::BX, (cuuint32_t)tiled::BY, 1, (cuuint32_t)box_fields};
+  cuuint32_t box[4] = {(cuuint32_t)box_x, (cuuint32_t)box_y, 1, (cuuint32_t)box_fields};
   cuuint32_t es[4] = {1, 1, 1, 1};
   CUresult r = enc(tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, base, dims, strides, box, es,
                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
