@@ -187,14 +187,14 @@ __global__ void __launch_bounds__(NT, 2) rk_pair_kernel(const __grid_constant__ 
     zm::tma_plane(&tmd, dfs + s * DFT, &mbd[s], DFT * 4, x0 + XOFF, y0 + NG, k + NG, 0);
     dpending |= 1u << s;
   };
-  auto load = [&](int p, int pbase, int x0, int y0) {
-    const int s = (p - pbase) % NR;
+  // ring slots are tracked incrementally (slot of plane p = (p - pbase) mod NR)
+  auto wrap = [](int s) { return s >= NR ? s - NR : s; };
+  auto load = [&](int p, int s, int x0, int y0) {
     zm::tma_plane(&tm, raw + s * PLANE, &mbar[s], PLANE * 4, x0, y0, p + NG, 0);
     pending |= 1u << s;
   };
   // collective bounded wait for plane p; false on time-out (uniform)
-  auto wait = [&](int p, int pbase) -> bool {
-    const int s = (p - pbase) % NR;
+  auto wait = [&](int s) -> bool {
     const bool to = !zm::mbar_wait(&mbar[s], (phase >> s) & 1u);
     if (__syncthreads_or(to)) return false;
     phase ^= 1u << s;
@@ -202,8 +202,8 @@ __global__ void __launch_bounds__(NT, 2) rk_pair_kernel(const __grid_constant__ 
     return true;
   };
   // front of plane p: values and mixed sources of the pair into TMEM
-  auto front = [&](int p, int pbase) {
-    const float* P = raw + ((p - pbase) % NR) * PLANE + cen;
+  auto front = [&](int p, int sp) {
+    const float* P = raw + sp * PLANE + cen;
     V16 v, s;
 #pragma unroll
     for (int f = 0; f < NF; ++f) v.set(f, ld2(P + f * FP));
@@ -231,18 +231,21 @@ __global__ void __launch_bounds__(NT, 2) rk_pair_kernel(const __grid_constant__ 
     const int k0 = ch * a.kchunk, k1 = min(L.nz, k0 + a.kchunk);
     const int pbase = k0 - NG, plast = k1 + NG - 1;
     if (tid == 0) {
-      for (int p = pbase; p <= min(pbase + NR - 1, plast); ++p) load(p, pbase, x0, y0);
+      for (int p = pbase; p <= min(pbase + NR - 1, plast); ++p) load(p, p - pbase, x0, y0);
       if (sub > 0) load_df(k0, k0, x0, y0);
     }
     // prologue: planes k0-3 .. k0+2; the three below k0 are released at once
     for (int p = pbase; p < k0 + NG && !bad; ++p) {
-      bad = !wait(p, pbase);
+      const int sp = wrap(p - pbase);
+      bad = !wait(sp);
       if (bad) break;
       // every thread is past the front of p - 1; below k0 that was its last use
-      if (p > pbase && p - 1 < k0 && tid == 0 && p - 1 + NR <= plast) load(p - 1 + NR, pbase, x0, y0);
-      front(p, pbase);
+      if (p > pbase && p - 1 < k0 && tid == 0 && p - 1 + NR <= plast) load(p - 1 + NR, p - 1 - pbase, x0, y0);
+      front(p, sp);
     }
-    for (int k = k0; k < k1 && !bad; ++k) {
+    int sk = NG;  // slot of centre k (k0 - pbase = NG < NR)
+    for (int k = k0; k < k1 && !bad; ++k, sk = wrap(sk + 1)) {
+      const int s3 = wrap(sk + NG);  // slot of plane k + 3
       const int i = x0 + 2 * tx, j = y0 + ty;
       const bool live = i < L.nx && j < L.ny;
       const long long cq = live ? L.at(0, k, j, i) : 0;
@@ -250,18 +253,18 @@ __global__ void __launch_bounds__(NT, 2) rk_pair_kernel(const __grid_constant__ 
       const float wk = a.wtab[k], wpk = a.wptab[k];
       const float lbk = a.bg.lbar[k + NG], tbk = a.bg.tbar[k + NG];
       const float dlk = a.bg.dl[k], dtk = a.bg.dt[k], d2lk = a.bg.d2l[k], d2tk = a.bg.d2t[k];
-      bad = !wait(k + NG, pbase);
+      bad = !wait(s3);
       if (bad) break;
       if (tid == 0) {
         // every thread is past centre k - 1: plane k - 1's slot takes k + 4,
         // and its accumulator buffer the tile of centre k + 1
-        if (k > k0 && k - 1 + NR <= plast) load(k - 1 + NR, pbase, x0, y0);
+        if (k > k0 && k - 1 + NR <= plast) load(k - 1 + NR, wrap(sk + NR - 1), x0, y0);
         if (sub > 0 && k + 1 < k1) load_df(k + 1, k0, x0, y0);
       }
-      front(k + NG, pbase);
+      front(k + NG, s3);
       tm_wait_st();
 
-      const float* Pk = raw + ((k - pbase) % NR) * PLANE + cen;
+      const float* Pk = raw + sk * PLANE + cen;
       // ---- z derivatives from the TMEM rings --------------------------------
       f2 vz[NF], d1z[NF], d2z[NF], mz[6];
 #pragma unroll
@@ -328,7 +331,7 @@ __global__ void __launch_bounds__(NT, 2) rk_pair_kernel(const __grid_constant__ 
         *reinterpret_cast<f2*>(sc + 2 * SCF) = dyUy;
         *reinterpret_cast<f2*>(sc + 3 * SCF) = dyUx;
         f2 h;
-        ds_pair(raw + ((k - pbase) % NR) * PLANE + hfield * FP + (hr + 3) * BX + hx, BX, a.cy, h, nullptr);
+        ds_pair(raw + sk * PLANE + hfield * FP + (hr + 3) * BX + hx, BX, a.cy, h, nullptr);
         *reinterpret_cast<f2*>(scr + hq * SCF + hr * BX + hx) = h;
       }
       __syncthreads();
@@ -495,18 +498,26 @@ __global__ void __launch_bounds__(NT, 2) rk_pair_kernel(const __grid_constant__ 
         const int ox = i < NG ? L.nx : (i + 1 >= L.nx - NG ? -L.nx : 0);
         const long long oy = j < NG ? (long long)L.ny * L.mx : (j >= L.ny - NG ? -(long long)L.ny * L.mx : 0);
         const f2 vv[NF] = {A0, A1, A2, u0, u1, u2, vz[LR], vz[LT]};
+        f2 vn[NF];
+        {
+          float* dq = a.df + cq;
+          float* fq = a.fout + cq;
 #pragma unroll
-        for (int f = 0; f < NF; ++f) {
-          const long long q = cq + (long long)f * L.fs;
-          const f2 dfn = fma2(F2(alpha), dfo[f], mul(F2(dt), out[f]));
-          if (sub < 2) *reinterpret_cast<f2*>(a.df + q) = dfn;
-          if (!eval) {
-            const f2 vn = fma2(F2(beta), dfn, vv[f]);
-            f2* o = reinterpret_cast<f2*>(a.fout + q);
-            o[0] = vn;
-            if (ox) *reinterpret_cast<f2*>(a.fout + q + ox) = vn;
-            if (oy) *reinterpret_cast<f2*>(a.fout + q + oy) = vn;
-            if (ox && oy) *reinterpret_cast<f2*>(a.fout + q + ox + oy) = vn;
+          for (int f = 0; f < NF; ++f) {
+            const f2 dfn = fma2(F2(alpha), dfo[f], mul(F2(dt), out[f]));
+            if (sub < 2) *reinterpret_cast<f2*>(dq + f * L.fs) = dfn;
+            vn[f] = fma2(F2(beta), dfn, vv[f]);
+            if (!eval) *reinterpret_cast<f2*>(fq + f * L.fs) = vn[f];
+          }
+          if (!eval && (ox | (int)(oy != 0))) {
+            // periodic images (pairs at the x, y edges only)
+#pragma unroll
+            for (int f = 0; f < NF; ++f) {
+              float* o = fq + f * L.fs;
+              if (ox) *reinterpret_cast<f2*>(o + ox) = vn[f];
+              if (oy) *reinterpret_cast<f2*>(o + oy) = vn[f];
+              if (ox && oy) *reinterpret_cast<f2*>(o + ox + oy) = vn[f];
+            }
           }
         }
         if (ph.bcz == 0 && k == 0) {
