@@ -157,7 +157,7 @@ def rk_traffic_bytes():
         sha = hashlib.sha256(blob).hexdigest()[:16]
         if kv.get("kernel_source_sha") != sha:
             return None
-        return float(kv["bytes_per_launch_scaled"])
+        return float(kv["bytes_per_launch_avg"])
     except Exception:
         return None
 
