@@ -1,0 +1,318 @@
+// mhd_adj_gather_zm.cu -- the transposed-stencil gather of the adjoint right-
+// hand side as a z-march.
+//
+// Given the 40 coefficient fields h of a substep (the adjoints of the cell
+// values and of every derivative the right-hand side read, [q][nz][ny][nx]),
+// the adjoint of the ghost-filled input is, per output field,
+//   sum over first-derivative coefficients   D1_a^T h = -D1_a h,
+//   + Laplacian coefficients                  (D2x + D2y + D2z) h,
+//   + gradient-of-divergence coefficients     D2_a h (own axis) and
+//                                             D1_a D1_c h (c != a, symmetric),
+//   + value coefficients (u, ln rho, ln T),
+// periodic in x and y, zero outside the interior layers, evaluated on the
+// interior and the three z ghost layers on each side.
+//
+// A CTA (256 threads, one cell each) owns a 32 x 8 tile and one output group
+// -- {A_x, A_y, A_z, ln rho} or {u_x, u_y, u_z, ln T}, 20 coefficient fields
+// each -- and marches over the coefficient planes p of a z chunk.  Plane p of
+// the group's 20 fields (with a 3-cell x, y halo, wrapped periodically) is
+// staged in shared memory by cp.async, double-buffered.  Its in-plane terms go
+// to the output at plane p; the z terms are scattered from the cell's column:
+// h(p) contributes to outputs p - 3 .. p + 3, held in a 7-plane accumulator
+// ring per output field in registers.  When plane p is done, output plane
+// p - 3 is complete and is written.  The in-plane mixed terms D1x D1y use the
+// commuted form D1x(D1y h) through a scratch row with an x halo.
+//
+// Output (as in the 3D-tiled gather): on layers klo <= k < khi the substep's
+// update F += G, D = alpha D + beta F; elsewhere G into gbar, with the value
+// adjoints of the photospheric nudging (A_x, A_y at k = 0, Eq. 4) and of the
+// stateful u_x, u_y ghost rows (Eq. 5).
+#include "mhd_adjoint_point.cuh"
+#include "mhd_internal.h"
+#include "mhd_zmarch.cuh"
+
+namespace mhd {
+namespace gzm {
+
+constexpr int TX = 32, TY = 8, NT = TX * TY;
+constexpr int XO = 4;                 // staged rows start 4 columns left of the tile
+constexpr int SX = TX + 8, SY = TY + 6;
+constexpr int SP = SX * SY;           // elements of one staged field plane
+constexpr int NQ = 20;                // coefficient fields of an output group
+constexpr int NO = 4;                 // output fields of a group
+
+template <typename R> __host__ __device__ constexpr int epc() { return 16 / (int)sizeof(R); }
+template <typename R> __host__ __device__ constexpr int chunks_row() { return SX / epc<R>(); }
+template <typename R> __host__ __device__ constexpr int chunks_plane() { return chunks_row<R>() * SY; }
+template <typename R> constexpr size_t smem_bytes() {
+  return (size_t)2 * NQ * SP * sizeof(R) + (size_t)2 * TY * SX * sizeof(R);
+}
+static_assert(chunks_plane<float>() <= 2 * TX * TY && chunks_plane<double>() <= 2 * TX * TY, "two chunks per thread");
+
+// staged order of the coefficient fields: 0..8 first derivatives (component
+// c, axis a at 3c + a), 9..11 Laplacians, 12..14 gradient-of-divergence (A)
+// or values (u), 15 value, 16..18 gradient, 19 Laplacian of the scalar
+__constant__ int kQ[2][NQ] = {
+    {CDA + 0, CDA + 1, CDA + 2, CDA + 3, CDA + 4, CDA + 5, CDA + 6, CDA + 7, CDA + 8, CLA + 0, CLA + 1, CLA + 2,
+     CGA + 0, CGA + 1, CGA + 2, CV + LR, CGL + 0, CGL + 1, CGL + 2, CLL},
+    {CDU + 0, CDU + 1, CDU + 2, CDU + 3, CDU + 4, CDU + 5, CDU + 6, CDU + 7, CDU + 8, CLU + 0, CLU + 1, CLU + 2,
+     CV + UX, CV + UY, CV + UZ, CV + LT, CGT + 0, CGT + 1, CGT + 2, CLT}};
+
+template <typename R>
+struct ZArgs {
+  Layout L;
+  Phys<R> ph;
+  const R* coef;
+  R* dbar;
+  R* gbar;
+  R* fbar;
+  R alpha, beta;
+  int klo, khi;
+  const StepState* ss;
+  int ntx, nty, nch, kchunk;
+};
+
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"((unsigned)__cvta_generic_to_shared(dst)), "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N> __device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// stencils on a staged plane at offset c (stride s), unscaled
+template <typename R> __device__ __forceinline__ R sd1(const R* p, int c, int s) {
+  return W<R>::c1 * (p[c + s] - p[c - s]) + W<R>::c2 * (p[c + 2 * s] - p[c - 2 * s]) +
+         W<R>::c3 * (p[c + 3 * s] - p[c - 3 * s]);
+}
+template <typename R> __device__ __forceinline__ R sd2(const R* p, int c, int s) {
+  return W<R>::e0 * p[c] + W<R>::e1 * (p[c + s] + p[c - s]) + W<R>::e2 * (p[c + 2 * s] + p[c - 2 * s]) +
+         W<R>::e3 * (p[c + 3 * s] + p[c - 3 * s]);
+}
+
+// z scatters into a 7-plane ring (index 3 = the current plane)
+// D1z^T h:  +c_m h into p + m, -c_m h into p - m
+template <typename R> __device__ __forceinline__ void z_d1t(R (&a)[7], R v) {
+  a[4] += W<R>::c1 * v; a[2] -= W<R>::c1 * v;
+  a[5] += W<R>::c2 * v; a[1] -= W<R>::c2 * v;
+  a[6] += W<R>::c3 * v; a[0] -= W<R>::c3 * v;
+}
+// D1z f:  +c_m f into p - m, -c_m f into p + m
+template <typename R> __device__ __forceinline__ void z_d1(R (&a)[7], R v) { z_d1t<R>(a, -v); }
+// D2z h (symmetric)
+template <typename R> __device__ __forceinline__ void z_d2(R (&a)[7], R v) {
+  a[3] += W<R>::e0 * v;
+  a[4] += W<R>::e1 * v; a[2] += W<R>::e1 * v;
+  a[5] += W<R>::e2 * v; a[1] += W<R>::e2 * v;
+  a[6] += W<R>::e3 * v; a[0] += W<R>::e3 * v;
+}
+
+template <typename R>
+__global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 2 : 1) gather_zm_kernel(ZArgs<R> a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  R* buf = reinterpret_cast<R*>(smem_raw);           // [2][NQ][SP]
+  R* scr = buf + 2 * NQ * SP;                         // [2][TY][SX]
+  const Layout& L = a.L;
+  if (halted(a.ss)) return;
+  const int tid = threadIdx.x, tx = tid & (TX - 1), ty = tid / TX;
+  const int nx = L.nx, ny = L.ny, nz = L.nz;
+  const long long n2 = (long long)nx * ny, n3 = n2 * nz;
+  const Phys<R>& ph = a.ph;
+  const R idx = ph.idx, idy = ph.idy, idz = ph.idz, idx2 = ph.idx2, idy2 = ph.idy2, idz2 = ph.idz2;
+  const R dt = R(a.ss->dt);
+  const int cen = (ty + 3) * SX + tx + XO;
+  // x-halo items of the in-plane mixed scratch: 2 fields x 8 rows x 6 columns
+  const int hf = tid / 48, hr = (tid % 48) / 6, hcol = (tid % 6) < 3 ? 1 + tid % 6 : 33 + tid % 6;
+  const int nzo = nz + 2 * NG;  // output planes -3 .. nz + 2
+  const int nitems = a.ntx * a.nty * a.nch * 2;
+
+  for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
+    const int grp = item & 1;
+    const int rest = item >> 1;
+    const int ch = rest % a.nch, tile = rest / a.nch;
+    const int x0 = (tile % a.ntx) * TX, y0 = (tile / a.ntx) * TY;
+    const int n0 = ch * a.kchunk - NG, n1 = min(nzo, (ch + 1) * a.kchunk) - NG;  // output planes [n0, n1)
+    const int pa = max(0, n0 - NG), pb = min(nz - 1, n1 + NG - 1);              // valid input planes
+    __syncthreads();  // the previous item's readers are done with the buffers
+    // thread tid copies chunks tid and tid + NT (if they exist) of every
+    // field plane: their source offsets within a plane (periodic wrap in x, y)
+    long long myoff[2] = {0, 0};
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int c = tid + h * NT;
+      if (c < chunks_plane<R>()) {
+        const int r = c / chunks_row<R>(), cc = c - r * chunks_row<R>();
+        const int jj = ((y0 - 3 + r) % ny + ny) % ny;
+        const int ii = ((x0 - XO + cc * epc<R>()) % nx + nx) % nx;
+        myoff[h] = (long long)jj * nx + ii;
+      }
+    }
+    auto stage = [&](int p, int b) {
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int c = tid + h * NT;
+        if (c < chunks_plane<R>()) {
+          R* dst = buf + b * NQ * SP + c * epc<R>();
+          const R* src = a.coef + (long long)p * n2 + myoff[h];
+#pragma unroll 4
+          for (int q = 0; q < NQ; ++q) cp_async16(dst + q * SP, src + (long long)kQ[grp][q] * n3);
+        }
+      }
+      cp_commit();
+    };
+    if (pa <= pb) stage(pa, 0);
+    int b = 0;
+    R acc[NO][7];
+#pragma unroll
+    for (int t = 0; t < NO; ++t)
+#pragma unroll
+      for (int d = 0; d < 7; ++d) acc[t][d] = R(0);
+    const int i = x0 + tx, j = y0 + ty;
+    const bool live = i < nx && j < ny;
+
+    for (int p = n0 - NG; p <= n1 + NG - 1; ++p) {
+      // output plane p - 3 is written at the end of this plane: its
+      // accumulator and D values are fetched now, ahead of the compute
+      const int n = p - NG;
+      const bool emit = n >= n0 && live;
+      const bool fz = n >= a.klo && n < a.khi;
+      R fo[NO], dd[NO];
+#pragma unroll
+      for (int t = 0; t < NO; ++t) {
+        const int f = grp == 0 ? (t < 3 ? AX + t : LR) : (t < 3 ? UX + t : LT);
+        const long long q = emit ? L.at(f, n, j, i) : 0;
+        fo[t] = (emit && fz) ? a.fbar[q] : R(0);
+        dd[t] = (emit && (fz || (ph.bcz == 0 && n <= 0))) ? a.dbar[q] : R(0);
+      }
+      if (p >= pa && p <= pb) {
+        if (p + 1 <= pb) {
+          stage(p + 1, b ^ 1);
+          cp_wait<1>();
+        } else {
+          cp_wait<0>();
+        }
+        __syncthreads();
+        const R* s = buf + b * NQ * SP;
+        auto S = [&](int q) { return s + q * SP; };
+        // first derivatives of the three components: -D1x, -D1y, D1z^T
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          acc[c][3] -= idx * sd1<R>(S(3 * c), cen, 1) + idy * sd1<R>(S(3 * c + 1), cen, SX);
+          z_d1t<R>(acc[c], idz * S(3 * c + 2)[cen]);
+        }
+        // Laplacians (u: with the own-axis part of grad div u = lap u / 3)
+        const R f43 = R(4.0 / 3.0), g = grp == 0 ? R(1) : R(1.0 / 3.0);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const R* h = S(9 + c);
+          const R wx = (grp == 1 && c == 0) ? f43 : R(1), wy = (grp == 1 && c == 1) ? f43 : R(1);
+          const R wz = (grp == 1 && c == 2) ? f43 : R(1);
+          acc[c][3] += wx * idx2 * sd2<R>(h, cen, 1) + wy * idy2 * sd2<R>(h, cen, SX);
+          z_d2<R>(acc[c], wz * idz2 * h[cen]);
+        }
+        // gradient of divergence: gd_a coefficients (A: fields 12..14; u:
+        // the Laplacian ones / 3)
+        const R* gx = grp == 0 ? S(12) : S(9);
+        const R* gy = grp == 0 ? S(13) : S(10);
+        const R* gz = grp == 0 ? S(14) : S(11);
+        if (grp == 0) {
+          // own-axis parts (for u they are in the weighted Laplacians)
+          acc[0][3] += idx2 * sd2<R>(gx, cen, 1);
+          acc[1][3] += idy2 * sd2<R>(gy, cen, SX);
+          z_d2<R>(acc[2], idz2 * gz[cen]);
+        } else {
+          // values of u
+#pragma unroll
+          for (int c = 0; c < 3; ++c) acc[c][3] += S(12 + c)[cen];
+        }
+        // xz, yz, zx, zy mixed: D1z of in-plane first derivatives
+        z_d1<R>(acc[2], g * idz * (idx * sd1<R>(gx, cen, 1) + idy * sd1<R>(gy, cen, SX)));
+        z_d1<R>(acc[0], g * idz * idx * sd1<R>(gz, cen, 1));
+        z_d1<R>(acc[1], g * idz * idy * sd1<R>(gz, cen, SX));
+        // xy mixed: D1x(D1y gd_x) -> component y, D1x(D1y gd_y) -> component x
+        scr[ty * SX + tx + XO] = sd1<R>(gx, cen, SX);
+        scr[TY * SX + ty * SX + tx + XO] = sd1<R>(gy, cen, SX);
+        if (tid < 96) scr[hf * TY * SX + hr * SX + hcol] = sd1<R>(hf == 0 ? gx : gy, (hr + 3) * SX + hcol, SX);
+        // the scalar: value, -D1x, -D1y, D1z^T, Laplacian
+        acc[3][3] += S(15)[cen] - idx * sd1<R>(S(16), cen, 1) - idy * sd1<R>(S(17), cen, SX) +
+                     idx2 * sd2<R>(S(19), cen, 1) + idy2 * sd2<R>(S(19), cen, SX);
+        z_d1t<R>(acc[3], idz * S(18)[cen]);
+        z_d2<R>(acc[3], idz2 * S(19)[cen]);
+        __syncthreads();
+        {
+          const int o = ty * SX + tx + XO;
+          acc[1][3] += g * idx * idy * sd1<R>(scr, o, 1);
+          acc[0][3] += g * idx * idy * sd1<R>(scr + TY * SX, o, 1);
+        }
+        b ^= 1;
+      }
+      // output plane p - 3 is complete
+      if (emit) {
+#pragma unroll
+        for (int t = 0; t < NO; ++t) {
+          const int f = grp == 0 ? (t < 3 ? AX + t : LR) : (t < 3 ? UX + t : LT);
+          const long long q = L.at(f, n, j, i);
+          const R v = acc[t][0];
+          if (fz) {
+            const R fv = fo[t] + v;
+            a.fbar[q] = fv;
+            a.dbar[q] = a.alpha * dd[t] + a.beta * fv;
+          } else {
+            R gv = v;
+            if (ph.bcz == 0 && ((n == 0 && (f == AX || f == AY)) || (n < 0 && (f == UX || f == UY))))
+              gv -= (f == AX || f == AY ? ph.tau_A : ph.tau_u) * dt * dd[t];
+            a.gbar[q] = gv;
+          }
+        }
+      }
+#pragma unroll
+      for (int t = 0; t < NO; ++t) {
+#pragma unroll
+        for (int d = 0; d < 6; ++d) acc[t][d] = acc[t][d + 1];
+        acc[t][6] = R(0);
+      }
+    }
+  }
+}
+
+}  // namespace gzm
+
+template <typename R>
+void launch_adj_gather_zm(const Layout& L, const Phys<R>& ph, const R* coef, R* dbar, R* gbar, R* fbar,
+                          double alpha, double beta, int klo, int khi, const StepState* ss, cudaStream_t st) {
+  static int ctas = 0;
+  constexpr size_t smem = gzm::smem_bytes<R>();
+  if (!ctas) {
+    cudaFuncSetAttribute(gzm::gather_zm_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, gzm::gather_zm_kernel<R>, gzm::NT, smem);
+    ctas = sms * (per > 0 ? per : 1);
+  }
+  gzm::ZArgs<R> a;
+  a.L = L;
+  a.ph = ph;
+  a.coef = coef;
+  a.dbar = dbar;
+  a.gbar = gbar;
+  a.fbar = fbar;
+  a.alpha = (R)alpha;
+  a.beta = (R)beta;
+  a.klo = klo;
+  a.khi = khi;
+  a.ss = ss;
+  a.ntx = (L.nx + gzm::TX - 1) / gzm::TX;
+  a.nty = (L.ny + gzm::TY - 1) / gzm::TY;
+  const int tiles = a.ntx * a.nty;
+  a.kchunk = zm::zchunk(L.nz + 2 * NG, 2 * tiles, ctas);
+  a.nch = (L.nz + 2 * NG + a.kchunk - 1) / a.kchunk;
+  const int nitems = 2 * tiles * a.nch;
+  gzm::gather_zm_kernel<R><<<nitems < ctas ? nitems : ctas, gzm::NT, smem, st>>>(a);
+}
+
+template void launch_adj_gather_zm<float>(const Layout&, const Phys<float>&, const float*, float*, float*, float*,
+                                          double, double, int, int, const StepState*, cudaStream_t);
+template void launch_adj_gather_zm<double>(const Layout&, const Phys<double>&, const double*, double*, double*,
+                                           double*, double, double, int, int, const StepState*, cudaStream_t);
+
+}  // namespace mhd

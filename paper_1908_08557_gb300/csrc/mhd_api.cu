@@ -27,6 +27,7 @@ struct mhd_ctx {
   void* sw;            // split: [3][nz - ksw][ny][nx] swamp terms
   int ksw;             // first layer with a nonzero swamp weight or slope (nz if none)
   bool adj_tiled;      // adjoint: tiled gather and (FP32) z-march point kernel, else one thread per point
+  bool adj_zm;         // adjoint gather as a z-march (else 3D tiles after a grad-div fold)
   mhd_params p;
   Layout L;
   cudaStream_t st;
@@ -566,6 +567,7 @@ extern "C" int mhd_create(const mhd_params* p, void* workspace, size_t ws_bytes,
               rk_pair_supported(h->L);
     const char* va = getenv("MHD_ADJ_VARIANT");
     h->adj_tiled = !(va && strcmp(va, "simple") == 0);
+    h->adj_zm = h->adj_tiled && !(va && strcmp(va, "tiled3d") == 0);
   }
   h->t0 = 0.0;
   h->t1 = 0.0;
@@ -976,7 +978,10 @@ static void adjoint_step_impl(mhd_ctx* h) {
     else
       launch_adj_point<R>(h->L, ph, bg, S[s], (const R*)h->dbar, (R*)h->coef, h->thbar, (const R*)h->wtab,
                           (const R*)h->wptab, h->ss, s, h->st);
-    if (tg)
+    if (tg && h->adj_zm)
+      launch_adj_gather_zm<R>(h->L, ph, (const R*)h->coef, (R*)h->dbar, (R*)h->gbar, (R*)h->fbar, alpha, beta, klo,
+                              khi, h->ss, h->st);
+    else if (tg)
       launch_adj_gather_tiled<R>(h->L, ph, (R*)h->coef, (R*)h->dbar, (R*)h->gbar, (R*)h->fbar, alpha, beta, klo, khi,
                                  h->ss, h->st);
     else
@@ -984,7 +989,7 @@ static void adjoint_step_impl(mhd_ctx* h) {
     launch_adj_bc<R>(h->L, ph, bg, S[s], (R*)h->gbar, (R)h->p.dz, h->ss, h->st);
     launch_pfe_adjoint<R>(fpa, h->L, (R*)h->gbar, h->ss, h->st);
     launch_adj_update<R>(h->L, (R*)h->fbar, (R*)h->dbar, (const R*)h->gbar, alpha, beta, 1, klo, khi, h->ss, h->st);
-    h->nlaunch += tg ? 8 : 7;  // point, [fold], gather, bc, 3 FFT, update
+    h->nlaunch += (tg && !h->adj_zm) ? 8 : 7;  // point, [fold], gather, bc, 3 FFT, update
   }
 }
 

@@ -210,15 +210,20 @@ def _adjoint_with_variant(case, prec, variant, lam):
     return out
 
 
-@pytest.mark.parametrize("shape,prec", [((16, 8, 13), 64), ((64, 32, 21), 64), ((64, 32, 21), 32)])
-def test_tiled_gather_matches_simple(shape, prec):
-    """The shared-memory tiled transposed-stencil gather against the one
-    thread per point gather: tiles ragged in x (16 < 32) and z (13 + 6 and
-    21 + 6 output layers are not multiples of 8), several tiles in x and y."""
+@pytest.mark.parametrize("variant", ["tiled", "tiled3d"])
+@pytest.mark.parametrize("shape,prec", [((16, 8, 13), 64), ((64, 32, 21), 64), ((64, 32, 21), 32),
+                                        ((32, 16, 37), 32)])
+def test_tiled_gather_matches_simple(shape, prec, variant):
+    """The shared-memory transposed-stencil gathers ("tiled", the default: a
+    z-march over coefficient planes with a z-scatter register ring;
+    "tiled3d": 3D tiles after a grad-div fold) against the one thread per
+    point gather: tiles ragged in x (16 < 32), several y tiles, z chunks
+    ragged (13 + 6, 21 + 6, 37 + 6 output layers), several tiles in x and
+    y."""
     nx, ny, nz = shape
     case = _case(nx, ny, nz, seed=12)
     lam = np.random.default_rng(13).standard_normal((8, nz, ny, nx))
-    a = _adjoint_with_variant(case, prec, "tiled", lam)
+    a = _adjoint_with_variant(case, prec, variant, lam)
     b = _adjoint_with_variant(case, prec, "simple", lam)
     tol = 1e-12 if prec == 64 else 1e-5
     for name in ("lam", "bz", "v0", "v1"):
