@@ -16,7 +16,9 @@
 // -- {A_x, A_y, A_z, ln rho} or {u_x, u_y, u_z, ln T}, 20 coefficient fields
 // each -- and marches over the coefficient planes p of a z chunk.  Plane p of
 // the group's 20 fields (with a 3-cell x, y halo, wrapped periodically) is
-// staged in shared memory by cp.async, double-buffered.  Its in-plane terms go
+// staged in shared memory by cp.async in 16-byte chunks (one chunk position
+// per thread, all 20 fields), double-buffered.  Items run tile-fastest, so
+// CTAs working at the same time share z chunks and their halo planes in L2.  Its in-plane terms go
 // to the output at plane p; the z terms are scattered from the cell's column:
 // h(p) contributes to outputs p - 3 .. p + 3, held in a 7-plane accumulator
 // ring per output field in registers.  When plane p is done, output plane
@@ -41,13 +43,9 @@ constexpr int SP = SX * SY;           // elements of one staged field plane
 constexpr int NQ = 20;                // coefficient fields of an output group
 constexpr int NO = 4;                 // output fields of a group
 
-template <typename R> __host__ __device__ constexpr int epc() { return 16 / (int)sizeof(R); }
-template <typename R> __host__ __device__ constexpr int chunks_row() { return SX / epc<R>(); }
-template <typename R> __host__ __device__ constexpr int chunks_plane() { return chunks_row<R>() * SY; }
 template <typename R> constexpr size_t smem_bytes() {
-  return (size_t)2 * NQ * SP * sizeof(R) + (size_t)2 * TY * SX * sizeof(R);
+  return (size_t)2 * NQ * SP * sizeof(R) + (size_t)4 * TY * SX * sizeof(R);
 }
-static_assert(chunks_plane<float>() <= 2 * TX * TY && chunks_plane<double>() <= 2 * TX * TY, "two chunks per thread");
 
 // staged order of the coefficient fields: 0..8 first derivatives (component
 // c, axis a at 3c + a), 9..11 Laplacians, 12..14 gradient-of-divergence (A)
@@ -68,16 +66,9 @@ struct ZArgs {
   R* fbar;
   R alpha, beta;
   int klo, khi;
-  const StepState* ss;
+  StepState* ss;
   int ntx, nty, nch, kchunk;
 };
-
-__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"((unsigned)__cvta_generic_to_shared(dst)), "l"(src)
-               : "memory");
-}
-__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N> __device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
 // stencils on a staged plane at offset c (stride s), unscaled
 template <typename R> __device__ __forceinline__ R sd1(const R* p, int c, int s) {
@@ -107,12 +98,15 @@ template <typename R> __device__ __forceinline__ void z_d2(R (&a)[7], R v) {
 }
 
 template <typename R>
-__global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 2 : 1) gather_zm_kernel(ZArgs<R> a) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  R* buf = reinterpret_cast<R*>(smem_raw);           // [2][NQ][SP]
-  R* scr = buf + 2 * NQ * SP;                         // [2][TY][SX]
+struct Smem {
+  R* buf;          // [2][NQ][SP]
+  R* scr;          // [2 buffers][2 fields][TY][SX]
+};
+
+// One item: output group GRP of a tile over output planes [n0, n1).
+template <typename R, int GRP>
+__device__ __forceinline__ void item_body(const ZArgs<R>& a, const Smem<R>& sm, int x0, int y0, int n0, int n1) {
   const Layout& L = a.L;
-  if (halted(a.ss)) return;
   const int tid = threadIdx.x, tx = tid & (TX - 1), ty = tid / TX;
   const int nx = L.nx, ny = L.ny, nz = L.nz;
   const long long n2 = (long long)nx * ny, n3 = n2 * nz;
@@ -120,157 +114,176 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 2 : 1) gather_zm_kernel(Z
   const R idx = ph.idx, idy = ph.idy, idz = ph.idz, idx2 = ph.idx2, idy2 = ph.idy2, idz2 = ph.idz2;
   const R dt = R(a.ss->dt);
   const int cen = (ty + 3) * SX + tx + XO;
+  const int pa = max(0, n0 - NG), pb = min(nz - 1, n1 + NG - 1);  // valid input planes
+  // cp.async staging: thread tid copies 16-byte chunk position tid (and
+  // tid + NT, if it exists) of the 20 field planes; source offsets within a
+  // plane wrap periodically in x and y
+  constexpr int EPC = 16 / (int)sizeof(R), CR = SX / EPC, CP = CR * SY;
+  auto chunk_off = [&](int c) -> long long {
+    if (c >= CP) return 0;
+    const int r = c / CR, cc = c - r * CR;
+    const int yy = ((y0 - 3 + r) % ny + ny) % ny, xx = ((x0 - XO + cc * EPC) % nx + nx) % nx;
+    return (long long)yy * nx + xx;
+  };
+  const long long off0 = chunk_off(tid), off1 = chunk_off(tid + NT);
+  auto cp16 = [](R* dst, const R* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(zm::sa(dst)), "l"(src) : "memory");
+  };
+  auto stage = [&](int p, int b) {
+    R* dst = sm.buf + b * NQ * SP;
+    const R* src = a.coef + (long long)p * n2;
+    if (tid < CP) {
+#pragma unroll 4
+      for (int q = 0; q < NQ; ++q) cp16(dst + q * SP + tid * EPC, src + (long long)kQ[GRP][q] * n3 + off0);
+    }
+    if (tid + NT < CP) {
+#pragma unroll 4
+      for (int q = 0; q < NQ; ++q) cp16(dst + q * SP + (tid + NT) * EPC, src + (long long)kQ[GRP][q] * n3 + off1);
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
+  if (pa <= pb) stage(pa, 0);
+  int b = 0;
+  R acc[NO][7];
+#pragma unroll
+  for (int t = 0; t < NO; ++t)
+#pragma unroll
+    for (int d = 0; d < 7; ++d) acc[t][d] = R(0);
+  const int i = x0 + tx, j = y0 + ty;
+  const bool live = i < nx && j < ny;
   // x-halo items of the in-plane mixed scratch: 2 fields x 8 rows x 6 columns
   const int hf = tid / 48, hr = (tid % 48) / 6, hcol = (tid % 6) < 3 ? 1 + tid % 6 : 33 + tid % 6;
-  const int nzo = nz + 2 * NG;  // output planes -3 .. nz + 2
-  const int nitems = a.ntx * a.nty * a.nch * 2;
+  constexpr R g = GRP == 0 ? R(1) : R(1.0 / 3.0);
 
+  for (int p = n0 - NG; p <= n1 + NG - 1; ++p) {
+    // output plane p - 3 is written at the end of this plane: its
+    // accumulator and D values are fetched now, ahead of the compute
+    const int n = p - NG;
+    const bool emit = n >= n0 && live;
+    const bool fz = n >= a.klo && n < a.khi;
+    R fo[NO], dd[NO];
+#pragma unroll
+    for (int t = 0; t < NO; ++t) {
+      const int f = GRP == 0 ? (t < 3 ? AX + t : LR) : (t < 3 ? UX + t : LT);
+      const long long q = emit ? L.at(f, n, j, i) : 0;
+      fo[t] = (emit && fz) ? a.fbar[q] : R(0);
+      dd[t] = (emit && (fz || (ph.bcz == 0 && n <= 0))) ? a.dbar[q] : R(0);
+    }
+    if (p >= pa && p <= pb) {
+      if (p + 1 <= pb) {
+        stage(p + 1, b ^ 1);
+        asm volatile("cp.async.wait_group 1;" ::: "memory");
+      } else {
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
+      }
+      __syncthreads();
+      const R* s = sm.buf + b * NQ * SP;
+      auto S = [&](int q) { return s + q * SP; };
+      // first derivatives of the three components: -D1x, -D1y, D1z^T
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        acc[c][3] -= idx * sd1<R>(S(3 * c), cen, 1) + idy * sd1<R>(S(3 * c + 1), cen, SX);
+        z_d1t<R>(acc[c], idz * S(3 * c + 2)[cen]);
+      }
+      // Laplacians (u: with the own-axis part of grad div u = lap u / 3)
+      const R f43 = R(4.0 / 3.0);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const R* h = S(9 + c);
+        const R wx = (GRP == 1 && c == 0) ? f43 : R(1), wy = (GRP == 1 && c == 1) ? f43 : R(1);
+        const R wz = (GRP == 1 && c == 2) ? f43 : R(1);
+        acc[c][3] += wx * idx2 * sd2<R>(h, cen, 1) + wy * idy2 * sd2<R>(h, cen, SX);
+        z_d2<R>(acc[c], wz * idz2 * h[cen]);
+      }
+      // gradient of divergence: gd_a coefficients (A: fields 12..14; u:
+      // the Laplacian ones / 3)
+      const R* gx = GRP == 0 ? S(12) : S(9);
+      const R* gy = GRP == 0 ? S(13) : S(10);
+      const R* gz = GRP == 0 ? S(14) : S(11);
+      if (GRP == 0) {
+        // own-axis parts (for u they are in the weighted Laplacians)
+        acc[0][3] += idx2 * sd2<R>(gx, cen, 1);
+        acc[1][3] += idy2 * sd2<R>(gy, cen, SX);
+        z_d2<R>(acc[2], idz2 * gz[cen]);
+      } else {
+        // values of u
+#pragma unroll
+        for (int c = 0; c < 3; ++c) acc[c][3] += S(12 + c)[cen];
+      }
+      // xz, yz, zx, zy mixed: D1z of in-plane first derivatives
+      z_d1<R>(acc[2], g * idz * (idx * sd1<R>(gx, cen, 1) + idy * sd1<R>(gy, cen, SX)));
+      z_d1<R>(acc[0], g * idz * idx * sd1<R>(gz, cen, 1));
+      z_d1<R>(acc[1], g * idz * idy * sd1<R>(gz, cen, SX));
+      // xy mixed: D1x(D1y gd_x) -> component y, D1x(D1y gd_y) -> component x
+      // (scratch double-buffered like the staged planes: a thread writes
+      // buffer b only after every thread has passed the previous barrier)
+      R* scr = sm.scr + b * 2 * TY * SX;
+      scr[ty * SX + tx + XO] = sd1<R>(gx, cen, SX);
+      scr[TY * SX + ty * SX + tx + XO] = sd1<R>(gy, cen, SX);
+      if (tid < 96) scr[hf * TY * SX + hr * SX + hcol] = sd1<R>(hf == 0 ? gx : gy, (hr + 3) * SX + hcol, SX);
+      // the scalar: value, -D1x, -D1y, D1z^T, Laplacian
+      acc[3][3] += S(15)[cen] - idx * sd1<R>(S(16), cen, 1) - idy * sd1<R>(S(17), cen, SX) +
+                   idx2 * sd2<R>(S(19), cen, 1) + idy2 * sd2<R>(S(19), cen, SX);
+      z_d1t<R>(acc[3], idz * S(18)[cen]);
+      z_d2<R>(acc[3], idz2 * S(19)[cen]);
+      // every thread is done with staged buffer b and scratch b is complete
+      __syncthreads();
+      {
+        const int o = ty * SX + tx + XO;
+        acc[1][3] += g * idx * idy * sd1<R>(scr, o, 1);
+        acc[0][3] += g * idx * idy * sd1<R>(scr + TY * SX, o, 1);
+      }
+      b ^= 1;
+    }
+    // output plane p - 3 is complete
+    if (emit) {
+#pragma unroll
+      for (int t = 0; t < NO; ++t) {
+        const int f = GRP == 0 ? (t < 3 ? AX + t : LR) : (t < 3 ? UX + t : LT);
+        const long long q = L.at(f, n, j, i);
+        const R v = acc[t][0];
+        if (fz) {
+          const R fv = fo[t] + v;
+          a.fbar[q] = fv;
+          a.dbar[q] = a.alpha * dd[t] + a.beta * fv;
+        } else {
+          R gv = v;
+          if (ph.bcz == 0 && ((n == 0 && (f == AX || f == AY)) || (n < 0 && (f == UX || f == UY))))
+            gv -= (f == AX || f == AY ? ph.tau_A : ph.tau_u) * dt * dd[t];
+          a.gbar[q] = gv;
+        }
+      }
+    }
+#pragma unroll
+    for (int t = 0; t < NO; ++t) {
+#pragma unroll
+      for (int d = 0; d < 6; ++d) acc[t][d] = acc[t][d + 1];
+      acc[t][6] = R(0);
+    }
+  }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 2 : 1) gather_zm_kernel(ZArgs<R> a) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  Smem<R> sm;
+  sm.buf = reinterpret_cast<R*>(smem_raw);
+  sm.scr = sm.buf + 2 * NQ * SP;
+  if (halted(a.ss)) return;
+  const int nzo = a.L.nz + 2 * NG;  // output planes -3 .. nz + 2
+  const int nitems = a.ntx * a.nty * a.nch * 2;
   for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
     const int grp = item & 1;
     const int rest = item >> 1;
-    const int ch = rest % a.nch, tile = rest / a.nch;
+    const int tiles = a.ntx * a.nty;
+    const int ch = rest / tiles, tile = rest % tiles;
     const int x0 = (tile % a.ntx) * TX, y0 = (tile / a.ntx) * TY;
     const int n0 = ch * a.kchunk - NG, n1 = min(nzo, (ch + 1) * a.kchunk) - NG;  // output planes [n0, n1)
-    const int pa = max(0, n0 - NG), pb = min(nz - 1, n1 + NG - 1);              // valid input planes
     __syncthreads();  // the previous item's readers are done with the buffers
-    // thread tid copies chunks tid and tid + NT (if they exist) of every
-    // field plane: their source offsets within a plane (periodic wrap in x, y)
-    long long myoff[2] = {0, 0};
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int c = tid + h * NT;
-      if (c < chunks_plane<R>()) {
-        const int r = c / chunks_row<R>(), cc = c - r * chunks_row<R>();
-        const int jj = ((y0 - 3 + r) % ny + ny) % ny;
-        const int ii = ((x0 - XO + cc * epc<R>()) % nx + nx) % nx;
-        myoff[h] = (long long)jj * nx + ii;
-      }
-    }
-    auto stage = [&](int p, int b) {
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int c = tid + h * NT;
-        if (c < chunks_plane<R>()) {
-          R* dst = buf + b * NQ * SP + c * epc<R>();
-          const R* src = a.coef + (long long)p * n2 + myoff[h];
-#pragma unroll 4
-          for (int q = 0; q < NQ; ++q) cp_async16(dst + q * SP, src + (long long)kQ[grp][q] * n3);
-        }
-      }
-      cp_commit();
-    };
-    if (pa <= pb) stage(pa, 0);
-    int b = 0;
-    R acc[NO][7];
-#pragma unroll
-    for (int t = 0; t < NO; ++t)
-#pragma unroll
-      for (int d = 0; d < 7; ++d) acc[t][d] = R(0);
-    const int i = x0 + tx, j = y0 + ty;
-    const bool live = i < nx && j < ny;
-
-    for (int p = n0 - NG; p <= n1 + NG - 1; ++p) {
-      // output plane p - 3 is written at the end of this plane: its
-      // accumulator and D values are fetched now, ahead of the compute
-      const int n = p - NG;
-      const bool emit = n >= n0 && live;
-      const bool fz = n >= a.klo && n < a.khi;
-      R fo[NO], dd[NO];
-#pragma unroll
-      for (int t = 0; t < NO; ++t) {
-        const int f = grp == 0 ? (t < 3 ? AX + t : LR) : (t < 3 ? UX + t : LT);
-        const long long q = emit ? L.at(f, n, j, i) : 0;
-        fo[t] = (emit && fz) ? a.fbar[q] : R(0);
-        dd[t] = (emit && (fz || (ph.bcz == 0 && n <= 0))) ? a.dbar[q] : R(0);
-      }
-      if (p >= pa && p <= pb) {
-        if (p + 1 <= pb) {
-          stage(p + 1, b ^ 1);
-          cp_wait<1>();
-        } else {
-          cp_wait<0>();
-        }
-        __syncthreads();
-        const R* s = buf + b * NQ * SP;
-        auto S = [&](int q) { return s + q * SP; };
-        // first derivatives of the three components: -D1x, -D1y, D1z^T
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          acc[c][3] -= idx * sd1<R>(S(3 * c), cen, 1) + idy * sd1<R>(S(3 * c + 1), cen, SX);
-          z_d1t<R>(acc[c], idz * S(3 * c + 2)[cen]);
-        }
-        // Laplacians (u: with the own-axis part of grad div u = lap u / 3)
-        const R f43 = R(4.0 / 3.0), g = grp == 0 ? R(1) : R(1.0 / 3.0);
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          const R* h = S(9 + c);
-          const R wx = (grp == 1 && c == 0) ? f43 : R(1), wy = (grp == 1 && c == 1) ? f43 : R(1);
-          const R wz = (grp == 1 && c == 2) ? f43 : R(1);
-          acc[c][3] += wx * idx2 * sd2<R>(h, cen, 1) + wy * idy2 * sd2<R>(h, cen, SX);
-          z_d2<R>(acc[c], wz * idz2 * h[cen]);
-        }
-        // gradient of divergence: gd_a coefficients (A: fields 12..14; u:
-        // the Laplacian ones / 3)
-        const R* gx = grp == 0 ? S(12) : S(9);
-        const R* gy = grp == 0 ? S(13) : S(10);
-        const R* gz = grp == 0 ? S(14) : S(11);
-        if (grp == 0) {
-          // own-axis parts (for u they are in the weighted Laplacians)
-          acc[0][3] += idx2 * sd2<R>(gx, cen, 1);
-          acc[1][3] += idy2 * sd2<R>(gy, cen, SX);
-          z_d2<R>(acc[2], idz2 * gz[cen]);
-        } else {
-          // values of u
-#pragma unroll
-          for (int c = 0; c < 3; ++c) acc[c][3] += S(12 + c)[cen];
-        }
-        // xz, yz, zx, zy mixed: D1z of in-plane first derivatives
-        z_d1<R>(acc[2], g * idz * (idx * sd1<R>(gx, cen, 1) + idy * sd1<R>(gy, cen, SX)));
-        z_d1<R>(acc[0], g * idz * idx * sd1<R>(gz, cen, 1));
-        z_d1<R>(acc[1], g * idz * idy * sd1<R>(gz, cen, SX));
-        // xy mixed: D1x(D1y gd_x) -> component y, D1x(D1y gd_y) -> component x
-        scr[ty * SX + tx + XO] = sd1<R>(gx, cen, SX);
-        scr[TY * SX + ty * SX + tx + XO] = sd1<R>(gy, cen, SX);
-        if (tid < 96) scr[hf * TY * SX + hr * SX + hcol] = sd1<R>(hf == 0 ? gx : gy, (hr + 3) * SX + hcol, SX);
-        // the scalar: value, -D1x, -D1y, D1z^T, Laplacian
-        acc[3][3] += S(15)[cen] - idx * sd1<R>(S(16), cen, 1) - idy * sd1<R>(S(17), cen, SX) +
-                     idx2 * sd2<R>(S(19), cen, 1) + idy2 * sd2<R>(S(19), cen, SX);
-        z_d1t<R>(acc[3], idz * S(18)[cen]);
-        z_d2<R>(acc[3], idz2 * S(19)[cen]);
-        __syncthreads();
-        {
-          const int o = ty * SX + tx + XO;
-          acc[1][3] += g * idx * idy * sd1<R>(scr, o, 1);
-          acc[0][3] += g * idx * idy * sd1<R>(scr + TY * SX, o, 1);
-        }
-        b ^= 1;
-      }
-      // output plane p - 3 is complete
-      if (emit) {
-#pragma unroll
-        for (int t = 0; t < NO; ++t) {
-          const int f = grp == 0 ? (t < 3 ? AX + t : LR) : (t < 3 ? UX + t : LT);
-          const long long q = L.at(f, n, j, i);
-          const R v = acc[t][0];
-          if (fz) {
-            const R fv = fo[t] + v;
-            a.fbar[q] = fv;
-            a.dbar[q] = a.alpha * dd[t] + a.beta * fv;
-          } else {
-            R gv = v;
-            if (ph.bcz == 0 && ((n == 0 && (f == AX || f == AY)) || (n < 0 && (f == UX || f == UY))))
-              gv -= (f == AX || f == AY ? ph.tau_A : ph.tau_u) * dt * dd[t];
-            a.gbar[q] = gv;
-          }
-        }
-      }
-#pragma unroll
-      for (int t = 0; t < NO; ++t) {
-#pragma unroll
-        for (int d = 0; d < 6; ++d) acc[t][d] = acc[t][d + 1];
-        acc[t][6] = R(0);
-      }
-    }
+    if (grp == 0)
+      item_body<R, 0>(a, sm, x0, y0, n0, n1);
+    else
+      item_body<R, 1>(a, sm, x0, y0, n0, n1);
   }
 }
 
@@ -278,7 +291,7 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 2 : 1) gather_zm_kernel(Z
 
 template <typename R>
 void launch_adj_gather_zm(const Layout& L, const Phys<R>& ph, const R* coef, R* dbar, R* gbar, R* fbar,
-                          double alpha, double beta, int klo, int khi, const StepState* ss, cudaStream_t st) {
+                          double alpha, double beta, int klo, int khi, StepState* ss, cudaStream_t st) {
   static int ctas = 0;
   constexpr size_t smem = gzm::smem_bytes<R>();
   if (!ctas) {
@@ -311,8 +324,8 @@ void launch_adj_gather_zm(const Layout& L, const Phys<R>& ph, const R* coef, R* 
 }
 
 template void launch_adj_gather_zm<float>(const Layout&, const Phys<float>&, const float*, float*, float*, float*,
-                                          double, double, int, int, const StepState*, cudaStream_t);
+                                          double, double, int, int, StepState*, cudaStream_t);
 template void launch_adj_gather_zm<double>(const Layout&, const Phys<double>&, const double*, double*, double*,
-                                           double*, double, double, int, int, const StepState*, cudaStream_t);
+                                           double*, double, double, int, int, StepState*, cudaStream_t);
 
 }  // namespace mhd

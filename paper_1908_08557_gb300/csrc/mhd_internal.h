@@ -95,8 +95,8 @@ template <typename R> void launch_adj_gather_tiled(const Layout& L, const Phys<R
 // CTA stages one output group's 20 coefficient fields plane by plane and
 // scatters the z stencils into a register ring (needs adj_gather_tiled_ok)
 template <typename R> void launch_adj_gather_zm(const Layout& L, const Phys<R>& ph, const R* coef, R* dbar, R* gbar,
-                                                R* fbar, double alpha, double beta, int klo, int khi,
-                                                const StepState* ss, cudaStream_t st);
+                                                R* fbar, double alpha, double beta, int klo, int khi, StepState* ss,
+                                                cudaStream_t st);
 template <typename R> void launch_adj_bc(const Layout& L, const Phys<R>& ph, const Background<R>& bg, const R* g,
                                          R* gbar, R dz, const StepState* ss, cudaStream_t st);
 // adjoint elementwise updates (mode 0: D = beta F; mode 1: F += G, D = alpha D + beta F),
