@@ -20,6 +20,7 @@ struct mhd_ctx {
   CUtensorMap tma[2];  // the two state sets, boxes of A only (split pass A)
   CUtensorMap tmr[2];  // the two state sets, boxes of u, ln rho, ln T (split pass R)
   CUtensorMap tmdf;    // the RK accumulator, 32 x 8 tiles of the 8 fields (pair kernel)
+  CUtensorMap tmdbar;  // its adjoint D, the same tiles (pair kernel, adjoint mode)
   bool tiled;          // FP32: TMA-fed z-march kernels; otherwise the simple kernel
   bool split;          // FP32 forward: split passes (else the fused z-march kernel)
   bool pair;           // FP32 forward: one-pass f32x2 kernel with TMEM z histories
@@ -28,6 +29,7 @@ struct mhd_ctx {
   int ksw;             // first layer with a nonzero swamp weight or slope (nz if none)
   bool adj_tiled;      // adjoint: tiled gather and (FP32) z-march point kernel, else one thread per point
   bool adj_zm;         // adjoint gather as a z-march (else 3D tiles after a grad-div fold)
+  bool adj_pair;       // FP32 adjoint point kernel on the pair z-march (else the one-cell-per-thread z-march)
   mhd_params p;
   Layout L;
   cudaStream_t st;
@@ -568,6 +570,7 @@ extern "C" int mhd_create(const mhd_params* p, void* workspace, size_t ws_bytes,
     const char* va = getenv("MHD_ADJ_VARIANT");
     h->adj_tiled = !(va && strcmp(va, "simple") == 0);
     h->adj_zm = h->adj_tiled && !(va && strcmp(va, "tiled3d") == 0);
+    h->adj_pair = h->adj_zm && h->pair;
   }
   h->t0 = 0.0;
   h->t1 = 0.0;
@@ -607,6 +610,8 @@ extern "C" int mhd_create(const mhd_params* p, void* workspace, size_t ws_bytes,
         rc = fail(h, MHD_ERR_CUDA, "cuTensorMapEncodeTiled failed for the split boxes of state set %d", s);
     if (!rc && make_state_tensor_map(&h->tmdf, h->L, h->df, NF, 32, 8) != 0)
       rc = fail(h, MHD_ERR_CUDA, "cuTensorMapEncodeTiled failed for the RK accumulator");
+    if (!rc && p->adjoint && make_state_tensor_map(&h->tmdbar, h->L, h->dbar, NF, 32, 8) != 0)
+      rc = fail(h, MHD_ERR_CUDA, "cuTensorMapEncodeTiled failed for the adjoint accumulator");
   }
   if (!rc) {
     StepState s0;
@@ -971,7 +976,11 @@ static void adjoint_step_impl(mhd_ctx* h) {
   const int tmi[3] = {h->cur, 1 - h->cur, 2};
   for (int s = 2; s >= 0; --s) {
     const double alpha = rk_alpha(s), beta = rk_beta(s > 0 ? s - 1 : 2);
-    if (sizeof(R) == 4 && h->tiled && h->adj_tiled)
+    if (sizeof(R) == 4 && h->adj_pair)
+      launch_adj_point_pair(&h->tm[tmi[s]], &h->tmdbar, h->L, *(const Phys<float>*)&ph, h->bgf, (const float*)h->dbar,
+                            (float*)h->coef, h->thbar, (const float*)h->wtab, (const float*)h->wptab, h->ss, s,
+                            h->p.dx, h->p.dy, h->p.dz, h->st);
+    else if (sizeof(R) == 4 && h->tiled && h->adj_tiled)
       launch_adj_point_tiled(&h->tm[tmi[s]], h->L, *(const Phys<float>*)&ph, h->bgf, (const float*)h->dbar,
                              (float*)h->coef, h->thbar, (const float*)h->wtab, (const float*)h->wptab, h->ss, s,
                              h->p.dx, h->p.dy, h->p.dz, h->st);

@@ -77,6 +77,12 @@ bool rk_pair_supported(const Layout& L);
 void launch_rk_pair(const CUtensorMap* tm, const CUtensorMap* tmd, const Layout& L, const Phys<float>& ph, const Background<float>& bg,
                     float* fout, float* df, const float* wtab, const float* wptab, const Driver& drv, StepState* ss,
                     int sub, double dx, double dy, double dz, cudaStream_t st);
+// pointwise adjoint of substep sub on the same z-march (tm: the ghost-filled
+// substep state, tmd: D, the adjoint of the RK accumulator, 32 x 8 tiles)
+void launch_adj_point_pair(const CUtensorMap* tm, const CUtensorMap* tmd, const Layout& L, const Phys<float>& ph,
+                           const Background<float>& bg, const float* dbar, float* coef, double* thbar,
+                           const float* wtab, const float* wptab, StepState* ss, int sub, double dx, double dy,
+                           double dz, cudaStream_t st);
 // adjoint (transposed linearisation of one substep)
 constexpr int NCOEF_ADJ = 40;
 template <typename R> void launch_adj_point(const Layout& L, const Phys<R>& ph, const Background<R>& bg, const R* g,

@@ -27,6 +27,7 @@
 // waits.  Every exit path deallocates.
 #include <cuda.h>
 
+#include "mhd_adjoint_point.cuh"
 #include "mhd_internal.h"
 #include "mhd_zmarch.cuh"
 
@@ -77,6 +78,12 @@ struct Args {
   int sub;
   int ntx, nty, nch, kchunk;
   Coef cx, cy, cz;
+  // adjoint mode: D (adjoint of the RK accumulator, padded layout; the
+  // accumulator tiles then carry D), the NCOEF coefficient fields
+  // ([NCOEF][nz][ny][nx]) and the driver adjoints out
+  const float* dbar;
+  float* coef;
+  double* thbar;
 };
 
 // ---- TMEM access (32x32b shape: each thread its own lane) -----------------
@@ -127,7 +134,190 @@ __device__ __forceinline__ void ds_pair(const float* p, int s, const Coef& c, f2
   if (d2) *d2 = fma2(c.e0, z0, fma2(c.e1, add(a1, b1), fma2(c.e2, add(a2, b2), mul(c.e3, add(a3, b3)))));
 }
 
+// ---- a packed pair of FP32 numbers with the arithmetic the templated
+// pointwise adjoint uses (each operation one f32x2 instruction, or two
+// scalar ones for division and exp) --------------------------------------
+struct P2 {
+  f2 v;
+  __device__ __forceinline__ P2() {}
+  __device__ __forceinline__ P2(float a) : v(make_float2(a, a)) {}
+  __device__ __forceinline__ P2(double a) : v(make_float2((float)a, (float)a)) {}
+  __device__ __forceinline__ P2(int a) : v(make_float2((float)a, (float)a)) {}
+  __device__ __forceinline__ explicit P2(f2 a) : v(a) {}
+  __device__ __forceinline__ P2& operator+=(P2 b) { v = add(v, b.v); return *this; }
+  __device__ __forceinline__ P2& operator-=(P2 b) { v = dif(v, b.v); return *this; }
+};
+__device__ __forceinline__ P2 operator+(P2 a, P2 b) { return P2(add(a.v, b.v)); }
+__device__ __forceinline__ P2 operator-(P2 a, P2 b) { return P2(dif(a.v, b.v)); }
+__device__ __forceinline__ P2 operator*(P2 a, P2 b) { return P2(mul(a.v, b.v)); }
+__device__ __forceinline__ P2 operator-(P2 a) { return P2(mul(a.v, F2(-1.f))); }
+__device__ __forceinline__ P2 operator/(P2 a, P2 b) { return P2(make_float2(a.v.x / b.v.x, a.v.y / b.v.y)); }
+}  // namespace pair
+template <> __device__ __forceinline__ pair::P2 rexp<pair::P2>(pair::P2 x) {
+  return pair::P2(make_float2(expf(x.v.x), expf(x.v.y)));
+}
+namespace pair {
+
+// ---- adjoint mode: the derivatives the pointwise adjoint reads, then the
+// per-cell transpose (adjoint_cell) of each of the pair's two cells --------
+__device__ __forceinline__ void adjoint_centre(const Args& a, const float* Pk, const float* Praw, float* scr,
+                                               const float* dtile, uint64_t* dbar_mb, uint32_t& dphase,
+                                               uint32_t& dpending, int k, int k0, int x0, int y0,
+                                               const f2 (&vz)[NF], const f2 (&d1z)[NF], const f2 (&d2z)[NF],
+                                               const f2 (&mz)[6], float wk, float wpk, float lbk, float tbk,
+                                               float dlk, float dtk, float d2tk, float dt, int sub) {
+  const Layout& L = a.L;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4, warp = tid >> 5;
+  const int e = 2 * tx + 4;
+  // y derivatives of A_y, A_x (also the sources of the xy-mixed terms of
+  // grad div A) and of u_y, u_x; the scratch holds D1y A_y, D1y A_x on the
+  // tile plus an x halo (fields 0, 1; warps 0, 1 compute the halo items)
+  f2 dyAy, yyAy, dyAx, yyAx, dyUy, dyUx;
+  ds_pair(Pk + AY * FP, BX, a.cy, dyAy, &yyAy);
+  ds_pair(Pk + AX * FP, BX, a.cy, dyAx, &yyAx);
+  ds_pair(Pk + UY * FP, BX, a.cy, dyUy, nullptr);
+  ds_pair(Pk + UX * FP, BX, a.cy, dyUx, nullptr);
+  {
+    float* sc = scr + ty * BX + e;
+    *reinterpret_cast<f2*>(sc + 0 * SCF) = dyAy;
+    *reinterpret_cast<f2*>(sc + 1 * SCF) = dyAx;
+    if (warp < 2) {
+      const int hr = (tid & 31) >> 2, hx = ((tid & 3) < 2) ? 2 * (tid & 3) : 32 + 2 * (tid & 3);
+      f2 h;
+      ds_pair(Praw + (warp == 0 ? AY : AX) * FP + (hr + 3) * BX + hx, BX, a.cy, h, nullptr);
+      *reinterpret_cast<f2*>(scr + warp * SCF + hr * BX + hx) = h;
+    }
+  }
+  __syncthreads();
+  f2 m0, m1;
+  dx_pair(scr + 0 * SCF + ty * BX + e, a.cx, m0, nullptr);
+  dx_pair(scr + 1 * SCF + ty * BX + e, a.cx, m1, nullptr);
+  // A: off-diagonal first derivatives, Laplacians, grad div
+  f2 dxAy, xxAy, dxAz, xxAz, dyAz, yyAz, dxAx, xxAx;
+  dx_pair(Pk + AX * FP, a.cx, dxAx, &xxAx);
+  dx_pair(Pk + AY * FP, a.cx, dxAy, &xxAy);
+  dx_pair(Pk + AZ * FP, a.cx, dxAz, &xxAz);
+  ds_pair(Pk + AZ * FP, BX, a.cy, dyAz, &yyAz);
+  const f2 lapA0 = add(add(xxAx, yyAx), d2z[AX]);
+  const f2 lapA1 = add(add(xxAy, yyAy), d2z[AY]);
+  const f2 lapA2 = add(add(xxAz, yyAz), d2z[AZ]);
+  const f2 gdA0 = add(add(xxAx, m0), mz[0]);
+  const f2 gdA1 = add(add(m1, yyAy), mz[1]);
+  const f2 gdA2 = add(mz[2], d2z[AZ]);
+  // u: first derivatives; ln rho, ln T: gradients, Laplacian of ln T
+  f2 U00, U10, U20, U21, gL0, gL1, gT0, gT1, xxT, yyT;
+  dx_pair(Pk + UX * FP, a.cx, U00, nullptr);
+  dx_pair(Pk + UY * FP, a.cx, U10, nullptr);
+  dx_pair(Pk + UZ * FP, a.cx, U20, nullptr);
+  ds_pair(Pk + UZ * FP, BX, a.cy, U21, nullptr);
+  dx_pair(Pk + LR * FP, a.cx, gL0, nullptr);
+  ds_pair(Pk + LR * FP, BX, a.cy, gL1, nullptr);
+  dx_pair(Pk + LT * FP, a.cx, gT0, &xxT);
+  ds_pair(Pk + LT * FP, BX, a.cy, gT1, &yyT);
+  const f2 lapT = add(add(add(xxT, yyT), d2z[LT]), F2(d2tk));
+  // D of the pair (bounded wait; a time-out is recorded and the CTA goes on)
+  const int sl = (k - k0) & 1;
+  if (!zm::mbar_wait(dbar_mb, (dphase >> sl) & 1u)) atomicOr(&a.ss->nonfinite, 2);
+  dphase ^= 1u << sl;
+  if (tid == 0) dpending &= ~(1u << sl);
+  f2 dq[NF];
+  {
+    const float* d = dtile + ty * TX + 2 * tx;
+#pragma unroll
+    for (int f = 0; f < NF; ++f) dq[f] = ld2(d + f * TY * TX);
+  }
+  const int i = x0 + 2 * tx, j = y0 + ty;
+  if (i >= L.nx || j >= L.ny) return;
+  const long long n2 = (long long)L.nx * L.ny, n3 = n2 * L.nz;
+  if (k > 0 || a.ph.bcz != 0) {
+    // both cells at once: the templated transpose on packed pairs
+    const Phys<float>& pf = a.ph;
+    Phys<P2> pp;
+    pp.idx = pf.idx; pp.idy = pf.idy; pp.idz = pf.idz;
+    pp.idx2 = pf.idx2; pp.idy2 = pf.idy2; pp.idz2 = pf.idz2;
+    pp.gamma = pf.gamma; pp.gm1 = pf.gm1; pp.gz = pf.gz;
+    pp.nu = pf.nu; pp.eta = pf.eta; pp.kappa0 = pf.kappa0; pp.drho = pf.drho;
+    pp.eta_s = pf.eta_s; pp.chi_s = pf.chi_s; pp.drho_s = pf.drho_s;
+    pp.tau_u = pf.tau_u; pp.tau_A = pf.tau_A;
+    pp.bext[0] = pf.bext[0]; pp.bext[1] = pf.bext[1]; pp.bext[2] = pf.bext[2];
+    pp.bcz = pf.bcz;
+    Cell<P2> cl;
+    cl.A[0] = P2(vz[AX]); cl.A[1] = P2(vz[AY]); cl.A[2] = P2(vz[AZ]);
+    cl.U[0] = P2(vz[UX]); cl.U[1] = P2(vz[UY]); cl.U[2] = P2(vz[UZ]);
+    cl.L = P2(add(F2(lbk), vz[LR]));
+    cl.Th = P2(add(F2(tbk), vz[LT]));
+    cl.dA[0][0] = P2(dxAx); cl.dA[0][1] = P2(dyAx); cl.dA[0][2] = P2(d1z[AX]);
+    cl.dA[1][0] = P2(dxAy); cl.dA[1][1] = P2(dyAy); cl.dA[1][2] = P2(d1z[AY]);
+    cl.dA[2][0] = P2(dxAz); cl.dA[2][1] = P2(dyAz); cl.dA[2][2] = P2(d1z[AZ]);
+    cl.dU[0][0] = P2(U00); cl.dU[0][1] = P2(dyUx); cl.dU[0][2] = P2(d1z[UX]);
+    cl.dU[1][0] = P2(U10); cl.dU[1][1] = P2(dyUy); cl.dU[1][2] = P2(d1z[UY]);
+    cl.dU[2][0] = P2(U20); cl.dU[2][1] = P2(U21); cl.dU[2][2] = P2(d1z[UZ]);
+    cl.lapA[0] = P2(lapA0); cl.lapA[1] = P2(lapA1); cl.lapA[2] = P2(lapA2);
+    cl.gdA[0] = P2(gdA0); cl.gdA[1] = P2(gdA1); cl.gdA[2] = P2(gdA2);
+    // the adjoint reads no second derivative of u and no Laplacian of ln rho
+    cl.lapU[0] = cl.lapU[1] = cl.lapU[2] = P2(0.f);
+    cl.gdU[0] = cl.gdU[1] = cl.gdU[2] = P2(0.f);
+    cl.lapL = P2(0.f);
+    cl.gL[0] = P2(gL0); cl.gL[1] = P2(gL1); cl.gL[2] = P2(add(d1z[LR], F2(dlk)));
+    cl.gT[0] = P2(gT0); cl.gT[1] = P2(gT1); cl.gT[2] = P2(add(d1z[LT], F2(dtk)));
+    cl.lapT = P2(lapT);
+    P2 wo[NF];
+#pragma unroll
+    for (int f = 0; f < NF; ++f) wo[f] = P2(mul(F2(dt), dq[f]));
+    // closed top: du_z/dt = 0 (the photosphere is the scalar path below)
+    if (pf.bcz == 0 && k == L.nz - 1) wo[UZ] = P2(0.f);
+    P2 cf[NCOEF];
+    rhs_point_adjoint<P2>(cl, pp, P2(wk), P2(wpk), wo, cf);
+    float* co = a.coef + (long long)k * n2 + (long long)j * L.nx + i;
+#pragma unroll
+    for (int q = 0; q < NCOEF; ++q) *reinterpret_cast<f2*>(co + q * n3) = cf[q].v;
+    return;
+  }
+  // photosphere: one cell at a time (nudging rows, FP64 driver adjoints)
+#pragma unroll 1
+  for (int c = 0; c < 2; ++c) {
+    auto P = [c](f2 v) { return c == 0 ? v.x : v.y; };
+    Cell<float> cl;
+    cl.A[0] = P(vz[AX]); cl.A[1] = P(vz[AY]); cl.A[2] = P(vz[AZ]);
+    cl.U[0] = P(vz[UX]); cl.U[1] = P(vz[UY]); cl.U[2] = P(vz[UZ]);
+    cl.L = lbk + P(vz[LR]);
+    cl.Th = tbk + P(vz[LT]);
+    cl.dA[0][0] = P(dxAx); cl.dA[0][1] = P(dyAx); cl.dA[0][2] = P(d1z[AX]);
+    cl.dA[1][0] = P(dxAy); cl.dA[1][1] = P(dyAy); cl.dA[1][2] = P(d1z[AY]);
+    cl.dA[2][0] = P(dxAz); cl.dA[2][1] = P(dyAz); cl.dA[2][2] = P(d1z[AZ]);
+    cl.dU[0][0] = P(U00); cl.dU[0][1] = P(dyUx); cl.dU[0][2] = P(d1z[UX]);
+    cl.dU[1][0] = P(U10); cl.dU[1][1] = P(dyUy); cl.dU[1][2] = P(d1z[UY]);
+    cl.dU[2][0] = P(U20); cl.dU[2][1] = P(U21); cl.dU[2][2] = P(d1z[UZ]);
+    cl.lapA[0] = P(lapA0); cl.lapA[1] = P(lapA1); cl.lapA[2] = P(lapA2);
+    cl.gdA[0] = P(gdA0); cl.gdA[1] = P(gdA1); cl.gdA[2] = P(gdA2);
+    // the adjoint reads no second derivative of u and no Laplacian of ln rho
+    cl.lapU[0] = cl.lapU[1] = cl.lapU[2] = 0.f;
+    cl.gdU[0] = cl.gdU[1] = cl.gdU[2] = 0.f;
+    cl.lapL = 0.f;
+    cl.gL[0] = P(gL0); cl.gL[1] = P(gL1); cl.gL[2] = P(d1z[LR]) + dlk;
+    cl.gT[0] = P(gT0); cl.gT[1] = P(gT1); cl.gT[2] = P(d1z[LT]) + dtk;
+    cl.lapT = P(lapT);
+    float wo[NF];
+#pragma unroll
+    for (int f = 0; f < NF; ++f) wo[f] = dt * P(dq[f]);
+    const long long q2 = (long long)j * L.nx + i + c;
+    const long long cu = L.at(UX, 0, j, i + c);
+    float cf[NCOEF];
+    adjoint_cell<float>(cl, a.ph, wk, wpk, wo, dt, k, L.nz, a.dbar + cu, a.dbar + cu + L.fs, L.sz(), a.thbar, q2,
+                        n2, a.ss, sub, cf);
+    float* co = a.coef + (long long)k * n2 + q2;
+#pragma unroll
+    for (int q = 0; q < NCOEF; ++q) co[q * n3] = cf[q];
+  }
+}
+
 // ---- the kernel -------------------------------------------------------------
+// ADJ = false: right-hand side + RK update of substep `sub` (sub < 0: store
+// the right-hand side only).  ADJ = true: the pointwise adjoint of substep
+// `sub` (the input is the ghost-filled substep state, tmd maps D): per
+// interior cell the NCOEF coefficients of the transposed right-hand side and,
+// at the photosphere, the driver adjoints; no state is stored.
+template <bool ADJ>
 __global__ void __launch_bounds__(NT, 2) rk_pair_kernel(const __grid_constant__ CUtensorMap tm,
                                                         const __grid_constant__ CUtensorMap tmd, const Args a) {
   extern __shared__ __align__(128) float smem[];
@@ -232,7 +422,7 @@ __global__ void __launch_bounds__(NT, 2) rk_pair_kernel(const __grid_constant__ 
     const int pbase = k0 - NG, plast = k1 + NG - 1;
     if (tid == 0) {
       for (int p = pbase; p <= min(pbase + NR - 1, plast); ++p) load(p, p - pbase, x0, y0);
-      if (sub > 0) load_df(k0, k0, x0, y0);
+      if (ADJ || sub > 0) load_df(k0, k0, x0, y0);
     }
     // prologue: planes k0-3 .. k0+2; the three below k0 are released at once
     for (int p = pbase; p < k0 + NG && !bad; ++p) {
@@ -259,7 +449,7 @@ __global__ void __launch_bounds__(NT, 2) rk_pair_kernel(const __grid_constant__ 
         // every thread is past centre k - 1: plane k - 1's slot takes k + 4,
         // and its accumulator buffer the tile of centre k + 1
         if (k > k0 && k - 1 + NR <= plast) load(k - 1 + NR, wrap(sk + NR - 1), x0, y0);
-        if (sub > 0 && k + 1 < k1) load_df(k + 1, k0, x0, y0);
+        if ((ADJ || sub > 0) && k + 1 < k1) load_df(k + 1, k0, x0, y0);
       }
       front(k + NG, s3);
       tm_wait_st();
@@ -297,7 +487,7 @@ __global__ void __launch_bounds__(NT, 2) rk_pair_kernel(const __grid_constant__ 
       // stateful u_x, u_y ghost rows below the photosphere (k = 0): their
       // values are the TMEM copies of planes -1 .. -3 (loaded warp-wide)
       f2 gux[NG], guy[NG];
-      if (a.ph.bcz == 0 && k == 0) {
+      if (!ADJ && a.ph.bcz == 0 && k == 0) {
 #pragma unroll
         for (int m = 1; m <= NG; ++m) {
           uint32_t g[4];
@@ -310,6 +500,11 @@ __global__ void __launch_bounds__(NT, 2) rk_pair_kernel(const __grid_constant__ 
         }
       }
 
+      if constexpr (ADJ) {
+        adjoint_centre(a, Pk, raw + sk * PLANE, scr, dfs + ((k - k0) & 1) * DFT, &mbd[(k - k0) & 1], dphase,
+                       dpending, k, k0, x0, y0, vz, d1z, d2z, mz, wk, wpk, lbk, tbk, dlk, dtk, d2tk, dt, sub);
+        continue;
+      }
       // ---- x, y derivatives from the shared ring, folded as they come -------
       // (the own-axis second derivatives D2x A_x, D2y A_y cancel in J outside
       // the swamp layers)
@@ -571,11 +766,13 @@ static int g_pair_ctas = 0;
 
 bool rk_pair_supported(const Layout& L) { return L.nx % 2 == 0 && L.nx >= 8 && L.ny >= 6; }
 
-void launch_rk_pair(const CUtensorMap* tm, const CUtensorMap* tmd, const Layout& L, const Phys<float>& ph, const Background<float>& bg,
-                    float* fout, float* df, const float* wtab, const float* wptab, const Driver& drv, StepState* ss,
-                    int sub, double dx, double dy, double dz, cudaStream_t st) {
+static pair::Args pair_args(const Layout& L, const Phys<float>& ph, const Background<float>& bg, const float* wtab,
+                            const float* wptab, StepState* ss, int sub, double dx, double dy, double dz) {
   if (!g_pair_ctas) {
-    cudaFuncSetAttribute(pair::rk_pair_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pair::SMEM_BYTES);
+    cudaFuncSetAttribute(pair::rk_pair_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)pair::SMEM_BYTES);
+    cudaFuncSetAttribute(pair::rk_pair_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)pair::SMEM_BYTES);
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -586,14 +783,8 @@ void launch_rk_pair(const CUtensorMap* tm, const CUtensorMap* tmd, const Layout&
   a.L = L;
   a.ph = ph;
   a.bg = bg;
-  a.fout = fout;
-  a.df = df;
   a.wtab = wtab;
   a.wptab = wptab;
-  a.axt = (const float*)drv.axt;
-  a.ayt = (const float*)drv.ayt;
-  a.v0 = (const float*)drv.v0;
-  a.v1 = (const float*)drv.v1;
   a.ss = ss;
   a.sub = sub;
   a.ntx = (L.nx + pair::TX - 1) / pair::TX;
@@ -617,9 +808,35 @@ void launch_rk_pair(const CUtensorMap* tm, const CUtensorMap* tmd, const Layout&
   const int tiles = a.ntx * a.nty;
   a.kchunk = zm::zchunk(L.nz, tiles, g_pair_ctas);
   a.nch = (L.nz + a.kchunk - 1) / a.kchunk;
-  const int nitems = tiles * a.nch;
+  return a;
+}
+
+void launch_rk_pair(const CUtensorMap* tm, const CUtensorMap* tmd, const Layout& L, const Phys<float>& ph,
+                    const Background<float>& bg, float* fout, float* df, const float* wtab, const float* wptab,
+                    const Driver& drv, StepState* ss, int sub, double dx, double dy, double dz, cudaStream_t st) {
+  pair::Args a = pair_args(L, ph, bg, wtab, wptab, ss, sub, dx, dy, dz);
+  a.fout = fout;
+  a.df = df;
+  a.axt = (const float*)drv.axt;
+  a.ayt = (const float*)drv.ayt;
+  a.v0 = (const float*)drv.v0;
+  a.v1 = (const float*)drv.v1;
+  const int nitems = a.ntx * a.nty * a.nch;
   const int grid = nitems < g_pair_ctas ? nitems : g_pair_ctas;
-  pair::rk_pair_kernel<<<grid, pair::NT, pair::SMEM_BYTES, st>>>(*tm, *tmd, a);
+  pair::rk_pair_kernel<false><<<grid, pair::NT, pair::SMEM_BYTES, st>>>(*tm, *tmd, a);
+}
+
+void launch_adj_point_pair(const CUtensorMap* tm, const CUtensorMap* tmd, const Layout& L, const Phys<float>& ph,
+                           const Background<float>& bg, const float* dbar, float* coef, double* thbar,
+                           const float* wtab, const float* wptab, StepState* ss, int sub, double dx, double dy,
+                           double dz, cudaStream_t st) {
+  pair::Args a = pair_args(L, ph, bg, wtab, wptab, ss, sub, dx, dy, dz);
+  a.dbar = dbar;
+  a.coef = coef;
+  a.thbar = thbar;
+  const int nitems = a.ntx * a.nty * a.nch;
+  const int grid = nitems < g_pair_ctas ? nitems : g_pair_ctas;
+  pair::rk_pair_kernel<true><<<grid, pair::NT, pair::SMEM_BYTES, st>>>(*tm, *tmd, a);
 }
 
 }  // namespace mhd
