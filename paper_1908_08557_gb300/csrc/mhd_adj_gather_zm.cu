@@ -31,6 +31,7 @@
 // stateful u_x, u_y ghost rows (Eq. 5).
 #include "mhd_adjoint_point.cuh"
 #include "mhd_internal.h"
+#include "mhd_pair.cuh"
 #include "mhd_zmarch.cuh"
 
 namespace mhd {
@@ -287,6 +288,231 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 2 : 1) gather_zm_kernel(Z
   }
 }
 
+// ---------------------------------------------------------------------------
+// FP32: the same z-march with two x-adjacent cells per thread in packed f32x2
+// arithmetic (128 threads per 32 x 8 tile; 8-byte shared loads and global
+// accesses).  The x stencils assemble the odd-offset pairs from even ones.
+namespace zp {
+using namespace pk;
+constexpr int NTP = TX / 2 * TY;  // 128 threads
+constexpr int CP = SX / 4 * SY;   // 16-byte chunks of a staged field plane (140)
+
+__device__ __forceinline__ void zs_d1t(f2 (&a)[7], f2 v) {  // D1z^T
+  a[4] = fma2(F2(W<float>::c1), v, a[4]); a[2] = fma2(F2(-W<float>::c1), v, a[2]);
+  a[5] = fma2(F2(W<float>::c2), v, a[5]); a[1] = fma2(F2(-W<float>::c2), v, a[1]);
+  a[6] = fma2(F2(W<float>::c3), v, a[6]); a[0] = fma2(F2(-W<float>::c3), v, a[0]);
+}
+__device__ __forceinline__ void zs_d1(f2 (&a)[7], f2 v) {  // D1z
+  a[2] = fma2(F2(W<float>::c1), v, a[2]); a[4] = fma2(F2(-W<float>::c1), v, a[4]);
+  a[1] = fma2(F2(W<float>::c2), v, a[1]); a[5] = fma2(F2(-W<float>::c2), v, a[5]);
+  a[0] = fma2(F2(W<float>::c3), v, a[0]); a[6] = fma2(F2(-W<float>::c3), v, a[6]);
+}
+__device__ __forceinline__ void zs_d2(f2 (&a)[7], f2 v) {  // D2z
+  a[3] = fma2(F2(W<float>::e0), v, a[3]);
+  a[4] = fma2(F2(W<float>::e1), v, a[4]); a[2] = fma2(F2(W<float>::e1), v, a[2]);
+  a[5] = fma2(F2(W<float>::e2), v, a[5]); a[1] = fma2(F2(W<float>::e2), v, a[1]);
+  a[6] = fma2(F2(W<float>::e3), v, a[6]); a[0] = fma2(F2(W<float>::e3), v, a[0]);
+}
+// second derivative only
+__device__ __forceinline__ f2 dxx(const float* p, const Coef& c) {
+  f2 d1, d2;
+  dx_pair(p, c, d1, &d2);
+  return d2;
+}
+__device__ __forceinline__ f2 dyy(const float* p, const Coef& c) {
+  f2 d1, d2;
+  ds_pair(p, SX, c, d1, &d2);
+  return d2;
+}
+__device__ __forceinline__ f2 dx1(const float* p, const Coef& c) {
+  f2 d1;
+  dx_pair(p, c, d1, nullptr);
+  return d1;
+}
+__device__ __forceinline__ f2 dy1(const float* p, const Coef& c) {
+  f2 d1;
+  ds_pair(p, SX, c, d1, nullptr);
+  return d1;
+}
+
+struct PArgs {
+  ZArgs<float> z;
+  Coef cx, cy;  // D1, D2 weights over dx, dy
+};
+
+template <int GRP>
+__device__ __forceinline__ void item_pair(const PArgs& pa_, float* buf, float* scrb, int x0, int y0, int n0,
+                                          int n1) {
+  const ZArgs<float>& a = pa_.z;
+  const Layout& L = a.L;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int nx = L.nx, ny = L.ny, nz = L.nz;
+  const long long n2 = (long long)nx * ny, n3 = n2 * nz;
+  const Phys<float>& ph = a.ph;
+  const float idz = ph.idz, idz2 = ph.idz2;
+  const float dt = (float)a.ss->dt;
+  const int e = 2 * tx + XO;
+  const int cen = (ty + 3) * SX + e;
+  const int pa = max(0, n0 - NG), pb = min(nz - 1, n1 + NG - 1);
+  auto chunk_off = [&](int c) -> long long {
+    if (c >= CP) return 0;
+    const int r = c / (SX / 4), cc = c - r * (SX / 4);
+    const int yy = ((y0 - 3 + r) % ny + ny) % ny, xx = ((x0 - XO + cc * 4) % nx + nx) % nx;
+    return (long long)yy * nx + xx;
+  };
+  const long long off0 = chunk_off(tid), off1 = chunk_off(tid + NTP);
+  auto cp16 = [](float* dst, const float* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(zm::sa(dst)), "l"(src) : "memory");
+  };
+  auto stage = [&](int p, int b) {
+    float* dst = buf + b * NQ * SP;
+    const float* src = a.coef + (long long)p * n2;
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+      const long long fo = (long long)kQ[GRP][q] * n3;
+      cp16(dst + q * SP + tid * 4, src + fo + off0);
+      if (tid + NTP < CP) cp16(dst + q * SP + (tid + NTP) * 4, src + fo + off1);
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
+  if (pa <= pb) stage(pa, 0);
+  int b = 0;
+  f2 acc[NO][7];
+#pragma unroll
+  for (int t = 0; t < NO; ++t)
+#pragma unroll
+    for (int d = 0; d < 7; ++d) acc[t][d] = F2(0.f);
+  const int i = x0 + 2 * tx, j = y0 + ty;
+  const bool live = i < nx && j < ny;
+  // x-halo pairs of the in-plane mixed scratch: 2 fields x 8 rows x 4 pairs
+  const int hf = tid >> 5, hr = (tid & 31) >> 2, hx = (tid & 3) < 2 ? 2 * (tid & 3) : 32 + 2 * (tid & 3);
+  const float g = GRP == 0 ? 1.f : 1.f / 3.f;
+  const Coef& cx = pa_.cx;
+  const Coef& cy = pa_.cy;
+
+  for (int p = n0 - NG; p <= n1 + NG - 1; ++p) {
+    const int n = p - NG;
+    const bool emit = n >= n0 && live;
+    const bool fz = n >= a.klo && n < a.khi;
+    f2 fo[NO], dd[NO];
+    long long qo = 0;
+    if (emit) qo = L.at(0, n, j, i);
+#pragma unroll
+    for (int t = 0; t < NO; ++t) {
+      const int f = GRP == 0 ? (t < 3 ? AX + t : LR) : (t < 3 ? UX + t : LT);
+      const long long q = qo + (long long)f * L.fs;
+      fo[t] = (emit && fz) ? ld2(a.fbar + q) : F2(0.f);
+      dd[t] = (emit && (fz || (ph.bcz == 0 && n <= 0))) ? ld2(a.dbar + q) : F2(0.f);
+    }
+    if (p >= pa && p <= pb) {
+      if (p + 1 <= pb) {
+        stage(p + 1, b ^ 1);
+        asm volatile("cp.async.wait_group 1;" ::: "memory");
+      } else {
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
+      }
+      __syncthreads();
+      const float* s = buf + b * NQ * SP;
+      auto S = [&](int q) { return s + q * SP + cen; };
+      // first derivatives of the three components: -D1x, -D1y, D1z^T
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        acc[c][3] = dif(acc[c][3], add(dx1(S(3 * c), cx), dy1(S(3 * c + 1), cy)));
+        zs_d1t(acc[c], mul(F2(idz), ld2(S(3 * c + 2))));
+      }
+      // Laplacians (u: with the own-axis part of grad div u = lap u / 3)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const float* h = S(9 + c);
+        const float wx = (GRP == 1 && c == 0) ? 4.f / 3.f : 1.f, wy = (GRP == 1 && c == 1) ? 4.f / 3.f : 1.f;
+        const float wz = (GRP == 1 && c == 2) ? 4.f / 3.f : 1.f;
+        acc[c][3] = fma2(F2(wx), dxx(h, cx), fma2(F2(wy), dyy(h, cy), acc[c][3]));
+        zs_d2(acc[c], mul(F2(wz * idz2), ld2(h)));
+      }
+      const float* gx = GRP == 0 ? S(12) : S(9);
+      const float* gy = GRP == 0 ? S(13) : S(10);
+      const float* gz = GRP == 0 ? S(14) : S(11);
+      if (GRP == 0) {
+        acc[0][3] = add(acc[0][3], dxx(gx, cx));
+        acc[1][3] = add(acc[1][3], dyy(gy, cy));
+        zs_d2(acc[2], mul(F2(idz2), ld2(gz)));
+      } else {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) acc[c][3] = add(acc[c][3], ld2(S(12 + c)));
+      }
+      // xz, yz, zx, zy mixed: D1z of in-plane first derivatives
+      const f2 gyy = dy1(gy, cy);
+      zs_d1(acc[2], mul(F2(g * idz), add(dx1(gx, cx), gyy)));
+      zs_d1(acc[0], mul(F2(g * idz), dx1(gz, cx)));
+      zs_d1(acc[1], mul(F2(g * idz), dy1(gz, cy)));
+      // xy mixed through the x-halo scratch: D1x(D1y gd_x) -> y, D1x(D1y gd_y) -> x
+      float* scr = scrb + b * 2 * TY * SX;
+      *reinterpret_cast<f2*>(scr + ty * SX + e) = dy1(gx, cy);
+      *reinterpret_cast<f2*>(scr + TY * SX + ty * SX + e) = gyy;
+      if (tid < 64)
+        *reinterpret_cast<f2*>(scr + hf * TY * SX + hr * SX + hx) =
+            dy1(s + (GRP == 0 ? 12 + hf : 9 + hf) * SP + (hr + 3) * SX + hx, cy);
+      // the scalar: value, -D1x, -D1y, D1z^T, Laplacian
+      acc[3][3] = add(acc[3][3], dif(add(ld2(S(15)), add(dxx(S(19), cx), dyy(S(19), cy))),
+                                     add(dx1(S(16), cx), dy1(S(17), cy))));
+      zs_d1t(acc[3], mul(F2(idz), ld2(S(18))));
+      zs_d2(acc[3], mul(F2(idz2), ld2(S(19))));
+      __syncthreads();
+      acc[1][3] = fma2(F2(g), dx1(scr + ty * SX + e, cx), acc[1][3]);
+      acc[0][3] = fma2(F2(g), dx1(scr + TY * SX + ty * SX + e, cx), acc[0][3]);
+      b ^= 1;
+    }
+    if (emit) {
+#pragma unroll
+      for (int t = 0; t < NO; ++t) {
+        const int f = GRP == 0 ? (t < 3 ? AX + t : LR) : (t < 3 ? UX + t : LT);
+        const long long q = qo + (long long)f * L.fs;
+        const f2 v = acc[t][0];
+        if (fz) {
+          const f2 fv = add(fo[t], v);
+          *reinterpret_cast<f2*>(a.fbar + q) = fv;
+          *reinterpret_cast<f2*>(a.dbar + q) = fma2(F2(a.alpha), dd[t], mul(F2(a.beta), fv));
+        } else {
+          f2 gv = v;
+          if (ph.bcz == 0 && ((n == 0 && (f == AX || f == AY)) || (n < 0 && (f == UX || f == UY))))
+            gv = dif(gv, mul(F2((f == AX || f == AY ? ph.tau_A : ph.tau_u) * dt), dd[t]));
+          *reinterpret_cast<f2*>(a.gbar + q) = gv;
+        }
+      }
+    }
+#pragma unroll
+    for (int t = 0; t < NO; ++t) {
+#pragma unroll
+      for (int d = 0; d < 6; ++d) acc[t][d] = acc[t][d + 1];
+      acc[t][6] = F2(0.f);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(NTP, 2) gather_pair_kernel(PArgs pa_) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float* buf = reinterpret_cast<float*>(smem_raw);
+  float* scr = buf + 2 * NQ * SP;
+  const ZArgs<float>& a = pa_.z;
+  if (halted(a.ss)) return;
+  const int nzo = a.L.nz + 2 * NG;
+  const int tiles = a.ntx * a.nty;
+  const int nitems = tiles * a.nch * 2;
+  for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
+    const int grp = item & 1;
+    const int rest = item >> 1;
+    const int ch = rest / tiles, tile = rest % tiles;
+    const int x0 = (tile % a.ntx) * TX, y0 = (tile / a.ntx) * TY;
+    const int n0 = ch * a.kchunk - NG, n1 = min(nzo, (ch + 1) * a.kchunk) - NG;
+    __syncthreads();
+    if (grp == 0)
+      item_pair<0>(pa_, buf, scr, x0, y0, n0, n1);
+    else
+      item_pair<1>(pa_, buf, scr, x0, y0, n0, n1);
+  }
+}
+}  // namespace zp
+
 }  // namespace gzm
 
 template <typename R>
@@ -320,6 +546,36 @@ void launch_adj_gather_zm(const Layout& L, const Phys<R>& ph, const R* coef, R* 
   a.kchunk = zm::zchunk(L.nz + 2 * NG, 2 * tiles, ctas);
   a.nch = (L.nz + 2 * NG + a.kchunk - 1) / a.kchunk;
   const int nitems = 2 * tiles * a.nch;
+  if constexpr (sizeof(R) == 4) {
+    static int pctas = 0;
+    if (!pctas) {
+      cudaFuncSetAttribute(gzm::zp::gather_pair_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      int dev = 0, sms = 0, per = 0;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, gzm::zp::gather_pair_kernel, gzm::zp::NTP, smem);
+      pctas = sms * (per > 0 ? per : 1);
+    }
+    gzm::zp::PArgs pa;
+    pa.z = a;
+    a.kchunk = zm::zchunk(L.nz + 2 * NG, 2 * tiles, pctas);
+    a.nch = (L.nz + 2 * NG + a.kchunk - 1) / a.kchunk;
+    pa.z = a;
+    const double W1[4] = {0.0, 45.0 / 60.0, -9.0 / 60.0, 1.0 / 60.0};
+    const double W2[4] = {-490.0 / 180.0, 270.0 / 180.0, -27.0 / 180.0, 2.0 / 180.0};
+    auto coef = [&](double h) {
+      pk::Coef c;
+      c.c1 = pk::F2((float)(W1[1] / h)); c.c2 = pk::F2((float)(W1[2] / h)); c.c3 = pk::F2((float)(W1[3] / h));
+      c.e0 = pk::F2((float)(W2[0] / (h * h))); c.e1 = pk::F2((float)(W2[1] / (h * h)));
+      c.e2 = pk::F2((float)(W2[2] / (h * h))); c.e3 = pk::F2((float)(W2[3] / (h * h)));
+      return c;
+    };
+    pa.cx = coef(1.0 / (double)ph.idx);
+    pa.cy = coef(1.0 / (double)ph.idy);
+    const int pitems = 2 * tiles * a.nch;
+    gzm::zp::gather_pair_kernel<<<pitems < pctas ? pitems : pctas, gzm::zp::NTP, smem, st>>>(pa);
+    return;
+  }
   gzm::gather_zm_kernel<R><<<nitems < ctas ? nitems : ctas, gzm::NT, smem, st>>>(a);
 }
 

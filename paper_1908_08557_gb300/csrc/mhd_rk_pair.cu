@@ -29,10 +29,13 @@
 
 #include "mhd_adjoint_point.cuh"
 #include "mhd_internal.h"
+#include "mhd_pair.cuh"
 #include "mhd_zmarch.cuh"
 
 namespace mhd {
 namespace pair {
+
+using namespace pk;
 
 constexpr int TX = zm::TX, TY = zm::TY;  // 32 x 8 cells
 constexpr int BX = zm::BX, BY = zm::BY;  // 40 x 14 box
@@ -47,20 +50,6 @@ constexpr size_t SMEM_BYTES = (size_t)NR * PLANE * 4 + (size_t)NSC * SCF * 4 + (
 static_assert(SMEM_BYTES > 233472 / 3, "ring must keep TMEM users at <= 2 CTAs per SM");
 constexpr int TMEM_COLS = 256;
 constexpr int VCOL = 0, SCOL = 128;      // value / source rings in TMEM
-
-typedef float2 f2;
-__device__ __forceinline__ f2 F2(float a) { return make_float2(a, a); }
-__device__ __forceinline__ f2 add(f2 a, f2 b) { return __fadd2_rn(a, b); }
-__device__ __forceinline__ f2 mul(f2 a, f2 b) { return __fmul2_rn(a, b); }
-__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) { return __ffma2_rn(a, b, c); }
-// a - b, one rounding
-__device__ __forceinline__ f2 dif(f2 a, f2 b) { return __ffma2_rn(b, F2(-1.f), a); }
-__device__ __forceinline__ f2 ld2(const float* p) { return *reinterpret_cast<const f2*>(p); }
-
-struct Coef {
-  f2 c1, c2, c3;        // D1 weights / spacing
-  f2 e0, e1, e2, e3;    // D2 weights / spacing^2
-};
 
 struct Args {
   Layout L;
@@ -116,23 +105,6 @@ __device__ __forceinline__ void tm_st(uint32_t t, const V16& v) {
 }
 __device__ __forceinline__ void tm_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 __device__ __forceinline__ void tm_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
-
-// ---- stencils on a box row / column at an even x position -----------------
-// first and second x derivatives of the cell pair at p (p even, p - 4 .. p + 5 in the row)
-__device__ __forceinline__ void dx_pair(const float* p, const Coef& c, f2& d1, f2* d2) {
-  const f2 m4 = ld2(p - 4), m2 = ld2(p - 2), z0 = ld2(p), p2 = ld2(p + 2), p4 = ld2(p + 4);
-  const f2 om3 = make_float2(m4.y, m2.x), om1 = make_float2(m2.y, z0.x);
-  const f2 op1 = make_float2(z0.y, p2.x), op3 = make_float2(p2.y, p4.x);
-  d1 = fma2(c.c1, dif(op1, om1), fma2(c.c2, dif(p2, m2), mul(c.c3, dif(op3, om3))));
-  if (d2) *d2 = fma2(c.e0, z0, fma2(c.e1, add(op1, om1), fma2(c.e2, add(p2, m2), mul(c.e3, add(op3, om3)))));
-}
-// first and second derivatives along a stride s (in floats) of the pair at p
-__device__ __forceinline__ void ds_pair(const float* p, int s, const Coef& c, f2& d1, f2* d2) {
-  const f2 z0 = ld2(p), a1 = ld2(p + s), b1 = ld2(p - s), a2 = ld2(p + 2 * s), b2 = ld2(p - 2 * s),
-           a3 = ld2(p + 3 * s), b3 = ld2(p - 3 * s);
-  d1 = fma2(c.c1, dif(a1, b1), fma2(c.c2, dif(a2, b2), mul(c.c3, dif(a3, b3))));
-  if (d2) *d2 = fma2(c.e0, z0, fma2(c.e1, add(a1, b1), fma2(c.e2, add(a2, b2), mul(c.e3, add(a3, b3)))));
-}
 
 // ---- a packed pair of FP32 numbers with the arithmetic the templated
 // pointwise adjoint uses (each operation one f32x2 instruction, or two
