@@ -212,15 +212,15 @@ def _adjoint_with_variant(case, prec, variant, lam):
 
 @pytest.mark.parametrize("variant", ["tiled", "tiled3d"])
 @pytest.mark.parametrize("shape,prec", [((16, 8, 13), 64), ((64, 32, 21), 64), ((64, 32, 21), 32),
-                                        ((32, 16, 37), 32)])
+                                        ((32, 16, 37), 32), ((128, 32, 21), 32)])
 def test_tiled_gather_matches_simple(shape, prec, variant):
     """The shared-memory adjoint kernels ("tiled", the default: the FP32
     pointwise adjoint on the f32x2 / TMEM z-march and a gather that
     z-marches over coefficient planes with a z-scatter register ring;
     "tiled3d": the one-cell-per-thread z-march point kernel and a 3D-tiled
-    gather after a grad-div fold) against the one thread per point kernels: tiles ragged in x (16 < 32), several y tiles, z chunks
-    ragged (13 + 6, 21 + 6, 37 + 6 output layers), several tiles in x and
-    y."""
+    gather after a grad-div fold) against the one thread per point kernels:
+    tiles ragged in x (16 < 32), several y tiles, z chunks ragged (13 + 6,
+    21 + 6, 37 + 6 output layers), several tiles in x and y (128 x 32)."""
     nx, ny, nz = shape
     case = _case(nx, ny, nz, seed=12)
     lam = np.random.default_rng(13).standard_normal((8, nz, ny, nx))
