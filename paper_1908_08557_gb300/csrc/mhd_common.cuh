@@ -8,9 +8,12 @@
 namespace mhd {
 
 constexpr int NG = 3;     // ghost layers per side (Sect. 2.4, 2.5)
-constexpr int XOFF = 4;   // interior x = 0 sits at element 4 of a padded row,
-                          // so tile loads starting 4 cells left of an
-                          // interior multiple of 4 are 16-byte aligned
+constexpr int XOFF = 8;   // interior x = 0 sits at element 8 of a padded row:
+                          // rows (pitch a multiple of 8 elements) start on
+                          // 32-byte sectors, so a warp's row of interior cells
+                          // is whole sectors, and tile loads starting 4 cells
+                          // left of an interior multiple of 4 are 16-byte
+                          // aligned (TMA)
 constexpr int NF = 8;
 enum Field { AX = 0, AY, AZ, UX, UY, UZ, LR, LT };
 
@@ -29,7 +32,9 @@ struct Layout {
 inline Layout make_layout(int nx, int ny, int nz) {
   Layout L;
   L.nx = nx; L.ny = ny; L.nz = nz;
-  L.mx = XOFF + ((nx + NG + 3) / 4) * 4;
+  // x from -XOFF to the last periodic image (nx + 3, written by the pair
+  // kernels), rounded to whole 32-byte sectors
+  L.mx = (XOFF + nx + 4 + 7) / 8 * 8;
   L.my = ny + 2 * NG;
   L.mz = nz + 2 * NG;
   long long n = (long long)L.mx * L.my * L.mz;

@@ -352,7 +352,7 @@ __global__ void __launch_bounds__(NT, 2) rk_pair_kernel(const __grid_constant__ 
   // ring slots are tracked incrementally (slot of plane p = (p - pbase) mod NR)
   auto wrap = [](int s) { return s >= NR ? s - NR : s; };
   auto load = [&](int p, int s, int x0, int y0) {
-    zm::tma_plane(&tm, raw + s * PLANE, &mbar[s], PLANE * 4, x0, y0, p + NG, 0);
+    zm::tma_plane(&tm, raw + s * PLANE, &mbar[s], PLANE * 4, x0 - 4 + XOFF, y0, p + NG, 0);
     pending |= 1u << s;
   };
   // collective bounded wait for plane p; false on time-out (uniform)

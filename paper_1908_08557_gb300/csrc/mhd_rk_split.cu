@@ -83,7 +83,7 @@ struct Ring {
   }
   __device__ void load(const CUtensorMap* tm, float* raw, int stride, unsigned bytes, int slot, int x0, int y0,
                        int p, int f0) {
-    zm::tma_plane(tm, raw + slot * stride, &mbar[slot], bytes, x0, y0, p + NG, f0);
+    zm::tma_plane(tm, raw + slot * stride, &mbar[slot], bytes, x0 - 4 + XOFF, y0, p + NG, f0);
     pending |= 1u << slot;
   }
   // collective: false (for every thread) if any thread's wait timed out

@@ -75,7 +75,7 @@ struct Args {
 };
 
 __device__ __forceinline__ void tma_plane(const CUtensorMap* tm, float* dst, uint64_t* bar, int x, int y, int z) {
-  zm::tma_plane(tm, dst, bar, PLANE_BYTES, x, y, z, 0);
+  zm::tma_plane(tm, dst, bar, PLANE_BYTES, x - 4 + XOFF, y, z, 0);
 }
 
 // front processing of one plane: the z-mixed sources and the xy-mixed terms
