@@ -229,7 +229,12 @@ def adjoint_ratios(case, dev, ws):
     sim.set_driver(torch.tensor(c4.bz, dtype=torch.float32, device=dev),
                    torch.tensor(c4.v0, dtype=torch.float32, device=dev),
                    torch.tensor(c4.v1, dtype=torch.float32, device=dev), c4.t0, c4.t1)
-    n, slots = c4.nsteps, 10
+    # checkpoint slots from a state-history budget of 120 GB (the budget of
+    # the 512 x 512 x 256 checkpointed workload): at 64^3 every step fits, so
+    # the reverse sweep recomputes nothing
+    budget = 120 * 2**30
+    n = c4.nsteps
+    slots = int(max(1, min(n - 1, budget // sim.checkpoint_bytes() - 1)))
     sim.set_time(0.0)
     ck0 = sim.new_checkpoint()
     t0 = sim.save(ck0)
@@ -239,7 +244,8 @@ def adjoint_ratios(case, dev, ws):
     fwd_ck = _cuda_ms(sim.stream, lambda: rv.forward(n))
     sim.adjoint_init(torch.zeros((8, p4["nz"], p4["ny"], p4["nx"]), dtype=torch.float32, device=dev))
     rev_ms = _cuda_ms(sim.stream, rv.reverse)
-    out["bipoles8_64x64x64"] = {"steps": n, "slots": slots, "forward_ms": fwd, "forward_with_checkpoints_ms": fwd_ck,
+    out["bipoles8_64x64x64"] = {"steps": n, "slots": slots, "budget_gb": budget / 2**30, "forward_ms": fwd,
+                                 "forward_with_checkpoints_ms": fwd_ck,
                                  "reverse_ms": rev_ms, "ratio": rev_ms / fwd,
                                  "recompute_fraction": rv.recomputed_steps / n}
     sim.close()
@@ -419,7 +425,7 @@ def run_native(args, ws, rank, local):
     # adjoint / forward time: one adjoint step (recompute of its substeps
     # included) against one forward step, at the bench size; and a full
     # checkpointed sweep of the gradient workload bipoles8_64x64x64
-    # (100 steps, 10 slots) against its forward run
+    # (100 steps, slots from a 120 GB budget) against its forward run
     adj = None
     if not args.no_adjoint:
         adj = adjoint_ratios(case, dev, ws)
