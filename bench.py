@@ -47,6 +47,10 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-production", action="store_true")
+    ap.add_argument("--adjoint-scale", action="store_true",
+                    help="also run the checkpointed gradient of bipoles100_512x512x256 (minutes)")
+    ap.add_argument("--scale-steps", type=int, default=1000)
+    ap.add_argument("--scale-iters", type=int, default=3)
     return ap.parse_args()
 
 
@@ -254,6 +258,100 @@ def adjoint_ratios(case, dev, ws):
     return out
 
 
+def adjoint_scale_line(dev, steps, iters):
+    """bipoles100_512x512x256, FP32, frozen dt: the B_z misfit on layer 48
+    after `steps` steps against a target made by a forward run driven by a
+    different seeded 100-bipole magnetogram and driver; its gradient with
+    respect to (B_z, v0, v1) by the adjoint under binomial checkpointing with
+    slots from a 120 GB state budget; `iters` gradient-descent steps (step
+    length a quarter of loss / |g|^2, halved once if the loss rises)."""
+    import numpy as np
+    import torch
+
+    import inputs
+    from paper_1908_08557_gb300 import Simulation
+    from paper_1908_08557_gb300.adjoint import BzPlane, DrivenRun
+    c = inputs.make_case("bipoles100_512x512x256", dtype=np.float32)
+    ct = inputs.make_case("bipoles100_512x512x256", seed=1, dtype=np.float32)
+    p = dict(c.params, dt_fixed=0.017)
+    k = 48
+    T = lambda a: torch.tensor(a, dtype=torch.float32, device=dev)
+    sim = Simulation(p, T(c.state), c.lnrho0, c.lnT0, precision=32, adjoint=True, device=str(dev))
+    state0 = sim.read().clone()
+    budget = 120 * 2**30
+    slots = int(max(1, min(steps - 1, budget // sim.checkpoint_bytes() - 1)))
+
+    def run(bz, v0, v1):
+        sim.set_driver(bz, v0, v1, c.t0, c.t1)
+        sim.write(state0)
+        sim.set_time(0.0)
+        sim.step(steps)
+        return sim.bz_plane(sim.read(), k)
+
+    target = run(T(ct.bz), T(ct.v0), T(ct.v1)).detach()
+    params = [T(c.bz), T(c.v0), T(c.v1)]
+    fwd_ms = _cuda_ms(sim.stream, lambda: run(*params))
+    loss_of = lambda ps: float(0.5 * ((run(*ps) - target) ** 2).sum())
+    hist, out = [], {"steps": steps, "slots": slots, "budget_gb": budget / 2**30, "forward_ms": fwd_ms}
+    loss = loss_of(params)
+    for it in range(iters):
+        leaves = [q.clone().requires_grad_(True) for q in params]
+        box = {}
+
+        def fwd():
+            box["st"] = DrivenRun.apply(leaves[0], leaves[1], leaves[2], sim, state0, steps, slots, c.t0, c.t1)
+
+        fwd_ck = _cuda_ms(sim.stream, fwd)
+        lossv = 0.5 * ((BzPlane.apply(box["st"], sim, k) - target) ** 2).sum()
+        rev = _cuda_ms(sim.stream, lambda: lossv.backward())
+        g = [q.grad.detach() for q in leaves]
+        g2 = sum(float((x.double() ** 2).sum()) for x in g)
+        eta = 0.25 * float(lossv) / max(g2, 1e-300)
+        trial = [q - eta * x for q, x in zip(params, g)]
+        new = loss_of(trial)
+        if new > loss:
+            eta *= 0.5
+            trial = [q - eta * x for q, x in zip(params, g)]
+            new = loss_of(trial)
+        hist.append({"loss": float(lossv), "forward_with_checkpoints_ms": fwd_ck, "reverse_ms": rev,
+                     "ratio": rev / fwd_ms, "loss_after_step": new})
+        params, loss = trial, new
+    out["iterations"] = hist
+    out["loss_reduction"] = hist[0]["loss"] / loss if hist else None
+    out["recompute_fraction"] = _revolve_recompute(steps, slots) / steps
+    sim.close()
+    del sim
+    torch.cuda.empty_cache()
+    return out
+
+
+def _revolve_recompute(n, slots):
+    """Forward steps the reverse sweep of Revolver recomputes: its schedule
+    replayed on the host against a stand-in that only counts."""
+    from paper_1908_08557_gb300.adjoint import Revolver
+
+    class _Count:
+        def new_checkpoint(self):
+            return None
+
+        def save(self, buf):
+            return 0.0
+
+        def restore(self, buf, t):
+            pass
+
+        def step(self, k):
+            pass
+
+        def adjoint_step(self):
+            pass
+
+    rv = Revolver(_Count(), slots)
+    rv.forward(n)
+    rv.reverse()
+    return rv.recomputed_steps
+
+
 def production_line(dev, ws):
     import numpy as np
     import torch
@@ -435,6 +533,13 @@ def run_native(args, ws, rank, local):
     if not args.no_production:
         prod = production_line(dev, ws)
 
+    scale = None
+    if args.adjoint_scale:
+        try:
+            scale = adjoint_scale_line(dev, args.scale_steps, args.scale_iters)
+        except Exception as exc:  # reported, not fatal: the run is optional
+            scale = {"error": f"{type(exc).__name__}: {exc}"}
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         import oracle
@@ -444,7 +549,7 @@ def run_native(args, ws, rank, local):
                "sample": f"one RK3 step of a 256x256x32 slab of the same recipe ({secs:.1f} s, FP64 oracle, OpenMP)"}
 
     if rank == 0:
-        state_gb = 3 * 8 * (p["nx"] + 8) * (p["ny"] + 6) * (p["nz"] + 6) * 4 / 1e9
+        state_gb = 3 * 8 * (p["nx"] + 16) * (p["ny"] + 6) * (p["nz"] + 6) * 4 / 1e9
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -455,6 +560,8 @@ def run_native(args, ws, rank, local):
                            "parallelism": f"replicas x{ws}"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                 "clocks": clocks, "fp64": fp64, "adjoint": adj, "production_1024x1024x256": prod}
+        if scale is not None:
+            line["adjoint_bipoles100_512x512x256"] = scale
         print(json.dumps(line), flush=True)
 
 

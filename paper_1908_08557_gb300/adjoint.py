@@ -81,34 +81,47 @@ class Revolver:
         self._rev(0, self.n, (0, self.t_start), self.slots)
 
     def _rev(self, i0: int, i1: int, ck, s: int):
+        """Reverse steps i0 .. i1-1 starting from checkpoint ck with s free
+        slots: split at m (binomial_split), reverse the right part with s - 1
+        slots from a checkpoint at m, release that slot, then reverse the left
+        part.  An explicit stack keeps that order without recursion (one
+        level per slot would exceed Python's recursion limit for large slot
+        counts)."""
         sim = self.sim
-        slot0, t0 = ck
-        if i1 - i0 == 1:
-            sim.restore(self.pool[slot0], t0)
-            sim.adjoint_step()
-            self.adjoint_steps += 1
-            return
-        if s == 0:
-            for j in range(i1 - 1, i0 - 1, -1):
+        stack = [("rev", i0, i1, ck, s)]
+        while stack:
+            item = stack.pop()
+            if item[0] == "free":
+                self.free.append(item[1])
+                continue
+            _, i0, i1, ck, s = item
+            slot0, t0 = ck
+            if i1 - i0 == 1:
                 sim.restore(self.pool[slot0], t0)
-                if j > i0:
-                    sim.step(j - i0)
-                    self.recomputed_steps += j - i0
                 sim.adjoint_step()
                 self.adjoint_steps += 1
-            return
-        m = i0 + binomial_split(i1 - i0, s)
-        if m in self.saved:
-            ckm = self.saved.pop(m)
-        else:
-            sim.restore(self.pool[slot0], t0)
-            sim.step(m - i0)
-            self.recomputed_steps += m - i0
-            slot = self.free.pop()
-            ckm = (slot, sim.save(self.pool[slot]))
-        self._rev(m, i1, ckm, s - 1)
-        self.free.append(ckm[0])
-        self._rev(i0, m, ck, s)
+                continue
+            if s == 0:
+                for j in range(i1 - 1, i0 - 1, -1):
+                    sim.restore(self.pool[slot0], t0)
+                    if j > i0:
+                        sim.step(j - i0)
+                        self.recomputed_steps += j - i0
+                    sim.adjoint_step()
+                    self.adjoint_steps += 1
+                continue
+            m = i0 + binomial_split(i1 - i0, s)
+            if m in self.saved:
+                ckm = self.saved.pop(m)
+            else:
+                sim.restore(self.pool[slot0], t0)
+                sim.step(m - i0)
+                self.recomputed_steps += m - i0
+                slot = self.free.pop()
+                ckm = (slot, sim.save(self.pool[slot]))
+            stack.append(("rev", i0, m, ck, s))
+            stack.append(("free", ckm[0]))
+            stack.append(("rev", m, i1, ckm, s - 1))
 
 
 class DrivenRun(torch.autograd.Function):
