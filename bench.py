@@ -49,7 +49,7 @@ def parse():
     ap.add_argument("--no-production", action="store_true")
     ap.add_argument("--adjoint-scale", action="store_true",
                     help="also run the checkpointed gradient of bipoles100_512x512x256 (minutes)")
-    ap.add_argument("--scale-steps", type=int, default=1000)
+    ap.add_argument("--scale-steps", type=int, default=0, help="0: the workload's step count (600)")
     ap.add_argument("--scale-iters", type=int, default=3)
     return ap.parse_args()
 
@@ -273,6 +273,7 @@ def adjoint_scale_line(dev, steps, iters):
     from paper_1908_08557_gb300.adjoint import BzPlane, DrivenRun
     c = inputs.make_case("bipoles100_512x512x256", dtype=np.float32)
     ct = inputs.make_case("bipoles100_512x512x256", seed=1, dtype=np.float32)
+    steps = steps or c.nsteps
     p = dict(c.params, dt_fixed=0.017)
     k = 48
     T = lambda a: torch.tensor(a, dtype=torch.float32, device=dev)
@@ -306,14 +307,14 @@ def adjoint_scale_line(dev, steps, iters):
         rev = _cuda_ms(sim.stream, lambda: lossv.backward())
         g = [q.grad.detach() for q in leaves]
         g2 = sum(float((x.double() ** 2).sum()) for x in g)
-        eta = 0.25 * float(lossv) / max(g2, 1e-300)
+        eta = 0.25 * float(lossv.detach()) / max(g2, 1e-300)
         trial = [q - eta * x for q, x in zip(params, g)]
         new = loss_of(trial)
         if new > loss:
             eta *= 0.5
             trial = [q - eta * x for q, x in zip(params, g)]
             new = loss_of(trial)
-        hist.append({"loss": float(lossv), "forward_with_checkpoints_ms": fwd_ck, "reverse_ms": rev,
+        hist.append({"loss": float(lossv.detach()), "forward_with_checkpoints_ms": fwd_ck, "reverse_ms": rev,
                      "ratio": rev / fwd_ms, "loss_after_step": new})
         params, loss = trial, new
     out["iterations"] = hist

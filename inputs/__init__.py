@@ -259,12 +259,13 @@ class Case:
 
 def make_box(nx, ny, nz, seed=0, magnetogram="spots", n_mag=4, sigma=3.0,
              driver="noise", driver_rms=0.01, dx=1.0, dy=1.0, dz=1.0,
-             nsteps=50, name=None, ar_pair=None, t1=1.0, dtype=np.float64, **over) -> Case:
+             nsteps=50, name=None, ar_pair=None, t1=1.0, dtype=np.float64, bz_scale=1.0, **over) -> Case:
     p = scheme_params(nx, ny, nz, dx, dy, dz, **over)
     if magnetogram == "spots":
         bz = magnetogram_spots(nx, ny, n_mag, sigma, seed)
     else:
         bz = magnetogram_bipoles(nx, ny, n_mag, seed, sigma=sigma, ar_pair=ar_pair)
+    bz = bz * bz_scale
     if driver == "noise":
         v0 = driver_smoothed_noise(nx, ny, 2.0, driver_rms, seed)
         v1 = driver_smoothed_noise(nx, ny, 2.0, driver_rms, seed + 1)
@@ -293,8 +294,12 @@ WORKLOADS = {
                              nsteps=1000),
     "bipoles8_64x64x64": dict(nx=64, ny=64, nz=64, magnetogram="bipoles",
                               n_mag=8, driver="noise", nsteps=100),
+    # a third of the flux unit: with the full unit the strongest of the 100
+    # log-normal poles (|B_z| = 4.7, photospheric beta 0.09) drives grid-scale
+    # growth within 200 steps; at a third the box stays finite for ~800 steps
+    # (then the same growth sets in), so gradients use 600 steps
     "bipoles100_512x512x256": dict(nx=512, ny=512, nz=256, magnetogram="bipoles",
-                                   n_mag=100, driver="solenoidal", nsteps=1000),
+                                   n_mag=100, driver="solenoidal", nsteps=600, bz_scale=1.0 / 3.0),
     # the 256^3 recipe at an eighth of the volume: profiler captures of the
     # adjoint kernels (coefficient fields 0.34 GB, above the 129 MB L2)
     "bipoles20_128x128x128": dict(nx=128, ny=128, nz=128, magnetogram="bipoles",
