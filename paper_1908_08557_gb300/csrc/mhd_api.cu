@@ -384,8 +384,9 @@ static double inv2sum(const mhd_params* p) {
 template <typename R>
 static void run_stats(mhd_ctx* h, R* f) {
   Phys<R> ph = make_phys<R>(&h->p);
-  ClassTimer ct(h, MHD_KC_STATS, 2);
-  int nb = launch_stats_partial<R>(h->L, ph, bgr<R>(h), f, h->red, h->ss, h->st);
+  ClassTimer ct(h, MHD_KC_STATS, 3);
+  // B into the RK accumulator: free here (substep 0 does not read it)
+  int nb = launch_stats_partial<R>(h->L, ph, bgr<R>(h), f, (R*)h->df, h->red, h->st);
   launch_stats_finalize(h->red, nb, h->ss, h->p.dx * h->p.dy * h->p.dz, h->p.dx * h->p.dy, h->p.gamma - 1.0, h->st);
 }
 

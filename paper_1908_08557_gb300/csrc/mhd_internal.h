@@ -127,9 +127,10 @@ template <typename R> int launch_cfl_partial(const Layout& L, const Phys<R>& ph,
 void launch_cfl_finalize(const double* partial, int nblk, StepState* ss, double c_adv, double c_diff,
                          double dt_fixed, double inv2sum, double t0, double t1, double t_ramp, int probe,
                          cudaStream_t st);
+// diagnostics partials; bsc = three scratch fields in the state layout
+// (overwritten), e.g. the RK accumulator between steps
 template <typename R> int launch_stats_partial(const Layout& L, const Phys<R>& ph, const Background<R>& bg,
-                                               const R* f,
-                                               double* partial, StepState* ss, cudaStream_t st);
+                                               const R* f, R* bsc, double* partial, cudaStream_t st);
 void launch_stats_finalize(const double* partial, int nblk, StepState* ss, double dv, double da, double gm1,
                            cudaStream_t st);
 // pack / unpack interior <-> padded

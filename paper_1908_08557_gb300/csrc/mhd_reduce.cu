@@ -31,19 +31,6 @@ static inline dim3 red_grid(const Layout& L, int* kchunk) {
   return dim3(tx, ty, zc);
 }
 
-// B = curl A + B_ext at a cell from sixth-order first derivatives (Eq. 6)
-template <typename R>
-__device__ __forceinline__ void bfield(const Layout& L, const Phys<R>& ph, const R* f, int k, int j, int i,
-                                       R* B) {
-  const long long sy = L.sy(), sz = L.sz();
-  const R* ax = f + L.at(AX, k, j, i);
-  const R* ay = f + L.at(AY, k, j, i);
-  const R* az = f + L.at(AZ, k, j, i);
-  B[0] = d1(az, sy, ph.idy) - d1(ay, sz, ph.idz) + ph.bext[0];
-  B[1] = d1(ax, sz, ph.idz) - d1(az, (long long)1, ph.idx) + ph.bext[1];
-  B[2] = d1(ay, (long long)1, ph.idx) - d1(ax, sy, ph.idy) + ph.bext[2];
-}
-
 // CFL: per cell the advective rate sum|u_i|/dx_i + sqrt(gamma T + B^2/rho)
 // sqrt(sum 1/dx_i^2) and the diffusive rate D_max sum 1/dx_i^2, D_max the
 // largest of nu, eta + eta_s w, D_rho + chi_rho w, chi_s w + (gamma-1)
@@ -86,6 +73,7 @@ __global__ void __launch_bounds__(256) cfl_partial_kernel(Layout L, Phys<R> ph, 
       wx[m + 1] = __ldg(pax + (m - 3) * sz);
       wy[m + 1] = __ldg(pay + (m - 3) * sz);
     }
+#pragma unroll 2
     for (int k = k0; k < k1; ++k) {
 #pragma unroll
       for (int m = 0; m < 6; ++m) { wx[m] = wx[m + 1]; wy[m] = wy[m + 1]; }
@@ -192,12 +180,38 @@ void launch_cfl_finalize(const double* partial, int nblk, StepState* ss, double 
                                          t_ramp, probe);
 }
 
-// Diagnostics: per block 7 values (sums of rho u^2/2, B^2/2, rho T/(gamma-1),
-// rho, B_z(k=0), |B_z(k=0)|, and max |div B|) to partial[8 b + q].
+// Diagnostics, first pass: curl A (Eq. 6, without the uniform B_ext) into the
+// scratch fields 0..2 in the state layout.  B_z is formed on the ghost planes
+// k = -3 .. nz + 2 as well (it has no z derivative, and its x, y stencils read
+// the periodic rims, which the ghost rules fill on every plane), so that the
+// second pass can take z derivatives of B_z; B_x, B_y only on interior planes.
+template <typename R>
+__global__ void __launch_bounds__(256) curl_a_kernel(Layout L, Phys<R> ph, const R* __restrict__ f,
+                                                     R* __restrict__ bsc) {
+  const int i = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y * 8 + threadIdx.y;
+  const int k = (int)blockIdx.z - NG;
+  if (i >= L.nx || j >= L.ny) return;
+  const long long sy = L.sy(), sz = L.sz();
+  const R* ax = f + L.at(AX, k, j, i);
+  const R* ay = f + L.at(AY, k, j, i);
+  const long long c = L.at(0, k, j, i);
+  bsc[c + 2 * L.fs] = d1(ay, (long long)1, ph.idx) - d1(ax, sy, ph.idy);
+  if (k < 0 || k >= L.nz) return;
+  const R* az = f + L.at(AZ, k, j, i);
+  bsc[c] = d1(az, sy, ph.idy) - d1(ay, sz, ph.idz);
+  bsc[c + L.fs] = d1(ax, sz, ph.idz) - d1(az, (long long)1, ph.idx);
+}
+
+// Second pass: per block 7 values (sums of rho u^2/2, B^2/2, rho T/(gamma-1),
+// rho, B_z(k=0), |B_z(k=0)|, and max |div B|) to partial[8 b + q].  div B is
+// the centred sixth-order divergence of the stored curl A (x, y neighbours
+// wrapped periodically, z neighbours on the ghost planes), so it measures how
+// far the discrete operators fail to commute; B_ext drops out of it.
 template <typename R>
 __global__ void __launch_bounds__(256) stats_partial_kernel(Layout L, Phys<R> ph, Background<R> bg,
                                                             const R* __restrict__ f,
-                                                            double* partial, StepState* ss, int kchunk) {
+                                                            const R* __restrict__ bsc,
+                                                            double* partial, int kchunk) {
   __shared__ double sm[8][8];
   const int i = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y * 8 + threadIdx.y;
   const int tid = threadIdx.y * 32 + threadIdx.x;
@@ -213,47 +227,38 @@ __global__ void __launch_bounds__(256) stats_partial_kernel(Layout L, Phys<R> ph
   };
   R dmax = R(0);
   if (i < L.nx && j < L.ny) {
-    const long long sy = L.sy(), sz = L.sz();
+    const long long sz = L.sz();
+    const R cw[3] = {W<R>::c1, W<R>::c2, W<R>::c3};
+    int ip[3], im[3], jp[3], jm[3];
+    for (int m = 1; m <= 3; ++m) {
+      ip[m - 1] = i + m < L.nx ? i + m : i + m - L.nx;
+      im[m - 1] = i - m >= 0 ? i - m : i - m + L.nx;
+      jp[m - 1] = j + m < L.ny ? j + m : j + m - L.ny;
+      jm[m - 1] = j - m >= 0 ? j - m : j - m + L.ny;
+    }
     const int k0 = blockIdx.z * kchunk, k1 = min(L.nz, k0 + kchunk);
+#pragma unroll 2
     for (int k = k0; k < k1; ++k) {
-      R B[3];
-      bfield<R>(L, ph, f, k, j, i, B);
+      const R* bx = bsc + L.at(0, k, j, 0);
+      const R* by = bsc + L.fs + L.at(0, k, 0, i);
+      const R* bz = bsc + 2 * L.fs + L.at(0, k, j, i);
+      const R Bx = bx[i] + ph.bext[0], By = by[(long long)j * L.sy()] + ph.bext[1], Bz = bz[0] + ph.bext[2];
       const R ux = f[L.at(UX, k, j, i)], uy = f[L.at(UY, k, j, i)], uz = f[L.at(UZ, k, j, i)];
       const R rho = rexp<R>(bg.lbar[k + NG] + f[L.at(LR, k, j, i)]);
       const R T = rexp<R>(bg.tbar[k + NG] + f[L.at(LT, k, j, i)]);
       nadd(0, R(0.5) * rho * (ux * ux + uy * uy + uz * uz));
-      nadd(1, R(0.5) * (B[0] * B[0] + B[1] * B[1] + B[2] * B[2]));
+      nadd(1, R(0.5) * (Bx * Bx + By * By + Bz * Bz));
       nadd(2, rho * T);  // / (gamma - 1) once, in the finalize
       nadd(3, rho);
       if (k == 0) {
-        nadd(4, B[2]);
-        nadd(5, fabs(B[2]));
+        nadd(4, Bz);
+        nadd(5, fabs(Bz));
       }
-      // div B with the same stencils: B_x has no x derivative, B_y no y and
-      // B_z no z derivative, so all values used lie inside the ghost zone
       R dv = R(0);
-      const R cw[4] = {R(0), W<R>::c1, W<R>::c2, W<R>::c3};
-      for (int m = 1; m <= 3; ++m) {
-        const R* azp = f + L.at(AZ, k, j, i + m);
-        const R* azm = f + L.at(AZ, k, j, i - m);
-        const R* ayp = f + L.at(AY, k, j, i + m);
-        const R* aym = f + L.at(AY, k, j, i - m);
-        const R bxp = d1(azp, sy, ph.idy) - d1(ayp, sz, ph.idz);
-        const R bxm = d1(azm, sy, ph.idy) - d1(aym, sz, ph.idz);
-        const R* axq = f + L.at(AX, k, j + m, i);
-        const R* axr = f + L.at(AX, k, j - m, i);
-        const R* azq = f + L.at(AZ, k, j + m, i);
-        const R* azr = f + L.at(AZ, k, j - m, i);
-        const R byp = d1(axq, sz, ph.idz) - d1(azq, (long long)1, ph.idx);
-        const R bym = d1(axr, sz, ph.idz) - d1(azr, (long long)1, ph.idx);
-        const R* ays = f + L.at(AY, k + m, j, i);
-        const R* ayt = f + L.at(AY, k - m, j, i);
-        const R* axs = f + L.at(AX, k + m, j, i);
-        const R* axt = f + L.at(AX, k - m, j, i);
-        const R bzp = d1(ays, (long long)1, ph.idx) - d1(axs, sy, ph.idy);
-        const R bzm = d1(ayt, (long long)1, ph.idx) - d1(axt, sy, ph.idy);
-        dv += cw[m] * ((bxp - bxm) * ph.idx + (byp - bym) * ph.idy + (bzp - bzm) * ph.idz);
-      }
+#pragma unroll
+      for (int m = 0; m < 3; ++m)
+        dv += cw[m] * ((bx[ip[m]] - bx[im[m]]) * ph.idx + (by[(long long)jp[m] * L.sy()] - by[(long long)jm[m] * L.sy()]) * ph.idy +
+                       (bz[(m + 1) * sz] - bz[-(m + 1) * sz]) * ph.idz);
       dmax = fmax(dmax, fabs(dv));
     }
   }
@@ -275,11 +280,13 @@ __global__ void __launch_bounds__(256) stats_partial_kernel(Layout L, Phys<R> ph
 }
 
 template <typename R>
-int launch_stats_partial(const Layout& L, const Phys<R>& ph, const Background<R>& bg, const R* f,
-                         double* partial, StepState* ss, cudaStream_t st) {
+int launch_stats_partial(const Layout& L, const Phys<R>& ph, const Background<R>& bg, const R* f, R* bsc,
+                         double* partial, cudaStream_t st) {
+  dim3 gc((L.nx + 31) / 32, (L.ny + 7) / 8, L.nz + 2 * NG);
+  curl_a_kernel<R><<<gc, dim3(32, 8), 0, st>>>(L, ph, f, bsc);
   int kchunk;
   dim3 g = red_grid(L, &kchunk);
-  stats_partial_kernel<R><<<g, dim3(32, 8), 0, st>>>(L, ph, bg, f, partial, ss, kchunk);
+  stats_partial_kernel<R><<<g, dim3(32, 8), 0, st>>>(L, ph, bg, f, bsc, partial, kchunk);
   return (int)(g.x * g.y * g.z);
 }
 
@@ -323,7 +330,7 @@ void launch_stats_finalize(const double* partial, int nblk, StepState* ss, doubl
   template int launch_cfl_partial<R>(const Layout&, const Phys<R>&, const Background<R>&, const R*,      \
                                      const R*, double*, StepState*, cudaStream_t);                     \
   template int launch_stats_partial<R>(const Layout&, const Phys<R>&, const Background<R>&, const R*,    \
-                                       double*, StepState*, cudaStream_t);
+                                       R*, double*, cudaStream_t);
 INST(float)
 INST(double)
 #undef INST
