@@ -33,6 +33,9 @@ struct mhd_ctx {
   mhd_params p;
   Layout L;
   cudaStream_t st;
+  cudaStream_t side;   // highest-priority stream for the potential-field FFT of substep 0,
+                       // forked from and joined to `st` by events (FFT boundary only)
+  cudaEvent_t evf, evj;
   size_t esz;          // bytes per state element
   char* ws;
   size_t ws_bytes;
@@ -48,6 +51,7 @@ struct mhd_ctx {
   void* v0;            // [2][ny][nx]
   void* v1;
   double* red;         // reduction partials
+  double* cfl;         // CFL maxima slots [2 * CFL_SLOTS] (after the partials)
   StepState* ss;
   void* bgtab;         // background tables: lbar, tbar [nz+6]; dl, d2l, dt, d2t [nz]
   // adjoint buffers (params.adjoint)
@@ -75,19 +79,20 @@ struct mhd_ctx {
 struct ClassTimer {
   mhd_ctx* h;
   mhd_ctx::Ev ev;
-  ClassTimer(mhd_ctx* h_, int cls, int nk) : h(h_) {
+  cudaStream_t st;
+  ClassTimer(mhd_ctx* h_, int cls, int nk, cudaStream_t s = nullptr) : h(h_), st(s ? s : h_->st) {
     h->nlaunch += nk;
     ev.cls = cls;
     ev.nk = nk;
     if (h->prof) {
       cudaEventCreate(&ev.a);
       cudaEventCreate(&ev.b);
-      cudaEventRecord(ev.a, h->st);
+      cudaEventRecord(ev.a, st);
     }
   }
   ~ClassTimer() {
     if (h->prof) {
-      cudaEventRecord(ev.b, h->st);
+      cudaEventRecord(ev.b, st);
       h->evs->push_back(ev);
     }
   }
@@ -194,7 +199,7 @@ static Offsets plan_offsets(const mhd_params* p) {
   o.ayt = c.take(n2 * es);
   o.v0 = c.take(2 * n2 * es);
   o.v1 = c.take(2 * n2 * es);
-  o.red = c.take((size_t)RED_BLOCKS_MAX * 8 * sizeof(double));
+  o.red = c.take(((size_t)RED_BLOCKS_MAX * 8 + 2 * CFL_SLOTS) * sizeof(double));
   o.ss = c.take(sizeof(StepState));
   o.bg = c.take((size_t)(6 * p->nz + 12) * es);
   if (p->precision == 32) {
@@ -377,6 +382,15 @@ static void ghost_fill(mhd_ctx* h, R* f) {
   }
 }
 
+static void release_side(mhd_ctx* h) {
+  if (h->side) cudaStreamSynchronize(h->side);
+  if (h->evf) cudaEventDestroy(h->evf);
+  if (h->evj) cudaEventDestroy(h->evj);
+  if (h->side) cudaStreamDestroy(h->side);
+  h->evf = h->evj = nullptr;
+  h->side = nullptr;
+}
+
 static double inv2sum(const mhd_params* p) {
   return 1.0 / (p->dx * p->dx) + 1.0 / (p->dy * p->dy) + 1.0 / (p->dz * p->dz);
 }
@@ -427,15 +441,49 @@ static void run_step(mhd_ctx* h, bool stats) {
   for (int sub = 0; sub < 3; ++sub) {
     R* fin = (R*)h->f[h->cur];
     R* fout = (R*)h->f[1 - h->cur];
-    ghost_fill<R>(h, fin);
-    if (sub == 0) {
+    const bool adaptive = !(h->p.dt_fixed > 0.0);
+    if (sub == 0 && adaptive && h->side && h->L.nz > 2 * NG) {
+      // The FFT of the potential-field ghosts (FP64-pipe bound) runs on the
+      // side stream while the ghost rules and the CFL reduction over the
+      // inner layers (whose stencils read no ghost plane) run here; the
+      // three layers at each end follow once the FFT has joined.  Neither
+      // side writes what the other reads: the FFT writes only the A ghost
+      // planes, the ghost rules only those of u, ln rho, ln T.
+      cudaEventRecord(h->evf, h->st);
+      cudaStreamWaitEvent(h->side, h->evf, 0);
+      {
+        ClassTimer ct(h, MHD_KC_PFE, 3, h->side);
+        launch_pfe<R>(h->fp, h->L, fin, h->ss, h->side);
+      }
+      cudaEventRecord(h->evj, h->side);
+      {
+        ClassTimer ct(h, MHD_KC_GHOST, 1);
+        launch_bc<R>(h->L, ph, bgr<R>(h), fin, (R)h->p.dz, h->ss, h->st);
+      }
+      {
+        ClassTimer ct(h, MHD_KC_CFL, 1);
+        launch_cfl_partial<R>(h->L, ph, bgr<R>(h), fin, (const R*)h->wtab, h->cfl, h->ss, CflPlanes::inner, true,
+                              h->st);
+      }
+      cudaStreamWaitEvent(h->st, h->evj, 0);
       if (stats) run_stats<R>(h, fin);
-      const bool adaptive = !(h->p.dt_fixed > 0.0);
-      ClassTimer ct(h, MHD_KC_CFL, adaptive ? 2 : 1);
-      int nb = 0;
-      if (adaptive) nb = launch_cfl_partial<R>(h->L, ph, bgr<R>(h), fin, (const R*)h->wtab, h->red, h->ss, h->st);
-      launch_cfl_finalize(h->red, nb, h->ss, h->p.c_adv, h->p.c_diff, h->p.dt_fixed, inv2sum(&h->p), h->t0,
+      ClassTimer ct(h, MHD_KC_CFL, 2);
+      int nb = launch_cfl_partial<R>(h->L, ph, bgr<R>(h), fin, (const R*)h->wtab, h->cfl, h->ss, CflPlanes::ends,
+                                     false, h->st);
+      launch_cfl_finalize(h->cfl, nb, h->ss, h->p.c_adv, h->p.c_diff, h->p.dt_fixed, inv2sum(&h->p), h->t0,
                           h->t1, h->p.t_ramp, 0, h->st);
+    } else {
+      ghost_fill<R>(h, fin);
+      if (sub == 0) {
+        if (stats) run_stats<R>(h, fin);
+        ClassTimer ct(h, MHD_KC_CFL, adaptive ? 2 : 1);
+        int nb = 0;
+        if (adaptive)
+          nb = launch_cfl_partial<R>(h->L, ph, bgr<R>(h), fin, (const R*)h->wtab, h->cfl, h->ss, CflPlanes::all,
+                                     true, h->st);
+        launch_cfl_finalize(h->cfl, nb, h->ss, h->p.c_adv, h->p.c_diff, h->p.dt_fixed, inv2sum(&h->p), h->t0,
+                            h->t1, h->p.t_ramp, 0, h->st);
+      }
     }
     {
       ClassTimer ct(h, MHD_KC_RK, 1);
@@ -548,6 +596,7 @@ extern "C" int mhd_create(const mhd_params* p, void* workspace, size_t ws_bytes,
   h->v0 = h->ws + o.v0;
   h->v1 = h->ws + o.v1;
   h->red = (double*)(h->ws + o.red);
+  h->cfl = h->red + (size_t)RED_BLOCKS_MAX * 8;
   h->ss = (StepState*)(h->ws + o.ss);
   h->bgtab = h->ws + o.bg;
   h->bj = h->ws + o.bj;
@@ -599,6 +648,13 @@ extern "C" int mhd_create(const mhd_params* p, void* workspace, size_t ws_bytes,
                                             cudaMemcpyHostToDevice), "upload wp");
   }
   if (!rc && h->have_fft) rc = upload_fft_tables(h, o);
+  if (!rc && h->have_fft) {
+    int lo = 0, hi = 0;
+    cudaDeviceGetStreamPriorityRange(&lo, &hi);
+    rc = cuda_check(h, cudaStreamCreateWithPriority(&h->side, cudaStreamNonBlocking, hi), "side stream");
+    if (!rc) rc = cuda_check(h, cudaEventCreateWithFlags(&h->evf, cudaEventDisableTiming), "fork event");
+    if (!rc) rc = cuda_check(h, cudaEventCreateWithFlags(&h->evj, cudaEventDisableTiming), "join event");
+  }
   if (!rc && h->tiled) {
     for (int s = 0; s < 2 && !rc; ++s)
       if (make_state_tensor_map(&h->tm[s], h->L, h->f[s]) != 0)
@@ -645,6 +701,7 @@ extern "C" int mhd_create(const mhd_params* p, void* workspace, size_t ws_bytes,
   if (!rc) rc = cuda_check(h, cudaStreamSynchronize(h->st), "create synchronize");
   if (rc) {
     snprintf(g_err, sizeof g_err, "%s", h->err);
+    release_side(h);
     free(h);
     return rc;
   }
@@ -796,14 +853,14 @@ extern "C" int mhd_compute_dt(mhd_handle h, double* dt) {
   int nb;
   if (h->esz == 8) {
     Phys<double> ph = make_phys<double>(&h->p);
-    nb = launch_cfl_partial<double>(h->L, ph, h->bgd, (const double*)h->f[h->cur], (const double*)h->wtab, h->red,
-                                    h->ss, h->st);
+    nb = launch_cfl_partial<double>(h->L, ph, h->bgd, (const double*)h->f[h->cur], (const double*)h->wtab, h->cfl,
+                                    h->ss, CflPlanes::all, true, h->st);
   } else {
     Phys<float> ph = make_phys<float>(&h->p);
-    nb = launch_cfl_partial<float>(h->L, ph, h->bgf, (const float*)h->f[h->cur], (const float*)h->wtab, h->red,
-                                   h->ss, h->st);
+    nb = launch_cfl_partial<float>(h->L, ph, h->bgf, (const float*)h->f[h->cur], (const float*)h->wtab, h->cfl,
+                                   h->ss, CflPlanes::all, true, h->st);
   }
-  launch_cfl_finalize(h->red, nb, h->ss, h->p.c_adv, h->p.c_diff, 0.0, inv2sum(&h->p), h->t0, h->t1,
+  launch_cfl_finalize(h->cfl, nb, h->ss, h->p.c_adv, h->p.c_diff, 0.0, inv2sum(&h->p), h->t0, h->t1,
                       h->p.t_ramp, 1, h->st);
   int rc = sync_status(h);
   if (rc) return rc;
@@ -951,7 +1008,7 @@ static void adjoint_step_impl(mhd_ctx* h) {
   R* S[3] = {(R*)h->f[h->cur], (R*)h->f[1 - h->cur], (R*)h->s2};
   // forward recompute of the substep states (ghost-filled)
   ghost_fill<R>(h, S[0]);
-  launch_cfl_finalize(h->red, 0, h->ss, h->p.c_adv, h->p.c_diff, h->p.dt_fixed, inv2sum(&h->p), h->t0, h->t1,
+  launch_cfl_finalize(h->cfl, 0, h->ss, h->p.c_adv, h->p.c_diff, h->p.dt_fixed, inv2sum(&h->p), h->t0, h->t1,
                       h->p.t_ramp, 0, h->st);
   launch_rk_any<R>(h, S[0], S[1], 0);
   ghost_fill<R>(h, S[1]);
@@ -1112,6 +1169,7 @@ extern "C" long long mhd_launch_count(mhd_handle h) { return h ? h->nlaunch : 0;
 extern "C" void mhd_destroy(mhd_handle h) {
   if (!h) return;
   cudaStreamSynchronize(h->st);
+  release_side(h);
   drop_events(h);
   delete h->evs;
   free(h);

@@ -31,6 +31,7 @@ void set_global_error(const char* fmt, ...);
 
 constexpr int FFT_PTS = 2048;          // complex points per shared buffer
 constexpr int RED_BLOCKS_MAX = 4096;   // partial-reduction slots
+constexpr int CFL_SLOTS = 256;         // CFL maxima slot pairs (after the partials)
 
 // ghost fill
 template <typename R> void launch_rims(const Layout& L, R* f, int k0, int k1, cudaStream_t st);
@@ -121,9 +122,14 @@ template <typename R> void launch_pfe_adjoint(const FFTPlan& fp_adj, const Layou
 template <typename R> void launch_atarget_adjoint(const FFTPlan& fp, const double* abx, const double* aby, R* out,
                                                   cudaStream_t st);
 // reductions
+// CFL block maxima by atomicMax into CFL_SLOTS slot pairs at `partial`
+// (zeroed first when `zero`); the planes: all, the inner ones whose stencils
+// read no ghost plane (k = 3 .. nz - 4), or the three at each end.  Returns
+// the slot count for launch_cfl_finalize.
+enum class CflPlanes { all, inner, ends };
 template <typename R> int launch_cfl_partial(const Layout& L, const Phys<R>& ph, const Background<R>& bg,
-                                             const R* f, const R* wtab,
-                                             double* partial, StepState* ss, cudaStream_t st);
+                                             const R* f, const R* wtab, double* partial, StepState* ss,
+                                             CflPlanes planes, bool zero, cudaStream_t st);
 void launch_cfl_finalize(const double* partial, int nblk, StepState* ss, double c_adv, double c_diff,
                          double dt_fixed, double inv2sum, double t0, double t1, double t_ramp, int probe,
                          cudaStream_t st);

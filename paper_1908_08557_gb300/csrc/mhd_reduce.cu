@@ -41,69 +41,50 @@ __device__ __forceinline__ R d1s(const R* __restrict__ p, int s, R inv) {
           W<R>::c3 * (__ldg(p + 3 * s) - __ldg(p - 3 * s))) * inv;
 }
 
+// One thread per cell, all of a cell's loads in flight at once.  Planes
+// k0 .. k0 + nlo - 1, then (blockIdx.z >= nlo) shifted by kgap, so one launch
+// can cover the three layers at each end.  Block maxima go by atomicMax on
+// the bit patterns (non-negative IEEE doubles order like their bits read as
+// unsigned integers, so the result does not depend on the order of the
+// blocks) into one of CFL_SLOTS slot pairs, zeroed beforehand.
 template <typename R>
 __global__ void __launch_bounds__(256) cfl_partial_kernel(Layout L, Phys<R> ph, Background<R> bg,
-                                                          const R* __restrict__ f,
-                                                          const R* __restrict__ wtab, double* partial,
-                                                          StepState* ss, int kchunk, R sqinv2) {
+                                                          const R* __restrict__ f, const R* __restrict__ wtab,
+                                                          double* partial, StepState* ss, R sqinv2, int k0, int nlo,
+                                                          int kgap) {
   __shared__ R sa[8], sd[8];
   const int i = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y * 8 + threadIdx.y;
+  const int k = k0 + (int)blockIdx.z + ((int)blockIdx.z >= nlo ? kgap : 0);
   const int tid = threadIdx.y * 32 + threadIdx.x;
-  // per-thread maxima in the state precision (conversion to FP64 is exact and
-  // monotonic, so converting the maximum equals the maximum of conversions)
+  if (halted(ss)) return;
+  // maxima in the state precision (conversion to FP64 is exact and monotonic,
+  // so converting the maximum equals the maximum of conversions)
   R mar = R(0), mdr = R(0);
-  bool bad = false;
-  if (i < L.nx && j < L.ny && !halted(ss)) {
-    const int k0 = blockIdx.z * kchunk, k1 = min(L.nz, k0 + kchunk);
+  if (i < L.nx && j < L.ny) {
     const int sy = L.mx;
-    const long long sz = L.sz();
-    // column pointers at (k0, j, i); the z derivatives of A_x, A_y come from
-    // a register window over k - 3 .. k + 3
-    const R* pax = f + L.at(AX, k0, j, i);
-    const R* pay = f + L.at(AY, k0, j, i);
-    const R* paz = f + L.at(AZ, k0, j, i);
-    const R* pux = f + L.at(UX, k0, j, i);
-    const R* puy = f + L.at(UY, k0, j, i);
-    const R* puz = f + L.at(UZ, k0, j, i);
-    const R* plr = f + L.at(LR, k0, j, i);
-    const R* plt = f + L.at(LT, k0, j, i);
-    R wx[7], wy[7];
-#pragma unroll
-    for (int m = 0; m < 6; ++m) {
-      wx[m + 1] = __ldg(pax + (m - 3) * sz);
-      wy[m + 1] = __ldg(pay + (m - 3) * sz);
-    }
-#pragma unroll 2
-    for (int k = k0; k < k1; ++k) {
-#pragma unroll
-      for (int m = 0; m < 6; ++m) { wx[m] = wx[m + 1]; wy[m] = wy[m + 1]; }
-      wx[6] = __ldg(pax + 3 * sz);
-      wy[6] = __ldg(pay + 3 * sz);
-      const R dzax = (W<R>::c1 * (wx[4] - wx[2]) + W<R>::c2 * (wx[5] - wx[1]) + W<R>::c3 * (wx[6] - wx[0])) * ph.idz;
-      const R dzay = (W<R>::c1 * (wy[4] - wy[2]) + W<R>::c2 * (wy[5] - wy[1]) + W<R>::c3 * (wy[6] - wy[0])) * ph.idz;
-      // B = curl A + B_ext (Eq. 6)
-      const R B0 = d1s(paz, sy, ph.idy) - dzay + ph.bext[0];
-      const R B1 = dzax - d1s(paz, 1, ph.idx) + ph.bext[1];
-      const R B2 = d1s(pay, 1, ph.idx) - d1s(pax, sy, ph.idy) + ph.bext[2];
-      const R ux = __ldg(pux), uy = __ldg(puy), uz = __ldg(puz);
-      const R lr = bg.lbar[k + NG] + __ldg(plr), lt = bg.tbar[k + NG] + __ldg(plt);
-      const R T = rexp<R>(lt), rho1 = rexp<R>(-lr);
-      const R B2s = B0 * B0 + B1 * B1 + B2 * B2;
-      const R adv = fabs(ux) * ph.idx + fabs(uy) * ph.idy + fabs(uz) * ph.idz +
-                    rsqrt_<R>(ph.gamma * T + B2s * rho1) * sqinv2;
-      const R w = wtab[k];
-      R dm = ph.nu;
-      dm = fmax(dm, ph.eta + ph.eta_s * w);
-      dm = fmax(dm, ph.drho + ph.drho_s * w);
-      dm = fmax(dm, ph.chi_s * w + ph.gm1 * ph.kappa0 * rexp<R>(R(2.5) * lt - lr));
-      if (!isfinite(adv) || !isfinite(dm)) bad = true;
-      mar = fmax(mar, adv);
-      mdr = fmax(mdr, dm);
-      pax += sz; pay += sz; paz += sz; pux += sz; puy += sz; puz += sz; plr += sz; plt += sz;
-    }
+    const int sz = (int)L.sz();
+    const R* pax = f + L.at(AX, k, j, i);
+    const R* pay = f + L.at(AY, k, j, i);
+    const R* paz = f + L.at(AZ, k, j, i);
+    // B = curl A + B_ext (Eq. 6)
+    const R B0 = d1s(paz, sy, ph.idy) - d1s(pay, sz, ph.idz) + ph.bext[0];
+    const R B1 = d1s(pax, sz, ph.idz) - d1s(paz, 1, ph.idx) + ph.bext[1];
+    const R B2 = d1s(pay, 1, ph.idx) - d1s(pax, sy, ph.idy) + ph.bext[2];
+    const R ux = __ldg(f + L.at(UX, k, j, i)), uy = __ldg(f + L.at(UY, k, j, i)), uz = __ldg(f + L.at(UZ, k, j, i));
+    const R lr = bg.lbar[k + NG] + __ldg(f + L.at(LR, k, j, i)), lt = bg.tbar[k + NG] + __ldg(f + L.at(LT, k, j, i));
+    const R T = rexp<R>(lt), rho1 = rexp<R>(-lr);
+    const R B2s = B0 * B0 + B1 * B1 + B2 * B2;
+    const R adv = fabs(ux) * ph.idx + fabs(uy) * ph.idy + fabs(uz) * ph.idz +
+                  rsqrt_<R>(ph.gamma * T + B2s * rho1) * sqinv2;
+    const R w = wtab[k];
+    R dm = ph.nu;
+    dm = fmax(dm, ph.eta + ph.eta_s * w);
+    dm = fmax(dm, ph.drho + ph.drho_s * w);
+    dm = fmax(dm, ph.chi_s * w + ph.gm1 * ph.kappa0 * rexp<R>(R(2.5) * lt - lr));
+    if (!isfinite(adv) || !isfinite(dm)) atomicOr(&ss->nonfinite, 1);
+    mar = adv;
+    mdr = dm;
   }
-  if (bad) atomicOr(&ss->nonfinite, 1);
-  // block maxima in the state precision too (exact); FP64 from here on
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     mar = fmax(mar, __shfl_xor_sync(0xffffffffu, mar, o));
@@ -113,20 +94,31 @@ __global__ void __launch_bounds__(256) cfl_partial_kernel(Layout L, Phys<R> ph, 
   __syncthreads();
   if (tid == 0) {
     for (int w = 1; w < 8; ++w) { mar = fmax(mar, sa[w]); mdr = fmax(mdr, sd[w]); }
-    const int b = (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
-    partial[2 * b] = (double)mar;
-    partial[2 * b + 1] = (double)mdr;
+    const int b = ((blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x) & (CFL_SLOTS - 1);
+    atomicMax((unsigned long long*)&partial[2 * b], (unsigned long long)__double_as_longlong((double)mar));
+    atomicMax((unsigned long long*)&partial[2 * b + 1], (unsigned long long)__double_as_longlong((double)mdr));
   }
 }
 
 template <typename R>
 int launch_cfl_partial(const Layout& L, const Phys<R>& ph, const Background<R>& bg, const R* f, const R* wtab,
-                       double* partial, StepState* ss, cudaStream_t st) {
-  int kchunk;
-  dim3 g = red_grid(L, &kchunk);
-  R s2 = (R)sqrt((double)ph.idx2 + (double)ph.idy2 + (double)ph.idz2);
-  cfl_partial_kernel<R><<<g, dim3(32, 8), 0, st>>>(L, ph, bg, f, wtab, partial, ss, kchunk, s2);
-  return (int)(g.x * g.y * g.z);
+                       double* partial, StepState* ss, CflPlanes planes, bool zero, cudaStream_t st) {
+  if (zero) cudaMemsetAsync(partial, 0, sizeof(double) * 2 * CFL_SLOTS, st);
+  int k0 = 0, nlo = L.nz, kgap = 0;
+  if (planes == CflPlanes::inner) {
+    k0 = NG;
+    nlo = L.nz - 2 * NG;
+  } else if (planes == CflPlanes::ends) {
+    nlo = NG;
+    kgap = L.nz - 2 * NG;
+  }
+  const int nk = planes == CflPlanes::ends ? 2 * NG : nlo;
+  if (nk > 0) {
+    R s2 = (R)sqrt((double)ph.idx2 + (double)ph.idy2 + (double)ph.idz2);
+    cfl_partial_kernel<R><<<dim3((L.nx + 31) / 32, (L.ny + 7) / 8, nk), dim3(32, 8), 0, st>>>(
+        L, ph, bg, f, wtab, partial, ss, s2, k0, nlo, kgap);
+  }
+  return CFL_SLOTS;
 }
 
 // dt = min(C_adv / max adv, C_diff / max(D_max) / sum 1/dx_i^2) (or dt_fixed);
@@ -237,7 +229,6 @@ __global__ void __launch_bounds__(256) stats_partial_kernel(Layout L, Phys<R> ph
       jm[m - 1] = j - m >= 0 ? j - m : j - m + L.ny;
     }
     const int k0 = blockIdx.z * kchunk, k1 = min(L.nz, k0 + kchunk);
-#pragma unroll 2
     for (int k = k0; k < k1; ++k) {
       const R* bx = bsc + L.at(0, k, j, 0);
       const R* by = bsc + L.fs + L.at(0, k, 0, i);
@@ -328,7 +319,7 @@ void launch_stats_finalize(const double* partial, int nblk, StepState* ss, doubl
 
 #define INST(R)                                                                                        \
   template int launch_cfl_partial<R>(const Layout&, const Phys<R>&, const Background<R>&, const R*,      \
-                                     const R*, double*, StepState*, cudaStream_t);                     \
+                                     const R*, double*, StepState*, CflPlanes, bool, cudaStream_t);                     \
   template int launch_stats_partial<R>(const Layout&, const Phys<R>&, const Background<R>&, const R*,    \
                                        R*, double*, cudaStream_t);
 INST(float)
