@@ -12,7 +12,7 @@
 // is a F(k) + b conj(F(-k)), a = (M_t + M_b)/2, b = (M_t - M_b)/2, whose inverse
 // has real part = top ghost and imaginary part = bottom ghost.
 //
-// Kernels (radix-2 Stockham autosort in shared memory, FP64):
+// Kernels (radix-4 Stockham autosort in shared memory, FP64):
 //   1. rows_fwd: pack rows from the state, FFT along x, store transposed
 //   2. cols:     FFT along y, for each ghost layer j = 1..3 form the
 //                extrapolated spectrum (M_t = exp(-|k| j dz),
@@ -30,27 +30,63 @@ __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
 }
 
 // nb lines of n = 2^logn complex points in a (b is scratch of equal size).
-// Stockham radix-2: at stage p (1, 2, ..., n/2) butterfly i in [0, n/2):
-// k = i mod p, u0 = x[i], u1 = x[i + n/2] w^k with w = exp(-+2 pi i / (2p)),
-// y[2i - k] = u0 + u1, y[2i - k + p] = u0 - u1.  Returns the buffer holding
-// the (unnormalised) transform.
+// Stockham autosort, radix 4, with one radix-2 stage first when logn is odd.
+// With p the length of the sub-transforms done so far, radix-4 butterfly
+// i in [0, n/4) has k = i mod p, j = i div p; it takes x[i + m n/4]
+// (m = 0..3) times w^(m k), w = exp(-+2 pi i / (4p)), and writes their
+// 4-point DFT c_q to y[4 j p + k + q p] = y[4i - 3k + q p].  At p = 1 every
+// k is 0 and the twiddles drop out; the radix-2 stage (p = 1) writes
+// x[i] +- x[i + n/2] to y[2i], y[2i + 1].  Returns the buffer holding the
+// (unnormalised) transform.
 __device__ double2* fft_lines(double2* a, double2* b, int n, int logn, int nb, const double2* __restrict__ tw,
                               bool inverse) {
-  const int half = n >> 1;
-  const int total = nb * half;
-  for (int p = 1, s = 0; p < n; p <<= 1, ++s) {
-    const int tws = logn - 1 - s;  // twiddle index k * n / (2p) = k << tws
+  int p = 1, lp = 0;
+  if (logn & 1) {
+    const int half = n >> 1;
+    const int total = nb * half;
     for (int q = threadIdx.x; q < total; q += blockDim.x) {
       const int line = q >> (logn - 1);
       const int i = q & (half - 1);
+      const double2 u0 = a[line * n + i], u1 = a[line * n + i + half];
+      b[line * n + 2 * i] = cadd(u0, u1);
+      b[line * n + 2 * i + 1] = csub(u0, u1);
+    }
+    __syncthreads();
+    double2* t = a;
+    a = b;
+    b = t;
+    p = 2;
+    lp = 1;
+  }
+  const int quarter = n >> 2;
+  const int total = nb * quarter;
+  for (; p < n; p <<= 2, lp += 2) {
+    const int tws = logn - 2 - lp;  // twiddle index m k n / (4p) = (m k) << tws
+    for (int q = threadIdx.x; q < total; q += blockDim.x) {
+      const int line = q >> (logn - 2);
+      const int i = q & (quarter - 1);
       const int k = i & (p - 1);
-      double2 w = __ldg(tw + (k << tws));
-      if (inverse) w.y = -w.y;
-      const double2 u0 = a[line * n + i];
-      const double2 u1 = cmul(w, a[line * n + i + half]);
-      const int o = (i << 1) - k;
-      b[line * n + o] = cadd(u0, u1);
-      b[line * n + o + p] = csub(u0, u1);
+      const double2* x = a + line * n + i;
+      double2 b0 = x[0], b1 = x[quarter], b2 = x[2 * quarter], b3 = x[3 * quarter];
+      if (p > 1) {
+        double2 w1 = __ldg(tw + (k << tws)), w2 = __ldg(tw + ((2 * k) << tws)), w3 = __ldg(tw + ((3 * k) << tws));
+        if (inverse) {
+          w1.y = -w1.y;
+          w2.y = -w2.y;
+          w3.y = -w3.y;
+        }
+        b1 = cmul(w1, b1);
+        b2 = cmul(w2, b2);
+        b3 = cmul(w3, b3);
+      }
+      const double2 t0 = cadd(b0, b2), t1 = csub(b0, b2), t2 = cadd(b1, b3), t3 = csub(b1, b3);
+      // -i t3 for the forward transform, +i t3 for the inverse
+      const double2 r3 = inverse ? make_double2(-t3.y, t3.x) : make_double2(t3.y, -t3.x);
+      double2* y = b + line * n + 4 * i - 3 * k;
+      y[0] = cadd(t0, t2);
+      y[p] = cadd(t1, r3);
+      y[2 * p] = csub(t0, t2);
+      y[3 * p] = csub(t1, r3);
     }
     __syncthreads();
     double2* t = a;
