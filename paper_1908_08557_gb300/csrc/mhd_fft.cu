@@ -153,7 +153,10 @@ __global__ void __launch_bounds__(256) rows_fwd_kernel(FFTPlan fp, Layout L, con
 // 2. columns.  A block owns column pairs (kx, nx - kx); both columns of a pair
 // are needed to split the packed plane P2 (F(-k) lives in the mirror column).
 // mode 0: potential-field extrapolation, 3 layers; mode 1: magnetogram
-// inversion (Eq. 7): A^_x + i A^_y = (kt_x + i kt_y) B^_z / kt^2.
+// inversion (Eq. 7): A^_x + i A^_y = (kt_x + i kt_y) B^_z / kt^2; mode 2: its
+// transpose.  The spectra of all output layers are formed first and inverted
+// as one batch of lines, so each stage of the inverse transform has nout
+// times the butterflies between two barriers.
 __global__ void __launch_bounds__(256) cols_kernel(FFTPlan fp, int mode, const StepState* ss, int ppb) {
   extern __shared__ double2 sm[];
   if (ss && halted(ss)) return;
@@ -163,81 +166,79 @@ __global__ void __launch_bounds__(256) cols_kernel(FFTPlan fp, int mode, const S
   const int np = min(ppb, npairs - pair0);
   const int nl = 2 * np;
   const int p = blockIdx.y;
-  const int buf = 2 * ppb * ny;
-  double2* S = sm;
-  double2* Wa = sm + buf;
-  double2* Wb = sm + 2 * buf;
+  const int nout = mode == 0 ? 3 : 1;
+  const int npts = nl * ny;            // points of one layer
+  double2* A = sm;                     // nout layers of 2 ppb ny points each
+  double2* B = sm + nout * 2 * ppb * ny;
   // columns of line l: pair (l >> 1), mirror if odd
-  for (int q = threadIdx.x; q < nl * ny; q += blockDim.x) {
+  for (int q = threadIdx.x; q < npts; q += blockDim.x) {
     const int line = q / ny, y = q - line * ny;
     const int kx = pair0 + (line >> 1);
     const int col = (line & 1) ? ((nx - kx) & (nx - 1)) : kx;
-    Wa[line * ny + y] = fp.P[((long long)p * nx + col) * ny + y];
+    A[line * ny + y] = fp.P[((long long)p * nx + col) * ny + y];
   }
   __syncthreads();
-  double2* spec = fft_lines(Wa, S, ny, fp.logny, nl, fp.twy, false);
-  double2* work0 = (spec == Wa) ? S : Wa;
-  const int nout = mode == 0 ? 3 : 1;
-  for (int o = 0; o < nout; ++o) {
-    for (int q = threadIdx.x; q < nl * ny; q += blockDim.x) {
-      const int line = q / ny, ky = q - line * ny;
-      const int kx = pair0 + (line >> 1);
-      const int col = (line & 1) ? ((nx - kx) & (nx - 1)) : kx;
-      const double2 F = spec[line * ny + ky];
-      double2 G;
-      if (mode == 1) {
-        const double kxm = fp.ktx[col], kym = fp.kty[ky];
-        const double k2 = kxm * kxm + kym * kym;
-        if (k2 > 0.0) {
-          const double2 m = make_double2(kxm / k2, kym / k2);
-          G = cmul(m, F);
-        } else {
-          G = make_double2(0.0, 0.0);
-        }
-      } else if (mode == 2) {
-        // transpose of Eq. 7's inversion: with F = FFT(X + i Y) for real X,
-        // Y (the adjoints of A_x, A_y), the spectrum of the B_z adjoint is
-        // conj(m_x) X + conj(m_y) Y = [(kt_x - i kt_y) F - (kt_x + i kt_y) conj F(-k)] / (2 kt^2)
-        const double kxm = fp.ktx[col], kym = fp.kty[ky];
-        const double k2 = kxm * kxm + kym * kym;
-        if (k2 > 0.0) {
-          const double2 Fm = spec[(line ^ 1) * ny + ((ny - ky) & (ny - 1))];
-          const double2 Fc = make_double2(Fm.x, -Fm.y);
-          const double2 t1 = cmul(make_double2(kxm, -kym), F);
-          const double2 t2 = cmul(make_double2(kxm, kym), Fc);
-          G = make_double2((t1.x - t2.x) / (2.0 * k2), (t1.y - t2.y) / (2.0 * k2));
-        } else {
-          G = make_double2(0.0, 0.0);
-        }
+  double2* spec = fft_lines(A, B, ny, fp.logny, nl, fp.twy, false);
+  double2* G = (spec == A) ? B : A;  // layer o's lines at G + o npts
+  for (int q = threadIdx.x; q < nout * npts; q += blockDim.x) {
+    const int o = q / npts, qq = q - o * npts;
+    const int line = qq / ny, ky = qq - line * ny;
+    const int kx = pair0 + (line >> 1);
+    const int col = (line & 1) ? ((nx - kx) & (nx - 1)) : kx;
+    const double2 F = spec[qq];
+    double2 g;
+    if (mode == 1) {
+      const double kxm = fp.ktx[col], kym = fp.kty[ky];
+      const double k2 = kxm * kxm + kym * kym;
+      if (k2 > 0.0) {
+        const double2 m = make_double2(kxm / k2, kym / k2);
+        g = cmul(m, F);
       } else {
-        const double e_t = fp.et[(long long)col * ny + ky], e_b = fp.eb[(long long)col * ny + ky];
-        double mt = e_t, mb = e_b;
-        for (int jj = 0; jj < o; ++jj) { mt *= e_t; mb *= e_b; }
-        if (p == 0) {
-          G = make_double2(mt * F.x, mt * F.y);
-        } else if (p == 1) {
-          G = make_double2(mb * F.x, mb * F.y);
-        } else {
-          const double2 Fm = spec[(line ^ 1) * ny + ((ny - ky) & (ny - 1))];
-          const double ca = 0.5 * (mt + mb), cb = 0.5 * (mt - mb);
-          G = make_double2(ca * F.x + cb * Fm.x, ca * F.y - cb * Fm.y);
-        }
+        g = make_double2(0.0, 0.0);
       }
-      work0[line * ny + ky] = G;
+    } else if (mode == 2) {
+      // transpose of Eq. 7's inversion: with F = FFT(X + i Y) for real X,
+      // Y (the adjoints of A_x, A_y), the spectrum of the B_z adjoint is
+      // conj(m_x) X + conj(m_y) Y = [(kt_x - i kt_y) F - (kt_x + i kt_y) conj F(-k)] / (2 kt^2)
+      const double kxm = fp.ktx[col], kym = fp.kty[ky];
+      const double k2 = kxm * kxm + kym * kym;
+      if (k2 > 0.0) {
+        const double2 Fm = spec[(line ^ 1) * ny + ((ny - ky) & (ny - 1))];
+        const double2 Fc = make_double2(Fm.x, -Fm.y);
+        const double2 t1 = cmul(make_double2(kxm, -kym), F);
+        const double2 t2 = cmul(make_double2(kxm, kym), Fc);
+        g = make_double2((t1.x - t2.x) / (2.0 * k2), (t1.y - t2.y) / (2.0 * k2));
+      } else {
+        g = make_double2(0.0, 0.0);
+      }
+    } else {
+      // layer o + 1: multipliers M_t^(o+1), M_b^(o+1)
+      const double e_t = fp.et[(long long)col * ny + ky], e_b = fp.eb[(long long)col * ny + ky];
+      double mt = e_t, mb = e_b;
+      for (int jj = 0; jj < o; ++jj) { mt *= e_t; mb *= e_b; }
+      if (p == 0) {
+        g = make_double2(mt * F.x, mt * F.y);
+      } else if (p == 1) {
+        g = make_double2(mb * F.x, mb * F.y);
+      } else {
+        const double2 Fm = spec[(line ^ 1) * ny + ((ny - ky) & (ny - 1))];
+        const double ca = 0.5 * (mt + mb), cb = 0.5 * (mt - mb);
+        g = make_double2(ca * F.x + cb * Fm.x, ca * F.y - cb * Fm.y);
+      }
     }
-    __syncthreads();
-    double2* r = fft_lines(work0, Wb, ny, fp.logny, nl, fp.twy, true);
-    const int nplanes = mode == 0 ? 3 : 1;
-    for (int q = threadIdx.x; q < nl * ny; q += blockDim.x) {
-      const int line = q / ny, y = q - line * ny;
-      const int kx = pair0 + (line >> 1);
-      const bool self = (kx == 0 || 2 * kx == nx);
-      if ((line & 1) && self) continue;  // the mirror of a self-paired column
-      const int col = (line & 1) ? ((nx - kx) & (nx - 1)) : kx;
-      fp.Q[(((long long)o * nplanes + p) * nx + col) * ny + y] = r[line * ny + y];
-    }
-    __syncthreads();
-    if (r == Wb) { double2* t = Wb; Wb = work0; work0 = t; }
+    G[q] = g;
+  }
+  __syncthreads();
+  double2* r = fft_lines(G, spec == A ? A : B, ny, fp.logny, nout * nl, fp.twy, true);
+  const int nplanes = mode == 0 ? 3 : 1;
+  for (int q = threadIdx.x; q < nout * npts; q += blockDim.x) {
+    const int o = q / npts, qq = q - o * npts;
+    const int line = qq / ny, y = qq - line * ny;
+    const int kx = pair0 + (line >> 1);
+    const bool self = (kx == 0 || 2 * kx == nx);
+    if ((line & 1) && self) continue;  // the mirror of a self-paired column
+    const int col = (line & 1) ? ((nx - kx) & (nx - 1)) : kx;
+    fp.Q[(((long long)o * nplanes + p) * nx + col) * ny + y] = r[q];
   }
 }
 
@@ -366,7 +367,7 @@ static void set_smem_once() {
   cudaFuncSetAttribute(rows_fwd_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * FFT_PTS * 16);
   cudaFuncSetAttribute(rows_inv_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * FFT_PTS * 16);
   cudaFuncSetAttribute(rows_inv_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * FFT_PTS * 16);
-  cudaFuncSetAttribute(cols_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 3 * FFT_PTS * 16);
+  cudaFuncSetAttribute(cols_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 6 * FFT_PTS * 16);
   cudaFuncSetAttribute(cols_adj_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 3 * FFT_PTS * 16);
 }
 
@@ -375,7 +376,7 @@ static void set_smem_once() {
 // memory sized to the batch
 struct FFTLaunch {
   int nb, ppb;
-  size_t smem_rows, smem_cols;
+  size_t smem_rows, smem_cols, smem_cols3;  // cols: one output layer, three
 };
 
 static FFTLaunch fft_launch(const FFTPlan& fp) {
@@ -386,7 +387,8 @@ static FFTLaunch fft_launch(const FFTPlan& fp) {
   l.ppb = 256 / fp.ny;
   if (l.ppb < 1) l.ppb = 1;
   l.smem_rows = (size_t)2 * l.nb * fp.nx * sizeof(double2);
-  l.smem_cols = (size_t)3 * 2 * l.ppb * fp.ny * sizeof(double2);
+  l.smem_cols = (size_t)3 * 2 * l.ppb * fp.ny * sizeof(double2);  // also cols_adj_kernel
+  l.smem_cols3 = (size_t)6 * 2 * l.ppb * fp.ny * sizeof(double2);
   return l;
 }
 
@@ -397,7 +399,7 @@ void launch_pfe(const FFTPlan& fp, const Layout& L, R* f, const StepState* ss, c
   const int npairs = fp.nx / 2 + 1;
   rows_fwd_kernel<R><<<dim3(fp.ny / l.nb, 3), 256, l.smem_rows, st>>>(fp, L, f, nullptr, 0, ss, l.nb, nullptr,
                                                                        nullptr);
-  cols_kernel<<<dim3((npairs + l.ppb - 1) / l.ppb, 3), 256, l.smem_cols, st>>>(fp, 0, ss, l.ppb);
+  cols_kernel<<<dim3((npairs + l.ppb - 1) / l.ppb, 3), 256, l.smem_cols3, st>>>(fp, 0, ss, l.ppb);
   rows_inv_kernel<R><<<dim3(fp.ny / l.nb, 3, 3), 256, l.smem_rows, st>>>(fp, L, f, nullptr, nullptr, 0, ss, l.nb);
 }
 

@@ -34,26 +34,46 @@ static inline dim3 red_grid(const Layout& L, int* kchunk) {
 // CFL: per cell the advective rate sum|u_i|/dx_i + sqrt(gamma T + B^2/rho)
 // sqrt(sum 1/dx_i^2) and the diffusive rate D_max sum 1/dx_i^2, D_max the
 // largest of nu, eta + eta_s w, D_rho + chi_rho w, chi_s w + (gamma-1)
-// kappa0 T^{5/2}/rho.  Block maxima to partial[2 b], partial[2 b + 1].
+// kappa0 T^{5/2}/rho; their maxima over the cells.
+//
+// Two x-adjacent cells (i even, i + 1) per thread, loaded as 8- or 16-byte
+// pairs: the y, z stencils take one pair load per neighbour, the x stencils
+// five pair loads for both cells.
+template <typename R> struct Pair2;
+template <> struct Pair2<float> { using T = float2; };
+template <> struct Pair2<double> { using T = double2; };
 template <typename R>
-__device__ __forceinline__ R d1s(const R* __restrict__ p, int s, R inv) {
-  return (W<R>::c1 * (__ldg(p + s) - __ldg(p - s)) + W<R>::c2 * (__ldg(p + 2 * s) - __ldg(p - 2 * s)) +
-          W<R>::c3 * (__ldg(p + 3 * s) - __ldg(p - 3 * s))) * inv;
+__device__ __forceinline__ typename Pair2<R>::T ldp(const R* p) {
+  return __ldg(reinterpret_cast<const typename Pair2<R>::T*>(p));
+}
+// first derivative at p and p + 1 along a stride s that is not x
+template <typename R>
+__device__ __forceinline__ void d1s_pair(const R* __restrict__ p, int s, R inv, R& r0, R& r1) {
+  const auto a1 = ldp(p + s), b1 = ldp(p - s), a2 = ldp(p + 2 * s), b2 = ldp(p - 2 * s);
+  const auto a3 = ldp(p + 3 * s), b3 = ldp(p - 3 * s);
+  r0 = (W<R>::c1 * (a1.x - b1.x) + W<R>::c2 * (a2.x - b2.x) + W<R>::c3 * (a3.x - b3.x)) * inv;
+  r1 = (W<R>::c1 * (a1.y - b1.y) + W<R>::c2 * (a2.y - b2.y) + W<R>::c3 * (a3.y - b3.y)) * inv;
+}
+// first x derivative at p and p + 1 from the pairs at p - 4 .. p + 4
+template <typename R>
+__device__ __forceinline__ void d1x_pair(const R* __restrict__ p, R inv, R& r0, R& r1) {
+  const auto m4 = ldp(p - 4), m2 = ldp(p - 2), z0 = ldp(p), p2 = ldp(p + 2), p4 = ldp(p + 4);
+  r0 = (W<R>::c1 * (z0.y - m2.y) + W<R>::c2 * (p2.x - m2.x) + W<R>::c3 * (p2.y - m4.y)) * inv;
+  r1 = (W<R>::c1 * (p2.x - z0.x) + W<R>::c2 * (p2.y - m2.y) + W<R>::c3 * (p4.x - m2.x)) * inv;
 }
 
-// One thread per cell, all of a cell's loads in flight at once.  Planes
-// k0 .. k0 + nlo - 1, then (blockIdx.z >= nlo) shifted by kgap, so one launch
-// can cover the three layers at each end.  Block maxima go by atomicMax on
-// the bit patterns (non-negative IEEE doubles order like their bits read as
-// unsigned integers, so the result does not depend on the order of the
-// blocks) into one of CFL_SLOTS slot pairs, zeroed beforehand.
+// Planes k0 .. k0 + nlo - 1, then (blockIdx.z >= nlo) shifted by kgap, so one
+// launch can cover the three layers at each end.  Block maxima go by
+// atomicMax on the bit patterns (non-negative IEEE doubles order like their
+// bits read as unsigned integers, so the result does not depend on the order
+// of the blocks) into one of CFL_SLOTS slot pairs, zeroed beforehand.
 template <typename R>
 __global__ void __launch_bounds__(256) cfl_partial_kernel(Layout L, Phys<R> ph, Background<R> bg,
                                                           const R* __restrict__ f, const R* __restrict__ wtab,
                                                           double* partial, StepState* ss, R sqinv2, int k0, int nlo,
                                                           int kgap) {
   __shared__ R sa[8], sd[8];
-  const int i = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y * 8 + threadIdx.y;
+  const int i = 2 * (blockIdx.x * 32 + threadIdx.x), j = blockIdx.y * 8 + threadIdx.y;
   const int k = k0 + (int)blockIdx.z + ((int)blockIdx.z >= nlo ? kgap : 0);
   const int tid = threadIdx.y * 32 + threadIdx.x;
   if (halted(ss)) return;
@@ -66,24 +86,39 @@ __global__ void __launch_bounds__(256) cfl_partial_kernel(Layout L, Phys<R> ph, 
     const R* pax = f + L.at(AX, k, j, i);
     const R* pay = f + L.at(AY, k, j, i);
     const R* paz = f + L.at(AZ, k, j, i);
-    // B = curl A + B_ext (Eq. 6)
-    const R B0 = d1s(paz, sy, ph.idy) - d1s(pay, sz, ph.idz) + ph.bext[0];
-    const R B1 = d1s(pax, sz, ph.idz) - d1s(paz, 1, ph.idx) + ph.bext[1];
-    const R B2 = d1s(pay, 1, ph.idx) - d1s(pax, sy, ph.idy) + ph.bext[2];
-    const R ux = __ldg(f + L.at(UX, k, j, i)), uy = __ldg(f + L.at(UY, k, j, i)), uz = __ldg(f + L.at(UZ, k, j, i));
-    const R lr = bg.lbar[k + NG] + __ldg(f + L.at(LR, k, j, i)), lt = bg.tbar[k + NG] + __ldg(f + L.at(LT, k, j, i));
-    const R T = rexp<R>(lt), rho1 = rexp<R>(-lr);
-    const R B2s = B0 * B0 + B1 * B1 + B2 * B2;
-    const R adv = fabs(ux) * ph.idx + fabs(uy) * ph.idy + fabs(uz) * ph.idz +
-                  rsqrt_<R>(ph.gamma * T + B2s * rho1) * sqinv2;
+    // B = curl A + B_ext (Eq. 6) at both cells
+    R dyaz[2], dzay[2], dzax[2], dxaz[2], dxay[2], dyax[2];
+    d1s_pair(paz, sy, ph.idy, dyaz[0], dyaz[1]);
+    d1s_pair(pay, sz, ph.idz, dzay[0], dzay[1]);
+    d1s_pair(pax, sz, ph.idz, dzax[0], dzax[1]);
+    d1x_pair(paz, ph.idx, dxaz[0], dxaz[1]);
+    d1x_pair(pay, ph.idx, dxay[0], dxay[1]);
+    d1s_pair(pax, sy, ph.idy, dyax[0], dyax[1]);
+    const auto u0 = ldp(f + L.at(UX, k, j, i)), u1 = ldp(f + L.at(UY, k, j, i)), u2 = ldp(f + L.at(UZ, k, j, i));
+    const auto plr = ldp(f + L.at(LR, k, j, i)), plt = ldp(f + L.at(LT, k, j, i));
+    const R ux[2] = {u0.x, u0.y}, uy[2] = {u1.x, u1.y}, uz[2] = {u2.x, u2.y};
+    const R lrs[2] = {plr.x, plr.y}, lts[2] = {plt.x, plt.y};
     const R w = wtab[k];
-    R dm = ph.nu;
-    dm = fmax(dm, ph.eta + ph.eta_s * w);
-    dm = fmax(dm, ph.drho + ph.drho_s * w);
-    dm = fmax(dm, ph.chi_s * w + ph.gm1 * ph.kappa0 * rexp<R>(R(2.5) * lt - lr));
-    if (!isfinite(adv) || !isfinite(dm)) atomicOr(&ss->nonfinite, 1);
-    mar = adv;
-    mdr = dm;
+    const int nc = i + 1 < L.nx ? 2 : 1;
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      if (c >= nc) break;
+      const R B0 = dyaz[c] - dzay[c] + ph.bext[0];
+      const R B1 = dzax[c] - dxaz[c] + ph.bext[1];
+      const R B2 = dxay[c] - dyax[c] + ph.bext[2];
+      const R lr = bg.lbar[k + NG] + lrs[c], lt = bg.tbar[k + NG] + lts[c];
+      const R T = rexp<R>(lt), rho1 = rexp<R>(-lr);
+      const R B2s = B0 * B0 + B1 * B1 + B2 * B2;
+      const R adv = fabs(ux[c]) * ph.idx + fabs(uy[c]) * ph.idy + fabs(uz[c]) * ph.idz +
+                    rsqrt_<R>(ph.gamma * T + B2s * rho1) * sqinv2;
+      R dm = ph.nu;
+      dm = fmax(dm, ph.eta + ph.eta_s * w);
+      dm = fmax(dm, ph.drho + ph.drho_s * w);
+      dm = fmax(dm, ph.chi_s * w + ph.gm1 * ph.kappa0 * rexp<R>(R(2.5) * lt - lr));
+      if (!isfinite(adv) || !isfinite(dm)) atomicOr(&ss->nonfinite, 1);
+      mar = fmax(mar, adv);
+      mdr = fmax(mdr, dm);
+    }
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -115,7 +150,7 @@ int launch_cfl_partial(const Layout& L, const Phys<R>& ph, const Background<R>& 
   const int nk = planes == CflPlanes::ends ? 2 * NG : nlo;
   if (nk > 0) {
     R s2 = (R)sqrt((double)ph.idx2 + (double)ph.idy2 + (double)ph.idz2);
-    cfl_partial_kernel<R><<<dim3((L.nx + 31) / 32, (L.ny + 7) / 8, nk), dim3(32, 8), 0, st>>>(
+    cfl_partial_kernel<R><<<dim3((L.nx + 63) / 64, (L.ny + 7) / 8, nk), dim3(32, 8), 0, st>>>(
         L, ph, bg, f, wtab, partial, ss, s2, k0, nlo, kgap);
   }
   return CFL_SLOTS;
