@@ -21,7 +21,7 @@ __device__ __forceinline__ double warp_sum(double v) {
 
 // grid over (x tiles, y tiles, z chunks); each thread walks its z chunk
 static inline dim3 red_grid(const Layout& L, int* kchunk) {
-  int tx = (L.nx + 31) / 32, ty = (L.ny + 7) / 8;
+  int tx = (L.nx + 63) / 64, ty = (L.ny + 7) / 8;
   int zc = 2432 / (tx * ty);  // about 16 blocks per SM
   if (zc < 1) zc = 1;
   if (zc > L.nz) zc = L.nz;
@@ -208,42 +208,46 @@ void launch_cfl_finalize(const double* partial, int nblk, StepState* ss, double 
 }
 
 // Diagnostics, first pass: curl A (Eq. 6, without the uniform B_ext) into the
-// scratch fields 0..2 in the state layout.  B_z is formed on the ghost planes
-// k = -3 .. nz + 2 as well (it has no z derivative, and its x, y stencils read
-// the periodic rims, which the ghost rules fill on every plane), so that the
-// second pass can take z derivatives of B_z; B_x, B_y only on interior planes.
+// scratch fields 0..2 in the state layout.  B_z is formed on the interior
+// columns of every plane k = -3 .. nz + 2 (it has no z derivative, and its
+// x, y stencils read the periodic rims, which the ghost rules fill on every
+// plane); B_x on interior rows and planes for x = -3 .. nx + 2 (it has no x
+// derivative), B_y on interior columns and planes for y = -3 .. ny + 2.  So
+// the second pass finds every neighbour of its divergence stencil stored,
+// the periodic images being computed from the state's images, bit for bit
+// equal to the interior values they copy.
 template <typename R>
 __global__ void __launch_bounds__(256) curl_a_kernel(Layout L, Phys<R> ph, const R* __restrict__ f,
                                                      R* __restrict__ bsc) {
-  const int i = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y * 8 + threadIdx.y;
+  const int i = (int)(blockIdx.x * 32 + threadIdx.x) - NG, j = (int)(blockIdx.y * 8 + threadIdx.y) - NG;
   const int k = (int)blockIdx.z - NG;
-  if (i >= L.nx || j >= L.ny) return;
+  if (i >= L.nx + NG || j >= L.ny + NG) return;
+  const bool ix = i >= 0 && i < L.nx, jy = j >= 0 && j < L.ny, kz = k >= 0 && k < L.nz;
   const long long sy = L.sy(), sz = L.sz();
   const R* ax = f + L.at(AX, k, j, i);
   const R* ay = f + L.at(AY, k, j, i);
-  const long long c = L.at(0, k, j, i);
-  bsc[c + 2 * L.fs] = d1(ay, (long long)1, ph.idx) - d1(ax, sy, ph.idy);
-  if (k < 0 || k >= L.nz) return;
   const R* az = f + L.at(AZ, k, j, i);
-  bsc[c] = d1(az, sy, ph.idy) - d1(ay, sz, ph.idz);
-  bsc[c + L.fs] = d1(ax, sz, ph.idz) - d1(az, (long long)1, ph.idx);
+  const long long c = L.at(0, k, j, i);
+  if (ix && jy) bsc[c + 2 * L.fs] = d1(ay, (long long)1, ph.idx) - d1(ax, sy, ph.idy);
+  if (jy && kz) bsc[c] = d1(az, sy, ph.idy) - d1(ay, sz, ph.idz);
+  if (ix && kz) bsc[c + L.fs] = d1(ax, sz, ph.idz) - d1(az, (long long)1, ph.idx);
 }
 
 // Second pass: per block 7 values (sums of rho u^2/2, B^2/2, rho T/(gamma-1),
-// rho, B_z(k=0), |B_z(k=0)|, and max |div B|) to partial[8 b + q].  div B is
-// the centred sixth-order divergence of the stored curl A (x, y neighbours
-// wrapped periodically, z neighbours on the ghost planes), so it measures how
-// far the discrete operators fail to commute; B_ext drops out of it.
+// rho, B_z(k=0), |B_z(k=0)|, and max |div B|) to partial[8 b + q], two
+// x-adjacent cells per thread with pair loads.  div B is the centred
+// sixth-order divergence of the stored curl A, so it measures how far the
+// discrete operators fail to commute; B_ext drops out of it.
 template <typename R>
 __global__ void __launch_bounds__(256) stats_partial_kernel(Layout L, Phys<R> ph, Background<R> bg,
                                                             const R* __restrict__ f,
                                                             const R* __restrict__ bsc,
                                                             double* partial, int kchunk) {
   __shared__ double sm[8][8];
-  const int i = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y * 8 + threadIdx.y;
+  const int i = 2 * (blockIdx.x * 32 + threadIdx.x), j = blockIdx.y * 8 + threadIdx.y;
   const int tid = threadIdx.y * 32 + threadIdx.x;
   double acc[7] = {0, 0, 0, 0, 0, 0, 0};
-  // a thread's own chunk is summed in the state precision with Neumaier
+  // a thread's own cells are summed in the state precision with Neumaier
   // compensation (sum + correction carried separately), then taken to FP64:
   // FP64 arithmetic is ~60x slower than FP32 here
   R ps[6] = {R(0), R(0), R(0), R(0), R(0), R(0)}, pc[6] = {R(0), R(0), R(0), R(0), R(0), R(0)};
@@ -254,38 +258,40 @@ __global__ void __launch_bounds__(256) stats_partial_kernel(Layout L, Phys<R> ph
   };
   R dmax = R(0);
   if (i < L.nx && j < L.ny) {
-    const long long sz = L.sz();
-    const R cw[3] = {W<R>::c1, W<R>::c2, W<R>::c3};
-    int ip[3], im[3], jp[3], jm[3];
-    for (int m = 1; m <= 3; ++m) {
-      ip[m - 1] = i + m < L.nx ? i + m : i + m - L.nx;
-      im[m - 1] = i - m >= 0 ? i - m : i - m + L.nx;
-      jp[m - 1] = j + m < L.ny ? j + m : j + m - L.ny;
-      jm[m - 1] = j - m >= 0 ? j - m : j - m + L.ny;
-    }
+    const int sy = L.mx;
+    const int sz = (int)L.sz();
+    const int nc = i + 1 < L.nx ? 2 : 1;
     const int k0 = blockIdx.z * kchunk, k1 = min(L.nz, k0 + kchunk);
     for (int k = k0; k < k1; ++k) {
-      const R* bx = bsc + L.at(0, k, j, 0);
-      const R* by = bsc + L.fs + L.at(0, k, 0, i);
-      const R* bz = bsc + 2 * L.fs + L.at(0, k, j, i);
-      const R Bx = bx[i] + ph.bext[0], By = by[(long long)j * L.sy()] + ph.bext[1], Bz = bz[0] + ph.bext[2];
-      const R ux = f[L.at(UX, k, j, i)], uy = f[L.at(UY, k, j, i)], uz = f[L.at(UZ, k, j, i)];
-      const R rho = rexp<R>(bg.lbar[k + NG] + f[L.at(LR, k, j, i)]);
-      const R T = rexp<R>(bg.tbar[k + NG] + f[L.at(LT, k, j, i)]);
-      nadd(0, R(0.5) * rho * (ux * ux + uy * uy + uz * uz));
-      nadd(1, R(0.5) * (Bx * Bx + By * By + Bz * Bz));
-      nadd(2, rho * T);  // / (gamma - 1) once, in the finalize
-      nadd(3, rho);
-      if (k == 0) {
-        nadd(4, Bz);
-        nadd(5, fabs(Bz));
-      }
-      R dv = R(0);
+      const R* bx = bsc + L.at(0, k, j, i);
+      const R* by = bx + L.fs;
+      const R* bz = bx + 2 * L.fs;
+      R dbx[2], dby[2], dbz[2];
+      d1x_pair(bx, ph.idx, dbx[0], dbx[1]);
+      d1s_pair(by, sy, ph.idy, dby[0], dby[1]);
+      d1s_pair(bz, sz, ph.idz, dbz[0], dbz[1]);
+      const auto cx = ldp(bx), cy = ldp(by), cz = ldp(bz);
+      const auto u0 = ldp(f + L.at(UX, k, j, i)), u1 = ldp(f + L.at(UY, k, j, i)), u2 = ldp(f + L.at(UZ, k, j, i));
+      const auto plr = ldp(f + L.at(LR, k, j, i)), plt = ldp(f + L.at(LT, k, j, i));
+      const R bxs[2] = {cx.x, cx.y}, bys[2] = {cy.x, cy.y}, bzs[2] = {cz.x, cz.y};
+      const R ux[2] = {u0.x, u0.y}, uy[2] = {u1.x, u1.y}, uz[2] = {u2.x, u2.y};
+      const R lrs[2] = {plr.x, plr.y}, lts[2] = {plt.x, plt.y};
 #pragma unroll
-      for (int m = 0; m < 3; ++m)
-        dv += cw[m] * ((bx[ip[m]] - bx[im[m]]) * ph.idx + (by[(long long)jp[m] * L.sy()] - by[(long long)jm[m] * L.sy()]) * ph.idy +
-                       (bz[(m + 1) * sz] - bz[-(m + 1) * sz]) * ph.idz);
-      dmax = fmax(dmax, fabs(dv));
+      for (int c = 0; c < 2; ++c) {
+        if (c >= nc) break;
+        const R Bx = bxs[c] + ph.bext[0], By = bys[c] + ph.bext[1], Bz = bzs[c] + ph.bext[2];
+        const R rho = rexp<R>(bg.lbar[k + NG] + lrs[c]);
+        const R T = rexp<R>(bg.tbar[k + NG] + lts[c]);
+        nadd(0, R(0.5) * rho * (ux[c] * ux[c] + uy[c] * uy[c] + uz[c] * uz[c]));
+        nadd(1, R(0.5) * (Bx * Bx + By * By + Bz * Bz));
+        nadd(2, rho * T);  // / (gamma - 1) once, in the finalize
+        nadd(3, rho);
+        if (k == 0) {
+          nadd(4, Bz);
+          nadd(5, fabs(Bz));
+        }
+        dmax = fmax(dmax, fabs(dbx[c] + dby[c] + dbz[c]));
+      }
     }
   }
   for (int q = 0; q < 6; ++q) acc[q] = (double)ps[q] + (double)pc[q];
@@ -308,7 +314,7 @@ __global__ void __launch_bounds__(256) stats_partial_kernel(Layout L, Phys<R> ph
 template <typename R>
 int launch_stats_partial(const Layout& L, const Phys<R>& ph, const Background<R>& bg, const R* f, R* bsc,
                          double* partial, cudaStream_t st) {
-  dim3 gc((L.nx + 31) / 32, (L.ny + 7) / 8, L.nz + 2 * NG);
+  dim3 gc((L.nx + 2 * NG + 31) / 32, (L.ny + 2 * NG + 7) / 8, L.nz + 2 * NG);
   curl_a_kernel<R><<<gc, dim3(32, 8), 0, st>>>(L, ph, f, bsc);
   int kchunk;
   dim3 g = red_grid(L, &kchunk);
