@@ -392,15 +392,55 @@ static FFTLaunch fft_launch(const FFTPlan& fp) {
   return l;
 }
 
+// Row transforms of `planes` planes: lines per block chosen so that the
+// blocks spread evenly over the SMs (all blocks of these kernels are resident
+// at once and share each SM's FP64 pipe, so the busiest SM sets the time);
+// one thread per radix-4 butterfly of a stage.
+struct RowsCfg {
+  int nb, threads;
+  size_t smem;
+};
+
+static RowsCfg rows_cfg(const FFTPlan& fp, int planes) {
+  static int nsm = 0;
+  if (nsm == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (nsm <= 0) nsm = 1;
+  }
+  int nbmax = 1024 / fp.nx;
+  if (nbmax < 1) nbmax = 1;
+  if (nbmax > fp.ny) nbmax = fp.ny;
+  RowsCfg c{nbmax, 0, 0};
+  double best = -1.0;
+  for (int nb = nbmax; nb >= 1; nb >>= 1) {
+    const long long blocks = (long long)planes * (fp.ny / nb);
+    const long long per_sm = (blocks + nsm - 1) / nsm;
+    const double eff = (double)blocks / (double)(per_sm * nsm);
+    if (eff > best + 1e-9) {
+      best = eff;
+      c.nb = nb;
+    }
+  }
+  c.threads = c.nb * fp.nx / 4;
+  if (c.threads > 256) c.threads = 256;
+  if (c.threads < 32) c.threads = 32;
+  c.smem = (size_t)2 * c.nb * fp.nx * sizeof(double2);
+  return c;
+}
+
 template <typename R>
 void launch_pfe(const FFTPlan& fp, const Layout& L, R* f, const StepState* ss, cudaStream_t st) {
   set_smem_once();
   const FFTLaunch l = fft_launch(fp);
   const int npairs = fp.nx / 2 + 1;
-  rows_fwd_kernel<R><<<dim3(fp.ny / l.nb, 3), 256, l.smem_rows, st>>>(fp, L, f, nullptr, 0, ss, l.nb, nullptr,
-                                                                       nullptr);
+  const RowsCfg rf = rows_cfg(fp, 3), ri = rows_cfg(fp, 9);
+  rows_fwd_kernel<R><<<dim3(fp.ny / rf.nb, 3), rf.threads, rf.smem, st>>>(fp, L, f, nullptr, 0, ss, rf.nb, nullptr,
+                                                                          nullptr);
   cols_kernel<<<dim3((npairs + l.ppb - 1) / l.ppb, 3), 256, l.smem_cols3, st>>>(fp, 0, ss, l.ppb);
-  rows_inv_kernel<R><<<dim3(fp.ny / l.nb, 3, 3), 256, l.smem_rows, st>>>(fp, L, f, nullptr, nullptr, 0, ss, l.nb);
+  rows_inv_kernel<R><<<dim3(fp.ny / ri.nb, 3, 3), ri.threads, ri.smem, st>>>(fp, L, f, nullptr, nullptr, 0, ss,
+                                                                            ri.nb);
 }
 
 template <typename R>

@@ -221,6 +221,29 @@ def test_periodic_ragged_run_fp64():
     assert max(errs) <= 1e-12, errs
 
 
+@pytest.mark.parametrize("precision", [64, 32])
+def test_periodic_odd_nx_cfl_and_stats(precision):
+    """Odd nx in the periodic test geometry: the CFL and diagnostics kernels
+    work on x pairs, the last of which has one cell outside the box."""
+    case = _perturbed(37, 22, 13, seed=9)
+    p = dict(case.params, bc_z=1, eta_swamp=0.0, chi_swamp=0.0, diffrho_swamp=0.0, gz=0.0)
+    sim = _sim(case, precision, params=p, driver=False)
+    sim.fill_ghosts()
+    u = np.ascontiguousarray(sim.read_padded(0), dtype=np.float64)
+    tol = 1e-12 if precision == 64 else 1e-5
+    dt = sim.compute_dt()
+    assert abs(dt - oracle.cfl(p, u)) <= tol * dt
+    st = sim.compute_stats()
+    ref = oracle.stats(p, u)
+    keys = ["e_kin", "e_mag", "e_th", "mass", "flux_net", "flux_abs", "divb_max"]
+    for k in ("e_kin", "e_mag", "e_th", "mass", "flux_abs"):
+        r = ref[keys.index(k)]
+        assert abs(st[k] - r) <= tol * abs(r), (k, st[k], r)
+    assert abs(st["flux_net"] - ref[4]) <= tol * ref[5]
+    bscale = np.sqrt(2.0 * ref[1] / (37 * 22 * 13 * p["dx"] ** 3)) / p["dx"]
+    assert st["divb_max"] <= (1e-10 if precision == 64 else 1e-3) * bscale
+
+
 def test_nonfinite_detected():
     from paper_1908_08557_gb300 import MHDError
     from paper_1908_08557_gb300.binding import MHD_ERR_NONFINITE
