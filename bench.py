@@ -51,6 +51,9 @@ def parse():
                     help="also run the checkpointed gradient of bipoles100_512x512x256 (minutes)")
     ap.add_argument("--scale-steps", type=int, default=0, help="0: the workload's step count (600)")
     ap.add_argument("--scale-iters", type=int, default=3)
+    ap.add_argument("--drift", action="store_true",
+                    help="also run ar_1024x1024x256 in FP32 and FP64 and compare energies, fluxes and fields")
+    ap.add_argument("--drift-steps", type=int, default=100)
     return ap.parse_args()
 
 
@@ -385,6 +388,68 @@ def production_line(dev, ws):
             "rk_achieved_gbs": achieved, "class_ms_per_step": {kk: v[0] / 3 for kk, v in prof.items()}}
 
 
+def drift_line(dev, steps, reseed=50):
+    """Production geometry ar_1024x1024x256: the FP32 path against an FP64 GPU
+    run of the same steps from the same state.  The driver is re-seeded every
+    `reseed` steps: the last snapshot becomes v0 and a new seeded solenoidal
+    field v1, reached `reseed` steps of the current dt later.  Reports the
+    diagnostics of both runs at the start and the end, their relative drift,
+    the FP32/FP64 differences of the end values and the per-field relative L2
+    difference of the end states."""
+    import numpy as np
+    import torch
+
+    import inputs
+    from paper_1908_08557_gb300 import Simulation
+    c = inputs.make_case("ar_1024x1024x256")
+    p = c.params
+    km = min(32, p["nx"] // 2, p["ny"] // 2)
+    drivers = [c.v0, c.v1]
+    keys = ["e_kin", "e_mag", "e_th", "mass", "flux_net", "flux_abs", "divb_max"]
+    res, ends = {}, {}
+    for prec in (32, 64):
+        tdt = torch.float32 if prec == 32 else torch.float64
+        sim = Simulation(p, torch.tensor(c.state, dtype=tdt, device=dev), c.lnrho0, c.lnT0, precision=prec,
+                         stats_every=0, device=str(dev))
+        bz = torch.tensor(c.bz, dtype=tdt, device=dev)
+        sim.set_driver(bz, torch.tensor(c.v0, dtype=tdt, device=dev), torch.tensor(c.v1, dtype=tdt, device=dev),
+                       c.t0, c.t1)
+        sim.fill_ghosts()  # the diagnostics read the ghost planes; the ghost rules are idempotent
+        s0 = sim.compute_stats()
+        t0 = time.perf_counter()
+        for n in range(steps):
+            if n > 0 and n % reseed == 0:
+                k = n // reseed
+                while len(drivers) < k + 2:
+                    drivers.append(inputs.driver_solenoidal(p["nx"], p["ny"], km, 0.01, len(drivers)))
+                t, dt = sim.time()
+                sim.set_driver(bz, torch.tensor(drivers[k], dtype=tdt, device=dev),
+                               torch.tensor(drivers[k + 1], dtype=tdt, device=dev), t, t + reseed * dt)
+            sim.step(1)
+        sim.fill_ghosts()
+        s1 = sim.compute_stats()
+        secs = time.perf_counter() - t0
+        ends[prec] = sim.read().to(torch.float64)
+        res[f"fp{prec}"] = {"start": {q: s0[q] for q in keys}, "end": {q: s1[q] for q in keys},
+                            "drift": {q: (s1[q] - s0[q]) / abs(s0[q]) if s0[q] != 0 else None for q in keys[:4]},
+                            "t_end": sim.time()[0], "seconds": secs}
+        sim.close()
+        del sim
+        torch.cuda.empty_cache()
+    e32, e64 = res["fp32"]["end"], res["fp64"]["end"]
+    res["fp32_vs_fp64_end"] = {q: (e32[q] - e64[q]) / abs(e64[q]) if e64[q] != 0 else None for q in keys[:4]}
+    res["fp32_vs_fp64_end"]["flux_net_over_flux_abs"] = (e32["flux_net"] - e64["flux_net"]) / e64["flux_abs"]
+    res["fp32_vs_fp64_end"]["flux_abs"] = (e32["flux_abs"] - e64["flux_abs"]) / e64["flux_abs"]
+    names = ["A_x", "A_y", "A_z", "u_x", "u_y", "u_z", "ln_rho", "ln_T"]
+    res["field_rel_l2"] = {names[f]: float(torch.linalg.vector_norm(ends[32][f] - ends[64][f]) /
+                                           torch.linalg.vector_norm(ends[64][f])) for f in range(8)}
+    res["steps"] = steps
+    res["reseed_every"] = reseed
+    del ends
+    torch.cuda.empty_cache()
+    return res
+
+
 def run_reference(args, ws, rank):
     if rank != 0:
         return
@@ -534,6 +599,13 @@ def run_native(args, ws, rank, local):
     if not args.no_production:
         prod = production_line(dev, ws)
 
+    drift = None
+    if args.drift:
+        try:
+            drift = drift_line(dev, args.drift_steps)
+        except Exception as exc:  # reported, not fatal: the run is optional
+            drift = {"error": f"{type(exc).__name__}: {exc}"}
+
     scale = None
     if args.adjoint_scale:
         try:
@@ -563,6 +635,8 @@ def run_native(args, ws, rank, local):
                 "clocks": clocks, "fp64": fp64, "adjoint": adj, "production_1024x1024x256": prod}
         if scale is not None:
             line["adjoint_bipoles100_512x512x256"] = scale
+        if drift is not None:
+            line["drift_ar_1024x1024x256"] = drift
         print(json.dumps(line), flush=True)
 
 
