@@ -449,11 +449,12 @@ void launch_atarget(const FFTPlan& fp, const R* bz, R* axt, R* ayt, cudaStream_t
   Layout L{};
   const FFTLaunch l = fft_launch(fp);
   const int npairs = fp.nx / 2 + 1;
-  rows_fwd_kernel<R><<<dim3(fp.ny / l.nb, 1), 256, l.smem_rows, st>>>(fp, L, nullptr, bz, 1, nullptr, l.nb, nullptr,
-                                                                       nullptr);
+  const RowsCfg r1 = rows_cfg(fp, 1);
+  rows_fwd_kernel<R><<<dim3(fp.ny / r1.nb, 1), r1.threads, r1.smem, st>>>(fp, L, nullptr, bz, 1, nullptr, r1.nb,
+                                                                          nullptr, nullptr);
   cols_kernel<<<dim3((npairs + l.ppb - 1) / l.ppb, 1), 256, l.smem_cols, st>>>(fp, 1, nullptr, l.ppb);
-  rows_inv_kernel<R><<<dim3(fp.ny / l.nb, 1, 1), 256, l.smem_rows, st>>>(fp, L, nullptr, axt, ayt, 1, nullptr,
-                                                                          l.nb);
+  rows_inv_kernel<R><<<dim3(fp.ny / r1.nb, 1, 1), r1.threads, r1.smem, st>>>(fp, L, nullptr, axt, ayt, 1, nullptr,
+                                                                             r1.nb);
 }
 
 // Adjoint of the potential-field ghosts: gbar (adjoint of the ghost-filled
@@ -465,11 +466,12 @@ void launch_pfe_adjoint(const FFTPlan& fp_adj, const Layout& L, R* gbar, const S
   set_smem_once();
   const FFTLaunch l = fft_launch(fp_adj);
   const int npairs = fp_adj.nx / 2 + 1;
-  rows_fwd_kernel<R><<<dim3(fp_adj.ny / l.nb, 9), 256, l.smem_rows, st>>>(fp_adj, L, gbar, nullptr, 2, ss, l.nb,
-                                                                           nullptr, nullptr);
+  const RowsCfg r9 = rows_cfg(fp_adj, 9), r3 = rows_cfg(fp_adj, 3);
+  rows_fwd_kernel<R><<<dim3(fp_adj.ny / r9.nb, 9), r9.threads, r9.smem, st>>>(fp_adj, L, gbar, nullptr, 2, ss, r9.nb,
+                                                                              nullptr, nullptr);
   cols_adj_kernel<<<dim3((npairs + l.ppb - 1) / l.ppb, 3), 256, l.smem_cols, st>>>(fp_adj, ss, l.ppb);
-  rows_inv_kernel<R><<<dim3(fp_adj.ny / l.nb, 3, 1), 256, l.smem_rows, st>>>(fp_adj, L, gbar, nullptr, nullptr, 2, ss,
-                                                                             l.nb);
+  rows_inv_kernel<R><<<dim3(fp_adj.ny / r3.nb, 3, 1), r3.threads, r3.smem, st>>>(fp_adj, L, gbar, nullptr, nullptr, 2,
+                                                                                ss, r3.nb);
 }
 
 // Transpose of the magnetogram inversion: B_z adjoint (out, [ny][nx]) from

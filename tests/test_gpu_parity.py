@@ -244,6 +244,25 @@ def test_periodic_odd_nx_cfl_and_stats(precision):
     assert st["divb_max"] <= (1e-10 if precision == 64 else 1e-3) * bscale
 
 
+@pytest.mark.parametrize("precision", [64, 32])
+def test_minimum_size_run(precision):
+    """The smallest box the FFT boundary and the pair kernel take (8 x 8
+    horizontal points, 7 layers): step(0) changes nothing; 5 steps against
+    the oracle."""
+    case = _perturbed(8, 8, 7, seed=12)
+    sim = _sim(case, precision)
+    before = sim.read().clone()
+    sim.step(0)
+    assert torch.equal(sim.read(), before) and sim.time()[0] == 0.0
+    sim.step(5)
+    got = sim.read().cpu().numpy().astype(np.float64)
+    u, t, dts = oracle.run_case(case, nsteps=5)
+    ref = oracle.interior(u)
+    errs = [_rel_l2(got[f], ref[f]) for f in range(8)]
+    assert max(errs) <= (1e-11 if precision == 64 else 1e-4), errs
+    assert abs(sim.time()[0] - t) <= (1e-12 if precision == 64 else 1e-5) * t
+
+
 def test_nonfinite_detected():
     from paper_1908_08557_gb300 import MHDError
     from paper_1908_08557_gb300.binding import MHD_ERR_NONFINITE
