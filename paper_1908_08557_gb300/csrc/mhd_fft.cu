@@ -154,10 +154,12 @@ __global__ void __launch_bounds__(256) rows_fwd_kernel(FFTPlan fp, Layout L, con
 // are needed to split the packed plane P2 (F(-k) lives in the mirror column).
 // mode 0: potential-field extrapolation, 3 layers; mode 1: magnetogram
 // inversion (Eq. 7): A^_x + i A^_y = (kt_x + i kt_y) B^_z / kt^2; mode 2: its
-// transpose.  The spectra of all output layers are formed first and inverted
-// as one batch of lines, so each stage of the inverse transform has nout
-// times the butterflies between two barriers.
-__global__ void __launch_bounds__(256) cols_kernel(FFTPlan fp, int mode, const StepState* ss, int ppb) {
+// transpose.  The spectra of lg output layers at a time are formed and
+// inverted as one batch of lines, so each stage of the inverse transform has
+// lg times the butterflies between two barriers; lg = nout needs two buffers
+// of lg layers (the forward spectrum's buffer becomes the scratch), lg < nout
+// three (the spectrum is kept).
+__global__ void __launch_bounds__(256) cols_kernel(FFTPlan fp, int mode, const StepState* ss, int ppb, int lg) {
   extern __shared__ double2 sm[];
   if (ss && halted(ss)) return;
   const int nx = fp.nx, ny = fp.ny;
@@ -168,8 +170,10 @@ __global__ void __launch_bounds__(256) cols_kernel(FFTPlan fp, int mode, const S
   const int p = blockIdx.y;
   const int nout = mode == 0 ? 3 : 1;
   const int npts = nl * ny;            // points of one layer
-  double2* A = sm;                     // nout layers of 2 ppb ny points each
-  double2* B = sm + nout * 2 * ppb * ny;
+  const int bsz = lg * 2 * ppb * ny;   // points of one buffer
+  double2* A = sm;
+  double2* B = sm + bsz;
+  double2* Z = sm + 2 * bsz;           // used when lg < nout
   // columns of line l: pair (l >> 1), mirror if odd
   for (int q = threadIdx.x; q < npts; q += blockDim.x) {
     const int line = q / ny, y = q - line * ny;
@@ -179,9 +183,12 @@ __global__ void __launch_bounds__(256) cols_kernel(FFTPlan fp, int mode, const S
   }
   __syncthreads();
   double2* spec = fft_lines(A, B, ny, fp.logny, nl, fp.twy, false);
-  double2* G = (spec == A) ? B : A;  // layer o's lines at G + o npts
-  for (int q = threadIdx.x; q < nout * npts; q += blockDim.x) {
-    const int o = q / npts, qq = q - o * npts;
+  double2* G = (spec == A) ? B : A;  // layer o0 + o's lines at G + o npts
+  double2* T = lg == nout ? spec : Z;
+  const int nplanes = mode == 0 ? 3 : 1;
+  for (int o0 = 0; o0 < nout; o0 += lg) {
+  for (int q = threadIdx.x; q < lg * npts; q += blockDim.x) {
+    const int o = o0 + q / npts, qq = q - (o - o0) * npts;
     const int line = qq / ny, ky = qq - line * ny;
     const int kx = pair0 + (line >> 1);
     const int col = (line & 1) ? ((nx - kx) & (nx - 1)) : kx;
@@ -229,16 +236,17 @@ __global__ void __launch_bounds__(256) cols_kernel(FFTPlan fp, int mode, const S
     G[q] = g;
   }
   __syncthreads();
-  double2* r = fft_lines(G, spec == A ? A : B, ny, fp.logny, nout * nl, fp.twy, true);
-  const int nplanes = mode == 0 ? 3 : 1;
-  for (int q = threadIdx.x; q < nout * npts; q += blockDim.x) {
-    const int o = q / npts, qq = q - o * npts;
+  const double2* r = fft_lines(G, T, ny, fp.logny, lg * nl, fp.twy, true);
+  for (int q = threadIdx.x; q < lg * npts; q += blockDim.x) {
+    const int o = o0 + q / npts, qq = q - (o - o0) * npts;
     const int line = qq / ny, y = qq - line * ny;
     const int kx = pair0 + (line >> 1);
     const bool self = (kx == 0 || 2 * kx == nx);
     if ((line & 1) && self) continue;  // the mirror of a self-paired column
     const int col = (line & 1) ? ((nx - kx) & (nx - 1)) : kx;
     fp.Q[(((long long)o * nplanes + p) * nx + col) * ny + y] = r[q];
+  }
+  __syncthreads();
   }
 }
 
@@ -375,7 +383,7 @@ static void set_smem_once() {
 // pairs per block (ppb) so there are enough blocks for every SM; shared
 // memory sized to the batch
 struct FFTLaunch {
-  int nb, ppb;
+  int nb, ppb, lg;                          // lg: ghost layers per inverse batch in cols
   size_t smem_rows, smem_cols, smem_cols3;  // cols: one output layer, three
 };
 
@@ -388,7 +396,11 @@ static FFTLaunch fft_launch(const FFTPlan& fp) {
   if (l.ppb < 1) l.ppb = 1;
   l.smem_rows = (size_t)2 * l.nb * fp.nx * sizeof(double2);
   l.smem_cols = (size_t)3 * 2 * l.ppb * fp.ny * sizeof(double2);  // also cols_adj_kernel
-  l.smem_cols3 = (size_t)6 * 2 * l.ppb * fp.ny * sizeof(double2);
+  // the three ghost layers in one batch while that keeps two column blocks
+  // per SM (at most 96 KB), one at a time otherwise (at 1024^2 the batched
+  // form, 192 KB and one block per SM, measured 8 % slower)
+  l.lg = (size_t)6 * 2 * l.ppb * fp.ny * sizeof(double2) <= (size_t)96 * 1024 ? 3 : 1;
+  l.smem_cols3 = (size_t)(l.lg == 3 ? 6 : 3) * 2 * l.ppb * fp.ny * sizeof(double2);
   return l;
 }
 
@@ -438,7 +450,7 @@ void launch_pfe(const FFTPlan& fp, const Layout& L, R* f, const StepState* ss, c
   const RowsCfg rf = rows_cfg(fp, 3), ri = rows_cfg(fp, 9);
   rows_fwd_kernel<R><<<dim3(fp.ny / rf.nb, 3), rf.threads, rf.smem, st>>>(fp, L, f, nullptr, 0, ss, rf.nb, nullptr,
                                                                           nullptr);
-  cols_kernel<<<dim3((npairs + l.ppb - 1) / l.ppb, 3), 256, l.smem_cols3, st>>>(fp, 0, ss, l.ppb);
+  cols_kernel<<<dim3((npairs + l.ppb - 1) / l.ppb, 3), 256, l.smem_cols3, st>>>(fp, 0, ss, l.ppb, l.lg);
   rows_inv_kernel<R><<<dim3(fp.ny / ri.nb, 3, 3), ri.threads, ri.smem, st>>>(fp, L, f, nullptr, nullptr, 0, ss,
                                                                             ri.nb);
 }
@@ -452,7 +464,7 @@ void launch_atarget(const FFTPlan& fp, const R* bz, R* axt, R* ayt, cudaStream_t
   const RowsCfg r1 = rows_cfg(fp, 1);
   rows_fwd_kernel<R><<<dim3(fp.ny / r1.nb, 1), r1.threads, r1.smem, st>>>(fp, L, nullptr, bz, 1, nullptr, r1.nb,
                                                                           nullptr, nullptr);
-  cols_kernel<<<dim3((npairs + l.ppb - 1) / l.ppb, 1), 256, l.smem_cols, st>>>(fp, 1, nullptr, l.ppb);
+  cols_kernel<<<dim3((npairs + l.ppb - 1) / l.ppb, 1), 256, l.smem_cols, st>>>(fp, 1, nullptr, l.ppb, 1);
   rows_inv_kernel<R><<<dim3(fp.ny / r1.nb, 1, 1), r1.threads, r1.smem, st>>>(fp, L, nullptr, axt, ayt, 1, nullptr,
                                                                              r1.nb);
 }
@@ -484,7 +496,7 @@ void launch_atarget_adjoint(const FFTPlan& fp, const double* abx, const double* 
   const int npairs = fp.nx / 2 + 1;
   rows_fwd_kernel<R><<<dim3(fp.ny / l.nb, 1), 256, l.smem_rows, st>>>(fp, L, nullptr, nullptr, 3, nullptr, l.nb, abx,
                                                                        aby);
-  cols_kernel<<<dim3((npairs + l.ppb - 1) / l.ppb, 1), 256, l.smem_cols, st>>>(fp, 2, nullptr, l.ppb);
+  cols_kernel<<<dim3((npairs + l.ppb - 1) / l.ppb, 1), 256, l.smem_cols, st>>>(fp, 2, nullptr, l.ppb, 1);
   rows_inv_kernel<R><<<dim3(fp.ny / l.nb, 1, 1), 256, l.smem_rows, st>>>(fp, L, nullptr, out, nullptr, 3, nullptr,
                                                                           l.nb);
 }
