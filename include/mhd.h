@@ -275,13 +275,16 @@ int mhd_invert_magnetogram_static(int nx, int ny, double dx, double dy,
 /* Kernel classes timed by the profiler. */
 #define MHD_KC_GHOST 0   /* pointwise ghost rules (and periodic copies)   */
 #define MHD_KC_PFE 1     /* potential-field FFT, three kernels             */
-#define MHD_KC_CFL 2     /* time-step reduction, two kernels               */
-#define MHD_KC_STATS 3   /* diagnostics reduction, two kernels             */
+#define MHD_KC_CFL 2     /* time-step reduction: partial maxima, finalize  */
+#define MHD_KC_STATS 3   /* diagnostics: curl A, partial sums, finalize    */
 #define MHD_KC_RK 4      /* fused right-hand side + RK update              */
 #define MHD_NKC 5
 
 /* enable != 0: from now on bracket every kernel class launched by mhd_step
- * with CUDA events on the handle's stream; enable = 0 stops recording. */
+ * with CUDA events on the stream it runs on; enable = 0 stops recording.
+ * Classes that overlap (the first substep's FFT on the side stream, the
+ * ghost rules and CFL reduction beside it) are each timed in full, so the
+ * class times of a step can sum to more than the step. */
 int mhd_profile(mhd_handle h, int enable);
 
 /* Synchronise, then return per class the summed event time in ms and the
