@@ -127,13 +127,27 @@ __device__ __forceinline__ R d2(const R* __restrict__ p, long long s, R inv2) {
   return (W<R>::e0 * __ldg(p) + W<R>::e1 * (__ldg(p + s) + __ldg(p - s)) +
           W<R>::e2 * (__ldg(p + 2 * s) + __ldg(p - 2 * s)) + W<R>::e3 * (__ldg(p + 3 * s) + __ldg(p - 3 * s))) * inv2;
 }
-// Mixed derivative D1_a(D1_b f): outer along sa, inner along sb.
+// Mixed derivative D1_a(D1_b f), written as the product stencil: the sum
+// over m, n = 1..3 of c_m c_n [f(+m,+n) - f(+m,-n) - f(-m,+n) + f(-m,-n)]
+// (m along sa, n along sb), times ia ib.  Same operator as applying D1_b and
+// then D1_a, with 4 operations per (m, n) instead of recomputing six inner
+// first derivatives.
 template <typename R>
 __device__ __forceinline__ R d11(const R* __restrict__ p, long long sa, long long sb, R ia, R ib) {
-  R e1 = d1(p + sa, sb, ib) - d1(p - sa, sb, ib);
-  R e2 = d1(p + 2 * sa, sb, ib) - d1(p - 2 * sa, sb, ib);
-  R e3 = d1(p + 3 * sa, sb, ib) - d1(p - 3 * sa, sb, ib);
-  return (W<R>::c1 * e1 + W<R>::c2 * e2 + W<R>::c3 * e3) * ia;
+  const R c[3] = {W<R>::c1, W<R>::c2, W<R>::c3};
+  R acc = R(0);
+#pragma unroll
+  for (int m = 1; m <= 3; ++m) {
+    R in = R(0);
+#pragma unroll
+    for (int n = 1; n <= 3; ++n) {
+      const R t = (__ldg(p + m * sa + n * sb) - __ldg(p + m * sa - n * sb)) -
+                  (__ldg(p - m * sa + n * sb) - __ldg(p - m * sa - n * sb));
+      in += c[n - 1] * t;
+    }
+    acc += c[m - 1] * in;
+  }
+  return acc * (ia * ib);
 }
 
 // Everything the right-hand side needs at one cell.

@@ -60,6 +60,7 @@ __global__ void __launch_bounds__(256) rk_simple_kernel(RKArgs<R> a) {
   for (int fl = 0; fl < NF; ++fl) base[fl] = a.fin + L.at(fl, k, j, i);
 
   Cell<R> c;
+  R a2[3], u2[3];  // own-axis second derivatives d_c^2 A_c, d_c^2 u_c (Laplacian and grad div share them)
 #pragma unroll
   for (int cc = 0; cc < 3; ++cc) {
     const R* pa = base[AX + cc];
@@ -72,8 +73,13 @@ __global__ void __launch_bounds__(256) rk_simple_kernel(RKArgs<R> a) {
     for (int ax = 0; ax < 3; ++ax) {
       c.dA[cc][ax] = d1(pa, st[ax], inv[ax]);
       c.dU[cc][ax] = d1(pu, st[ax], inv[ax]);
-      c.lapA[cc] += d2(pa, st[ax], inv2[ax]);
-      c.lapU[cc] += d2(pu, st[ax], inv2[ax]);
+      const R da2 = d2(pa, st[ax], inv2[ax]), du2 = d2(pu, st[ax], inv2[ax]);
+      if (ax == cc) {
+        a2[cc] = da2;
+        u2[cc] = du2;
+      }
+      c.lapA[cc] += da2;
+      c.lapU[cc] += du2;
     }
   }
 #pragma unroll
@@ -82,8 +88,8 @@ __global__ void __launch_bounds__(256) rk_simple_kernel(RKArgs<R> a) {
 #pragma unroll
     for (int cc = 0; cc < 3; ++cc) {
       if (cc == ax) {
-        sa += d2(base[AX + cc], st[ax], inv2[ax]);
-        su += d2(base[UX + cc], st[ax], inv2[ax]);
+        sa += a2[cc];
+        su += u2[cc];
       } else {
         sa += d11(base[AX + cc], st[ax], st[cc], inv[ax], inv[cc]);
         su += d11(base[UX + cc], st[ax], st[cc], inv[ax], inv[cc]);
