@@ -44,7 +44,7 @@ __device__ __forceinline__ void store_images(const Layout& L, R* __restrict__ f,
 }
 
 template <typename R>
-__global__ void __launch_bounds__(256) rk_simple_kernel(RKArgs<R> a) {
+__global__ void __launch_bounds__(256, sizeof(R) == 8 ? 2 : 0) rk_simple_kernel(RKArgs<R> a) {
   const Layout& L = a.L;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
