@@ -36,6 +36,7 @@ struct mhd_ctx {
   cudaStream_t side;   // highest-priority stream for the potential-field FFT of substep 0,
                        // forked from and joined to `st` by events (FFT boundary only)
   cudaEvent_t evf, evj;
+  cudaEvent_t evc;     // end of the host-to-device driver copies (mhd_set_driver)
   size_t esz;          // bytes per state element
   char* ws;
   size_t ws_bytes;
@@ -386,8 +387,9 @@ static void release_side(mhd_ctx* h) {
   if (h->side) cudaStreamSynchronize(h->side);
   if (h->evf) cudaEventDestroy(h->evf);
   if (h->evj) cudaEventDestroy(h->evj);
+  if (h->evc) cudaEventDestroy(h->evc);
   if (h->side) cudaStreamDestroy(h->side);
-  h->evf = h->evj = nullptr;
+  h->evf = h->evj = h->evc = nullptr;
   h->side = nullptr;
 }
 
@@ -655,6 +657,7 @@ extern "C" int mhd_create(const mhd_params* p, void* workspace, size_t ws_bytes,
     if (!rc) rc = cuda_check(h, cudaEventCreateWithFlags(&h->evf, cudaEventDisableTiming), "fork event");
     if (!rc) rc = cuda_check(h, cudaEventCreateWithFlags(&h->evj, cudaEventDisableTiming), "join event");
   }
+  if (!rc) rc = cuda_check(h, cudaEventCreateWithFlags(&h->evc, cudaEventDisableTiming), "copy event");
   if (!rc && h->tiled) {
     for (int s = 0; s < 2 && !rc; ++s)
       if (make_state_tensor_map(&h->tm[s], h->L, h->f[s]) != 0)
@@ -749,6 +752,7 @@ extern "C" int mhd_set_driver(mhd_handle h, const void* bz, const void* v0, cons
   int rc = cuda_check(h, cudaMemcpyAsync(h->bz, bz, n2, kind_in(mem), h->st), "copy bz");
   if (!rc) rc = cuda_check(h, cudaMemcpyAsync(h->v0, v0, 2 * n2, kind_in(mem), h->st), "copy v0");
   if (!rc) rc = cuda_check(h, cudaMemcpyAsync(h->v1, v1, 2 * n2, kind_in(mem), h->st), "copy v1");
+  if (!rc) rc = cuda_check(h, cudaEventRecord(h->evc, h->st), "copy event");
   if (rc) return rc;
   h->t0 = t0;
   h->t1 = t1;
@@ -759,7 +763,9 @@ extern "C" int mhd_set_driver(mhd_handle h, const void* bz, const void* v0, cons
     if (rc) return rc;
   }
   h->driver_set = true;
-  if (mem == MHD_MEM_HOST) rc = cuda_check(h, cudaStreamSynchronize(h->st), "driver synchronize");
+  // host buffers may be reused once the copies are done; the inversion
+  // runs on behind the return
+  if (mem == MHD_MEM_HOST) rc = cuda_check(h, cudaEventSynchronize(h->evc), "driver copies");
   return rc;
 }
 
