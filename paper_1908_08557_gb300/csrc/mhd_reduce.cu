@@ -1,8 +1,9 @@
 // mhd_reduce.cu -- FP64 reductions: the CFL time step and the global
 // diagnostics.  Per-cell values are formed in the state precision; block
-// partials and the grid-wide result are FP64.  Maxima are order independent;
-// sums are taken in a fixed order (per thread, warp tree, block, then one
-// block over the partials) so repeated runs give identical bits.
+// partials and the grid-wide result are FP64.  Maxima are order independent
+// (the CFL blocks combine theirs by atomicMax); sums are taken in a fixed
+// order (per thread, warp tree, block, then one block over the partials) so
+// repeated runs give identical bits.
 #include <float.h>
 #include "mhd_internal.h"
 
@@ -19,7 +20,8 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-// grid over (x tiles, y tiles, z chunks); each thread walks its z chunk
+// diagnostics grid over (x tiles of 64 cells, y tiles, z chunks); each
+// thread walks its z chunk
 static inline dim3 red_grid(const Layout& L, int* kchunk) {
   int tx = (L.nx + 63) / 64, ty = (L.ny + 7) / 8;
   int zc = 2432 / (tx * ty);  // about 16 blocks per SM
