@@ -54,6 +54,10 @@ PARAM_DEFAULTS = dict(
     bext_y=0.0,
     bext_z=0.0,
     bc_z=0,
+    # Newtonian cooling (Sect. 3.1): off in every named workload
+    nc_tau=0.0,
+    nc_lnrho_magn=8.0,
+    nc_lnrho_width=2.0,
 )
 
 
@@ -64,7 +68,7 @@ def scheme_params(nx: int, ny: int, nz: int, dx: float = 1.0, dy: float = 1.0,
     ztop = (nz - 1) * dz
     p.update(nx=int(nx), ny=int(ny), nz=int(nz), dx=float(dx), dy=float(dy),
              dz=float(dz), z_swamp_start=ztop - swamp_cells * dz,
-             z_swamp_end=ztop)
+             z_swamp_end=ztop, nc_z_max=10.0 * dz, nc_z_width=1.0 * dz)
     p.update(over)
     return p
 

@@ -55,6 +55,7 @@ def lib():
         ip = ctypes.POINTER(ctypes.c_int)
         _lib.or_fill_ghosts.argtypes = [ip, dp, dp, dp]
         _lib.or_fill_ghosts_nopfe.argtypes = [ip, dp, dp, dp]
+        _lib.or_set_nc_profile.argtypes = [ctypes.c_int, dp, dp]
         _lib.or_rhs.argtypes = [ip, dp, dp, dp, dp, dp, dp, ctypes.c_double,
                                 ctypes.c_double, ctypes.c_double, dp]
         _lib.or_cfl.argtypes = [ip, dp, dp]
@@ -84,8 +85,31 @@ def _dims(p: Dict) -> np.ndarray:
     return np.array([p["nx"], p["ny"], p["nz"], int(p.get("bc_z", 0))], dtype=np.int32)
 
 
+_NC_ORDER = ("nc_tau", "nc_lnrho_magn", "nc_lnrho_width", "nc_z_max", "nc_z_width")
+_nc_nz = [None]
+
+
+def _nc_default(p: Dict, k: str) -> float:
+    d = {"nc_tau": 0.0, "nc_lnrho_magn": 8.0, "nc_lnrho_width": 2.0,
+         "nc_z_max": 10.0 * float(p["dz"]), "nc_z_width": float(p["dz"])}
+    return float(p.get(k, d[k]))
+
+
 def _pvec(p: Dict) -> np.ndarray:
-    return np.array([float(p[k]) for k in _PARAM_ORDER], dtype=np.float64)
+    if _nc_default(p, "nc_tau") > 0.0 and _nc_nz[0] != int(p["nz"]):
+        raise ValueError("Newtonian cooling on: call set_nc_profile(lnrho0, lnT0) for this nz first")
+    return np.array([float(p[k]) for k in _PARAM_ORDER] + [_nc_default(p, k) for k in _NC_ORDER],
+                    dtype=np.float64)
+
+
+def set_nc_profile(lnrho0: np.ndarray, lnT0: np.ndarray) -> None:
+    """Initial ln rho, ln T profiles ([nz + 6], ghost layers included) that the
+    Newtonian cooling term (Sect. 3.1) relaxes toward."""
+    lr = np.ascontiguousarray(lnrho0, dtype=np.float64)
+    lt = np.ascontiguousarray(lnT0, dtype=np.float64)
+    nz = lr.shape[0] - 2 * NG
+    lib().or_set_nc_profile(int(nz), _d(lr), _d(lt))
+    _nc_nz[0] = nz
 
 
 def _i(a: np.ndarray):

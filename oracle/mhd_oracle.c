@@ -35,7 +35,8 @@ enum { F_AX, F_AY, F_AZ, F_UX, F_UY, F_UZ, F_LNRHO, F_LNTT, NFIELD };
 enum {
   P_DX, P_DY, P_DZ, P_GAMMA, P_GZ, P_NU, P_ETA, P_KAPPA0, P_DIFFRHO,
   P_ETA_S, P_CHI_S, P_DIFFRHO_S, P_ZS, P_ZT, P_TAU_U, P_TAU_A, P_T_RAMP,
-  P_FB, P_CADV, P_CDIFF, P_DT_FIXED, P_BEXT_X, P_BEXT_Y, P_BEXT_Z, NPARAM
+  P_FB, P_CADV, P_CDIFF, P_DT_FIXED, P_BEXT_X, P_BEXT_Y, P_BEXT_Z,
+  P_NC_TAU, P_NC_LMAG, P_NC_LW, P_NC_ZMAX, P_NC_ZW, NPARAM
 };
 
 typedef struct {
@@ -397,6 +398,57 @@ static void driver_weights(const double* p, double t0, double t1, double t,
  *          + chi_s w lap ln T                                       (Eq. 19)
  *  photosphere: dlnrho/dt = 0 (density held at its initial profile,
  *  Sect. 2.5), du_z/dt = 0 (closed); top layer: du_z/dt = 0 (Sect. 4). */
+/* ---- Newtonian cooling (Sect. 3.1, Eqs. 9-10) -------------------------
+ * Read as a relaxation of ln T: d ln T/dt += -tau (1 - T* / T) c_rho c_z,
+ * T* = sqrt(T0(z) T'(rho)), with T'(rho) the initial temperature T0(z') at
+ * the height z' where the initial density rho0(z') equals the local rho.
+ * The initial profiles over the interior layers are set once by
+ * or_set_nc_profile (arrays of nz + 6 entries, ghost layers included). */
+static double* nc_lr = NULL; /* ln rho0 at layers 0 .. nz-1 */
+static double* nc_lt = NULL; /* ln T0 at layers 0 .. nz-1 */
+static int nc_nz = 0;
+
+void or_set_nc_profile(int nz, const double* lnrho0, const double* lnT0) {
+  free(nc_lr);
+  free(nc_lt);
+  nc_lr = (double*)malloc(sizeof(double) * nz);
+  nc_lt = (double*)malloc(sizeof(double) * nz);
+  for (int k = 0; k < nz; ++k) {
+    nc_lr[k] = lnrho0[NG + k];
+    nc_lt[k] = lnT0[NG + k];
+  }
+  nc_nz = nz;
+}
+
+/* ln T'(rho): walk up the layers to the first segment [m, m+1] whose initial
+ * ln rho brackets L and interpolate ln T0 linearly there; below the bottom
+ * value or above the top one, the end layers. */
+static double nc_lnT_prime(double L) {
+  if (L >= nc_lr[0]) return nc_lt[0];
+  if (L <= nc_lr[nc_nz - 1]) return nc_lt[nc_nz - 1];
+  for (int m = 0; m + 1 < nc_nz; ++m) {
+    if (L <= nc_lr[m] && L >= nc_lr[m + 1]) {
+      double s = (L - nc_lr[m]) / (nc_lr[m + 1] - nc_lr[m]);
+      return nc_lt[m] + s * (nc_lt[m + 1] - nc_lt[m]);
+    }
+  }
+  return nc_lt[nc_nz - 1];
+}
+
+/* 1 up to x1 - w, 0 from x1 on, half a cosine period between */
+static double nc_cutoff(double x, double x1, double w) {
+  if (x <= x1 - w) return 1.0;
+  if (x >= x1) return 0.0;
+  return 0.5 * (1.0 + cos(M_PI * (x - (x1 - w)) / w));
+}
+
+static double nc_term(const double* p, int k, double lnrho, double lnT) {
+  double cz = nc_cutoff((double)k * p[P_DZ], p[P_NC_ZMAX], p[P_NC_ZW]);
+  double crho = nc_cutoff(nc_lr[0] - lnrho, p[P_NC_LMAG], p[P_NC_LW]);
+  double lnTstar = 0.5 * (nc_lt[k] + nc_lnT_prime(lnrho));
+  return -p[P_NC_TAU] * (1.0 - exp(lnTstar - lnT)) * crho * cz;
+}
+
 /* Right-hand side at one interior cell (k, j, i); out[8] in field order.
  * r, s: ramp and driver interpolation weight at the evaluation time. */
 static void rhs_cell(const grid_t* g, const double* u, const double* axt, const double* ayt,
@@ -494,6 +546,7 @@ static void rhs_cell(const grid_t* g, const double* u, const double* axt, const 
   double heat = (gam - 1.0) * (eta * J2 + 2.0 * rho * nu * S2) / (rho * T);
   double cond = (gam - 1.0) * kap * pow(T, 2.5) / rho * (lapT + 3.5 * gT2);
   double dTh = -ugT - (gam - 1.0) * divU + heat + cond + chi_s * w * lapT;
+  if (p[P_NC_TAU] > 0.0 && g->bcz == 0) dTh += nc_term(p, k, lnrho, lnT);
 
   if (g->bcz == 0) {
     if (k == 0) {
