@@ -90,6 +90,18 @@ typedef struct mhd_params {
   double c_adv, c_diff;/* CFL coefficients */
   double dt_fixed;     /* > 0: fixed time step instead of the CFL rule */
   double bext[3];      /* uniform external field added to curl A */
+  /* Newtonian cooling of the chromosphere (Sect. 3.1, Eqs. 9-10), read as a
+   * relaxation d ln T/dt += -nc_tau (1 - T* / T) c_rho c_z with
+   * T* = sqrt(T0(z) T'(rho)), T'(rho) = T0(z') where ln rho0(z') = ln rho
+   * (piecewise-linear inverse of the initial profile over the layers, clamped
+   * at its ends).  c_rho: 1 down to nc_lnrho_magn - nc_lnrho_width e-folds
+   * below the photospheric density, a cosine step to 0 at nc_lnrho_magn;
+   * c_z: 1 up to nc_z_max - nc_z_width, a cosine step to 0 at nc_z_max.
+   * nc_tau = 0 turns the term off; with nc_tau > 0 the initial ln rho profile
+   * must fall strictly with height. */
+  double nc_tau;       /* inverse relaxation time (the paper: 0.5 / s) */
+  double nc_lnrho_magn, nc_lnrho_width; /* density cut-off: 8 and 2 e-folds */
+  double nc_z_max, nc_z_width;          /* height cut-off (3 and 0.3 Mm) */
 } mhd_params;
 
 /* Diagnostics of the ghost-filled state at time t (FP64 sums). */

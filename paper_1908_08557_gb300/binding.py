@@ -62,7 +62,10 @@ class Params(ctypes.Structure):
                 ("tau_u", ctypes.c_double), ("tau_A", ctypes.c_double),
                 ("t_ramp", ctypes.c_double), ("f_pfe_bottom", ctypes.c_double),
                 ("c_adv", ctypes.c_double), ("c_diff", ctypes.c_double),
-                ("dt_fixed", ctypes.c_double), ("bext", ctypes.c_double * 3)]
+                ("dt_fixed", ctypes.c_double), ("bext", ctypes.c_double * 3),
+                ("nc_tau", ctypes.c_double), ("nc_lnrho_magn", ctypes.c_double),
+                ("nc_lnrho_width", ctypes.c_double), ("nc_z_max", ctypes.c_double),
+                ("nc_z_width", ctypes.c_double)]
 
 
 class Stats(ctypes.Structure):
@@ -151,6 +154,12 @@ def make_params(p: Dict, precision: int = 32, stats_every: int = 0, adjoint: boo
     q.bext[0], q.bext[1], q.bext[2] = (float(p.get("bext_x", 0.0)),
                                        float(p.get("bext_y", 0.0)),
                                        float(p.get("bext_z", 0.0)))
+    # Newtonian cooling: off unless nc_tau > 0
+    q.nc_tau = float(p.get("nc_tau", 0.0))
+    q.nc_lnrho_magn = float(p.get("nc_lnrho_magn", 8.0))
+    q.nc_lnrho_width = float(p.get("nc_lnrho_width", 2.0))
+    q.nc_z_max = float(p.get("nc_z_max", 10.0 * float(p["dz"])))
+    q.nc_z_width = float(p.get("nc_z_width", 1.0 * float(p["dz"])))
     return q
 
 

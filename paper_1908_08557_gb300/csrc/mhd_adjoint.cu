@@ -106,6 +106,7 @@ __global__ void __launch_bounds__(128) adj_point_kernel(AdjPointArgs<R> a) {
   R cf[NCOEF];
   adjoint_cell<R>(c, ph, a.wtab[k], a.wptab[k], wo, dt, k, L.nz, a.dbar + L.at(UX, 0, j, i),
                   a.dbar + L.at(UY, 0, j, i), L.sz(), a.thbar, q2, n2, a.ss, a.sub, cf);
+  if (k < ph.nc_k1) nc_adjoint<R>(ph, a.bg, L.nz, k, c.L, c.Th, wo[LT], cf);
   const long long n3 = n2 * L.nz, cq = (long long)k * n2 + q2;
   for (int q = 0; q < NCOEF; ++q) a.coef[q * n3 + cq] = cf[q];
 }

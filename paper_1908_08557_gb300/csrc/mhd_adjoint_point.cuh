@@ -213,4 +213,16 @@ __device__ __forceinline__ void adjoint_cell(const Cell<R>& c, const Phys<R>& ph
   cf[CV + UY] += vU1;
 }
 
+// Adjoint of the Newtonian cooling term of the ln T equation (Sect. 3.1):
+// its derivatives by ln T and ln rho, times the output adjoint of ln T, into
+// the value adjoints of the two.
+template <typename R>
+__device__ __forceinline__ void nc_adjoint(const Phys<R>& ph, const Background<R>& bg, int nz, int k, R L, R Th, R wT,
+                                           R (&cf)[NCOEF]) {
+  R dTh, dL;
+  nc_term<R>(ph, bg, nz, k, L, Th, &dTh, &dL);
+  cf[CV + LT] += wT * dTh;
+  cf[CV + LR] += wT * dL;
+}
+
 }  // namespace mhd

@@ -150,6 +150,9 @@ static const char* check_params(const mhd_params* p) {
     return "grid too large for the adjoint (8 (nz + 6) ny nx / 4 must stay below 2^31)";
   if ((long long)((p->nx + 31) / 32) * ((p->ny + 7) / 8) > RED_BLOCKS_MAX)
     return "horizontal grid too large for the reduction buffer (nx * ny <= 2^20)";
+  if (!(p->nc_tau >= 0.0)) return "nc_tau must be >= 0";
+  if (p->nc_tau > 0.0 && !(p->nc_lnrho_width > 0.0 && p->nc_lnrho_width <= p->nc_lnrho_magn && p->nc_z_width > 0.0))
+    return "Newtonian cooling needs 0 < nc_lnrho_width <= nc_lnrho_magn and nc_z_width > 0";
   return nullptr;
 }
 
@@ -264,6 +267,16 @@ static Phys<R> make_phys(const mhd_params* p) {
   ph.tau_A = (R)p->tau_A;
   for (int c = 0; c < 3; ++c) ph.bext[c] = (R)p->bext[c];
   ph.bcz = p->bc_z;
+  ph.nc_tau = (R)p->nc_tau;
+  ph.nc_lmag = (R)p->nc_lnrho_magn;
+  ph.nc_lw = (R)p->nc_lnrho_width;
+  ph.nc_zmax = (R)p->nc_z_max;
+  ph.nc_zw = (R)p->nc_z_width;
+  ph.dz = (R)p->dz;
+  // layers below the height cut-off (c_z(k dz) > 0); none when off
+  ph.nc_k1 = 0;
+  if (p->nc_tau > 0.0 && p->bc_z == 0)
+    while (ph.nc_k1 < p->nz && (double)ph.nc_k1 * p->dz < p->nc_z_max) ++ph.nc_k1;
   return ph;
 }
 
@@ -569,6 +582,10 @@ extern "C" int mhd_create(const mhd_params* p, void* workspace, size_t ws_bytes,
   if (bad) return fail(nullptr, MHD_ERR_ARG, "%s", bad);
   if (!init_state || !lnrho0) return fail(nullptr, MHD_ERR_ARG, "init_state and lnrho0 are required");
   if (mem != MHD_MEM_DEVICE && mem != MHD_MEM_HOST) return fail(nullptr, MHD_ERR_ARG, "bad mem flag");
+  if (p->nc_tau > 0.0)
+    for (int k = 0; k + 1 < p->nz; ++k)
+      if (!(lnrho0[NG + k + 1] < lnrho0[NG + k]))
+        return fail(nullptr, MHD_ERR_ARG, "Newtonian cooling needs ln rho0 falling strictly with height");
   Offsets o = plan_offsets(p);
   if (!workspace) return fail(nullptr, MHD_ERR_WORKSPACE, "workspace is NULL");
   if (((uintptr_t)workspace & 255u) != 0) return fail(nullptr, MHD_ERR_WORKSPACE, "workspace not 256-byte aligned");

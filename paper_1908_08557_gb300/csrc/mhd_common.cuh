@@ -53,6 +53,11 @@ struct Phys {
   R tau_u, tau_A;
   R bext[3];
   int bcz;
+  // Newtonian cooling (Sect. 3.1): rate, density cut-off (e-folds below the
+  // photospheric value, transition width), height cut-off (z_max, width),
+  // layer spacing; the term acts on layers k < nc_k1 (c_z > 0 there)
+  R nc_tau, nc_lmag, nc_lw, nc_zmax, nc_zw, dz;
+  int nc_k1;
 };
 
 // ln rho and ln T are stored as perturbations about fixed background
@@ -108,6 +113,66 @@ template <> __device__ __forceinline__ double rexp<double>(double x) { return ex
 template <typename R> __device__ __forceinline__ R rsqrt_(R x);
 template <> __device__ __forceinline__ float rsqrt_<float>(float x) { return sqrtf(x); }
 template <> __device__ __forceinline__ double rsqrt_<double>(double x) { return sqrt(x); }
+
+template <typename R> __device__ __forceinline__ R rcos(R x);
+template <> __device__ __forceinline__ float rcos<float>(float x) { return cosf(x); }
+template <> __device__ __forceinline__ double rcos<double>(double x) { return cos(x); }
+template <typename R> __device__ __forceinline__ R rsin(R x);
+template <> __device__ __forceinline__ float rsin<float>(float x) { return sinf(x); }
+template <> __device__ __forceinline__ double rsin<double>(double x) { return sin(x); }
+
+// Cosine step: 1 for x <= x1 - w, 0 for x >= x1, 0.5 (1 + cos(pi (x - x1 +
+// w) / w)) between; *d (if non-null) receives its derivative.
+template <typename R>
+__device__ __forceinline__ R nc_step(R x, R x1, R w, R* d) {
+  if (d) *d = R(0);
+  if (x <= x1 - w) return R(1);
+  if (x >= x1) return R(0);
+  const R pw = R(3.14159265358979323846) / w;
+  const R a = pw * (x - x1 + w);
+  if (d) *d = R(-0.5) * pw * rsin<R>(a);
+  return R(0.5) * (R(1) + rcos<R>(a));
+}
+
+// Newtonian cooling (Sect. 3.1, Eqs. 9-10, read as a relaxation of ln T):
+// the d ln T/dt term -tau (1 - T*/T) c_rho c_z at layer k for the full
+// ln rho = L and ln T = Th, with T* = sqrt(T0(z) T'(rho)) and T'(rho) = T0(z')
+// where the initial ln rho profile (bg.lbar, falling with height) equals L,
+// by the piecewise-linear inverse over the interior layers (clamped at the
+// end layers).  c_rho cuts off nc_lmag e-folds below the photospheric
+// density, c_z above nc_zmax, each through a cosine step.  With dTh, dL
+// non-null, also the derivatives of the term (for the adjoint).
+template <typename R>
+__device__ __forceinline__ R nc_term(const Phys<R>& ph, const Background<R>& bg, int nz, int k, R L, R Th, R* dTh,
+                                     R* dL) {
+  const R* lr = bg.lbar + NG;
+  const R* lt = bg.tbar + NG;
+  R dcr = R(0);
+  const R cz = nc_step<R>(R(k) * ph.dz, ph.nc_zmax, ph.nc_zw, nullptr);
+  const R cr = nc_step<R>(lr[0] - L, ph.nc_lmag, ph.nc_lw, dL ? &dcr : nullptr);
+  R lnTp, slope = R(0);
+  if (L >= lr[0]) {
+    lnTp = lt[0];
+  } else if (L <= lr[nz - 1]) {
+    lnTp = lt[nz - 1];
+  } else {
+    int lo = 0, hi = nz - 1;  // lr[lo] >= L > lr[hi]
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (lr[mid] >= L) lo = mid; else hi = mid;
+    }
+    const R s = (L - lr[lo]) / (lr[hi] - lr[lo]);
+    lnTp = lt[lo] + s * (lt[hi] - lt[lo]);
+    slope = (lt[hi] - lt[lo]) / (lr[hi] - lr[lo]);
+  }
+  const R r = rexp<R>(R(0.5) * (lt[k] + lnTp) - Th);  // T*/T
+  const R c = cr * cz;
+  if (dTh) *dTh = -ph.nc_tau * c * r;
+  // d/dL: T*/T through ln T'(L); c_rho through its argument lr[0] - L
+  if (dL) *dL = -ph.nc_tau * cz * (-r * R(0.5) * slope * cr - (R(1) - r) * dcr);
+  return -ph.nc_tau * (R(1) - r) * c;
+}
+
 
 // Sixth-order centred stencil weights.
 template <typename R> struct W {

@@ -117,6 +117,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 8 ? 2 : 0) rk_simple_kernel(
   c.lapT += a.bg.d2t[k];
   R out[NF];
   rhs_point<R>(c, ph, a.wtab[k], a.wptab[k], out);
+  if (k < ph.nc_k1) out[LT] += nc_term<R>(ph, a.bg, L.nz, k, c.L, c.Th, nullptr, nullptr);
 
   // substep constants
   const int sub = a.sub;

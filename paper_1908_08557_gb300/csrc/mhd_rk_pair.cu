@@ -240,6 +240,14 @@ __device__ __forceinline__ void adjoint_centre(const Args& a, const float* Pk, c
     if (pf.bcz == 0 && k == L.nz - 1) wo[UZ] = P2(0.f);
     P2 cf[NCOEF];
     rhs_point_adjoint<P2>(cl, pp, P2(wk), P2(wpk), wo, cf);
+    if (k < pf.nc_k1) {
+      // Newtonian cooling, one cell at a time
+      float dT0, dL0, dT1, dL1;
+      nc_term<float>(pf, a.bg, L.nz, k, cl.L.v.x, cl.Th.v.x, &dT0, &dL0);
+      nc_term<float>(pf, a.bg, L.nz, k, cl.L.v.y, cl.Th.v.y, &dT1, &dL1);
+      cf[CV + LT] += wo[LT] * P2(make_float2(dT0, dT1));
+      cf[CV + LR] += wo[LT] * P2(make_float2(dL0, dL1));
+    }
     float* co = a.coef + (long long)k * n2 + (long long)j * L.nx + i;
 #pragma unroll
     for (int q = 0; q < NCOEF; ++q) *reinterpret_cast<f2*>(co + q * n3) = cf[q].v;
@@ -277,6 +285,7 @@ __device__ __forceinline__ void adjoint_centre(const Args& a, const float* Pk, c
     float cf[NCOEF];
     adjoint_cell<float>(cl, a.ph, wk, wpk, wo, dt, k, L.nz, a.dbar + cu, a.dbar + cu + L.fs, L.sz(), a.thbar, q2,
                         n2, a.ss, sub, cf);
+    if (k < a.ph.nc_k1) nc_adjoint<float>(a.ph, a.bg, L.nz, k, cl.L, cl.Th, wo[LT], cf);
     float* co = a.coef + (long long)k * n2 + q2;
 #pragma unroll
     for (int q = 0; q < NCOEF; ++q) co[q * n3] = cf[q];
@@ -641,6 +650,9 @@ __global__ void __launch_bounds__(NT, 2) rk_pair_kernel(const __grid_constant__ 
         const f2 kt = mul(F2(ph.gm1 * ph.kappa0), make_float2(expf(ka.x), expf(ka.y)));
         out[LT] = add(add(dif(heat, fma2(gm1, divU, ugT)), mul(kt, fma2(F2(3.5f), gTs, lapT))),
                       mul(mul(F2(ph.chi_s), w), lapT));
+        if (k < ph.nc_k1)  // Newtonian cooling, one cell at a time
+          out[LT] = add(out[LT], make_float2(nc_term<float>(ph, a.bg, L.nz, k, Lr.x, Th.x, nullptr, nullptr),
+                                             nc_term<float>(ph, a.bg, L.nz, k, Lr.y, Th.y, nullptr, nullptr)));
 
         // ---- nudging and boundary rows -----------------------------------------
         f2 tgx = F2(0.f), tgy = F2(0.f);

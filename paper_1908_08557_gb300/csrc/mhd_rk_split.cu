@@ -402,6 +402,7 @@ __global__ void __launch_bounds__(TILE, 2) pass_r_kernel(const __grid_constant__
         c.lapT = d[RT].xx + d[RT].yy + d[RT].zz + a.bg.d2t[k];
         float out[NF];
         rhs_point_bj<float>(c, a.ph, a.wtab[k], B, J, sw, out);
+        if (k < a.ph.nc_k1) out[LT] += nc_term<float>(a.ph, a.bg, L.nz, k, c.L, c.Th, nullptr, nullptr);
 
         float tgx = 0.f, tgy = 0.f;
         const Phys<float>& ph = a.ph;

@@ -293,6 +293,7 @@ __global__ void __launch_bounds__(TILE, 1) rk_tiled_kernel(const __grid_constant
           const long long cu = L.at(UX, 0, j, i);
           adjoint_cell<float>(c, a.ph, a.wtab[k], a.wptab[k], wo, dt, k, L.nz, a.dbar + cu, a.dbar + cu + L.fs,
                               L.sz(), a.thbar, q2, n2, a.ss, sub, cf);
+          if (k < a.ph.nc_k1) nc_adjoint<float>(a.ph, a.bg, L.nz, k, c.L, c.Th, wo[LT], cf);
           float* co = a.coef + (long long)k * n2 + q2;
           const long long n3 = n2 * L.nz;
 #pragma unroll
@@ -300,6 +301,7 @@ __global__ void __launch_bounds__(TILE, 1) rk_tiled_kernel(const __grid_constant
         } else {
           float out[NF];
           rhs_point<float>(c, a.ph, a.wtab[k], a.wptab[k], out);
+          if (k < a.ph.nc_k1) out[LT] += nc_term<float>(a.ph, a.bg, L.nz, k, c.L, c.Th, nullptr, nullptr);
 
           float tgx = 0.f, tgy = 0.f;
           const Phys<float>& ph = a.ph;

@@ -263,6 +263,68 @@ def test_minimum_size_run(precision):
     assert abs(sim.time()[0] - t) <= (1e-12 if precision == 64 else 1e-5) * t
 
 
+NC = dict(nc_tau=0.5, nc_z_max=10.0, nc_z_width=3.0)
+
+
+def _cooling_case(nx, ny, nz, seed):
+    """A perturbed box with Newtonian cooling on (Sect. 3.1); ln rho is
+    perturbed too, so the local densities fall between the layers' initial
+    values and the inverse lookup interpolates."""
+    case = _perturbed(nx, ny, nz, seed=seed)
+    rng = np.random.default_rng(seed + 300)
+    case.state[6] += 0.05 * rng.standard_normal(case.state[6].shape)
+    case.params = dict(case.params, **NC)
+    oracle.set_nc_profile(case.lnrho0, case.lnT0)
+    return case
+
+
+@pytest.mark.parametrize("variant", ["fp64", "pair", "tiled", "fused", "simple"])
+def test_cooling_rhs(variant):
+    """Right-hand side with Newtonian cooling against the oracle: the FP64
+    kernel to 1e-11 of each field's scale, each FP32 kernel to 2e-4."""
+    case = _cooling_case(16, 16, 16, seed=21)
+    p = case.params
+    t = 0.31
+    if variant == "fp64":
+        sim = _sim(case, 64)
+        sim.fill_ghosts()
+        got = sim.eval_rhs(t)
+        u = sim.read_padded(0).astype(np.float64)
+        sim.close()
+        axt, ayt = oracle.a_target(p, case.bz)
+        v0, v1, tol = case.v0, case.v1, 1e-11
+    else:
+        got, u = _eval_with_variant(case, variant, t=t)
+        cast = lambda a: a.astype(np.float32).astype(np.float64)
+        axt, ayt = (cast(a) for a in oracle.a_target(p, case.bz))
+        v0, v1, tol = cast(case.v0), cast(case.v1), 2e-4
+    ref = oracle.rhs(p, u, axt, ayt, v0, v1, case.t0, case.t1, t)
+    for f in range(8):
+        s = np.abs(ref[f]).max()
+        e = np.abs(got[f] - ref[f]).max()
+        assert e <= tol * max(s, 1e-30), (f, e, s)
+    # the term is active: the same state without it differs in ln T only
+    off = oracle.rhs(dict(p, nc_tau=0.0), u, axt, ayt, v0, v1, case.t0, case.t1, t)
+    assert np.abs(off[7] - ref[7]).max() > 1e-4
+    assert all(np.array_equal(off[f], ref[f]) for f in range(7))
+
+
+@pytest.mark.parametrize("precision,tol", [(64, 1e-11), (32, 1e-4)])
+def test_cooling_full_run(precision, tol):
+    """Workload spots4_32x32x32 with Newtonian cooling on (rate 0.5, height
+    cut-off over layers 7-10): 50 steps against the oracle."""
+    case = inputs.make_case("spots4_32x32x32")
+    p = dict(case.params, **NC)
+    oracle.set_nc_profile(case.lnrho0, case.lnT0)
+    sim = _sim(case, precision, params=p)
+    sim.step(case.nsteps)
+    got = sim.read().cpu().numpy().astype(np.float64)
+    u, t, dts = oracle.run_case(case, params=p)
+    ref = oracle.interior(u)
+    errs = [_rel_l2(got[f], ref[f]) for f in range(8)]
+    assert max(errs) <= tol, errs
+
+
 def test_nonfinite_detected():
     from paper_1908_08557_gb300 import MHDError
     from paper_1908_08557_gb300.binding import MHD_ERR_NONFINITE
