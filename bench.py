@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--drift", action="store_true",
                     help="also run ar_1024x1024x256 in FP32 and FP64 and compare energies, fluxes and fields")
     ap.add_argument("--drift-steps", type=int, default=100)
+    ap.add_argument("--cooling", action="store_true",
+                    help="Newtonian cooling on (rate 0.5, height cut-off at 10 dz) in the throughput leg")
     return ap.parse_args()
 
 
@@ -489,6 +491,8 @@ def run_native(args, ws, rank, local):
     build()  # no-op when up to date
 
     case = inputs.make_case(args.workload)
+    if args.cooling:
+        case.params = dict(case.params, nc_tau=0.5)
     p = case.params
     cells = p["nx"] * p["ny"] * p["nz"]
     dev = torch.device("cuda", local)
@@ -629,6 +633,7 @@ def run_native(args, ws, rank, local):
                 "config": {"workload": args.workload, "nx": p["nx"], "ny": p["ny"], "nz": p["nz"],
                            "precision": "fp32 state and stencils; fp64 FFT, CFL and diagnostics",
                            "stats_every": args.stats_every,
+                           "newton_cooling": bool(args.cooling),
                            "l2": f"working set {state_gb:.2f} GB > 129 MB L2, no flush",
                            "parallelism": f"replicas x{ws}"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,

@@ -298,7 +298,9 @@ __device__ __forceinline__ void adjoint_centre(const Args& a, const float* Pk, c
 // `sub` (the input is the ghost-filled substep state, tmd maps D): per
 // interior cell the NCOEF coefficients of the transposed right-hand side and,
 // at the photosphere, the driver adjoints; no state is stored.
-template <bool ADJ>
+// NC: the forward right-hand side includes the Newtonian cooling term (a
+// separate instantiation, so that the default path carries none of it)
+template <bool ADJ, bool NC>
 __global__ void __launch_bounds__(NT, 2) rk_pair_kernel(const __grid_constant__ CUtensorMap tm,
                                                         const __grid_constant__ CUtensorMap tmd, const Args a) {
   extern __shared__ __align__(128) float smem[];
@@ -650,9 +652,11 @@ __global__ void __launch_bounds__(NT, 2) rk_pair_kernel(const __grid_constant__ 
         const f2 kt = mul(F2(ph.gm1 * ph.kappa0), make_float2(expf(ka.x), expf(ka.y)));
         out[LT] = add(add(dif(heat, fma2(gm1, divU, ugT)), mul(kt, fma2(F2(3.5f), gTs, lapT))),
                       mul(mul(F2(ph.chi_s), w), lapT));
-        if (k < ph.nc_k1)  // Newtonian cooling, one cell at a time
-          out[LT] = add(out[LT], make_float2(nc_term<float>(ph, a.bg, L.nz, k, Lr.x, Th.x, nullptr, nullptr),
-                                             nc_term<float>(ph, a.bg, L.nz, k, Lr.y, Th.y, nullptr, nullptr)));
+        if constexpr (NC) {
+          if (k < ph.nc_k1)  // Newtonian cooling, one cell at a time
+            out[LT] = add(out[LT], make_float2(nc_term<float>(ph, a.bg, L.nz, k, Lr.x, Th.x, nullptr, nullptr),
+                                               nc_term<float>(ph, a.bg, L.nz, k, Lr.y, Th.y, nullptr, nullptr)));
+        }
 
         // ---- nudging and boundary rows -----------------------------------------
         f2 tgx = F2(0.f), tgy = F2(0.f);
@@ -753,9 +757,11 @@ bool rk_pair_supported(const Layout& L) { return L.nx % 2 == 0 && L.nx >= 8 && L
 static pair::Args pair_args(const Layout& L, const Phys<float>& ph, const Background<float>& bg, const float* wtab,
                             const float* wptab, StepState* ss, int sub, double dx, double dy, double dz) {
   if (!g_pair_ctas) {
-    cudaFuncSetAttribute(pair::rk_pair_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(pair::rk_pair_kernel<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)pair::SMEM_BYTES);
-    cudaFuncSetAttribute(pair::rk_pair_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(pair::rk_pair_kernel<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)pair::SMEM_BYTES);
+    cudaFuncSetAttribute(pair::rk_pair_kernel<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)pair::SMEM_BYTES);
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
@@ -807,7 +813,10 @@ void launch_rk_pair(const CUtensorMap* tm, const CUtensorMap* tmd, const Layout&
   a.v1 = (const float*)drv.v1;
   const int nitems = a.ntx * a.nty * a.nch;
   const int grid = nitems < g_pair_ctas ? nitems : g_pair_ctas;
-  pair::rk_pair_kernel<false><<<grid, pair::NT, pair::SMEM_BYTES, st>>>(*tm, *tmd, a);
+  if (ph.nc_k1 > 0)
+    pair::rk_pair_kernel<false, true><<<grid, pair::NT, pair::SMEM_BYTES, st>>>(*tm, *tmd, a);
+  else
+    pair::rk_pair_kernel<false, false><<<grid, pair::NT, pair::SMEM_BYTES, st>>>(*tm, *tmd, a);
 }
 
 void launch_adj_point_pair(const CUtensorMap* tm, const CUtensorMap* tmd, const Layout& L, const Phys<float>& ph,
@@ -820,7 +829,7 @@ void launch_adj_point_pair(const CUtensorMap* tm, const CUtensorMap* tmd, const 
   a.thbar = thbar;
   const int nitems = a.ntx * a.nty * a.nch;
   const int grid = nitems < g_pair_ctas ? nitems : g_pair_ctas;
-  pair::rk_pair_kernel<true><<<grid, pair::NT, pair::SMEM_BYTES, st>>>(*tm, *tmd, a);
+  pair::rk_pair_kernel<true, false><<<grid, pair::NT, pair::SMEM_BYTES, st>>>(*tm, *tmd, a);
 }
 
 }  // namespace mhd
