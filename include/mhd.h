@@ -153,7 +153,11 @@ int mhd_set_driver(mhd_handle h, const void* bz, const void* v0,
 
 /* Advance the state by nsteps full RK3 steps (three substeps each: ghost
  * fill, potential-field FFT, fused right-hand side + RK update; the time step
- * from the FP64 CFL reduction at the first substep).  Asynchronous. */
+ * from the FP64 CFL reduction at the first substep).  Asynchronous; no host
+ * synchronisation, so the calls may be captured into a CUDA graph on the
+ * handle's stream.  Each substep swaps the two state sets on the host: a
+ * graph replays correctly when it holds an even number of steps, and the
+ * diagnostics schedule (stats_every) is the one seen at capture. */
 int mhd_step(mhd_handle h, int nsteps);
 
 /* Copy the interior of one field (0..7) or of all fields (-1) into dst

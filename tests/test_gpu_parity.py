@@ -325,6 +325,40 @@ def test_cooling_full_run(precision, tol):
     assert max(errs) <= tol, errs
 
 
+def test_steps_captured_in_a_cuda_graph():
+    """Two RK steps captured in a CUDA graph on the handle's stream (the
+    substep-0 FFT forks to the side stream and joins back inside the capture)
+    and replayed twice equal four eagerly launched steps bit for bit: the
+    time step, substep times and driver weights live on the device, and two
+    steps (six substeps) return the ping-pong state sets to where they were."""
+    from paper_1908_08557_gb300 import Simulation
+    case = inputs.make_case("spots4_32x32x32")
+    s = torch.cuda.Stream()
+
+    def make(stream):
+        sim = Simulation(case.params, torch.tensor(case.state, dtype=torch.float32, device="cuda"), case.lnrho0,
+                         case.lnT0, precision=32, stream=stream)
+        sim.set_driver(torch.tensor(case.bz, dtype=torch.float32, device="cuda"),
+                       torch.tensor(case.v0, dtype=torch.float32, device="cuda"),
+                       torch.tensor(case.v1, dtype=torch.float32, device="cuda"), case.t0, case.t1)
+        return sim
+
+    sg, se = make(s), make(None)
+    with torch.cuda.stream(s):
+        sg.step(2)  # first launches (one-time kernel attributes) outside the capture
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        sg.step(2)
+    g.replay()
+    g.replay()
+    torch.cuda.synchronize()
+    se.step(6)
+    torch.cuda.synchronize()
+    assert torch.equal(sg.read(), se.read())
+    assert sg.time()[0] == se.time()[0]
+
+
 def test_nonfinite_detected():
     from paper_1908_08557_gb300 import MHDError
     from paper_1908_08557_gb300.binding import MHD_ERR_NONFINITE
