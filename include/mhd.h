@@ -28,9 +28,11 @@
  * - Every launch is ordered on the stream given to mhd_create(); calls are
  *   asynchronous unless stated otherwise.  With the potential-field boundary,
  *   the FFT of each step's first substep runs on a library-owned
- *   highest-priority stream that is forked from and joined back to that
- *   stream by events (created by mhd_create, released by mhd_destroy), so the
- *   caller's stream still orders all of the handle's work.
+ *   highest-priority stream, and the FFTs of the three packed boundary
+ *   planes run side by side on it and two more such streams; all are forked
+ *   from and joined back to that stream by events (created by mhd_create,
+ *   released by mhd_destroy), so the caller's stream still orders all of the
+ *   handle's work.
  * - Return value: MHD_OK (0) or a negative MHD_ERR_* code; the message is
  *   available from mhd_last_error().  Argument errors are reported before any
  *   launch.  A non-finite value met by the time-step reduction (or a device

@@ -37,6 +37,7 @@ struct mhd_ctx {
                        // forked from and joined to `st` by events (FFT boundary only)
   cudaEvent_t evf, evj;
   cudaEvent_t evc;     // end of the host-to-device driver copies (mhd_set_driver)
+  PlaneStreams ps;     // two more FFT streams (planes 1, 2 of the potential-field boundary)
   size_t esz;          // bytes per state element
   char* ws;
   size_t ws_bytes;
@@ -392,11 +393,22 @@ static void ghost_fill(mhd_ctx* h, R* f) {
   }
   if (h->p.bc_z == 0) {
     ClassTimer ct(h, MHD_KC_PFE, 3);
-    launch_pfe<R>(h->fp, h->L, f, h->ss, h->st);
+    launch_pfe<R>(h->fp, h->L, f, h->ss, h->st, &h->ps);
   }
 }
 
 static void release_side(mhd_ctx* h) {
+  for (int i = 0; i < 2; ++i) {
+    if (h->ps.s[i]) {
+      cudaStreamSynchronize(h->ps.s[i]);
+      cudaStreamDestroy(h->ps.s[i]);
+    }
+    if (h->ps.join[i]) cudaEventDestroy(h->ps.join[i]);
+    h->ps.s[i] = nullptr;
+    h->ps.join[i] = nullptr;
+  }
+  if (h->ps.fork) cudaEventDestroy(h->ps.fork);
+  h->ps.fork = nullptr;
   if (h->side) cudaStreamSynchronize(h->side);
   if (h->evf) cudaEventDestroy(h->evf);
   if (h->evj) cudaEventDestroy(h->evj);
@@ -468,7 +480,7 @@ static void run_step(mhd_ctx* h, bool stats) {
       cudaStreamWaitEvent(h->side, h->evf, 0);
       {
         ClassTimer ct(h, MHD_KC_PFE, 3, h->side);
-        launch_pfe<R>(h->fp, h->L, fin, h->ss, h->side);
+        launch_pfe<R>(h->fp, h->L, fin, h->ss, h->side, &h->ps);
       }
       cudaEventRecord(h->evj, h->side);
       {
@@ -673,6 +685,11 @@ extern "C" int mhd_create(const mhd_params* p, void* workspace, size_t ws_bytes,
     rc = cuda_check(h, cudaStreamCreateWithPriority(&h->side, cudaStreamNonBlocking, hi), "side stream");
     if (!rc) rc = cuda_check(h, cudaEventCreateWithFlags(&h->evf, cudaEventDisableTiming), "fork event");
     if (!rc) rc = cuda_check(h, cudaEventCreateWithFlags(&h->evj, cudaEventDisableTiming), "join event");
+    for (int i = 0; i < 2 && !rc; ++i) {
+      rc = cuda_check(h, cudaStreamCreateWithPriority(&h->ps.s[i], cudaStreamNonBlocking, hi), "plane stream");
+      if (!rc) rc = cuda_check(h, cudaEventCreateWithFlags(&h->ps.join[i], cudaEventDisableTiming), "plane event");
+    }
+    if (!rc) rc = cuda_check(h, cudaEventCreateWithFlags(&h->ps.fork, cudaEventDisableTiming), "plane event");
   }
   if (!rc) rc = cuda_check(h, cudaEventCreateWithFlags(&h->evc, cudaEventDisableTiming), "copy event");
   if (!rc && h->tiled) {

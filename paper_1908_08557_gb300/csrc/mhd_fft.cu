@@ -111,7 +111,7 @@ __global__ void __launch_bounds__(256) rows_fwd_kernel(FFTPlan fp, Layout L, con
   if (ss && halted(ss)) return;
   const int nx = fp.nx, ny = fp.ny;
   const int y0 = blockIdx.x * nb;
-  const int p = blockIdx.y;
+  const int p = fp.p0 + blockIdx.y;
   double2* a = sm;
   double2* b = sm + nb * nx;
   const int kt = L.nz - 1;
@@ -167,7 +167,7 @@ __global__ void __launch_bounds__(256) cols_kernel(FFTPlan fp, int mode, const S
   const int pair0 = blockIdx.x * ppb;  // ppb column pairs per block
   const int np = min(ppb, npairs - pair0);
   const int nl = 2 * np;
-  const int p = blockIdx.y;
+  const int p = fp.p0 + blockIdx.y;
   const int nout = mode == 0 ? 3 : 1;
   const int npts = nl * ny;            // points of one layer
   const int bsz = lg * 2 * ppb * ny;   // points of one buffer
@@ -263,7 +263,7 @@ __global__ void __launch_bounds__(256) rows_inv_kernel(FFTPlan fp, Layout L, R* 
   if (ss && halted(ss)) return;
   const int nx = fp.nx, ny = fp.ny;
   const int y0 = blockIdx.x * nb;
-  const int p = blockIdx.y, o = blockIdx.z;
+  const int p = fp.p0 + blockIdx.y, o = blockIdx.z;
   const int nplanes = mode == 0 ? 3 : (mode == 2 ? 3 : 1);
   double2* a = sm;
   double2* b = sm + nb * nx;
@@ -443,16 +443,40 @@ static RowsCfg rows_cfg(const FFTPlan& fp, int planes) {
 }
 
 template <typename R>
-void launch_pfe(const FFTPlan& fp, const Layout& L, R* f, const StepState* ss, cudaStream_t st) {
+void launch_pfe(const FFTPlan& fp, const Layout& L, R* f, const StepState* ss, cudaStream_t st,
+                const PlaneStreams* ps) {
   set_smem_once();
   const FFTLaunch l = fft_launch(fp);
   const int npairs = fp.nx / 2 + 1;
-  const RowsCfg rf = rows_cfg(fp, 3), ri = rows_cfg(fp, 9);
-  rows_fwd_kernel<R><<<dim3(fp.ny / rf.nb, 3), rf.threads, rf.smem, st>>>(fp, L, f, nullptr, 0, ss, rf.nb, nullptr,
-                                                                          nullptr);
-  cols_kernel<<<dim3((npairs + l.ppb - 1) / l.ppb, 3), 256, l.smem_cols3, st>>>(fp, 0, ss, l.ppb, l.lg);
-  rows_inv_kernel<R><<<dim3(fp.ny / ri.nb, 3, 3), ri.threads, ri.smem, st>>>(fp, L, f, nullptr, nullptr, 0, ss,
-                                                                            ri.nb);
+  if (!ps) {
+    const RowsCfg rf = rows_cfg(fp, 3), ri = rows_cfg(fp, 9);
+    rows_fwd_kernel<R><<<dim3(fp.ny / rf.nb, 3), rf.threads, rf.smem, st>>>(fp, L, f, nullptr, 0, ss, rf.nb,
+                                                                            nullptr, nullptr);
+    cols_kernel<<<dim3((npairs + l.ppb - 1) / l.ppb, 3), 256, l.smem_cols3, st>>>(fp, 0, ss, l.ppb, l.lg);
+    rows_inv_kernel<R><<<dim3(fp.ny / ri.nb, 3, 3), ri.threads, ri.smem, st>>>(fp, L, f, nullptr, nullptr, 0, ss,
+                                                                              ri.nb);
+    return;
+  }
+  // one chain (rows, columns, inverse rows) per packed plane, on its own
+  // stream: the chains share no data, and running them side by side fills
+  // the SMs' FP64 pipes where one launch's tail would leave them idle
+  const RowsCfg rf = rows_cfg(fp, 1), ri = rows_cfg(fp, 3);
+  cudaEventRecord(ps->fork, st);
+  for (int i = 0; i < 2; ++i) cudaStreamWaitEvent(ps->s[i], ps->fork, 0);
+  for (int p = 0; p < 3; ++p) {
+    cudaStream_t sp = p == 0 ? st : ps->s[p - 1];
+    FFTPlan fq = fp;
+    fq.p0 = p;
+    rows_fwd_kernel<R><<<dim3(fp.ny / rf.nb, 1), rf.threads, rf.smem, sp>>>(fq, L, f, nullptr, 0, ss, rf.nb,
+                                                                            nullptr, nullptr);
+    cols_kernel<<<dim3((npairs + l.ppb - 1) / l.ppb, 1), 256, l.smem_cols3, sp>>>(fq, 0, ss, l.ppb, l.lg);
+    rows_inv_kernel<R><<<dim3(fp.ny / ri.nb, 1, 3), ri.threads, ri.smem, sp>>>(fq, L, f, nullptr, nullptr, 0, ss,
+                                                                              ri.nb);
+  }
+  for (int i = 0; i < 2; ++i) {
+    cudaEventRecord(ps->join[i], ps->s[i]);
+    cudaStreamWaitEvent(st, ps->join[i], 0);
+  }
 }
 
 template <typename R>
@@ -505,8 +529,10 @@ template void launch_pfe_adjoint<float>(const FFTPlan&, const Layout&, float*, c
 template void launch_pfe_adjoint<double>(const FFTPlan&, const Layout&, double*, const StepState*, cudaStream_t);
 template void launch_atarget_adjoint<float>(const FFTPlan&, const double*, const double*, float*, cudaStream_t);
 template void launch_atarget_adjoint<double>(const FFTPlan&, const double*, const double*, double*, cudaStream_t);
-template void launch_pfe<float>(const FFTPlan&, const Layout&, float*, const StepState*, cudaStream_t);
-template void launch_pfe<double>(const FFTPlan&, const Layout&, double*, const StepState*, cudaStream_t);
+template void launch_pfe<float>(const FFTPlan&, const Layout&, float*, const StepState*, cudaStream_t,
+                                const PlaneStreams*);
+template void launch_pfe<double>(const FFTPlan&, const Layout&, double*, const StepState*, cudaStream_t,
+                                 const PlaneStreams*);
 template void launch_atarget<float>(const FFTPlan&, const float*, float*, float*, cudaStream_t);
 template void launch_atarget<double>(const FFTPlan&, const double*, double*, double*, cudaStream_t);
 

@@ -17,6 +17,14 @@ struct FFTPlan {
   const double* kty;   // [ny]
   double2* P;          // [3][nx][ny] row spectra, transposed
   double2* Q;          // [3][3][nx][ny] extrapolated spectra, transposed
+  int p0;              // first plane of a launch (blockIdx.y offset; 0 unless planes run apart)
+};
+
+// three streams for the potential-field planes of one substep: the caller's
+// and two more, forked from and joined back to it
+struct PlaneStreams {
+  cudaStream_t s[2];
+  cudaEvent_t fork, join[2];
 };
 
 struct Driver {
@@ -39,8 +47,9 @@ template <typename R> void launch_init_u_ghosts(const Layout& L, R* f, cudaStrea
 template <typename R> void launch_bc(const Layout& L, const Phys<R>& ph, const Background<R>& bg, R* f,
                                      R dz, const StepState* ss, cudaStream_t st);
 // potential-field ghosts of A (three FFT kernels)
+// (ps: run the three planes on three streams; nullptr: one stream)
 template <typename R> void launch_pfe(const FFTPlan& fp, const Layout& L, R* f, const StepState* ss,
-                                      cudaStream_t st);
+                                      cudaStream_t st, const PlaneStreams* ps = nullptr);
 // vector potential of the target magnetogram into axt, ayt
 template <typename R> void launch_atarget(const FFTPlan& fp, const R* bz, R* axt, R* ayt, cudaStream_t st);
 // fused right-hand side + RK update; sub = 0,1,2, or -1 to write the raw RHS into df

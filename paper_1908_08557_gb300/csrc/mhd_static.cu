@@ -112,6 +112,7 @@ extern "C" int mhd_invert_magnetogram_static(int nx, int ny, double dx, double d
   }
   cudaStream_t st = (cudaStream_t)stream;
   FFTPlan fp;
+  fp.p0 = 0;
   fp.nx = nx;
   fp.ny = ny;
   fp.lognx = 0;
