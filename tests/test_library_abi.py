@@ -60,3 +60,23 @@ def test_workspace_sizing_and_argument_errors(lib):
                         None, ctypes.byref(h))
     assert rc == binding.MHD_ERR_WORKSPACE   # misaligned
     assert lib.mhd_step(None, 1) == binding.MHD_ERR_ARG
+
+
+def test_cooling_parameter_errors(lib):
+    """Newtonian cooling (Sect. 3.1): invalid rates and cut-off widths are
+    rejected before any allocation, and so is an initial ln rho profile that
+    does not fall strictly with height (its inverse is the lookup of T')."""
+    import inputs
+    from paper_1908_08557_gb300 import binding
+    p = inputs.scheme_params(32, 32, 32, nc_tau=0.5)
+    ok = binding.make_params(p, 32)
+    assert lib.mhd_workspace_bytes(ctypes.byref(ok)) > 0
+    for over in (dict(nc_tau=-0.1), dict(nc_lnrho_width=9.0), dict(nc_lnrho_width=0.0), dict(nc_z_width=0.0)):
+        bad = binding.make_params(dict(p, **over), 32)
+        assert lib.mhd_workspace_bytes(ctypes.byref(bad)) == 0, over
+    h = ctypes.c_void_p()
+    flat = (ctypes.c_double * 38)()  # ln rho0 = 0 everywhere: not strictly falling
+    rc = lib.mhd_create(ctypes.byref(ok), ctypes.c_void_p(256), 1 << 40, ctypes.c_void_p(1), 0, flat, None, None,
+                        ctypes.byref(h))
+    assert rc == binding.MHD_ERR_ARG and not h.value
+    assert b"falling strictly" in lib.mhd_last_error(None)
