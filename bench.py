@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--drift", action="store_true",
                     help="also run ar_1024x1024x256 in FP32 and FP64 and compare energies, fluxes and fields")
     ap.add_argument("--drift-steps", type=int, default=100)
+    ap.add_argument("--granulation", action="store_true",
+                    help="also time the granulation driver on a 1024 x 1024 plane (Sect. 2.3)")
     ap.add_argument("--cooling", action="store_true",
                     help="Newtonian cooling on (rate 0.5, height cut-off at 10 dz) in the throughput leg")
     return ap.parse_args()
@@ -360,6 +362,51 @@ def _revolve_recompute(n, slots):
     return rv.recomputed_steps
 
 
+def granulation_line(dev, n=1024, dt=10.0, t_end=600.0):
+    """The granulation driver on an n x n plane of 0.23 Mm pixels (the
+    driver figure's), Sect. 2.3's parameters: the first fill of the empty
+    plane, then one update and one velocity every dt = 10 s of solar time
+    (the snapshot cadence the paper names) up to t_end; the random draws of
+    every update resident on the device before timing.  Steady-state means
+    over the updates from one lifetime (300 s) on."""
+    import numpy as np
+    import torch
+
+    import inputs
+    from paper_1908_08557_gb300 import Granulation
+    from paper_1908_08557_gb300.granulation import paper_params
+    gen = Granulation(n, n, 1.0, 1.0, paper_params(mm_per_unit=0.23), device=str(dev))
+    times = np.arange(0.0, t_end + dt / 2, dt)
+    dr = []
+    for u in range(len(times)):
+        k, cl, ca = inputs.granulation_draws(n, n, seed=17, update=u)
+        dr.append((torch.as_tensor(k.view(np.int32), device=dev), torch.as_tensor(cl, device=dev),
+                   torch.as_tensor(ca, device=dev)))
+    v = torch.empty((2, n, n), dtype=torch.float32, device=dev)
+    gen.update(-1e6, *dr[0])  # warm-up: loads the kernels, places a population ...
+    gen.velocity(-1e6, precision=32, out=v)
+    gen.close()               # ... discarded: a fresh generator for the timed run
+    gen = Granulation(n, n, 1.0, 1.0, paper_params(mm_per_unit=0.23), device=str(dev))
+    l0 = gen.launch_count()
+    rec = []
+    for u, t in enumerate(times):
+        box = {}
+        tu = _cuda_ms(gen.stream, lambda: box.update(r=gen.update(float(t), *dr[u])))
+        tv = _cuda_ms(gen.stream, lambda: gen.velocity(float(t), precision=32, out=v))
+        occ, _ = gen.granules()
+        rec.append((float(t), tu, box["r"], tv, int(occ.sum())))
+    steady = [r for r in rec if r[0] >= 300.0]
+    out = {"plane": f"{n}x{n}", "pixel_mm": 0.23, "update_every_s": dt, "updates": len(rec),
+           "fill_ms": rec[0][1], "fill_rounds": rec[0][2], "granules_after_fill": rec[0][4],
+           "update_ms": float(np.mean([r[1] for r in steady])),
+           "update_rounds": float(np.mean([r[2] for r in steady])),
+           "velocity_ms": float(np.mean([r[3] for r in steady])),
+           "granules": float(np.mean([r[4] for r in steady])),
+           "gpu_launches": gen.launch_count() - l0}
+    gen.close()
+    return out
+
+
 def production_line(dev, ws):
     import numpy as np
     import torch
@@ -612,6 +659,13 @@ def run_native(args, ws, rank, local):
         except Exception as exc:  # reported, not fatal: the run is optional
             drift = {"error": f"{type(exc).__name__}: {exc}"}
 
+    gran = None
+    if args.granulation:
+        try:
+            gran = granulation_line(dev)
+        except Exception as exc:  # reported, not fatal: the run is optional
+            gran = {"error": f"{type(exc).__name__}: {exc}"}
+
     scale = None
     if args.adjoint_scale:
         try:
@@ -644,6 +698,8 @@ def run_native(args, ws, rank, local):
             line["adjoint_bipoles100_512x512x256"] = scale
         if drift is not None:
             line["drift_ar_1024x1024x256"] = drift
+        if gran is not None:
+            line["granulation_1024x1024"] = gran
         print(json.dumps(line), flush=True)
 
 

@@ -288,6 +288,103 @@ int mhd_invert_magnetogram_static(int nx, int ny, double dx, double dy,
                                   int precision, const void* bz, void* ax,
                                   void* ay, void* stream);
 
+/* ---- granulation driver (Sect. 2.3, Eqs. 1-4) ---- */
+
+/* A generator of photospheric driver velocities that resemble granulation,
+ * on a periodic nx x ny plane of spacings dx, dy, independent of any
+ * simulation handle (the paper runs it as a 2D pre-step whose snapshots the
+ * 3D model interpolates in time: pass two of its outputs to mhd_set_driver
+ * as v0, v1).  All arithmetic is FP64 on the GPU.
+ *
+ * Granules sit on pixel centres, at most one per pixel.  Each carries its
+ * birth time t0, lifetime T = lifetime (1 + lifetime_spread c_T), peak
+ * amplitude v_max = v0 (1 + amp_spread c_v) (c_T, c_v: the caller's standard
+ * normal draws at that pixel, clipped to [-1, 1]) and peak time
+ * t_max = T sqrt(|ln(v_min / v_max)|) (Eq. 1), v_min = vmin_frac v0; its
+ * amplitude is v(t) = v_max exp(-((t - t0 - t_max) / T)^2) (Eq. 2), equal to
+ * v_min at birth and again at t0 + 2 t_max, when the granule dies.
+ *
+ * Lengths are in the units of dx, dy; times and speeds in any consistent
+ * units (the paper's values: r_inner 0.64 Mm, r_granule 0.8 Mm, r_lane
+ * 1.04 Mm, v0 1.028 km/s, vmin_frac 0.78, lifetime 5 min, spreads 0.10 and
+ * 0.15, f_rot 5). */
+typedef struct mhd_gran_params {
+  double r_inner;          /* no new centre closer than this to a live one    */
+  double r_granule;        /* the radial speed rises linearly to here ...      */
+  double r_lane;           /* ... and falls as cos^2 to zero here (> r_granule) */
+  double v0;               /* typical amplitude                                */
+  double vmin_frac;        /* v_min / v0, in (0, 1 - amp_spread)               */
+  double lifetime;         /* T_gran                                           */
+  double lifetime_spread;  /* in [0, 1)                                        */
+  double amp_spread;       /* in [0, 1)                                        */
+  double f_rot;            /* amplification of the rotational part (Eq. 3)    */
+} mhd_gran_params;
+
+typedef struct mhd_gran_ctx* mhd_gran_handle;
+
+/* Bytes of device workspace a generator needs (0 if the arguments are
+ * invalid: nx, ny powers of two in [8, 1024]; dx, dy > 0; 0 < r_inner;
+ * 0 < r_granule < r_lane; r_inner and r_lane below half the plane in each
+ * direction and at most 64 pixels; the other parameters as stated above). */
+size_t mhd_gran_workspace_bytes(int nx, int ny, double dx, double dy,
+                                const mhd_gran_params* gp);
+
+/* Create a generator with no granules.  workspace: caller-owned device
+ * memory of mhd_gran_workspace_bytes() bytes, 256-byte aligned, kept alive
+ * until mhd_gran_destroy.  stream: cudaStream_t (NULL: legacy default
+ * stream) on which every launch of the generator is ordered.  Synchronises
+ * the stream before returning.  Errors: mhd_last_error(NULL). */
+int mhd_gran_create(int nx, int ny, double dx, double dy,
+                    const mhd_gran_params* gp, void* workspace,
+                    size_t ws_bytes, void* stream, mhd_gran_handle* out);
+
+/* Advance the granule population to time t: remove every granule with
+ * t - t0 - t_max > t_max (its amplitude has fallen below v_min after the
+ * peak), then fill the plane: visiting the pixels by ascending
+ * (keys[p], p), a granule starts at pixel p (t0 = t) when no live centre lies
+ * closer than r_inner (nearest periodic image).  The result equals that
+ * sequential visit exactly; the GPU reaches it in parallel rounds (a pixel
+ * joins once no undecided pixel within r_inner precedes it), and the call
+ * synchronises the stream once per round.
+ *   keys [ny][nx] uint32, c_life, c_amp [ny][nx] double: the random draws
+ *   (uniform keys, standard normals); mem: MHD_MEM_DEVICE or MHD_MEM_HOST.
+ *   rounds (may be NULL): the parallel rounds taken.
+ * Times passed to successive calls should not decrease. */
+int mhd_gran_update(mhd_gran_handle g, double t, const unsigned int* keys,
+                    const double* c_life, const double* c_amp, int mem,
+                    int* rounds);
+
+/* The driver velocity v*_gran at time t (Eqs. 2-4) into v [2][ny][nx]
+ * (vx, vy; float for precision 32, double for 64): the live granules'
+ * radial fields, amplitude (Eq. 2) times the radial profile times the unit
+ * vector from the centre, added where they overlap (v_gran); its
+ * divergence-free part, times exp(-(2 |k| / k_N)^4) with
+ * |k| / k_N = sqrt((k_x dx / pi)^2 + (k_y dy / pi)^2) and the mean and
+ * Nyquist modes dropped (Eq. 3), times f_rot added back (v_vor); the sum
+ * scaled by sqrt(<|v_gran|^2> / <|v_vor|^2>) (Eq. 4; zero if v_vor is).
+ * Asynchronous for device output. */
+int mhd_gran_velocity(mhd_gran_handle g, double t, int precision, void* v,
+                      int mem);
+
+/* The granule maps: occ [ny][nx] int (1 where a granule is centred) and, if
+ * par is not NULL, par [4][ny][nx] double (t0, T, v_max, t_max; zero where
+ * occ is 0). */
+int mhd_gran_read_granules(mhd_gran_handle g, int* occ, double* par, int mem);
+
+/* Intermediate fields of the last mhd_gran_velocity, [2][ny][nx] double:
+ * which = 0 the granular field v_gran, 1 the filtered rotational part
+ * v_rot' of Eq. 3. */
+int mhd_gran_read_field(mhd_gran_handle g, int which, double* dst, int mem);
+
+/* Number of kernels this generator has launched since mhd_gran_create. */
+long long mhd_gran_launch_count(mhd_gran_handle g);
+
+/* The message of the generator's last error (NULL: of the last create). */
+const char* mhd_gran_last_error(mhd_gran_handle g);
+
+/* Frees host-side bookkeeping only (the workspace is the caller's). */
+void mhd_gran_destroy(mhd_gran_handle g);
+
 /* ---- instrumentation ---- */
 
 /* Kernel classes timed by the profiler. */

@@ -320,3 +320,12 @@ def make_case(name: str, seed: int = 0, dtype=np.float64) -> Case:
 
 def padded_shape(nx, ny, nz):
     return (NFIELD, nz + 2 * NGHOST, ny + 2 * NGHOST, nx + 2 * NGHOST)
+
+
+def granulation_draws(nx: int, ny: int, seed: int, update: int = 0):
+    """The random inputs of one granulation-driver update: uint32 visiting
+    keys and two standard normal fields (lifetime and amplitude draws),
+    [ny][nx] each, from a generator seeded by (seed, update)."""
+    rng = np.random.default_rng([seed, update])
+    keys = rng.integers(0, 2 ** 32, (ny, nx), dtype=np.uint64).astype(np.uint32)
+    return keys, rng.standard_normal((ny, nx)), rng.standard_normal((ny, nx))

@@ -141,6 +141,23 @@ class Granulation:
             vy += a * prof * uy
         return vx, vy
 
+    def granular_field_at(self, t, pix):
+        """v_gran at the pixels pix [(j, i), ...] only: the sum over every live
+        granule, one pixel at a time (for planes too large for the full map)."""
+        gp = self.gp
+        c = np.array(list(self.live.keys()), dtype=np.int64).reshape(-1, 2)
+        par = np.array(list(self.live.values()), dtype=np.float64).reshape(-1, 4)
+        a = par[:, 2] * np.exp(-((t - par[:, 0] - par[:, 3]) / par[:, 1]) ** 2)
+        out = np.zeros((len(pix), 2))
+        for n, (j, i) in enumerate(pix):
+            ox = ((i - c[:, 1] + self.nx // 2) % self.nx - self.nx // 2) * self.dx
+            oy = ((j - c[:, 0] + self.ny // 2) % self.ny - self.ny // 2) * self.dy
+            r = np.hypot(ox, oy)
+            near = (r > 0) & (r < gp.r_lane)
+            f = a[near] * radial_profile(r[near], gp.r_granule, gp.r_lane) / r[near]
+            out[n] = (np.sum(f * ox[near]), np.sum(f * oy[near]))
+        return out
+
     def velocity(self, t):
         """v*_gran (Eq. 4) at time t, with the filtered rotational part."""
         vx, vy = self.granular_field(t)

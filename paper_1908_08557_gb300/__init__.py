@@ -8,4 +8,5 @@
     sim.step(10)
 """
 from .binding import MHDError, Simulation, load, workspace_bytes  # noqa: F401
+from .granulation import Granulation  # noqa: F401
 from .build import build  # noqa: F401

@@ -38,7 +38,9 @@ EXPORTED = ("mhd_workspace_bytes", "mhd_create", "mhd_set_driver", "mhd_step",
             "mhd_read_profile", "mhd_launch_count", "mhd_invert_magnetogram_static",
             "mhd_set_time", "mhd_checkpoint_bytes", "mhd_save", "mhd_restore",
             "mhd_adjoint_init", "mhd_adjoint_step", "mhd_adjoint_read", "mhd_bz_plane",
-            "mhd_bz_plane_adjoint")
+            "mhd_bz_plane_adjoint", "mhd_gran_workspace_bytes", "mhd_gran_create", "mhd_gran_update",
+            "mhd_gran_velocity", "mhd_gran_read_granules", "mhd_gran_read_field", "mhd_gran_launch_count",
+            "mhd_gran_last_error", "mhd_gran_destroy")
 KERNEL_CLASSES = ("ghost", "pfe", "cfl", "stats", "rk")
 
 
@@ -78,6 +80,12 @@ class Stats(ctypes.Structure):
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad_"}
+
+
+class GranParams(ctypes.Structure):
+    """mhd_gran_params (Sect. 2.3): lengths in the units of dx, dy."""
+    _fields_ = [(n, ctypes.c_double) for n in ("r_inner", "r_granule", "r_lane", "v0", "vmin_frac", "lifetime",
+                                               "lifetime_spread", "amp_spread", "f_rot")]
 
 
 _lib = None
@@ -131,9 +139,24 @@ def load(path: Optional[str] = None):
     lib.mhd_bz_plane_adjoint.argtypes = [vp, vp, i, vp]
     lib.mhd_launch_count.argtypes = [vp]
     lib.mhd_launch_count.restype = ctypes.c_longlong
+    G = ctypes.POINTER(GranParams)
+    lib.mhd_gran_workspace_bytes.argtypes = [i, i, d, d, G]
+    lib.mhd_gran_workspace_bytes.restype = sz
+    lib.mhd_gran_create.argtypes = [i, i, d, d, G, vp, sz, vp, ctypes.POINTER(vp)]
+    lib.mhd_gran_update.argtypes = [vp, d, vp, vp, vp, i, ctypes.POINTER(ctypes.c_int)]
+    lib.mhd_gran_velocity.argtypes = [vp, d, i, vp, i]
+    lib.mhd_gran_read_granules.argtypes = [vp, vp, vp, i]
+    lib.mhd_gran_read_field.argtypes = [vp, i, vp, i]
+    lib.mhd_gran_launch_count.argtypes = [vp]
+    lib.mhd_gran_launch_count.restype = ctypes.c_longlong
+    lib.mhd_gran_last_error.argtypes = [vp]
+    lib.mhd_gran_last_error.restype = ctypes.c_char_p
+    lib.mhd_gran_destroy.argtypes = [vp]
+    lib.mhd_gran_destroy.restype = None
     for name in EXPORTED:
         if name not in ("mhd_workspace_bytes", "mhd_destroy", "mhd_last_error",
-                        "mhd_launch_count", "mhd_checkpoint_bytes"):
+                        "mhd_launch_count", "mhd_checkpoint_bytes", "mhd_gran_workspace_bytes",
+                        "mhd_gran_launch_count", "mhd_gran_last_error", "mhd_gran_destroy"):
             getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib

@@ -154,7 +154,8 @@ __global__ void __launch_bounds__(256) rows_fwd_kernel(FFTPlan fp, Layout L, con
 // are needed to split the packed plane P2 (F(-k) lives in the mirror column).
 // mode 0: potential-field extrapolation, 3 layers; mode 1: magnetogram
 // inversion (Eq. 7): A^_x + i A^_y = (kt_x + i kt_y) B^_z / kt^2; mode 2: its
-// transpose.  The spectra of lg output layers at a time are formed and
+// transpose; mode 4: the filtered rotational part of the granulation field
+// (Sect. 2.3, Eq. 3).  The spectra of lg output layers at a time are formed and
 // inverted as one batch of lines, so each stage of the inverse transform has
 // lg times the butterflies between two barriers; lg = nout needs two buffers
 // of lg layers (the forward spectrum's buffer becomes the scratch), lg < nout
@@ -200,6 +201,25 @@ __global__ void __launch_bounds__(256) cols_kernel(FFTPlan fp, int mode, const S
       if (k2 > 0.0) {
         const double2 m = make_double2(kxm / k2, kym / k2);
         g = cmul(m, F);
+      } else {
+        g = make_double2(0.0, 0.0);
+      }
+    } else if (mode == 4) {
+      // F = FFT(v_x + i v_y).  With V_x = (F + conj F(-k)) / 2 and
+      // V_y = (F - conj F(-k)) / 2i, the divergence-free part
+      // V - k (k . V) / |k|^2 packs as (F - e^(2 i theta) conj F(-k)) / 2,
+      // e^(i theta) = (k_x + i k_y) / |k|; times the filter
+      // exp(-(2 |k| / k_N)^4).  The mean and the Nyquist modes (whose signed
+      // wavenumber has no partner) carry none.
+      const double kxw = fp.ktx[col], kyw = fp.kty[ky];
+      const double k2 = kxw * kxw + kyw * kyw;
+      if (k2 > 0.0 && 2 * col != nx && 2 * ky != ny) {
+        const double2 Fm = spec[(line ^ 1) * ny + ((ny - ky) & (ny - 1))];
+        const double c2 = (kxw * kxw - kyw * kyw) / k2, s2 = 2.0 * kxw * kyw / k2;
+        const double ax = kxw / fp.knx, ay = kyw / fp.kny;
+        const double q4 = 4.0 * (ax * ax + ay * ay);
+        const double w = 0.5 * exp(-q4 * q4);
+        g = make_double2(w * (F.x - (c2 * Fm.x + s2 * Fm.y)), w * (F.y - (s2 * Fm.x - c2 * Fm.y)));
       } else {
         g = make_double2(0.0, 0.0);
       }
@@ -491,6 +511,20 @@ void launch_atarget(const FFTPlan& fp, const R* bz, R* axt, R* ayt, cudaStream_t
   cols_kernel<<<dim3((npairs + l.ppb - 1) / l.ppb, 1), 256, l.smem_cols, st>>>(fp, 1, nullptr, l.ppb, 1);
   rows_inv_kernel<R><<<dim3(fp.ny / r1.nb, 1, 1), r1.threads, r1.smem, st>>>(fp, L, nullptr, axt, ayt, 1, nullptr,
                                                                              r1.nb);
+}
+
+void launch_rotational(const FFTPlan& fp, const double* vx, const double* vy, double* rx, double* ry,
+                       cudaStream_t st) {
+  set_smem_once();
+  Layout L{};
+  const FFTLaunch l = fft_launch(fp);
+  const int npairs = fp.nx / 2 + 1;
+  const RowsCfg r1 = rows_cfg(fp, 1);
+  rows_fwd_kernel<double><<<dim3(fp.ny / r1.nb, 1), r1.threads, r1.smem, st>>>(fp, L, nullptr, nullptr, 3, nullptr,
+                                                                               r1.nb, vx, vy);
+  cols_kernel<<<dim3((npairs + l.ppb - 1) / l.ppb, 1), 256, l.smem_cols, st>>>(fp, 4, nullptr, l.ppb, 1);
+  rows_inv_kernel<double><<<dim3(fp.ny / r1.nb, 1, 1), r1.threads, r1.smem, st>>>(fp, L, nullptr, rx, ry, 1,
+                                                                                 nullptr, r1.nb);
 }
 
 // Adjoint of the potential-field ghosts: gbar (adjoint of the ghost-filled

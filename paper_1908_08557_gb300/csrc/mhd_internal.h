@@ -18,6 +18,7 @@ struct FFTPlan {
   double2* P;          // [3][nx][ny] row spectra, transposed
   double2* Q;          // [3][3][nx][ny] extrapolated spectra, transposed
   int p0;              // first plane of a launch (blockIdx.y offset; 0 unless planes run apart)
+  double knx, kny;     // Nyquist wavenumbers pi / dx, pi / dy (the granulation filter only)
 };
 
 // three streams for the potential-field planes of one substep: the caller's
@@ -52,6 +53,10 @@ template <typename R> void launch_pfe(const FFTPlan& fp, const Layout& L, R* f, 
                                       cudaStream_t st, const PlaneStreams* ps = nullptr);
 // vector potential of the target magnetogram into axt, ayt
 template <typename R> void launch_atarget(const FFTPlan& fp, const R* bz, R* axt, R* ayt, cudaStream_t st);
+// filtered rotational part (Eq. 3) of the plane field (vx, vy) into (rx, ry),
+// all [ny][nx]; fp.ktx, fp.kty hold the signed wavenumbers 2 pi m / L
+void launch_rotational(const FFTPlan& fp, const double* vx, const double* vy, double* rx, double* ry,
+                       cudaStream_t st);
 // fused right-hand side + RK update; sub = 0,1,2, or -1 to write the raw RHS into df
 template <typename R> void launch_rk(const Layout& L, const Phys<R>& ph, const Background<R>& bg,
                                      const R* fin, R* fout, R* df,

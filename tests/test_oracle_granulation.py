@@ -209,3 +209,14 @@ def test_velocity_rms_and_vorticity():
     k = 2 * np.pi * np.fft.fftfreq(32)
     curl = lambda u, v: np.abs(1j * k[None, :] * np.fft.fft2(v) - 1j * k[:, None] * np.fft.fft2(u)).sum()
     assert curl(ox, oy) > curl(vx, vy)
+
+
+def test_field_at_sampled_pixels_matches_the_map():
+    g = Granulation(32, 24, 1.0, 1.25, GP)
+    g.update(0.0, *_draws(32, 24, 9))
+    vx, vy = g.granular_field(50.0)
+    pix = [(0, 0), (5, 31), (23, 7), (12, 12)]
+    got = g.granular_field_at(50.0, pix)
+    for n, (j, i) in enumerate(pix):
+        assert got[n, 0] == pytest.approx(vx[j, i], rel=1e-12, abs=1e-15)
+        assert got[n, 1] == pytest.approx(vy[j, i], rel=1e-12, abs=1e-15)
