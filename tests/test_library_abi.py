@@ -80,3 +80,49 @@ def test_cooling_parameter_errors(lib):
                         ctypes.byref(h))
     assert rc == binding.MHD_ERR_ARG and not h.value
     assert b"falling strictly" in lib.mhd_last_error(None)
+
+
+def test_granulation_argument_errors(lib):
+    """The granulation driver (Sect. 2.3): workspace sizing, and every
+    argument error returned before any CUDA call."""
+    from paper_1908_08557_gb300 import binding
+    from paper_1908_08557_gb300.granulation import paper_params
+    gp = binding.GranParams(**paper_params(mm_per_unit=0.23))
+    n256 = lib.mhd_gran_workspace_bytes(256, 256, 1.0, 1.0, ctypes.byref(gp))
+    n1k = lib.mhd_gran_workspace_bytes(1024, 1024, 1.0, 1.0, ctypes.byref(gp))
+    # 132 bytes per pixel (granule slots, placement state, fields, staged
+    # draws, two complex FFT planes) plus small tables
+    assert 132 * 256 * 256 <= n256 < 132 * 256 * 256 + (1 << 20)
+    assert 132 * 1024 * 1024 <= n1k < 132 * 1024 * 1024 + (1 << 20)
+    bad = [(48, 256, 1.0, 1.0, {}),                      # not a power of two
+           (2048, 256, 1.0, 1.0, {}),                    # beyond the FFT's 1024
+           (8, 8, 1.0, 1.0, {}),                         # lane radius above half the plane
+           (256, 256, 0.0, 1.0, {}),                     # spacing
+           (256, 256, 0.01, 1.0, {}),                    # lane radius beyond 64 pixels
+           (256, 256, 1.0, 1.0, dict(r_lane=3.0)),       # r_lane below r_granule
+           (256, 256, 1.0, 1.0, dict(vmin_frac=0.9)),    # v_min above the lowest v_max
+           (256, 256, 1.0, 1.0, dict(amp_spread=1.0)),
+           (256, 256, 1.0, 1.0, dict(lifetime=0.0)),
+           (256, 256, 1.0, 1.0, dict(f_rot=float("nan")))]
+    for nx, ny, dx, dy, over in bad:
+        q = binding.GranParams(**dict(paper_params(mm_per_unit=0.23), **over))
+        assert lib.mhd_gran_workspace_bytes(nx, ny, dx, dy, ctypes.byref(q)) == 0, (nx, ny, dx, over)
+    h = ctypes.c_void_p()
+    rc = lib.mhd_gran_create(256, 256, 1.0, 1.0, ctypes.byref(gp), None, 0, None, ctypes.byref(h))
+    assert rc == binding.MHD_ERR_WORKSPACE and not h.value
+    assert b"workspace" in lib.mhd_gran_last_error(None)
+    rc = lib.mhd_gran_create(256, 256, 1.0, 1.0, ctypes.byref(gp), ctypes.c_void_p(256 + 8), 1 << 40, None,
+                             ctypes.byref(h))
+    assert rc == binding.MHD_ERR_WORKSPACE
+    rc = lib.mhd_gran_create(48, 256, 1.0, 1.0, ctypes.byref(gp), ctypes.c_void_p(256), 1 << 40, None,
+                             ctypes.byref(h))
+    assert rc == binding.MHD_ERR_ARG and b"powers of two" in lib.mhd_gran_last_error(None)
+    assert lib.mhd_gran_create(256, 256, 1.0, 1.0, ctypes.byref(gp), ctypes.c_void_p(256), 1 << 40, None,
+                               None) == binding.MHD_ERR_ARG
+    r = ctypes.c_int()
+    assert lib.mhd_gran_update(None, 0.0, None, None, None, 0, ctypes.byref(r)) == binding.MHD_ERR_ARG
+    assert lib.mhd_gran_velocity(None, 0.0, 32, None, 0) == binding.MHD_ERR_ARG
+    assert lib.mhd_gran_read_granules(None, None, None, 0) == binding.MHD_ERR_ARG
+    assert lib.mhd_gran_read_field(None, 0, None, 0) == binding.MHD_ERR_ARG
+    assert lib.mhd_gran_launch_count(None) == 0
+    lib.mhd_gran_destroy(None)
