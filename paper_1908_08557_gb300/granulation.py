@@ -77,9 +77,9 @@ class Granulation:
         import torch
         shape = (self.ny, self.nx)
         if isinstance(a, torch.Tensor) and a.is_cuda:
-            want = torch.int32 if dtype == np.uint32 else torch.float64
-            if a.dtype not in (want, torch.uint32 if dtype == np.uint32 else want) or tuple(a.shape) != shape \
-                    or not a.is_contiguous():
+            # keys: 32-bit integers, read as unsigned; draws: float64
+            ok = (torch.int32, torch.uint32) if dtype == np.uint32 else (torch.float64,)
+            if a.dtype not in ok or tuple(a.shape) != shape or not a.is_contiguous():
                 raise ValueError(f"expected a contiguous {shape} tensor of {dtype.__name__}")
             return ctypes.c_void_p(a.data_ptr()), MHD_MEM_DEVICE, a
         arr = np.ascontiguousarray(a if not hasattr(a, "numpy") else a.numpy(), dtype=dtype)
