@@ -201,22 +201,39 @@ def driver_solenoidal(nx, ny, kmax, rms, seed, slope=-5.0 / 3.0):
 # initial state
 
 def initial_atmosphere(nz, dz, gz, t_bottom=1.0, t_top=100.0, zc_cells=12.0,
-                       width_cells=2.0):
+                       width_cells=2.0, z=None):
     """ln T0 and ln rho0 on k = -3 .. nz+2.
 
-    T0(z) = T_b + (T_t - T_b)/2 (1 + tanh((z - z_c)/w)); ln p from trapezoid
-    hydrostatics, ln p_{k+1} = ln p_k + dz g_z (1/T_k + 1/T_{k+1})/2 with
-    p = 1 at z = 0; ln rho0 = ln p - ln T0 (p = rho T)."""
+    T0(z) = T_b + (T_t - T_b)/2 (1 + tanh((z - z_c)/w)), z_c = zc_cells dz,
+    w = width_cells dz; ln p from trapezoid hydrostatics, ln p_{k+1} = ln p_k
+    + (z_{k+1} - z_k) g_z (1/T_k + 1/T_{k+1})/2 with p = 1 at z = 0; ln rho0 =
+    ln p - ln T0 (p = rho T).  z: the layer positions (nz + 6, a
+    non-uniform grid); default z_k = k dz."""
     k = np.arange(-NGHOST, nz + NGHOST)
-    z = k * dz
+    z = k * dz if z is None else np.asarray(z, dtype=np.float64)
     T = t_bottom + (t_top - t_bottom) * 0.5 * (1.0 + np.tanh((z - zc_cells * dz) / (width_cells * dz)))
     lnp = np.zeros_like(z)
     k0 = NGHOST
     for q in range(k0 + 1, len(z)):
-        lnp[q] = lnp[q - 1] + dz * gz * 0.5 * (1.0 / T[q - 1] + 1.0 / T[q])
+        lnp[q] = lnp[q - 1] + (z[q] - z[q - 1]) * gz * 0.5 * (1.0 / T[q - 1] + 1.0 / T[q])
     for q in range(k0 - 1, -1, -1):
-        lnp[q] = lnp[q + 1] - dz * gz * 0.5 * (1.0 / T[q + 1] + 1.0 / T[q])
+        lnp[q] = lnp[q + 1] - (z[q + 1] - z[q]) * gz * 0.5 * (1.0 / T[q + 1] + 1.0 / T[q])
     return np.log(T), lnp - np.log(T)
+
+
+def stretched_z(nz, dz_bottom, dz_top, k_c, width):
+    """Positions of the layers k = -3 .. nz+2 of a vertical grid whose
+    spacing rises smoothly from dz_bottom to dz_top around layer k_c (the
+    production grid goes from about 100 km to about 800 km, Sect. 1):
+    z'(k) = dz_b + (dz_t - dz_b) (1 + tanh((k - k_c)/width)) / 2, integrated
+    in closed form, z(0) = 0.  Returns (z, z'(k), z''(k))."""
+    k = np.arange(-NGHOST, nz + NGHOST, dtype=np.float64)
+    d = dz_top - dz_bottom
+    lc = lambda x: np.log(np.cosh(x))
+    z = dz_bottom * k + 0.5 * d * (k + width * (lc((k - k_c) / width) - lc(-k_c / width)))
+    zp = dz_bottom + 0.5 * d * (1.0 + np.tanh((k - k_c) / width))
+    zpp = 0.5 * d / width / np.cosh((k - k_c) / width) ** 2
+    return z, zp, zpp
 
 
 def initial_potential_field(bz, nz, dx, dy, dz, dtype=np.float64):

@@ -56,6 +56,7 @@ def lib():
         _lib.or_fill_ghosts.argtypes = [ip, dp, dp, dp]
         _lib.or_fill_ghosts_nopfe.argtypes = [ip, dp, dp, dp]
         _lib.or_set_nc_profile.argtypes = [ctypes.c_int, dp, dp]
+        _lib.or_set_zgrid.argtypes = [ctypes.c_int, dp]
         _lib.or_rhs.argtypes = [ip, dp, dp, dp, dp, dp, dp, ctypes.c_double,
                                 ctypes.c_double, ctypes.c_double, dp]
         _lib.or_cfl.argtypes = [ip, dp, dp]
@@ -95,7 +96,22 @@ def _nc_default(p: Dict, k: str) -> float:
     return float(p.get(k, d[k]))
 
 
+def _sync_zgrid(p: Dict) -> None:
+    """The vertical grid of this call: p["z"], the positions of the layers
+    k = -3 .. nz+2 (strictly increasing), or the uniform z_k = k dz when p
+    has none."""
+    z = p.get("z")
+    if z is None:
+        lib().or_set_zgrid(0, None)
+        return
+    z = np.ascontiguousarray(z, dtype=np.float64)
+    if z.shape != (int(p["nz"]) + 2 * NG,) or not np.all(np.diff(z) > 0):
+        raise ValueError("p['z'] must hold nz + 6 strictly increasing layer positions")
+    lib().or_set_zgrid(int(p["nz"]), _d(z))
+
+
 def _pvec(p: Dict) -> np.ndarray:
+    _sync_zgrid(p)
     if _nc_default(p, "nc_tau") > 0.0 and _nc_nz[0] != int(p["nz"]):
         raise ValueError("Newtonian cooling on: call set_nc_profile(lnrho0, lnT0) for this nz first")
     return np.array([float(p[k]) for k in _PARAM_ORDER] + [_nc_default(p, k) for k in _NC_ORDER],
@@ -141,12 +157,14 @@ def fill_ghosts(p: Dict, u: np.ndarray, lnrho0: np.ndarray, pfe: str = "dft") ->
         return u
     lib().or_fill_ghosts_nopfe(_i(_dims(p)), _d(_pvec(p)), _d(u), _d(lnrho0))
     nx, ny, nz = p["nx"], p["ny"], p["nz"]
-    lx, ly, dz = nx * p["dx"], ny * p["dy"], p["dz"]
+    lx, ly = nx * p["dx"], ny * p["dy"]
+    z = np.asarray(p["z"], dtype=np.float64) if p.get("z") is not None else \
+        np.arange(-NG, nz + NG) * float(p["dz"])
     kt = NG + nz - 1
     for c in range(3):
-        top = pfe_plane_fft(lx, ly, u[c, kt, NG:-NG, NG:-NG], [-m * dz for m in (1, 2, 3)])
+        top = pfe_plane_fft(lx, ly, u[c, kt, NG:-NG, NG:-NG], [-(z[kt + m] - z[kt]) for m in (1, 2, 3)])
         bot = pfe_plane_fft(lx, ly, u[c, NG, NG:-NG, NG:-NG],
-                            [p["f_pfe_bottom"] * m * dz for m in (1, 2, 3)])
+                            [p["f_pfe_bottom"] * (z[NG] - z[NG - m]) for m in (1, 2, 3)])
         for m in (1, 2, 3):
             u[c, kt + m] = np.pad(top[m - 1], NG, mode="wrap")
             u[c, NG - m] = np.pad(bot[m - 1], NG, mode="wrap")

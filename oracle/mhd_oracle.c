@@ -62,6 +62,44 @@ static double spacing(const grid_t* g, int axis) {
   return axis == 0 ? g->p[P_DX] : axis == 1 ? g->p[P_DY] : g->p[P_DZ];
 }
 
+/* Vertical grid (the production grid's spacing grows from about 100 km in
+ * the photosphere and chromosphere to about 800 km in the upper corona,
+ * Sect. 1; the snapshots carry the inverse spacing dz_1, Sect. 5.3).  The
+ * positions z_k of the layers k = -3 .. nz+2 are given (or_set_zgrid); the
+ * layer index xi = k is the uniform coordinate, and with the sixth-order
+ * index-space derivatives z' = D1_xi z, z'' = D2_xi z the chain rule gives
+ *   df/dz = f_xi / z',  d2f/dz2 = f_xixi / z'^2 - f_xi z'' / z'^3.
+ * Unset, z_k = k dz and the stencils divide by dz as before. */
+static double* zg = NULL; /* z at k = -3 .. nz+2 */
+static int zg_nz = -1;
+
+void or_set_zgrid(int nz, const double* z) {
+  free(zg);
+  zg = NULL;
+  zg_nz = -1;
+  if (!z || nz <= 0) return;
+  zg = (double*)malloc(sizeof(double) * (size_t)(nz + 2 * NG));
+  memcpy(zg, z, sizeof(double) * (size_t)(nz + 2 * NG));
+  zg_nz = nz;
+}
+
+static int zgrid_on(const grid_t* g) { return zg != NULL && zg_nz == g->nz; }
+
+static double zpos(const grid_t* g, int k) { return zgrid_on(g) ? zg[k + NG] : (double)k * g->p[P_DZ]; }
+
+/* dxi/dz and d2xi/dz2 at layer k (interior layers only: the stencil of z
+ * reaches k +- 3) */
+static void zmetric(const grid_t* g, int k, double* m1, double* m2) {
+  double z1 = 0.0, z2 = 0.0;
+  for (int m = 1; m <= 3; ++m) {
+    z1 += W1[m] * (zpos(g, k + m) - zpos(g, k - m));
+    z2 += W2[m] * (zpos(g, k + m) + zpos(g, k - m));
+  }
+  z2 += W2[0] * zpos(g, k);
+  *m1 = 1.0 / z1;
+  *m2 = -z2 / (z1 * z1 * z1);
+}
+
 /* value of field f at (i,j,k) displaced by m along `axis` */
 static double at(const grid_t* g, const double* u, int f, int k, int j, int i,
                  int axis, int m) {
@@ -76,6 +114,11 @@ static double d1(const grid_t* g, const double* u, int f, int k, int j, int i,
   double s = 0.0;
   for (int m = 1; m <= 3; ++m)
     s += W1[m] * (at(g, u, f, k, j, i, axis, m) - at(g, u, f, k, j, i, axis, -m));
+  if (axis == 2 && zgrid_on(g)) {
+    double m1, m2;
+    zmetric(g, k, &m1, &m2);
+    return s * m1;
+  }
   return s / spacing(g, axis);
 }
 
@@ -84,6 +127,13 @@ static double d2(const grid_t* g, const double* u, int f, int k, int j, int i,
   double s = W2[0] * u[ix(g, f, k, j, i)];
   for (int m = 1; m <= 3; ++m)
     s += W2[m] * (at(g, u, f, k, j, i, axis, m) + at(g, u, f, k, j, i, axis, -m));
+  if (axis == 2 && zgrid_on(g)) {
+    double s1 = 0.0, m1, m2;
+    for (int m = 1; m <= 3; ++m)
+      s1 += W1[m] * (at(g, u, f, k, j, i, axis, m) - at(g, u, f, k, j, i, axis, -m));
+    zmetric(g, k, &m1, &m2);
+    return s * m1 * m1 + s1 * m2;
+  }
   double h = spacing(g, axis);
   return s / (h * h);
 }
@@ -105,6 +155,11 @@ static double d11(const grid_t* g, const double* u, int f, int k, int j, int i,
         }
       s += W1[m] * W1[n] * acc;
     }
+  if ((a == 2 || b == 2) && zgrid_on(g)) {
+    double m1, m2;
+    zmetric(g, k, &m1, &m2);
+    return s * m1 / spacing(g, a == 2 ? b : a);
+  }
   return s / (spacing(g, a) * spacing(g, b));
 }
 
@@ -313,7 +368,8 @@ static void fill_ghosts_impl(const int* dims, const double* p, double* u, const 
         double th1 = u[ix(g, F_LNTT, -m + 1, j, i)];
         double l1 = u[ix(g, F_LNRHO, -m + 1, j, i)];
         double l0 = u[ix(g, F_LNRHO, -m, j, i)];
-        u[ix(g, F_LNTT, -m, j, i)] = th1 + l1 - l0 - dz * gz / exp(th1);
+        double dzl = zgrid_on(g) ? zpos(g, -m + 1) - zpos(g, -m) : dz;
+        u[ix(g, F_LNTT, -m, j, i)] = th1 + l1 - l0 - dzl * gz / exp(th1);
       }
       /* closed bottom: u_z antisymmetric about the photosphere (u_z = 0 there) */
       for (int m = 1; m <= NG; ++m) u[ix(g, F_UZ, -m, j, i)] = -u[ix(g, F_UZ, m, j, i)];
@@ -325,9 +381,10 @@ static void fill_ghosts_impl(const int* dims, const double* p, double* u, const 
        * signed g_z < 0 and p = rho T): rho_{nz+j} = rho_{nz-j} exp((z_{nz+j} -
        * z_{nz-j}) g_z / T_nz) */
       double ttop = exp(u[ix(g, F_LNTT, kt, j, i)]);
-      for (int m = 1; m <= NG; ++m)
-        u[ix(g, F_LNRHO, kt + m, j, i)] =
-            u[ix(g, F_LNRHO, kt - m, j, i)] + (2.0 * m * dz) * gz / ttop;
+      for (int m = 1; m <= NG; ++m) {
+        double span = zgrid_on(g) ? zpos(g, kt + m) - zpos(g, kt - m) : 2.0 * m * dz;
+        u[ix(g, F_LNRHO, kt + m, j, i)] = u[ix(g, F_LNRHO, kt - m, j, i)] + span * gz / ttop;
+      }
       /* closed top: u_z antisymmetric, horizontal velocity symmetric */
       for (int m = 1; m <= NG; ++m) {
         u[ix(g, F_UZ, kt + m, j, i)] = -u[ix(g, F_UZ, kt - m, j, i)];
@@ -337,8 +394,9 @@ static void fill_ghosts_impl(const int* dims, const double* p, double* u, const 
     }
 
   /* (3) potential-field ghosts of all three components of A: regular
-   * extrapolation upward (Eq. 17, Delta''z = m dz), inverted extrapolation
-   * downward with the contrast growth reduced by f_b (Sect. 2.4). */
+   * extrapolation upward (Eq. 17, Delta''z = z_{nz-1+m} - z_{nz-1}, m dz on
+   * the uniform grid), inverted extrapolation downward over z_0 - z_{-m}
+   * with the contrast growth reduced by f_b (Sect. 2.4). */
   if (!do_pfe) return;
   size_t n = (size_t)nx * ny;
   double* plane = (double*)malloc(sizeof(double) * n);
@@ -347,8 +405,11 @@ static void fill_ghosts_impl(const int* dims, const double* p, double* u, const 
   for (int side = 0; side < 2; ++side) {
     int kb = side == 0 ? nz - 1 : 0;
     double zf[NG];
-    for (int m = 1; m <= NG; ++m)
-      zf[m - 1] = side == 0 ? -(double)m * dz : p[P_FB] * (double)m * dz;
+    for (int m = 1; m <= NG; ++m) {
+      double d = zgrid_on(g) ? (side == 0 ? zpos(g, kb + m) - zpos(g, kb) : zpos(g, kb) - zpos(g, kb - m))
+                             : (double)m * dz;
+      zf[m - 1] = side == 0 ? -d : p[P_FB] * d;
+    }
     for (int f = F_AX; f <= F_AZ; ++f) {
       for (int j = 0; j < ny; ++j)
         for (int i = 0; i < nx; ++i) plane[(size_t)j * nx + i] = u[ix(g, f, kb, j, i)];
@@ -442,8 +503,9 @@ static double nc_cutoff(double x, double x1, double w) {
   return 0.5 * (1.0 + cos(M_PI * (x - (x1 - w)) / w));
 }
 
-static double nc_term(const double* p, int k, double lnrho, double lnT) {
-  double cz = nc_cutoff((double)k * p[P_DZ], p[P_NC_ZMAX], p[P_NC_ZW]);
+/* z: the height of layer k */
+static double nc_term(const double* p, int k, double z, double lnrho, double lnT) {
+  double cz = nc_cutoff(z, p[P_NC_ZMAX], p[P_NC_ZW]);
   double crho = nc_cutoff(nc_lr[0] - lnrho, p[P_NC_LMAG], p[P_NC_LW]);
   double lnTstar = 0.5 * (nc_lt[k] + nc_lnT_prime(lnrho));
   return -p[P_NC_TAU] * (1.0 - exp(lnTstar - lnT)) * crho * cz;
@@ -460,7 +522,7 @@ static void rhs_cell(const grid_t* g, const double* u, const double* axt, const 
   double kap = p[P_KAPPA0], drho = p[P_DIFFRHO];
   double eta_s = p[P_ETA_S], chi_s = p[P_CHI_S], drho_s = p[P_DIFFRHO_S];
   double w = 0.0, wp = 0.0;
-  or_swamp_weight(p, (double)k * p[P_DZ], &w, &wp);
+  or_swamp_weight(p, zpos(g, k), &w, &wp);
   double A[3], U[3], D1A[3][3], D1U[3][3], lapA[3], lapU[3];
   double gdA[3], gdU[3], gL[3], gT[3];
   for (int c = 0; c < 3; ++c) {
@@ -546,7 +608,7 @@ static void rhs_cell(const grid_t* g, const double* u, const double* axt, const 
   double heat = (gam - 1.0) * (eta * J2 + 2.0 * rho * nu * S2) / (rho * T);
   double cond = (gam - 1.0) * kap * pow(T, 2.5) / rho * (lapT + 3.5 * gT2);
   double dTh = -ugT - (gam - 1.0) * divU + heat + cond + chi_s * w * lapT;
-  if (p[P_NC_TAU] > 0.0 && g->bcz == 0) dTh += nc_term(p, k, lnrho, lnT);
+  if (p[P_NC_TAU] > 0.0 && g->bcz == 0) dTh += nc_term(p, k, zpos(g, k), lnrho, lnT);
 
   if (g->bcz == 0) {
     if (k == 0) {
@@ -627,12 +689,19 @@ double or_cfl(const int* dims, const double* p, const double* u) {
   grid_t G = {dims[0], dims[1], dims[2], dims[3], p};
   const grid_t* g = &G;
   double dx = p[P_DX], dy = p[P_DY], dz = p[P_DZ];
-  double inv2 = 1.0 / (dx * dx) + 1.0 / (dy * dy) + 1.0 / (dz * dz);
   double gam = p[P_GAMMA];
   double max_adv = 0.0, max_dif = 0.0;
   for (int k = 0; k < g->nz; ++k) {
+    /* the local vertical spacing 1 / (dxi/dz) on a non-uniform grid */
+    double dzk = dz;
+    if (zgrid_on(g)) {
+      double m1, m2;
+      zmetric(g, k, &m1, &m2);
+      dzk = 1.0 / m1;
+    }
+    double inv2 = 1.0 / (dx * dx) + 1.0 / (dy * dy) + 1.0 / (dzk * dzk);
     double w = 0.0, wp = 0.0;
-    or_swamp_weight(p, (double)k * dz, &w, &wp);
+    or_swamp_weight(p, zpos(g, k), &w, &wp);
     for (int j = 0; j < g->ny; ++j)
       for (int i = 0; i < g->nx; ++i) {
         double B[3];
@@ -641,7 +710,7 @@ double or_cfl(const int* dims, const double* p, const double* u) {
         double T = exp(u[ix(g, F_LNTT, k, j, i)]);
         double B2 = B[0] * B[0] + B[1] * B[1] + B[2] * B[2];
         double adv = fabs(u[ix(g, F_UX, k, j, i)]) / dx + fabs(u[ix(g, F_UY, k, j, i)]) / dy +
-                     fabs(u[ix(g, F_UZ, k, j, i)]) / dz + sqrt(gam * T + B2 / rho) * sqrt(inv2);
+                     fabs(u[ix(g, F_UZ, k, j, i)]) / dzk + sqrt(gam * T + B2 / rho) * sqrt(inv2);
         double dm = p[P_NU];
         double c1 = p[P_ETA] + p[P_ETA_S] * w;
         double c2 = p[P_DIFFRHO] + p[P_DIFFRHO_S] * w;
@@ -667,10 +736,17 @@ double or_cfl(const int* dims, const double* p, const double* u) {
 void or_stats(const int* dims, const double* p, const double* u, double* out) {
   grid_t G = {dims[0], dims[1], dims[2], dims[3], p};
   const grid_t* g = &G;
-  double dx = p[P_DX], dy = p[P_DY], dz = p[P_DZ], dv = dx * dy * dz;
+  double dx = p[P_DX], dy = p[P_DY], dz = p[P_DZ];
   double ek = 0, em = 0, eth = 0, ms = 0, fn = 0, fa = 0, dbm = 0;
   int nx = g->nx, ny = g->ny, nz = g->nz;
-  for (int k = 0; k < nz; ++k)
+  for (int k = 0; k < nz; ++k) {
+    /* cell volume dx dy Delta'z, Delta'z = (z_{k+1} - z_{k-1}) / 2 the
+     * vertical extent of the cell (Sect. 4.1); dz on the uniform grid */
+    double dv = dx * dy * dz, m1 = 1.0 / dz, m2;
+    if (zgrid_on(g)) {
+      dv = dx * dy * 0.5 * (zpos(g, k + 1) - zpos(g, k - 1));
+      zmetric(g, k, &m1, &m2);
+    }
     for (int j = 0; j < ny; ++j)
       for (int i = 0; i < nx; ++i) {
         double B[3];
@@ -694,10 +770,12 @@ void or_stats(const int* dims, const double* p, const double* u, double* out) {
           double bym = d1(g, u, F_AX, k, j - m, i, 2) - d1(g, u, F_AZ, k, j - m, i, 0);
           double bzp = d1(g, u, F_AY, k + m, j, i, 0) - d1(g, u, F_AX, k + m, j, i, 1);
           double bzm = d1(g, u, F_AY, k - m, j, i, 0) - d1(g, u, F_AX, k - m, j, i, 1);
-          divb += W1[m] * ((bxp - bxm) / dx + (byp - bym) / dy + (bzp - bzm) / dz);
+          divb += W1[m] * ((bxp - bxm) / dx + (byp - bym) / dy +
+                           (zgrid_on(g) ? (bzp - bzm) * m1 : (bzp - bzm) / dz));
         }
         if (fabs(divb) > dbm) dbm = fabs(divb);
       }
+  }
   out[0] = ek; out[1] = em; out[2] = eth; out[3] = ms; out[4] = fn; out[5] = fa; out[6] = dbm;
 }
 
