@@ -158,13 +158,18 @@ def fill_ghosts(p: Dict, u: np.ndarray, lnrho0: np.ndarray, pfe: str = "dft") ->
     lib().or_fill_ghosts_nopfe(_i(_dims(p)), _d(_pvec(p)), _d(u), _d(lnrho0))
     nx, ny, nz = p["nx"], p["ny"], p["nz"]
     lx, ly = nx * p["dx"], ny * p["dy"]
-    z = np.asarray(p["z"], dtype=np.float64) if p.get("z") is not None else \
-        np.arange(-NG, nz + NG) * float(p["dz"])
     kt = NG + nz - 1
+    if p.get("z") is not None:
+        z = np.asarray(p["z"], dtype=np.float64)
+        up = [-(z[kt + m] - z[kt]) for m in (1, 2, 3)]
+        down = [p["f_pfe_bottom"] * (z[NG] - z[NG - m]) for m in (1, 2, 3)]
+    else:
+        dz = p["dz"]
+        up = [-m * dz for m in (1, 2, 3)]
+        down = [p["f_pfe_bottom"] * m * dz for m in (1, 2, 3)]
     for c in range(3):
-        top = pfe_plane_fft(lx, ly, u[c, kt, NG:-NG, NG:-NG], [-(z[kt + m] - z[kt]) for m in (1, 2, 3)])
-        bot = pfe_plane_fft(lx, ly, u[c, NG, NG:-NG, NG:-NG],
-                            [p["f_pfe_bottom"] * (z[NG] - z[NG - m]) for m in (1, 2, 3)])
+        top = pfe_plane_fft(lx, ly, u[c, kt, NG:-NG, NG:-NG], up)
+        bot = pfe_plane_fft(lx, ly, u[c, NG, NG:-NG, NG:-NG], down)
         for m in (1, 2, 3):
             u[c, kt + m] = np.pad(top[m - 1], NG, mode="wrap")
             u[c, NG - m] = np.pad(bot[m - 1], NG, mode="wrap")

@@ -406,9 +406,12 @@ static void fill_ghosts_impl(const int* dims, const double* p, double* u, const 
     int kb = side == 0 ? nz - 1 : 0;
     double zf[NG];
     for (int m = 1; m <= NG; ++m) {
-      double d = zgrid_on(g) ? (side == 0 ? zpos(g, kb + m) - zpos(g, kb) : zpos(g, kb) - zpos(g, kb - m))
-                             : (double)m * dz;
-      zf[m - 1] = side == 0 ? -d : p[P_FB] * d;
+      if (zgrid_on(g)) {
+        double d = side == 0 ? zpos(g, kb + m) - zpos(g, kb) : zpos(g, kb) - zpos(g, kb - m);
+        zf[m - 1] = side == 0 ? -d : p[P_FB] * d;
+      } else {
+        zf[m - 1] = side == 0 ? -(double)m * dz : p[P_FB] * (double)m * dz;
+      }
     }
     for (int f = F_AX; f <= F_AZ; ++f) {
       for (int j = 0; j < ny; ++j)
