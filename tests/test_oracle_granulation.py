@@ -220,3 +220,29 @@ def test_field_at_sampled_pixels_matches_the_map():
     for n, (j, i) in enumerate(pix):
         assert got[n, 0] == pytest.approx(vx[j, i], rel=1e-12, abs=1e-15)
         assert got[n, 1] == pytest.approx(vy[j, i], rel=1e-12, abs=1e-15)
+
+
+def test_population_over_updates():
+    # every update leaves a full packing; a granule keeps its centre and
+    # parameters from birth to death, is born at an update time and is gone
+    # after t0 + 2 t_max
+    nx, ny = 32, 24
+    g = Granulation(nx, ny, 1.0, 1.0, GP)
+    seen = {}
+    deaths = 0
+    for u, t in enumerate(np.arange(0.0, 600.0, 40.0)):
+        before = dict(g.live)
+        g.update(float(t), *_draws(nx, ny, 100 + u))
+        deaths += sum(1 for c in before if c not in g.live)
+        c = np.array(list(g.live.keys()))
+        for j in range(ny):
+            for i in range(nx):
+                assert np.min(g._dist2(j, i, c[:, 0], c[:, 1])) < GP.r_inner ** 2
+        for key, v in g.live.items():
+            if key in seen and seen[key][0] == v[0]:
+                assert seen[key] == v  # unchanged while alive
+            else:
+                assert v[0] == t       # a new granule is born now
+            seen[key] = v
+            assert t - v[0] - v[3] <= v[3]
+    assert deaths > 0
