@@ -18,7 +18,7 @@ Plain numpy, written as the section states the method:
   filtered (Eq. 3), is amplified by f_rot and added back; the sum is scaled
   to the rms speed of the granular field (Eq. 4).
 
-Readings where the section leaves a choice (listed with the design notes):
+Readings where the section leaves a choice:
 the radial profile rises linearly from 0 at the centre to 1 at r_granule
 and falls to 0 at r_lane as cos^2; overlapping fields add; T and v_max
 take a standard normal draw clipped to [-1, 1] times 10 % and 15 %; the
