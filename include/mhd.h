@@ -349,7 +349,12 @@ int mhd_gran_create(int nx, int ny, double dx, double dy,
  *   keys [ny][nx] uint32, c_life, c_amp [ny][nx] double: the random draws
  *   (uniform keys, standard normals); mem: MHD_MEM_DEVICE or MHD_MEM_HOST.
  *   rounds (may be NULL): the parallel rounds taken.
- * Times passed to successive calls should not decrease. */
+ * The arrays are the caller's and may be reused when the call returns (host
+ * arrays are staged into the workspace first).  Times passed to successive
+ * calls should not decrease.  Errors: MHD_ERR_ARG (NULL generator or array,
+ * bad mem flag, non-finite t), MHD_ERR_CUDA, MHD_ERR_TIMEOUT if the rounds
+ * did not settle within nx ny + 1 (they cannot, by the argument above; the
+ * population is then partly updated). */
 int mhd_gran_update(mhd_gran_handle g, double t, const unsigned int* keys,
                     const double* c_life, const double* c_amp, int mem,
                     int* rounds);
@@ -362,7 +367,10 @@ int mhd_gran_update(mhd_gran_handle g, double t, const unsigned int* keys,
  * |k| / k_N = sqrt((k_x dx / pi)^2 + (k_y dy / pi)^2) and the mean and
  * Nyquist modes dropped (Eq. 3), times f_rot added back (v_vor); the sum
  * scaled by sqrt(<|v_gran|^2> / <|v_vor|^2>) (Eq. 4; zero if v_vor is).
- * Asynchronous for device output. */
+ * v is the caller's (device or host per mem).  Asynchronous for device
+ * output; host output returns once copied.  Errors: MHD_ERR_ARG (NULL
+ * generator or v, precision not 32 or 64, bad mem flag, non-finite t),
+ * MHD_ERR_CUDA. */
 int mhd_gran_velocity(mhd_gran_handle g, double t, int precision, void* v,
                       int mem);
 
