@@ -10,7 +10,8 @@
  * photosphere (Sect. 2.4), hydrostatic / symmetric atmospheric ghosts
  * (Sect. 2.5 Eq. 8, Sect. 4.1 Eqs. 11, 13), regular potential-field
  * extrapolation above the top (Sect. 4.2, Eqs. 16-17) and the swamp layer
- * (Sect. 4.3, Eqs. 18-20).
+ * (Sect. 4.3, Eqs. 18-20); its adjoint; and a generator of granulation
+ * driver velocities (Sect. 2.3, Eqs. 1-4, the mhd_gran_* calls).
  *
  * Conventions shared by every entry point
  * - Fields, in this order: Ax, Ay, Az, ux, uy, uz, ln rho, ln T (the
