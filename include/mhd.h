@@ -281,10 +281,15 @@ int mhd_bz_plane_adjoint(mhd_handle h, const void* bbar, int k, void* lam);
  * Allocates nothing: no cudaMalloc, cudaFree or allocating library call.  The
  * first call on a device looks up the array's device address
  * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture.  All calls on a device share the one scratch
- * array: calls that overlap on the GPU (different streams, or different host
- * threads) race and give wrong results.  Asynchronous; errors are reported
- * through mhd_last_error(NULL). */
+ * before any stream capture.  Under CUDA's default lazy module loading that
+ * first call is also what loads the library's module holding the array, so
+ * the 8 MiB + 24 KiB are taken from the device then: a caller that reserves
+ * all of the GPU's memory should make one call first (any size) and reserve
+ * afterwards; later calls take nothing more.  The address is looked up again
+ * if the device's context was destroyed and recreated (cudaDeviceReset).
+ * All calls on a device share the one scratch array: calls that overlap on
+ * the GPU (different streams, or different host threads) race and give wrong
+ * results.  Asynchronous; errors are reported through mhd_last_error(NULL). */
 int mhd_invert_magnetogram_static(int nx, int ny, double dx, double dy,
                                   int precision, const void* bz, void* ax,
                                   void* ay, void* stream);

@@ -8,8 +8,13 @@
 // blocks with a device-wide synchronisation), or code on a latency-critical
 // path that must not pay for an allocation.  This entry point needs no
 // workspace: its FFT scratch (two complex FP64 planes, twiddles and modified
-// wavenumbers) lives in one file-scope __device__ array of fixed size, which
-// every GPU that loads the library keeps until the process exits.
+// wavenumbers) lives in one file-scope __device__ array of fixed size.  The
+// array belongs to this file's device module: under CUDA's default lazy
+// module loading the module, and with it the array, is loaded on a device by
+// the first call there, and stays until the process exits or the context is
+// destroyed.
+#include <cuda.h>
+
 #include <mutex>
 
 #include "../../include/mhd.h"
@@ -28,7 +33,36 @@ constexpr size_t kStaticBytes = kOffKty + (size_t)kStaticMaxN * 8;
 constexpr int kMaxDevices = 64;
 
 std::mutex g_mu;
-void* g_scratch_addr[kMaxDevices];  // device address of the array, per device
+// Device address of the array per device, and the id of the context it was
+// looked up in: a context destroyed and created again (cudaDeviceReset)
+// reloads the module at another address, so the id is checked on every call.
+void* g_scratch_addr[kMaxDevices];
+unsigned long long g_scratch_ctx[kMaxDevices];
+
+// cuCtxGetCurrent and cuCtxGetId through the runtime's driver entry points,
+// so that the library does not link libcuda itself (it must load on hosts
+// without a driver for the ABI checks).
+typedef CUresult (*CtxGetCurrentFn)(CUcontext*);
+typedef CUresult (*CtxGetIdFn)(CUcontext, unsigned long long*);
+
+bool current_context_id(unsigned long long* id) {
+  static CtxGetCurrentFn get_current = nullptr;
+  static CtxGetIdFn get_id = nullptr;
+  if (!get_current || !get_id) {  // called with g_mu held
+    void* f1 = nullptr;
+    void* f2 = nullptr;
+    cudaDriverEntryPointQueryResult q1, q2;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1) != cudaSuccess ||
+        cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) != cudaSuccess ||
+        q1 != cudaDriverEntryPointSuccess || q2 != cudaDriverEntryPointSuccess || !f1 || !f2)
+      return false;
+    get_current = (CtxGetCurrentFn)f1;
+    get_id = (CtxGetIdFn)f2;
+  }
+  CUcontext ctx = nullptr;
+  if (get_current(&ctx) != CUDA_SUCCESS || !ctx) return false;
+  return get_id(ctx, id) == CUDA_SUCCESS;
+}
 }  // namespace
 
 // 8.0 MiB + 24 KiB of FFT scratch, shared by every call on a device.
@@ -96,17 +130,26 @@ extern "C" int mhd_invert_magnetogram_static(int nx, int ny, double dx, double d
   }
   unsigned char* base;
   {
-    // once per device, with that device current: the device address of the
-    // array (its host-side name is only a stand-in)
+    // once per device (and again after its context was recreated), with that
+    // device current: the device address of the array (its host-side name is
+    // only a stand-in).  The lookup also makes the device's primary context
+    // current when the calling thread has none yet.
     std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_scratch_addr[dev]) {
+    unsigned long long ctx = 0;
+    const bool have_ctx = current_context_id(&ctx);
+    if (!have_ctx || !g_scratch_addr[dev] || g_scratch_ctx[dev] != ctx) {
       void* p = nullptr;
       e = cudaGetSymbolAddress(&p, g_inv_scratch);
       if (e != cudaSuccess || !p) {
         set_global_error("mhd_invert_magnetogram_static: cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
         return MHD_ERR_CUDA;
       }
+      if (!have_ctx && !current_context_id(&ctx)) {
+        set_global_error("mhd_invert_magnetogram_static: no current CUDA context after the symbol lookup");
+        return MHD_ERR_CUDA;
+      }
       g_scratch_addr[dev] = p;
+      g_scratch_ctx[dev] = ctx;
     }
     base = (unsigned char*)g_scratch_addr[dev];
   }

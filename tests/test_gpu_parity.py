@@ -413,7 +413,7 @@ def test_tiled_kernel_matches_simple_fp32(shape, bcz, variant):
 
 def test_tiled_full_size_sampled_bipoles40_256():
     """Bench workload bipoles40_256x256x256 in the bench configuration (FP32,
-    tiled kernel): ghost fill + RHS at 3000 sampled cells -- random, plus the
+    the default z-march kernel rk_pair_kernel): ghost fill + RHS at 3000 sampled cells -- random, plus the
     photosphere, the top layer, the swamp and the x,y edges -- against the
     FP64 oracle, which fills its own ghosts (plain DFT) and evaluates the
     sampled cells one by one.  Both sides start from the same values: A and u

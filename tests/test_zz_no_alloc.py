@@ -65,6 +65,28 @@ def test_static_inversion_matches_workspace_path(lib, precision, shape):
         assert np.abs(got - ref).max() <= tol * scale
 
 
+def test_static_inversion_takes_no_device_memory_after_the_first_call(lib):
+    """The first call on a device loads the module that holds the scratch
+    array (lazy module loading); every later call must leave the device's free
+    memory exactly as it was."""
+    nx = ny = 256
+    bz = torch.zeros((ny, nx), dtype=torch.float32, device="cuda")
+    bz[10, 20], bz[200, 100] = 1.0, -1.0
+    ax = torch.empty_like(bz)
+    ay = torch.empty_like(bz)
+    stream = torch.cuda.current_stream()
+    args = (nx, ny, 1.0, 1.0, 32, ctypes.c_void_p(bz.data_ptr()), ctypes.c_void_p(ax.data_ptr()),
+            ctypes.c_void_p(ay.data_ptr()), ctypes.c_void_p(stream.cuda_stream))
+    assert lib.mhd_invert_magnetogram_static(*args) == 0, lib.mhd_last_error(None)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for _ in range(3):
+        assert lib.mhd_invert_magnetogram_static(*args) == 0, lib.mhd_last_error(None)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+
+
 def test_static_inversion_rejects_oversize(lib):
     from paper_1908_08557_gb300 import binding
     rc = lib.mhd_invert_magnetogram_static(1024, 1024, 1.0, 1.0, 32, ctypes.c_void_p(256), ctypes.c_void_p(256),
