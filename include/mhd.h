@@ -105,6 +105,16 @@ typedef struct mhd_params {
   double nc_tau;       /* inverse relaxation time (the paper: 0.5 / s) */
   double nc_lnrho_magn, nc_lnrho_width; /* density cut-off: 8 and 2 e-folds */
   double nc_z_max, nc_z_width;          /* height cut-off (3 and 0.3 Mm) */
+  /* 1: store A as a perturbation A' = A - A_bg about a fixed background field
+   * A_bg given in FP64 by mhd_set_a_background (zero until then), the way ln
+   * rho and ln T are stored about their profiles.  The workspace then also
+   * holds, per interior cell, the background's B_bg = curl A_bg and
+   * J_bg = grad div A_bg - lap A_bg (FP64 stencils, stored in the state
+   * precision), lap A_bg and div A_bg on the swamp layers, and A_bg itself.
+   * The discrete equations are unchanged (the stencils are linear); FP32
+   * rounding then scales with |A'| instead of |A|, which matters where A is
+   * large (hundreds in the production-size box).  Not with adjoint = 1. */
+  int a_background;
 } mhd_params;
 
 /* Diagnostics of the ghost-filled state at time t (FP64 sums). */
@@ -162,6 +172,27 @@ int mhd_set_driver(mhd_handle h, const void* bz, const void* v0,
  * graph replays correctly when it holds an even number of steps, and the
  * diagnostics schedule (stats_every) is the one seen at capture. */
 int mhd_step(mhd_handle h, int nsteps);
+
+/* Background of the vector potential (needs params.a_background = 1; not a
+ * step of the paper's method but a storage format, like the ln rho and ln T
+ * profiles of mhd_create).  Sets A = a_bg + a_pert, stored as the fixed
+ * background a_bg and the perturbation A' = a_pert:
+ *   a_bg: [3][nz][ny][nx] FP64 (A_x, A_y, A_z; mem selects host or device),
+ *     typically the initial potential field in FP64.  Its ghost layers come
+ *     from the same boundary rules as the state's (the potential-field
+ *     extrapolations of Sect. 4.2 and 2.4, or periodic copies when bc_z = 1),
+ *     applied once here in FP64.
+ *   a_pert: [3][nz][ny][nx] in the handle's precision (same mem), or NULL
+ *     for A' = 0.
+ * The other five fields are left as they are.  Afterwards mhd_read and
+ * mhd_read_padded return A' + A_bg (A_bg rounded to the handle's precision),
+ * mhd_write stores A' = A - A_bg, and the diagnostics, the CFL rule and the
+ * nudging of A_hor toward the target (whose difference from A_bg at the
+ * photosphere is formed in FP64) see the full A; max |div B| is that of
+ * curl A' (div curl A_bg vanishes to FP64 rounding).  May be called again
+ * (each call replaces the background and the state's A).  Synchronises the
+ * stream. */
+int mhd_set_a_background(mhd_handle h, const double* a_bg, const void* a_pert, int mem);
 
 /* Copy the interior of one field (0..7) or of all fields (-1) into dst
  * ([nz][ny][nx] or [8][nz][ny][nx]).  With MHD_MEM_HOST the call

@@ -40,7 +40,7 @@ EXPORTED = ("mhd_workspace_bytes", "mhd_create", "mhd_set_driver", "mhd_step",
             "mhd_adjoint_init", "mhd_adjoint_step", "mhd_adjoint_read", "mhd_bz_plane",
             "mhd_bz_plane_adjoint", "mhd_gran_workspace_bytes", "mhd_gran_create", "mhd_gran_update",
             "mhd_gran_velocity", "mhd_gran_read_granules", "mhd_gran_read_field", "mhd_gran_launch_count",
-            "mhd_gran_last_error", "mhd_gran_destroy")
+            "mhd_gran_last_error", "mhd_gran_destroy", "mhd_set_a_background")
 KERNEL_CLASSES = ("ghost", "pfe", "cfl", "stats", "rk")
 
 
@@ -67,7 +67,7 @@ class Params(ctypes.Structure):
                 ("dt_fixed", ctypes.c_double), ("bext", ctypes.c_double * 3),
                 ("nc_tau", ctypes.c_double), ("nc_lnrho_magn", ctypes.c_double),
                 ("nc_lnrho_width", ctypes.c_double), ("nc_z_max", ctypes.c_double),
-                ("nc_z_width", ctypes.c_double)]
+                ("nc_z_width", ctypes.c_double), ("a_background", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -108,6 +108,7 @@ def load(path: Optional[str] = None):
     dpp = ctypes.POINTER(ctypes.c_double)
     lib.mhd_create.argtypes = [P, vp, sz, vp, i, dpp, dpp, vp, ctypes.POINTER(vp)]
     lib.mhd_set_driver.argtypes = [vp, vp, vp, vp, d, d, i]
+    lib.mhd_set_a_background.argtypes = [vp, vp, vp, i]
     lib.mhd_step.argtypes = [vp, i]
     lib.mhd_read.argtypes = [vp, i, vp, i]
     lib.mhd_write.argtypes = [vp, vp, i]
@@ -162,7 +163,8 @@ def load(path: Optional[str] = None):
     return lib
 
 
-def make_params(p: Dict, precision: int = 32, stats_every: int = 0, adjoint: bool = False) -> Params:
+def make_params(p: Dict, precision: int = 32, stats_every: int = 0, adjoint: bool = False,
+                a_background: bool = False) -> Params:
     q = Params()
     q.nx, q.ny, q.nz = int(p["nx"]), int(p["ny"]), int(p["nz"])
     q.precision = int(precision)
@@ -183,21 +185,28 @@ def make_params(p: Dict, precision: int = 32, stats_every: int = 0, adjoint: boo
     q.nc_lnrho_width = float(p.get("nc_lnrho_width", 2.0))
     q.nc_z_max = float(p.get("nc_z_max", 10.0 * float(p["dz"])))
     q.nc_z_width = float(p.get("nc_z_width", 1.0 * float(p["dz"])))
+    q.a_background = 1 if a_background else 0
     return q
 
 
-def workspace_bytes(p: Dict, precision: int = 32) -> int:
-    q = make_params(p, precision)
+def workspace_bytes(p: Dict, precision: int = 32, a_background: bool = False) -> int:
+    q = make_params(p, precision, a_background=a_background)
     return int(load().mhd_workspace_bytes(ctypes.byref(q)))
 
 
 class Simulation:
     """One libmhd handle.  Arrays passed in may be torch CUDA tensors
     (device pointers) or numpy arrays (host pointers); the element type must
-    match the precision (float32 / float64)."""
+    match the precision (float32 / float64).
+
+    a_background: an FP64 [3][nz][ny][nx] field (numpy array or float64 CUDA
+    tensor), typically the initial potential field.  A is then stored as a
+    perturbation about it (mhd_set_a_background): the state's A fields are
+    replaced by this background, with zero perturbation."""
 
     def __init__(self, params: Dict, init_state, lnrho0, lnT0=None, precision: int = 32,
-                 stats_every: int = 0, device: str = "cuda:0", stream=None, adjoint: bool = False):
+                 stats_every: int = 0, device: str = "cuda:0", stream=None, adjoint: bool = False,
+                 a_background=None):
         import torch
         self.lib = load()
         self.params = dict(params)
@@ -205,7 +214,7 @@ class Simulation:
         self.np_dtype = np.float32 if precision == 32 else np.float64
         self.torch_dtype = torch.float32 if precision == 32 else torch.float64
         self.device = torch.device(device)
-        self._p = make_params(params, precision, stats_every, adjoint)
+        self._p = make_params(params, precision, stats_every, adjoint, a_background is not None)
         nbytes = int(self.lib.mhd_workspace_bytes(ctypes.byref(self._p)))
         if nbytes == 0:
             raise MHDError(MHD_ERR_ARG, "invalid parameters")
@@ -235,6 +244,8 @@ class Simulation:
         if rc != MHD_OK:
             raise MHDError(rc, self.lib.mhd_last_error(None).decode())
         self.h = h
+        if a_background is not None:
+            self.set_a_background(a_background)
 
     # -- marshalling --
     def _in(self, a, shape):
@@ -256,6 +267,37 @@ class Simulation:
             raise MHDError(rc, self.lib.mhd_last_error(self.h).decode())
 
     # -- API --
+    def set_a_background(self, a_bg, a_pert=None):
+        """A = a_bg (FP64, [3][nz][ny][nx]) + a_pert (the handle's precision,
+        or None for zero), stored as background and perturbation."""
+        import torch
+        shape = (3, self._p.nz, self._p.ny, self._p.nx)
+        on_dev = lambda a: isinstance(a, torch.Tensor) and a.is_cuda
+        # one mem flag for both arrays: a host array beside a device one is
+        # copied to the device first
+        if on_dev(a_pert) and not on_dev(a_bg):
+            a_bg = torch.as_tensor(np.ascontiguousarray(a_bg, dtype=np.float64), device=self.device)
+        elif on_dev(a_bg) and a_pert is not None and not on_dev(a_pert):
+            a_pert = torch.as_tensor(np.ascontiguousarray(a_pert, dtype=self.np_dtype), device=self.device)
+        if on_dev(a_bg):
+            if a_bg.dtype != torch.float64 or tuple(a_bg.shape) != shape or not a_bg.is_contiguous():
+                raise ValueError(f"a_bg must be a contiguous float64 tensor of shape {shape}")
+            bp, mem, keep_b = ctypes.c_void_p(a_bg.data_ptr()), MHD_MEM_DEVICE, a_bg
+        else:
+            if isinstance(a_bg, torch.Tensor):
+                a_bg = a_bg.numpy()
+            keep_b = np.ascontiguousarray(a_bg, dtype=np.float64)
+            if keep_b.shape != shape:
+                raise ValueError(f"a_bg must have shape {shape}")
+            bp, mem = ctypes.c_void_p(keep_b.ctypes.data), MHD_MEM_HOST
+        pp, keep_p = None, None
+        if a_pert is not None:
+            pp, mp, keep_p = self._in(a_pert, shape)
+            if mp != mem:
+                raise ValueError("a_bg and a_pert must both be host arrays or both device tensors")
+        self._check(self.lib.mhd_set_a_background(self.h, bp, pp, mem))
+        del keep_b, keep_p
+
     def set_driver(self, bz, v0, v1, t0: float, t1: float):
         n = (self._p.ny, self._p.nx)
         b, mb, k1 = self._in(bz, n)

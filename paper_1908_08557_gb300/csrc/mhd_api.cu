@@ -65,6 +65,14 @@ struct mhd_ctx {
   double* thbar;       // [6][ny][nx] parameter adjoints (FP64)
   Background<float> bgf;
   Background<double> bgd;
+  // A stored about a fixed FP64 background (params a_background)
+  bool abg_mode;
+  void* abB;           // [6][nz][ny][nx]: B_bg (3), J_bg (3), state precision
+  void* abL;           // [4][nz - ksw][ny][nx]: lap A_bg (3), div A_bg on the swamp layers
+  void* abgR;          // A_bg in the padded layout, fields 0..2, state precision
+  double* abg0;        // [2][ny][nx] FP64 A_bg_x, A_bg_y at the photosphere
+  double* at64;        // [3][ny][nx] FP64 scratch: B_z target, A_x, A_y of the target
+  void* atrel;         // [2][ny][nx] nudging target minus A_bg(k = 0), state precision
   FFTPlan fp;
   bool have_fft;
   bool driver_set;
@@ -146,6 +154,8 @@ static const char* check_params(const mhd_params* p) {
   if (!(p->gamma > 1.0)) return "gamma must exceed 1";
   if (p->stats_every < 0) return "stats_every must be >= 0";
   if (p->adjoint != 0 && p->adjoint != 1) return "adjoint must be 0 or 1";
+  if (p->a_background != 0 && p->a_background != 1) return "a_background must be 0 or 1";
+  if (p->a_background && p->adjoint) return "a_background is not supported with adjoint = 1";
   if ((long long)p->nx * p->ny * p->nz > (1LL << 34)) return "grid too large";
   if (p->adjoint && (long long)NF * (p->nz + 2 * NG) * p->ny * (p->nx / 4) >= (1LL << 31))
     return "grid too large for the adjoint (8 (nz + 6) ny nx / 4 must stay below 2^31)";
@@ -170,6 +180,7 @@ struct Carve {
 struct Offsets {
   size_t f0, f1, df, lnrho0, wtab, wptab, bz, axt, ayt, v0, v1, red, ss, bg, bj, sw;
   size_t s2, fbar, dbar, gbar, coef, thbar;
+  size_t abB, abL, abgR, abg0, at64, atrel;
   size_t twx, twy, et, eb, ktx, kty, P, Q;
   size_t total;
 };
@@ -207,11 +218,21 @@ static Offsets plan_offsets(const mhd_params* p) {
   o.red = c.take(((size_t)RED_BLOCKS_MAX * 8 + 2 * CFL_SLOTS) * sizeof(double));
   o.ss = c.take(sizeof(StepState));
   o.bg = c.take((size_t)(6 * p->nz + 12) * es);
-  if (p->precision == 32) {
+  if (p->precision == 32 && !p->a_background) {
     o.bj = c.take((size_t)6 * n2 * p->nz * 4);
     o.sw = c.take((size_t)3 * n2 * (p->nz - swamp_first_layer(p)) * 4);
   } else {
     o.bj = o.sw = 0;
+  }
+  if (p->a_background) {
+    o.abB = c.take((size_t)6 * n2 * p->nz * es);
+    o.abL = c.take((size_t)4 * n2 * (p->nz - swamp_first_layer(p)) * es);
+    o.abgR = c.take((size_t)3 * L.fs * es);
+    o.abg0 = c.take(2 * n2 * 8);
+    o.at64 = c.take(3 * n2 * 8);
+    o.atrel = c.take(2 * n2 * es);
+  } else {
+    o.abB = o.abL = o.abgR = o.abg0 = o.at64 = o.atrel = 0;
   }
   if (p->adjoint) {
     o.s2 = c.take(set);
@@ -372,6 +393,15 @@ static int upload_background(mhd_ctx* h, const double* lnrho0, const double* lnT
   bg.dt = bg.d2l + nz;
   bg.d2t = bg.dt + nz;
   for (int m = 0; m <= NG; ++m) { bg.cb[m] = R(0); bg.ctT[m] = R(0); bg.ctL[m] = R(0); }
+  bg.ksw = h->ksw;
+  bg.bB = bg.bJ = bg.bL = bg.abg = nullptr;
+  if (h->abg_mode) {
+    const long long n3 = (long long)p->nx * p->ny * nz;
+    bg.bB = (const R*)h->abB;
+    bg.bJ = bg.bB + 3 * n3;
+    bg.bL = (const R*)h->abL;
+    bg.abg = (const R*)h->abgR;
+  }
   for (int m = 1; m <= NG; ++m) {
     const int b1 = NG - m + 1, b0 = NG - m;
     bg.cb[m] = (R)(tb[b1] - tb[b0] + lb[b1] - lb[b0]);
@@ -433,10 +463,18 @@ static void run_stats(mhd_ctx* h, R* f) {
 
 // fused RHS + RK launch: TMA-fed z-march for FP32 (unless disabled), the
 // simple one-thread-per-cell kernel otherwise
+// the nudging target the kernels see: A_target itself, or (A stored about a
+// background) A_target - A_bg(k = 0), formed in FP64
+static Driver kernel_driver(const mhd_ctx* h) {
+  if (h->abg_mode)
+    return Driver{h->atrel, (const char*)h->atrel + (size_t)h->p.nx * h->p.ny * h->esz, h->v0, h->v1};
+  return Driver{h->axt, h->ayt, h->v0, h->v1};
+}
+
 template <typename R>
 static void launch_rk_any(mhd_ctx* h, const R* fin, R* fout, int sub) {
   Phys<R> ph = make_phys<R>(&h->p);
-  Driver drv{h->axt, h->ayt, h->v0, h->v1};
+  Driver drv = kernel_driver(h);
   if (sizeof(R) == 4 && h->pair) {
     const int which = (const void*)fin == h->f[0] ? 0 : 1;
     launch_rk_pair(&h->tm[which], &h->tmdf, h->L, *(const Phys<float>*)&ph, h->bgf, (float*)fout, (float*)h->df,
@@ -464,7 +502,6 @@ static void launch_rk_any(mhd_ctx* h, const R* fin, R* fout, int sub) {
 template <typename R>
 static void run_step(mhd_ctx* h, bool stats) {
   Phys<R> ph = make_phys<R>(&h->p);
-  Driver drv{h->axt, h->ayt, h->v0, h->v1};
   for (int sub = 0; sub < 3; ++sub) {
     R* fin = (R*)h->f[h->cur];
     R* fout = (R*)h->f[1 - h->cur];
@@ -633,6 +670,15 @@ extern "C" int mhd_create(const mhd_params* p, void* workspace, size_t ws_bytes,
   h->bj = h->ws + o.bj;
   h->sw = h->ws + o.sw;
   h->ksw = swamp_first_layer(p);
+  h->abg_mode = p->a_background != 0;
+  if (h->abg_mode) {
+    h->abB = h->ws + o.abB;
+    h->abL = h->ws + o.abL;
+    h->abgR = h->ws + o.abgR;
+    h->abg0 = (double*)(h->ws + o.abg0);
+    h->at64 = (double*)(h->ws + o.at64);
+    h->atrel = h->ws + o.atrel;
+  }
   if (p->adjoint) {
     h->s2 = h->ws + o.s2;
     h->fbar = h->ws + o.fbar;
@@ -648,6 +694,14 @@ extern "C" int mhd_create(const mhd_params* p, void* workspace, size_t ws_bytes,
     h->split = h->tiled && !(v && strcmp(v, "fused") == 0);
     h->pair = h->split && !(v && (strcmp(v, "tiled") == 0 || strcmp(v, "split") == 0)) &&
               rk_pair_supported(h->L);
+    if (h->abg_mode && h->tiled && !h->pair) {
+      // the background tables are read by the pair kernel and the simple
+      // kernel only
+      free(h);
+      return fail(nullptr, MHD_ERR_UNSUPPORTED,
+                  "a_background needs the default FP32 kernel (nx even, nx >= 8, ny >= 6) or MHD_RK_VARIANT=simple");
+    }
+    if (h->abg_mode) h->split = false;
     const char* va = getenv("MHD_ADJ_VARIANT");
     h->adj_tiled = !(va && strcmp(va, "simple") == 0);
     h->adj_zm = h->adj_tiled && !(va && strcmp(va, "tiled3d") == 0);
@@ -716,6 +770,12 @@ extern "C" int mhd_create(const mhd_params* p, void* workspace, size_t ws_bytes,
     // zero the driver (no nudging target until mhd_set_driver)
     rc = cuda_check(h, cudaMemsetAsync(h->bz, 0, (size_t)(o.red - o.bz), h->st), "zero driver");
   }
+  if (!rc && h->abg_mode) {
+    // no background until mhd_set_a_background: every table zero
+    rc = cuda_check(h, cudaMemsetAsync(h->ws + o.abB, 0, o.at64 - o.abB, h->st), "zero background tables");
+    if (!rc) rc = cuda_check(h, cudaMemsetAsync(h->atrel, 0, 2 * (size_t)p->nx * p->ny * h->esz, h->st),
+                             "zero background target");
+  }
   // background profiles: ln T from the given profile or the layer means of
   // the initial state (staged in the accumulator buffer)
   if (!rc) {
@@ -776,6 +836,77 @@ extern "C" int mhd_write(mhd_handle h, const void* src, int mem) {
   return rc;
 }
 
+// A stored about a background: the nudging target relative to the
+// background's photospheric layer, A_target - A_bg(k = 0), with A_target
+// inverted again in FP64 (the stored axt, ayt are rounded to the state
+// precision, which at |A| ~ 1e2 would put FP32 rounding noise into the
+// nudging at the photosphere).
+static int background_target(mhd_ctx* h) {
+  const long long n2 = (long long)h->p.nx * h->p.ny;
+  double* bz64 = h->at64 + 2 * n2;
+  if (h->esz == 8) launch_widen<double>((const double*)h->bz, bz64, n2, h->st);
+  else launch_widen<float>((const float*)h->bz, bz64, n2, h->st);
+  launch_atarget<double>(h->fp, bz64, h->at64, h->at64 + n2, h->st);
+  if (h->esz == 8) launch_abg_target<double>(h->at64, h->abg0, (double*)h->atrel, 2 * n2, h->st);
+  else launch_abg_target<float>(h->at64, h->abg0, (float*)h->atrel, 2 * n2, h->st);
+  return cuda_check(h, cudaSuccess, "background nudging target");
+}
+
+template <typename R>
+static void background_tables(mhd_ctx* h, const double* a64) {
+  const Layout& L = h->L;
+  launch_abg_tables<R>(L, h->p.dx, h->p.dy, h->p.dz, a64, (R*)h->abB, (R*)h->abB + 3LL * L.nx * L.ny * L.nz,
+                       (R*)h->abL, h->ksw, h->abg0, (R*)h->abgR, h->st);
+}
+
+extern "C" int mhd_set_a_background(mhd_handle h, const double* a_bg, const void* a_pert, int mem) {
+  if (!h) return fail(nullptr, MHD_ERR_ARG, "NULL handle");
+  if (!h->abg_mode) return fail(h, MHD_ERR_ARG, "the handle was created with a_background = 0");
+  if (!a_bg) return fail(h, MHD_ERR_ARG, "a_bg is NULL");
+  if (mem != MHD_MEM_DEVICE && mem != MHD_MEM_HOST) return fail(h, MHD_ERR_ARG, "bad mem flag");
+  const Layout& L = h->L;
+  const size_t n3 = (size_t)L.nx * L.ny * L.nz;
+  // FP64 background, ghost-filled, in the RK accumulator's memory (fields
+  // 0..2 of an FP64 state layout: 24 fs bytes of the accumulator's 8 fs esz);
+  // a host input is staged in the other state set first
+  double* a64 = (double*)h->df;
+  const double* src = a_bg;
+  int rc = MHD_OK;
+  if (mem == MHD_MEM_HOST) {
+    double* stage = (double*)h->f[1 - h->cur];
+    rc = cuda_check(h, cudaMemcpyAsync(stage, a_bg, 3 * n3 * 8, cudaMemcpyHostToDevice, h->st), "copy background in");
+    src = stage;
+  }
+  if (!rc) rc = cuda_check(h, cudaMemsetAsync(a64, 0, (size_t)3 * L.fs * 8, h->st), "zero background scratch");
+  if (rc) return rc;
+  launch_abg_unpack64(L, src, a64, h->st);
+  if (h->have_fft) launch_pfe<double>(h->fp, L, a64, h->ss, h->st, nullptr);
+  else launch_abg_zper(L, a64, h->st);
+  if (h->esz == 8) background_tables<double>(h, a64);
+  else background_tables<float>(h, a64);
+  rc = cuda_check(h, cudaSuccess, "background tables");
+  if (rc) return rc;
+  // the state's A is now the perturbation: a_pert, or zero
+  const size_t abytes = (size_t)3 * L.fs * h->esz;
+  rc = cuda_check(h, cudaMemsetAsync(h->f[h->cur], 0, abytes, h->st), "zero A");
+  if (!rc && a_pert) {
+    const void* ps = a_pert;
+    if (mem == MHD_MEM_HOST) {
+      rc = cuda_check(h, cudaMemcpyAsync(h->df, a_pert, 3 * n3 * h->esz, cudaMemcpyHostToDevice, h->st),
+                      "copy perturbation in");
+      ps = h->df;
+    }
+    if (!rc) {
+      if (h->esz == 8) launch_abg_pert<double>(L, (const double*)ps, (double*)h->f[h->cur], h->st);
+      else launch_abg_pert<float>(L, (const float*)ps, (float*)h->f[h->cur], h->st);
+      rc = cuda_check(h, cudaSuccess, "perturbation");
+    }
+  }
+  if (!rc && h->have_fft && h->driver_set) rc = background_target(h);
+  if (!rc) rc = cuda_check(h, cudaStreamSynchronize(h->st), "background synchronize");
+  return rc;
+}
+
 extern "C" int mhd_set_driver(mhd_handle h, const void* bz, const void* v0, const void* v1, double t0,
                               double t1, int mem) {
   if (!h) return fail(nullptr, MHD_ERR_ARG, "NULL handle");
@@ -794,6 +925,8 @@ extern "C" int mhd_set_driver(mhd_handle h, const void* bz, const void* v0, cons
     if (h->esz == 8) launch_atarget<double>(h->fp, (const double*)h->bz, (double*)h->axt, (double*)h->ayt, h->st);
     else launch_atarget<float>(h->fp, (const float*)h->bz, (float*)h->axt, (float*)h->ayt, h->st);
     rc = cuda_check(h, cudaSuccess, "magnetogram inversion");
+    if (rc) return rc;
+    if (h->abg_mode) rc = background_target(h);
     if (rc) return rc;
   }
   h->driver_set = true;

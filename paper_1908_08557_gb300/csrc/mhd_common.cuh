@@ -78,6 +78,16 @@ struct Background {
   R cb[4];         // bottom ghost rule constants, index m = 1..3
   R ctT[4];        // top ln T rule constants
   R ctL[4];        // top ln rho rule constants
+  // A stored as a perturbation A' about a fixed field A_bg (params
+  // a_background; all null otherwise).  The stencils are linear, so
+  // B = curl A' + bB, J = grad div A' - lap A' + bJ, and on the swamp layers
+  // lap A = lap A' + bL[0..2], div A = div A' + bL[3]; these tables come from
+  // FP64 stencils of the ghost-filled A_bg.
+  const R* bB;     // [3][nz][ny][nx] curl A_bg
+  const R* bJ;     // [3][nz][ny][nx] grad div A_bg - lap A_bg
+  const R* bL;     // [4][nz - ksw][ny][nx] lap A_bg (3), div A_bg on layers k >= ksw
+  const R* abg;    // A_bg itself in the padded layout, fields 0..2 (read, write)
+  int ksw;         // first layer with a nonzero swamp weight or slope
 };
 
 // Device-resident bookkeeping of the time integration (FP64).

@@ -113,10 +113,14 @@ void launch_bc(const Layout& L, const Phys<R>& ph, const Background<R>& bg, R* f
 }
 
 // interior [field][nz][ny][nx] <-> padded; the background is added on the
-// way out and removed on the way in
+// way out and removed on the way in (ln rho, ln T: the profiles; A: the
+// background field when A is stored about one)
 template <typename R>
-__device__ __forceinline__ R bg_at(const Background<R>& bg, int fl, int k) {
-  return fl == LR ? bg.lbar[k + NG] : (fl == LT ? bg.tbar[k + NG] : R(0));
+__device__ __forceinline__ R bg_at(const Layout& L, const Background<R>& bg, int fl, int k, int j, int i) {
+  if (fl == LR) return bg.lbar[k + NG];
+  if (fl == LT) return bg.tbar[k + NG];
+  if (fl <= AZ && bg.abg) return bg.abg[L.at(fl, k, j, i)];
+  return R(0);
 }
 
 template <typename R>
@@ -131,7 +135,7 @@ __global__ void pack_kernel(Layout L, Background<R> bg, const R* __restrict__ f,
     r /= L.ny;
     int k = (int)(r % L.nz);
     int fl = f0 + (int)(r / L.nz);
-    out[q] = f[L.at(fl, k, j, i)] + bg_at(bg, fl, k);
+    out[q] = f[L.at(fl, k, j, i)] + bg_at(L, bg, fl, k, j, i);
   }
 }
 
@@ -146,7 +150,7 @@ __global__ void unpack_kernel(Layout L, Background<R> bg, const R* __restrict__ 
     r /= L.ny;
     int k = (int)(r % L.nz);
     int fl = (int)(r / L.nz);
-    f[L.at(fl, k, j, i)] = in[q] - bg_at(bg, fl, k);
+    f[L.at(fl, k, j, i)] = in[q] - bg_at(L, bg, fl, k, j, i);
   }
 }
 
@@ -163,7 +167,7 @@ __global__ void pack_padded_kernel(Layout L, Background<R> bg, const R* __restri
     r /= ph;
     int k = (int)(r % L.mz) - NG;
     int fl = (int)(r / L.mz);
-    out[q] = f[L.at(fl, k, j, i)] + bg_at(bg, fl, k);
+    out[q] = f[L.at(fl, k, j, i)] + bg_at(L, bg, fl, k, j, i);
   }
 }
 

@@ -135,6 +135,22 @@ template <typename R> void launch_pfe_adjoint(const FFTPlan& fp_adj, const Layou
                                               cudaStream_t st);
 template <typename R> void launch_atarget_adjoint(const FFTPlan& fp, const double* abx, const double* aby, R* out,
                                                   cudaStream_t st);
+// A stored about a fixed background (params a_background): FP64 packed
+// [3][nz][ny][nx] into fields 0..2 of a padded FP64 array (interior and x,y
+// images); a perturbation A' into the state's fields 0..2 likewise; periodic
+// z ghosts of the FP64 background (bc_z = 1); the per-cell tables B, J and the
+// swamp-layer lap A, div A of the ghost-filled background, its photospheric
+// A_x, A_y (FP64, a0 [2][ny][nx]) and its padded copy in the state precision
+// (abg, 3 fields); the nudging target relative to the background,
+// rel = at - a0 over n values; R -> FP64 widening
+void launch_abg_unpack64(const Layout& L, const double* in, double* a, cudaStream_t st);
+template <typename R> void launch_abg_pert(const Layout& L, const R* in, R* f, cudaStream_t st);
+void launch_abg_zper(const Layout& L, double* a, cudaStream_t st);
+template <typename R> void launch_abg_tables(const Layout& L, double dx, double dy, double dz, const double* a,
+                                             R* bB, R* bJ, R* bL, int ksw, double* a0, R* abg, cudaStream_t st);
+template <typename R> void launch_abg_target(const double* at, const double* a0, R* rel, long long n,
+                                             cudaStream_t st);
+template <typename R> void launch_widen(const R* in, double* out, long long n, cudaStream_t st);
 // reductions
 // CFL block maxima by atomicMax into CFL_SLOTS slot pairs at `partial`
 // (zeroed first when `zero`); the planes: all, the inner ones whose stencils

@@ -102,12 +102,22 @@ __global__ void __launch_bounds__(256) cfl_partial_kernel(Layout L, Phys<R> ph, 
     const R lrs[2] = {plr.x, plr.y}, lts[2] = {plt.x, plt.y};
     const R w = wtab[k];
     const int nc = i + 1 < L.nx ? 2 : 1;
+    // A stored about a background: its curl per cell
+    R gb[3][2] = {{R(0), R(0)}, {R(0), R(0)}, {R(0), R(0)}};
+    if (bg.bB) {
+      const long long n2 = (long long)L.nx * L.ny, n3 = n2 * L.nz, q3 = (long long)k * n2 + (long long)j * L.nx + i;
+#pragma unroll
+      for (int cc = 0; cc < 3; ++cc) {
+        gb[cc][0] = bg.bB[cc * n3 + q3];
+        if (nc == 2) gb[cc][1] = bg.bB[cc * n3 + q3 + 1];
+      }
+    }
 #pragma unroll
     for (int c = 0; c < 2; ++c) {
       if (c >= nc) break;
-      const R B0 = dyaz[c] - dzay[c] + ph.bext[0];
-      const R B1 = dzax[c] - dxaz[c] + ph.bext[1];
-      const R B2 = dxay[c] - dyax[c] + ph.bext[2];
+      const R B0 = dyaz[c] - dzay[c] + ph.bext[0] + gb[0][c];
+      const R B1 = dzax[c] - dxaz[c] + ph.bext[1] + gb[1][c];
+      const R B2 = dxay[c] - dyax[c] + ph.bext[2] + gb[2][c];
       const R lr = bg.lbar[k + NG] + lrs[c], lt = bg.tbar[k + NG] + lts[c];
       const R T = rexp<R>(lt), rho1 = rexp<R>(-lr);
       const R B2s = B0 * B0 + B1 * B1 + B2 * B2;
@@ -278,10 +288,23 @@ __global__ void __launch_bounds__(256) stats_partial_kernel(Layout L, Phys<R> ph
       const R bxs[2] = {cx.x, cx.y}, bys[2] = {cy.x, cy.y}, bzs[2] = {cz.x, cz.y};
       const R ux[2] = {u0.x, u0.y}, uy[2] = {u1.x, u1.y}, uz[2] = {u2.x, u2.y};
       const R lrs[2] = {plr.x, plr.y}, lts[2] = {plt.x, plt.y};
+      // A stored about a background: its curl per cell (div B stays that of
+      // curl A'; div curl A_bg vanishes to FP64 rounding)
+      R gb[3][2] = {{R(0), R(0)}, {R(0), R(0)}, {R(0), R(0)}};
+      if (bg.bB) {
+        const long long n2 = (long long)L.nx * L.ny, n3 = n2 * L.nz;
+        const long long q3 = (long long)k * n2 + (long long)j * L.nx + i;
+#pragma unroll
+        for (int cc = 0; cc < 3; ++cc) {
+          gb[cc][0] = bg.bB[cc * n3 + q3];
+          if (nc == 2) gb[cc][1] = bg.bB[cc * n3 + q3 + 1];
+        }
+      }
 #pragma unroll
       for (int c = 0; c < 2; ++c) {
         if (c >= nc) break;
-        const R Bx = bxs[c] + ph.bext[0], By = bys[c] + ph.bext[1], Bz = bzs[c] + ph.bext[2];
+        const R Bx = bxs[c] + ph.bext[0] + gb[0][c], By = bys[c] + ph.bext[1] + gb[1][c],
+                Bz = bzs[c] + ph.bext[2] + gb[2][c];
         const R rho = rexp<R>(bg.lbar[k + NG] + lrs[c]);
         const R T = rexp<R>(bg.tbar[k + NG] + lts[c]);
         nadd(0, R(0.5) * rho * (ux[c] * ux[c] + uy[c] * uy[c] + uz[c] * uz[c]));

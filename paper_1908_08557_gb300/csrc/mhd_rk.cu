@@ -116,7 +116,30 @@ __global__ void __launch_bounds__(256, sizeof(R) == 8 ? 2 : 0) rk_simple_kernel(
   c.gT[2] += a.bg.dt[k];
   c.lapT += a.bg.d2t[k];
   R out[NF];
-  rhs_point<R>(c, ph, a.wtab[k], a.wptab[k], out);
+  {
+    const R w = a.wtab[k], wp = a.wptab[k];
+    R B[3], J[3], sw[3];
+    a_terms<R>(c, ph, w, wp, B, J, sw);
+    if (a.bg.bB) {
+      // A stored about a background: add its B, J and (swamp layers) its
+      // lap A, div A terms, all linear in A
+      const long long n2 = (long long)L.nx * L.ny, n3 = n2 * L.nz;
+      const long long q3 = (long long)k * n2 + (long long)j * L.nx + i;
+#pragma unroll
+      for (int cc = 0; cc < 3; ++cc) {
+        B[cc] += a.bg.bB[cc * n3 + q3];
+        J[cc] += a.bg.bJ[cc * n3 + q3];
+      }
+      if (k >= a.bg.ksw) {
+        const long long ns = n2 * (L.nz - a.bg.ksw), qs = (long long)(k - a.bg.ksw) * n2 + (long long)j * L.nx + i;
+        const R ews = ph.eta_s * w;
+        sw[0] += ews * a.bg.bL[qs];
+        sw[1] += ews * a.bg.bL[ns + qs];
+        sw[2] += ews * a.bg.bL[2 * ns + qs] + ph.eta_s * wp * a.bg.bL[3 * ns + qs];
+      }
+    }
+    rhs_point_bj<R>(c, ph, w, B, J, sw, out);
+  }
   if (k < ph.nc_k1) out[LT] += nc_term<R>(ph, a.bg, L.nz, k, c.L, c.Th, nullptr, nullptr);
 
   // substep constants

@@ -299,8 +299,10 @@ __device__ __forceinline__ void adjoint_centre(const Args& a, const float* Pk, c
 // interior cell the NCOEF coefficients of the transposed right-hand side and,
 // at the photosphere, the driver adjoints; no state is stored.
 // NC: the forward right-hand side includes the Newtonian cooling term (a
-// separate instantiation, so that the default path carries none of it)
-template <bool ADJ, bool NC>
+// separate instantiation, so that the default path carries none of it).
+// BG: A is stored about a background field; the background's B, J (every
+// cell) and lap A, div A (swamp layers) come from per-cell tables.
+template <bool ADJ, bool NC, bool BG>
 __global__ void __launch_bounds__(NT, 2) rk_pair_kernel(const __grid_constant__ CUtensorMap tm,
                                                         const __grid_constant__ CUtensorMap tmd, const Args a) {
   extern __shared__ __align__(128) float smem[];
@@ -426,6 +428,17 @@ __global__ void __launch_bounds__(NT, 2) rk_pair_kernel(const __grid_constant__ 
       const float wk = a.wtab[k], wpk = a.wptab[k];
       const float lbk = a.bg.lbar[k + NG], tbk = a.bg.tbar[k + NG];
       const float dlk = a.bg.dl[k], dtk = a.bg.dt[k], d2lk = a.bg.d2l[k], d2tk = a.bg.d2t[k];
+      // background B, J of the pair (A stored about a background), issued
+      // before the waits so that their latency overlaps them
+      f2 gB[3], gJ[3];
+      if constexpr (BG) {
+        const long long n3 = n2 * L.nz, q3 = (long long)k * n2 + (long long)j * L.nx + i;
+#pragma unroll
+        for (int cc = 0; cc < 3; ++cc) {
+          gB[cc] = live ? __ldg(reinterpret_cast<const float2*>(a.bg.bB + cc * n3 + q3)) : F2(0.f);
+          gJ[cc] = live ? __ldg(reinterpret_cast<const float2*>(a.bg.bJ + cc * n3 + q3)) : F2(0.f);
+        }
+      }
       bad = !wait(s3);
       if (bad) break;
       if (tid == 0) {
@@ -544,10 +557,29 @@ __global__ void __launch_bounds__(NT, 2) rk_pair_kernel(const __grid_constant__ 
           J1 = dif(add(add(mxy[1], yyAy), mz[1]), lap1);
           J2 = dif(add(mz[2], d2z[AZ]), lap2);
           const f2 ews = mul(F2(ph.eta_s), w);
-          const f2 divA = add(add(dxAx, dyAy), d1z[AZ]);
-          sw0 = mul(ews, lap0);
-          sw1 = mul(ews, lap1);
-          sw2 = fma2(mul(F2(ph.eta_s), wp), divA, mul(ews, lap2));
+          f2 divA = add(add(dxAx, dyAy), d1z[AZ]);
+          f2 l0 = lap0, l1 = lap1, l2 = lap2;
+          if constexpr (BG) {
+            // the background's lap A and div A on the swamp layers
+            if (live && k >= a.bg.ksw) {
+              const long long ns = n2 * (L.nz - a.bg.ksw), qs = (long long)(k - a.bg.ksw) * n2 + (long long)j * L.nx + i;
+              l0 = add(l0, __ldg(reinterpret_cast<const float2*>(a.bg.bL + qs)));
+              l1 = add(l1, __ldg(reinterpret_cast<const float2*>(a.bg.bL + ns + qs)));
+              l2 = add(l2, __ldg(reinterpret_cast<const float2*>(a.bg.bL + 2 * ns + qs)));
+              divA = add(divA, __ldg(reinterpret_cast<const float2*>(a.bg.bL + 3 * ns + qs)));
+            }
+          }
+          sw0 = mul(ews, l0);
+          sw1 = mul(ews, l1);
+          sw2 = fma2(mul(F2(ph.eta_s), wp), divA, mul(ews, l2));
+        }
+        if constexpr (BG) {
+          B0 = add(B0, gB[0]);
+          B1 = add(B1, gB[1]);
+          B2 = add(B2, gB[2]);
+          J0 = add(J0, gJ[0]);
+          J1 = add(J1, gJ[1]);
+          J2 = add(J2, gJ[2]);
         }
       }
       // u: dU[c][a] = d_a u_c, lap u, grad div u
@@ -757,11 +789,15 @@ bool rk_pair_supported(const Layout& L) { return L.nx % 2 == 0 && L.nx >= 8 && L
 static pair::Args pair_args(const Layout& L, const Phys<float>& ph, const Background<float>& bg, const float* wtab,
                             const float* wptab, StepState* ss, int sub, double dx, double dy, double dz) {
   if (!g_pair_ctas) {
-    cudaFuncSetAttribute(pair::rk_pair_kernel<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(pair::rk_pair_kernel<false, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)pair::SMEM_BYTES);
-    cudaFuncSetAttribute(pair::rk_pair_kernel<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(pair::rk_pair_kernel<false, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)pair::SMEM_BYTES);
-    cudaFuncSetAttribute(pair::rk_pair_kernel<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(pair::rk_pair_kernel<false, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)pair::SMEM_BYTES);
+    cudaFuncSetAttribute(pair::rk_pair_kernel<false, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)pair::SMEM_BYTES);
+    cudaFuncSetAttribute(pair::rk_pair_kernel<true, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)pair::SMEM_BYTES);
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
@@ -813,10 +849,14 @@ void launch_rk_pair(const CUtensorMap* tm, const CUtensorMap* tmd, const Layout&
   a.v1 = (const float*)drv.v1;
   const int nitems = a.ntx * a.nty * a.nch;
   const int grid = nitems < g_pair_ctas ? nitems : g_pair_ctas;
-  if (ph.nc_k1 > 0)
-    pair::rk_pair_kernel<false, true><<<grid, pair::NT, pair::SMEM_BYTES, st>>>(*tm, *tmd, a);
-  else
-    pair::rk_pair_kernel<false, false><<<grid, pair::NT, pair::SMEM_BYTES, st>>>(*tm, *tmd, a);
+  const bool bgA = bg.bB != nullptr;
+  if (ph.nc_k1 > 0) {
+    if (bgA) pair::rk_pair_kernel<false, true, true><<<grid, pair::NT, pair::SMEM_BYTES, st>>>(*tm, *tmd, a);
+    else pair::rk_pair_kernel<false, true, false><<<grid, pair::NT, pair::SMEM_BYTES, st>>>(*tm, *tmd, a);
+  } else {
+    if (bgA) pair::rk_pair_kernel<false, false, true><<<grid, pair::NT, pair::SMEM_BYTES, st>>>(*tm, *tmd, a);
+    else pair::rk_pair_kernel<false, false, false><<<grid, pair::NT, pair::SMEM_BYTES, st>>>(*tm, *tmd, a);
+  }
 }
 
 void launch_adj_point_pair(const CUtensorMap* tm, const CUtensorMap* tmd, const Layout& L, const Phys<float>& ph,
@@ -829,7 +869,7 @@ void launch_adj_point_pair(const CUtensorMap* tm, const CUtensorMap* tmd, const 
   a.thbar = thbar;
   const int nitems = a.ntx * a.nty * a.nch;
   const int grid = nitems < g_pair_ctas ? nitems : g_pair_ctas;
-  pair::rk_pair_kernel<true, false><<<grid, pair::NT, pair::SMEM_BYTES, st>>>(*tm, *tmd, a);
+  pair::rk_pair_kernel<true, false, false><<<grid, pair::NT, pair::SMEM_BYTES, st>>>(*tm, *tmd, a);
 }
 
 }  // namespace mhd
