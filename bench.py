@@ -408,35 +408,47 @@ def granulation_line(dev, n=1024, dt=10.0, t_end=600.0):
 
 
 def production_line(dev, ws):
+    """Workload ar_1024x1024x256 in FP32, timed twice: with A stored about the
+    FP64 initial potential field (a_background, the configuration that meets
+    the FP32 tolerance at this size, where |A| reaches several hundred) and
+    with A stored whole.  `value` is the former."""
     import numpy as np
     import torch
 
     import inputs
     from paper_1908_08557_gb300 import Simulation
-    c = inputs.make_case("ar_1024x1024x256", dtype=np.float32)
+    c = inputs.make_case("ar_1024x1024x256")
     p = c.params
-    sim = Simulation(p, c.state, c.lnrho0, c.lnT0, precision=32, stats_every=10, device=str(dev))
-    del c.state
-    sim.set_driver(torch.tensor(c.bz, dtype=torch.float32, device=dev),
-                   torch.tensor(c.v0, dtype=torch.float32, device=dev),
-                   torch.tensor(c.v1, dtype=torch.float32, device=dev), c.t0, c.t1)
-    sim.step(3)
-    torch.cuda.synchronize()
-    k = 10
-    ms = _cuda_ms(sim.stream, lambda: sim.step(k))
-    ms = max_over_ranks(ms, ws)
     cells = p["nx"] * p["ny"] * p["nz"]
-    sim.profile(True)
-    sim.step(3)
-    prof = sim.read_profile()
-    sim.profile(False)
-    sim.close()
-    del sim
-    torch.cuda.empty_cache()
-    rk_ms, rk_n = prof["rk"]
-    achieved = WORDS_PER_CELL_STEP * cells * 4 / 3.0 / (rk_ms / rk_n / 1e3) / 1e9
-    return {"value": ws * cells * k / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / k, "steps": k,
-            "rk_achieved_gbs": achieved, "class_ms_per_step": {kk: v[0] / 3 for kk, v in prof.items()}}
+    out = {}
+    for mode in ("a_background", "plain"):
+        a0 = torch.tensor(c.state[0:3], dtype=torch.float64, device=dev) if mode == "a_background" else None
+        sim = Simulation(p, c.state.astype(np.float32), c.lnrho0, c.lnT0, precision=32, stats_every=10,
+                         device=str(dev), a_background=a0)
+        del a0
+        sim.set_driver(torch.tensor(c.bz, dtype=torch.float32, device=dev),
+                       torch.tensor(c.v0, dtype=torch.float32, device=dev),
+                       torch.tensor(c.v1, dtype=torch.float32, device=dev), c.t0, c.t1)
+        sim.step(3)
+        torch.cuda.synchronize()
+        k = 10
+        ms = _cuda_ms(sim.stream, lambda: sim.step(k))
+        ms = max_over_ranks(ms, ws)
+        sim.profile(True)
+        sim.step(3)
+        prof = sim.read_profile()
+        sim.profile(False)
+        sim.close()
+        del sim
+        torch.cuda.empty_cache()
+        rk_ms, rk_n = prof["rk"]
+        achieved = WORDS_PER_CELL_STEP * cells * 4 / 3.0 / (rk_ms / rk_n / 1e3) / 1e9
+        out[mode] = {"value": ws * cells * k / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / k, "steps": k,
+                     "rk_achieved_gbs": achieved, "class_ms_per_step": {kk: v[0] / 3 for kk, v in prof.items()}}
+    line = dict(out["a_background"])
+    line["storage"] = "A about the FP64 initial field (a_background)"
+    line["plain"] = out["plain"]
+    return line
 
 
 def drift_line(dev, steps, reseed=50):
@@ -460,8 +472,11 @@ def drift_line(dev, steps, reseed=50):
     res, ends = {}, {}
     for prec in (32, 64):
         tdt = torch.float32 if prec == 32 else torch.float64
+        # FP32: A stored about the FP64 initial potential field
+        a0 = torch.tensor(c.state[0:3], dtype=torch.float64, device=dev) if prec == 32 else None
         sim = Simulation(p, torch.tensor(c.state, dtype=tdt, device=dev), c.lnrho0, c.lnT0, precision=prec,
-                         stats_every=0, device=str(dev))
+                         stats_every=0, device=str(dev), a_background=a0)
+        del a0
         bz = torch.tensor(c.bz, dtype=tdt, device=dev)
         sim.set_driver(bz, torch.tensor(c.v0, dtype=tdt, device=dev), torch.tensor(c.v1, dtype=tdt, device=dev),
                        c.t0, c.t1)
@@ -496,6 +511,7 @@ def drift_line(dev, steps, reseed=50):
                                            torch.linalg.vector_norm(ends[64][f])) for f in range(8)}
     res["steps"] = steps
     res["reseed_every"] = reseed
+    res["fp32_storage"] = "A about the FP64 initial field (a_background)"
     del ends
     torch.cuda.empty_cache()
     return res

@@ -455,16 +455,29 @@ def test_production_geometry_1024_sampled(prec):
     """Production geometry: 1024 x 1024 horizontal points, horizontal spacing
     4x vertical (workload ar_1024x1024x256 recipe on 8 layers): the full
     ghost fill (1024^2 FFT planes; FP64) and the RHS at 3000 sampled cells
-    against the oracle (potential-field ghosts by numpy's FFT)."""
+    against the oracle (potential-field ghosts by numpy's FFT).  |A| reaches
+    several hundred here; the FP32 handle stores A about the FP64 initial
+    field (a_background), so its rounding scales with the perturbation and
+    the plain FP32 tolerance applies (1e-4 of each row's sampled scale)."""
     case = inputs.make_box(1024, 1024, 8, seed=3, dx=4.0, dy=4.0, magnetogram="bipoles", n_mag=400,
                            driver="solenoidal", ar_pair=(5.0, 40.0, 200.0))
     rng = np.random.default_rng(1)
     st = case.state.copy()
+    a0 = st[0:3].copy()
+    assert np.abs(a0).max() > 100.0
     st[3:6] += 0.01 * rng.standard_normal(st[3:6].shape)
     if prec == 32:
-        st[0:6] = st[0:6].astype(np.float32).astype(np.float64)
+        st[3:8] = st[3:8].astype(np.float32).astype(np.float64)
     case.state = st
-    sim = _sim(case, prec)
+    if prec == 64:
+        sim = _sim(case, prec)
+    else:
+        from paper_1908_08557_gb300 import Simulation
+        f32 = dict(dtype=torch.float32, device="cuda")
+        sim = Simulation(case.params, torch.tensor(st, **f32), case.lnrho0, case.lnT0, precision=32,
+                         a_background=a0)
+        sim.set_driver(torch.tensor(case.bz, **f32), torch.tensor(case.v0, **f32), torch.tensor(case.v1, **f32),
+                       case.t0, case.t1)
     sim.fill_ghosts()
     p = case.params
     u = oracle.to_padded(st)
@@ -484,32 +497,14 @@ def test_production_geometry_1024_sampled(prec):
     iss = rng.integers(0, nx, 3000)
     cells = np.stack([ks, js, iss], axis=1)
     cast = (lambda a: a.astype(np.float32).astype(np.float64)) if prec == 32 else (lambda a: a)
-    axt, ayt = oracle.a_target_fft(p, case.bz)
-    ref = oracle.rhs_cells(p, u, cast(axt), cast(ayt), cast(case.v0), cast(case.v1), case.t0, case.t1, t, cells)
+    # the FP32 handle forms its nudging target difference in FP64 from its
+    # FP32 copy of B_z
+    axt, ayt = oracle.a_target_fft(p, cast(case.bz))
+    ref = oracle.rhs_cells(p, u, axt, ayt, cast(case.v0), cast(case.v1), case.t0, case.t1, t, cells)
     g = rhs[:, ks + NG, js + NG, iss + NG].T.astype(np.float64)
-    # FP32 bound from the arithmetic: |A| reaches several hundred here (the
-    # sigma = 40-cell pair's flux over dx = 4), and an FP32 second difference
-    # of A in z carries up to dJ = u * max|A| * sum|w2| / dz^2 of rounding
-    # (u = 2^-24, sum|w2| = 6.04).  J enters dA/dt through eta J and the
-    # swamp term eta_s w lap A (w <= 1), and du/dt through J x B / rho: per
-    # sampled cell the A rows may be off by (eta + eta_s) dJ and the u rows
-    # by dJ |B| / rho (|B| from second-order differences of A), each with a
-    # factor 3; every row also takes 1e-3 of its scale.
-    tol = 1e-10 if prec == 64 else 1e-3
-    floor = np.full((len(ks), 8), 0.0)
-    if prec == 32:
-        dJ = 2.0 ** -24 * np.abs(st[0:3]).max() * 6.04 / p["dz"] ** 2
-        gx = lambda a, ax, h: np.gradient(a, h, axis=ax)
-        bx = gx(st[2], 1, p["dy"]) - gx(st[1], 0, p["dz"])
-        by = gx(st[0], 0, p["dz"]) - gx(st[2], 2, p["dx"])
-        bz = gx(st[1], 2, p["dx"]) - gx(st[0], 1, p["dy"])
-        bmag = np.sqrt(bx ** 2 + by ** 2 + bz ** 2)[ks, js, iss]
-        rho = np.exp(st[6][ks, js, iss])
-        floor[:, 0:3] = 3.0 * (p["eta"] + p["eta_swamp"]) * dJ
-        floor[:, 3:6] = 3.0 * dJ * (bmag / rho)[:, None]
+    tol = 1e-10 if prec == 64 else 1e-4
     for f in range(8):
         s = np.abs(ref[:, f]).max()
         err = np.abs(g[:, f] - ref[:, f])
-        bound = np.maximum(tol * max(s, 1e-30), floor[:, f])
-        worst = int(np.argmax(err - bound))
-        assert np.all(err <= bound), (f, err[worst], bound[worst], s)
+        worst = int(np.argmax(err))
+        assert err[worst] <= tol * max(s, 1e-30), (f, err[worst], s)
