@@ -194,13 +194,28 @@ int mhd_step(mhd_handle h, int nsteps);
  * stream. */
 int mhd_set_a_background(mhd_handle h, const double* a_bg, const void* a_pert, int mem);
 
+/* Test hook of the bounded device waits (not part of the method): the next
+ * launch of the FP32 fused kernel (the default FP32 path) skips, in the
+ * first work item of its first CTA, the copy of state plane `plane`
+ * (-3 .. nz + 2, of that item's z chunk) together with its barrier arrival,
+ * so the wait for that plane finds no copy in flight and gives up after
+ * `wait_limit` polls; every wait of that launch uses this limit.  The CTA
+ * then drains its copies in flight, frees its tensor memory, records the
+ * time-out in the device flag and returns; the step is left incomplete, the
+ * following kernels of the handle return without work, and the next
+ * synchronising call returns MHD_ERR_TIMEOUT.  mhd_write clears the flag.
+ * MHD_ERR_UNSUPPORTED for an FP64 handle or another FP32 kernel variant. */
+int mhd_debug_skip_copy(mhd_handle h, int plane, int wait_limit);
+
 /* Copy the interior of one field (0..7) or of all fields (-1) into dst
  * ([nz][ny][nx] or [8][nz][ny][nx]).  With MHD_MEM_HOST the call
  * synchronises the stream. */
 int mhd_read(mhd_handle h, int field, void* dst, int mem);
 
 /* Copy the whole state into the handle (same layout as init_state); the
- * stateful velocity ghosts are reset to the photospheric layer. */
+ * stateful velocity ghosts are reset to the photospheric layer.  Also clears
+ * the device flag of a non-finite value or a timed-out wait, so a handle
+ * halted by either can be stepped again from the state written. */
 int mhd_write(mhd_handle h, const void* src, int mem);
 
 /* Synchronise the stream and return the diagnostics of the last step that

@@ -182,8 +182,11 @@ class Revolver:
 
 
 class DrivenRun(torch.autograd.Function):
-    """(bz, v0, v1) -> state after `nsteps` steps from `state0` at t = 0.
-    The handle must have been created with adjoint=True and dt_fixed > 0."""
+    """(bz, v0, v1, state0) -> state after `nsteps` steps from `state0` at
+    t = 0; gradients for the driver (B_z, v0, v1) and, when state0 requires
+    one, for the initial state (the adjoint of the initial state, the
+    stateful ghost layers folded onto the photosphere).  The handle must have
+    been created with adjoint=True and dt_fixed > 0."""
 
     @staticmethod
     def forward(ctx, bz, v0, v1, sim, state0, nsteps: int, slots: int, t0: float = 0.0, t1: float = 1.0):
@@ -201,7 +204,8 @@ class DrivenRun(torch.autograd.Function):
         sim.adjoint_init(gstate.contiguous())
         rv.reverse()
         g = sim.adjoint_read()
-        return g["bz"], g["v0"], g["v1"], None, None, None, None, None, None
+        gs = g["lam"] if ctx.needs_input_grad[4] else None
+        return g["bz"], g["v0"], g["v1"], None, gs, None, None, None, None
 
 
 class BzPlane(torch.autograd.Function):

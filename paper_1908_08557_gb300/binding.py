@@ -40,7 +40,8 @@ EXPORTED = ("mhd_workspace_bytes", "mhd_create", "mhd_set_driver", "mhd_step",
             "mhd_adjoint_init", "mhd_adjoint_step", "mhd_adjoint_read", "mhd_bz_plane",
             "mhd_bz_plane_adjoint", "mhd_gran_workspace_bytes", "mhd_gran_create", "mhd_gran_update",
             "mhd_gran_velocity", "mhd_gran_read_granules", "mhd_gran_read_field", "mhd_gran_launch_count",
-            "mhd_gran_last_error", "mhd_gran_destroy", "mhd_set_a_background")
+            "mhd_gran_last_error", "mhd_gran_destroy", "mhd_set_a_background",
+            "mhd_debug_skip_copy")
 KERNEL_CLASSES = ("ghost", "pfe", "cfl", "stats", "rk")
 
 
@@ -109,6 +110,7 @@ def load(path: Optional[str] = None):
     lib.mhd_create.argtypes = [P, vp, sz, vp, i, dpp, dpp, vp, ctypes.POINTER(vp)]
     lib.mhd_set_driver.argtypes = [vp, vp, vp, vp, d, d, i]
     lib.mhd_set_a_background.argtypes = [vp, vp, vp, i]
+    lib.mhd_debug_skip_copy.argtypes = [vp, i, i]
     lib.mhd_step.argtypes = [vp, i]
     lib.mhd_read.argtypes = [vp, i, vp, i]
     lib.mhd_write.argtypes = [vp, vp, i]
@@ -427,6 +429,10 @@ class Simulation:
         n = (ctypes.c_longlong * len(KERNEL_CLASSES))()
         self._check(self.lib.mhd_read_profile(self.h, ms, n))
         return {c: (ms[q], n[q]) for q, c in enumerate(KERNEL_CLASSES)}
+
+    def debug_skip_copy(self, plane: int, wait_limit: int):
+        """Test hook of the bounded waits (mhd_debug_skip_copy)."""
+        self._check(self.lib.mhd_debug_skip_copy(self.h, int(plane), int(wait_limit)))
 
     def launch_count(self) -> int:
         return int(self.lib.mhd_launch_count(self.h))

@@ -80,6 +80,8 @@ struct mhd_ctx {
   long long host_steps;
   long long nlaunch;                  // kernels launched since create
   bool prof;                          // bracket kernel classes with events
+  int dbg_skip_plane;                 // time-out test hook for the next forward FP32 launch (INT_MIN: off)
+  int dbg_wait_limit;
   struct Ev { cudaEvent_t a, b; int cls; int nk; };
   std::vector<Ev>* evs;
   char err[512];
@@ -478,7 +480,9 @@ static void launch_rk_any(mhd_ctx* h, const R* fin, R* fout, int sub) {
   if (sizeof(R) == 4 && h->pair) {
     const int which = (const void*)fin == h->f[0] ? 0 : 1;
     launch_rk_pair(&h->tm[which], &h->tmdf, h->L, *(const Phys<float>*)&ph, h->bgf, (float*)fout, (float*)h->df,
-                   (const float*)h->wtab, (const float*)h->wptab, drv, h->ss, sub, h->p.dx, h->p.dy, h->p.dz, h->st);
+                   (const float*)h->wtab, (const float*)h->wptab, drv, h->ss, sub, h->p.dx, h->p.dy, h->p.dz, h->st,
+                   h->dbg_skip_plane, h->dbg_wait_limit);
+    h->dbg_skip_plane = INT_MIN;  // one launch only
     return;
   }
   if (sizeof(R) == 4 && h->split) {
@@ -709,6 +713,7 @@ extern "C" int mhd_create(const mhd_params* p, void* workspace, size_t ws_bytes,
   }
   h->t0 = 0.0;
   h->t1 = 0.0;
+  h->dbg_skip_plane = INT_MIN;
   snprintf(h->err, sizeof h->err, "no error");
 
   int rc = MHD_OK;
@@ -814,6 +819,9 @@ extern "C" int mhd_write(mhd_handle h, const void* src, int mem) {
   size_t bytes = (size_t)NF * L.nx * L.ny * L.nz * h->esz;
   int rc = cuda_check(h, cudaMemcpyAsync(h->df, src, bytes, kind_in(mem), h->st), "copy state in");
   if (rc) return rc;
+  // a state written afresh may be stepped again: clear the halt flag
+  rc = cuda_check(h, cudaMemsetAsync(&h->ss->nonfinite, 0, sizeof(int), h->st), "clear status");
+  if (rc) return rc;
   for (int s = 0; s < 2; ++s) {
     if (h->esz == 8) {
       double* f = (double*)h->f[s];
@@ -905,6 +913,16 @@ extern "C" int mhd_set_a_background(mhd_handle h, const double* a_bg, const void
   if (!rc && h->have_fft && h->driver_set) rc = background_target(h);
   if (!rc) rc = cuda_check(h, cudaStreamSynchronize(h->st), "background synchronize");
   return rc;
+}
+
+extern "C" int mhd_debug_skip_copy(mhd_handle h, int plane, int wait_limit) {
+  if (!h) return fail(nullptr, MHD_ERR_ARG, "NULL handle");
+  if (!(h->esz == 4 && h->pair)) return fail(h, MHD_ERR_UNSUPPORTED, "the hook acts on the FP32 pair kernel only");
+  if (plane < -NG || plane > h->p.nz + NG - 1) return fail(h, MHD_ERR_ARG, "plane must be in -3 .. nz + 2");
+  if (wait_limit < 1) return fail(h, MHD_ERR_ARG, "wait_limit must be >= 1");
+  h->dbg_skip_plane = plane;
+  h->dbg_wait_limit = wait_limit;
+  return MHD_OK;
 }
 
 extern "C" int mhd_set_driver(mhd_handle h, const void* bz, const void* v0, const void* v1, double t0,

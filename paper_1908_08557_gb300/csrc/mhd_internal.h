@@ -1,5 +1,7 @@
 // mhd_internal.h -- launchers shared between the translation units of libmhd.
 #pragma once
+#include <climits>
+
 #include <cuda.h>
 #include <cuda_runtime.h>
 #include "mhd_common.cuh"
@@ -89,9 +91,12 @@ void launch_rk_split(const CUtensorMap* tm_a, const CUtensorMap* tm_r, const Lay
 // 8-field halo boxes, tmd the RK accumulator with 8-field 32 x 8 tiles.
 // Requires nx even, nx >= 8, ny >= 6.
 bool rk_pair_supported(const Layout& L);
+// skip_plane, wait_limit: the time-out test hook (mhd_debug_skip_copy); INT_MIN
+// for a normal launch
 void launch_rk_pair(const CUtensorMap* tm, const CUtensorMap* tmd, const Layout& L, const Phys<float>& ph, const Background<float>& bg,
                     float* fout, float* df, const float* wtab, const float* wptab, const Driver& drv, StepState* ss,
-                    int sub, double dx, double dy, double dz, cudaStream_t st);
+                    int sub, double dx, double dy, double dz, cudaStream_t st, int skip_plane = INT_MIN,
+                    int wait_limit = 0);
 // pointwise adjoint of substep sub on the same z-march (tm: the ghost-filled
 // substep state, tmd: D, the adjoint of the RK accumulator, 32 x 8 tiles)
 void launch_adj_point_pair(const CUtensorMap* tm, const CUtensorMap* tmd, const Layout& L, const Phys<float>& ph,

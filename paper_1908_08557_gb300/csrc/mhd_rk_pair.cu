@@ -73,6 +73,12 @@ struct Args {
   const float* dbar;
   float* coef;
   double* thbar;
+  // bounded waits: polls before a ring or accumulator wait gives up; and a
+  // test hook for the time-out path: CTA 0 does not issue the copy of plane
+  // skip_plane in its first work item (INT_MIN: every copy is issued), so
+  // its wait for that plane runs out with no copy in flight
+  int wait_limit;
+  int skip_plane;
 };
 
 // ---- TMEM access (32x32b shape: each thread its own lane) -----------------
@@ -364,13 +370,15 @@ __global__ void __launch_bounds__(NT, 2) rk_pair_kernel(const __grid_constant__ 
   };
   // ring slots are tracked incrementally (slot of plane p = (p - pbase) mod NR)
   auto wrap = [](int s) { return s >= NR ? s - NR : s; };
+  bool inject = false;  // the time-out test hook applies to this item
   auto load = [&](int p, int s, int x0, int y0) {
+    if (inject && p == a.skip_plane) return;
     zm::tma_plane(&tm, raw + s * PLANE, &mbar[s], PLANE * 4, x0 - 4 + XOFF, y0, p + NG, 0);
     pending |= 1u << s;
   };
   // collective bounded wait for plane p; false on time-out (uniform)
   auto wait = [&](int s) -> bool {
-    const bool to = !zm::mbar_wait(&mbar[s], (phase >> s) & 1u);
+    const bool to = !zm::mbar_wait(&mbar[s], (phase >> s) & 1u, a.wait_limit);
     if (__syncthreads_or(to)) return false;
     phase ^= 1u << s;
     pending &= ~(1u << s);
@@ -405,6 +413,7 @@ __global__ void __launch_bounds__(NT, 2) rk_pair_kernel(const __grid_constant__ 
     const int x0 = (tile % a.ntx) * TX, y0 = (tile / a.ntx) * TY;
     const int k0 = ch * a.kchunk, k1 = min(L.nz, k0 + a.kchunk);
     const int pbase = k0 - NG, plast = k1 + NG - 1;
+    inject = a.skip_plane != INT_MIN && item == 0;
     if (tid == 0) {
       for (int p = pbase; p <= min(pbase + NR - 1, plast); ++p) load(p, p - pbase, x0, y0);
       if (ADJ || sub > 0) load_df(k0, k0, x0, y0);
@@ -618,7 +627,7 @@ __global__ void __launch_bounds__(NT, 2) rk_pair_kernel(const __grid_constant__ 
       f2 dfo[NF];
       if (sub > 0) {
         const int sl = (k - k0) & 1;
-        if (!zm::mbar_wait(&mbd[sl], (dphase >> sl) & 1u)) atomicOr(&a.ss->nonfinite, 2);
+        if (!zm::mbar_wait(&mbd[sl], (dphase >> sl) & 1u, a.wait_limit)) atomicOr(&a.ss->nonfinite, 2);
         dphase ^= 1u << sl;
         if (tid == 0) dpending &= ~(1u << sl);
         const float* dq = dfs + sl * DFT + ty * TX + 2 * tx;
@@ -768,9 +777,9 @@ __global__ void __launch_bounds__(NT, 2) rk_pair_kernel(const __grid_constant__ 
     // a ring wait timed out: record it and drain the copies in flight (bounded)
     atomicOr(&a.ss->nonfinite, 2);
     for (int s = 0; s < NR; ++s)
-      if (pending & (1u << s)) zm::mbar_wait(&mbar[s], (phase >> s) & 1u);
+      if (pending & (1u << s)) zm::mbar_wait(&mbar[s], (phase >> s) & 1u, a.wait_limit);
     for (int s = 0; s < 2; ++s)
-      if (dpending & (1u << s)) zm::mbar_wait(&mbd[s], (dphase >> s) & 1u);
+      if (dpending & (1u << s)) zm::mbar_wait(&mbd[s], (dphase >> s) & 1u, a.wait_limit);
   }
   tm_wait_st();
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -806,6 +815,8 @@ static pair::Args pair_args(const Layout& L, const Phys<float>& ph, const Backgr
     g_pair_ctas = 2 * sms;
   }
   pair::Args a{};
+  a.wait_limit = zm::WAIT_LIMIT;
+  a.skip_plane = INT_MIN;
   a.L = L;
   a.ph = ph;
   a.bg = bg;
@@ -839,8 +850,13 @@ static pair::Args pair_args(const Layout& L, const Phys<float>& ph, const Backgr
 
 void launch_rk_pair(const CUtensorMap* tm, const CUtensorMap* tmd, const Layout& L, const Phys<float>& ph,
                     const Background<float>& bg, float* fout, float* df, const float* wtab, const float* wptab,
-                    const Driver& drv, StepState* ss, int sub, double dx, double dy, double dz, cudaStream_t st) {
+                    const Driver& drv, StepState* ss, int sub, double dx, double dy, double dz, cudaStream_t st,
+                    int skip_plane, int wait_limit) {
   pair::Args a = pair_args(L, ph, bg, wtab, wptab, ss, sub, dx, dy, dz);
+  if (skip_plane != INT_MIN) {
+    a.skip_plane = skip_plane;
+    a.wait_limit = wait_limit;
+  }
   a.fout = fout;
   a.df = df;
   a.axt = (const float*)drv.axt;

@@ -35,9 +35,10 @@ __device__ __forceinline__ void tma_plane(const CUtensorMap* tm, float* dst, uin
       : "memory");
 }
 
-// bounded wait for the given phase parity; false on time-out
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-  for (int it = 0; it < WAIT_LIMIT; ++it) {
+// bounded wait for the given phase parity; false on time-out (after `limit`
+// polls, each of which may suspend the thread for a short hardware interval)
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int limit = WAIT_LIMIT) {
+  for (int it = 0; it < limit; ++it) {
     uint32_t ok;
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
