@@ -29,6 +29,11 @@ sys.path.insert(0, ROOT)
 METRIC = "MHD cell-updates/s per RK step"
 UNIT = "cell-updates/s"
 WORDS_PER_CELL_STEP = 80  # algorithmic state words moved per cell per RK3 step
+RUNS = 5                  # timed runs of K steps; the median is reported
+# FP64 operations per cell and substep of rk_simple_kernel<double> (2 per
+# DFMA, 1 per DADD / DMUL), from the ncu instruction counts summarised in
+# profiles/rk_simple_fp64_flops_bipoles20_128x128x128.md
+FP64_FLOPS_PER_CELL_SUBSTEP = 1059.4
 RK_KERNEL = ("rk_pair_kernel (fused RHS + RK update, TMA z-march, two cells per thread in f32x2, "
              "z histories in TMEM)")
 
@@ -185,6 +190,34 @@ def cpu_oracle_sample(nx=256, ny=256, nz=32, steps=1):
     oracle.run(case.params, u, case.lnrho0, axt, ayt, case.v0, case.v1, case.t0, case.t1, 0.0, steps)
     dt = time.perf_counter() - t0
     return nx * ny * nz * steps / dt, dt
+
+
+def cpu_oracle_runs():
+    """The oracle on the smaller named workloads, once on one thread and once
+    on every core (OMP_NUM_THREADS), each in a fresh interpreter: spots4 at
+    32^3 for 50 steps, the 64^3 gradient workload for 5 steps.  The 256^3
+    workload's 20 steps would take minutes on all cores and most of an hour
+    on one, so its rate is the slab sample above."""
+    import subprocess
+    import sys
+    code = ("import json, sys, time; sys.path.insert(0, %r); import inputs, oracle; "
+            "c = inputs.make_case(sys.argv[1]); n = int(sys.argv[2]); t = time.perf_counter(); "
+            "oracle.run_case(c, nsteps=n); el = time.perf_counter() - t; "
+            "q = c.params; print(json.dumps({'seconds': el, 'value': q['nx'] * q['ny'] * q['nz'] * n / el}))"
+            % ROOT)
+    out = []
+    for name, steps in (("spots4_32x32x32", 50), ("bipoles8_64x64x64", 5)):
+        for threads in (1, os.cpu_count()):
+            env = dict(os.environ, OMP_NUM_THREADS=str(threads))
+            r = subprocess.run([sys.executable, "-c", code, name, str(steps)], capture_output=True, text=True,
+                               env=env, timeout=600)
+            if r.returncode != 0:
+                out.append({"workload": name, "steps": steps, "threads": threads, "error": r.stderr[-300:]})
+                continue
+            d = json.loads(r.stdout.strip().splitlines()[-1])
+            out.append({"workload": name, "steps": steps, "threads": threads, "value": d["value"], "unit": UNIT,
+                        "seconds": d["seconds"]})
+    return out
 
 
 def _cuda_ms(stream, fn):
@@ -576,20 +609,26 @@ def run_native(args, ws, rank, local):
     torch.cuda.synchronize()
     barrier(ws)
     torch.cuda.synchronize()
+    # five timed runs of exactly K steps each, every one bracketed by a
+    # barrier and a device synchronisation; the median run is the value
     clk = ClockSampler(local)
     clk.start()
-    n0 = sim.launch_count()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    sim.step(args.steps)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1)
-    launches = sim.launch_count() - n0
+    runs = []
+    for r in range(RUNS):
+        barrier(ws)
+        torch.cuda.synchronize()
+        n0 = sim.launch_count()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sim.step(args.steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        launches = sim.launch_count() - n0
+        barrier(ws)
+        runs.append(max_over_ranks(e0.elapsed_time(e1), ws))
     clocks = clk.stop()
-    barrier(ws)
-    ms_max = max_over_ranks(ms, ws)
+    ms_max = sorted(runs)[RUNS // 2]
     value = ws * cells * args.steps / (ms_max / 1e3)
 
     # per-kernel-class timing on the library's stream (separate pass)
@@ -611,27 +650,35 @@ def run_native(args, ws, rank, local):
                 "class_ms_per_step": {k: v[0] / nprof for k, v in prof.items()}}
 
     # end to end through the C ABI with host buffers: each step uploads its
-    # driver snapshot (B_z, v0, v1) from pinned host memory and reads back
-    # the time and time step
+    # driver snapshot (B_z, v0, v1) from pinned host memory, steps, and
+    # reads back one layer of the new state (u_z at mid-height) into pinned
+    # host memory with the time and time step
     e2e = None
     if not args.no_e2e:
         pin = lambda a: torch.tensor(a, dtype=torch.float32).pin_memory().numpy()
         hb, hv0, hv1 = pin(case.bz), pin(case.v0), pin(case.v1)
-        for _ in range(2):
+        plane = torch.empty((p["ny"], p["nx"]), dtype=torch.float32).pin_memory().numpy()
+        kmid = p["nz"] // 2
+
+        def e2e_step():
             sim.set_driver(hb, hv0, hv1, case.t0, case.t1)
             sim.step(1)
+            sim.read_plane(5, kmid, plane)
             sim.time()
+
+        for _ in range(2):
+            e2e_step()
         barrier(ws)
         t0 = time.perf_counter()
         ne2e = min(args.steps, 50)
         for _ in range(ne2e):
-            sim.set_driver(hb, hv0, hv1, case.t0, case.t1)
-            sim.step(1)
-            sim.time()
+            e2e_step()
         el = time.perf_counter() - t0
         el = max_over_ranks(el, ws)
         e2e = {"value": ws * cells * ne2e / el, "unit": UNIT, "steps": ne2e,
-               "h2d_bytes_per_step": int(hb.nbytes + hv0.nbytes + hv1.nbytes), "d2h_bytes_per_step": 20}
+               "h2d_bytes_per_step": int(hb.nbytes + hv0.nbytes + hv1.nbytes),
+               "d2h_bytes_per_step": int(plane.nbytes) + 16,
+               "read_back": "u_z on layer nz/2, t and dt"}
     sim.close()
     del sim
     torch.cuda.empty_cache()
@@ -648,9 +695,29 @@ def run_native(args, ws, rank, local):
         f1.record(s64.stream)
         torch.cuda.synchronize()
         ms64 = max_over_ranks(f0.elapsed_time(f1), ws)
+        s64.profile(True)
+        s64.step(1)
+        prof64 = s64.read_profile()
+        s64.profile(False)
         fp64 = {"value": ws * cells * args.fp64_steps / (ms64 / 1e3), "unit": UNIT,
                 "ms_per_step": ms64 / args.fp64_steps, "steps": args.fp64_steps,
                 "dtype": "f64"}
+        # the FP64 right-hand side is bound by the FP64 FMA pipe: its
+        # roofline is the kernel's FP64 flops (per cell and substep, from an
+        # ncu count of its DFMA / DADD / DMUL instructions) over its launch
+        # time, against the FP64 FMA rate the library's probe measures here
+        try:
+            from paper_1908_08557_gb300.binding import fma_peak
+            peak64 = fma_peak(64, str(dev)) / 1e12
+            rk64_ms, rk64_n = prof64["rk"]
+            ach64 = FP64_FLOPS_PER_CELL_SUBSTEP * cells / (rk64_ms / rk64_n / 1e3) / 1e12
+            fp64["roofline"] = {"bound": "alu", "achieved": ach64, "peak": peak64, "unit": "TFLOP/s",
+                                "frac": ach64 / peak64, "kernel": "rk_simple_kernel<double>",
+                                "flops_per_cell_substep": FP64_FLOPS_PER_CELL_SUBSTEP,
+                                "avg_launch_ms": rk64_ms / rk64_n,
+                                "peak_source": "measured in this run (mhd_fma_peak, FP64 FMA chains)"}
+        except Exception as exc:  # reported, not fatal
+            fp64["roofline"] = {"error": f"{type(exc).__name__}: {exc}"}
         s64.close()
         del s64
         torch.cuda.empty_cache()
@@ -695,12 +762,15 @@ def run_native(args, ws, rank, local):
         oracle.build()
         v, secs = cpu_oracle_sample()
         cpu = {"value": v, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-               "sample": f"one RK3 step of a 256x256x32 slab of the same recipe ({secs:.1f} s, FP64 oracle, OpenMP)"}
+               "sample": f"one RK3 step of a 256x256x32 slab of the same recipe ({secs:.1f} s, FP64 oracle, OpenMP)",
+               "runs": cpu_oracle_runs()}
 
     if rank == 0:
         state_gb = 3 * 8 * (p["nx"] + 16) * (p["ny"] + 6) * (p["nz"] + 6) * 4 / 1e9
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
-                "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+                "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+                "runs_ms_per_step": [r / args.steps for r in runs], "timing": f"median of {RUNS} runs of K steps",
+                "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": {"workload": args.workload, "nx": p["nx"], "ny": p["ny"], "nz": p["nz"],
                            "precision": "fp32 state and stencils; fp64 FFT, CFL and diagnostics",

@@ -194,6 +194,21 @@ int mhd_step(mhd_handle h, int nsteps);
  * stream. */
 int mhd_set_a_background(mhd_handle h, const double* a_bg, const void* a_pert, int mem);
 
+/* Copy layer k (0 .. nz-1) of one field (0..7) into dst ([ny][nx]); the
+ * same values mhd_read returns for that layer.  With MHD_MEM_HOST the call
+ * synchronises the stream. */
+int mhd_read_plane(mhd_handle h, int field, int k, void* dst, int mem);
+
+/* Arithmetic throughput of the current device in the given precision (32 or
+ * 64): eight independent fused multiply-add chains per thread, 8 blocks of
+ * 256 threads per SM, timed with CUDA events on `stream` (the best of three
+ * launches after one warm-up), written to *flops_per_s (2 flops per FMA).
+ * scratch: any device pointer to at least 8 x SM-count elements (written
+ * only in a case that does not occur).  Instrumentation for the rooflines
+ * of the ALU-bound kernels; synchronises the stream; errors through
+ * mhd_last_error(NULL). */
+int mhd_fma_peak(int precision, void* scratch, void* stream, double* flops_per_s);
+
 /* Test hook of the bounded device waits (not part of the method): the next
  * launch of the FP32 fused kernel (the default FP32 path) skips, in the
  * first work item of its first CTA, the copy of state plane `plane`

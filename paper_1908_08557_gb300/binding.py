@@ -41,7 +41,7 @@ EXPORTED = ("mhd_workspace_bytes", "mhd_create", "mhd_set_driver", "mhd_step",
             "mhd_bz_plane_adjoint", "mhd_gran_workspace_bytes", "mhd_gran_create", "mhd_gran_update",
             "mhd_gran_velocity", "mhd_gran_read_granules", "mhd_gran_read_field", "mhd_gran_launch_count",
             "mhd_gran_last_error", "mhd_gran_destroy", "mhd_set_a_background",
-            "mhd_debug_skip_copy")
+            "mhd_debug_skip_copy", "mhd_read_plane", "mhd_fma_peak")
 KERNEL_CLASSES = ("ghost", "pfe", "cfl", "stats", "rk")
 
 
@@ -111,6 +111,8 @@ def load(path: Optional[str] = None):
     lib.mhd_set_driver.argtypes = [vp, vp, vp, vp, d, d, i]
     lib.mhd_set_a_background.argtypes = [vp, vp, vp, i]
     lib.mhd_debug_skip_copy.argtypes = [vp, i, i]
+    lib.mhd_read_plane.argtypes = [vp, i, i, vp, i]
+    lib.mhd_fma_peak.argtypes = [i, vp, vp, ctypes.POINTER(ctypes.c_double)]
     lib.mhd_step.argtypes = [vp, i]
     lib.mhd_read.argtypes = [vp, i, vp, i]
     lib.mhd_write.argtypes = [vp, vp, i]
@@ -189,6 +191,20 @@ def make_params(p: Dict, precision: int = 32, stats_every: int = 0, adjoint: boo
     q.nc_z_width = float(p.get("nc_z_width", 1.0 * float(p["dz"])))
     q.a_background = 1 if a_background else 0
     return q
+
+
+def fma_peak(precision: int, device: str = "cuda:0") -> float:
+    """FMA throughput of the device in FP32 or FP64 (flop/s), measured by
+    the library's probe kernel (mhd_fma_peak)."""
+    import torch
+    lib = load()
+    scratch = torch.empty(1 << 16, dtype=torch.float64, device=device)
+    out = ctypes.c_double()
+    rc = lib.mhd_fma_peak(int(precision), ctypes.c_void_p(scratch.data_ptr()),
+                          ctypes.c_void_p(torch.cuda.current_stream(device).cuda_stream), ctypes.byref(out))
+    if rc != MHD_OK:
+        raise MHDError(rc, lib.mhd_last_error(None).decode())
+    return out.value
 
 
 def workspace_bytes(p: Dict, precision: int = 32, a_background: bool = False) -> int:
@@ -321,6 +337,20 @@ class Simulation:
             self._check(self.lib.mhd_read(self.h, int(field), ctypes.c_void_p(out.ctypes.data), MHD_MEM_HOST))
         else:
             self._check(self.lib.mhd_read(self.h, int(field), ctypes.c_void_p(out.data_ptr()), MHD_MEM_DEVICE))
+        return out
+
+    def read_plane(self, field: int, k: int, out=None):
+        """Layer k of one field, [ny][nx]; out: a numpy array (host) or a
+        CUDA tensor (device), allocated on the device when None."""
+        import torch
+        if out is None:
+            out = torch.empty((self._p.ny, self._p.nx), dtype=self.torch_dtype, device=self.device)
+        if isinstance(out, np.ndarray):
+            self._check(self.lib.mhd_read_plane(self.h, int(field), int(k), ctypes.c_void_p(out.ctypes.data),
+                                                MHD_MEM_HOST))
+        else:
+            self._check(self.lib.mhd_read_plane(self.h, int(field), int(k), ctypes.c_void_p(out.data_ptr()),
+                                                MHD_MEM_DEVICE))
         return out
 
     def write(self, state):

@@ -915,6 +915,42 @@ extern "C" int mhd_set_a_background(mhd_handle h, const double* a_bg, const void
   return rc;
 }
 
+extern "C" int mhd_fma_peak(int precision, void* scratch, void* stream, double* flops_per_s) {
+  if ((precision != 32 && precision != 64) || !scratch || !flops_per_s) {
+    set_global_error("mhd_fma_peak: precision 32 or 64, a device scratch pointer and an output are required");
+    return MHD_ERR_ARG;
+  }
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaStream_t st = (cudaStream_t)stream;
+  const int grid = 8 * (sms > 0 ? sms : 1);        // 8 blocks of 256 threads per SM
+  const int iters = precision == 64 ? 1 << 12 : 1 << 16;
+  cudaEvent_t a, b;
+  cudaEventCreate(&a);
+  cudaEventCreate(&b);
+  float best = 0.f;
+  for (int rep = 0; rep < 4; ++rep) {  // the first launch warms up
+    cudaEventRecord(a, st);
+    if (precision == 64) launch_fma_probe<double>((double*)scratch, grid, iters, st);
+    else launch_fma_probe<float>((float*)scratch, grid, iters, st);
+    cudaEventRecord(b, st);
+    cudaEventSynchronize(b);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, a, b);
+    if (rep > 0 && (best == 0.f || ms < best)) best = ms;
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || !(best > 0.f)) {
+    set_global_error("mhd_fma_peak: %s", cudaGetErrorString(e));
+    return MHD_ERR_CUDA;
+  }
+  *flops_per_s = 2.0 * 8.0 * (double)iters * 256.0 * (double)grid / (best * 1e-3);
+  return MHD_OK;
+}
+
 extern "C" int mhd_debug_skip_copy(mhd_handle h, int plane, int wait_limit) {
   if (!h) return fail(nullptr, MHD_ERR_ARG, "NULL handle");
   if (!(h->esz == 4 && h->pair)) return fail(h, MHD_ERR_UNSUPPORTED, "the hook acts on the FP32 pair kernel only");
@@ -979,6 +1015,26 @@ extern "C" int mhd_read(mhd_handle h, int field, void* dst, int mem) {
   if (rc) return rc;
   if (mem == MHD_MEM_HOST) {
     rc = cuda_check(h, cudaMemcpyAsync(dst, h->df, bytes, cudaMemcpyDeviceToHost, h->st), "copy out");
+    if (!rc) rc = cuda_check(h, cudaStreamSynchronize(h->st), "read synchronize");
+  }
+  return rc;
+}
+
+extern "C" int mhd_read_plane(mhd_handle h, int field, int k, void* dst, int mem) {
+  if (!h) return fail(nullptr, MHD_ERR_ARG, "NULL handle");
+  if (!dst) return fail(h, MHD_ERR_ARG, "dst is NULL");
+  if (field < 0 || field >= NF) return fail(h, MHD_ERR_ARG, "field must be 0..7");
+  if (k < 0 || k >= h->L.nz) return fail(h, MHD_ERR_ARG, "k must be 0..nz-1");
+  if (mem != MHD_MEM_DEVICE && mem != MHD_MEM_HOST) return fail(h, MHD_ERR_ARG, "bad mem flag");
+  const Layout& L = h->L;
+  void* tgt = mem == MHD_MEM_HOST ? h->df : dst;
+  if (h->esz == 8) launch_pack_plane<double>(L, h->bgd, (const double*)h->f[h->cur], (double*)tgt, field, k, h->st);
+  else launch_pack_plane<float>(L, h->bgf, (const float*)h->f[h->cur], (float*)tgt, field, k, h->st);
+  int rc = cuda_check(h, cudaSuccess, "pack plane");
+  if (rc) return rc;
+  if (mem == MHD_MEM_HOST) {
+    rc = cuda_check(h, cudaMemcpyAsync(dst, h->df, (size_t)L.nx * L.ny * h->esz, cudaMemcpyDeviceToHost, h->st),
+                    "copy plane out");
     if (!rc) rc = cuda_check(h, cudaStreamSynchronize(h->st), "read synchronize");
   }
   return rc;

@@ -171,6 +171,17 @@ __global__ void pack_padded_kernel(Layout L, Background<R> bg, const R* __restri
   }
 }
 
+// one z layer k of one field, interior [ny][nx], background added
+template <typename R>
+__global__ void pack_plane_kernel(Layout L, Background<R> bg, const R* __restrict__ f, R* __restrict__ out, int field,
+                                  int k) {
+  const long long n2 = (long long)L.nx * L.ny;
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n2; q += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(q % L.nx), j = (int)(q / L.nx);
+    out[q] = f[L.at(field, k, j, i)] + bg_at(L, bg, field, k, j, i);
+  }
+}
+
 // per-layer mean of one field of an interior-packed state, FP64, fixed order
 template <typename R>
 __global__ void layer_mean_kernel(Layout L, const R* __restrict__ in, int field, double* out) {
@@ -202,6 +213,11 @@ void launch_pack_padded(const Layout& L, const Background<R>& bg, const R* f, R*
   pack_padded_kernel<R><<<1216, 256, 0, st>>>(L, bg, f, out);
 }
 template <typename R>
+void launch_pack_plane(const Layout& L, const Background<R>& bg, const R* f, R* out, int field, int k, cudaStream_t st) {
+  const long long n2 = (long long)L.nx * L.ny;
+  pack_plane_kernel<R><<<(int)((n2 + 255) / 256 < 1216 ? (n2 + 255) / 256 : 1216), 256, 0, st>>>(L, bg, f, out, field, k);
+}
+template <typename R>
 void launch_layer_mean(const Layout& L, const R* in, int field, double* out, cudaStream_t st) {
   layer_mean_kernel<R><<<L.nz, 256, 0, st>>>(L, in, field, out);
 }
@@ -214,7 +230,8 @@ void launch_layer_mean(const Layout& L, const R* in, int field, double* out, cud
   template void launch_pack<R>(const Layout&, const Background<R>&, const R*, R*, int, cudaStream_t); \
   template void launch_unpack<R>(const Layout&, const Background<R>&, const R*, R*, cudaStream_t); \
   template void launch_pack_padded<R>(const Layout&, const Background<R>&, const R*, R*, cudaStream_t); \
-  template void launch_layer_mean<R>(const Layout&, const R*, int, double*, cudaStream_t);
+  template void launch_layer_mean<R>(const Layout&, const R*, int, double*, cudaStream_t);                 \
+  template void launch_pack_plane<R>(const Layout&, const Background<R>&, const R*, R*, int, int, cudaStream_t);
 INST(float)
 INST(double)
 #undef INST

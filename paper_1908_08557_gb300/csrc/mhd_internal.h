@@ -156,6 +156,9 @@ template <typename R> void launch_abg_tables(const Layout& L, double dx, double 
 template <typename R> void launch_abg_target(const double* at, const double* a0, R* rel, long long n,
                                              cudaStream_t st);
 template <typename R> void launch_widen(const R* in, double* out, long long n, cudaStream_t st);
+// throughput probe: `iters` rounds of 8 independent FMA chains per thread
+// over grid x 256 threads, in R (instrumentation, not a step of the method)
+template <typename R> void launch_fma_probe(R* out, int grid, int iters, cudaStream_t st);
 // reductions
 // CFL block maxima by atomicMax into CFL_SLOTS slot pairs at `partial`
 // (zeroed first when `zero`); the planes: all, the inner ones whose stencils
@@ -183,6 +186,9 @@ template <typename R> void launch_unpack(const Layout& L, const Background<R>& b
 // padded copy with the background added (diagnostics)
 template <typename R> void launch_pack_padded(const Layout& L, const Background<R>& bg, const R* f, R* out,
                                               cudaStream_t st);
+// one layer k (0 .. nz-1) of one field into out [ny][nx], background added
+template <typename R> void launch_pack_plane(const Layout& L, const Background<R>& bg, const R* f, R* out, int field,
+                                             int k, cudaStream_t st);
 // per-layer FP64 mean of field `field` of an interior-packed state
 template <typename R> void launch_layer_mean(const Layout& L, const R* in, int field, double* out,
                                              cudaStream_t st);
