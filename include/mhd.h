@@ -115,6 +115,20 @@ typedef struct mhd_params {
    * rounding then scales with |A'| instead of |A|, which matters where A is
    * large (hundreds in the production-size box).  Not with adjoint = 1. */
   int a_background;
+  /* Non-uniform vertical grid (Sect. 1: the spacing grows from about 100 km
+   * in the photosphere to about 800 km in the corona; the snapshots carry
+   * the inverse spacing dz_1, Sect. 5.3): NULL for z_k = k dz, or a host
+   * array of the nz + 6 strictly increasing positions of the layers
+   * k = -3 .. nz + 2, read by mhd_workspace_bytes and mhd_create only.  The
+   * layer index is the uniform coordinate: dz/dxi and d2z/dxi2 come from the
+   * same sixth-order stencils, every z derivative follows by the chain rule,
+   * the ghost rules (Eqs. 8, 13) and the potential-field extrapolations
+   * (Eq. 17 and its inverted form) take the layer distances, the CFL rule the
+   * local spacing, the diagnostics the cell extents (z_{k+1} - z_{k-1}) / 2,
+   * the swamp weight and the cooling cut-off the positions.  dz is then
+   * unused.  Needs the default FP32 kernel or MHD_RK_VARIANT=simple; not
+   * with adjoint = 1. */
+  const double* z;
 } mhd_params;
 
 /* Diagnostics of the ghost-filled state at time t (FP64 sums). */

@@ -236,10 +236,12 @@ def stretched_z(nz, dz_bottom, dz_top, k_c, width):
     return z, zp, zpp
 
 
-def initial_potential_field(bz, nz, dx, dy, dz, dtype=np.float64):
+def initial_potential_field(bz, nz, dx, dy, dz, dtype=np.float64, z=None):
     """Potential field whose vertical component at z = 0 is bz, as a vector
     potential in the Weyl gauge with A_z = 0, using exact spectral wavenumbers:
-    A^(k, z) = (i k_y, -i k_x, 0) B^_z(k) / |k|^2 exp(-|k| z) for k = 0..nz-1.
+    A^(k, z) = (i k_y, -i k_x, 0) B^_z(k) / |k|^2 exp(-|k| z) for k = 0..nz-1,
+    at z = k dz or, with z (the nz + 6 layer positions of a non-uniform grid),
+    at the positions of the interior layers.
     (Initial-condition preparation; not the library's own inversion.)"""
     ny, nx = bz.shape
     kx = 2 * np.pi * np.fft.rfftfreq(nx, d=dx)[None, :]
@@ -256,8 +258,9 @@ def initial_potential_field(bz, nz, dx, dy, dz, dtype=np.float64):
         ayh = np.where(kk > 0, -1j * kx * bh / kk ** 2, 0.0)
     ax = np.empty((nz, ny, nx), dtype=dtype)
     ay = np.empty((nz, ny, nx), dtype=dtype)
+    zi = np.arange(nz) * dz if z is None else np.asarray(z, dtype=np.float64)[NGHOST:NGHOST + nz]
     for k in range(nz):
-        dec = np.exp(-kk * k * dz)
+        dec = np.exp(-kk * zi[k])
         ax[k] = np.fft.irfft2(axh * dec, s=(ny, nx))
         ay[k] = np.fft.irfft2(ayh * dec, s=(ny, nx))
     return ax, ay, np.zeros((nz, ny, nx), dtype=dtype)
@@ -280,8 +283,18 @@ class Case:
 
 def make_box(nx, ny, nz, seed=0, magnetogram="spots", n_mag=4, sigma=3.0,
              driver="noise", driver_rms=0.01, dx=1.0, dy=1.0, dz=1.0,
-             nsteps=50, name=None, ar_pair=None, t1=1.0, dtype=np.float64, bz_scale=1.0, **over) -> Case:
+             nsteps=50, name=None, ar_pair=None, t1=1.0, dtype=np.float64, bz_scale=1.0, z=None,
+             **over) -> Case:
+    """z: the nz + 6 layer positions of a non-uniform vertical grid (p["z"]);
+    the swamp then spans the top four local spacings and the atmosphere and
+    the potential field are evaluated at the positions (dz stays the scale
+    of the temperature transition)."""
     p = scheme_params(nx, ny, nz, dx, dy, dz, **over)
+    if z is not None:
+        z = np.asarray(z, dtype=np.float64)
+        ztop = z[NGHOST + nz - 1]
+        p.update(z=z, z_swamp_start=ztop - 4.0 * (ztop - z[NGHOST + nz - 2]), z_swamp_end=ztop)
+        p.update(over)
     if magnetogram == "spots":
         bz = magnetogram_spots(nx, ny, n_mag, sigma, seed)
     else:
@@ -294,8 +307,8 @@ def make_box(nx, ny, nz, seed=0, magnetogram="spots", n_mag=4, sigma=3.0,
         km = min(32, nx // 2, ny // 2)
         v0 = driver_solenoidal(nx, ny, km, driver_rms, seed)
         v1 = driver_solenoidal(nx, ny, km, driver_rms, seed + 1)
-    lnT0, lnrho0 = initial_atmosphere(nz, dz, p["gz"])
-    ax, ay, az = initial_potential_field(bz, nz, dx, dy, dz, dtype)
+    lnT0, lnrho0 = initial_atmosphere(nz, dz, p["gz"], z=z)
+    ax, ay, az = initial_potential_field(bz, nz, dx, dy, dz, dtype, z=z)
     st = np.zeros((NFIELD, nz, ny, nx), dtype=dtype)
     st[0], st[1], st[2] = ax, ay, az
     st[6] = lnrho0[NGHOST:NGHOST + nz, None, None]

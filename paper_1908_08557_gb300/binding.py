@@ -68,7 +68,8 @@ class Params(ctypes.Structure):
                 ("dt_fixed", ctypes.c_double), ("bext", ctypes.c_double * 3),
                 ("nc_tau", ctypes.c_double), ("nc_lnrho_magn", ctypes.c_double),
                 ("nc_lnrho_width", ctypes.c_double), ("nc_z_max", ctypes.c_double),
-                ("nc_z_width", ctypes.c_double), ("a_background", ctypes.c_int)]
+                ("nc_z_width", ctypes.c_double), ("a_background", ctypes.c_int),
+                ("z", ctypes.POINTER(ctypes.c_double))]
 
 
 class Stats(ctypes.Structure):
@@ -190,6 +191,14 @@ def make_params(p: Dict, precision: int = 32, stats_every: int = 0, adjoint: boo
     q.nc_z_max = float(p.get("nc_z_max", 10.0 * float(p["dz"])))
     q.nc_z_width = float(p.get("nc_z_width", 1.0 * float(p["dz"])))
     q.a_background = 1 if a_background else 0
+    # non-uniform vertical grid: p["z"], the nz + 6 layer positions (k = -3 ..
+    # nz + 2); the array stays referenced by the struct while it is in use
+    if p.get("z") is not None:
+        zarr = np.ascontiguousarray(p["z"], dtype=np.float64)
+        if zarr.shape != (q.nz + 2 * NGHOST,):
+            raise ValueError("p['z'] must hold nz + 6 layer positions")
+        q.z = zarr.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        q._zkeep = zarr
     return q
 
 

@@ -73,6 +73,11 @@ struct mhd_ctx {
   double* abg0;        // [2][ny][nx] FP64 A_bg_x, A_bg_y at the photosphere
   double* at64;        // [3][ny][nx] FP64 scratch: B_z target, A_x, A_y of the target
   void* atrel;         // [2][ny][nx] nudging target minus A_bg(k = 0), state precision
+  // non-uniform vertical grid (params z): the handle's copy of the positions
+  // (p.z points here), and the device tables dxi/dz, (d2xi/dz2)/(dxi/dz),
+  // z_k, cell extent, [4][nz] in the state precision
+  double* zh;
+  void* ztab;
   FFTPlan fp;
   bool have_fft;
   bool driver_set;
@@ -136,6 +141,28 @@ static int cuda_check(mhd_ctx* h, cudaError_t e, const char* what) {
 }
 
 static bool is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
+
+// position of layer k (-3 .. nz + 2): the given vertical grid, or k dz
+static double zpos(const mhd_params* p, int k) { return p->z ? p->z[k + NG] : (double)k * p->dz; }
+
+// sixth-order index-space derivatives of the positions at an interior layer:
+// dz/dxi and d2z/dxi2 (dz and 0 on the uniform grid)
+static void zderiv(const mhd_params* p, int k, double* z1, double* z2) {
+  static const double W1[4] = {0.0, 45.0 / 60.0, -9.0 / 60.0, 1.0 / 60.0};
+  static const double W2[4] = {-490.0 / 180.0, 270.0 / 180.0, -27.0 / 180.0, 2.0 / 180.0};
+  if (!p->z) {
+    *z1 = p->dz;
+    *z2 = 0.0;
+    return;
+  }
+  double a = 0.0, b = W2[0] * zpos(p, k);
+  for (int m = 1; m <= 3; ++m) {
+    a += W1[m] * (zpos(p, k + m) - zpos(p, k - m));
+    b += W2[m] * (zpos(p, k + m) + zpos(p, k - m));
+  }
+  *z1 = a;
+  *z2 = b;
+}
 static int ilog2(int n) {
   int l = 0;
   while ((1 << l) < n) ++l;
@@ -158,6 +185,16 @@ static const char* check_params(const mhd_params* p) {
   if (p->adjoint != 0 && p->adjoint != 1) return "adjoint must be 0 or 1";
   if (p->a_background != 0 && p->a_background != 1) return "a_background must be 0 or 1";
   if (p->a_background && p->adjoint) return "a_background is not supported with adjoint = 1";
+  if (p->z) {
+    if (p->adjoint) return "a non-uniform vertical grid is not supported with adjoint = 1";
+    for (int q = 0; q + 1 < p->nz + 2 * NG; ++q)
+      if (!(p->z[q + 1] > p->z[q])) return "z: the nz + 6 layer positions must increase strictly";
+    for (int k = 0; k < p->nz; ++k) {
+      double z1, z2;
+      zderiv(p, k, &z1, &z2);
+      if (!(z1 > 0.0)) return "z: the sixth-order dz/dxi must be positive at every interior layer";
+    }
+  }
   if ((long long)p->nx * p->ny * p->nz > (1LL << 34)) return "grid too large";
   if (p->adjoint && (long long)NF * (p->nz + 2 * NG) * p->ny * (p->nx / 4) >= (1LL << 31))
     return "grid too large for the adjoint (8 (nz + 6) ny nx / 4 must stay below 2^31)";
@@ -182,7 +219,7 @@ struct Carve {
 struct Offsets {
   size_t f0, f1, df, lnrho0, wtab, wptab, bz, axt, ayt, v0, v1, red, ss, bg, bj, sw;
   size_t s2, fbar, dbar, gbar, coef, thbar;
-  size_t abB, abL, abgR, abg0, at64, atrel;
+  size_t abB, abL, abgR, abg0, at64, atrel, ztab;
   size_t twx, twy, et, eb, ktx, kty, P, Q;
   size_t total;
 };
@@ -193,7 +230,7 @@ static void swamp_weight(const mhd_params* p, double z, double* w, double* wp);
 static int swamp_first_layer(const mhd_params* p) {
   for (int k = 0; k < p->nz; ++k) {
     double w, wp;
-    swamp_weight(p, k * p->dz, &w, &wp);
+    swamp_weight(p, zpos(p, k), &w, &wp);
     if (w != 0.0 || wp != 0.0) return k;
   }
   return p->nz;
@@ -220,6 +257,7 @@ static Offsets plan_offsets(const mhd_params* p) {
   o.red = c.take(((size_t)RED_BLOCKS_MAX * 8 + 2 * CFL_SLOTS) * sizeof(double));
   o.ss = c.take(sizeof(StepState));
   o.bg = c.take((size_t)(6 * p->nz + 12) * es);
+  o.ztab = c.take((size_t)4 * p->nz * es);
   if (p->precision == 32 && !p->a_background) {
     o.bj = c.take((size_t)6 * n2 * p->nz * 4);
     o.sw = c.take((size_t)3 * n2 * (p->nz - swamp_first_layer(p)) * 4);
@@ -249,8 +287,8 @@ static Offsets plan_offsets(const mhd_params* p) {
   if (p->bc_z == 0) {
     o.twx = c.take((size_t)p->nx * 16);
     o.twy = c.take((size_t)p->ny * 16);
-    o.et = c.take(n2 * 8);
-    o.eb = c.take(n2 * 8);
+    o.et = c.take(3 * n2 * 8);
+    o.eb = c.take(3 * n2 * 8);
     o.ktx = c.take((size_t)p->nx * 8);
     o.kty = c.take((size_t)p->ny * 8);
     o.P = c.take(3 * n2 * 16);
@@ -300,7 +338,7 @@ static Phys<R> make_phys(const mhd_params* p) {
   // layers below the height cut-off (c_z(k dz) > 0); none when off
   ph.nc_k1 = 0;
   if (p->nc_tau > 0.0 && p->bc_z == 0)
-    while (ph.nc_k1 < p->nz && (double)ph.nc_k1 * p->dz < p->nc_z_max) ++ph.nc_k1;
+    while (ph.nc_k1 < p->nz && zpos(p, ph.nc_k1) < p->nc_z_max) ++ph.nc_k1;
   return ph;
 }
 
@@ -358,7 +396,8 @@ static int upload_background(mhd_ctx* h, const double* lnrho0, const double* lnT
       for (int k = 0; k < nz; ++k) tb[k + NG] = tmean[k];
       for (int m = 1; m <= NG; ++m) {
         const int b1 = NG - m + 1, b0 = NG - m;
-        tb[b0] = tb[b1] + lb[b1] - lb[b0] - p->dz * p->gz / exp(tb[b1]);
+        const double dzm = zpos(p, 1 - m) - zpos(p, -m);
+        tb[b0] = tb[b1] + lb[b1] - lb[b0] - dzm * p->gz / exp(tb[b1]);
         tb[NG + kt + m] = tb[NG + kt - m];
       }
     }
@@ -382,10 +421,20 @@ static int upload_background(mhd_ctx* h, const double* lnrho0, const double* lnT
       b1 += W1[m] * (tb[c + m] - tb[c - m]);
       b2 += W2[m] * (tb[c + m] + tb[c - m]);
     }
-    t_dl[k] = (R)(a1 / p->dz);
-    t_d2l[k] = (R)(a2 / (p->dz * p->dz));
-    t_dt[k] = (R)(b1 / p->dz);
-    t_d2t[k] = (R)(b2 / (p->dz * p->dz));
+    if (p->z) {
+      // chain rule: D_z f = f_xi / z', D_z^2 f = f_xixi / z'^2 - f_xi z'' / z'^3
+      double z1, z2;
+      zderiv(p, k, &z1, &z2);
+      t_dl[k] = (R)(a1 / z1);
+      t_d2l[k] = (R)(a2 / (z1 * z1) - a1 * z2 / (z1 * z1 * z1));
+      t_dt[k] = (R)(b1 / z1);
+      t_d2t[k] = (R)(b2 / (z1 * z1) - b1 * z2 / (z1 * z1 * z1));
+    } else {
+      t_dl[k] = (R)(a1 / p->dz);
+      t_d2l[k] = (R)(a2 / (p->dz * p->dz));
+      t_dt[k] = (R)(b1 / p->dz);
+      t_d2t[k] = (R)(b2 / (p->dz * p->dz));
+    }
   }
   Background<R> bg;
   bg.lbar = (const R*)h->bgtab;
@@ -397,6 +446,31 @@ static int upload_background(mhd_ctx* h, const double* lnrho0, const double* lnT
   for (int m = 0; m <= NG; ++m) { bg.cb[m] = R(0); bg.ctT[m] = R(0); bg.ctL[m] = R(0); }
   bg.ksw = h->ksw;
   bg.bB = bg.bJ = bg.bL = bg.abg = nullptr;
+  // vertical grid: ghost-rule distances, and the per-layer tables
+  for (int m = 0; m <= NG; ++m) { bg.dzb[m] = R(0); bg.dzt[m] = R(0); }
+  for (int m = 1; m <= NG; ++m) {
+    bg.dzb[m] = (R)(zpos(p, 1 - m) - zpos(p, -m));
+    bg.dzt[m] = (R)(zpos(p, kt + m) - zpos(p, kt - m));
+  }
+  bg.zm1 = bg.zr21 = bg.zk = bg.zcell = nullptr;
+  if (p->z) {
+    std::vector<R> zt((size_t)4 * nz);
+    for (int k = 0; k < nz; ++k) {
+      double z1, z2;
+      zderiv(p, k, &z1, &z2);
+      zt[k] = (R)(1.0 / z1);
+      zt[(size_t)nz + k] = (R)(-z2 / (z1 * z1));
+      zt[(size_t)2 * nz + k] = (R)zpos(p, k);
+      zt[(size_t)3 * nz + k] = (R)(0.5 * (zpos(p, k + 1) - zpos(p, k - 1)));
+    }
+    int rz = cuda_check(h, cudaMemcpy(h->ztab, zt.data(), zt.size() * sizeof(R), cudaMemcpyHostToDevice),
+                        "upload vertical grid");
+    if (rz) return rz;
+    bg.zm1 = (const R*)h->ztab;
+    bg.zr21 = bg.zm1 + nz;
+    bg.zk = bg.zm1 + 2 * nz;
+    bg.zcell = bg.zm1 + 3 * nz;
+  }
   if (h->abg_mode) {
     const long long n3 = (long long)p->nx * p->ny * nz;
     bg.bB = (const R*)h->abB;
@@ -450,7 +524,10 @@ static void release_side(mhd_ctx* h) {
   h->side = nullptr;
 }
 
+// sum of the inverse squared spacings of the CFL rule; with a non-uniform
+// vertical grid the reduction applies each layer's own sum (this is then 1)
 static double inv2sum(const mhd_params* p) {
+  if (p->z) return 1.0;
   return 1.0 / (p->dx * p->dx) + 1.0 / (p->dy * p->dy) + 1.0 / (p->dz * p->dz);
 }
 
@@ -460,7 +537,10 @@ static void run_stats(mhd_ctx* h, R* f) {
   ClassTimer ct(h, MHD_KC_STATS, 3);
   // B into the RK accumulator: free here (substep 0 does not read it)
   int nb = launch_stats_partial<R>(h->L, ph, bgr<R>(h), f, (R*)h->df, h->red, h->st);
-  launch_stats_finalize(h->red, nb, h->ss, h->p.dx * h->p.dy * h->p.dz, h->p.dx * h->p.dy, h->p.gamma - 1.0, h->st);
+  // cell volume dx dy dz; with a non-uniform vertical grid each cell's
+  // extent is applied in the partial sums
+  const double dv = h->p.dx * h->p.dy * (h->p.z ? 1.0 : h->p.dz);
+  launch_stats_finalize(h->red, nb, h->ss, dv, h->p.dx * h->p.dy, h->p.gamma - 1.0, h->st);
 }
 
 // fused RHS + RK launch: TMA-fed z-march for FP32 (unless disabled), the
@@ -479,9 +559,11 @@ static void launch_rk_any(mhd_ctx* h, const R* fin, R* fout, int sub) {
   Driver drv = kernel_driver(h);
   if (sizeof(R) == 4 && h->pair) {
     const int which = (const void*)fin == h->f[0] ? 0 : 1;
+    // on a non-uniform vertical grid the z stencils run in index space
+    // (unit spacing) and the kernel applies the metric per layer
     launch_rk_pair(&h->tm[which], &h->tmdf, h->L, *(const Phys<float>*)&ph, h->bgf, (float*)fout, (float*)h->df,
-                   (const float*)h->wtab, (const float*)h->wptab, drv, h->ss, sub, h->p.dx, h->p.dy, h->p.dz, h->st,
-                   h->dbg_skip_plane, h->dbg_wait_limit);
+                   (const float*)h->wtab, (const float*)h->wptab, drv, h->ss, sub, h->p.dx, h->p.dy,
+                   h->p.z ? 1.0 : h->p.dz, h->st, h->dbg_skip_plane, h->dbg_wait_limit);
     h->dbg_skip_plane = INT_MIN;  // one launch only
     return;
   }
@@ -590,18 +672,26 @@ static int upload_fft_tables(mhd_ctx* h, const Offsets& o) {
                                   cudaMemcpyHostToDevice), "upload twiddles");
     if (rc) return rc;
   }
-  // continuous |k| = 2 pi sqrt((m/Lx)^2 + (n/Ly)^2), signed m, n; tables [kx][ky]
+  // continuous |k| = 2 pi sqrt((m/Lx)^2 + (n/Ly)^2), signed m, n; tables
+  // [m - 1][kx][ky] for ghost layer m: exp(-|k| d_m) above the top layer,
+  // d_m = z_{nz-1+m} - z_{nz-1} (Eq. 17), and exp(f_b |k| d'_m) below the
+  // photosphere, d'_m = z_0 - z_{-m} (m dz on the uniform grid)
   double lx = nx * p->dx, ly = ny * p->dy;
-  std::vector<double> et((size_t)nx * ny), eb((size_t)nx * ny);
-  for (int a = 0; a < nx; ++a) {
-    int ma = 2 * a > nx ? a - nx : a;
-    double kx = 2.0 * M_PI * ma / lx;
-    for (int b = 0; b < ny; ++b) {
-      int mb = 2 * b > ny ? b - ny : b;
-      double ky = 2.0 * M_PI * mb / ly;
-      double kk = sqrt(kx * kx + ky * ky);
-      et[(size_t)a * ny + b] = exp(-kk * p->dz);
-      eb[(size_t)a * ny + b] = exp(p->f_pfe_bottom * kk * p->dz);
+  const size_t n2 = (size_t)nx * ny;
+  std::vector<double> et(3 * n2), eb(3 * n2);
+  const int kt = p->nz - 1;
+  for (int m = 1; m <= NG; ++m) {
+    const double dt = zpos(p, kt + m) - zpos(p, kt), db = zpos(p, 0) - zpos(p, -m);
+    for (int a = 0; a < nx; ++a) {
+      int ma = 2 * a > nx ? a - nx : a;
+      double kx = 2.0 * M_PI * ma / lx;
+      for (int b = 0; b < ny; ++b) {
+        int mb = 2 * b > ny ? b - ny : b;
+        double ky = 2.0 * M_PI * mb / ly;
+        double kk = sqrt(kx * kx + ky * ky);
+        et[(size_t)(m - 1) * n2 + (size_t)a * ny + b] = exp(-kk * dt);
+        eb[(size_t)(m - 1) * n2 + (size_t)a * ny + b] = exp(p->f_pfe_bottom * kk * db);
+      }
     }
   }
   rc = cuda_check(h, cudaMemcpy((void*)fp.et, et.data(), et.size() * 8, cudaMemcpyHostToDevice), "upload et");
@@ -651,6 +741,16 @@ extern "C" int mhd_create(const mhd_params* p, void* workspace, size_t ws_bytes,
   memset(mem_ctx, 0, sizeof(mhd_ctx));
   mhd_ctx* h = (mhd_ctx*)mem_ctx;
   h->p = *p;
+  if (p->z) {
+    // the handle keeps its own copy of the vertical grid
+    h->zh = (double*)malloc(sizeof(double) * (size_t)(p->nz + 2 * NG));
+    if (!h->zh) {
+      free(h);
+      return fail(nullptr, MHD_ERR_ARG, "host allocation failed");
+    }
+    memcpy(h->zh, p->z, sizeof(double) * (size_t)(p->nz + 2 * NG));
+    h->p.z = h->zh;
+  }
   h->L = make_layout(p->nx, p->ny, p->nz);
   h->st = (cudaStream_t)stream;
   h->esz = p->precision == 64 ? 8 : 4;
@@ -671,6 +771,7 @@ extern "C" int mhd_create(const mhd_params* p, void* workspace, size_t ws_bytes,
   h->cfl = h->red + (size_t)RED_BLOCKS_MAX * 8;
   h->ss = (StepState*)(h->ws + o.ss);
   h->bgtab = h->ws + o.bg;
+  h->ztab = h->ws + o.ztab;
   h->bj = h->ws + o.bj;
   h->sw = h->ws + o.sw;
   h->ksw = swamp_first_layer(p);
@@ -698,12 +799,14 @@ extern "C" int mhd_create(const mhd_params* p, void* workspace, size_t ws_bytes,
     h->split = h->tiled && !(v && strcmp(v, "fused") == 0);
     h->pair = h->split && !(v && (strcmp(v, "tiled") == 0 || strcmp(v, "split") == 0)) &&
               rk_pair_supported(h->L);
-    if (h->abg_mode && h->tiled && !h->pair) {
-      // the background tables are read by the pair kernel and the simple
-      // kernel only
+    if ((h->abg_mode || h->zh) && h->tiled && !h->pair) {
+      // the background tables and the vertical grid are read by the pair
+      // kernel and the simple kernel only
+      free(h->zh);
       free(h);
       return fail(nullptr, MHD_ERR_UNSUPPORTED,
-                  "a_background needs the default FP32 kernel (nx even, nx >= 8, ny >= 6) or MHD_RK_VARIANT=simple");
+                  "a_background and a non-uniform z grid need the default FP32 kernel (nx even, nx >= 8, ny >= 6) "
+                  "or MHD_RK_VARIANT=simple");
     }
     if (h->abg_mode) h->split = false;
     const char* va = getenv("MHD_ADJ_VARIANT");
@@ -727,7 +830,7 @@ extern "C" int mhd_create(const mhd_params* p, void* workspace, size_t ws_bytes,
     }
     rc = cuda_check(h, cudaMemcpy(h->lnrho0, buf.data(), 8 * es, cudaMemcpyHostToDevice), "upload lnrho0");
     std::vector<double> w(p->nz), wp(p->nz);
-    for (int k = 0; k < p->nz; ++k) swamp_weight(p, k * p->dz, &w[k], &wp[k]);
+    for (int k = 0; k < p->nz; ++k) swamp_weight(p, zpos(p, k), &w[k], &wp[k]);
     char* wb = buf.data() + 8 * es;
     for (int k = 0; k < p->nz; ++k) {
       if (es == 8) { ((double*)wb)[k] = w[k]; ((double*)wb)[p->nz + k] = wp[k]; }
@@ -804,6 +907,7 @@ extern "C" int mhd_create(const mhd_params* p, void* workspace, size_t ws_bytes,
   if (rc) {
     snprintf(g_err, sizeof g_err, "%s", h->err);
     release_side(h);
+    free(h->zh);
     free(h);
     return rc;
   }
@@ -1419,6 +1523,7 @@ extern "C" void mhd_destroy(mhd_handle h) {
   release_side(h);
   drop_events(h);
   delete h->evs;
+  free(h->zh);
   free(h);
 }
 

@@ -88,6 +88,18 @@ struct Background {
   const R* bL;     // [4][nz - ksw][ny][nx] lap A_bg (3), div A_bg on layers k >= ksw
   const R* abg;    // A_bg itself in the padded layout, fields 0..2 (read, write)
   int ksw;         // first layer with a nonzero swamp weight or slope
+  // Non-uniform vertical grid (params z; all null on the uniform grid): per
+  // interior layer dxi/dz, (d2xi/dz2) / (dxi/dz) (so that
+  // D_z^2 f = m1^2 D_xi^2 f + r21 D_z f), the position and the cell extent
+  // (z_{k+1} - z_{k-1}) / 2.  The ghost rules take dzb[m] = z_{1-m} - z_{-m}
+  // below the photosphere and dzt[m] = z_{nz-1+m} - z_{nz-1-m} at the top (on
+  // the uniform grid dz and 2 m dz).
+  const R* zm1;
+  const R* zr21;
+  const R* zk;
+  const R* zcell;
+  R dzb[4];
+  R dzt[4];
 };
 
 // Device-resident bookkeeping of the time integration (FP64).
@@ -158,7 +170,7 @@ __device__ __forceinline__ R nc_term(const Phys<R>& ph, const Background<R>& bg,
   const R* lr = bg.lbar + NG;
   const R* lt = bg.tbar + NG;
   R dcr = R(0);
-  const R cz = nc_step<R>(R(k) * ph.dz, ph.nc_zmax, ph.nc_zw, nullptr);
+  const R cz = nc_step<R>(bg.zk ? bg.zk[k] : R(k) * ph.dz, ph.nc_zmax, ph.nc_zw, nullptr);
   const R cr = nc_step<R>(lr[0] - L, ph.nc_lmag, ph.nc_lw, dL ? &dcr : nullptr);
   R lnTp, slope = R(0);
   if (L >= lr[0]) {

@@ -242,10 +242,10 @@ __global__ void __launch_bounds__(256) cols_kernel(FFTPlan fp, int mode, const S
         g = make_double2(0.0, 0.0);
       }
     } else {
-      // layer o + 1: multipliers M_t^(o+1), M_b^(o+1)
-      const double e_t = fp.et[(long long)col * ny + ky], e_b = fp.eb[(long long)col * ny + ky];
-      double mt = e_t, mb = e_b;
-      for (int jj = 0; jj < o; ++jj) { mt *= e_t; mb *= e_b; }
+      // ghost layer o + 1: the multipliers of its distance from the top
+      // layer (M_t) and, below the photosphere, from the bottom one (M_b)
+      const long long e = (long long)o * nx * ny + (long long)col * ny + ky;
+      const double mt = fp.et[e], mb = fp.eb[e];
       if (p == 0) {
         g = make_double2(mt * F.x, mt * F.y);
       } else if (p == 1) {
@@ -368,9 +368,8 @@ __global__ void __launch_bounds__(256) cols_adj_kernel(FFTPlan fp, const StepSta
       const int line = q / ny, ky = q - line * ny;
       const int kx = pair0 + (line >> 1);
       const int col = (line & 1) ? ((nx - kx) & (nx - 1)) : kx;
-      const double e_t = fp.et[(long long)col * ny + ky], e_b = fp.eb[(long long)col * ny + ky];
-      double mt = e_t, mb = e_b;
-      for (int jj = 1; jj < m; ++jj) { mt *= e_t; mb *= e_b; }
+      const long long e = (long long)(m - 1) * nx * ny + (long long)col * ny + ky;
+      const double mt = fp.et[e], mb = fp.eb[e];
       const double2 F = spec[line * ny + ky];
       const double2 Fm = spec[(line ^ 1) * ny + ((ny - ky) & (ny - 1))];
       const double ca = 0.5 * (mt + mb), cb = 0.5 * (mt - mb);

@@ -81,13 +81,14 @@ __global__ void bc_kernel(Layout L, Phys<R> ph, Background<R> bg, R* __restrict_
     return;
   }
   // bottom
+  // (layer distances from the vertical grid: bg.dzb[m] = z_{1-m} - z_{-m},
+  // bg.dzt[m] = z_{nz-1+m} - z_{nz-1-m}; dz and 2 m dz on the uniform grid)
   R th1 = f[L.at(LT, 0, j, i)];
   R l1 = f[L.at(LR, 0, j, i)];
-  const R dzg = dz * ph.gz;
   for (int m = 1; m <= NG; ++m) {
     const R T1 = rexp<R>(bg.tbar[NG - m + 1] + th1);
     const R l0 = R(0);
-    const R th0 = th1 + l1 - l0 + bg.cb[m] - dzg / T1;
+    const R th0 = th1 + l1 - l0 + bg.cb[m] - bg.dzb[m] * ph.gz / T1;
     f[L.at(LR, -m, j, i)] = l0;
     f[L.at(LT, -m, j, i)] = th0;
     f[L.at(UZ, -m, j, i)] = -f[L.at(UZ, m, j, i)];
@@ -98,7 +99,7 @@ __global__ void bc_kernel(Layout L, Phys<R> ph, Background<R> bg, R* __restrict_
   const R Ttop = rexp<R>(bg.tbar[NG + kt] + f[L.at(LT, kt, j, i)]);
   for (int m = 1; m <= NG; ++m) {
     f[L.at(LT, kt + m, j, i)] = f[L.at(LT, kt - m, j, i)] + bg.ctT[m];
-    f[L.at(LR, kt + m, j, i)] = f[L.at(LR, kt - m, j, i)] + bg.ctL[m] + (R(2 * m) * dz) * ph.gz / Ttop;
+    f[L.at(LR, kt + m, j, i)] = f[L.at(LR, kt - m, j, i)] + bg.ctL[m] + bg.dzt[m] * ph.gz / Ttop;
     f[L.at(UZ, kt + m, j, i)] = -f[L.at(UZ, kt - m, j, i)];
     f[L.at(UX, kt + m, j, i)] = f[L.at(UX, kt - m, j, i)];
     f[L.at(UY, kt + m, j, i)] = f[L.at(UY, kt - m, j, i)];

@@ -13,8 +13,8 @@ struct FFTPlan {
   int nx, ny, lognx, logny;
   const double2* twx;  // exp(-2 pi i r / nx), r < nx
   const double2* twy;  // exp(-2 pi i r / ny), r < ny
-  const double* et;    // [kx][ky] exp(-|k| dz)           (Eq. 17, upward)
-  const double* eb;    // [kx][ky] exp(+f_b |k| dz)       (Sect. 2.4, downward)
+  const double* et;    // [3][kx][ky] exp(-|k| d_m), ghost layer m above the top (Eq. 17)
+  const double* eb;    // [3][kx][ky] exp(+f_b |k| d'_m), ghost layer m below the photosphere (Sect. 2.4)
   const double* ktx;   // modified first-derivative wavenumbers, [nx]
   const double* kty;   // [ny]
   double2* P;          // [3][nx][ny] row spectra, transposed

@@ -85,14 +85,21 @@ __global__ void __launch_bounds__(256) cfl_partial_kernel(Layout L, Phys<R> ph, 
   if (i < L.nx && j < L.ny) {
     const int sy = L.mx;
     const int sz = (int)L.sz();
+    // a non-uniform vertical grid: the layer's own inverse spacing dxi/dz in
+    // the z derivatives and the advective rate, its own sum of inverse
+    // squared spacings in both rates (the finalize then takes 1)
+    const bool zg = bg.zm1 != nullptr;
+    const R idzk = zg ? bg.zm1[k] : ph.idz;
+    const R sqk = zg ? rsqrt_<R>(ph.idx2 + ph.idy2 + idzk * idzk) : sqinv2;
+    const R dsc = zg ? ph.idx2 + ph.idy2 + idzk * idzk : R(1);
     const R* pax = f + L.at(AX, k, j, i);
     const R* pay = f + L.at(AY, k, j, i);
     const R* paz = f + L.at(AZ, k, j, i);
     // B = curl A + B_ext (Eq. 6) at both cells
     R dyaz[2], dzay[2], dzax[2], dxaz[2], dxay[2], dyax[2];
     d1s_pair(paz, sy, ph.idy, dyaz[0], dyaz[1]);
-    d1s_pair(pay, sz, ph.idz, dzay[0], dzay[1]);
-    d1s_pair(pax, sz, ph.idz, dzax[0], dzax[1]);
+    d1s_pair(pay, sz, idzk, dzay[0], dzay[1]);
+    d1s_pair(pax, sz, idzk, dzax[0], dzax[1]);
     d1x_pair(paz, ph.idx, dxaz[0], dxaz[1]);
     d1x_pair(pay, ph.idx, dxay[0], dxay[1]);
     d1s_pair(pax, sy, ph.idy, dyax[0], dyax[1]);
@@ -121,12 +128,13 @@ __global__ void __launch_bounds__(256) cfl_partial_kernel(Layout L, Phys<R> ph, 
       const R lr = bg.lbar[k + NG] + lrs[c], lt = bg.tbar[k + NG] + lts[c];
       const R T = rexp<R>(lt), rho1 = rexp<R>(-lr);
       const R B2s = B0 * B0 + B1 * B1 + B2 * B2;
-      const R adv = fabs(ux[c]) * ph.idx + fabs(uy[c]) * ph.idy + fabs(uz[c]) * ph.idz +
-                    rsqrt_<R>(ph.gamma * T + B2s * rho1) * sqinv2;
+      const R adv = fabs(ux[c]) * ph.idx + fabs(uy[c]) * ph.idy + fabs(uz[c]) * idzk +
+                    rsqrt_<R>(ph.gamma * T + B2s * rho1) * sqk;
       R dm = ph.nu;
       dm = fmax(dm, ph.eta + ph.eta_s * w);
       dm = fmax(dm, ph.drho + ph.drho_s * w);
       dm = fmax(dm, ph.chi_s * w + ph.gm1 * ph.kappa0 * rexp<R>(R(2.5) * lt - lr));
+      if (zg) dm *= dsc;
       if (!isfinite(adv) || !isfinite(dm)) atomicOr(&ss->nonfinite, 1);
       mar = fmax(mar, adv);
       mdr = fmax(mdr, dm);
@@ -229,7 +237,7 @@ void launch_cfl_finalize(const double* partial, int nblk, StepState* ss, double 
 // the periodic images being computed from the state's images, bit for bit
 // equal to the interior values they copy.
 template <typename R>
-__global__ void __launch_bounds__(256) curl_a_kernel(Layout L, Phys<R> ph, const R* __restrict__ f,
+__global__ void __launch_bounds__(256) curl_a_kernel(Layout L, Phys<R> ph, Background<R> bg, const R* __restrict__ f,
                                                      R* __restrict__ bsc) {
   const int i = (int)(blockIdx.x * 32 + threadIdx.x) - NG, j = (int)(blockIdx.y * 8 + threadIdx.y) - NG;
   const int k = (int)blockIdx.z - NG;
@@ -240,9 +248,10 @@ __global__ void __launch_bounds__(256) curl_a_kernel(Layout L, Phys<R> ph, const
   const R* ay = f + L.at(AY, k, j, i);
   const R* az = f + L.at(AZ, k, j, i);
   const long long c = L.at(0, k, j, i);
+  const R idzk = (kz && bg.zm1) ? bg.zm1[k] : ph.idz;  // dxi/dz of the layer on a non-uniform grid
   if (ix && jy) bsc[c + 2 * L.fs] = d1(ay, (long long)1, ph.idx) - d1(ax, sy, ph.idy);
-  if (jy && kz) bsc[c] = d1(az, sy, ph.idy) - d1(ay, sz, ph.idz);
-  if (ix && kz) bsc[c + L.fs] = d1(ax, sz, ph.idz) - d1(az, (long long)1, ph.idx);
+  if (jy && kz) bsc[c] = d1(az, sy, ph.idy) - d1(ay, sz, idzk);
+  if (ix && kz) bsc[c + L.fs] = d1(ax, sz, idzk) - d1(az, (long long)1, ph.idx);
 }
 
 // Second pass: per block 7 values (sums of rho u^2/2, B^2/2, rho T/(gamma-1),
@@ -278,10 +287,12 @@ __global__ void __launch_bounds__(256) stats_partial_kernel(Layout L, Phys<R> ph
       const R* bx = bsc + L.at(0, k, j, i);
       const R* by = bx + L.fs;
       const R* bz = bx + 2 * L.fs;
+      // a non-uniform vertical grid: the layer's dxi/dz and cell extent
+      const R idzk = bg.zm1 ? bg.zm1[k] : ph.idz, vk = bg.zcell ? bg.zcell[k] : R(1);
       R dbx[2], dby[2], dbz[2];
       d1x_pair(bx, ph.idx, dbx[0], dbx[1]);
       d1s_pair(by, sy, ph.idy, dby[0], dby[1]);
-      d1s_pair(bz, sz, ph.idz, dbz[0], dbz[1]);
+      d1s_pair(bz, sz, idzk, dbz[0], dbz[1]);
       const auto cx = ldp(bx), cy = ldp(by), cz = ldp(bz);
       const auto u0 = ldp(f + L.at(UX, k, j, i)), u1 = ldp(f + L.at(UY, k, j, i)), u2 = ldp(f + L.at(UZ, k, j, i));
       const auto plr = ldp(f + L.at(LR, k, j, i)), plt = ldp(f + L.at(LT, k, j, i));
@@ -307,10 +318,10 @@ __global__ void __launch_bounds__(256) stats_partial_kernel(Layout L, Phys<R> ph
                 Bz = bzs[c] + ph.bext[2] + gb[2][c];
         const R rho = rexp<R>(bg.lbar[k + NG] + lrs[c]);
         const R T = rexp<R>(bg.tbar[k + NG] + lts[c]);
-        nadd(0, R(0.5) * rho * (ux[c] * ux[c] + uy[c] * uy[c] + uz[c] * uz[c]));
-        nadd(1, R(0.5) * (Bx * Bx + By * By + Bz * Bz));
-        nadd(2, rho * T);  // / (gamma - 1) once, in the finalize
-        nadd(3, rho);
+        nadd(0, R(0.5) * rho * (ux[c] * ux[c] + uy[c] * uy[c] + uz[c] * uz[c]) * vk);
+        nadd(1, R(0.5) * (Bx * Bx + By * By + Bz * Bz) * vk);
+        nadd(2, rho * T * vk);  // / (gamma - 1) once, in the finalize
+        nadd(3, rho * vk);
         if (k == 0) {
           nadd(4, Bz);
           nadd(5, fabs(Bz));
@@ -340,7 +351,7 @@ template <typename R>
 int launch_stats_partial(const Layout& L, const Phys<R>& ph, const Background<R>& bg, const R* f, R* bsc,
                          double* partial, cudaStream_t st) {
   dim3 gc((L.nx + 2 * NG + 31) / 32, (L.ny + 2 * NG + 7) / 8, L.nz + 2 * NG);
-  curl_a_kernel<R><<<gc, dim3(32, 8), 0, st>>>(L, ph, f, bsc);
+  curl_a_kernel<R><<<gc, dim3(32, 8), 0, st>>>(L, ph, bg, f, bsc);
   int kchunk;
   dim3 g = red_grid(L, &kchunk);
   stats_partial_kernel<R><<<g, dim3(32, 8), 0, st>>>(L, ph, bg, f, bsc, partial, kchunk);

@@ -53,8 +53,12 @@ __global__ void __launch_bounds__(256, sizeof(R) == 8 ? 2 : 0) rk_simple_kernel(
   if (halted(a.ss)) return;
   const Phys<R>& ph = a.ph;
   const long long st[3] = {1, L.sy(), L.sz()};
-  const R inv[3] = {ph.idx, ph.idy, ph.idz};
-  const R inv2[3] = {ph.idx2, ph.idy2, ph.idz2};
+  // a non-uniform vertical grid: z derivatives scaled by dxi/dz of the layer,
+  // and D_z^2 f = (dxi/dz)^2 D_xi^2 f + r21 D_z f (added below)
+  const bool zg = a.bg.zm1 != nullptr;
+  const R m1 = zg ? a.bg.zm1[k] : ph.idz, r21 = zg ? a.bg.zr21[k] : R(0);
+  const R inv[3] = {ph.idx, ph.idy, m1};
+  const R inv2[3] = {ph.idx2, ph.idy2, zg ? m1 * m1 : ph.idz2};
   const R* base[NF];
 #pragma unroll
   for (int fl = 0; fl < NF; ++fl) base[fl] = a.fin + L.at(fl, k, j, i);
@@ -73,7 +77,11 @@ __global__ void __launch_bounds__(256, sizeof(R) == 8 ? 2 : 0) rk_simple_kernel(
     for (int ax = 0; ax < 3; ++ax) {
       c.dA[cc][ax] = d1(pa, st[ax], inv[ax]);
       c.dU[cc][ax] = d1(pu, st[ax], inv[ax]);
-      const R da2 = d2(pa, st[ax], inv2[ax]), du2 = d2(pu, st[ax], inv2[ax]);
+      R da2 = d2(pa, st[ax], inv2[ax]), du2 = d2(pu, st[ax], inv2[ax]);
+      if (ax == 2 && zg) {
+        da2 += r21 * c.dA[cc][2];
+        du2 += r21 * c.dU[cc][2];
+      }
       if (ax == cc) {
         a2[cc] = da2;
         u2[cc] = du2;
@@ -110,6 +118,10 @@ __global__ void __launch_bounds__(256, sizeof(R) == 8 ? 2 : 0) rk_simple_kernel(
     c.gT[ax] = d1(base[LT], st[ax], inv[ax]);
     c.lapL += d2(base[LR], st[ax], inv2[ax]);
     c.lapT += d2(base[LT], st[ax], inv2[ax]);
+  }
+  if (zg) {
+    c.lapL += r21 * c.gL[2];
+    c.lapT += r21 * c.gT[2];
   }
   c.gL[2] += a.bg.dl[k];
   c.lapL += a.bg.d2l[k];

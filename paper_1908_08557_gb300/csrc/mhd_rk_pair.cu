@@ -437,6 +437,10 @@ __global__ void __launch_bounds__(NT, 2) rk_pair_kernel(const __grid_constant__ 
       const float wk = a.wtab[k], wpk = a.wptab[k];
       const float lbk = a.bg.lbar[k + NG], tbk = a.bg.tbar[k + NG];
       const float dlk = a.bg.dl[k], dtk = a.bg.dt[k], d2lk = a.bg.d2l[k], d2tk = a.bg.d2t[k];
+      // non-uniform vertical grid: the z stencils ran in index space; the
+      // metric of layer k (dxi/dz, and r21 with D_z^2 = m1^2 D_xi^2 + r21 D_z)
+      const bool zg = a.bg.zm1 != nullptr;
+      const float zm1k = zg ? a.bg.zm1[k] : 1.f, zr21k = zg ? a.bg.zr21[k] : 0.f;
       // background B, J of the pair (A stored about a background), issued
       // before the waits so that their latency overlaps them
       f2 gB[3], gJ[3];
@@ -487,6 +491,15 @@ __global__ void __launch_bounds__(NT, 2) rk_pair_kernel(const __grid_constant__ 
         }
 #pragma unroll
         for (int q = 0; q < 6; ++q) mz[q] = fma2(cm, dif(sp.get(q), sm.get(q)), mz[q]);
+      }
+      if (zg) {
+#pragma unroll
+        for (int f = 0; f < NF; ++f) {
+          d1z[f] = mul(F2(zm1k), d1z[f]);
+          d2z[f] = fma2(F2(zr21k), d1z[f], mul(F2(zm1k * zm1k), d2z[f]));
+        }
+#pragma unroll
+        for (int q = 0; q < 6; ++q) mz[q] = mul(F2(zm1k), mz[q]);
       }
 
       // stateful u_x, u_y ghost rows below the photosphere (k = 0): their

@@ -62,6 +62,32 @@ def test_workspace_sizing_and_argument_errors(lib):
     assert lib.mhd_step(None, 1) == binding.MHD_ERR_ARG
 
 
+def test_background_and_vertical_grid_parameters(lib):
+    """Workspace sizing with A stored about a background (more tables) and
+    with a non-uniform vertical grid; neither combines with the adjoint; the
+    positions must increase strictly."""
+    import numpy as np
+
+    import inputs
+    from paper_1908_08557_gb300 import binding
+    p = inputs.scheme_params(32, 32, 24)
+    n = lib.mhd_workspace_bytes(ctypes.byref(binding.make_params(p, 32)))
+    nb = lib.mhd_workspace_bytes(ctypes.byref(binding.make_params(p, 32, a_background=True)))
+    assert nb > n > 0
+    bad = binding.make_params(p, 32, adjoint=True, a_background=True)
+    assert lib.mhd_workspace_bytes(ctypes.byref(bad)) == 0
+    z, _, _ = inputs.stretched_z(24, 0.5, 1.5, 12, 4)
+    qz = binding.make_params(dict(p, z=z), 32)
+    assert lib.mhd_workspace_bytes(ctypes.byref(qz)) > 0
+    assert lib.mhd_workspace_bytes(ctypes.byref(binding.make_params(dict(p, z=z), 32, adjoint=True))) == 0
+    zbad = z.copy()
+    zbad[10] = zbad[9]
+    assert lib.mhd_workspace_bytes(ctypes.byref(binding.make_params(dict(p, z=zbad), 32))) == 0
+    assert lib.mhd_workspace_bytes(ctypes.byref(binding.make_params(dict(p, z=z[::-1].copy()), 64))) == 0
+    with np.testing.assert_raises(ValueError):
+        binding.make_params(dict(p, z=z[:-1]), 32)
+
+
 def test_cooling_parameter_errors(lib):
     """Newtonian cooling (Sect. 3.1): invalid rates and cut-off widths are
     rejected before any allocation, and so is an initial ln rho profile that
