@@ -631,11 +631,17 @@ def run_native(args, ws, rank, local):
     ms_max = sorted(runs)[RUNS // 2]
     value = ws * cells * args.steps / (ms_max / 1e3)
 
-    # per-kernel-class timing on the library's stream (separate pass)
+    # per-kernel-class timing on the library's stream (separate passes):
+    # as the step runs (overlapped classes counted in full), and with every
+    # kernel serialised on one stream, whose class times add up to the step
     nprof = min(args.steps, 20)
     sim.profile(True)
     sim.step(nprof)
     prof = sim.read_profile()
+    sim.profile(False)
+    sim.profile(2)
+    sim.step(nprof)
+    prof_serial = sim.read_profile()
     sim.profile(False)
     rk_ms, rk_n = prof["rk"]
     esz = 4
@@ -647,7 +653,8 @@ def run_native(args, ws, rank, local):
                 "traffic": rk_traffic_bytes(), "kernel": RK_KERNEL,
                 "peak_source": "measured" if peaks else "fallback",
                 "alg_bytes_per_launch": alg_bytes_per_launch, "avg_launch_ms": rk_ms / rk_n,
-                "class_ms_per_step": {k: v[0] / nprof for k, v in prof.items()}}
+                "class_ms_per_step": {k: v[0] / nprof for k, v in prof.items()},
+                "class_ms_per_step_serialised": {k: v[0] / nprof for k, v in prof_serial.items()}}
 
     # end to end through the C ABI with host buffers: each step uploads its
     # driver snapshot (B_z, v0, v1) from pinned host memory, steps, and

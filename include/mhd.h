@@ -486,9 +486,12 @@ void mhd_gran_destroy(mhd_gran_handle g);
 
 /* enable != 0: from now on bracket every kernel class launched by mhd_step
  * with CUDA events on the stream it runs on; enable = 0 stops recording.
- * Classes that overlap (the first substep's FFT on the side stream, the
- * ghost rules and CFL reduction beside it) are each timed in full, so the
- * class times of a step can sum to more than the step. */
+ * enable = 1: the step runs as usual, and classes that overlap (the first
+ * substep's FFT on the side stream, the ghost rules and CFL reduction beside
+ * it, the three FFT plane chains) are each timed in full, so the class times
+ * of a step can sum to more than the step.  enable = 2: while recording,
+ * every kernel runs on the handle's stream one after another (no side
+ * streams), so the class times add up to the (slightly longer) step. */
 int mhd_profile(mhd_handle h, int enable);
 
 /* Synchronise, then return per class the summed event time in ms and the

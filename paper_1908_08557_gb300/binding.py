@@ -460,8 +460,11 @@ class Simulation:
                                                   ctypes.c_void_p(lam.data_ptr())))
         return lam
 
-    def profile(self, enable: bool = True):
-        self._check(self.lib.mhd_profile(self.h, 1 if enable else 0))
+    def profile(self, enable=True):
+        """True / 1: record class times as the step runs; 2: record with every
+        kernel serialised on the handle's stream; False / 0: stop."""
+        mode = 0 if enable is False else (1 if enable is True else int(enable))
+        self._check(self.lib.mhd_profile(self.h, mode))
 
     def read_profile(self) -> Dict:
         ms = (ctypes.c_double * len(KERNEL_CLASSES))()

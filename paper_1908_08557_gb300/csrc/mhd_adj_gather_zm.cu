@@ -340,6 +340,29 @@ struct PArgs {
   Coef cx, cy;  // D1, D2 weights over dx, dy
 };
 
+// Staged fields.  Only the coefficients whose in-plane stencils the gather
+// takes need the x, y halo in shared memory; the ones it reads at the cell
+// alone (the z-derivative coefficients, the values) are loaded straight from
+// global memory, as 8-byte pairs of the thread's two cells.  Staged slot of
+// the group's field q (-1: read at the cell), and the centre slot (-1: staged).
+constexpr int NHP = 15;   // staged fields, at most (group 0; group 1 stages 12)
+constexpr int NCP = 8;    // centre-only fields, at most (group 1; group 0 reads 5)
+constexpr int NBP = 3;    // plane buffers: two planes in flight while one is used
+__host__ __device__ constexpr int hslot(int grp, int q) {
+  return grp == 0 ? (q == 2 || q == 5 || q == 8 || q == 15 || q == 18
+                         ? -1
+                         : q < 2 ? q : q < 5 ? q - 1 : q < 8 ? q - 2 : q < 15 ? q - 3 : q < 18 ? q - 4 : q - 5)
+                  : (q == 2 || q == 5 || q == 8 || (q >= 12 && q <= 15) || q == 18
+                         ? -1
+                         : q < 2 ? q : q < 5 ? q - 1 : q < 8 ? q - 2 : q < 12 ? q - 3 : q < 18 ? q - 7 : q - 8);
+}
+__host__ __device__ constexpr int cslot(int grp, int q) {
+  return grp == 0 ? (q == 2 ? 0 : q == 5 ? 1 : q == 8 ? 2 : q == 15 ? 3 : q == 18 ? 4 : -1)
+                  : (q == 2 ? 0 : q == 5 ? 1 : q == 8 ? 2 : (q >= 12 && q <= 15) ? q - 9 : q == 18 ? 7 : -1);
+}
+static_assert(hslot(0, 19) == 14 && hslot(1, 19) == 11 && hslot(1, 16) == 9 && cslot(1, 15) == 6, "slot maps");
+constexpr size_t smem_pair() { return (size_t)NBP * NHP * SP * 4 + (size_t)4 * TY * SX * 4; }
+
 template <int GRP>
 __device__ __forceinline__ void item_pair(const PArgs& pa_, float* buf, float* scrb, int x0, int y0, int n0,
                                           int n1) {
@@ -364,18 +387,21 @@ __device__ __forceinline__ void item_pair(const PArgs& pa_, float* buf, float* s
   auto cp16 = [](float* dst, const float* src) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(zm::sa(dst)), "l"(src) : "memory");
   };
-  auto stage = [&](int p, int b) {
-    float* dst = buf + b * NQ * SP;
+  auto stage = [&](int p, int bb) {
+    float* dst = buf + bb * NHP * SP;
     const float* src = a.coef + (long long)p * n2;
 #pragma unroll
     for (int q = 0; q < NQ; ++q) {
+      const int hs = hslot(GRP, q);
+      if (hs < 0) continue;
       const long long fo = (long long)kQ[GRP][q] * n3;
-      cp16(dst + q * SP + tid * 4, src + fo + off0);
-      if (tid + NTP < CP) cp16(dst + q * SP + (tid + NTP) * 4, src + fo + off1);
+      cp16(dst + hs * SP + tid * 4, src + fo + off0);
+      if (tid + NTP < CP) cp16(dst + hs * SP + (tid + NTP) * 4, src + fo + off1);
     }
     asm volatile("cp.async.commit_group;" ::: "memory");
   };
   if (pa <= pb) stage(pa, 0);
+  if (pa + 1 <= pb) stage(pa + 1, 1);
   int b = 0;
   f2 acc[NO][7];
 #pragma unroll
@@ -389,6 +415,7 @@ __device__ __forceinline__ void item_pair(const PArgs& pa_, float* buf, float* s
   const float g = GRP == 0 ? 1.f : 1.f / 3.f;
   const Coef& cx = pa_.cx;
   const Coef& cy = pa_.cy;
+  const long long qc = (long long)j * nx + i;  // the pair's offset within a plane
 
   for (int p = n0 - NG; p <= n1 + NG - 1; ++p) {
     const int n = p - NG;
@@ -405,20 +432,32 @@ __device__ __forceinline__ void item_pair(const PArgs& pa_, float* buf, float* s
       dd[t] = (emit && (fz || (ph.bcz == 0 && n <= 0))) ? ld2(a.dbar + q) : F2(0.f);
     }
     if (p >= pa && p <= pb) {
-      if (p + 1 <= pb) {
-        stage(p + 1, b ^ 1);
+      // the centre-only coefficients of plane p (issued before the wait)
+      f2 cv[NCP];
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) {
+        const int cs = cslot(GRP, q);
+        if (cs < 0) continue;
+        cv[cs] = live ? __ldg(reinterpret_cast<const float2*>(a.coef + (long long)kQ[GRP][q] * n3 + (long long)p * n2 + qc))
+                      : F2(0.f);
+      }
+      if (p + 2 <= pb) {
+        stage(p + 2, b == 0 ? 2 : b - 1);
+        asm volatile("cp.async.wait_group 2;" ::: "memory");
+      } else if (p + 1 <= pb) {
         asm volatile("cp.async.wait_group 1;" ::: "memory");
       } else {
         asm volatile("cp.async.wait_group 0;" ::: "memory");
       }
       __syncthreads();
-      const float* s = buf + b * NQ * SP;
-      auto S = [&](int q) { return s + q * SP + cen; };
+      const float* s = buf + b * NHP * SP;
+      auto S = [&](int q) { return s + hslot(GRP, q) * SP + cen; };
+      auto C = [&](int q) { return cv[cslot(GRP, q)]; };
       // first derivatives of the three components: -D1x, -D1y, D1z^T
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
         acc[c][3] = dif(acc[c][3], add(dx1(S(3 * c), cx), dy1(S(3 * c + 1), cy)));
-        zs_d1t(acc[c], mul(F2(idz), ld2(S(3 * c + 2))));
+        zs_d1t(acc[c], mul(F2(idz), C(3 * c + 2)));
       }
       // Laplacians (u: with the own-axis part of grad div u = lap u / 3)
 #pragma unroll
@@ -438,7 +477,7 @@ __device__ __forceinline__ void item_pair(const PArgs& pa_, float* buf, float* s
         zs_d2(acc[2], mul(F2(idz2), ld2(gz)));
       } else {
 #pragma unroll
-        for (int c = 0; c < 3; ++c) acc[c][3] = add(acc[c][3], ld2(S(12 + c)));
+        for (int c = 0; c < 3; ++c) acc[c][3] = add(acc[c][3], C(12 + c));
       }
       // xz, yz, zx, zy mixed: D1z of in-plane first derivatives
       const f2 gyy = dy1(gy, cy);
@@ -446,21 +485,21 @@ __device__ __forceinline__ void item_pair(const PArgs& pa_, float* buf, float* s
       zs_d1(acc[0], mul(F2(g * idz), dx1(gz, cx)));
       zs_d1(acc[1], mul(F2(g * idz), dy1(gz, cy)));
       // xy mixed through the x-halo scratch: D1x(D1y gd_x) -> y, D1x(D1y gd_y) -> x
-      float* scr = scrb + b * 2 * TY * SX;
+      float* scr = scrb + ((p - pa) & 1) * 2 * TY * SX;
       *reinterpret_cast<f2*>(scr + ty * SX + e) = dy1(gx, cy);
       *reinterpret_cast<f2*>(scr + TY * SX + ty * SX + e) = gyy;
       if (tid < 64)
         *reinterpret_cast<f2*>(scr + hf * TY * SX + hr * SX + hx) =
-            dy1(s + (GRP == 0 ? 12 + hf : 9 + hf) * SP + (hr + 3) * SX + hx, cy);
+            dy1(s + hslot(GRP, GRP == 0 ? 12 + hf : 9 + hf) * SP + (hr + 3) * SX + hx, cy);
       // the scalar: value, -D1x, -D1y, D1z^T, Laplacian
-      acc[3][3] = add(acc[3][3], dif(add(ld2(S(15)), add(dxx(S(19), cx), dyy(S(19), cy))),
+      acc[3][3] = add(acc[3][3], dif(add(C(15), add(dxx(S(19), cx), dyy(S(19), cy))),
                                      add(dx1(S(16), cx), dy1(S(17), cy))));
-      zs_d1t(acc[3], mul(F2(idz), ld2(S(18))));
+      zs_d1t(acc[3], mul(F2(idz), C(18)));
       zs_d2(acc[3], mul(F2(idz2), ld2(S(19))));
       __syncthreads();
       acc[1][3] = fma2(F2(g), dx1(scr + ty * SX + e, cx), acc[1][3]);
       acc[0][3] = fma2(F2(g), dx1(scr + TY * SX + ty * SX + e, cx), acc[0][3]);
-      b ^= 1;
+      b = b == NBP - 1 ? 0 : b + 1;
     }
     if (emit) {
 #pragma unroll
@@ -492,7 +531,7 @@ __device__ __forceinline__ void item_pair(const PArgs& pa_, float* buf, float* s
 __global__ void __launch_bounds__(NTP, 2) gather_pair_kernel(PArgs pa_) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float* buf = reinterpret_cast<float*>(smem_raw);
-  float* scr = buf + 2 * NQ * SP;
+  float* scr = buf + NBP * NHP * SP;
   const ZArgs<float>& a = pa_.z;
   if (halted(a.ss)) return;
   const int nzo = a.L.nz + 2 * NG;
@@ -548,12 +587,13 @@ void launch_adj_gather_zm(const Layout& L, const Phys<R>& ph, const R* coef, R* 
   const int nitems = 2 * tiles * a.nch;
   if constexpr (sizeof(R) == 4) {
     static int pctas = 0;
+    constexpr size_t psmem = gzm::zp::smem_pair();
     if (!pctas) {
-      cudaFuncSetAttribute(gzm::zp::gather_pair_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      cudaFuncSetAttribute(gzm::zp::gather_pair_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psmem);
       int dev = 0, sms = 0, per = 0;
       cudaGetDevice(&dev);
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, gzm::zp::gather_pair_kernel, gzm::zp::NTP, smem);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, gzm::zp::gather_pair_kernel, gzm::zp::NTP, psmem);
       pctas = sms * (per > 0 ? per : 1);
     }
     gzm::zp::PArgs pa;
@@ -573,7 +613,7 @@ void launch_adj_gather_zm(const Layout& L, const Phys<R>& ph, const R* coef, R* 
     pa.cx = coef(1.0 / (double)ph.idx);
     pa.cy = coef(1.0 / (double)ph.idy);
     const int pitems = 2 * tiles * a.nch;
-    gzm::zp::gather_pair_kernel<<<pitems < pctas ? pitems : pctas, gzm::zp::NTP, smem, st>>>(pa);
+    gzm::zp::gather_pair_kernel<<<pitems < pctas ? pitems : pctas, gzm::zp::NTP, psmem, st>>>(pa);
     return;
   }
   gzm::gather_zm_kernel<R><<<nitems < ctas ? nitems : ctas, gzm::NT, smem, st>>>(a);

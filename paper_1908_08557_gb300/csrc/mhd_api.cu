@@ -85,6 +85,7 @@ struct mhd_ctx {
   long long host_steps;
   long long nlaunch;                  // kernels launched since create
   bool prof;                          // bracket kernel classes with events
+  bool serial;                        // profiling with every kernel on the handle's stream, one after another
   int dbg_skip_plane;                 // time-out test hook for the next forward FP32 launch (INT_MIN: off)
   int dbg_wait_limit;
   struct Ev { cudaEvent_t a, b; int cls; int nk; };
@@ -499,7 +500,7 @@ static void ghost_fill(mhd_ctx* h, R* f) {
   }
   if (h->p.bc_z == 0) {
     ClassTimer ct(h, MHD_KC_PFE, 3);
-    launch_pfe<R>(h->fp, h->L, f, h->ss, h->st, &h->ps);
+    launch_pfe<R>(h->fp, h->L, f, h->ss, h->st, h->serial ? nullptr : &h->ps);
   }
 }
 
@@ -592,7 +593,7 @@ static void run_step(mhd_ctx* h, bool stats) {
     R* fin = (R*)h->f[h->cur];
     R* fout = (R*)h->f[1 - h->cur];
     const bool adaptive = !(h->p.dt_fixed > 0.0);
-    if (sub == 0 && adaptive && h->side && h->L.nz > 2 * NG) {
+    if (sub == 0 && adaptive && h->side && !h->serial && h->L.nz > 2 * NG) {
       // The FFT of the potential-field ghosts (FP64-pipe bound) runs on the
       // side stream while the ghost rules and the CFL reduction over the
       // inner layers (whose stencils read no ghost plane) run here; the
@@ -1495,6 +1496,7 @@ extern "C" int mhd_profile(mhd_handle h, int enable) {
   if (!h->evs) h->evs = new std::vector<mhd_ctx::Ev>();
   if (enable && !h->prof) drop_events(h);
   h->prof = enable != 0;
+  h->serial = enable == 2;
   return MHD_OK;
 }
 
