@@ -260,8 +260,19 @@ def adjoint_ratios(case, dev, ws):
         rst.append(_cuda_ms(sim.stream, lambda: sim.restore(ck, t)))
         adj.append(_cuda_ms(sim.stream, sim.adjoint_step))
     adj = sum(adj) / len(adj)
+    # the same reverse step from a tape of the step's substep states (kept by
+    # the forward step when memory allows): no forward recomputation
+    tape = sim.new_tape()
+    sim.restore(ck, t)
+    fwd_taped = _cuda_ms(sim.stream, lambda: sim.step_taped(tape))
+    sim.adjoint_step_taped(tape)  # warm-up
+    adj_taped = sum(_cuda_ms(sim.stream, lambda: sim.adjoint_step_taped(tape)) for _ in range(3)) / 3
     out["bench_workload"] = {"forward_ms_per_step": fwd, "adjoint_ms_per_step": adj,
-                             "restore_ms": sum(rst) / len(rst), "ratio": adj / fwd}
+                             "restore_ms": sum(rst) / len(rst), "ratio": adj / fwd,
+                             "taped": {"forward_taped_ms_per_step": fwd_taped, "adjoint_ms_per_step": adj_taped,
+                                       "ratio": adj_taped / fwd,
+                                       "tape_gb": sim.tape_bytes() / 1e9}}
+    del tape
     sim.close()
     del sim, ck
     torch.cuda.empty_cache()
@@ -274,11 +285,12 @@ def adjoint_ratios(case, dev, ws):
                    torch.tensor(c4.v0, dtype=torch.float32, device=dev),
                    torch.tensor(c4.v1, dtype=torch.float32, device=dev), c4.t0, c4.t1)
     # checkpoint slots from a state-history budget of 120 GB (the budget of
-    # the 512 x 512 x 256 checkpointed workload): at 64^3 every step fits, so
-    # the reverse sweep recomputes nothing
+    # the 512 x 512 x 256 checkpointed workload): at 64^3 the whole history
+    # fits as tapes (three substep states per step), so the reverse sweep
+    # recomputes no forward substep at all
     budget = 120 * 2**30
     n = c4.nsteps
-    slots = int(max(1, min(n - 1, budget // sim.checkpoint_bytes() - 1)))
+    slots = int(max(1, budget // sim.checkpoint_bytes() - 1))
     sim.set_time(0.0)
     ck0 = sim.new_checkpoint()
     t0 = sim.save(ck0)
@@ -292,6 +304,7 @@ def adjoint_ratios(case, dev, ws):
     out["bipoles8_64x64x64"] = {"steps": n, "slots": slots, "budget_gb": budget / 2**30, "forward_ms": fwd,
                                  "forward_with_checkpoints_ms": fwd_ck,
                                  "reverse_ms": rev_ms, "ratio": rev_ms / fwd,
+                                 "taped": bool(rv.tapes),
                                  "recompute_fraction": rv.recomputed_steps / n}
     sim.close()
     del sim

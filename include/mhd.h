@@ -325,6 +325,26 @@ int mhd_adjoint_init(mhd_handle h, const void* lam, int mem);
  * f_n again (time undefined until the next mhd_restore). */
 int mhd_adjoint_step(mhd_handle h);
 
+/* Tapes: when device memory allows, a step's three substep input states are
+ * kept instead of recomputed, so its reverse step reads them back (the
+ * recomputation of forward substeps is then needed only when the state
+ * history does not fit).  mhd_tape_bytes: bytes of one step's tape, three
+ * state sets (3 x mhd_checkpoint_bytes) and 256 bytes for the step's start
+ * time.
+ * mhd_step_taped: one full RK step from the current state, exactly as
+ * mhd_step(h, 1) computes it, that also leaves in `tape` (caller-owned
+ * device memory of mhd_tape_bytes bytes, 256-byte aligned) the ghost-filled
+ * state each of its three substeps read and the start time.  Asynchronous.
+ * mhd_adjoint_step_taped: the reverse step of the step recorded in `tape`,
+ * as mhd_adjoint_step computes it after restoring that step's first state,
+ * without the forward recomputation; the handle's own state is not touched.
+ * Asynchronous.  Both need the default FP32 kernels or MHD_RK_VARIANT=simple
+ * (MHD_ERR_UNSUPPORTED otherwise); the adjoint one needs params.adjoint and
+ * dt_fixed > 0 like mhd_adjoint_step. */
+size_t mhd_tape_bytes(mhd_handle h);
+int mhd_step_taped(mhd_handle h, void* tape);
+int mhd_adjoint_step_taped(mhd_handle h, const void* tape);
+
 /* Read the results of a reverse sweep: lam ([8][nz][ny][nx]) the adjoint of
  * the state at the sweep's current step (the velocity ghost adjoints folded
  * onto the photospheric layer, matching how mhd_create initialises them),

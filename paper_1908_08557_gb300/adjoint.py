@@ -83,14 +83,22 @@ def optimal_splits(n: int, slots: int):
 
 
 class Revolver:
-    """Forward sweep with checkpoints and the reverse sweep over them."""
+    """Forward sweep with checkpoints and the reverse sweep over them.
+
+    `slots` checkpoints of the state fit the memory budget (besides the
+    initial one).  When the whole history fits as tapes -- three substep
+    states per step, i.e. 3 n checkpoints for n steps -- the forward sweep
+    keeps every step's tape and the reverse sweep reads them back: no forward
+    substep is recomputed.  Otherwise the checkpoints are placed by the
+    split program and the reverse sweep recomputes from them."""
 
     def __init__(self, sim, slots: int):
         if slots < 0:
             raise ValueError("slots >= 0")
         self.sim = sim
         self.slots = slots
-        self.pool: List[torch.Tensor] = [sim.new_checkpoint() for _ in range(slots + 1)]
+        self.pool: List[torch.Tensor] = []
+        self.tapes: List[torch.Tensor] = []
         self.free = list(range(1, slots + 1))
         self.forward_steps = 0      # steps taken in the forward sweep
         self.recomputed_steps = 0   # steps recomputed during the reverse sweep
@@ -113,11 +121,24 @@ class Revolver:
             i0, s = m, s - 1
         return out
 
+    def taped(self, nsteps: int) -> bool:
+        """The whole history of nsteps fits as tapes."""
+        return nsteps >= 1 and 3 * nsteps <= self.slots + 1
+
     def forward(self, nsteps: int):
-        """From the current state (time t0), take nsteps, saving the
-        checkpoints the reverse sweep starts from."""
+        """From the current state (time t0), take nsteps, saving the tapes
+        or the checkpoints the reverse sweep starts from."""
         sim = self.sim
         self.n = nsteps
+        if self.taped(nsteps):
+            self.tapes = [sim.new_tape() for _ in range(nsteps)]
+            for tp in self.tapes:
+                sim.step_taped(tp)
+            self.forward_steps += nsteps
+            return
+        self.tapes = []
+        if not self.pool:
+            self.pool = [sim.new_checkpoint() for _ in range(self.slots + 1)]
         self.mT = self.mR = None
         if nsteps > 1 and nsteps * min(self.slots, nsteps - 1) <= DP_MAX_WORK:
             _, _, self.mT, self.mR = optimal_splits(nsteps, self.slots)
@@ -135,6 +156,11 @@ class Revolver:
     def reverse(self):
         """Reverse sweep over the forward run; the adjoint must have been
         seeded with mhd_adjoint_init."""
+        if self.tapes:
+            for tp in reversed(self.tapes):
+                self.sim.adjoint_step_taped(tp)
+                self.adjoint_steps += 1
+            return
         self._rev(0, self.n, (0, self.t_start), self.slots)
 
     def _rev(self, i0: int, i1: int, ck, s: int):

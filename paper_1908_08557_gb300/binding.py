@@ -41,7 +41,8 @@ EXPORTED = ("mhd_workspace_bytes", "mhd_create", "mhd_set_driver", "mhd_step",
             "mhd_bz_plane_adjoint", "mhd_gran_workspace_bytes", "mhd_gran_create", "mhd_gran_update",
             "mhd_gran_velocity", "mhd_gran_read_granules", "mhd_gran_read_field", "mhd_gran_launch_count",
             "mhd_gran_last_error", "mhd_gran_destroy", "mhd_set_a_background",
-            "mhd_debug_skip_copy", "mhd_read_plane", "mhd_fma_peak")
+            "mhd_debug_skip_copy", "mhd_read_plane", "mhd_fma_peak", "mhd_tape_bytes", "mhd_step_taped",
+            "mhd_adjoint_step_taped")
 KERNEL_CLASSES = ("ghost", "pfe", "cfl", "stats", "rk")
 
 
@@ -114,6 +115,10 @@ def load(path: Optional[str] = None):
     lib.mhd_debug_skip_copy.argtypes = [vp, i, i]
     lib.mhd_read_plane.argtypes = [vp, i, i, vp, i]
     lib.mhd_fma_peak.argtypes = [i, vp, vp, ctypes.POINTER(ctypes.c_double)]
+    lib.mhd_tape_bytes.argtypes = [vp]
+    lib.mhd_tape_bytes.restype = sz
+    lib.mhd_step_taped.argtypes = [vp, vp]
+    lib.mhd_adjoint_step_taped.argtypes = [vp, vp]
     lib.mhd_step.argtypes = [vp, i]
     lib.mhd_read.argtypes = [vp, i, vp, i]
     lib.mhd_write.argtypes = [vp, vp, i]
@@ -160,7 +165,7 @@ def load(path: Optional[str] = None):
     lib.mhd_gran_destroy.argtypes = [vp]
     lib.mhd_gran_destroy.restype = None
     for name in EXPORTED:
-        if name not in ("mhd_workspace_bytes", "mhd_destroy", "mhd_last_error",
+        if name not in ("mhd_workspace_bytes", "mhd_destroy", "mhd_last_error", "mhd_tape_bytes",
                         "mhd_launch_count", "mhd_checkpoint_bytes", "mhd_gran_workspace_bytes",
                         "mhd_gran_launch_count", "mhd_gran_last_error", "mhd_gran_destroy"):
             getattr(lib, name).restype = ctypes.c_int
@@ -425,6 +430,21 @@ class Simulation:
 
     def restore(self, buf, t: float):
         self._check(self.lib.mhd_restore(self.h, ctypes.c_void_p(buf.data_ptr()), float(t)))
+
+    def tape_bytes(self) -> int:
+        return int(self.lib.mhd_tape_bytes(self.h))
+
+    def new_tape(self):
+        import torch
+        return torch.empty(self.tape_bytes(), dtype=torch.uint8, device=self.device)
+
+    def step_taped(self, tape):
+        """One step that keeps its substep states (and start time) in `tape`."""
+        self._check(self.lib.mhd_step_taped(self.h, ctypes.c_void_p(tape.data_ptr())))
+
+    def adjoint_step_taped(self, tape):
+        """The reverse step of the step recorded in `tape`."""
+        self._check(self.lib.mhd_adjoint_step_taped(self.h, ctypes.c_void_p(tape.data_ptr())))
 
     def adjoint_init(self, lam):
         ptr, mem, keep = self._in(lam, (NFIELD, self._p.nz, self._p.ny, self._p.nx))

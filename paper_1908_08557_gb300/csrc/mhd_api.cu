@@ -554,15 +554,17 @@ static Driver kernel_driver(const mhd_ctx* h) {
   return Driver{h->axt, h->ayt, h->v0, h->v1};
 }
 
+// tmin: the tensor map of fin when fin is not one of the handle's two state
+// sets (a tape of substep states)
 template <typename R>
-static void launch_rk_any(mhd_ctx* h, const R* fin, R* fout, int sub) {
+static void launch_rk_any(mhd_ctx* h, const R* fin, R* fout, int sub, const CUtensorMap* tmin = nullptr) {
   Phys<R> ph = make_phys<R>(&h->p);
   Driver drv = kernel_driver(h);
   if (sizeof(R) == 4 && h->pair) {
     const int which = (const void*)fin == h->f[0] ? 0 : 1;
     // on a non-uniform vertical grid the z stencils run in index space
     // (unit spacing) and the kernel applies the metric per layer
-    launch_rk_pair(&h->tm[which], &h->tmdf, h->L, *(const Phys<float>*)&ph, h->bgf, (float*)fout, (float*)h->df,
+    launch_rk_pair(tmin ? tmin : &h->tm[which], &h->tmdf, h->L, *(const Phys<float>*)&ph, h->bgf, (float*)fout, (float*)h->df,
                    (const float*)h->wtab, (const float*)h->wptab, drv, h->ss, sub, h->p.dx, h->p.dy,
                    h->p.z ? 1.0 : h->p.dz, h->st, h->dbg_skip_plane, h->dbg_wait_limit);
     h->dbg_skip_plane = INT_MIN;  // one launch only
@@ -1354,9 +1356,10 @@ extern "C" int mhd_adjoint_init(mhd_handle h, const void* lam, int mem) {
 }
 
 template <typename R>
+static void adjoint_reverse(mhd_ctx* h, R* const (&S)[3], const CUtensorMap* const (&tms)[3]);
+
+template <typename R>
 static void adjoint_step_impl(mhd_ctx* h) {
-  Phys<R> ph = make_phys<R>(&h->p);
-  const Background<R>& bg = bgr<R>(h);
   R* S[3] = {(R*)h->f[h->cur], (R*)h->f[1 - h->cur], (R*)h->s2};
   // forward recompute of the substep states (ghost-filled)
   ghost_fill<R>(h, S[0]);
@@ -1367,6 +1370,16 @@ static void adjoint_step_impl(mhd_ctx* h) {
   launch_rk_any<R>(h, S[1], S[2], 1);
   ghost_fill<R>(h, S[2]);
   h->nlaunch += 3;  // cfl finalize and the two RK substeps (ghost_fill counts its own)
+  const CUtensorMap* tms[3] = {&h->tm[h->cur], &h->tm[1 - h->cur], &h->tm[2]};
+  adjoint_reverse<R>(h, S, tms);
+}
+
+// The reverse substeps of one step from its three ghost-filled substep
+// states S (and, for the FP32 z-march point kernel, their tensor maps).
+template <typename R>
+static void adjoint_reverse(mhd_ctx* h, R* const (&S)[3], const CUtensorMap* const (&tms)[3]) {
+  Phys<R> ph = make_phys<R>(&h->p);
+  const Background<R>& bg = bgr<R>(h);
   // reverse substeps
   FFTPlan fpa = h->fp;
   fpa.P = h->fp.Q;   // 9 packed ghost-adjoint planes
@@ -1383,15 +1396,14 @@ static void adjoint_step_impl(mhd_ctx* h) {
   // next step: alpha_0 = 0 makes the accumulator's own adjoint vanish at a
   // step boundary, so the last substep leaves D = beta_2 F (and
   // mhd_adjoint_init starts from D = beta_2 lam).
-  const int tmi[3] = {h->cur, 1 - h->cur, 2};
   for (int s = 2; s >= 0; --s) {
     const double alpha = rk_alpha(s), beta = rk_beta(s > 0 ? s - 1 : 2);
     if (sizeof(R) == 4 && h->adj_pair)
-      launch_adj_point_pair(&h->tm[tmi[s]], &h->tmdbar, h->L, *(const Phys<float>*)&ph, h->bgf, (const float*)h->dbar,
+      launch_adj_point_pair(tms[s], &h->tmdbar, h->L, *(const Phys<float>*)&ph, h->bgf, (const float*)h->dbar,
                             (float*)h->coef, h->thbar, (const float*)h->wtab, (const float*)h->wptab, h->ss, s,
                             h->p.dx, h->p.dy, h->p.dz, h->st);
     else if (sizeof(R) == 4 && h->tiled && h->adj_tiled)
-      launch_adj_point_tiled(&h->tm[tmi[s]], h->L, *(const Phys<float>*)&ph, h->bgf, (const float*)h->dbar,
+      launch_adj_point_tiled(tms[s], h->L, *(const Phys<float>*)&ph, h->bgf, (const float*)h->dbar,
                              (float*)h->coef, h->thbar, (const float*)h->wtab, (const float*)h->wptab, h->ss, s,
                              h->p.dx, h->p.dy, h->p.dz, h->st);
     else
@@ -1418,6 +1430,114 @@ extern "C" int mhd_adjoint_step(mhd_handle h) {
   if (rc) return rc;
   if (h->esz == 8) adjoint_step_impl<double>(h); else adjoint_step_impl<float>(h);
   return cuda_check(h, cudaSuccess, "adjoint step");
+}
+
+// ---- tapes: a step's three substep states kept for its adjoint ------------------
+// layout: the three state sets, then 256 bytes holding the step's start time
+extern "C" size_t mhd_tape_bytes(mhd_handle h) { return h ? 3 * mhd_checkpoint_bytes(h) + 256 : 0; }
+
+static int tape_supported(mhd_ctx* h, const void* tape) {
+  if (!tape) return fail(h, MHD_ERR_ARG, "tape is NULL");
+  if (((uintptr_t)tape & 255u) != 0) return fail(h, MHD_ERR_ARG, "tape must be 256-byte aligned");
+  if (h->esz == 4 && !(h->pair || !h->tiled))
+    return fail(h, MHD_ERR_UNSUPPORTED, "tapes need the default FP32 kernel or MHD_RK_VARIANT=simple");
+  if (h->esz == 4 && h->p.adjoint && h->tiled && h->adj_tiled && !h->adj_pair)
+    return fail(h, MHD_ERR_UNSUPPORTED, "tapes need the default FP32 adjoint kernels");
+  return MHD_OK;
+}
+
+static int tape_maps(mhd_ctx* h, const void* tape, CUtensorMap* maps) {
+  if (h->esz != 4 || !h->tiled) return MHD_OK;  // the one-thread-per-cell kernels take plain pointers
+  const size_t set = mhd_checkpoint_bytes(h);
+  for (int s = 0; s < 3; ++s)
+    if (make_state_tensor_map(&maps[s], h->L, (char*)tape + s * set) != 0)
+      return fail(h, MHD_ERR_CUDA, "cuTensorMapEncodeTiled failed for tape state %d", s);
+  return MHD_OK;
+}
+
+template <typename R>
+static void run_step_taped(mhd_ctx* h, char* tape, const CUtensorMap* maps, bool stats) {
+  const size_t set = mhd_checkpoint_bytes(h);
+  Phys<R> ph = make_phys<R>(&h->p);
+  R* S0 = (R*)h->f[h->cur];
+  R* T[3] = {(R*)tape, (R*)(tape + set), (R*)(tape + 2 * set)};
+  const bool adaptive = !(h->p.dt_fixed > 0.0);
+  ghost_fill<R>(h, S0);
+  if (stats) run_stats<R>(h, S0);
+  {
+    ClassTimer ct(h, MHD_KC_CFL, adaptive ? 2 : 1);
+    int nb = 0;
+    if (adaptive)
+      nb = launch_cfl_partial<R>(h->L, ph, bgr<R>(h), S0, (const R*)h->wtab, h->cfl, h->ss, CflPlanes::all, true,
+                                 h->st);
+    launch_cfl_finalize(h->cfl, nb, h->ss, h->p.c_adv, h->p.c_diff, h->p.dt_fixed, inv2sum(&h->p), h->t0, h->t1,
+                        h->p.t_ramp, 0, h->st);
+  }
+  // the ghost-filled substep inputs go to the tape: S0 by a copy, S1 and S2
+  // as the RK kernel's outputs (filled in place there)
+  cudaMemcpyAsync(T[0], S0, set, cudaMemcpyDeviceToDevice, h->st);
+  {
+    ClassTimer ct(h, MHD_KC_RK, 1);
+    launch_rk_any<R>(h, S0, T[1], 0);
+  }
+  ghost_fill<R>(h, T[1]);
+  {
+    ClassTimer ct(h, MHD_KC_RK, 1);
+    launch_rk_any<R>(h, T[1], T[2], 1, maps ? &maps[1] : nullptr);
+  }
+  ghost_fill<R>(h, T[2]);
+  {
+    ClassTimer ct(h, MHD_KC_RK, 1);
+    launch_rk_any<R>(h, T[2], (R*)h->f[1 - h->cur], 2, maps ? &maps[2] : nullptr);
+  }
+  h->cur = 1 - h->cur;
+}
+
+extern "C" int mhd_step_taped(mhd_handle h, void* tape) {
+  if (!h) return fail(nullptr, MHD_ERR_ARG, "NULL handle");
+  int rc = tape_supported(h, tape);
+  if (rc) return rc;
+  alignas(64) CUtensorMap maps[3];
+  rc = tape_maps(h, tape, maps);
+  if (rc) return rc;
+  const bool use_maps = h->esz == 4 && h->tiled;
+  // the start time, kept with the states
+  rc = cuda_check(h, cudaMemcpyAsync((char*)tape + 3 * mhd_checkpoint_bytes(h), &h->ss->t, sizeof(double),
+                                     cudaMemcpyDeviceToDevice, h->st), "tape t");
+  if (rc) return rc;
+  const bool stats = h->p.stats_every > 0 && (h->host_steps % h->p.stats_every) == 0;
+  if (h->esz == 8) run_step_taped<double>(h, (char*)tape, nullptr, stats);
+  else run_step_taped<float>(h, (char*)tape, use_maps ? maps : nullptr, stats);
+  h->host_steps++;
+  return cuda_check(h, cudaSuccess, "taped step");
+}
+
+extern "C" int mhd_adjoint_step_taped(mhd_handle h, const void* tape) {
+  if (!h) return fail(nullptr, MHD_ERR_ARG, "NULL handle");
+  int rc = adjoint_ready(h);
+  if (!rc) rc = tape_supported(h, tape);
+  if (rc) return rc;
+  alignas(64) CUtensorMap maps[3];
+  rc = tape_maps(h, tape, maps);
+  if (rc) return rc;
+  rc = cuda_check(h, cudaMemcpyAsync(&h->ss->t, (const char*)tape + 3 * mhd_checkpoint_bytes(h), sizeof(double),
+                                     cudaMemcpyDeviceToDevice, h->st), "tape t");
+  if (rc) return rc;
+  // the substep times and driver weights of the recorded step
+  launch_cfl_finalize(h->cfl, 0, h->ss, h->p.c_adv, h->p.c_diff, h->p.dt_fixed, inv2sum(&h->p), h->t0, h->t1,
+                      h->p.t_ramp, 0, h->st);
+  h->nlaunch += 1;
+  const size_t set = mhd_checkpoint_bytes(h);
+  char* tp = (char*)tape;
+  const CUtensorMap* tms[3] = {&maps[0], &maps[1], &maps[2]};
+  if (h->esz == 8) {
+    double* const S[3] = {(double*)tp, (double*)(tp + set), (double*)(tp + 2 * set)};
+    adjoint_reverse<double>(h, S, tms);
+  } else {
+    float* const S[3] = {(float*)tp, (float*)(tp + set), (float*)(tp + 2 * set)};
+    adjoint_reverse<float>(h, S, tms);
+  }
+  return cuda_check(h, cudaSuccess, "taped adjoint step");
 }
 
 extern "C" int mhd_adjoint_read(mhd_handle h, void* lam, void* grad_bz, void* grad_v0, void* grad_v1, int mem) {

@@ -47,6 +47,17 @@ class StepCounter:
     def adjoint_step(self):
         self.adjoint_at.append(self.k)
 
+    # tapes: the substep states of one step, kept for its reverse step
+    def new_tape(self):
+        return {}
+
+    def step_taped(self, tape):
+        tape["k"] = self.k
+        self.k += 1
+
+    def adjoint_step_taped(self, tape):
+        self.adjoint_at.append(tape["k"])
+
 
 def _sweep(n, slots):
     sim = StepCounter()
@@ -64,6 +75,24 @@ def _sweep(n, slots):
 @pytest.mark.parametrize("slots", [0, 1, 2, 3, 5, 10, 99])
 def test_reverse_order_and_slots(n, slots):
     _sweep(n, slots)
+
+
+@pytest.mark.parametrize("n", [1, 2, 7, 33])
+def test_taped_history_when_it_fits(n):
+    """With memory for three checkpoints per step (a tape of the three
+    substep states), the forward sweep keeps every step's tape and the
+    reverse sweep reads them back in reverse order: nothing is recomputed
+    and no checkpoint slot is used; one slot less and the checkpoints take
+    over."""
+    sim = StepCounter()
+    rv = Revolver(sim, 3 * n - 1)
+    assert rv.taped(n)
+    rv.forward(n)
+    assert sim.k == n and len(rv.tapes) == n and not rv.pool
+    rv.reverse()
+    assert sim.adjoint_at == list(range(n - 1, -1, -1))
+    assert rv.recomputed_steps == 0 and rv.adjoint_steps == n
+    assert not Revolver(StepCounter(), 3 * n - 2).taped(n)
 
 
 @pytest.mark.parametrize("n", [2, 10, 57, 100])

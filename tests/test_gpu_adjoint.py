@@ -186,16 +186,59 @@ def test_misfit_gradient_finite_differences(prec, tol, eps, k):
         assert abs(fd - ad) <= tol * abs(ad), (fd, ad)
 
 
-def test_checkpoint_budget_does_not_change_the_gradient():
-    """Binomial checkpointing recomputes the same forward states: gradients
-    with 1 slot and with one slot per step are bitwise identical."""
+@pytest.mark.parametrize("prec", [64, 32])
+def test_checkpoint_budget_does_not_change_the_gradient(prec):
+    """Binomial checkpointing recomputes the same forward states, and a tape
+    keeps exactly the states the recomputation would produce: gradients with
+    1 slot, one slot per step, and the whole history taped (27 slots for 9
+    steps: three substep states per step, nothing recomputed) are bitwise
+    identical."""
     case = _case(16, 16, 12, seed=6)
     target = np.zeros((16, 16))
-    a = _loss_and_grads(case, 64, 9, 6, target, slots=1)
-    b = _loss_and_grads(case, 64, 9, 6, target, slots=9)
-    assert a[0] == b[0]
-    for x, y in zip(a[1:], b[1:]):
-        assert np.array_equal(x, y)
+    a = _loss_and_grads(case, prec, 9, 6, target, slots=1)
+    b = _loss_and_grads(case, prec, 9, 6, target, slots=9)
+    c = _loss_and_grads(case, prec, 9, 6, target, slots=27)
+    assert a[0] == b[0] == c[0]
+    for x, y, z in zip(a[1:], b[1:], c[1:]):
+        assert np.array_equal(x, y) and np.array_equal(x, z)
+
+
+@pytest.mark.parametrize("prec", [64, 32])
+def test_taped_steps_equal_plain_steps(prec):
+    """mhd_step_taped advances the state exactly as mhd_step; its tape holds
+    the ghost-filled first state of the step (the state read back after a
+    ghost fill); the taped reverse step equals restore + mhd_adjoint_step."""
+    case = _case(32, 16, 12, seed=14)
+    a, b = _sim(case, prec), _sim(case, prec)
+    for sim in (a, b):
+        sim.set_driver(_T(case.bz, prec), _T(case.v0, prec), _T(case.v1, prec), case.t0, case.t1)
+        sim.set_time(0.0)
+    tapes = [b.new_tape() for _ in range(3)]
+    a.step(3)
+    for tp in tapes:
+        b.step_taped(tp)
+    assert torch.equal(a.read(), b.read())
+    assert a.time() == b.time()
+    rng = np.random.default_rng(15)
+    lam = _T(rng.standard_normal((8, 12, 16, 32)), prec)
+    # reverse of the last step: recompute path from a checkpoint of its
+    # first state, against the taped path
+    a.set_time(0.0)
+    a.write(_T(case.state, prec))
+    a.step(2)
+    ck = a.new_checkpoint()
+    t = a.save(ck)
+    a.adjoint_init(lam)
+    a.restore(ck, t)
+    a.adjoint_step()
+    ga = a.adjoint_read()
+    b.adjoint_init(lam)
+    b.adjoint_step_taped(tapes[2])
+    gb = b.adjoint_read()
+    for k in ("lam", "bz", "v0", "v1"):
+        assert torch.equal(ga[k], gb[k]), k
+    a.close()
+    b.close()
 
 
 def test_bruteforce_oracle_gradient_8cube():
