@@ -34,6 +34,10 @@ RUNS = 5                  # timed runs of K steps; the median is reported
 # DFMA, 1 per DADD / DMUL), from the ncu instruction counts summarised in
 # profiles/rk_simple_fp64_flops_bipoles20_128x128x128.md
 FP64_FLOPS_PER_CELL_SUBSTEP = 1059.4
+# FP32 operations per cell and substep of rk_pair_kernel (f32x2 instructions
+# one operation per cell, FFMA two flops), from the ncu instruction counts in
+# profiles/rk_pair_fp32_flops_bipoles20_128x128x128.md
+FP32_FLOPS_PER_CELL_SUBSTEP = 1021.3
 RK_KERNEL = ("rk_pair_kernel (fused RHS + RK update, TMA z-march, two cells per thread in f32x2, "
              "z histories in TMEM)")
 
@@ -662,6 +666,18 @@ def run_native(args, ws, rank, local):
     achieved = alg_bytes_per_launch / (rk_ms / rk_n / 1e3) / 1e9
     peaks = measured_peaks()
     peak = peaks["hbm_gbs"] if peaks and "hbm_gbs" in peaks else 6800.0
+    # the same launch against the FP32 FMA rate (the kernel's arithmetic
+    # intensity is close to the ridge of the two peaks)
+    roofline_alu = None
+    try:
+        from paper_1908_08557_gb300.binding import fma_peak
+        peak32 = fma_peak(32, str(dev)) / 1e12
+        ach32 = FP32_FLOPS_PER_CELL_SUBSTEP * cells / (rk_ms / rk_n / 1e3) / 1e12
+        roofline_alu = {"bound": "alu", "achieved": ach32, "peak": peak32, "unit": "TFLOP/s",
+                        "frac": ach32 / peak32, "flops_per_cell_substep": FP32_FLOPS_PER_CELL_SUBSTEP,
+                        "peak_source": "measured in this run (mhd_fma_peak, FP32 FMA chains)"}
+    except Exception as exc:  # reported, not fatal
+        roofline_alu = {"error": f"{type(exc).__name__}: {exc}"}
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": rk_traffic_bytes(), "kernel": RK_KERNEL,
                 "peak_source": "measured" if peaks else "fallback",
@@ -798,7 +814,7 @@ def run_native(args, ws, rank, local):
                            "newton_cooling": bool(args.cooling),
                            "l2": f"working set {state_gb:.2f} GB > 129 MB L2, no flush",
                            "parallelism": f"replicas x{ws}"},
-                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+                "roofline": roofline, "roofline_alu": roofline_alu, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                 "clocks": clocks, "fp64": fp64, "adjoint": adj, "production_1024x1024x256": prod}
         if scale is not None:
             line["adjoint_bipoles100_512x512x256"] = scale
