@@ -308,7 +308,10 @@ __device__ __forceinline__ void adjoint_centre(const Args& a, const float* Pk, c
 // separate instantiation, so that the default path carries none of it).
 // BG: A is stored about a background field; the background's B, J (every
 // cell) and lap A, div A (swamp layers) come from per-cell tables.
-template <bool ADJ, bool NC, bool BG>
+// ZG: a non-uniform vertical grid (the z stencils in index space, the metric
+// applied per layer); separate instantiations keep the uniform path as lean
+// as before.
+template <bool ADJ, bool NC, bool BG, bool ZG>
 __global__ void __launch_bounds__(NT, 2) rk_pair_kernel(const __grid_constant__ CUtensorMap tm,
                                                         const __grid_constant__ CUtensorMap tmd, const Args a) {
   extern __shared__ __align__(128) float smem[];
@@ -439,8 +442,11 @@ __global__ void __launch_bounds__(NT, 2) rk_pair_kernel(const __grid_constant__ 
       const float dlk = a.bg.dl[k], dtk = a.bg.dt[k], d2lk = a.bg.d2l[k], d2tk = a.bg.d2t[k];
       // non-uniform vertical grid: the z stencils ran in index space; the
       // metric of layer k (dxi/dz, and r21 with D_z^2 = m1^2 D_xi^2 + r21 D_z)
-      const bool zg = a.bg.zm1 != nullptr;
-      const float zm1k = zg ? a.bg.zm1[k] : 1.f, zr21k = zg ? a.bg.zr21[k] : 0.f;
+      float zm1k = 1.f, zr21k = 0.f;
+      if constexpr (ZG) {
+        zm1k = a.bg.zm1[k];
+        zr21k = a.bg.zr21[k];
+      }
       // background B, J of the pair (A stored about a background), issued
       // before the waits so that their latency overlaps them
       f2 gB[3], gJ[3];
@@ -492,7 +498,7 @@ __global__ void __launch_bounds__(NT, 2) rk_pair_kernel(const __grid_constant__ 
 #pragma unroll
         for (int q = 0; q < 6; ++q) mz[q] = fma2(cm, dif(sp.get(q), sm.get(q)), mz[q]);
       }
-      if (zg) {
+      if constexpr (ZG) {
 #pragma unroll
         for (int f = 0; f < NF; ++f) {
           d1z[f] = mul(F2(zm1k), d1z[f]);
@@ -811,16 +817,18 @@ bool rk_pair_supported(const Layout& L) { return L.nx % 2 == 0 && L.nx >= 8 && L
 static pair::Args pair_args(const Layout& L, const Phys<float>& ph, const Background<float>& bg, const float* wtab,
                             const float* wptab, StepState* ss, int sub, double dx, double dy, double dz) {
   if (!g_pair_ctas) {
-    cudaFuncSetAttribute(pair::rk_pair_kernel<false, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)pair::SMEM_BYTES);
-    cudaFuncSetAttribute(pair::rk_pair_kernel<false, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)pair::SMEM_BYTES);
-    cudaFuncSetAttribute(pair::rk_pair_kernel<false, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)pair::SMEM_BYTES);
-    cudaFuncSetAttribute(pair::rk_pair_kernel<false, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)pair::SMEM_BYTES);
-    cudaFuncSetAttribute(pair::rk_pair_kernel<true, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)pair::SMEM_BYTES);
+    auto attr = [](const void* fn) {
+      cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pair::SMEM_BYTES);
+    };
+    attr((const void*)pair::rk_pair_kernel<false, false, false, false>);
+    attr((const void*)pair::rk_pair_kernel<false, true, false, false>);
+    attr((const void*)pair::rk_pair_kernel<false, false, true, false>);
+    attr((const void*)pair::rk_pair_kernel<false, true, true, false>);
+    attr((const void*)pair::rk_pair_kernel<false, false, false, true>);
+    attr((const void*)pair::rk_pair_kernel<false, true, false, true>);
+    attr((const void*)pair::rk_pair_kernel<false, false, true, true>);
+    attr((const void*)pair::rk_pair_kernel<false, true, true, true>);
+    attr((const void*)pair::rk_pair_kernel<true, false, false, false>);
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -878,13 +886,19 @@ void launch_rk_pair(const CUtensorMap* tm, const CUtensorMap* tmd, const Layout&
   a.v1 = (const float*)drv.v1;
   const int nitems = a.ntx * a.nty * a.nch;
   const int grid = nitems < g_pair_ctas ? nitems : g_pair_ctas;
-  const bool bgA = bg.bB != nullptr;
-  if (ph.nc_k1 > 0) {
-    if (bgA) pair::rk_pair_kernel<false, true, true><<<grid, pair::NT, pair::SMEM_BYTES, st>>>(*tm, *tmd, a);
-    else pair::rk_pair_kernel<false, true, false><<<grid, pair::NT, pair::SMEM_BYTES, st>>>(*tm, *tmd, a);
-  } else {
-    if (bgA) pair::rk_pair_kernel<false, false, true><<<grid, pair::NT, pair::SMEM_BYTES, st>>>(*tm, *tmd, a);
-    else pair::rk_pair_kernel<false, false, false><<<grid, pair::NT, pair::SMEM_BYTES, st>>>(*tm, *tmd, a);
+  // the instantiation for the options in use (cooling, A about a
+  // background, non-uniform vertical grid)
+  const int opt = (ph.nc_k1 > 0 ? 1 : 0) | (bg.bB != nullptr ? 2 : 0) | (bg.zm1 != nullptr ? 4 : 0);
+  const dim3 g(grid), b(pair::NT);
+  switch (opt) {
+    case 0: pair::rk_pair_kernel<false, false, false, false><<<g, b, pair::SMEM_BYTES, st>>>(*tm, *tmd, a); break;
+    case 1: pair::rk_pair_kernel<false, true, false, false><<<g, b, pair::SMEM_BYTES, st>>>(*tm, *tmd, a); break;
+    case 2: pair::rk_pair_kernel<false, false, true, false><<<g, b, pair::SMEM_BYTES, st>>>(*tm, *tmd, a); break;
+    case 3: pair::rk_pair_kernel<false, true, true, false><<<g, b, pair::SMEM_BYTES, st>>>(*tm, *tmd, a); break;
+    case 4: pair::rk_pair_kernel<false, false, false, true><<<g, b, pair::SMEM_BYTES, st>>>(*tm, *tmd, a); break;
+    case 5: pair::rk_pair_kernel<false, true, false, true><<<g, b, pair::SMEM_BYTES, st>>>(*tm, *tmd, a); break;
+    case 6: pair::rk_pair_kernel<false, false, true, true><<<g, b, pair::SMEM_BYTES, st>>>(*tm, *tmd, a); break;
+    default: pair::rk_pair_kernel<false, true, true, true><<<g, b, pair::SMEM_BYTES, st>>>(*tm, *tmd, a); break;
   }
 }
 
@@ -898,7 +912,7 @@ void launch_adj_point_pair(const CUtensorMap* tm, const CUtensorMap* tmd, const 
   a.thbar = thbar;
   const int nitems = a.ntx * a.nty * a.nch;
   const int grid = nitems < g_pair_ctas ? nitems : g_pair_ctas;
-  pair::rk_pair_kernel<true, false, false><<<grid, pair::NT, pair::SMEM_BYTES, st>>>(*tm, *tmd, a);
+  pair::rk_pair_kernel<true, false, false, false><<<grid, pair::NT, pair::SMEM_BYTES, st>>>(*tm, *tmd, a);
 }
 
 }  // namespace mhd
