@@ -149,7 +149,7 @@ def _loss_and_grads(case, prec, nsteps, k, target, slots):
     b = BzPlane.apply(st, sim, k)
     loss = 0.5 * ((b - _T(target, prec)) ** 2).sum()
     loss.backward()
-    out = (float(loss), bz.grad.double().cpu().numpy(), v0.grad.double().cpu().numpy(), v1.grad.double().cpu().numpy())
+    out = (float(loss.detach()), bz.grad.double().cpu().numpy(), v0.grad.double().cpu().numpy(), v1.grad.double().cpu().numpy())
     sim.close()
     return out
 
