@@ -498,9 +498,23 @@ def production_line(dev, ws):
         achieved = WORDS_PER_CELL_STEP * cells * 4 / 3.0 / (rk_ms / rk_n / 1e3) / 1e9
         out[mode] = {"value": ws * cells * k / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / k, "steps": k,
                      "rk_achieved_gbs": achieved, "class_ms_per_step": {kk: v[0] / 3 for kk, v in prof.items()}}
+    # the FP64 path at the same size (FP64-ALU bound; two timed steps)
+    sim = Simulation(p, c.state, c.lnrho0, c.lnT0, precision=64, stats_every=10, device=str(dev))
+    sim.set_driver(torch.tensor(c.bz, dtype=torch.float64, device=dev),
+                   torch.tensor(c.v0, dtype=torch.float64, device=dev),
+                   torch.tensor(c.v1, dtype=torch.float64, device=dev), c.t0, c.t1)
+    sim.step(1)
+    torch.cuda.synchronize()
+    k64 = 2
+    ms64 = max_over_ranks(_cuda_ms(sim.stream, lambda: sim.step(k64)), ws)
+    sim.close()
+    del sim
+    torch.cuda.empty_cache()
     line = dict(out["a_background"])
     line["storage"] = "A about the FP64 initial field (a_background)"
     line["plain"] = out["plain"]
+    line["fp64"] = {"value": ws * cells * k64 / (ms64 / 1e3), "unit": UNIT, "ms_per_step": ms64 / k64,
+                    "steps": k64, "dtype": "f64"}
     return line
 
 

@@ -557,16 +557,15 @@ __global__ void __launch_bounds__(NTP, 2) gather_pair_kernel(PArgs pa_) {
 template <typename R>
 void launch_adj_gather_zm(const Layout& L, const Phys<R>& ph, const R* coef, R* dbar, R* gbar, R* fbar,
                           double alpha, double beta, int klo, int khi, StepState* ss, cudaStream_t st) {
-  static int ctas = 0;
   constexpr size_t smem = gzm::smem_bytes<R>();
-  if (!ctas) {
+  // persistent CTAs on the current device (shared-memory limit set there)
+  static PerDevice<int> per_dev;
+  const int ctas = per_dev.get([] {
     cudaFuncSetAttribute(gzm::gather_zm_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    int dev = 0, sms = 0, per = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int per = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, gzm::gather_zm_kernel<R>, gzm::NT, smem);
-    ctas = sms * (per > 0 ? per : 1);
-  }
+    return sm_count() * (per > 0 ? per : 1);
+  });
   gzm::ZArgs<R> a;
   a.L = L;
   a.ph = ph;
@@ -586,16 +585,14 @@ void launch_adj_gather_zm(const Layout& L, const Phys<R>& ph, const R* coef, R* 
   a.nch = (L.nz + 2 * NG + a.kchunk - 1) / a.kchunk;
   const int nitems = 2 * tiles * a.nch;
   if constexpr (sizeof(R) == 4) {
-    static int pctas = 0;
     constexpr size_t psmem = gzm::zp::smem_pair();
-    if (!pctas) {
+    static PerDevice<int> per_dev_pair;
+    const int pctas = per_dev_pair.get([] {
       cudaFuncSetAttribute(gzm::zp::gather_pair_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psmem);
-      int dev = 0, sms = 0, per = 0;
-      cudaGetDevice(&dev);
-      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+      int per = 0;
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, gzm::zp::gather_pair_kernel, gzm::zp::NTP, psmem);
-      pctas = sms * (per > 0 ? per : 1);
-    }
+      return sm_count() * (per > 0 ? per : 1);
+    });
     gzm::zp::PArgs pa;
     pa.z = a;
     a.kchunk = zm::zchunk(L.nz + 2 * NG, 2 * tiles, pctas);

@@ -19,9 +19,6 @@
 //                M_b = exp(+f_b |k| j dz)), inverse FFT along y
 //   3. rows_inv: inverse FFT along x, write real/imaginary parts into the
 //                ghost layers (with their periodic x,y images)
-#include <atomic>
-#include <mutex>
-
 #include "mhd_internal.h"
 
 namespace mhd {
@@ -390,25 +387,18 @@ __global__ void __launch_bounds__(256) cols_adj_kernel(FFTPlan fp, const StepSta
 }
 
 // Dynamic shared-memory limits of the FFT kernels, set once per device (the
-// attribute belongs to the device's context) under a lock: several host
-// threads may drive handles, and the allocation-free inversion, at once.
-static std::mutex g_fft_attr_mu;
-static std::atomic<unsigned long long> g_fft_attr_done{0};  // bit per device
-
+// attribute belongs to the device's context).
 static void set_smem_once() {
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) dev = 0;
-  const unsigned long long bit = 1ull << dev;
-  if (g_fft_attr_done.load(std::memory_order_acquire) & bit) return;
-  std::lock_guard<std::mutex> lock(g_fft_attr_mu);
-  if (g_fft_attr_done.load(std::memory_order_relaxed) & bit) return;
-  cudaFuncSetAttribute(rows_fwd_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * FFT_PTS * 16);
-  cudaFuncSetAttribute(rows_fwd_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * FFT_PTS * 16);
-  cudaFuncSetAttribute(rows_inv_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * FFT_PTS * 16);
-  cudaFuncSetAttribute(rows_inv_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * FFT_PTS * 16);
-  cudaFuncSetAttribute(cols_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 6 * FFT_PTS * 16);
-  cudaFuncSetAttribute(cols_adj_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 3 * FFT_PTS * 16);
-  g_fft_attr_done.fetch_or(bit, std::memory_order_release);
+  static PerDevice<bool> done;
+  done.get([] {
+    cudaFuncSetAttribute(rows_fwd_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * FFT_PTS * 16);
+    cudaFuncSetAttribute(rows_fwd_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * FFT_PTS * 16);
+    cudaFuncSetAttribute(rows_inv_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * FFT_PTS * 16);
+    cudaFuncSetAttribute(rows_inv_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * FFT_PTS * 16);
+    cudaFuncSetAttribute(cols_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 6 * FFT_PTS * 16);
+    cudaFuncSetAttribute(cols_adj_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 3 * FFT_PTS * 16);
+    return true;
+  });
 }
 
 // batch sizes: rows per block (nb) so a block holds ~1024 points, column
@@ -446,11 +436,7 @@ struct RowsCfg {
 };
 
 static RowsCfg rows_cfg(const FFTPlan& fp, int planes) {
-  // the SM count of the current device (a cached runtime query, cheap and
-  // thread-safe)
-  int nsm = 0, dev = 0;
-  cudaGetDevice(&dev);
-  if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm <= 0) nsm = 1;
+  const int nsm = sm_count();
   int nbmax = 1024 / fp.nx;
   if (nbmax < 1) nbmax = 1;
   if (nbmax > fp.ny) nbmax = fp.ny;

@@ -1,6 +1,8 @@
 // mhd_internal.h -- launchers shared between the translation units of libmhd.
 #pragma once
+#include <atomic>
 #include <climits>
+#include <mutex>
 
 #include <cuda.h>
 #include <cuda_runtime.h>
@@ -39,6 +41,40 @@ struct Driver {
 
 // set the message returned by mhd_last_error(NULL)
 void set_global_error(const char* fmt, ...);
+
+// A value that belongs to a device -- kernel attributes set there, a launch
+// geometry from its SM count and occupancy -- computed once per device, under
+// a lock: handles on several devices or host threads may launch at once.
+template <typename T>
+class PerDevice {
+ public:
+  template <typename F>
+  T get(F make) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMax) dev = 0;
+    if (ready_[dev].load(std::memory_order_acquire)) return val_[dev];
+    std::lock_guard<std::mutex> lock(mu_);
+    if (!ready_[dev].load(std::memory_order_relaxed)) {
+      val_[dev] = make();
+      ready_[dev].store(true, std::memory_order_release);
+    }
+    return val_[dev];
+  }
+
+ private:
+  static constexpr int kMax = 64;
+  std::mutex mu_;
+  std::atomic<bool> ready_[kMax]{};
+  T val_[kMax]{};
+};
+
+// SM count of the current device
+inline int sm_count() {
+  int dev = 0, n = 0;
+  cudaGetDevice(&dev);
+  if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 1;
+  return n;
+}
 
 constexpr int FFT_PTS = 2048;          // complex points per shared buffer
 constexpr int RED_BLOCKS_MAX = 4096;   // partial-reduction slots

@@ -810,13 +810,14 @@ __global__ void __launch_bounds__(NT, 2) rk_pair_kernel(const __grid_constant__ 
 
 }  // namespace pair
 
-static int g_pair_ctas = 0;
-
 bool rk_pair_supported(const Layout& L) { return L.nx % 2 == 0 && L.nx >= 8 && L.ny >= 6; }
 
-static pair::Args pair_args(const Layout& L, const Phys<float>& ph, const Background<float>& bg, const float* wtab,
-                            const float* wptab, StepState* ss, int sub, double dx, double dy, double dz) {
-  if (!g_pair_ctas) {
+// persistent CTAs of the pair kernels on the current device (two per SM: the
+// shared ring admits no third, and TMEM holds two), after setting their
+// shared-memory limit there
+static int pair_ctas() {
+  static PerDevice<int> ctas;
+  return ctas.get([] {
     auto attr = [](const void* fn) {
       cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pair::SMEM_BYTES);
     };
@@ -829,12 +830,13 @@ static pair::Args pair_args(const Layout& L, const Phys<float>& ph, const Backgr
     attr((const void*)pair::rk_pair_kernel<false, false, true, true>);
     attr((const void*)pair::rk_pair_kernel<false, true, true, true>);
     attr((const void*)pair::rk_pair_kernel<true, false, false, false>);
-    int dev = 0, sms = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    // two CTAs per SM: the shared ring admits no third (and TMEM holds two)
-    g_pair_ctas = 2 * sms;
-  }
+    return 2 * sm_count();
+  });
+}
+
+static pair::Args pair_args(const Layout& L, const Phys<float>& ph, const Background<float>& bg, const float* wtab,
+                            const float* wptab, StepState* ss, int sub, double dx, double dy, double dz) {
+  const int ctas = pair_ctas();
   pair::Args a{};
   a.wait_limit = zm::WAIT_LIMIT;
   a.skip_plane = INT_MIN;
@@ -864,7 +866,7 @@ static pair::Args pair_args(const Layout& L, const Phys<float>& ph, const Backgr
   a.cy = coef(dy);
   a.cz = coef(dz);
   const int tiles = a.ntx * a.nty;
-  a.kchunk = zm::zchunk(L.nz, tiles, g_pair_ctas);
+  a.kchunk = zm::zchunk(L.nz, tiles, ctas);
   a.nch = (L.nz + a.kchunk - 1) / a.kchunk;
   return a;
 }
@@ -885,7 +887,7 @@ void launch_rk_pair(const CUtensorMap* tm, const CUtensorMap* tmd, const Layout&
   a.v0 = (const float*)drv.v0;
   a.v1 = (const float*)drv.v1;
   const int nitems = a.ntx * a.nty * a.nch;
-  const int grid = nitems < g_pair_ctas ? nitems : g_pair_ctas;
+  const int grid = nitems < pair_ctas() ? nitems : pair_ctas();
   // the instantiation for the options in use (cooling, A about a
   // background, non-uniform vertical grid)
   const int opt = (ph.nc_k1 > 0 ? 1 : 0) | (bg.bB != nullptr ? 2 : 0) | (bg.zm1 != nullptr ? 4 : 0);
@@ -911,7 +913,7 @@ void launch_adj_point_pair(const CUtensorMap* tm, const CUtensorMap* tmd, const 
   a.coef = coef;
   a.thbar = thbar;
   const int nitems = a.ntx * a.nty * a.nch;
-  const int grid = nitems < g_pair_ctas ? nitems : g_pair_ctas;
+  const int grid = nitems < pair_ctas() ? nitems : pair_ctas();
   pair::rk_pair_kernel<true, false, false, false><<<grid, pair::NT, pair::SMEM_BYTES, st>>>(*tm, *tmd, a);
 }
 

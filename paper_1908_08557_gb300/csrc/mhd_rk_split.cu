@@ -470,8 +470,6 @@ __global__ void __launch_bounds__(TILE, 2) pass_r_kernel(const __grid_constant__
 
 }  // namespace split
 
-static int g_split_ctas[2] = {0, 0};  // persistent CTAs of pass A, pass R (per device of first use)
-
 size_t rk_split_smem_a() { return split::SMEM_A; }
 size_t rk_split_smem_r() { return split::SMEM_R; }
 
@@ -479,19 +477,21 @@ void launch_rk_split(const CUtensorMap* tm_a, const CUtensorMap* tm_r, const Lay
                      const Background<float>& bg, const float* fin, float* fout, float* df, float* bj, float* sw,
                      int ksw, const float* wtab, const float* wptab, const Driver& drv, StepState* ss, int sub,
                      double dx, double dy, double dz, cudaStream_t st) {
-  static bool attr = false;
-  if (!attr) {
+  // persistent CTAs of pass A and pass R on the current device (their
+  // shared-memory limits set there first)
+  struct Ctas { int a, r; };
+  static PerDevice<Ctas> per_dev;
+  const Ctas pc = per_dev.get([] {
     cudaFuncSetAttribute(split::pass_a_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)split::SMEM_A);
     cudaFuncSetAttribute(split::pass_r_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)split::SMEM_R);
-    int dev = 0, sms = 0, na = 0, nr = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int na = 0, nr = 0;
+    const int sms = sm_count();
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&na, split::pass_a_kernel, zm::TILE, split::SMEM_A);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nr, split::pass_r_kernel, zm::TILE, split::SMEM_R);
-    g_split_ctas[0] = sms * (na > 0 ? na : 1);
-    g_split_ctas[1] = sms * (nr > 0 ? nr : 1);
-    attr = true;
-  }
+    return Ctas{sms * (na > 0 ? na : 1), sms * (nr > 0 ? nr : 1)};
+  });
+  const int split_ctas[2] = {pc.a, pc.r};
+
   split::Args a{};
   a.L = L;
   a.ph = ph;
@@ -526,7 +526,7 @@ void launch_rk_split(const CUtensorMap* tm_a, const CUtensorMap* tm_r, const Lay
   const int tiles = a.ntx * a.nty;
   const dim3 blk(zm::TX, zm::TY);
   for (int pass = 0; pass < 2; ++pass) {
-    const int ctas = g_split_ctas[pass];
+    const int ctas = split_ctas[pass];
     a.kchunk = zm::zchunk(L.nz, tiles, ctas);
     a.nch = (L.nz + a.kchunk - 1) / a.kchunk;
     const int nitems = tiles * a.nch;

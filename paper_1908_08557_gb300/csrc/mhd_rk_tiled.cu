@@ -384,25 +384,26 @@ __global__ void __launch_bounds__(TILE, 1) rk_tiled_kernel(const __grid_constant
 
 using tiled::Args;
 
-static int g_sms = 0;
-
 bool rk_tiled_supported() { return true; }
 
 size_t rk_tiled_smem() { return tiled::SMEM_BYTES; }
 
-static Args tiled_args(const Layout& L, const Phys<float>& ph, const Background<float>& bg, const float* wtab,
-                       const float* wptab, StepState* ss, int sub, double dx, double dy, double dz) {
-  static bool attr = false;
-  if (!attr) {
+// persistent CTAs (one per SM) on the current device, after setting the
+// kernels' shared-memory limit there
+static int tiled_ctas() {
+  static PerDevice<int> ctas;
+  return ctas.get([] {
     cudaFuncSetAttribute(tiled::rk_tiled_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)tiled::SMEM_BYTES);
     cudaFuncSetAttribute(tiled::rk_tiled_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)tiled::SMEM_BYTES);
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev);
-    attr = true;
-  }
+    return sm_count();
+  });
+}
+
+static Args tiled_args(const Layout& L, const Phys<float>& ph, const Background<float>& bg, const float* wtab,
+                       const float* wptab, StepState* ss, int sub, double dx, double dy, double dz) {
+  const int sms = tiled_ctas();
   Args a{};
   a.L = L;
   a.ph = ph;
@@ -414,7 +415,7 @@ static Args tiled_args(const Layout& L, const Phys<float>& ph, const Background<
   a.ntx = (L.nx + tiled::TX - 1) / tiled::TX;
   a.nty = (L.ny + tiled::TY - 1) / tiled::TY;
   const int tiles = a.ntx * a.nty;
-  a.kchunk = zm::zchunk(L.nz, tiles, g_sms);
+  a.kchunk = zm::zchunk(L.nz, tiles, sms);
   a.nch = (L.nz + a.kchunk - 1) / a.kchunk;
   const double W1[4] = {0.0, 45.0 / 60.0, -9.0 / 60.0, 1.0 / 60.0};
   const double W2[4] = {-490.0 / 180.0, 270.0 / 180.0, -27.0 / 180.0, 2.0 / 180.0};
@@ -432,7 +433,8 @@ static Args tiled_args(const Layout& L, const Phys<float>& ph, const Background<
 
 static int tiled_grid(const Args& a) {
   const int nitems = a.ntx * a.nty * a.nch;
-  return nitems < g_sms ? nitems : g_sms;
+  const int sms = tiled_ctas();
+  return nitems < sms ? nitems : sms;
 }
 
 void launch_rk_tiled(const CUtensorMap* tm, const Layout& L, const Phys<float>& ph, const Background<float>& bg,
