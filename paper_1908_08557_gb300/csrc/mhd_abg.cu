@@ -67,9 +67,13 @@ __global__ void abg_zper_kernel(Layout L, double* __restrict__ a) {
 
 // Tables of the ghost-filled FP64 background at interior cells: B = curl A,
 // J = grad div A - lap A, and on layers k >= ksw lap A and div A; the
-// photospheric A_x, A_y in FP64 (for the nudging target difference).
+// photospheric A_x, A_y in FP64 (for the nudging target difference).  zm: on
+// a non-uniform vertical grid the FP64 metric per interior layer ([2][nz]:
+// dxi/dz, then r21 with D_z^2 f = (dxi/dz)^2 D_xi^2 f + r21 D_z f); null on
+// the uniform grid.
 template <typename R>
 __global__ void __launch_bounds__(256) abg_tables_kernel(Layout L, double idx, double idy, double idz,
+                                                         const double* __restrict__ zm,
                                                          const double* __restrict__ a, R* __restrict__ bB,
                                                          R* __restrict__ bJ, R* __restrict__ bL, int ksw,
                                                          double* __restrict__ a0) {
@@ -78,22 +82,24 @@ __global__ void __launch_bounds__(256) abg_tables_kernel(Layout L, double idx, d
   const int k = blockIdx.z;
   if (i >= L.nx || j >= L.ny) return;
   const long long st[3] = {1, L.sy(), L.sz()};
-  const double inv[3] = {idx, idy, idz};
-  const double inv2[3] = {idx * idx, idy * idy, idz * idz};
+  const double m1 = zm ? zm[k] : idz, r21 = zm ? zm[L.nz + k] : 0.0;
+  const double inv[3] = {idx, idy, m1};
+  const double inv2[3] = {idx * idx, idy * idy, m1 * m1};
   const double* p[3];
   for (int c = 0; c < 3; ++c) p[c] = a + L.at(c, k, j, i);
   double d[3][3];  // d[c][x] = d_x A_c
   for (int c = 0; c < 3; ++c)
     for (int x = 0; x < 3; ++x) d[c][x] = d1<double>(p[c], st[x], inv[x]);
+  // second derivatives, with the vertical metric's first-derivative term
+  auto dd = [&](int c, int x) { return d2<double>(p[c], st[x], inv2[x]) + (x == 2 ? r21 * d[c][2] : 0.0); };
   double lap[3], gd[3];
   for (int c = 0; c < 3; ++c) {
     lap[c] = 0.0;
-    for (int x = 0; x < 3; ++x) lap[c] += d2<double>(p[c], st[x], inv2[x]);
+    for (int x = 0; x < 3; ++x) lap[c] += dd(c, x);
   }
   for (int x = 0; x < 3; ++x) {
     gd[x] = 0.0;
-    for (int c = 0; c < 3; ++c)
-      gd[x] += c == x ? d2<double>(p[c], st[x], inv2[x]) : d11<double>(p[c], st[x], st[c], inv[x], inv[c]);
+    for (int c = 0; c < 3; ++c) gd[x] += c == x ? dd(c, x) : d11<double>(p[c], st[x], st[c], inv[x], inv[c]);
   }
   const long long n2 = (long long)L.nx * L.ny, n3 = n2 * L.nz;
   const long long q = (long long)k * n2 + (long long)j * L.nx + i;
@@ -150,10 +156,10 @@ void launch_abg_zper(const Layout& L, double* a, cudaStream_t st) {
 }
 
 template <typename R>
-void launch_abg_tables(const Layout& L, double dx, double dy, double dz, const double* a, R* bB, R* bJ, R* bL,
-                       int ksw, double* a0, R* abg, cudaStream_t st) {
+void launch_abg_tables(const Layout& L, double dx, double dy, double dz, const double* zm, const double* a, R* bB,
+                       R* bJ, R* bL, int ksw, double* a0, R* abg, cudaStream_t st) {
   dim3 blk(32, 8, 1), grd((L.nx + 31) / 32, (L.ny + 7) / 8, L.nz);
-  abg_tables_kernel<R><<<grd, blk, 0, st>>>(L, 1.0 / dx, 1.0 / dy, 1.0 / dz, a, bB, bJ, bL, ksw, a0);
+  abg_tables_kernel<R><<<grd, blk, 0, st>>>(L, 1.0 / dx, 1.0 / dy, 1.0 / dz, zm, a, bB, bJ, bL, ksw, a0);
   abg_round_kernel<R><<<1216, 256, 0, st>>>(a, abg, 3 * L.fs);
 }
 
@@ -169,7 +175,8 @@ void launch_widen(const R* in, double* out, long long n, cudaStream_t st) {
 
 #define INST(R)                                                                                               \
   template void launch_abg_pert<R>(const Layout&, const R*, R*, cudaStream_t);                               \
-  template void launch_abg_tables<R>(const Layout&, double, double, double, const double*, R*, R*, R*, int,  \
+  template void launch_abg_tables<R>(const Layout&, double, double, double, const double*, const double*, R*,  \
+                                     R*, R*, int,                                                             \
                                      double*, R*, cudaStream_t);                                             \
   template void launch_abg_target<R>(const double*, const double*, R*, long long, cudaStream_t);             \
   template void launch_widen<R>(const R*, double*, long long, cudaStream_t);

@@ -78,6 +78,7 @@ struct mhd_ctx {
   // z_k, cell extent, [4][nz] in the state precision
   double* zh;
   void* ztab;
+  double* zt64;        // [2][nz] FP64 dxi/dz and r21 (the background tables' stencils)
   FFTPlan fp;
   bool have_fft;
   bool driver_set;
@@ -220,7 +221,7 @@ struct Carve {
 struct Offsets {
   size_t f0, f1, df, lnrho0, wtab, wptab, bz, axt, ayt, v0, v1, red, ss, bg, bj, sw;
   size_t s2, fbar, dbar, gbar, coef, thbar;
-  size_t abB, abL, abgR, abg0, at64, atrel, ztab;
+  size_t abB, abL, abgR, abg0, at64, atrel, ztab, zt64;
   size_t twx, twy, et, eb, ktx, kty, P, Q;
   size_t total;
 };
@@ -259,6 +260,7 @@ static Offsets plan_offsets(const mhd_params* p) {
   o.ss = c.take(sizeof(StepState));
   o.bg = c.take((size_t)(6 * p->nz + 12) * es);
   o.ztab = c.take((size_t)4 * p->nz * es);
+  o.zt64 = c.take((size_t)2 * p->nz * 8);
   if (p->precision == 32 && !p->a_background) {
     o.bj = c.take((size_t)6 * n2 * p->nz * 4);
     o.sw = c.take((size_t)3 * n2 * (p->nz - swamp_first_layer(p)) * 4);
@@ -456,6 +458,7 @@ static int upload_background(mhd_ctx* h, const double* lnrho0, const double* lnT
   bg.zm1 = bg.zr21 = bg.zk = bg.zcell = nullptr;
   if (p->z) {
     std::vector<R> zt((size_t)4 * nz);
+    std::vector<double> z64((size_t)2 * nz);
     for (int k = 0; k < nz; ++k) {
       double z1, z2;
       zderiv(p, k, &z1, &z2);
@@ -463,9 +466,13 @@ static int upload_background(mhd_ctx* h, const double* lnrho0, const double* lnT
       zt[(size_t)nz + k] = (R)(-z2 / (z1 * z1));
       zt[(size_t)2 * nz + k] = (R)zpos(p, k);
       zt[(size_t)3 * nz + k] = (R)(0.5 * (zpos(p, k + 1) - zpos(p, k - 1)));
+      z64[k] = 1.0 / z1;
+      z64[(size_t)nz + k] = -z2 / (z1 * z1);
     }
     int rz = cuda_check(h, cudaMemcpy(h->ztab, zt.data(), zt.size() * sizeof(R), cudaMemcpyHostToDevice),
                         "upload vertical grid");
+    if (!rz) rz = cuda_check(h, cudaMemcpy(h->zt64, z64.data(), z64.size() * 8, cudaMemcpyHostToDevice),
+                             "upload vertical grid (FP64)");
     if (rz) return rz;
     bg.zm1 = (const R*)h->ztab;
     bg.zr21 = bg.zm1 + nz;
@@ -775,6 +782,7 @@ extern "C" int mhd_create(const mhd_params* p, void* workspace, size_t ws_bytes,
   h->ss = (StepState*)(h->ws + o.ss);
   h->bgtab = h->ws + o.bg;
   h->ztab = h->ws + o.ztab;
+  h->zt64 = (double*)(h->ws + o.zt64);
   h->bj = h->ws + o.bj;
   h->sw = h->ws + o.sw;
   h->ksw = swamp_first_layer(p);
@@ -970,7 +978,8 @@ static int background_target(mhd_ctx* h) {
 template <typename R>
 static void background_tables(mhd_ctx* h, const double* a64) {
   const Layout& L = h->L;
-  launch_abg_tables<R>(L, h->p.dx, h->p.dy, h->p.dz, a64, (R*)h->abB, (R*)h->abB + 3LL * L.nx * L.ny * L.nz,
+  launch_abg_tables<R>(L, h->p.dx, h->p.dy, h->p.dz, h->p.z ? h->zt64 : nullptr, a64, (R*)h->abB,
+                       (R*)h->abB + 3LL * L.nx * L.ny * L.nz,
                        (R*)h->abL, h->ksw, h->abg0, (R*)h->abgR, h->st);
 }
 

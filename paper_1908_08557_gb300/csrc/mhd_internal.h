@@ -187,8 +187,9 @@ template <typename R> void launch_atarget_adjoint(const FFTPlan& fp, const doubl
 void launch_abg_unpack64(const Layout& L, const double* in, double* a, cudaStream_t st);
 template <typename R> void launch_abg_pert(const Layout& L, const R* in, R* f, cudaStream_t st);
 void launch_abg_zper(const Layout& L, double* a, cudaStream_t st);
-template <typename R> void launch_abg_tables(const Layout& L, double dx, double dy, double dz, const double* a,
-                                             R* bB, R* bJ, R* bL, int ksw, double* a0, R* abg, cudaStream_t st);
+template <typename R> void launch_abg_tables(const Layout& L, double dx, double dy, double dz, const double* zm,
+                                             const double* a, R* bB, R* bJ, R* bL, int ksw, double* a0, R* abg,
+                                             cudaStream_t st);
 template <typename R> void launch_abg_target(const double* at, const double* a0, R* rel, long long n,
                                              cudaStream_t st);
 template <typename R> void launch_widen(const R* in, double* out, long long n, cudaStream_t st);

@@ -136,6 +136,60 @@ def test_zgrid_full_run(precision, variant, monkeypatch):
     assert abs(tg - t) <= (1e-12 if precision == 64 else 1e-5) * t
 
 
+@pytest.mark.parametrize("precision", [64, 32])
+def test_zgrid_with_a_background_rhs(precision):
+    """A stored about an FP64 background on the stretched grid: the
+    background's B, J, lap A and div A carry the same chain-rule metric as
+    the kernels' stencils.  Right-hand side of A0 + A' against the oracle on
+    the full A (FP64 1e-11, FP32 2e-4 of each field's scale)."""
+    case = _zcase(16, 16, 24, seed=53)
+    rng = np.random.default_rng(153)
+    a0 = case.state[0:3].copy()
+    pert = 0.01 * rng.standard_normal(a0.shape)
+    dt = torch.float64 if precision == 64 else torch.float32
+    from paper_1908_08557_gb300 import Simulation
+    sim = Simulation(case.params, torch.tensor(case.state, dtype=dt, device="cuda"), case.lnrho0, case.lnT0,
+                     precision=precision, a_background=a0)
+    sim.set_a_background(a0, torch.tensor(pert, dtype=dt, device="cuda"))
+    sim.set_driver(torch.tensor(case.bz, dtype=dt, device="cuda"), torch.tensor(case.v0, dtype=dt, device="cuda"),
+                   torch.tensor(case.v1, dtype=dt, device="cuda"), case.t0, case.t1)
+    sim.fill_ghosts()
+    t = 0.29
+    got = sim.eval_rhs(t).astype(np.float64)
+    r32 = (lambda a: a.astype(np.float32).astype(np.float64)) if precision == 32 else (lambda a: a)
+    st = r32(case.state.copy())
+    st[0:3] = a0 + r32(pert)
+    u = oracle.fill_ghosts(case.params, oracle.to_padded(st), case.lnrho0)
+    axt, ayt = oracle.a_target(case.params, r32(case.bz))
+    ref = oracle.rhs(case.params, u, axt, ayt, r32(case.v0), r32(case.v1), case.t0, case.t1, t)
+    tol = 1e-11 if precision == 64 else 2e-4
+    for f in range(8):
+        s = np.abs(ref[f]).max()
+        e = np.abs(got[f] - ref[f]).max()
+        assert e <= tol * max(s, 1e-30), (f, e, s)
+
+
+@pytest.mark.parametrize("precision", [64, 32])
+def test_zgrid_with_a_background_full_run(precision):
+    """50 driven steps on the stretched grid with A stored about its initial
+    potential field: FP64 within 1e-11, FP32 within 1e-4 relative L2 per
+    field of the oracle."""
+    from paper_1908_08557_gb300 import Simulation
+    case = _zcase(32, 16, 24, seed=47, perturb=False)
+    dt = torch.float64 if precision == 64 else torch.float32
+    sim = Simulation(case.params, torch.tensor(case.state, dtype=dt, device="cuda"), case.lnrho0, case.lnT0,
+                     precision=precision, a_background=case.state[0:3].copy())
+    sim.set_driver(torch.tensor(case.bz, dtype=dt, device="cuda"), torch.tensor(case.v0, dtype=dt, device="cuda"),
+                   torch.tensor(case.v1, dtype=dt, device="cuda"), case.t0, case.t1)
+    sim.step(50)
+    got = sim.read().cpu().numpy().astype(np.float64)
+    u, t, dts = oracle.run_case(case, nsteps=50)
+    ref = oracle.interior(u)
+    errs = [_rel_l2(got[f], ref[f]) for f in range(8)]
+    print(precision, "zgrid + background rel L2 per field:", ["%.2e" % e for e in errs])
+    assert max(errs) <= (1e-11 if precision == 64 else 1e-4), errs
+
+
 def test_uniform_positions_reproduce_the_uniform_grid():
     """Positions k dz given explicitly: the same steps as the handle without
     them (FP64, to rounding; the extrapolation multipliers are then
