@@ -57,6 +57,7 @@ extern "C" {
 #define MHD_ERR_NONFINITE (-4)  /* NaN/Inf detected in the state              */
 #define MHD_ERR_UNSUPPORTED (-5)/* valid but not built (e.g. FFT size)        */
 #define MHD_ERR_TIMEOUT (-6)    /* a bounded device wait gave up              */
+#define MHD_ERR_IO (-7)         /* a snapshot file could not be written       */
 
 #define MHD_MEM_DEVICE 0
 #define MHD_MEM_HOST 1
@@ -262,6 +263,40 @@ void mhd_destroy(mhd_handle h);
 /* Message of the last error of this handle (or of the last failed
  * mhd_create when h is NULL).  Never NULL. */
 const char* mhd_last_error(mhd_handle h);
+
+/* ---- snapshots in the layout of the paper's HDF5 files (Sect. 5.3) ----
+ *
+ * var.h5: a scalar FP64 dataset `time`; group `data` with one dataset per
+ * variable -- ax, ay, az, ux, uy, uz, lnrho, lnTT -- each of shape
+ * [nz+6][ny+6][nx+6] (x fastest, i.e. the Fortran order (x, y, z) in which
+ * the paper's files are read, the outer ghost layers kept), in the handle's
+ * precision; group `grid` (x, y, z positions of the padded box, dx, dy, dz
+ * with dz the mean vertical spacing, dx_1, dy_1, dz_1 the inverse spacing
+ * per point -- on a non-uniform z grid the inverse of dz/dk -- and Lx, Ly,
+ * Lz); group `settings` (`precision` = "S" or "D", nghost, nx, ny, nz, mx,
+ * my, mz).  grid.h5: the groups `grid` and `settings` alone.  ln rho, ln T
+ * and A are the full values (backgrounds added); x_i = (i - 3) dx, y alike,
+ * z the layer positions.  The files are written in the HDF5 format without
+ * the HDF5 library (superblock version 2, compact groups, contiguous
+ * datasets; readable by HDF5 1.8 and later).
+ *
+ * mhd_write_snapshot: fills the ghosts of the current state (as a step's
+ * first substep does), stages the padded state in the handle's RK
+ * accumulator buffer (unused between steps) and writes var_path and/or
+ * grid_path (either may be NULL, not both).  Synchronises the stream; one
+ * field at a time passes through host memory.  Errors: MHD_ERR_ARG,
+ * MHD_ERR_NONFINITE / MHD_ERR_TIMEOUT for a halted handle, MHD_ERR_CUDA,
+ * MHD_ERR_IO (file not writable; a partial file may remain).
+ *
+ * mhd_h5_write: the same files from host data without a handle: p as for
+ * mhd_create, t the time, padded the host state [8][nz+6][ny+6][nx+6] in
+ * p->precision (may be NULL when var_path is NULL).  No CUDA call.
+ *
+ * mhd_h5_checksum: the checksum these files carry (Jenkins' lookup3
+ * hashlittle with initial value 0) of len bytes at data; host only. */
+int mhd_write_snapshot(mhd_handle h, const char* var_path, const char* grid_path);
+int mhd_h5_write(const char* var_path, const char* grid_path, const mhd_params* p, double t, const void* padded);
+unsigned int mhd_h5_checksum(const void* data, size_t len);
 
 /* ---- diagnostics and kernel-level entry points (used by the tests) ---- */
 

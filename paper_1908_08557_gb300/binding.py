@@ -25,6 +25,7 @@ MHD_ERR_CUDA = -3
 MHD_ERR_NONFINITE = -4
 MHD_ERR_UNSUPPORTED = -5
 MHD_ERR_TIMEOUT = -6
+MHD_ERR_IO = -7
 MHD_MEM_DEVICE = 0
 MHD_MEM_HOST = 1
 NFIELD = 8
@@ -42,7 +43,7 @@ EXPORTED = ("mhd_workspace_bytes", "mhd_create", "mhd_set_driver", "mhd_step",
             "mhd_gran_velocity", "mhd_gran_read_granules", "mhd_gran_read_field", "mhd_gran_launch_count",
             "mhd_gran_last_error", "mhd_gran_destroy", "mhd_set_a_background",
             "mhd_debug_skip_copy", "mhd_read_plane", "mhd_fma_peak", "mhd_tape_bytes", "mhd_step_taped",
-            "mhd_adjoint_step_taped")
+            "mhd_adjoint_step_taped", "mhd_write_snapshot", "mhd_h5_write", "mhd_h5_checksum")
 KERNEL_CLASSES = ("ghost", "pfe", "cfl", "stats", "rk")
 
 
@@ -115,6 +116,10 @@ def load(path: Optional[str] = None):
     lib.mhd_debug_skip_copy.argtypes = [vp, i, i]
     lib.mhd_read_plane.argtypes = [vp, i, i, vp, i]
     lib.mhd_fma_peak.argtypes = [i, vp, vp, ctypes.POINTER(ctypes.c_double)]
+    lib.mhd_write_snapshot.argtypes = [vp, ctypes.c_char_p, ctypes.c_char_p]
+    lib.mhd_h5_write.argtypes = [ctypes.c_char_p, ctypes.c_char_p, P, d, vp]
+    lib.mhd_h5_checksum.argtypes = [vp, sz]
+    lib.mhd_h5_checksum.restype = ctypes.c_uint
     lib.mhd_tape_bytes.argtypes = [vp]
     lib.mhd_tape_bytes.restype = sz
     lib.mhd_step_taped.argtypes = [vp, vp]
@@ -165,7 +170,7 @@ def load(path: Optional[str] = None):
     lib.mhd_gran_destroy.argtypes = [vp]
     lib.mhd_gran_destroy.restype = None
     for name in EXPORTED:
-        if name not in ("mhd_workspace_bytes", "mhd_destroy", "mhd_last_error", "mhd_tape_bytes",
+        if name not in ("mhd_workspace_bytes", "mhd_destroy", "mhd_last_error", "mhd_tape_bytes", "mhd_h5_checksum",
                         "mhd_launch_count", "mhd_checkpoint_bytes", "mhd_gran_workspace_bytes",
                         "mhd_gran_launch_count", "mhd_gran_last_error", "mhd_gran_destroy"):
             getattr(lib, name).restype = ctypes.c_int
@@ -219,6 +224,35 @@ def fma_peak(precision: int, device: str = "cuda:0") -> float:
     if rc != MHD_OK:
         raise MHDError(rc, lib.mhd_last_error(None).decode())
     return out.value
+
+
+def _path(p) -> Optional[bytes]:
+    return None if p is None else os.fsencode(p)
+
+
+def h5_write(var_path, grid_path, params: Dict, t: float, padded=None, precision: int = 64):
+    """Snapshot files in the paper's HDF5 layout from host data
+    (mhd_h5_write): padded is the [8][nz+6][ny+6][nx+6] state in the given
+    precision (numpy), or None when only grid_path is written."""
+    lib = load()
+    q = make_params(params, precision)
+    keep = None
+    ptr = None
+    if padded is not None:
+        keep = np.ascontiguousarray(padded, dtype=np.float64 if precision == 64 else np.float32)
+        ng = NGHOST
+        if keep.shape != (NFIELD, q.nz + 2 * ng, q.ny + 2 * ng, q.nx + 2 * ng):
+            raise ValueError("padded must be [8][nz+6][ny+6][nx+6]")
+        ptr = ctypes.c_void_p(keep.ctypes.data)
+    rc = lib.mhd_h5_write(_path(var_path), _path(grid_path), ctypes.byref(q), float(t), ptr)
+    if rc != MHD_OK:
+        raise MHDError(rc, lib.mhd_last_error(None).decode())
+
+
+def h5_checksum(data: bytes) -> int:
+    """The lookup3 checksum the snapshot files carry (mhd_h5_checksum)."""
+    buf = ctypes.create_string_buffer(bytes(data), len(data))
+    return int(load().mhd_h5_checksum(buf, len(data)))
 
 
 def workspace_bytes(p: Dict, precision: int = 32, a_background: bool = False) -> int:
@@ -352,6 +386,11 @@ class Simulation:
         else:
             self._check(self.lib.mhd_read(self.h, int(field), ctypes.c_void_p(out.data_ptr()), MHD_MEM_DEVICE))
         return out
+
+    def write_snapshot(self, var_path=None, grid_path=None):
+        """var.h5 and/or grid.h5 of the current state in the paper's HDF5
+        layout (mhd_write_snapshot; fills the ghosts first)."""
+        self._check(self.lib.mhd_write_snapshot(self.h, _path(var_path), _path(grid_path)))
 
     def read_plane(self, field: int, k: int, out=None):
         """Layer k of one field, [ny][nx]; out: a numpy array (host) or a

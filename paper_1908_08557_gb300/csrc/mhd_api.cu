@@ -1183,6 +1183,55 @@ extern "C" int mhd_read_padded(mhd_handle h, int which, void* dst, int mem) {
   return MHD_OK;
 }
 
+extern "C" int mhd_write_snapshot(mhd_handle h, const char* var_path, const char* grid_path) {
+  if (!h) return fail(nullptr, MHD_ERR_ARG, "NULL handle");
+  if (!var_path && !grid_path) return fail(h, MHD_ERR_ARG, "no file path given");
+  double t, dt;
+  int rc = mhd_get_time(h, &t, &dt);  // synchronises; reports a halted handle
+  if (rc) return rc;
+  const Layout& L = h->L;
+  const size_t bytes = (size_t)L.mz * L.my * (L.nx + 2 * NG) * h->esz;
+  if (var_path) {
+    // outer ghosts consistent with the state, then the padded state with its
+    // backgrounds added, staged in the accumulator buffer (free between steps)
+    rc = mhd_fill_ghosts(h);
+    if (rc) return rc;
+    if (h->esz == 8) launch_pack_padded<double>(L, h->bgd, (const double*)h->f[h->cur], (double*)h->df, h->st);
+    else launch_pack_padded<float>(L, h->bgf, (const float*)h->f[h->cur], (float*)h->df, h->st);
+    rc = cuda_check(h, cudaStreamSynchronize(h->st), "stage padded state");
+    if (rc) return rc;
+  }
+  std::vector<char> host(var_path ? bytes : 0);
+  cudaError_t ce = cudaSuccess;
+  auto field = [&](int f, FILE* fp) -> bool {
+    ce = cudaMemcpyAsync(host.data(), (const char*)h->df + (size_t)f * bytes, bytes, cudaMemcpyDeviceToHost, h->st);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(h->st);
+    return ce == cudaSuccess && std::fwrite(host.data(), 1, bytes, fp) == bytes;
+  };
+  const int w = h5_write_snapshot(var_path, grid_path, &h->p, t, field);
+  if (ce != cudaSuccess) return cuda_check(h, ce, "copy snapshot field");
+  if (w) return fail(h, MHD_ERR_IO, "cannot write the snapshot files (%s, %s)", var_path ? var_path : "-",
+                     grid_path ? grid_path : "-");
+  return MHD_OK;
+}
+
+extern "C" int mhd_h5_write(const char* var_path, const char* grid_path, const mhd_params* p, double t,
+                            const void* padded) {
+  if (!p) return fail(nullptr, MHD_ERR_ARG, "NULL params");
+  const char* bad = check_params(p);
+  if (bad) return fail(nullptr, MHD_ERR_ARG, "%s", bad);
+  if (!var_path && !grid_path) return fail(nullptr, MHD_ERR_ARG, "no file path given");
+  if (var_path && !padded) return fail(nullptr, MHD_ERR_ARG, "NULL state");
+  const size_t bytes = (size_t)(p->nz + 2 * NG) * (p->ny + 2 * NG) * (p->nx + 2 * NG) * (p->precision == 64 ? 8 : 4);
+  auto field = [&](int f, FILE* fp) -> bool {
+    return std::fwrite((const char*)padded + (size_t)f * bytes, 1, bytes, fp) == bytes;
+  };
+  if (h5_write_snapshot(var_path, grid_path, p, t, field))
+    return fail(nullptr, MHD_ERR_IO, "cannot write the snapshot files (%s, %s)", var_path ? var_path : "-",
+                grid_path ? grid_path : "-");
+  return MHD_OK;
+}
+
 extern "C" int mhd_fill_ghosts(mhd_handle h) {
   if (!h) return fail(nullptr, MHD_ERR_ARG, "NULL handle");
   if (h->esz == 8) ghost_fill<double>(h, (double*)h->f[h->cur]);

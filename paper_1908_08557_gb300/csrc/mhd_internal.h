@@ -2,6 +2,8 @@
 #pragma once
 #include <atomic>
 #include <climits>
+#include <cstdio>
+#include <functional>
 #include <mutex>
 
 #include <cuda.h>
@@ -196,6 +198,16 @@ template <typename R> void launch_widen(const R* in, double* out, long long n, c
 // throughput probe: `iters` rounds of 8 independent FMA chains per thread
 // over grid x 256 threads, in R (instrumentation, not a step of the method)
 template <typename R> void launch_fma_probe(R* out, int grid, int iters, cudaStream_t st);
+
+// Snapshot files in the paper's HDF5 layout (mhd_h5.cu): var.h5 (time,
+// data/<variable> with outer ghosts, grid, settings) and grid.h5; either path
+// may be null.  field(f, fp) writes field f's [nz+6][ny+6][nx+6] values in
+// the handle's precision to fp.  0, or -1 on an I/O error.
+}  // namespace mhd
+struct mhd_params;
+namespace mhd {
+int h5_write_snapshot(const char* var_path, const char* grid_path, const mhd_params* p, double t,
+                      const std::function<bool(int, FILE*)>& field);
 // reductions
 // CFL block maxima by atomicMax into CFL_SLOTS slot pairs at `partial`
 // (zeroed first when `zero`); the planes: all, the inner ones whose stencils
