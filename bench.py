@@ -30,14 +30,18 @@ METRIC = "MHD cell-updates/s per RK step"
 UNIT = "cell-updates/s"
 WORDS_PER_CELL_STEP = 80  # algorithmic state words moved per cell per RK3 step
 RUNS = 5                  # timed runs of K steps; the median is reported
-# FP64 operations per cell and substep of rk_simple_kernel<double> (2 per
-# DFMA, 1 per DADD / DMUL), from the ncu instruction counts summarised in
+# FP64 operations per cell and substep of rk_simple_kernel<double> (2 flops
+# per DFMA, 1 per DADD / DMUL; each of the three one FP64-pipe instruction),
+# from the ncu instruction counts summarised in
 # profiles/rk_simple_fp64_flops_bipoles20_128x128x128.md
-FP64_FLOPS_PER_CELL_SUBSTEP = 1059.4
+FP64_FLOPS_PER_CELL_SUBSTEP = 1459.4
+FP64_PIPE_OPS_PER_CELL_SUBSTEP = 1022.3
 # FP32 operations per cell and substep of rk_pair_kernel (f32x2 instructions
-# one operation per cell, FFMA two flops), from the ncu instruction counts in
+# one operation per cell, FFMA two flops; FFMA, FADD and FMUL one FMA-pipe
+# lane operation each), from the ncu instruction counts in
 # profiles/rk_pair_fp32_flops_bipoles20_128x128x128.md
 FP32_FLOPS_PER_CELL_SUBSTEP = 1021.3
+FP32_PIPE_OPS_PER_CELL_SUBSTEP = 621.3
 RK_KERNEL = ("rk_pair_kernel (fused RHS + RK update, TMA z-march, two cells per thread in f32x2, "
              "z histories in TMEM)")
 
@@ -721,8 +725,12 @@ def run_native(args, ws, rank, local):
         from paper_1908_08557_gb300.binding import fma_peak
         peak32 = fma_peak(32, str(dev)) / 1e12
         ach32 = FP32_FLOPS_PER_CELL_SUBSTEP * cells / (rk_ms / rk_n / 1e3) / 1e12
+        # pipe occupancy: lane operations against the FMA rate (peak / 2)
+        ops32 = FP32_PIPE_OPS_PER_CELL_SUBSTEP * cells / (rk_ms / rk_n / 1e3) / 1e12
         roofline_alu = {"bound": "alu", "achieved": ach32, "peak": peak32, "unit": "TFLOP/s",
                         "frac": ach32 / peak32, "flops_per_cell_substep": FP32_FLOPS_PER_CELL_SUBSTEP,
+                        "pipe_ops_per_cell_substep": FP32_PIPE_OPS_PER_CELL_SUBSTEP,
+                        "pipe_frac": ops32 / (peak32 / 2),
                         "peak_source": "measured in this run (mhd_fma_peak, FP32 FMA chains)"}
     except Exception as exc:  # reported, not fatal
         roofline_alu = {"error": f"{type(exc).__name__}: {exc}"}
@@ -795,9 +803,13 @@ def run_native(args, ws, rank, local):
             peak64 = fma_peak(64, str(dev)) / 1e12
             rk64_ms, rk64_n = prof64["rk"]
             ach64 = FP64_FLOPS_PER_CELL_SUBSTEP * cells / (rk64_ms / rk64_n / 1e3) / 1e12
+            # pipe occupancy: DFMA, DADD and DMUL each take one FP64-pipe slot
+            ops64 = FP64_PIPE_OPS_PER_CELL_SUBSTEP * cells / (rk64_ms / rk64_n / 1e3) / 1e12
             fp64["roofline"] = {"bound": "alu", "achieved": ach64, "peak": peak64, "unit": "TFLOP/s",
                                 "frac": ach64 / peak64, "kernel": "rk_simple_kernel<double>",
                                 "flops_per_cell_substep": FP64_FLOPS_PER_CELL_SUBSTEP,
+                                "pipe_ops_per_cell_substep": FP64_PIPE_OPS_PER_CELL_SUBSTEP,
+                                "pipe_frac": ops64 / (peak64 / 2),
                                 "avg_launch_ms": rk64_ms / rk64_n,
                                 "peak_source": "measured in this run (mhd_fma_peak, FP64 FMA chains)"}
         except Exception as exc:  # reported, not fatal
