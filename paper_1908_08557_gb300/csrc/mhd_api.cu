@@ -595,6 +595,20 @@ static void launch_rk_any(mhd_ctx* h, const R* fin, R* fout, int sub, const CUte
                h->st);
 }
 
+// CFL maxima over the inner layers (k = 3 .. nz - 4) of fin: the z-march
+// kernel for the FP32 state sets, else the plane-parallel one
+template <typename R>
+static void cfl_inner(mhd_ctx* h, const R* fin, bool zero) {
+  Phys<R> ph = make_phys<R>(&h->p);
+  if (sizeof(R) == 4 && h->pair && ((const void*)fin == h->f[0] || (const void*)fin == h->f[1])) {
+    const int which = (const void*)fin == h->f[0] ? 0 : 1;
+    launch_cfl_inner_zm(&h->tma[which], h->L, *(const Phys<float>*)&ph, h->bgf, (const float*)fin,
+                        (const float*)h->wtab, h->cfl, h->ss, zero, h->st);
+    return;
+  }
+  launch_cfl_partial<R>(h->L, ph, bgr<R>(h), fin, (const R*)h->wtab, h->cfl, h->ss, CflPlanes::inner, zero, h->st);
+}
+
 template <typename R>
 static void run_step(mhd_ctx* h, bool stats) {
   Phys<R> ph = make_phys<R>(&h->p);
@@ -622,8 +636,7 @@ static void run_step(mhd_ctx* h, bool stats) {
       }
       {
         ClassTimer ct(h, MHD_KC_CFL, 1);
-        launch_cfl_partial<R>(h->L, ph, bgr<R>(h), fin, (const R*)h->wtab, h->cfl, h->ss, CflPlanes::inner, true,
-                              h->st);
+        cfl_inner<R>(h, fin, true);
       }
       cudaStreamWaitEvent(h->st, h->evj, 0);
       if (stats) run_stats<R>(h, fin);
@@ -636,11 +649,17 @@ static void run_step(mhd_ctx* h, bool stats) {
       ghost_fill<R>(h, fin);
       if (sub == 0) {
         if (stats) run_stats<R>(h, fin);
-        ClassTimer ct(h, MHD_KC_CFL, adaptive ? 2 : 1);
+        const bool zmarch = adaptive && sizeof(R) == 4 && h->pair && h->L.nz > 2 * NG;
+        ClassTimer ct(h, MHD_KC_CFL, zmarch ? 3 : (adaptive ? 2 : 1));
         int nb = 0;
-        if (adaptive)
+        if (zmarch) {
+          cfl_inner<R>(h, fin, true);
+          nb = launch_cfl_partial<R>(h->L, ph, bgr<R>(h), fin, (const R*)h->wtab, h->cfl, h->ss, CflPlanes::ends,
+                                     false, h->st);
+        } else if (adaptive) {
           nb = launch_cfl_partial<R>(h->L, ph, bgr<R>(h), fin, (const R*)h->wtab, h->cfl, h->ss, CflPlanes::all,
                                      true, h->st);
+        }
         launch_cfl_finalize(h->cfl, nb, h->ss, h->p.c_adv, h->p.c_diff, h->p.dt_fixed, inv2sum(&h->p), h->t0,
                             h->t1, h->p.t_ramp, 0, h->st);
       }

@@ -217,6 +217,11 @@ enum class CflPlanes { all, inner, ends };
 template <typename R> int launch_cfl_partial(const Layout& L, const Phys<R>& ph, const Background<R>& bg,
                                              const R* f, const R* wtab, double* partial, StepState* ss,
                                              CflPlanes planes, bool zero, cudaStream_t st);
+// the same maxima over the inner layers for the FP32 state as a TMA-fed
+// z-march (mhd_cfl_zm.cu); tma: the state set's boxes of A (40 x 14 x 3)
+int launch_cfl_inner_zm(const CUtensorMap* tma, const Layout& L, const Phys<float>& ph, const Background<float>& bg,
+                        const float* f, const float* wtab, double* partial, StepState* ss, bool zero,
+                        cudaStream_t st);
 void launch_cfl_finalize(const double* partial, int nblk, StepState* ss, double c_adv, double c_diff,
                          double dt_fixed, double inv2sum, double t0, double t1, double t_ramp, int probe,
                          cudaStream_t st);

@@ -508,3 +508,37 @@ def test_production_geometry_1024_sampled(prec):
         err = np.abs(g[:, f] - ref[:, f])
         worst = int(np.argmax(err))
         assert err[worst] <= tol * max(s, 1e-30), (f, err[worst], s)
+
+
+@pytest.mark.parametrize("variant", ["plain", "ragged", "background", "zgrid"])
+def test_in_step_cfl_equals_standalone_fp32(variant):
+    """The step's CFL reduction on the FP32 state (the TMA-fed z-march over
+    the inner layers, the plane-parallel kernel over the three layers at each
+    end) gives the time step of the standalone plane-parallel reduction over
+    all layers bit for bit: same arithmetic per cell, order-independent
+    maxima.  A tile ragged in x (nx = 16) and ragged z chunks; A about a
+    background (its B added per cell); a stretched grid (metric per layer)."""
+    from paper_1908_08557_gb300 import Simulation
+    kw = {}
+    if variant == "zgrid":
+        z, _, _ = inputs.stretched_z(40, 0.5, 1.5, 20, 4)
+        case = _perturbed(32, 16, 40, seed=81, z=z, magnetogram="bipoles", n_mag=6)
+    elif variant == "ragged":
+        case = _perturbed(16, 16, 37, seed=82, magnetogram="bipoles", n_mag=6)
+    else:
+        case = _perturbed(64, 32, 41, seed=83, magnetogram="bipoles", n_mag=6)
+    if variant == "background":
+        kw["a_background"] = case.state[0:3] - 0.003
+    T = lambda a: torch.tensor(a, dtype=torch.float32, device="cuda")
+    sim = Simulation(case.params, T(case.state), case.lnrho0, case.lnT0, precision=32, **kw)
+    if variant == "background":
+        sim.set_a_background(kw["a_background"], T(np.full(case.state[0:3].shape, 0.003)))
+    sim.set_driver(T(case.bz), T(case.v0), T(case.v1), case.t0, case.t1)
+    for _ in range(3):
+        sim.fill_ghosts()
+        dt0 = sim.compute_dt()
+        t0 = sim.time()[0]
+        sim.step(1)
+        t1, dt1 = sim.time()
+        assert dt1 == dt0 and t1 == t0 + dt0, (dt0, dt1)
+    sim.close()
