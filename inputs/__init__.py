@@ -334,6 +334,12 @@ WORKLOADS = {
     # (then the same growth sets in), so gradients use 600 steps
     "bipoles100_512x512x256": dict(nx=512, ny=512, nz=256, magnetogram="bipoles",
                                    n_mag=100, driver="solenoidal", nsteps=600, bz_scale=1.0 / 3.0),
+    # the production recipe's 1024^2 planes on 16 layers: profiler captures of
+    # the potential-field FFT at full plane size with a few GB on the device
+    "ar_1024x1024x16": dict(nx=1024, ny=1024, nz=16, dx=4.0, dy=4.0,
+                            magnetogram="bipoles", n_mag=400,
+                            ar_pair=(5.0, 40.0, 200.0), driver="solenoidal",
+                            nsteps=1000),
     # the 256^3 recipe at an eighth of the volume: profiler captures of the
     # adjoint kernels (coefficient fields 0.34 GB, above the 129 MB L2)
     "bipoles20_128x128x128": dict(nx=128, ny=128, nz=128, magnetogram="bipoles",
