@@ -323,13 +323,14 @@ def adjoint_ratios(case, dev, ws):
     return out
 
 
-def adjoint_scale_line(dev, steps, iters):
+def adjoint_scale_line(dev, steps, iters, slots=None, k=48, descend=True):
     """bipoles100_512x512x256, FP32, frozen dt: the B_z misfit on layer 48
     after `steps` steps against a target made by a forward run driven by a
     different seeded 100-bipole magnetogram and driver; its gradient with
     respect to (B_z, v0, v1) by the adjoint under binomial checkpointing with
-    slots from a 120 GB state budget; `iters` gradient-descent steps (step
-    length a quarter of loss / |g|^2, halved once if the loss rises)."""
+    slots from a 120 GB state budget (or the given slot count); `iters`
+    gradient evaluations, each followed (descend) by a gradient-descent step
+    (step length a quarter of loss / |g|^2, halved once if the loss rises)."""
     import numpy as np
     import torch
 
@@ -340,12 +341,14 @@ def adjoint_scale_line(dev, steps, iters):
     ct = inputs.make_case("bipoles100_512x512x256", seed=1, dtype=np.float32)
     steps = steps or c.nsteps
     p = dict(c.params, dt_fixed=0.017)
-    k = 48
     T = lambda a: torch.tensor(a, dtype=torch.float32, device=dev)
     sim = Simulation(p, T(c.state), c.lnrho0, c.lnT0, precision=32, adjoint=True, device=str(dev))
     state0 = sim.read().clone()
     budget = 120 * 2**30
-    slots = int(max(1, min(steps - 1, budget // sim.checkpoint_bytes() - 1)))
+    if slots is None:
+        slots = int(max(1, min(steps - 1, budget // sim.checkpoint_bytes() - 1)))
+    else:
+        budget = (slots + 1) * sim.checkpoint_bytes()
 
     def run(bz, v0, v1):
         sim.set_driver(bz, v0, v1, c.t0, c.t1)
@@ -372,6 +375,10 @@ def adjoint_scale_line(dev, steps, iters):
         lossv = 0.5 * ((BzPlane.apply(box["st"], sim, k) - target) ** 2).sum()
         rev = _cuda_ms(sim.stream, lambda: lossv.backward())
         g = [q.grad.detach() for q in leaves]
+        if not descend:
+            hist.append({"loss": float(lossv.detach()), "forward_with_checkpoints_ms": fwd_ck, "reverse_ms": rev,
+                         "ratio": rev / fwd_ms})
+            continue
         g2 = sum(float((x.double() ** 2).sum()) for x in g)
         eta = 0.25 * float(lossv.detach()) / max(g2, 1e-300)
         trial = [q - eta * x for q, x in zip(params, g)]
@@ -384,7 +391,9 @@ def adjoint_scale_line(dev, steps, iters):
                      "ratio": rev / fwd_ms, "loss_after_step": new})
         params, loss = trial, new
     out["iterations"] = hist
-    out["loss_reduction"] = hist[0]["loss"] / loss if hist else None
+    out["layer"] = k
+    if descend:
+        out["loss_reduction"] = hist[0]["loss"] / loss if hist else None
     out["recompute_fraction"] = _revolve_recompute(steps, slots) / steps
     sim.close()
     del sim
@@ -825,6 +834,17 @@ def run_native(args, ws, rank, local):
     adj = None
     if not args.no_adjoint:
         adj = adjoint_ratios(case, dev, ws)
+        # the checkpointed regime at 512 x 512 x 256, bounded: 100 steps with
+        # 12 slots recompute 0.87 of the steps, as 1000 steps do with the 56
+        # slots of a 120 GB budget (0.94); one gradient-descent step
+        try:
+            sample = adjoint_scale_line(dev, 100, 1, slots=12, k=8, descend=False)
+            sample["sample"] = ("one gradient of the B_z misfit on layer 8 after 100 of the workload's steps, 12 "
+                                "checkpoint slots (recompute fraction close to that of 1000 steps under the 120 GB "
+                                "budget); --adjoint-scale runs 600 steps with descent on layer 48")
+            adj["bipoles100_512x512x256_sample"] = sample
+        except Exception as exc:  # reported, not fatal
+            adj["bipoles100_512x512x256_sample"] = {"error": f"{type(exc).__name__}: {exc}"}
 
     # production size 1024 x 1024 x 256 (FP32, horizontal spacing 4x vertical)
     prod = None
