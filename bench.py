@@ -72,6 +72,8 @@ def parse():
     ap.add_argument("--drift-steps", type=int, default=100)
     ap.add_argument("--no-granulation", action="store_true",
                     help="skip timing the granulation driver on a 1024 x 1024 plane (Sect. 2.3)")
+    ap.add_argument("--snapshot", action="store_true",
+                    help="also time mhd_write_snapshot (var.h5 + grid.h5) of a 1024 x 1024 x 64 FP32 box")
     ap.add_argument("--cooling", action="store_true",
                     help="Newtonian cooling on (rate 0.5, height cut-off at 10 dz) in the throughput leg")
     return ap.parse_args()
@@ -473,6 +475,39 @@ def granulation_line(dev, n=1024, dt=10.0, t_end=600.0):
     return out
 
 
+def snapshot_line(dev):
+    """mhd_write_snapshot of a 1024 x 1024 x 64 FP32 box of the production
+    recipe after two steps: var.h5 (8 fields with the outer ghosts, grid,
+    settings, time) and grid.h5 into a temporary directory of the host, the
+    ghost fill and the device-to-host copies included (wall clock, the
+    stream synchronised before; the files are not synced to disk, so the
+    rate is that of the host's page cache)."""
+    import torch
+
+    import inputs
+    from paper_1908_08557_gb300 import Simulation
+    c = inputs.make_box(1024, 1024, 64, seed=0, dx=4.0, dy=4.0, magnetogram="bipoles", n_mag=400,
+                        ar_pair=(5.0, 40.0, 200.0), driver="solenoidal")
+    T = lambda a: torch.tensor(a, dtype=torch.float32, device=dev)
+    sim = Simulation(c.params, T(c.state), c.lnrho0, c.lnT0, precision=32, device=str(dev))
+    sim.set_driver(T(c.bz), T(c.v0), T(c.v1), c.t0, c.t1)
+    sim.step(2)
+    torch.cuda.synchronize()
+    out = {}
+    with tempfile.TemporaryDirectory() as d:
+        var, grid = os.path.join(d, "var.h5"), os.path.join(d, "grid.h5")
+        t0 = time.perf_counter()
+        sim.write_snapshot(var, grid)
+        sec = time.perf_counter() - t0
+        size = os.path.getsize(var) + os.path.getsize(grid)
+        out = {"box": "1024x1024x64 (padded 1030x1030x70), FP32", "seconds": sec, "bytes": size,
+               "gb_per_s": size / sec / 1e9, "sync": "not synced to disk (page cache)"}
+    sim.close()
+    del sim
+    torch.cuda.empty_cache()
+    return out
+
+
 def production_line(dev, ws):
     """Workload ar_1024x1024x256 in FP32, timed twice: with A stored about the
     FP64 initial potential field (a_background, the configuration that meets
@@ -858,6 +893,13 @@ def run_native(args, ws, rank, local):
         except Exception as exc:  # reported, not fatal: the run is optional
             drift = {"error": f"{type(exc).__name__}: {exc}"}
 
+    snap = None
+    if args.snapshot:
+        try:
+            snap = snapshot_line(dev)
+        except Exception as exc:  # reported, not fatal: the run is optional
+            snap = {"error": f"{type(exc).__name__}: {exc}"}
+
     gran = None
     if not args.no_granulation:
         try:
@@ -904,6 +946,8 @@ def run_native(args, ws, rank, local):
             line["drift_ar_1024x1024x256"] = drift
         if gran is not None:
             line["granulation_1024x1024"] = gran
+        if snap is not None:
+            line["snapshot"] = snap
         print(json.dumps(line), flush=True)
 
 
