@@ -510,7 +510,7 @@ def test_production_geometry_1024_sampled(prec):
         assert err[worst] <= tol * max(s, 1e-30), (f, err[worst], s)
 
 
-@pytest.mark.parametrize("variant", ["plain", "ragged", "background", "zgrid"])
+@pytest.mark.parametrize("variant", ["plain", "ragged", "background", "zgrid", "thin7", "thin8"])
 def test_in_step_cfl_equals_standalone_fp32(variant):
     """The step's CFL reduction on the FP32 state (the TMA-fed z-march over
     the inner layers, the plane-parallel kernel over the three layers at each
@@ -525,6 +525,9 @@ def test_in_step_cfl_equals_standalone_fp32(variant):
         case = _perturbed(32, 16, 40, seed=81, z=z, magnetogram="bipoles", n_mag=6)
     elif variant == "ragged":
         case = _perturbed(16, 16, 37, seed=82, magnetogram="bipoles", n_mag=6)
+    elif variant.startswith("thin"):
+        # the thinnest boxes (nz >= 7): one and two inner layers
+        case = _perturbed(32, 16, int(variant[4:]), seed=84, magnetogram="bipoles", n_mag=6)
     else:
         case = _perturbed(64, 32, 41, seed=83, magnetogram="bipoles", n_mag=6)
     if variant == "background":
