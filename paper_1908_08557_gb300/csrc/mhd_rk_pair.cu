@@ -114,7 +114,8 @@ __device__ __forceinline__ void tm_wait_st() { asm volatile("tcgen05.wait::st.sy
 
 // ---- a packed pair of FP32 numbers with the arithmetic the templated
 // pointwise adjoint uses (each operation one f32x2 instruction, or two
-// scalar ones for division and exp) --------------------------------------
+// scalar ones for division and exp: the hardware approximations, as in the
+// forward mode) -------------------------------------------------------------
 struct P2 {
   f2 v;
   __device__ __forceinline__ P2() {}
@@ -129,10 +130,12 @@ __device__ __forceinline__ P2 operator+(P2 a, P2 b) { return P2(add(a.v, b.v)); 
 __device__ __forceinline__ P2 operator-(P2 a, P2 b) { return P2(dif(a.v, b.v)); }
 __device__ __forceinline__ P2 operator*(P2 a, P2 b) { return P2(mul(a.v, b.v)); }
 __device__ __forceinline__ P2 operator-(P2 a) { return P2(mul(a.v, F2(-1.f))); }
-__device__ __forceinline__ P2 operator/(P2 a, P2 b) { return P2(make_float2(a.v.x / b.v.x, a.v.y / b.v.y)); }
+__device__ __forceinline__ P2 operator/(P2 a, P2 b) {
+  return P2(make_float2(__fdividef(a.v.x, b.v.x), __fdividef(a.v.y, b.v.y)));
+}
 }  // namespace pair
 template <> __device__ __forceinline__ pair::P2 rexp<pair::P2>(pair::P2 x) {
-  return pair::P2(make_float2(expf(x.v.x), expf(x.v.y)));
+  return pair::P2(make_float2(__expf(x.v.x), __expf(x.v.y)));
 }
 namespace pair {
 
