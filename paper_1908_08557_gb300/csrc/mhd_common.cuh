@@ -115,7 +115,7 @@ struct StepState {
   double probe_dt;         // time step computed without advancing time
   long long step;
   int nonfinite;
-  int pad_;
+  int items;         // work-item counter of the z-march launches (zeroed before each)
 };
 
 // Low-storage RK3 of Williamson (1980): alpha, beta, c per substep.

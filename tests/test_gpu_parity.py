@@ -411,6 +411,20 @@ def test_tiled_kernel_matches_simple_fp32(shape, bcz, variant):
         assert np.abs(a[f] - b[f]).max() <= 2e-5 * max(s, 1e-30), f
 
 
+def test_pair_kernel_with_claimed_work_items():
+    """A launch with a dozen or more work items per CTA (1024 x 1024 x 16:
+    4096 tiles of one z chunk each on 304 CTAs) claims its items from a
+    counter instead of taking them by grid stride; the right-hand side
+    equals the one-thread-per-cell kernel's to the same tolerance."""
+    case = _perturbed(1024, 1024, 16, seed=12, magnetogram="bipoles", n_mag=40)
+    a, ua = _eval_with_variant(case, "pair")
+    b, ub = _eval_with_variant(case, "simple")
+    assert np.array_equal(ua, ub)
+    for f in range(8):
+        s = np.abs(b[f]).max()
+        assert np.abs(a[f] - b[f]).max() <= 2e-5 * max(s, 1e-30), f
+
+
 def test_tiled_full_size_sampled_bipoles40_256():
     """Bench workload bipoles40_256x256x256 in the bench configuration (FP32,
     the default z-march kernel rk_pair_kernel): ghost fill + RHS at 3000 sampled cells -- random, plus the
