@@ -344,6 +344,11 @@ WORKLOADS = {
     # adjoint kernels (coefficient fields 0.34 GB, above the 129 MB L2)
     "bipoles20_128x128x128": dict(nx=128, ny=128, nz=128, magnetogram="bipoles",
                                   n_mag=20, driver="solenoidal", nsteps=200),
+    # the 256^3 recipe's planes on 64 layers: profiler captures of the adjoint
+    # kernels with the 256^2 tiling and work-item count per chunk of the
+    # 256^3 box (coefficient fields 0.67 GB; about 2.5 GB on the device)
+    "bipoles40_256x256x64": dict(nx=256, ny=256, nz=64, magnetogram="bipoles",
+                                 n_mag=40, driver="solenoidal", nsteps=200),
 }
 
 
