@@ -537,10 +537,12 @@ __global__ void __launch_bounds__(NTP, 2) gather_pair_kernel(PArgs pa_) {
   const int nzo = a.L.nz + 2 * NG;
   const int tiles = a.ntx * a.nty;
   const int nitems = tiles * a.nch * 2;
+  // items group-major within a z chunk: the CTAs running together hold all
+  // tiles of one output group, whose halo planes they share in L2
   for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
-    const int grp = item & 1;
-    const int rest = item >> 1;
-    const int ch = rest / tiles, tile = rest % tiles;
+    const int ch = item / (2 * tiles), r = item - ch * 2 * tiles;
+    const int grp = r >= tiles ? 1 : 0;
+    const int tile = r - grp * tiles;
     const int x0 = (tile % a.ntx) * TX, y0 = (tile / a.ntx) * TY;
     const int n0 = ch * a.kchunk - NG, n1 = min(nzo, (ch + 1) * a.kchunk) - NG;
     __syncthreads();
