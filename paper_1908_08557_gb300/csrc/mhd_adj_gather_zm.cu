@@ -338,6 +338,7 @@ __device__ __forceinline__ f2 dy1(const float* p, const Coef& c) {
 struct PArgs {
   ZArgs<float> z;
   Coef cx, cy;  // D1, D2 weights over dx, dy
+  int dyn;      // items claimed from the step state's counter (else grid stride)
 };
 
 // Staged fields.  Only the coefficients whose in-plane stencils the gather
@@ -538,8 +539,19 @@ __global__ void __launch_bounds__(NTP, 2) gather_pair_kernel(PArgs pa_) {
   const int tiles = a.ntx * a.nty;
   const int nitems = tiles * a.nch * 2;
   // items group-major within a z chunk: the CTAs running together hold all
-  // tiles of one output group, whose halo planes they share in L2
-  for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
+  // tiles of one output group, whose halo planes they share in L2.  With
+  // several items per CTA (dyn) each CTA claims its next item from the step
+  // state's counter as it starts one (the claim is handed to the CTA at the
+  // end-of-item barrier), so that CTAs meeting dearer items (the x, y edges'
+  // wrapped halos, the update layers) do not hold up the launch.
+  __shared__ int s_next;
+  if (pa_.dyn) {
+    if (threadIdx.x == 0) s_next = atomicAdd(&a.ss->items, 1);
+    __syncthreads();
+  }
+  for (int item = pa_.dyn ? s_next : (int)blockIdx.x; item < nitems;) {
+    int next = 0;
+    if (pa_.dyn && threadIdx.x == 0) next = atomicAdd(&a.ss->items, 1);
     const int ch = item / (2 * tiles), r = item - ch * 2 * tiles;
     const int grp = r >= tiles ? 1 : 0;
     const int tile = r - grp * tiles;
@@ -550,6 +562,14 @@ __global__ void __launch_bounds__(NTP, 2) gather_pair_kernel(PArgs pa_) {
       item_pair<0>(pa_, buf, scr, x0, y0, n0, n1);
     else
       item_pair<1>(pa_, buf, scr, x0, y0, n0, n1);
+    if (pa_.dyn) {
+      __syncthreads();
+      if (threadIdx.x == 0) s_next = next;
+      __syncthreads();
+      item = s_next;
+    } else {
+      item += gridDim.x;
+    }
   }
 }
 }  // namespace zp
@@ -612,7 +632,10 @@ void launch_adj_gather_zm(const Layout& L, const Phys<R>& ph, const R* coef, R* 
     pa.cx = coef(1.0 / (double)ph.idx);
     pa.cy = coef(1.0 / (double)ph.idy);
     const int pitems = 2 * tiles * a.nch;
-    gzm::zp::gather_pair_kernel<<<pitems < pctas ? pitems : pctas, gzm::zp::NTP, psmem, st>>>(pa);
+    const int pgrid = pitems < pctas ? pitems : pctas;
+    pa.dyn = pitems >= 4 * pgrid;
+    if (pa.dyn) cudaMemsetAsync(&ss->items, 0, sizeof(int), st);
+    gzm::zp::gather_pair_kernel<<<pgrid, gzm::zp::NTP, psmem, st>>>(pa);
     return;
   }
   gzm::gather_zm_kernel<R><<<nitems < ctas ? nitems : ctas, gzm::NT, smem, st>>>(a);

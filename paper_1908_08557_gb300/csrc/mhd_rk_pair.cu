@@ -422,7 +422,10 @@ __global__ void __launch_bounds__(NT, 2) rk_pair_kernel(const __grid_constant__ 
   // it finishes one, so CTAs that meet dearer items (images at the x, y
   // edges, swamp layers) do not hold up the launch.  Thread 0 claims the
   // following item when it starts one; the claim is handed to the CTA at the
-  // end-of-item barrier.
+  // end-of-item barrier.  Item order: chunk-fastest (all z chunks of a tile
+  // in flight together) for the forward launches by grid stride;
+  // tile-fastest (the CTAs running together cover whole rows of tiles of one
+  // chunk) for the adjoint and for claimed items, where it measured faster.
   __shared__ int s_next;
   if (a.dyn) {
     if (tid == 0) s_next = atomicAdd(&a.ss->items, 1);
@@ -431,7 +434,10 @@ __global__ void __launch_bounds__(NT, 2) rk_pair_kernel(const __grid_constant__ 
   for (int item = a.dyn ? s_next : (int)blockIdx.x; item < nitems && !bad;) {
     int next = 0;
     if (a.dyn && tid == 0) next = atomicAdd(&a.ss->items, 1);
-    const int ch = item % a.nch, tile = item / a.nch;
+    const int tiles = a.ntx * a.nty;
+    const bool tile_fast = ADJ || a.dyn;
+    const int ch = tile_fast ? item / tiles : item % a.nch;
+    const int tile = tile_fast ? item - ch * tiles : item / a.nch;
     const int x0 = (tile % a.ntx) * TX, y0 = (tile / a.ntx) * TY;
     const int k0 = ch * a.kchunk, k1 = min(L.nz, k0 + a.kchunk);
     const int pbase = k0 - NG, plast = k1 + NG - 1;
