@@ -319,3 +319,17 @@ def test_tiled_gather_matches_simple(shape, prec, variant):
     for name in ("lam", "bz", "v0", "v1"):
         s = np.abs(b[name]).max()
         assert np.abs(a[name] - b[name]).max() <= tol * max(s, 1e-30), name
+
+
+def test_gather_with_claimed_work_items_matches_simple():
+    """256^3 in FP32: the gather has 2048 work items for the 304 resident CTAs
+    of a GB300, so each CTA claims its items from the step state's counter
+    (and the point kernel's items run tile-fastest); the result against the
+    one thread per point kernels, as in the smaller cases above."""
+    case = _case(256, 256, 256, seed=14)
+    lam = np.random.default_rng(15).standard_normal((8, 256, 256, 256))
+    a = _adjoint_with_variant(case, 32, "tiled", lam)
+    b = _adjoint_with_variant(case, 32, "simple", lam)
+    for name in ("lam", "bz", "v0", "v1"):
+        s = np.abs(b[name]).max()
+        assert np.abs(a[name] - b[name]).max() <= 1e-5 * max(s, 1e-30), name
