@@ -152,3 +152,49 @@ def test_granulation_argument_errors(lib):
     assert lib.mhd_gran_read_field(None, 0, None, 0) == binding.MHD_ERR_ARG
     assert lib.mhd_gran_launch_count(None) == 0
     lib.mhd_gran_destroy(None)
+
+
+def test_null_handle_is_an_argument_error(lib):
+    """Every entry point that takes a handle (or a granulation generator)
+    answers a NULL one with MHD_ERR_ARG before touching the device: size and
+    count queries with 0, the error-message queries with a message, the
+    destroy calls with nothing.  Argument types follow the header."""
+    from paper_1908_08557_gb300 import binding
+    own = ctypes.CDLL(lib._name)  # own function objects: the binding's argtypes stay as they are
+    src = open(os.path.join(ROOT, "include", "mhd.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    src = re.sub(r"//[^\n]*", "", src)
+    decls = re.findall(r"([A-Za-z_][\w\s\*]*?)\b(mhd_[a-z_0-9]+)\s*\(([^;{]*?)\)\s*;", src, flags=re.S)
+
+    def arg(a):
+        a = a.strip()
+        if "*" in a or a.startswith(("mhd_handle", "mhd_gran_handle")):
+            return ctypes.c_void_p, None
+        if a.startswith("double"):
+            return ctypes.c_double, 0.0
+        if a.startswith("size_t"):
+            return ctypes.c_size_t, 0
+        if a.startswith("long long"):
+            return ctypes.c_longlong, 0
+        return ctypes.c_int, 0
+
+    seen = 0
+    for ret, name, args in decls:
+        params = [x for x in " ".join(args.split()).split(",") if x.strip()]
+        if not params or not params[0].strip().startswith(("mhd_handle", "mhd_gran_handle")):
+            continue
+        f = getattr(own, name)
+        spec = [arg(p) for p in params]
+        f.argtypes = [t for t, _ in spec]
+        r = " ".join(ret.split())
+        kind = "msg" if "char" in r else "size" if r in ("size_t", "long long") else "void" if r == "void" else "rc"
+        f.restype = {"msg": ctypes.c_char_p, "size": ctypes.c_longlong, "void": None, "rc": ctypes.c_int}[kind]
+        out = f(*[v for _, v in spec])
+        if kind == "rc":
+            assert out == binding.MHD_ERR_ARG, (name, out)
+        elif kind == "size":
+            assert out == 0, (name, out)
+        elif kind == "msg":
+            assert out, name
+        seen += 1
+    assert seen >= 35
